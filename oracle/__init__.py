@@ -1,0 +1,130 @@
+"""Plain FP64 CPU oracle of the linear ADER-DG Space-Time Predictor.
+
+TEST INFRASTRUCTURE ONLY: the tests, the smoke check and the benchmark's
+CPU-baseline leg are the only callers. The product path (the CUDA library and
+its binding) never imports this package, and this package imports nothing from
+the product.
+
+The arithmetic lives in ``stp_oracle.c`` (plain C, one element at a time,
+dense 9x9 operators, no blocking or fusion); this module compiles it with gcc
+and marshals numpy arrays into it. See the header of ``stp_oracle.c`` for the
+paper's equations it follows and the readings taken where the paper is silent.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "stp_oracle.c")
+_OUT_DIR = os.path.join(_HERE, "_build")
+_LIB_PATH = os.path.join(_OUT_DIR, "liboracle_stp.so")
+_lock = threading.Lock()
+_lib = None
+
+M = 9  # quantities of the elastic system
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle into ``oracle/_build/liboracle_stp.so`` with gcc.
+
+    -O3 with -ffp-contract=off keeps plain IEEE binary64 arithmetic (no fused
+    multiply-add contraction), so x86 and Arm hosts round identically.
+    OpenMP only spreads independent elements over threads.
+    """
+    os.makedirs(_OUT_DIR, exist_ok=True)
+    if (not force and os.path.exists(_LIB_PATH)
+            and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC)):
+        return _LIB_PATH
+    tmp = _LIB_PATH + f".tmp{os.getpid()}"
+    cmd = ["gcc", "-O3", "-std=c11", "-ffp-contract=off", "-fno-fast-math",
+           "-fPIC", "-shared", "-fopenmp", _SRC, "-o", tmp, "-lm"]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            build()
+            lib = ctypes.CDLL(_LIB_PATH)
+            dp = ctypes.POINTER(ctypes.c_double)
+            lib.oracle_gl_nodes.argtypes = [ctypes.c_int, dp, dp]
+            lib.oracle_gl_nodes.restype = ctypes.c_int
+            lib.oracle_tables.argtypes = [ctypes.c_int, dp, dp, dp, dp]
+            lib.oracle_tables.restype = ctypes.c_int
+            lib.oracle_stp.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int64,
+                                       ctypes.c_double, ctypes.c_double,
+                                       ctypes.c_void_p, ctypes.c_void_p,
+                                       ctypes.c_void_p, ctypes.c_void_p,
+                                       ctypes.c_void_p]
+            lib.oracle_stp.restype = ctypes.c_int
+            lib.oracle_num_threads.argtypes = []
+            lib.oracle_num_threads.restype = ctypes.c_int
+            _lib = lib
+    return _lib
+
+
+def _dptr(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def gl_nodes(N: int):
+    """Gauss-Legendre nodes and weights on [0,1] (ascending)."""
+    xi = np.zeros(N)
+    w = np.zeros(N)
+    if _load().oracle_gl_nodes(N, _dptr(xi), _dptr(w)) != 0:
+        raise ValueError(f"oracle_gl_nodes failed for N={N}")
+    return xi, w
+
+
+def tables(N: int):
+    """(xi, D, phi0, phi1): nodes, D[i,j] = phi_j'(xi_i), phi_j(0), phi_j(1)."""
+    xi = np.zeros(N)
+    D = np.zeros((N, N))
+    p0 = np.zeros(N)
+    p1 = np.zeros(N)
+    if _load().oracle_tables(N, _dptr(xi), _dptr(D), _dptr(p0), _dptr(p1)) != 0:
+        raise ValueError(f"oracle_tables failed for N={N}")
+    return xi, D, p0, p1
+
+
+def num_threads() -> int:
+    """OpenMP threads the oracle uses (OMP_NUM_THREADS, else all cores)."""
+    return int(_load().oracle_num_threads())
+
+
+def stp(q: np.ndarray, params: np.ndarray, h: float, dt: float, K: int | None = None,
+        return_terms: bool = False):
+    """Run the oracle STP.
+
+    q: [E][N][N][N][9] float64 (z,y,x,quantity); params: [E][N][N][N][3]
+    (rho, cp, cs). K = number of Taylor terms q^(0..K-1), default N+1.
+    Returns (avg [E][N][N][N][9], faces [E][6][N][N][9]) and, with
+    return_terms, every q^(k) as [E][K][N][N][N][9].
+    """
+    q = np.ascontiguousarray(q, dtype=np.float64)
+    params = np.ascontiguousarray(params, dtype=np.float64)
+    if q.ndim != 5 or q.shape[4] != M or not (q.shape[1] == q.shape[2] == q.shape[3]):
+        raise ValueError(f"q must be [E][N][N][N][9], got {q.shape}")
+    E, N = q.shape[0], q.shape[1]
+    if params.shape != (E, N, N, N, 3):
+        raise ValueError(f"params must be {(E, N, N, N, 3)}, got {params.shape}")
+    K = N + 1 if K is None else int(K)
+    avg = np.empty_like(q)
+    faces = np.empty((E, 6, N, N, M))
+    terms = np.empty((E, K, N, N, N, M)) if return_terms else None
+    rc = _load().oracle_stp(N, K, E, float(h), float(dt), q.ctypes.data,
+                            params.ctypes.data, avg.ctypes.data, faces.ctypes.data,
+                            terms.ctypes.data if terms is not None else None)
+    if rc != 0:
+        raise RuntimeError(f"oracle_stp returned {rc}")
+    if return_terms:
+        return avg, faces, terms
+    return avg, faces

@@ -1,0 +1,291 @@
+/*
+ * Plain FP64 CPU oracle of the linear ADER-DG Space-Time Predictor (STP).
+ *
+ * TEST INFRASTRUCTURE ONLY. Nothing on the product path may call, link or
+ * load this file: only the tests, the smoke check and the benchmark's CPU
+ * baseline use it. It shares no code, header, table or constant generator with
+ * the CUDA library; it is written to be slow and obviously correct.
+ *
+ * What it computes (Gallard et al., "Vectorization and Minimization of Memory
+ * Footprint for Linear High-Order Discontinuous Galerkin Schemes", arXiv
+ * 2003.12787):
+ *   - Sec. II-A: nodal tensor-product Lagrange basis on N Gauss-Legendre nodes
+ *     per dimension of the reference cube [0,1]^3; the discrete derivative
+ *     operator D; N nodes per dimension ("order N" in the paper's wording).
+ *   - Eq. (exahypeTimeAverage) and the recurrence below it: the Taylor series
+ *     of the cell-local solution in time, built from powers of the volume
+ *     operator V applied to q(t_n): p_o = V p_{o-1}.
+ *   - Sec. II-B: the STP outputs the time-averaged degrees of freedom and
+ *     their projection onto the element faces.
+ *   - Sec. VI (benchmark setup): 3-D elastic wave equation, 3 velocities and
+ *     6 stresses, 3 material parameters per node.
+ *
+ * Readings (the paper is silent or its pseudocode is garbled on these):
+ *   - The operator is taken in the form q_t + sum_d B_d dq/dx_d = 0, so one CK
+ *     step is  q^(k+1) = - sum_d B_d(x) (D_d q^(k)) / h.
+ *   - K Taylor terms q^(0..K-1); the default reading is K = N + 1 (the sum in
+ *     Eq. (exahypeTimeAverage) runs over o = 0..N).
+ *   - The output is the time AVERAGE  sum_k dt^k/(k+1)! q^(k)  (the paper's
+ *     integral divided by dt).
+ *   - D_ij = phi_j'(xi_i) (strong collocation form), nodes on [0,1],
+ *     derivatives divided by the element side h.
+ *   - Quantity order (v1,v2,v3,s11,s22,s33,s12,s13,s23); material (rho,cp,cs)
+ *     with lambda = rho (cp^2 - 2 cs^2), mu = rho cs^2 (textbook
+ *     velocity-stress elasticity).
+ *   - Faces ordered x-,x+,y-,y+,z-,z+; in-plane indices are the two remaining
+ *     dimensions in (slower, faster) order.
+ *
+ * Layouts (row-major, last index fastest):
+ *   q, avg:   [E][N][N][N][9]   (element, z, y, x, quantity)
+ *   params:   [E][N][N][N][3]   (rho, cp, cs)
+ *   faces:    [E][6][N][N][9]
+ *   terms:    [E][K][N][N][N][9]  (optional: every q^(k), unscaled)
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#define M 9 /* quantities of the elastic system */
+
+/* Legendre polynomial P_n(x) on [-1,1] by the three-term (Bonnet) recurrence. */
+static double legendre(int n, double x) {
+  double p0 = 1.0, p1 = x;
+  if (n == 0) return p0;
+  for (int k = 1; k < n; ++k) {
+    double p2 = ((2.0 * k + 1.0) * x * p1 - k * p0) / (k + 1.0);
+    p0 = p1;
+    p1 = p2;
+  }
+  return p1;
+}
+
+/* Derivative P_n'(x) = n (x P_n - P_{n-1}) / (x^2 - 1), valid inside (-1,1). */
+static double legendre_deriv(int n, double x) {
+  return n * (x * legendre(n, x) - legendre(n - 1, x)) / (x * x - 1.0);
+}
+
+/*
+ * Gauss-Legendre nodes xi[0..N-1] (ascending) and weights w[0..N-1] on [0,1].
+ * The nodes are the N roots of P_N(2 xi - 1): every root is bracketed by a
+ * sign change on a fine uniform grid and then bisected down to adjacent
+ * doubles. Weights: w = 1 / ((1 - t^2) P_N'(t)^2) for t = 2 xi - 1 (the [-1,1]
+ * weight 2/((1-t^2)P_N'(t)^2) halved for the unit interval).
+ * Returns 0, or -1 if fewer than N roots were found.
+ */
+int oracle_gl_nodes(int N, double* xi, double* w) {
+  if (N < 1 || N > 64) return -1;
+  int found = 0;
+  const int samples = 4000 * N;
+  double a = -1.0, fa = legendre(N, a);
+  for (int s = 1; s <= samples && found < N; ++s) {
+    double b = -1.0 + 2.0 * s / samples;
+    double fb = legendre(N, b);
+    if (fb == 0.0) { /* root exactly on the grid */
+      xi[found++] = b;
+      a = b; fa = fb;
+      /* step past it so the same root is not bracketed again */
+      continue;
+    }
+    if (fa != 0.0 && ((fa < 0.0) != (fb < 0.0))) {
+      double lo = a, hi = b, flo = fa;
+      for (int it = 0; it < 200; ++it) {
+        double mid = 0.5 * (lo + hi);
+        if (mid <= lo || mid >= hi) break;
+        double fm = legendre(N, mid);
+        if (fm == 0.0) { lo = hi = mid; break; }
+        if ((fm < 0.0) == (flo < 0.0)) { lo = mid; flo = fm; } else { hi = mid; }
+      }
+      xi[found++] = 0.5 * (lo + hi);
+    }
+    a = b; fa = fb;
+  }
+  if (found != N) return -1;
+  for (int i = 0; i < N; ++i) {
+    double t = xi[i];
+    double dp = legendre_deriv(N, t);
+    if (w) w[i] = 1.0 / ((1.0 - t * t) * dp * dp);
+    xi[i] = 0.5 * (t + 1.0);
+  }
+  return 0;
+}
+
+/* Lagrange basis phi_j(x) = prod_{l != j} (x - xi_l) / (xi_j - xi_l). */
+static double lagrange(int N, const double* xi, int j, double x) {
+  double v = 1.0;
+  for (int l = 0; l < N; ++l)
+    if (l != j) v *= (x - xi[l]) / (xi[j] - xi[l]);
+  return v;
+}
+
+/* phi_j'(x) by the product rule on the same definition. */
+static double lagrange_deriv(int N, const double* xi, int j, double x) {
+  double s = 0.0;
+  for (int m = 0; m < N; ++m) {
+    if (m == j) continue;
+    double t = 1.0 / (xi[j] - xi[m]);
+    for (int l = 0; l < N; ++l)
+      if (l != j && l != m) t *= (x - xi[l]) / (xi[j] - xi[l]);
+    s += t;
+  }
+  return s;
+}
+
+/*
+ * Tables of the reference element: D[i*N+j] = phi_j'(xi_i), phi0[j] = phi_j(0),
+ * phi1[j] = phi_j(1). Any output pointer may be NULL.
+ */
+int oracle_tables(int N, double* xi_out, double* D, double* phi0, double* phi1) {
+  double xi[64];
+  if (oracle_gl_nodes(N, xi, NULL) != 0) return -1;
+  if (xi_out) memcpy(xi_out, xi, sizeof(double) * N);
+  for (int i = 0; i < N; ++i)
+    for (int j = 0; j < N; ++j)
+      if (D) D[i * N + j] = lagrange_deriv(N, xi, j, xi[i]);
+  for (int j = 0; j < N; ++j) {
+    if (phi0) phi0[j] = lagrange(N, xi, j, 0.0);
+    if (phi1) phi1[j] = lagrange(N, xi, j, 1.0);
+  }
+  return 0;
+}
+
+/*
+ * B_d (9x9, row r = equation of quantity r, column s = d/dx_d of quantity s)
+ * of the elastic system written as q_t + sum_d B_d dq/dx_d = 0:
+ *   rho dv_i/dt = sum_j d sigma_ij / dx_j
+ *   d sigma_ij/dt = lambda delta_ij div v + mu (dv_i/dx_j + dv_j/dx_i)
+ * Quantity indices: v1 0, v2 1, v3 2, s11 3, s22 4, s33 5, s12 6, s13 7, s23 8.
+ */
+static void elastic_B(int d, double rho, double cp, double cs, double B[M][M]) {
+  const double lam = rho * (cp * cp - 2.0 * cs * cs);
+  const double mu = rho * cs * cs;
+  static const int sig[3][3] = {{3, 6, 7}, {6, 4, 8}, {7, 8, 5}};
+  memset(B, 0, sizeof(double) * M * M);
+  /* velocities: dv_i/dt = (1/rho) d sigma_{i d}/dx_d */
+  for (int i = 0; i < 3; ++i) B[i][sig[i][d]] = -1.0 / rho;
+  /* normal stresses: d s_ii/dt = lambda dv_d/dx_d + 2 mu delta_id dv_d/dx_d */
+  for (int i = 0; i < 3; ++i) B[3 + i][d] = -(lam + (i == d ? 2.0 * mu : 0.0));
+  /* shear stresses s_ij (i<j): mu (dv_i/dx_j + dv_j/dx_i) */
+  for (int i = 0; i < 3; ++i)
+    for (int j = i + 1; j < 3; ++j) {
+      int r = sig[i][j];
+      if (d == j) B[r][i] += -mu;
+      if (d == i) B[r][j] += -mu;
+    }
+}
+
+/* flat index of node (z,y,x) quantity s inside one element */
+#define NODE(z, y, x) (((z) * N + (y)) * N + (x))
+
+/*
+ * One element. q, params, avg, faces point at that element's blocks; terms
+ * (may be NULL) at its [K][N][N][N][9] block.
+ */
+static void stp_element(int N, int K, double h, double dt, const double* D,
+                        const double* phi0, const double* phi1, const double* q,
+                        const double* params, double* avg, double* faces,
+                        double* terms, double* p, double* pn, double* g) {
+  const int n3 = N * N * N;
+  memcpy(p, q, sizeof(double) * n3 * M);
+  memcpy(avg, q, sizeof(double) * n3 * M);
+  if (terms) memcpy(terms, q, sizeof(double) * n3 * M);
+  double c = 1.0; /* dt^k / (k+1)! for the term being added */
+  for (int k = 0; k + 1 < K; ++k) {
+    /* pn = - sum_d B_d (D_d p) / h  : one application of the volume operator */
+    memset(pn, 0, sizeof(double) * n3 * M);
+    for (int d = 0; d < 3; ++d) {
+      /* g = (1/h) D applied along dimension d, all 9 quantities */
+      for (int z = 0; z < N; ++z)
+        for (int y = 0; y < N; ++y)
+          for (int x = 0; x < N; ++x) {
+            int i = (d == 0) ? x : (d == 1) ? y : z;
+            for (int s = 0; s < M; ++s) {
+              double acc = 0.0;
+              for (int l = 0; l < N; ++l) {
+                int zz = (d == 2) ? l : z, yy = (d == 1) ? l : y, xx = (d == 0) ? l : x;
+                acc += D[i * N + l] * p[NODE(zz, yy, xx) * M + s];
+              }
+              g[NODE(z, y, x) * M + s] = acc / h;
+            }
+          }
+      for (int n = 0; n < n3; ++n) {
+        double B[M][M];
+        elastic_B(d, params[n * 3 + 0], params[n * 3 + 1], params[n * 3 + 2], B);
+        for (int r = 0; r < M; ++r) {
+          double acc = 0.0;
+          for (int s = 0; s < M; ++s) acc += B[r][s] * g[n * M + s];
+          pn[n * M + r] -= acc;
+        }
+      }
+    }
+    memcpy(p, pn, sizeof(double) * n3 * M);
+    c = c * dt / (double)(k + 2);
+    for (int t = 0; t < n3 * M; ++t) avg[t] += c * p[t];
+    if (terms) memcpy(terms + (size_t)(k + 1) * n3 * M, p, sizeof(double) * n3 * M);
+  }
+  /* faces: phi(side)^T applied along dimension d to avg */
+  for (int d = 0; d < 3; ++d)
+    for (int side = 0; side < 2; ++side) {
+      const double* phi = side ? phi1 : phi0;
+      double* f = faces + (size_t)(2 * d + side) * N * N * M;
+      for (int a = 0; a < N; ++a)
+        for (int b = 0; b < N; ++b)
+          for (int s = 0; s < M; ++s) {
+            double acc = 0.0;
+            for (int i = 0; i < N; ++i) {
+              int z, y, x;
+              if (d == 0) { z = a; y = b; x = i; }
+              else if (d == 1) { z = a; y = i; x = b; }
+              else { z = i; y = a; x = b; }
+              acc += phi[i] * avg[NODE(z, y, x) * M + s];
+            }
+            f[(a * N + b) * M + s] = acc;
+          }
+    }
+}
+
+/*
+ * The STP over E independent elements. K = number of Taylor terms (N+1 by
+ * default reading). Returns 0, -1 on bad arguments, -2 on allocation failure.
+ * Elements are distributed over OpenMP threads when compiled with OpenMP;
+ * each element's arithmetic is the same either way.
+ */
+int oracle_stp(int N, int K, int64_t E, double h, double dt, const double* q,
+               const double* params, double* avg, double* faces, double* terms) {
+  if (N < 1 || N > 16 || K < 1 || E < 0 || !(h > 0.0)) return -1;
+  double D[16 * 16], phi0[16], phi1[16];
+  if (oracle_tables(N, NULL, D, phi0, phi1) != 0) return -1;
+  const size_t n3m = (size_t)N * N * N * M;
+  int err = 0;
+#pragma omp parallel
+  {
+    double* work = (double*)malloc(sizeof(double) * 3 * n3m);
+    if (!work) {
+#pragma omp atomic write
+      err = 1;
+    }
+#pragma omp for schedule(dynamic, 4)
+    for (int64_t e = 0; e < E; ++e) {
+      if (!work) continue;
+      stp_element(N, K, h, dt, D, phi0, phi1, q + e * n3m,
+                  params + e * (n3m / M) * 3, avg + e * n3m,
+                  faces + e * (size_t)6 * N * N * M,
+                  terms ? terms + e * (size_t)K * n3m : NULL, work, work + n3m,
+                  work + 2 * n3m);
+    }
+    free(work);
+  }
+  return err ? -2 : 0;
+}
+
+/* number of OpenMP threads the oracle runs on (1 without OpenMP) */
+int oracle_num_threads(void) {
+#ifdef _OPENMP
+  return omp_get_max_threads();
+#else
+  return 1;
+#endif
+}

@@ -1,0 +1,142 @@
+"""Seeded synthetic inputs for the elastic Space-Time Predictor.
+
+This module holds no arithmetic of the method: it only places sample points
+and draws material fields and an initial state. Both the CUDA path and the
+oracle receive the arrays it returns.
+
+Recipe (the paper's benchmark is a 3-D elastic wave problem with 9 state
+quantities and 3 material parameters per node, Sec. VI; its scenario files are
+not available, so seeded synthetic fields of that shape stand in for them):
+
+* Elements: an axis-aligned grid of Gx x Gy x Gz cubes of side h, element
+  index e = (ez*Gy + ey)*Gx + ex (x fastest); the first E elements in that
+  order. Node (z,y,x) of element e sits at ((ex, ey, ez) + (xi_x, xi_y, xi_z))*h
+  with xi the N Gauss-Legendre points on [0,1] (numpy's leggauss, used here
+  only to place sample points).
+* Material per node, seed ``seed_material``: rho ~ U[2,3], cp ~ U[4,6] drawn as
+  two arrays of shape (E,N,N,N) in that order; cs = cp/sqrt(3).
+* Initial state, seed ``seed_waves``: 4 plane waves. Direction ~ normalised
+  standard normal 3-vector, radius ~ U[0,1]^(1/3) (uniform in the unit ball),
+  wavevector k = 2*pi*radius*direction; amplitudes a[w,s] ~ U[0.5,1] and phases
+  ph[w,s] ~ U[0,2*pi) of shape (4,9).
+  q_s(x) = sum_w a[w,s] sin(k_w . x + ph[w,s]).
+* Time step dt = 0.4*h / ((2N-1) * max cp).
+
+Layouts: q [E][N][N][N][9] (z,y,x,quantity), params [E][N][N][N][3]
+(rho, cp, cs), float64.
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass
+
+import numpy as np
+import torch
+
+M = 9
+N_WAVES = 4
+
+
+@dataclass
+class Problem:
+    N: int
+    E: int
+    h: float
+    dt: float
+    q: torch.Tensor       # [E][N][N][N][9] float64
+    params: torch.Tensor  # [E][N][N][N][3] float64
+    grid: tuple
+
+    @property
+    def order(self) -> int:
+        return self.N - 1
+
+
+def sample_points(N: int) -> np.ndarray:
+    t, _ = np.polynomial.legendre.leggauss(N)
+    return (t + 1.0) / 2.0
+
+
+def wave_parameters(seed_waves: int):
+    rng = np.random.Generator(np.random.PCG64(seed_waves))
+    d = rng.standard_normal((N_WAVES, 3))
+    d /= np.linalg.norm(d, axis=1, keepdims=True)
+    r = rng.uniform(0.0, 1.0, N_WAVES) ** (1.0 / 3.0)
+    k = 2.0 * math.pi * r[:, None] * d
+    amp = rng.uniform(0.5, 1.0, (N_WAVES, M))
+    phase = rng.uniform(0.0, 2.0 * math.pi, (N_WAVES, M))
+    return k, amp, phase
+
+
+def material(N: int, E: int, seed_material: int) -> np.ndarray:
+    rng = np.random.Generator(np.random.PCG64(seed_material))
+    rho = rng.uniform(2.0, 3.0, (E, N, N, N))
+    cp = rng.uniform(4.0, 6.0, (E, N, N, N))
+    cs = cp / math.sqrt(3.0)
+    return np.stack([rho, cp, cs], axis=-1)
+
+
+def elastic_problem(N: int, grid=None, E: int | None = None, h: float | None = None,
+                    seed_material: int = 1001, seed_waves: int = 1002,
+                    device: str | torch.device = "cpu") -> Problem:
+    """Build one seeded elastic STP input set.
+
+    grid: (Gx, Gy, Gz); if omitted, a cube of side ceil(E^(1/3)).
+    h: element side; default 1/max(grid).
+    The state is evaluated with torch on ``device`` (float64) so large inputs
+    can be generated where they are used; the random draws are numpy PCG64.
+    """
+    if grid is None:
+        if E is None:
+            raise ValueError("give grid or E")
+        G = max(1, math.ceil(round(E ** (1.0 / 3.0), 9)))
+        while G ** 3 < E:
+            G += 1
+        grid = (G, G, G)
+    Gx, Gy, Gz = grid
+    if E is None:
+        E = Gx * Gy * Gz
+    if E > Gx * Gy * Gz:
+        raise ValueError("E larger than the grid")
+    if h is None:
+        h = 1.0 / max(grid)
+    params_np = material(N, E, seed_material)
+    cp_max = float(params_np[..., 1].max()) if E > 0 else 5.0
+    dt = 0.4 * h / ((2 * N - 1) * cp_max)
+    k, amp, phase = wave_parameters(seed_waves)
+
+    dev = torch.device(device)
+    xi = torch.tensor(sample_points(N), dtype=torch.float64, device=dev)
+    e = torch.arange(E, device=dev, dtype=torch.int64)
+    ex = (e % Gx).to(torch.float64)
+    ey = ((e // Gx) % Gy).to(torch.float64)
+    ez = (e // (Gx * Gy)).to(torch.float64)
+    # physical coordinates of every node, each broadcast to [E][N][N][N]
+    X = ((ex[:, None] + xi[None, :]) * h)[:, None, None, :]
+    Y = ((ey[:, None] + xi[None, :]) * h)[:, None, :, None]
+    Z = ((ez[:, None] + xi[None, :]) * h)[:, :, None, None]
+    q = torch.zeros((E, N, N, N, M), dtype=torch.float64, device=dev)
+    for w in range(N_WAVES):
+        kx, ky, kz = (float(v) for v in k[w])
+        arg = kx * X + ky * Y + kz * Z  # [E][N][N][N] by broadcasting
+        for s in range(M):
+            q[..., s] += float(amp[w, s]) * torch.sin(arg + float(phase[w, s]))
+    params = torch.from_numpy(params_np).to(dev)
+    return Problem(N=N, E=E, h=h, dt=dt, q=q, params=params, grid=tuple(grid))
+
+
+# --- named workloads --------------------------------------------------------
+
+def small_case() -> Problem:
+    """Order 3 (N=4), 8^3 = 512 elements of side 1/8."""
+    return elastic_problem(4, grid=(8, 8, 8))
+
+
+def order7_case(device="cpu") -> Problem:
+    """Order 7 (N=8), 32^3 = 32768 elements of side 1/32."""
+    return elastic_problem(8, grid=(32, 32, 32), device=device)
+
+
+def order9_case(device="cpu") -> Problem:
+    """Order 9 (N=10), 16384 elements on a 32x32x16 grid, side 1/32."""
+    return elastic_problem(10, grid=(32, 32, 16), h=1.0 / 32, device=device)
