@@ -1,0 +1,378 @@
+#!/usr/bin/env python
+"""Benchmark of the GB300 Space-Time Predictor.
+
+One step = one STP pass (CK loop, Taylor time average, six face projections)
+over the whole workload: order 7 (N=8), 32^3 = 32768 elastic elements of side
+1/32, FP64, inputs resident in HBM. Prints ONE JSON line (rank 0).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+--impl reference times the plain FP64 CPU oracle on the host cores on a
+bounded sample of the same workload per step (the reference arm).
+Under torchrun (N > 1) every rank runs its own seeded partition of the same
+size (weak scaling, no data-path collective); the time is the max over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "STP elements/s + % FP64 roofline; mixed vs FP64 at fixed error; p50/p99"
+UNIT = "elements/s"
+PROFILES = os.path.join(ROOT, "profiles")
+
+WORKLOADS = {
+    # name: (N, grid, h, description)
+    "order7": (8, (32, 32, 32), 1.0 / 32,
+               "order-7 (N=8) elastic STP, 32^3=32768 elements of side 1/32, one launch"),
+    "order3": (4, (8, 8, 8), 1.0 / 8,
+               "order-3 (N=4) elastic STP, 8^3=512 elements of side 1/8, one launch"),
+    "order9": (10, (32, 32, 16), 1.0 / 32,
+               "order-9 (N=10) elastic STP, 32x32x16=16384 elements of side 1/32, one launch"),
+}
+
+
+def flops_per_element(N: int) -> int:
+    """Algorithmic FP64 flops of one element (elastic sparsity, N CK steps):
+    36N^5 (derivative contractions) + 48N^4 (pointwise elastic update)
+    + 18N^4 (Taylor accumulation) + 108N^3 (six face projections)."""
+    return 36 * N ** 5 + 66 * N ** 4 + 108 * N ** 3
+
+
+def bytes_per_element(N: int) -> int:
+    """Algorithmic HBM bytes of one element: q (9N^3) + params (3N^3) in,
+    avg (9N^3) + faces (54N^2) out, 8 bytes each."""
+    return 8 * (21 * N ** 3 + 54 * N ** 2)
+
+
+# FP64 ALU peak derived from unit counts and clock: 152 SMs x 2 DFMA/clk/SM
+# (the FP64 pipe rate of GB300) x 2 flops x 2.07 GHz maximum SM clock.
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
+
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    for name in ("fp64_kernels.cu",):
+        with open(os.path.join(ROOT, "paper_2003_12787_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def traffic_from_profile(workload: str):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken
+    on the current kernel source; else None."""
+    path = os.path.join(PROFILES, f"traffic_fp64_stp_{workload}.json")
+    try:
+        with open(path) as f:
+            rec = json.load(f)
+    except (OSError, ValueError):
+        return None
+    if rec.get("kernel_source_sha") != kernel_source_hash():
+        return None
+    return rec.get("dram_bytes_per_launch")
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle sampling during the timed region."""
+
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.file = None
+
+    def start(self):
+        try:
+            self.file = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.QUERY}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=self.file, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        time.sleep(0.3)
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.2)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.file.flush()
+        self.file.seek(0)
+        rows = [l.strip().split(", ") for l in self.file.read().splitlines() if l.strip()]
+        self.file.close()
+        os.unlink(self.file.name)
+        sm, smax, reasons, power = [], None, set(), []
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            if len(r) < 9:
+                continue
+            try:
+                sm.append(float(r[1]))
+                smax = float(r[2])
+                power.append(float(r[3]))
+            except ValueError:
+                continue
+            for n, v in zip(names, r[5:9]):
+                if v.strip().lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": smax, "reasons": ["no samples"]}
+        top = max(sm)
+        loaded = [s for s in sm if s >= 0.5 * top] or sm
+        return {"sm_mhz": statistics.median(loaded), "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm),
+                "power_w_max": max(power) if power else None}
+
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def max_over_ranks(value: float, world: int, device=None) -> float:
+    if world == 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(world: int):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def oracle_baseline(prob_q, prob_params, h, dt, budget_s: float, max_elems: int):
+    """Time the oracle as it stands on a bounded sample (elements from the
+    front of the workload, in chunks, until the time budget is spent)."""
+    import oracle
+    E = prob_q.shape[0]
+    done, spent, chunk = 0, 0.0, 256
+    while done < min(E, max_elems) and spent < budget_s:
+        n = min(chunk, E - done, max_elems - done)
+        q = np.ascontiguousarray(prob_q[done:done + n])
+        p = np.ascontiguousarray(prob_params[done:done + n])
+        t0 = time.perf_counter()
+        oracle.stp(q, p, h, dt)
+        spent += time.perf_counter() - t0
+        done += n
+        chunk = min(chunk * 2, 4096)
+    return done, spent, oracle.num_threads()
+
+
+def run_gpu(args):
+    import torch
+    world, rank, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    else:
+        torch.cuda.set_device(0)
+    import paper_2003_12787_gb300 as stp
+    from paper_2003_12787_gb300.inputs import elastic_problem
+
+    N, grid, h, desc = WORKLOADS[args.workload]
+    prob = elastic_problem(N, grid=grid, h=h, seed_material=1001 + 16 * rank,
+                           seed_waves=1002 + 16 * rank, device="cuda")
+    E = prob.E
+    dev = torch.device("cuda", torch.cuda.current_device())
+    stream = torch.cuda.current_stream(dev)
+    P = stp.Predictor(N - 1, prob.h, prob.dt)
+    avg, faces = P.empty_outputs(E, device=dev)
+
+    fp64_probe = stp.stp_measure_fp64_peak(stream)
+
+    for _ in range(args.warmup):
+        P.predict(prob.q, prob.params, out=(avg, faces), stream=stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    torch.cuda.synchronize()
+
+    sampler = ClockSampler(dev.index) if rank == 0 else None
+    if sampler:
+        sampler.start()
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    t_all0 = torch.cuda.Event(enable_timing=True)
+    t_all1 = torch.cuda.Event(enable_timing=True)
+    t_all0.record(stream)
+    for i in range(args.steps):
+        starts[i].record(stream)
+        P.predict(prob.q, prob.params, out=(avg, faces), stream=stream)
+        ends[i].record(stream)
+    t_all1.record(stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    torch.cuda.synchronize()
+    clocks = sampler.stop() if sampler else None
+    total_ms = t_all0.elapsed_time(t_all1)
+    step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    total_ms_max = max_over_ranks(total_ms, world, dev)
+    value = E * args.steps * world / (total_ms_max / 1e3)
+
+    # spot parity of this run's outputs against the oracle (a few elements)
+    parity = None
+    if rank == 0:
+        import oracle
+        idx = torch.tensor([0, E // 3, E - 1], device=dev)
+        a_ref, f_ref = oracle.stp(prob.q[idx].cpu().numpy(), prob.params[idx].cpu().numpy(),
+                                  prob.h, prob.dt)
+        a = avg[idx].cpu().numpy()
+        f = faces[idx].cpu().numpy()
+        parity = max(float(np.abs(a - a_ref).max() / np.abs(a_ref).max()),
+                     float(np.abs(f - f_ref).max() / np.abs(f_ref).max()))
+
+    # end to end through the host-buffer entry point (pinned memory)
+    e2e = None
+    if not args.no_e2e:
+        qh = prob.q.cpu().pin_memory()
+        ph = prob.params.cpu().pin_memory()
+        ah, fh = P.empty_outputs(E, device="cpu", pin_memory=True)
+        P.predict_host(qh, ph, out=(ah, fh))  # warm-up: allocates staging buffers
+        barrier(world)
+        t0 = time.perf_counter()
+        ke = max(1, min(args.steps, 5))
+        for _ in range(ke):
+            P.predict_host(qh, ph, out=(ah, fh))
+        e2e_s = max_over_ranks(time.perf_counter() - t0, world, dev)
+        e2e = {"value": E * ke * world / e2e_s, "unit": UNIT,
+               "h2d_bytes_per_step": int(qh.numel() * 8 + ph.numel() * 8),
+               "d2h_bytes_per_step": int(ah.numel() * 8 + fh.numel() * 8),
+               "steps": ke}
+        if not np.array_equal(ah[:4].numpy(), avg[:4].cpu().numpy()):
+            e2e["mismatch_vs_device_path"] = True
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        qn = prob.q.cpu().numpy()
+        pn = prob.params.cpu().numpy()
+        done, spent, cores = oracle_baseline(qn, pn, prob.h, prob.dt, args.cpu_budget, E)
+        cpu = {"value": done / spent, "unit": UNIT, "cores": cores, "kind": "oracle",
+               "sample": f"first {done} of {E} elements of the same workload, "
+                         f"{spent:.1f} s wall on {cores} OpenMP threads"}
+
+    if rank == 0:
+        mean_step_s = statistics.mean(step_ms) / 1e3
+        achieved = E * flops_per_element(N) / mean_step_s / 1e12
+        srt = sorted(step_ms)
+        p99 = srt[min(len(srt) - 1, int(math.ceil(0.99 * len(srt))) - 1)]
+        traffic = traffic_from_profile(args.workload)
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms_max / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64", "data": "synthetic",
+            "config": {"workload": desc, "N": N, "order": N - 1, "elements": E,
+                       "elements_per_gpu": E, "dt": prob.dt, "dx": prob.h,
+                       "l2": "inputs larger than L2: %.2f GB read + %.2f GB written per step"
+                             % (E * 8 * 12 * N ** 3 / 1e9, E * 8 * (9 * N ** 3 + 54 * N ** 2) / 1e9),
+                       "parallelism": f"dp{world} (element partitions, no collective)"},
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
+                         "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
+                         "traffic": traffic,
+                         "peak_kind": "derived: 152 SM x 2 DFMA/clk x 2 flop x 2.07 GHz",
+                         "fp64_probe_tflops": fp64_probe / 1e3,
+                         "frac_of_probe": achieved / (fp64_probe / 1e3),
+                         "flops_per_element": flops_per_element(N),
+                         "hbm_gbs": E * bytes_per_element(N) / mean_step_s / 1e9},
+            "latency_ms": {"p50": statistics.median(step_ms), "p99": p99,
+                           "min": min(step_ms), "max": max(step_ms)},
+            "e2e": e2e, "cpu_baseline": cpu, "clocks": clocks,
+            "gpu_launches": args.steps, "parity_max_rel_sampled": parity,
+        }
+        print(json.dumps(line), flush=True)
+    P.close()
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def run_reference(args):
+    """The reference arm: the FP64 oracle on the host cores, bounded sample per step."""
+    world, rank, _ = dist_env()
+    if rank != 0:
+        return
+    import oracle
+    from paper_2003_12787_gb300.inputs import elastic_problem
+    N, grid, h, desc = WORKLOADS[args.workload]
+    prob = elastic_problem(N, grid=grid, h=h)
+    q = prob.q.numpy()
+    p = prob.params.numpy()
+    sample = min(prob.E, args.reference_sample)
+    qs, ps = np.ascontiguousarray(q[:sample]), np.ascontiguousarray(p[:sample])
+    for _ in range(args.warmup):
+        oracle.stp(qs, ps, prob.h, prob.dt)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        oracle.stp(qs, ps, prob.h, prob.dt)
+        times.append(time.perf_counter() - t0)
+    total = sum(times)
+    value = sample * args.steps / total
+    cores = oracle.num_threads()
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": desc, "N": N, "order": N - 1, "elements": prob.E,
+                   "sample_elements_per_step": sample},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": f"first {sample} of {prob.E} elements per step"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "gpu_launches": 0,
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__.splitlines()[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["gpu", "reference"], default="gpu")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="order7")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-budget", type=float, default=10.0,
+                    help="seconds of oracle time for cpu_baseline")
+    ap.add_argument("--reference-sample", type=int, default=1024,
+                    help="elements per step of the reference arm")
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "gpu":
+        print("warning: fewer than 3 warm-up steps", file=sys.stderr)
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,138 @@
+/*
+ * stp.h - C ABI of the GB300 (sm_103a) linear ADER-DG Space-Time Predictor.
+ *
+ * The Space-Time Predictor (STP) is the element-local part of a linear
+ * ADER-DG step (Gallard et al., arXiv 2003.12787, Sec. II-A and II-B): for
+ * every hexahedral element it evolves the nodal state q(t_n) in time with the
+ * Cauchy-Kowalewsky (CK) recurrence p_o = V p_{o-1} (the recurrence under
+ * Eq. (exahypeTimeAverage)), sums the Taylor series of Eq.
+ * (exahypeTimeAverage) on the fly, and projects the result onto the six faces
+ * of the element (Sec. II-B: the STP must hand the time-averaged degrees of
+ * freedom and their face projections to the corrector).
+ *
+ * Physics: the 3-D linear elastic wave equation in velocity-stress form
+ * (Sec. VI: 3 velocities + 6 stresses, 3 material parameters per node),
+ * written q_t + sum_d B_d(x) dq/dx_d = 0, so that one CK step is
+ *     q^(k+1) = - sum_d B_d(x) (D_d q^(k)) / dx
+ * with D the N x N Lagrange derivative matrix on N Gauss-Legendre nodes per
+ * dimension (Sec. II-A) applied along dimension d.
+ *
+ * Outputs per element:
+ *     avg  = sum_{k=0..N} dt^k/(k+1)! q^(k)          (time average over [t_n, t_n+dt])
+ *     face[d,side] = phi(side)^T applied along d to avg,  side 0 -> reference 0, 1 -> 1
+ *
+ * All arrays are FP64, row-major, last index fastest:
+ *     q, out_avg   [E][N][N][N][9]  element, z, y, x, quantity
+ *                  quantities (v1, v2, v3, s11, s22, s33, s12, s13, s23)
+ *     params       [E][N][N][N][3]  (rho, cp, cs): density, P and S wave speed
+ *     out_faces    [E][6][N][N][9]  faces x-, x+, y-, y+, z-, z+; the two in-plane
+ *                  indices are the remaining dimensions in (slower, faster) order:
+ *                  x faces [z][y], y faces [z][x], z faces [y][x]
+ *
+ * Error behaviour: every entry point returns a stp_status. Argument errors are
+ * detected before anything is enqueued and leave every buffer untouched.
+ * CUDA launch/runtime errors are reported as STP_ERR_CUDA; the message of the
+ * last failure on the calling thread is available from stp_last_error().
+ */
+#ifndef STP_GB300_H
+#define STP_GB300_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct stp_handle_s* stp_handle; /* opaque, owned by the library */
+
+typedef enum {
+  STP_OK = 0,
+  STP_ERR_INVALID_ARG = -1, /* null/misaligned/overlapping/host pointer, bad size */
+  STP_ERR_UNSUPPORTED = -2, /* order or number of quantities not implemented */
+  STP_ERR_OOM = -3,         /* device or pinned allocation failed */
+  STP_ERR_CUDA = -4,        /* a CUDA call failed (see stp_last_error) */
+  STP_ERR_TIMEOUT = -5      /* a bounded device-side wait gave up */
+} stp_status;
+
+/*
+ * Create a predictor for one (order, dx, dt).
+ *   order  polynomial degree p; N = p + 1 nodes per dimension, 1 <= N <= 12
+ *          ("order N" in the paper's wording is this N, Sec. II-A)
+ *   m      number of quantities; must be 9 (elastic system)
+ *   dx     element side (the same in x, y and z), > 0 and finite
+ *   dt     time step, > 0 and finite
+ *   out    receives the handle
+ * Computes the Gauss-Legendre nodes, the derivative matrix D (scaled per CK
+ * step by dt/((k+2) dx)) and the face interpolation vectors phi(0), phi(1) in
+ * extended precision on the host and uploads them to the current CUDA device,
+ * which the handle is bound to. Returns STP_ERR_UNSUPPORTED for m != 9 or N
+ * out of range, STP_ERR_INVALID_ARG for a bad dx, dt or a NULL out.
+ */
+stp_status stp_create(int order, int m, double dx, double dt, stp_handle* out);
+
+/*
+ * Enqueue the STP of `elements` elements on `stream` (a cudaStream_t; NULL =
+ * the legacy default stream). Asynchronous: returns once the kernel is
+ * enqueued, without a host synchronisation.
+ *   q, params           device pointers (inputs, read only)
+ *   out_avg, out_faces  device pointers (outputs, fully overwritten)
+ * All four must be device (or managed) memory on the handle's device,
+ * 16-byte aligned, and the outputs must not overlap the inputs or each other.
+ * The caller owns the buffers and keeps them alive until the stream has
+ * passed the kernel. elements == 0 returns STP_OK without a launch. The
+ * handle is not modified, so several streams may use one handle at once.
+ */
+stp_status stp_predict(stp_handle h, int64_t elements, const double* q,
+                       const double* params, double* out_avg, double* out_faces,
+                       void* stream);
+
+/*
+ * Same computation on HOST buffers (pinned host memory gives full copy
+ * bandwidth; pageable memory works but copies slower). Synchronous: returns
+ * once out_avg and out_faces hold the results. Elements are processed in
+ * chunks: the host-to-device copy of one chunk, the kernel of the previous
+ * chunk and the device-to-host copy of the one before run concurrently on
+ * library-owned streams and device buffers (allocated on first use and kept
+ * by the handle, so concurrent calls on ONE handle must be serialised by the
+ * caller). `stream` orders the call after work already on that stream.
+ */
+stp_status stp_predict_host(stp_handle h, int64_t elements, const double* q,
+                            const double* params, double* out_avg, double* out_faces,
+                            void* stream);
+
+/* Release the handle's device tables and buffers. NULL is a no-op (STP_OK). */
+stp_status stp_destroy(stp_handle h);
+
+/*
+ * The reference-element tables the library computes for `order` (N = order+1
+ * nodes), on the host, without touching a GPU (any output may be NULL):
+ *   nodes[N]   Gauss-Legendre nodes on [0,1], ascending (Sec. II-A)
+ *   D[N*N]     D[i*N+j] = phi_j'(xi_i), the collocation derivative matrix
+ *   phi0[N], phi1[N]   phi_j(0), phi_j(1), the face interpolation vectors
+ * Returns STP_ERR_UNSUPPORTED for N outside [1, 12].
+ */
+stp_status stp_reference_tables(int order, double* nodes, double* D, double* phi0,
+                                double* phi1);
+
+/* Nodes per dimension N of the handle, or -1 for an invalid handle. */
+int stp_nodes(stp_handle h);
+
+/* Static description of a status code. */
+const char* stp_status_string(stp_status s);
+
+/* Message of the last error on the calling thread ("" if none). */
+const char* stp_last_error(void);
+
+/*
+ * Measure the device's FP64 fused multiply-add throughput (GFLOP/s, 2 flops
+ * per FMA) with a dependent-chain-free DFMA loop over all SMs, timed with
+ * CUDA events on `stream`. Synchronous. Used as the roofline denominator of
+ * the FP64 path.
+ */
+stp_status stp_measure_fp64_peak(double* gflops, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* STP_GB300_H */

@@ -1,0 +1,13 @@
+"""GB300 (sm_103a) linear ADER-DG Space-Time Predictor.
+
+The compute lives in the CUDA library built from ``csrc/`` (C ABI:
+include/stp.h); ``_binding`` marshals arguments into it and ``Predictor``
+wraps a handle for torch tensors. ``inputs`` generates seeded synthetic
+elastic problems.
+"""
+from __future__ import annotations
+
+from ._binding import (STPError, stp_create, stp_destroy, stp_reference_tables,  # noqa: F401
+                       stp_last_error, stp_measure_fp64_peak, stp_nodes, stp_predict,
+                       stp_predict_host, stp_status_string)
+from .predictor import Predictor  # noqa: F401

@@ -1,0 +1,137 @@
+"""ctypes binding of the C ABI in include/stp.h (argument marshalling only).
+
+Every step of the predictor runs in the CUDA library; this module converts
+torch tensors / numpy arrays to pointers and status codes to exceptions. If
+the library has not been built, loading fails loudly: there is no CPU path.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+from . import build as _build
+
+STP_OK = 0
+STP_ERR_INVALID_ARG = -1
+STP_ERR_UNSUPPORTED = -2
+STP_ERR_OOM = -3
+STP_ERR_CUDA = -4
+STP_ERR_TIMEOUT = -5
+
+M = 9
+
+_lock = threading.Lock()
+_lib = None
+
+
+class STPError(RuntimeError):
+    def __init__(self, status: int, where: str, detail: str):
+        self.status = status
+        super().__init__(f"{where}: status {status} ({detail})")
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load():
+    """Load libstp_gb300.so (build it first with __graft_entry__.build())."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        path = _build.LIB
+        if not os.path.exists(path):
+            raise RuntimeError(f"CUDA library {path} is missing: build it with "
+                               "paper_2003_12787_gb300.build.build() (no CPU fallback exists)")
+        lib = ctypes.CDLL(path)
+        vp, i64, dbl = ctypes.c_void_p, ctypes.c_int64, ctypes.c_double
+        lib.stp_create.argtypes = [ctypes.c_int, ctypes.c_int, dbl, dbl, ctypes.POINTER(vp)]
+        lib.stp_predict.argtypes = [vp, i64, vp, vp, vp, vp, vp]
+        lib.stp_predict_host.argtypes = [vp, i64, vp, vp, vp, vp, vp]
+        lib.stp_destroy.argtypes = [vp]
+        lib.stp_reference_tables.argtypes = [ctypes.c_int, vp, vp, vp, vp]
+        lib.stp_nodes.argtypes = [vp]
+        lib.stp_nodes.restype = ctypes.c_int
+        lib.stp_status_string.argtypes = [ctypes.c_int]
+        lib.stp_status_string.restype = ctypes.c_char_p
+        lib.stp_last_error.argtypes = []
+        lib.stp_last_error.restype = ctypes.c_char_p
+        lib.stp_measure_fp64_peak.argtypes = [ctypes.POINTER(dbl), vp]
+        for name in ("stp_create", "stp_predict", "stp_predict_host", "stp_destroy",
+                     "stp_reference_tables", "stp_measure_fp64_peak"):
+            getattr(lib, name).restype = ctypes.c_int
+        _lib = lib
+        return lib
+
+
+def _check(status: int, where: str):
+    if status != STP_OK:
+        lib = load()
+        detail = lib.stp_last_error().decode() or lib.stp_status_string(status).decode()
+        raise STPError(status, where, detail)
+
+
+def _ptr(x) -> int | None:
+    """Address of a torch tensor, numpy array or raw integer pointer."""
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if hasattr(x, "data_ptr"):
+        return x.data_ptr()
+    if hasattr(x, "ctypes"):
+        return x.ctypes.data
+    raise TypeError(f"cannot take the address of {type(x)}")
+
+
+def _stream(stream) -> int | None:
+    if stream is None:
+        return None
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream  # torch.cuda.Stream
+
+
+def stp_create(order: int, m: int, dx: float, dt: float) -> int:
+    h = ctypes.c_void_p()
+    _check(load().stp_create(order, m, dx, dt, ctypes.byref(h)), "stp_create")
+    return h.value
+
+
+def stp_predict(h: int, elements: int, q, params, out_avg, out_faces, stream=None) -> None:
+    _check(load().stp_predict(h, elements, _ptr(q), _ptr(params), _ptr(out_avg),
+                              _ptr(out_faces), _stream(stream)), "stp_predict")
+
+
+def stp_predict_host(h: int, elements: int, q, params, out_avg, out_faces, stream=None) -> None:
+    _check(load().stp_predict_host(h, elements, _ptr(q), _ptr(params), _ptr(out_avg),
+                                   _ptr(out_faces), _stream(stream)), "stp_predict_host")
+
+
+def stp_destroy(h: int | None) -> None:
+    _check(load().stp_destroy(h), "stp_destroy")
+
+
+def stp_reference_tables(order: int, nodes=None, D=None, phi0=None, phi1=None) -> None:
+    _check(load().stp_reference_tables(order, _ptr(nodes), _ptr(D), _ptr(phi0), _ptr(phi1)),
+           "stp_reference_tables")
+
+
+def stp_nodes(h: int) -> int:
+    return int(load().stp_nodes(h))
+
+
+def stp_status_string(status: int) -> str:
+    return load().stp_status_string(status).decode()
+
+
+def stp_last_error() -> str:
+    return load().stp_last_error().decode()
+
+
+def stp_measure_fp64_peak(stream=None) -> float:
+    g = ctypes.c_double()
+    _check(load().stp_measure_fp64_peak(ctypes.byref(g), _stream(stream)), "stp_measure_fp64_peak")
+    return g.value

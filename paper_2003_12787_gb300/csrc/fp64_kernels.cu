@@ -1,0 +1,280 @@
+// FP64 Space-Time Predictor kernels for sm_103a.
+//
+// One CTA owns EPC whole elements (EPC = 1 from N = 6 up). The element's
+// current Taylor term lives in shared memory in structure-of-arrays layout
+// p[quantity][node]; every thread owns NPT nodes and, per Cauchy-Kowalewsky
+// step, forms the 18 directional derivatives its node needs straight from
+// shared memory, combines them with the node's elastic coefficients and adds
+// the new term to the running time average. This is the sum-factorised,
+// dimension-by-dimension scheme of Sec. IV (SplitCK) with the time average
+// accumulated on the fly, mapped onto one SM: the O(N^3 m) live set sits in
+// shared memory, the per-node result in registers.
+//
+// On GB300 the FP64 pipe retires about two DFMA per clock per SM while the
+// SM can issue four warp-instructions per clock, so the kernel is built to
+// minimise FP64 instructions (elastic sparsity: 6 of 9 quantities per
+// direction; dt/((k+2) dx) folded into per-step copies of D; coefficient
+// products shared between outputs) and leaves shared-memory traffic, address
+// arithmetic and synchronisation in the shadow of the FP64 pipe.
+//
+// Taylor bookkeeping: r_k = dt^k/(k+1)! q^(k) satisfies r_0 = q,
+// r_{k+1} = dt/(k+2) * L r_k with L q = -sum_d B_d (D_d q)/dx, and the time
+// average of Eq. (exahypeTimeAverage) divided by dt is sum_{k=0..N} r_k.
+#include "stp_internal.h"
+
+namespace stp {
+namespace {
+
+constexpr int ceil_div(int a, int b) { return (a + b - 1) / b; }
+
+// Quantity slots in p[] / r[] (the state vector order).
+enum : int { V1 = 0, V2, V3, S11, S22, S33, S12, S13, S23 };
+
+template <int N, int NPT, int EPC, bool AVG_SMEM>
+struct Fp64Shape {
+  static constexpr int N3 = N * N * N;
+  static constexpr int T = ceil_div(N3, NPT);       // threads per element
+  static constexpr int BLOCK = T * EPC;
+  static constexpr int S = N3 | 1;                  // odd row stride: no bank aliasing across quantities
+  static constexpr int LDD = N | 1;                 // odd row stride of D: distinct banks per row
+  static constexpr int SLOT = (kQuantities + 4 + (AVG_SMEM ? kQuantities : 0)) * S;
+  static constexpr int TABLE = N * N * LDD + 2 * N;
+  static constexpr size_t SMEM = sizeof(double) * (size_t)(TABLE + EPC * SLOT);
+  static constexpr int MINB_SMEM = (int)((232448 - 1024) / SMEM);
+  static constexpr int MINB_THR = 2048 / BLOCK;
+  static constexpr int MINB = MINB_SMEM < 1 ? 1 : (MINB_SMEM < MINB_THR ? MINB_SMEM : MINB_THR);
+};
+
+template <int N, int NPT, int EPC, bool AVG_SMEM>
+__global__ void __launch_bounds__(Fp64Shape<N, NPT, EPC, AVG_SMEM>::BLOCK,
+                                  Fp64Shape<N, NPT, EPC, AVG_SMEM>::MINB)
+fp64_stp_kernel(const double* __restrict__ q, const double* __restrict__ params,
+                double* __restrict__ out_avg, double* __restrict__ out_faces,
+                const double* __restrict__ tables, int64_t E) {
+  using Sh = Fp64Shape<N, NPT, EPC, AVG_SMEM>;
+  constexpr int N3 = Sh::N3, T = Sh::T, S = Sh::S, LDD = Sh::LDD;
+  constexpr int M = kQuantities;
+  extern __shared__ double smem[];
+  double* sD = smem;                     // [N steps][N rows][LDD]
+  double* sPhi = sD + N * N * LDD;       // phi0[N], phi1[N]
+  const int tid = threadIdx.x;
+  const int el = tid / T;
+  const int lt = tid - el * T;
+  const int64_t e = (int64_t)blockIdx.x * EPC + el;
+  const bool active = (el < EPC) && (e < E);
+  double* sp = sPhi + 2 * N + el * Sh::SLOT;  // p[M][S]: current Taylor term r_k
+  double* sc = sp + M * S;                     // coef[4][S]: 1/rho, lambda, mu, 2 mu
+  double* sa = sc + 4 * S;                     // avg[M][S] when AVG_SMEM
+  double* gavg = out_avg + e * (int64_t)(M * N3);
+
+  for (int i = tid; i < N * N * N; i += blockDim.x) {
+    const int row = i / N, col = i - row * N;  // row = k*N + r
+    sD[row * LDD + col] = tables[i];
+  }
+  for (int i = tid; i < 2 * N; i += blockDim.x) sPhi[i] = tables[N3 + i];
+
+  if (active) {
+    const double* qe = q + e * (int64_t)(M * N3);
+    for (int f = lt; f < M * N3; f += T) {  // coalesced AoS read, SoA scatter
+      const int n = f / M, s = f - n * M;
+      const double v = __ldg(qe + f);
+      sp[s * S + n] = v;
+      if (AVG_SMEM) sa[s * S + n] = v; else gavg[f] = v;
+    }
+    const double* pe = params + e * (int64_t)(kParams * N3);
+    for (int n = lt; n < N3; n += T) {
+      const double rho = __ldg(pe + 3 * n), cp = __ldg(pe + 3 * n + 1), cs = __ldg(pe + 3 * n + 2);
+      const double mu = rho * (cs * cs);
+      sc[n] = 1.0 / rho;
+      sc[S + n] = rho * (cp * cp - 2.0 * (cs * cs));
+      sc[2 * S + n] = mu;
+      sc[3 * S + n] = mu + mu;
+    }
+  }
+  __syncthreads();
+
+  for (int k = 0; k < N; ++k) {
+    const double* Dk = sD + k * N * LDD;
+    double r[NPT][M];
+#pragma unroll
+    for (int j = 0; j < NPT; ++j) {
+      const int n = lt + j * T;
+      if (!active || n >= N3) continue;
+      const int x = n % N, y = (n / N) % N, z = n / (N * N);
+      const double* Dx = Dk + x * LDD;
+      const double* Dy = Dk + y * LDD;
+      const double* Dz = Dk + z * LDD;
+      const double* px = sp + (z * N + y) * N;  // + l
+      const double* py = sp + z * N * N + x;    // + l*N
+      const double* pz = sp + y * N + x;        // + l*N*N
+      double v1 = 0.0, v2 = 0.0, v3 = 0.0, s12 = 0.0, s13 = 0.0, s23 = 0.0;
+      double a = 0.0, b = 0.0, c = 0.0;  // dv1/dx, dv2/dy, dv3/dz
+#pragma unroll
+      for (int l = 0; l < N; ++l) {
+        const double d = Dx[l];
+        v1 = fma(d, px[S11 * S + l], v1);
+        v2 = fma(d, px[S12 * S + l], v2);
+        v3 = fma(d, px[S13 * S + l], v3);
+        a = fma(d, px[V1 * S + l], a);
+        s12 = fma(d, px[V2 * S + l], s12);
+        s13 = fma(d, px[V3 * S + l], s13);
+      }
+#pragma unroll
+      for (int l = 0; l < N; ++l) {
+        const double d = Dy[l];
+        const int o = l * N;
+        v1 = fma(d, py[S12 * S + o], v1);
+        v2 = fma(d, py[S22 * S + o], v2);
+        v3 = fma(d, py[S23 * S + o], v3);
+        s12 = fma(d, py[V1 * S + o], s12);
+        b = fma(d, py[V2 * S + o], b);
+        s23 = fma(d, py[V3 * S + o], s23);
+      }
+#pragma unroll
+      for (int l = 0; l < N; ++l) {
+        const double d = Dz[l];
+        const int o = l * N * N;
+        v1 = fma(d, pz[S13 * S + o], v1);
+        v2 = fma(d, pz[S23 * S + o], v2);
+        v3 = fma(d, pz[S33 * S + o], v3);
+        s13 = fma(d, pz[V1 * S + o], s13);
+        s23 = fma(d, pz[V2 * S + o], s23);
+        c = fma(d, pz[V3 * S + o], c);
+      }
+      const double invrho = sc[n], lam = sc[S + n], mu = sc[2 * S + n], mu2 = sc[3 * S + n];
+      const double ltr = lam * ((a + b) + c);
+      r[j][V1] = invrho * v1;
+      r[j][V2] = invrho * v2;
+      r[j][V3] = invrho * v3;
+      r[j][S11] = fma(mu2, a, ltr);
+      r[j][S22] = fma(mu2, b, ltr);
+      r[j][S33] = fma(mu2, c, ltr);
+      r[j][S12] = mu * s12;
+      r[j][S13] = mu * s13;
+      r[j][S23] = mu * s23;
+      if (AVG_SMEM) {
+#pragma unroll
+        for (int s = 0; s < M; ++s) sa[s * S + n] += r[j][s];
+      } else {
+#pragma unroll
+        for (int s = 0; s < M; ++s) gavg[n * M + s] += r[j][s];
+      }
+    }
+    __syncthreads();  // every thread has read r_k
+    if (k + 1 < N) {
+#pragma unroll
+      for (int j = 0; j < NPT; ++j) {
+        const int n = lt + j * T;
+        if (!active || n >= N3) continue;
+#pragma unroll
+        for (int s = 0; s < M; ++s) sp[s * S + n] = r[j][s];
+      }
+      __syncthreads();  // r_{k+1} visible
+    }
+  }
+
+  if (!active) return;
+  if (AVG_SMEM) {
+    for (int f = lt; f < M * N3; f += T) {
+      const int n = f / M, s = f - n * M;
+      gavg[f] = sa[s * S + n];
+    }
+  }
+  // Face projections of the time average (Sec. II-B): one phi contraction per face.
+  double* fe = out_faces + e * (int64_t)(6 * N * N * M);
+  for (int o = lt; o < 6 * N * N * M; o += T) {
+    const int s = o % M;
+    int rest = o / M;
+    const int bb = rest % N;
+    rest /= N;
+    const int aa = rest % N;
+    const int f = rest / N;
+    const int d = f >> 1;
+    const double* phi = sPhi + (f & 1) * N;
+    int base, stride;
+    if (d == 0) { base = (aa * N + bb) * N; stride = 1; }
+    else if (d == 1) { base = aa * N * N + bb; stride = N; }
+    else { base = aa * N + bb; stride = N * N; }
+    double acc = 0.0;
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+      const int node = base + i * stride;
+      const double v = AVG_SMEM ? sa[s * S + node] : gavg[node * M + s];
+      acc = fma(phi[i], v, acc);
+    }
+    fe[o] = acc;
+  }
+}
+
+template <int N, int NPT, int EPC, bool AVG_SMEM>
+cudaError_t launch_shape(int64_t E, const double* q, const double* params, double* out_avg,
+                         double* out_faces, const double* tables, cudaStream_t stream) {
+  using Sh = Fp64Shape<N, NPT, EPC, AVG_SMEM>;
+  static_assert(Sh::SMEM <= 232448, "shared memory budget of one CTA exceeded");
+  auto kern = fp64_stp_kernel<N, NPT, EPC, AVG_SMEM>;
+  // per device context; cheap, and legal while a stream is being captured
+  cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Sh::SMEM);
+  if (err != cudaSuccess) return err;
+  const int64_t blocks = (E + EPC - 1) / EPC;
+  if (blocks > 0x7fffffffLL) return cudaErrorInvalidValue;
+  kern<<<(unsigned)blocks, Sh::BLOCK, Sh::SMEM, stream>>>(q, params, out_avg, out_faces, tables, E);
+  return cudaGetLastError();
+}
+
+// Launch shapes per N: nodes per thread, elements per CTA, average in smem.
+#define STP_FP64_SHAPES(X) \
+  X(1, 1, 64, true)        \
+  X(2, 1, 32, true)        \
+  X(3, 1, 8, true)         \
+  X(4, 1, 4, true)         \
+  X(5, 1, 2, true)         \
+  X(6, 1, 1, true)         \
+  X(7, 2, 1, true)         \
+  X(8, 2, 1, true)         \
+  X(9, 2, 1, true)         \
+  X(10, 2, 1, true)        \
+  X(11, 2, 1, false)       \
+  X(12, 2, 1, false)
+
+__global__ void fp64_peak_kernel(double* sink, int iters) {
+  double x0 = threadIdx.x * 1e-3, x1 = x0 + 1, x2 = x0 + 2, x3 = x0 + 3;
+  double x4 = x0 + 4, x5 = x0 + 5, x6 = x0 + 6, x7 = x0 + 7;
+  const double a = 1.0000001, b = 1e-9;
+  for (int it = 0; it < iters; ++it) {
+    x0 = fma(x0, a, b); x1 = fma(x1, a, b); x2 = fma(x2, a, b); x3 = fma(x3, a, b);
+    x4 = fma(x4, a, b); x5 = fma(x5, a, b); x6 = fma(x6, a, b); x7 = fma(x7, a, b);
+  }
+  const double s = ((x0 + x1) + (x2 + x3)) + ((x4 + x5) + (x6 + x7));
+  if (s == 123.456) sink[0] = s;  // keeps the loop alive; never true in practice
+}
+
+}  // namespace
+
+int fp64_elements_per_cta(int N) {
+  switch (N) {
+#define X(n, npt, epc, avg) case n: return epc;
+    STP_FP64_SHAPES(X)
+#undef X
+    default: return 1;
+  }
+}
+
+cudaError_t launch_fp64(int N, int64_t E, const double* q, const double* params,
+                        double* out_avg, double* out_faces, const double* tables,
+                        cudaStream_t stream) {
+  switch (N) {
+#define X(n, npt, epc, avg) \
+  case n: return launch_shape<n, npt, epc, avg>(E, q, params, out_avg, out_faces, tables, stream);
+    STP_FP64_SHAPES(X)
+#undef X
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+cudaError_t launch_fp64_peak(double* sink, int blocks, int threads, int iters,
+                             cudaStream_t stream) {
+  fp64_peak_kernel<<<blocks, threads, 0, stream>>>(sink, iters);
+  return cudaGetLastError();
+}
+
+}  // namespace stp

@@ -1,0 +1,301 @@
+// C ABI of the Space-Time Predictor library (declared in include/stp.h).
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+
+#include "stp_internal.h"
+
+struct stp_handle_s {
+  int N = 0;
+  int device = -1;
+  double dx = 0.0, dt = 0.0;
+  stp::HostTables host;
+  double* d_tables = nullptr;  // step matrices, phi0, phi1 (device)
+  // host-buffer path: chunked pipeline state, created on first use
+  static constexpr int kStages = 3;
+  cudaStream_t streams[kStages] = {nullptr, nullptr, nullptr};
+  cudaEvent_t done[kStages] = {nullptr, nullptr, nullptr};
+  double* stage_buf[kStages] = {nullptr, nullptr, nullptr};
+  int64_t stage_elems = 0;
+};
+
+namespace {
+
+thread_local std::string g_last_error;
+
+stp_status fail(stp_status s, const std::string& msg) {
+  g_last_error = msg;
+  return s;
+}
+
+stp_status cuda_fail(cudaError_t e, const char* what) {
+  return fail(STP_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+
+bool overlap(const void* a, size_t na, const void* b, size_t nb) {
+  const uintptr_t pa = reinterpret_cast<uintptr_t>(a), pb = reinterpret_cast<uintptr_t>(b);
+  return pa < pb + nb && pb < pa + na;
+}
+
+// Checks that p is device (or managed) memory reachable from `device`.
+stp_status check_device_ptr(const void* p, int device, const char* name) {
+  cudaPointerAttributes attr;
+  cudaError_t e = cudaPointerGetAttributes(&attr, p);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(STP_ERR_INVALID_ARG, std::string(name) + ": not a CUDA pointer");
+  }
+  if (attr.type != cudaMemoryTypeDevice && attr.type != cudaMemoryTypeManaged)
+    return fail(STP_ERR_INVALID_ARG, std::string(name) + ": not device memory");
+  if (attr.type == cudaMemoryTypeDevice && attr.device != device)
+    return fail(STP_ERR_INVALID_ARG, std::string(name) + ": on another device than the handle");
+  return STP_OK;
+}
+
+struct Sizes {
+  size_t q, params, avg, faces;  // bytes per element
+};
+
+Sizes sizes_per_element(int N) {
+  const size_t n3 = (size_t)N * N * N;
+  return {n3 * stp::kQuantities * 8, n3 * stp::kParams * 8, n3 * stp::kQuantities * 8,
+          (size_t)6 * N * N * stp::kQuantities * 8};
+}
+
+stp_status validate_common(stp_handle h, int64_t E, const void* q, const void* params,
+                           const void* avg, const void* faces) {
+  if (!h || h->N < 1) return fail(STP_ERR_INVALID_ARG, "invalid handle");
+  if (E < 0) return fail(STP_ERR_INVALID_ARG, "elements < 0");
+  if (E == 0) return STP_OK;
+  if (!q || !params || !avg || !faces) return fail(STP_ERR_INVALID_ARG, "null buffer");
+  if (!aligned16(q) || !aligned16(params) || !aligned16(avg) || !aligned16(faces))
+    return fail(STP_ERR_INVALID_ARG, "buffers must be 16-byte aligned");
+  const Sizes s = sizes_per_element(h->N);
+  const size_t E_ = (size_t)E;
+  if (E_ > ((size_t)1 << 40) / s.q) return fail(STP_ERR_INVALID_ARG, "elements too large");
+  const void* outs[2] = {avg, faces};
+  const size_t nout[2] = {s.avg * E_, s.faces * E_};
+  const void* ins[2] = {q, params};
+  const size_t nin[2] = {s.q * E_, s.params * E_};
+  for (int i = 0; i < 2; ++i)
+    for (int j = 0; j < 2; ++j)
+      if (overlap(outs[i], nout[i], ins[j], nin[j]))
+        return fail(STP_ERR_INVALID_ARG, "an output overlaps an input");
+  if (overlap(avg, nout[0], faces, nout[1])) return fail(STP_ERR_INVALID_ARG, "outputs overlap");
+  return STP_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* stp_status_string(stp_status s) {
+  switch (s) {
+    case STP_OK: return "ok";
+    case STP_ERR_INVALID_ARG: return "invalid argument";
+    case STP_ERR_UNSUPPORTED: return "unsupported configuration";
+    case STP_ERR_OOM: return "out of memory";
+    case STP_ERR_CUDA: return "CUDA error";
+    case STP_ERR_TIMEOUT: return "device-side wait timed out";
+  }
+  return "unknown status";
+}
+
+const char* stp_last_error(void) { return g_last_error.c_str(); }
+
+stp_status stp_create(int order, int m, double dx, double dt, stp_handle* out) {
+  if (!out) return fail(STP_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  const int N = order + 1;
+  if (m != stp::kQuantities) return fail(STP_ERR_UNSUPPORTED, "only m = 9 (elastic) is implemented");
+  if (N < 1 || N > stp::kMaxNodes) return fail(STP_ERR_UNSUPPORTED, "order must be in [0, 11]");
+  if (!(dx > 0.0) || !std::isfinite(dx)) return fail(STP_ERR_INVALID_ARG, "dx must be > 0 and finite");
+  if (!(dt > 0.0) || !std::isfinite(dt)) return fail(STP_ERR_INVALID_ARG, "dt must be > 0 and finite");
+  stp_handle h = new (std::nothrow) stp_handle_s;
+  if (!h) return fail(STP_ERR_OOM, "host allocation failed");
+  h->N = N;
+  h->dx = dx;
+  h->dt = dt;
+  if (!stp::make_tables(N, &h->host)) {
+    delete h;
+    return fail(STP_ERR_UNSUPPORTED, "node computation did not converge");
+  }
+  cudaError_t e = cudaGetDevice(&h->device);
+  if (e != cudaSuccess) { delete h; return cuda_fail(e, "cudaGetDevice"); }
+  const int nt = stp::table_doubles(N);
+  double buf[stp::kMaxNodes * stp::kMaxNodes * stp::kMaxNodes + 2 * stp::kMaxNodes];
+  stp::make_step_matrices(h->host, dx, dt, buf);
+  std::memcpy(buf + N * N * N, h->host.phi0, sizeof(double) * N);
+  std::memcpy(buf + N * N * N + N, h->host.phi1, sizeof(double) * N);
+  e = cudaMalloc(&h->d_tables, sizeof(double) * nt);
+  if (e != cudaSuccess) { cudaGetLastError(); delete h; return fail(STP_ERR_OOM, "cudaMalloc of tables failed"); }
+  e = cudaMemcpy(h->d_tables, buf, sizeof(double) * nt, cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) { cudaFree(h->d_tables); delete h; return cuda_fail(e, "table upload"); }
+  *out = h;
+  return STP_OK;
+}
+
+stp_status stp_destroy(stp_handle h) {
+  if (!h) return STP_OK;
+  int prev = -1;
+  cudaGetDevice(&prev);
+  if (h->device >= 0) cudaSetDevice(h->device);
+  for (int i = 0; i < stp_handle_s::kStages; ++i) {
+    if (h->streams[i]) cudaStreamSynchronize(h->streams[i]);
+    if (h->stage_buf[i]) cudaFree(h->stage_buf[i]);
+    if (h->done[i]) cudaEventDestroy(h->done[i]);
+    if (h->streams[i]) cudaStreamDestroy(h->streams[i]);
+  }
+  if (h->d_tables) cudaFree(h->d_tables);
+  if (prev >= 0) cudaSetDevice(prev);
+  delete h;
+  return STP_OK;
+}
+
+int stp_nodes(stp_handle h) { return h ? h->N : -1; }
+
+stp_status stp_reference_tables(int order, double* nodes, double* D, double* phi0, double* phi1) {
+  const int N = order + 1;
+  stp::HostTables t;
+  if (N < 1 || N > stp::kMaxNodes || !stp::make_tables(N, &t))
+    return fail(STP_ERR_UNSUPPORTED, "order must be in [0, 11]");
+  if (nodes) std::memcpy(nodes, t.nodes, sizeof(double) * N);
+  if (D) std::memcpy(D, t.D, sizeof(double) * N * N);
+  if (phi0) std::memcpy(phi0, t.phi0, sizeof(double) * N);
+  if (phi1) std::memcpy(phi1, t.phi1, sizeof(double) * N);
+  return STP_OK;
+}
+
+stp_status stp_predict(stp_handle h, int64_t elements, const double* q, const double* params,
+                       double* out_avg, double* out_faces, void* stream) {
+  stp_status s = validate_common(h, elements, q, params, out_avg, out_faces);
+  if (s != STP_OK || elements == 0) return s;
+  const char* names[4] = {"q", "params", "out_avg", "out_faces"};
+  const void* ptrs[4] = {q, params, out_avg, out_faces};
+  for (int i = 0; i < 4; ++i)
+    if ((s = check_device_ptr(ptrs[i], h->device, names[i])) != STP_OK) return s;
+  cudaError_t e = stp::launch_fp64(h->N, elements, q, params, out_avg, out_faces, h->d_tables,
+                                   static_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) return cuda_fail(e, "STP kernel launch");
+  return STP_OK;
+}
+
+stp_status stp_predict_host(stp_handle h, int64_t elements, const double* q, const double* params,
+                            double* out_avg, double* out_faces, void* stream) {
+  stp_status s = validate_common(h, elements, q, params, out_avg, out_faces);
+  if (s != STP_OK || elements == 0) return s;
+  const Sizes sz = sizes_per_element(h->N);
+  const size_t per_elem = sz.q + sz.params + sz.avg + sz.faces;
+  int prev = -1;
+  cudaGetDevice(&prev);
+  if (prev != h->device) cudaSetDevice(h->device);
+  struct Restore {
+    int dev;
+    ~Restore() { if (dev >= 0) cudaSetDevice(dev); }
+  } restore{prev};
+  cudaError_t e;
+  // Chunk: ~64 MiB of inputs+outputs per stage, a multiple of the CTA width.
+  const int epc = stp::fp64_elements_per_cta(h->N);
+  int64_t chunk = (int64_t)((64u << 20) / per_elem);
+  chunk = chunk < epc ? epc : (chunk / epc) * epc;
+  if (chunk > elements) chunk = elements;
+  if (h->stage_elems < chunk) {
+    for (int i = 0; i < stp_handle_s::kStages; ++i) {
+      if (h->streams[i]) cudaStreamSynchronize(h->streams[i]);
+      if (h->stage_buf[i]) { cudaFree(h->stage_buf[i]); h->stage_buf[i] = nullptr; }
+    }
+    h->stage_elems = 0;
+    for (int i = 0; i < stp_handle_s::kStages; ++i) {
+      if (!h->streams[i]) {
+        if ((e = cudaStreamCreateWithFlags(&h->streams[i], cudaStreamNonBlocking)) != cudaSuccess)
+          return cuda_fail(e, "cudaStreamCreate");
+        if ((e = cudaEventCreateWithFlags(&h->done[i], cudaEventDisableTiming)) != cudaSuccess)
+          return cuda_fail(e, "cudaEventCreate");
+      }
+      if (cudaMalloc(&h->stage_buf[i], per_elem * (size_t)chunk) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(STP_ERR_OOM, "cudaMalloc of staging buffers failed");
+      }
+    }
+    h->stage_elems = chunk;
+  }
+  // order after the caller's stream
+  cudaEvent_t start;
+  if ((e = cudaEventCreateWithFlags(&start, cudaEventDisableTiming)) != cudaSuccess)
+    return cuda_fail(e, "cudaEventCreate");
+  cudaEventRecord(start, static_cast<cudaStream_t>(stream));
+  for (int i = 0; i < stp_handle_s::kStages; ++i) cudaStreamWaitEvent(h->streams[i], start, 0);
+  cudaEventDestroy(start);
+
+  const char* hq = reinterpret_cast<const char*>(q);
+  const char* hp = reinterpret_cast<const char*>(params);
+  char* ha = reinterpret_cast<char*>(out_avg);
+  char* hf = reinterpret_cast<char*>(out_faces);
+  int stage = 0;
+  for (int64_t base = 0; base < elements; base += chunk, stage = (stage + 1) % stp_handle_s::kStages) {
+    const int64_t n = (elements - base < chunk) ? elements - base : chunk;
+    cudaStream_t st = h->streams[stage];
+    char* b = reinterpret_cast<char*>(h->stage_buf[stage]);
+    double* dq = reinterpret_cast<double*>(b);
+    double* dp = reinterpret_cast<double*>(b + sz.q * chunk);
+    double* da = reinterpret_cast<double*>(b + (sz.q + sz.params) * chunk);
+    double* df = reinterpret_cast<double*>(b + (sz.q + sz.params + sz.avg) * chunk);
+    // one stream per stage: its previous chunk's copies and kernel finish first
+    if ((e = cudaMemcpyAsync(dq, hq + base * sz.q, n * sz.q, cudaMemcpyHostToDevice, st)) != cudaSuccess ||
+        (e = cudaMemcpyAsync(dp, hp + base * sz.params, n * sz.params, cudaMemcpyHostToDevice, st)) != cudaSuccess)
+      return cuda_fail(e, "host-to-device copy");
+    e = stp::launch_fp64(h->N, n, dq, dp, da, df, h->d_tables, st);
+    if (e != cudaSuccess) return cuda_fail(e, "STP kernel launch");
+    if ((e = cudaMemcpyAsync(ha + base * sz.avg, da, n * sz.avg, cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
+        (e = cudaMemcpyAsync(hf + base * sz.faces, df, n * sz.faces, cudaMemcpyDeviceToHost, st)) != cudaSuccess)
+      return cuda_fail(e, "device-to-host copy");
+  }
+  for (int i = 0; i < stp_handle_s::kStages; ++i) {
+    if ((e = cudaStreamSynchronize(h->streams[i])) != cudaSuccess)
+      return cuda_fail(e, "host-path synchronisation");
+  }
+  if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "host-path copy");
+  return STP_OK;
+}
+
+stp_status stp_measure_fp64_peak(double* gflops, void* stream) {
+  if (!gflops) return fail(STP_ERR_INVALID_ARG, "gflops is NULL");
+  int dev = 0, sms = 0;
+  cudaError_t e;
+  if ((e = cudaGetDevice(&dev)) != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  double* sink = nullptr;
+  if (cudaMalloc(&sink, 64) != cudaSuccess) { cudaGetLastError(); return fail(STP_ERR_OOM, "cudaMalloc"); }
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const int threads = 256, blocks = sms * 4, iters = 4096;
+  cudaEvent_t a, b;
+  cudaEventCreate(&a);
+  cudaEventCreate(&b);
+  // warm-up long enough (~100 ms) for the SM clock to leave its idle state
+  for (int rep = 0; rep < 6; ++rep) stp::launch_fp64_peak(sink, blocks, threads, iters, st);
+  double best = 0.0;
+  for (int rep = 0; rep < 5; ++rep) {
+    cudaEventRecord(a, st);
+    e = stp::launch_fp64_peak(sink, blocks, threads, iters, st);
+    cudaEventRecord(b, st);
+    if (e != cudaSuccess) break;
+    if ((e = cudaEventSynchronize(b)) != cudaSuccess) break;
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, a, b);
+    const double flops = 2.0 * 8.0 * iters * (double)blocks * threads;
+    const double g = flops / (ms * 1e-3) / 1e9;
+    if (g > best) best = g;
+  }
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  cudaFree(sink);
+  if (e != cudaSuccess) return cuda_fail(e, "fp64 peak probe");
+  *gflops = best;
+  return STP_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,45 @@
+// Internal declarations shared by the translation units of the CUDA library.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/stp.h"
+
+namespace stp {
+
+constexpr int kQuantities = 9;  // v1 v2 v3 s11 s22 s33 s12 s13 s23
+constexpr int kParams = 3;      // rho cp cs
+constexpr int kMaxNodes = 12;
+
+// Host-side tables of the reference element for N nodes per dimension, in
+// double precision, computed in extended precision (tables.cpp).
+struct HostTables {
+  int N = 0;
+  double nodes[kMaxNodes];
+  double D[kMaxNodes * kMaxNodes];  // D[i*N+j] = phi_j'(xi_i)
+  double phi0[kMaxNodes];
+  double phi1[kMaxNodes];
+};
+
+// Gauss-Legendre nodes, derivative matrix and face vectors. Returns false if
+// the Newton iteration did not converge (never for 1 <= N <= 12).
+bool make_tables(int N, HostTables* t);
+
+// Per-step scaled derivative matrices: Dk[k][i][j] = D[i][j] * dt / ((k+2) dx)
+// for k = 0..N-1, rounded once from extended precision.
+void make_step_matrices(const HostTables& t, double dx, double dt, double* Dk);
+
+// Device tables: [N][N][N] step matrices, then phi0[N], then phi1[N].
+inline int table_doubles(int N) { return N * N * N + 2 * N; }
+
+// Kernel launchers (fp64_kernels.cu). Return cudaSuccess or the launch error.
+cudaError_t launch_fp64(int N, int64_t E, const double* q, const double* params,
+                        double* out_avg, double* out_faces, const double* tables,
+                        cudaStream_t stream);
+// Elements per CTA the FP64 kernel uses for N nodes (chunk sizes are multiples).
+int fp64_elements_per_cta(int N);
+
+cudaError_t launch_fp64_peak(double* sink, int blocks, int threads, int iters,
+                             cudaStream_t stream);
+
+}  // namespace stp

@@ -1,0 +1,73 @@
+"""Handle wrapper for torch tensors (allocation of outputs; no arithmetic)."""
+from __future__ import annotations
+
+import torch
+
+from . import _binding as B
+
+
+class Predictor:
+    """Owns one stp_handle for (order, dx, dt) on the current CUDA device."""
+
+    def __init__(self, order: int, dx: float, dt: float, m: int = 9):
+        self.order = order
+        self.N = order + 1
+        self.dx = dx
+        self.dt = dt
+        self.handle = B.stp_create(order, m, dx, dt)
+
+    def close(self):
+        if self.handle is not None:
+            B.stp_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def empty_outputs(self, E: int, device="cuda", pin_memory: bool = False):
+        N = self.N
+        if str(device) == "cpu":
+            avg = torch.empty((E, N, N, N, 9), dtype=torch.float64, pin_memory=pin_memory)
+            faces = torch.empty((E, 6, N, N, 9), dtype=torch.float64, pin_memory=pin_memory)
+        else:
+            avg = torch.empty((E, N, N, N, 9), dtype=torch.float64, device=device)
+            faces = torch.empty((E, 6, N, N, 9), dtype=torch.float64, device=device)
+        return avg, faces
+
+    def _check_inputs(self, q: torch.Tensor, params: torch.Tensor):
+        N = self.N
+        if q.dtype != torch.float64 or params.dtype != torch.float64:
+            raise TypeError("q and params must be float64")
+        if q.dim() != 5 or tuple(q.shape[1:]) != (N, N, N, 9):
+            raise ValueError(f"q must be [E][{N}][{N}][{N}][9], got {tuple(q.shape)}")
+        if tuple(params.shape) != (q.shape[0], N, N, N, 3):
+            raise ValueError(f"params must be [E][{N}][{N}][{N}][3], got {tuple(params.shape)}")
+        if not (q.is_contiguous() and params.is_contiguous()):
+            raise ValueError("q and params must be contiguous")
+
+    def predict(self, q: torch.Tensor, params: torch.Tensor, out=None, stream=None):
+        """Enqueue on `stream` (default: torch's current stream) for device tensors."""
+        self._check_inputs(q, params)
+        E = q.shape[0]
+        avg, faces = out if out is not None else self.empty_outputs(E, device=q.device)
+        if stream is None and q.is_cuda:
+            stream = torch.cuda.current_stream(q.device)
+        B.stp_predict(self.handle, E, q, params, avg, faces, stream)
+        return avg, faces
+
+    def predict_host(self, q: torch.Tensor, params: torch.Tensor, out=None, stream=None):
+        """Host tensors in and out (pinned gives full copy bandwidth); synchronous."""
+        self._check_inputs(q, params)
+        E = q.shape[0]
+        avg, faces = out if out is not None else self.empty_outputs(E, device="cpu")
+        B.stp_predict_host(self.handle, E, q, params, avg, faces, stream)
+        return avg, faces

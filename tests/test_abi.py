@@ -1,0 +1,127 @@
+"""CPU-side checks of the C-ABI library: it loads, exports every symbol that
+include/stp.h declares, and its host-computed tables agree with closed forms,
+a 50-digit reference and the oracle's independent construction. Argument
+errors that are detected before any CUDA call are checked too. No kernel runs.
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+import os
+import re
+
+import numpy as np
+import pytest
+
+import oracle
+import paper_2003_12787_gb300 as stp
+from paper_2003_12787_gb300 import _binding, build
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    build.build()
+    return _binding.load()
+
+
+def declared_functions():
+    text = open(os.path.join(ROOT, "include", "stp.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(stp_[a-z0-9_]+)\s*\(", text)))
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for required in ("stp_create", "stp_predict", "stp_destroy", "stp_predict_host"):
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    for name in declared_functions():
+        assert hasattr(lib, name), name
+
+
+def test_library_has_no_oracle_dependency():
+    # the product library must not link or embed the oracle
+    data = open(build.LIB, "rb").read()
+    assert b"oracle_stp" not in data and b"liboracle" not in data
+
+
+def test_status_strings(lib):
+    for s in range(0, -6, -1):
+        assert stp.stp_status_string(s) != "unknown status"
+
+
+@pytest.mark.parametrize("N", range(1, 13))
+def test_library_tables_match_oracle_tables(lib, N):
+    xi = np.zeros(N)
+    D = np.zeros((N, N))
+    p0 = np.zeros(N)
+    p1 = np.zeros(N)
+    stp.stp_reference_tables(N - 1, xi, D, p0, p1)
+    xo, Do, p0o, p1o = oracle.tables(N)
+    assert np.abs(xi - xo).max() <= 4e-16
+    assert np.abs(D - Do).max() <= 1e-14 * max(1.0, np.abs(Do).max())
+    assert np.abs(p0 - p0o).max() <= 2e-14 and np.abs(p1 - p1o).max() <= 2e-14
+
+
+@pytest.mark.parametrize("N", [3, 8, 12])
+def test_library_tables_against_50_digits(lib, N):
+    mpmath = pytest.importorskip("mpmath")
+    mp = mpmath.mp
+    mp.dps = 50
+    xi = np.zeros(N)
+    D = np.zeros((N, N))
+    p1 = np.zeros(N)
+    stp.stp_reference_tables(N - 1, xi, D, None, p1)
+    nodes = [mp.findroot(lambda x: mpmath.legendre(N, 2 * x - 1), mp.mpf(x)) for x in xi]
+    for i in range(N):
+        for j in range(N):
+            # product-rule derivative of the j-th Lagrange polynomial at node i
+            s = mp.mpf(0)
+            for m in range(N):
+                if m == j:
+                    continue
+                t = 1 / (nodes[j] - nodes[m])
+                for l in range(N):
+                    if l not in (j, m):
+                        t *= (nodes[i] - nodes[l]) / (nodes[j] - nodes[l])
+                s += t
+            assert abs(D[i, j] - float(s)) <= 2e-15 * max(1.0, float(abs(s))) + 1e-15 * N * N
+        lj = mpmath.fprod([(1 - nodes[l]) / (nodes[i] - nodes[l]) for l in range(N) if l != i])
+        assert abs(p1[i] - float(lj)) <= 2e-15
+
+
+def test_reference_tables_reject_bad_order(lib):
+    with pytest.raises(stp.STPError) as ei:
+        stp.stp_reference_tables(12)
+    assert ei.value.status == _binding.STP_ERR_UNSUPPORTED
+
+
+def test_create_rejects_before_touching_the_gpu(lib):
+    for args, status in [((7, 8, 0.1, 0.01), _binding.STP_ERR_UNSUPPORTED),
+                         ((12, 9, 0.1, 0.01), _binding.STP_ERR_UNSUPPORTED),
+                         ((-2, 9, 0.1, 0.01), _binding.STP_ERR_UNSUPPORTED),
+                         ((3, 9, 0.0, 0.01), _binding.STP_ERR_INVALID_ARG),
+                         ((3, 9, 0.1, -1.0), _binding.STP_ERR_INVALID_ARG),
+                         ((3, 9, math.inf, 0.01), _binding.STP_ERR_INVALID_ARG),
+                         ((3, 9, 0.1, math.nan), _binding.STP_ERR_INVALID_ARG)]:
+        with pytest.raises(stp.STPError) as ei:
+            stp.stp_create(*args)
+        assert ei.value.status == status, args
+
+
+def test_predict_rejects_null_handle(lib):
+    with pytest.raises(stp.STPError) as ei:
+        stp.stp_predict(None, 1, 16, 16, 16, 16)
+    assert ei.value.status == _binding.STP_ERR_INVALID_ARG
+    stp.stp_destroy(None)  # NULL is a no-op
+
+
+def test_binding_fails_loudly_without_library(monkeypatch, tmp_path):
+    monkeypatch.setattr(build, "LIB", str(tmp_path / "missing.so"))
+    monkeypatch.setattr(_binding, "_lib", None)
+    with pytest.raises(RuntimeError, match="no CPU fallback"):
+        _binding.load()

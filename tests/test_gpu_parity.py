@@ -1,0 +1,185 @@
+"""GPU parity: the CUDA STP (through the C ABI) against the FP64 oracle.
+
+Bar (FP64 path): for every output array - the time average and each of the
+six face arrays - max|gpu - oracle| / max|oracle| <= 1e-12. Full-size
+workloads are checked on a sample of elements, which the oracle computes one
+by one (the predictor is element-local, so a sample is an exact subproblem).
+"""
+from __future__ import annotations
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import paper_2003_12787_gb300 as stp
+from paper_2003_12787_gb300 import _binding
+from paper_2003_12787_gb300.inputs import elastic_problem
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-12
+
+
+def rel(a, b):
+    a = np.asarray(a)
+    b = np.asarray(b)
+    s = np.abs(b).max()
+    return float(np.abs(a - b).max() / (s if s > 0 else 1.0))
+
+
+def assert_parity(avg, faces, avg_ref, faces_ref, tol=TOL):
+    assert rel(avg, avg_ref) <= tol, rel(avg, avg_ref)
+    for f in range(6):
+        e = rel(faces[:, f], faces_ref[:, f])
+        assert e <= tol, (f, e)
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    stp.build.build()
+    _binding.load()
+
+
+def run_gpu(prob, stream=None):
+    q = prob.q.cuda().contiguous()
+    params = prob.params.cuda().contiguous()
+    with stp.Predictor(prob.N - 1, prob.h, prob.dt) as P:
+        avg, faces = P.predict(q, params, stream=stream)
+        torch.cuda.synchronize()
+    return avg.cpu().numpy(), faces.cpu().numpy()
+
+
+@pytest.mark.parametrize("N", range(1, 13))
+@pytest.mark.parametrize("E", [1, 7])
+def test_parity_every_order_small(N, E):
+    prob = elastic_problem(N, E=E, seed_material=1001 + N, seed_waves=1002 + N)
+    avg, faces = run_gpu(prob)
+    avg_ref, faces_ref = oracle.stp(prob.q.numpy(), prob.params.numpy(), prob.h, prob.dt)
+    assert_parity(avg, faces, avg_ref, faces_ref)
+
+
+@pytest.mark.parametrize("N,E", [(2, 97), (3, 33), (4, 37), (5, 11), (6, 5), (9, 3), (11, 2), (12, 3)])
+def test_parity_ragged_tiles(N, E):
+    # element counts that are not multiples of the elements per CTA
+    prob = elastic_problem(N, E=E, seed_material=7 * N, seed_waves=11 * N)
+    avg, faces = run_gpu(prob)
+    avg_ref, faces_ref = oracle.stp(prob.q.numpy(), prob.params.numpy(), prob.h, prob.dt)
+    assert_parity(avg, faces, avg_ref, faces_ref)
+
+
+def test_parity_order3_512_elements_full():
+    """Order 3 (N=4), 8^3 elements of side 1/8: every element checked."""
+    prob = elastic_problem(4, grid=(8, 8, 8))
+    avg, faces = run_gpu(prob)
+    avg_ref, faces_ref = oracle.stp(prob.q.numpy(), prob.params.numpy(), prob.h, prob.dt)
+    assert_parity(avg, faces, avg_ref, faces_ref)
+
+
+def _sampled_full_size(N, grid, h, n_sample, seed):
+    prob = elastic_problem(N, grid=grid, h=h, device="cuda")
+    E = prob.E
+    with stp.Predictor(N - 1, prob.h, prob.dt) as P:
+        avg, faces = P.predict(prob.q, prob.params)
+        torch.cuda.synchronize()
+    rng = np.random.default_rng(seed)
+    idx = np.unique(np.concatenate([[0, E - 1], rng.choice(E, n_sample, replace=False)]))
+    it = torch.as_tensor(idx, device="cuda")
+    q_s = prob.q[it].cpu().numpy()
+    p_s = prob.params[it].cpu().numpy()
+    avg_ref, faces_ref = oracle.stp(q_s, p_s, prob.h, prob.dt)
+    assert_parity(avg[it].cpu().numpy(), faces[it].cpu().numpy(), avg_ref, faces_ref)
+    # outputs everywhere are finite and the time average differs from q
+    assert torch.isfinite(avg).all() and torch.isfinite(faces).all()
+    assert (avg - prob.q).abs().max() > 0
+
+
+def test_parity_order7_32768_elements_sampled():
+    """Order 7 (N=8), 32^3 elements of side 1/32, one launch, sampled elements."""
+    _sampled_full_size(8, (32, 32, 32), 1.0 / 32, 96, seed=1)
+
+
+def test_parity_order9_16384_elements_sampled():
+    """Order 9 (N=10), 32x32x16 elements of side 1/32 (FP64 path), sampled."""
+    _sampled_full_size(10, (32, 32, 16), 1.0 / 32, 48, seed=2)
+
+
+def test_constant_state_exact_on_gpu():
+    N, E = 6, 9
+    prob = elastic_problem(N, E=E)
+    q = prob.q[:, :1, :1, :1, :].expand(E, N, N, N, 9).contiguous()
+    prob.q = q
+    avg, faces = run_gpu(prob)
+    qn = q.numpy()
+    assert rel(avg, qn) <= 1e-13
+    for f in range(6):
+        assert rel(faces[:, f], qn[:, 0]) <= 1e-13
+
+
+def test_element_permutation_is_bitwise():
+    prob = elastic_problem(8, E=40)
+    avg, faces = run_gpu(prob)
+    perm = torch.randperm(40, generator=torch.Generator().manual_seed(3))
+    prob.q = prob.q[perm].contiguous()
+    prob.params = prob.params[perm].contiguous()
+    avg_p, faces_p = run_gpu(prob)
+    assert np.array_equal(avg_p, avg[perm.numpy()])
+    assert np.array_equal(faces_p, faces[perm.numpy()])
+
+
+def test_host_path_equals_device_path_bitwise():
+    for N, E in [(4, 1000), (8, 300), (12, 5)]:
+        prob = elastic_problem(N, E=E)
+        avg_d, faces_d = run_gpu(prob)
+        with stp.Predictor(N - 1, prob.h, prob.dt) as P:
+            q = prob.q.pin_memory()
+            params = prob.params.pin_memory()
+            avg_h, faces_h = P.predict_host(q, params)
+            avg_h2, faces_h2 = P.predict_host(prob.q, prob.params)  # pageable
+        assert np.array_equal(avg_h.numpy(), avg_d) and np.array_equal(faces_h.numpy(), faces_d)
+        assert np.array_equal(avg_h2.numpy(), avg_d) and np.array_equal(faces_h2.numpy(), faces_d)
+
+
+def test_non_default_stream_and_zero_elements():
+    prob = elastic_problem(5, E=6)
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        avg, faces = run_gpu(prob, stream=s)
+    avg_ref, faces_ref = oracle.stp(prob.q.numpy(), prob.params.numpy(), prob.h, prob.dt)
+    assert_parity(avg, faces, avg_ref, faces_ref)
+    with stp.Predictor(4, prob.h, prob.dt) as P:
+        empty = torch.empty(0, dtype=torch.float64, device="cuda")
+        stp.stp_predict(P.handle, 0, empty, empty, empty, empty)  # no launch, STP_OK
+
+
+def test_argument_errors_leave_outputs_untouched():
+    N, E = 4, 3
+    prob = elastic_problem(N, E=E)
+    q = prob.q.cuda()
+    params = prob.params.cuda()
+    with stp.Predictor(N - 1, prob.h, prob.dt) as P:
+        avg = torch.full((E, N, N, N, 9), 7.0, dtype=torch.float64, device="cuda")
+        faces = torch.full((E, 6, N, N, 9), 7.0, dtype=torch.float64, device="cuda")
+        big = torch.zeros(E * N ** 3 * 9 + 2, dtype=torch.float64, device="cuda")
+        bad_cases = [
+            (prob.q, params, avg, faces),                   # host input to the device entry
+            (big[1:], params, avg, faces),                  # 8-byte, not 16-byte aligned
+            (q, params, q, faces),                          # output aliases an input
+            (q, params, avg, avg),                          # outputs overlap
+        ]
+        for args in bad_cases:
+            with pytest.raises(stp.STPError) as ei:
+                stp.stp_predict(P.handle, E, *args)
+            assert ei.value.status == _binding.STP_ERR_INVALID_ARG
+        torch.cuda.synchronize()
+        assert bool((avg == 7.0).all()) and bool((faces == 7.0).all())
+        with pytest.raises(stp.STPError):
+            stp.stp_predict(P.handle, -1, q, params, avg, faces)
+
+
+def test_fp64_peak_probe_is_plausible():
+    g = stp.stp_measure_fp64_peak()
+    # GB300 FP64 is about 1.2 TFLOP/s; anything far outside means a broken probe
+    assert 300.0 < g < 5000.0, g
