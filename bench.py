@@ -40,6 +40,8 @@ WORKLOADS = {
                "order-7 (N=8) elastic STP, 32^3=32768 elements of side 1/32, one launch"),
     "order3": (4, (8, 8, 8), 1.0 / 8,
                "order-3 (N=4) elastic STP, 8^3=512 elements of side 1/8, one launch"),
+    "order7_small": (8, (16, 16, 16), 1.0 / 32,
+                     "order-7 (N=8) elastic STP, 16^3=4096 elements of side 1/32, one launch"),
     "order9": (10, (32, 32, 16), 1.0 / 32,
                "order-9 (N=10) elastic STP, 32x32x16=16384 elements of side 1/32, one launch"),
 }
