@@ -236,18 +236,6 @@ cudaError_t launch_shape(int64_t E, const double* q, const double* params, doubl
   X(11, 2, 1, false)       \
   X(12, 2, 1, false)
 
-__global__ void fp64_peak_kernel(double* sink, int iters) {
-  double x0 = threadIdx.x * 1e-3, x1 = x0 + 1, x2 = x0 + 2, x3 = x0 + 3;
-  double x4 = x0 + 4, x5 = x0 + 5, x6 = x0 + 6, x7 = x0 + 7;
-  const double a = 1.0000001, b = 1e-9;
-  for (int it = 0; it < iters; ++it) {
-    x0 = fma(x0, a, b); x1 = fma(x1, a, b); x2 = fma(x2, a, b); x3 = fma(x3, a, b);
-    x4 = fma(x4, a, b); x5 = fma(x5, a, b); x6 = fma(x6, a, b); x7 = fma(x7, a, b);
-  }
-  const double s = ((x0 + x1) + (x2 + x3)) + ((x4 + x5) + (x6 + x7));
-  if (s == 123.456) sink[0] = s;  // keeps the loop alive; never true in practice
-}
-
 }  // namespace
 
 int fp64_elements_per_cta(int N) {
@@ -269,12 +257,6 @@ cudaError_t launch_fp64(int N, int64_t E, const double* q, const double* params,
 #undef X
     default: return cudaErrorInvalidValue;
   }
-}
-
-cudaError_t launch_fp64_peak(double* sink, int blocks, int threads, int iters,
-                             cudaStream_t stream) {
-  fp64_peak_kernel<<<blocks, threads, 0, stream>>>(sink, iters);
-  return cudaGetLastError();
 }
 
 }  // namespace stp
