@@ -100,6 +100,43 @@ stp_status stp_predict_host(stp_handle h, int64_t elements, const double* q,
                             const double* params, double* out_avg, double* out_faces,
                             void* stream);
 
+/*
+ * Arithmetic of the derivative contractions.
+ *   STP_PRECISION_FP64    every step in FP64 (default)
+ *   STP_PRECISION_BF16X2 / _BF16X3 / _FP16X2 / _FP16X3
+ *       split precision on the tensor cores: the first CK term
+ *       r_1 = dt/2 L q is computed in FP64 (the FP64 correction pass); every
+ *       later term r_k = dt^k/(k+1)! q^(k) is scaled per quantity by a power of
+ *       two, split into 2 or 3 BF16/FP16 slices, contracted with the equally
+ *       split D on the tensor cores with FP32 accumulation, and updated
+ *       pointwise in FP32. The Taylor average (FP32 tail added to the FP64 sum
+ *       of r_0 + r_1) and the face projections are FP64.
+ * Mixed variants need 2 <= N; for N = 1 the FP64 kernel runs.
+ */
+typedef enum {
+  STP_PRECISION_FP64 = 0,
+  STP_PRECISION_BF16X2 = 1,
+  STP_PRECISION_BF16X3 = 2,
+  STP_PRECISION_FP16X2 = 3,
+  STP_PRECISION_FP16X3 = 4
+} stp_precision;
+
+/* Select the precision used by later stp_predict / stp_predict_host calls on
+ * this handle (not synchronised with launches already enqueued: set it before
+ * sharing the handle between streams). STP_ERR_INVALID_ARG for an unknown value. */
+stp_status stp_set_precision(stp_handle h, stp_precision p);
+
+/* Current precision of the handle (STP_PRECISION_FP64 for NULL). */
+stp_precision stp_get_precision(stp_handle h);
+
+/*
+ * Synchronise `stream`, then read and clear the handle's device status word.
+ * *flags receives its bits (bit 0: a tensor-core completion wait in the mixed
+ * kernel exceeded its iteration limit; the outputs of that launch are invalid).
+ * Returns STP_ERR_TIMEOUT if any bit was set, else STP_OK.
+ */
+stp_status stp_device_status(stp_handle h, void* stream, unsigned int* flags);
+
 /* Release the handle's device tables and buffers. NULL is a no-op (STP_OK). */
 stp_status stp_destroy(stp_handle h);
 

@@ -7,7 +7,8 @@ elastic problems.
 """
 from __future__ import annotations
 
-from ._binding import (STPError, stp_create, stp_destroy, stp_reference_tables,  # noqa: F401
-                       stp_last_error, stp_measure_fp64_peak, stp_nodes, stp_predict,
-                       stp_predict_host, stp_status_string)
+from ._binding import (PRECISIONS, STPError, stp_create, stp_destroy,  # noqa: F401
+                       stp_device_status, stp_get_precision, stp_last_error,
+                       stp_measure_fp64_peak, stp_nodes, stp_predict, stp_predict_host,
+                       stp_reference_tables, stp_set_precision, stp_status_string)
 from .predictor import Predictor  # noqa: F401

@@ -59,8 +59,13 @@ def load():
         lib.stp_last_error.argtypes = []
         lib.stp_last_error.restype = ctypes.c_char_p
         lib.stp_measure_fp64_peak.argtypes = [ctypes.POINTER(dbl), vp]
+        lib.stp_set_precision.argtypes = [vp, ctypes.c_int]
+        lib.stp_get_precision.argtypes = [vp]
+        lib.stp_get_precision.restype = ctypes.c_int
+        lib.stp_device_status.argtypes = [vp, vp, ctypes.POINTER(ctypes.c_uint)]
         for name in ("stp_create", "stp_predict", "stp_predict_host", "stp_destroy",
-                     "stp_reference_tables", "stp_measure_fp64_peak"):
+                     "stp_reference_tables", "stp_measure_fp64_peak", "stp_set_precision",
+                     "stp_device_status"):
             getattr(lib, name).restype = ctypes.c_int
         _lib = lib
         return lib
@@ -129,6 +134,25 @@ def stp_status_string(status: int) -> str:
 
 def stp_last_error() -> str:
     return load().stp_last_error().decode()
+
+
+PRECISIONS = {"fp64": 0, "bf16x2": 1, "bf16x3": 2, "fp16x2": 3, "fp16x3": 4}
+
+
+def stp_set_precision(h: int, precision) -> None:
+    p = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+    _check(load().stp_set_precision(h, p), "stp_set_precision")
+
+
+def stp_get_precision(h: int) -> int:
+    return int(load().stp_get_precision(h))
+
+
+def stp_device_status(h: int, stream=None) -> int:
+    """Synchronise `stream`, read and clear the device status word; raises on a timeout bit."""
+    flags = ctypes.c_uint()
+    _check(load().stp_device_status(h, _stream(stream), ctypes.byref(flags)), "stp_device_status")
+    return flags.value
 
 
 def stp_measure_fp64_peak(stream=None) -> float:

@@ -20,15 +20,13 @@
 // Taylor bookkeeping: r_k = dt^k/(k+1)! q^(k) satisfies r_0 = q,
 // r_{k+1} = dt/(k+2) * L r_k with L q = -sum_d B_d (D_d q)/dx, and the time
 // average of Eq. (exahypeTimeAverage) divided by dt is sum_{k=0..N} r_k.
+#include "ck_fp64.cuh"
 #include "stp_internal.h"
 
 namespace stp {
 namespace {
 
 constexpr int ceil_div(int a, int b) { return (a + b - 1) / b; }
-
-// Quantity slots in p[] / r[] (the state vector order).
-enum : int { V1 = 0, V2, V3, S11, S22, S33, S12, S13, S23 };
 
 template <int N, int NPT, int EPC, bool AVG_SMEM>
 struct Fp64Shape {
@@ -84,11 +82,7 @@ fp64_stp_kernel(const double* __restrict__ q, const double* __restrict__ params,
     const double* pe = params + e * (int64_t)(kParams * N3);
     for (int n = lt; n < N3; n += T) {
       const double rho = __ldg(pe + 3 * n), cp = __ldg(pe + 3 * n + 1), cs = __ldg(pe + 3 * n + 2);
-      const double mu = rho * (cs * cs);
-      sc[n] = 1.0 / rho;
-      sc[S + n] = rho * (cp * cp - 2.0 * (cs * cs));
-      sc[2 * S + n] = mu;
-      sc[3 * S + n] = mu + mu;
+      elastic_coefficients(rho, cp, cs, &sc[n], &sc[S + n], &sc[2 * S + n], &sc[3 * S + n]);
     }
   }
   __syncthreads();
@@ -101,57 +95,7 @@ fp64_stp_kernel(const double* __restrict__ q, const double* __restrict__ params,
       const int n = lt + j * T;
       if (!active || n >= N3) continue;
       const int x = n % N, y = (n / N) % N, z = n / (N * N);
-      const double* Dx = Dk + x * LDD;
-      const double* Dy = Dk + y * LDD;
-      const double* Dz = Dk + z * LDD;
-      const double* px = sp + (z * N + y) * N;  // + l
-      const double* py = sp + z * N * N + x;    // + l*N
-      const double* pz = sp + y * N + x;        // + l*N*N
-      double v1 = 0.0, v2 = 0.0, v3 = 0.0, s12 = 0.0, s13 = 0.0, s23 = 0.0;
-      double a = 0.0, b = 0.0, c = 0.0;  // dv1/dx, dv2/dy, dv3/dz
-#pragma unroll
-      for (int l = 0; l < N; ++l) {
-        const double d = Dx[l];
-        v1 = fma(d, px[S11 * S + l], v1);
-        v2 = fma(d, px[S12 * S + l], v2);
-        v3 = fma(d, px[S13 * S + l], v3);
-        a = fma(d, px[V1 * S + l], a);
-        s12 = fma(d, px[V2 * S + l], s12);
-        s13 = fma(d, px[V3 * S + l], s13);
-      }
-#pragma unroll
-      for (int l = 0; l < N; ++l) {
-        const double d = Dy[l];
-        const int o = l * N;
-        v1 = fma(d, py[S12 * S + o], v1);
-        v2 = fma(d, py[S22 * S + o], v2);
-        v3 = fma(d, py[S23 * S + o], v3);
-        s12 = fma(d, py[V1 * S + o], s12);
-        b = fma(d, py[V2 * S + o], b);
-        s23 = fma(d, py[V3 * S + o], s23);
-      }
-#pragma unroll
-      for (int l = 0; l < N; ++l) {
-        const double d = Dz[l];
-        const int o = l * N * N;
-        v1 = fma(d, pz[S13 * S + o], v1);
-        v2 = fma(d, pz[S23 * S + o], v2);
-        v3 = fma(d, pz[S33 * S + o], v3);
-        s13 = fma(d, pz[V1 * S + o], s13);
-        s23 = fma(d, pz[V2 * S + o], s23);
-        c = fma(d, pz[V3 * S + o], c);
-      }
-      const double invrho = sc[n], lam = sc[S + n], mu = sc[2 * S + n], mu2 = sc[3 * S + n];
-      const double ltr = lam * ((a + b) + c);
-      r[j][V1] = invrho * v1;
-      r[j][V2] = invrho * v2;
-      r[j][V3] = invrho * v3;
-      r[j][S11] = fma(mu2, a, ltr);
-      r[j][S22] = fma(mu2, b, ltr);
-      r[j][S33] = fma(mu2, c, ltr);
-      r[j][S12] = mu * s12;
-      r[j][S13] = mu * s13;
-      r[j][S23] = mu * s23;
+      ck_node_fp64<N, S, LDD>(sp, Dk, x, y, z, sc[n], sc[S + n], sc[2 * S + n], sc[3 * S + n], r[j]);
       if (AVG_SMEM) {
 #pragma unroll
         for (int s = 0; s < M; ++s) sa[s * S + n] += r[j][s];

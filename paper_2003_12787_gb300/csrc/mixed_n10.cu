@@ -1,0 +1,8 @@
+// Explicit instantiations of the mixed-precision STP kernel for N = 10.
+#include "mixed_kernels.cuh"
+
+namespace stp {
+template cudaError_t launch_mixed_for<10>(int, int64_t, const double*, const double*, double*,
+                                          double*, const double*, const double*, double, unsigned int*,
+                                          cudaStream_t);
+}  // namespace stp

@@ -1,0 +1,20 @@
+// Explicit instantiations of the mixed-precision STP kernel for N = 2, 3, 4, 5, 6.
+#include "mixed_kernels.cuh"
+
+namespace stp {
+template cudaError_t launch_mixed_for<2>(int, int64_t, const double*, const double*, double*,
+                                          double*, const double*, const double*, double, unsigned int*,
+                                          cudaStream_t);
+template cudaError_t launch_mixed_for<3>(int, int64_t, const double*, const double*, double*,
+                                          double*, const double*, const double*, double, unsigned int*,
+                                          cudaStream_t);
+template cudaError_t launch_mixed_for<4>(int, int64_t, const double*, const double*, double*,
+                                          double*, const double*, const double*, double, unsigned int*,
+                                          cudaStream_t);
+template cudaError_t launch_mixed_for<5>(int, int64_t, const double*, const double*, double*,
+                                          double*, const double*, const double*, double, unsigned int*,
+                                          cudaStream_t);
+template cudaError_t launch_mixed_for<6>(int, int64_t, const double*, const double*, double*,
+                                          double*, const double*, const double*, double, unsigned int*,
+                                          cudaStream_t);
+}  // namespace stp

@@ -1,0 +1,14 @@
+// Explicit instantiations of the mixed-precision STP kernel for N = 7, 8, 9.
+#include "mixed_kernels.cuh"
+
+namespace stp {
+template cudaError_t launch_mixed_for<7>(int, int64_t, const double*, const double*, double*,
+                                          double*, const double*, const double*, double, unsigned int*,
+                                          cudaStream_t);
+template cudaError_t launch_mixed_for<8>(int, int64_t, const double*, const double*, double*,
+                                          double*, const double*, const double*, double, unsigned int*,
+                                          cudaStream_t);
+template cudaError_t launch_mixed_for<9>(int, int64_t, const double*, const double*, double*,
+                                          double*, const double*, const double*, double, unsigned int*,
+                                          cudaStream_t);
+}  // namespace stp

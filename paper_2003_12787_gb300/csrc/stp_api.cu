@@ -12,7 +12,9 @@ struct stp_handle_s {
   int device = -1;
   double dx = 0.0, dt = 0.0;
   stp::HostTables host;
-  double* d_tables = nullptr;  // step matrices, phi0, phi1 (device)
+  double* d_tables = nullptr;  // step matrices, phi0, phi1, D (device)
+  unsigned int* d_status = nullptr;  // device-side status word (bounded-wait timeouts)
+  stp_precision precision = STP_PRECISION_FP64;
   // host-buffer path: chunked pipeline state, created on first use
   static constexpr int kStages = 3;
   cudaStream_t streams[kStages] = {nullptr, nullptr, nullptr};
@@ -89,6 +91,16 @@ stp_status validate_common(stp_handle h, int64_t E, const void* q, const void* p
   return STP_OK;
 }
 
+// One launch of the handle's configured kernel.
+cudaError_t launch_configured(stp_handle h, int64_t E, const double* q, const double* params,
+                              double* avg, double* faces, cudaStream_t stream) {
+  if (h->precision == STP_PRECISION_FP64 || h->N < 2)
+    return stp::launch_fp64(h->N, E, q, params, avg, faces, h->d_tables, stream);
+  return stp::launch_mixed(h->N, (int)h->precision, E, q, params, avg, faces, h->d_tables,
+                           h->d_tables + stp::table_offset_D(h->N), h->dt / h->dx, h->d_status,
+                           stream);
+}
+
 }  // namespace
 
 extern "C" {
@@ -127,14 +139,22 @@ stp_status stp_create(int order, int m, double dx, double dt, stp_handle* out) {
   cudaError_t e = cudaGetDevice(&h->device);
   if (e != cudaSuccess) { delete h; return cuda_fail(e, "cudaGetDevice"); }
   const int nt = stp::table_doubles(N);
-  double buf[stp::kMaxNodes * stp::kMaxNodes * stp::kMaxNodes + 2 * stp::kMaxNodes];
+  double buf[stp::kMaxNodes * stp::kMaxNodes * stp::kMaxNodes + 2 * stp::kMaxNodes +
+             stp::kMaxNodes * stp::kMaxNodes];
   stp::make_step_matrices(h->host, dx, dt, buf);
   std::memcpy(buf + N * N * N, h->host.phi0, sizeof(double) * N);
   std::memcpy(buf + N * N * N + N, h->host.phi1, sizeof(double) * N);
+  std::memcpy(buf + stp::table_offset_D(N), h->host.D, sizeof(double) * N * N);
   e = cudaMalloc(&h->d_tables, sizeof(double) * nt);
   if (e != cudaSuccess) { cudaGetLastError(); delete h; return fail(STP_ERR_OOM, "cudaMalloc of tables failed"); }
+  e = cudaMalloc(&h->d_status, 16);
+  if (e != cudaSuccess) {
+    cudaGetLastError(); cudaFree(h->d_tables); delete h;
+    return fail(STP_ERR_OOM, "cudaMalloc of the status word failed");
+  }
   e = cudaMemcpy(h->d_tables, buf, sizeof(double) * nt, cudaMemcpyHostToDevice);
-  if (e != cudaSuccess) { cudaFree(h->d_tables); delete h; return cuda_fail(e, "table upload"); }
+  if (e == cudaSuccess) e = cudaMemset(h->d_status, 0, 16);
+  if (e != cudaSuccess) { cudaFree(h->d_tables); cudaFree(h->d_status); delete h; return cuda_fail(e, "table upload"); }
   *out = h;
   return STP_OK;
 }
@@ -151,6 +171,7 @@ stp_status stp_destroy(stp_handle h) {
     if (h->streams[i]) cudaStreamDestroy(h->streams[i]);
   }
   if (h->d_tables) cudaFree(h->d_tables);
+  if (h->d_status) cudaFree(h->d_status);
   if (prev >= 0) cudaSetDevice(prev);
   delete h;
   return STP_OK;
@@ -178,8 +199,8 @@ stp_status stp_predict(stp_handle h, int64_t elements, const double* q, const do
   const void* ptrs[4] = {q, params, out_avg, out_faces};
   for (int i = 0; i < 4; ++i)
     if ((s = check_device_ptr(ptrs[i], h->device, names[i])) != STP_OK) return s;
-  cudaError_t e = stp::launch_fp64(h->N, elements, q, params, out_avg, out_faces, h->d_tables,
-                                   static_cast<cudaStream_t>(stream));
+  cudaError_t e = launch_configured(h, elements, q, params, out_avg, out_faces,
+                                    static_cast<cudaStream_t>(stream));
   if (e != cudaSuccess) return cuda_fail(e, "STP kernel launch");
   return STP_OK;
 }
@@ -248,7 +269,7 @@ stp_status stp_predict_host(stp_handle h, int64_t elements, const double* q, con
     if ((e = cudaMemcpyAsync(dq, hq + base * sz.q, n * sz.q, cudaMemcpyHostToDevice, st)) != cudaSuccess ||
         (e = cudaMemcpyAsync(dp, hp + base * sz.params, n * sz.params, cudaMemcpyHostToDevice, st)) != cudaSuccess)
       return cuda_fail(e, "host-to-device copy");
-    e = stp::launch_fp64(h->N, n, dq, dp, da, df, h->d_tables, st);
+    e = launch_configured(h, n, dq, dp, da, df, st);
     if (e != cudaSuccess) return cuda_fail(e, "STP kernel launch");
     if ((e = cudaMemcpyAsync(ha + base * sz.avg, da, n * sz.avg, cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
         (e = cudaMemcpyAsync(hf + base * sz.faces, df, n * sz.faces, cudaMemcpyDeviceToHost, st)) != cudaSuccess)
@@ -260,6 +281,29 @@ stp_status stp_predict_host(stp_handle h, int64_t elements, const double* q, con
   }
   if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "host-path copy");
   return STP_OK;
+}
+
+stp_status stp_set_precision(stp_handle h, stp_precision p) {
+  if (!h) return fail(STP_ERR_INVALID_ARG, "invalid handle");
+  if (p < STP_PRECISION_FP64 || p > STP_PRECISION_FP16X3)
+    return fail(STP_ERR_INVALID_ARG, "unknown precision");
+  h->precision = p;
+  return STP_OK;
+}
+
+stp_precision stp_get_precision(stp_handle h) { return h ? h->precision : STP_PRECISION_FP64; }
+
+stp_status stp_device_status(stp_handle h, void* stream, unsigned int* flags) {
+  if (!h || !flags) return fail(STP_ERR_INVALID_ARG, "invalid handle or flags pointer");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  cudaError_t e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return cuda_fail(e, "stream synchronisation");
+  unsigned int v = 0;
+  if ((e = cudaMemcpy(&v, h->d_status, sizeof(v), cudaMemcpyDeviceToHost)) != cudaSuccess)
+    return cuda_fail(e, "status read");
+  if ((e = cudaMemset(h->d_status, 0, sizeof(v))) != cudaSuccess) return cuda_fail(e, "status reset");
+  *flags = v;
+  return v ? fail(STP_ERR_TIMEOUT, "a bounded device-side wait gave up") : STP_OK;
 }
 
 stp_status stp_measure_fp64_peak(double* gflops, void* stream) {

@@ -29,8 +29,10 @@ bool make_tables(int N, HostTables* t);
 // for k = 0..N-1, rounded once from extended precision.
 void make_step_matrices(const HostTables& t, double dx, double dt, double* Dk);
 
-// Device tables: [N][N][N] step matrices, then phi0[N], then phi1[N].
-inline int table_doubles(int N) { return N * N * N + 2 * N; }
+// Device tables: [N][N][N] step matrices, then phi0[N], phi1[N], then the
+// unscaled D[N][N].
+inline int table_doubles(int N) { return N * N * N + 2 * N + N * N; }
+inline int table_offset_D(int N) { return N * N * N + 2 * N; }
 
 // Kernel launchers (fp64_kernels.cu). Return cudaSuccess or the launch error.
 cudaError_t launch_fp64(int N, int64_t E, const double* q, const double* params,
@@ -38,6 +40,13 @@ cudaError_t launch_fp64(int N, int64_t E, const double* q, const double* params,
                         cudaStream_t stream);
 // Elements per CTA the FP64 kernel uses for N nodes (chunk sizes are multiples).
 int fp64_elements_per_cta(int N);
+
+// Mixed-precision kernel (mixed_kernels.cu); variant 1..4 = BF16x2, BF16x3,
+// FP16x2, FP16x3; 2 <= N <= 12. status receives bit 0 on a bounded-wait timeout.
+cudaError_t launch_mixed(int N, int variant, int64_t E, const double* q, const double* params,
+                         double* out_avg, double* out_faces, const double* tables,
+                         const double* Dref, double dt_over_dx, unsigned int* status,
+                         cudaStream_t stream);
 
 cudaError_t launch_fp64_peak(double* sink, int blocks, int threads, int iters,
                              cudaStream_t stream);

@@ -9,12 +9,19 @@ from . import _binding as B
 class Predictor:
     """Owns one stp_handle for (order, dx, dt) on the current CUDA device."""
 
-    def __init__(self, order: int, dx: float, dt: float, m: int = 9):
+    def __init__(self, order: int, dx: float, dt: float, m: int = 9, precision="fp64"):
         self.order = order
         self.N = order + 1
         self.dx = dx
         self.dt = dt
         self.handle = B.stp_create(order, m, dx, dt)
+        self.precision = precision
+        if precision != "fp64":
+            B.stp_set_precision(self.handle, precision)
+
+    def status(self, stream=None) -> int:
+        """Synchronise and read the device status word (raises STPError on a timeout)."""
+        return B.stp_device_status(self.handle, stream)
 
     def close(self):
         if self.handle is not None:
