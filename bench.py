@@ -188,6 +188,53 @@ def oracle_baseline(prob_q, prob_params, h, dt, budget_s: float, max_elems: int)
     return done, spent, oracle.num_threads()
 
 
+def mixed_comparison(stp, torch, args):
+    """Mixed vs FP64 at fixed error on the order-9 workload (N=10, 16384
+    elements): per precision, the CUDA-event time of one launch (mean of
+    args.mixed_steps after 3 warm-ups) and the max normwise error of avg and
+    the six face arrays against the oracle on a sample of elements."""
+    import oracle
+    from paper_2003_12787_gb300.inputs import elastic_problem
+    N, grid, h, desc = WORKLOADS["order9"]
+    prob = elastic_problem(N, grid=grid, h=h, device="cuda")
+    E = prob.E
+    rng = np.random.default_rng(4)
+    idx = np.unique(np.concatenate([[0, E - 1], rng.choice(E, 14, replace=False)]))
+    it = torch.as_tensor(idx, device="cuda")
+    a_ref, f_ref = oracle.stp(prob.q[it].cpu().numpy(), prob.params[it].cpu().numpy(),
+                              prob.h, prob.dt)
+    out = {"workload": desc, "elements": E, "N": N,
+           "error": "max over avg and 6 face arrays of max|gpu-oracle|/max|oracle|, "
+                    f"{len(idx)} sampled elements", "variants": {}}
+    stream = torch.cuda.current_stream()
+    for prec in ("fp64", "bf16x2", "bf16x3", "fp16x2", "fp16x3"):
+        P = stp.Predictor(N - 1, prob.h, prob.dt, precision=prec)
+        avg, faces = P.empty_outputs(E)
+        for _ in range(3):
+            P.predict(prob.q, prob.params, out=(avg, faces), stream=stream)
+        s0 = torch.cuda.Event(enable_timing=True)
+        s1 = torch.cuda.Event(enable_timing=True)
+        s0.record(stream)
+        for _ in range(args.mixed_steps):
+            P.predict(prob.q, prob.params, out=(avg, faces), stream=stream)
+        s1.record(stream)
+        torch.cuda.synchronize()
+        P.status(stream)
+        ms = s0.elapsed_time(s1) / args.mixed_steps
+        a = avg[it].cpu().numpy()
+        f = faces[it].cpu().numpy()
+        err = max([float(np.abs(a - a_ref).max() / np.abs(a_ref).max())] +
+                  [float(np.abs(f[:, i] - f_ref[:, i]).max() / np.abs(f_ref[:, i]).max())
+                   for i in range(6)])
+        out["variants"][prec] = {"ms_per_launch": ms, "elements_per_s": E / (ms / 1e3),
+                                 "max_rel_err": err}
+        P.close()
+    base = out["variants"]["fp64"]["ms_per_launch"]
+    for v in out["variants"].values():
+        v["speedup_vs_fp64"] = base / v["ms_per_launch"]
+    return out
+
+
 def run_gpu(args):
     import torch
     world, rank, local = dist_env()
@@ -271,6 +318,10 @@ def run_gpu(args):
         if not np.array_equal(ah[:4].numpy(), avg[:4].cpu().numpy()):
             e2e["mismatch_vs_device_path"] = True
 
+    mixed = None
+    if rank == 0 and world == 1 and not args.no_mixed:
+        mixed = mixed_comparison(stp, torch, args)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         qn = prob.q.cpu().numpy()
@@ -306,7 +357,7 @@ def run_gpu(args):
                          "hbm_gbs": E * bytes_per_element(N) / mean_step_s / 1e9},
             "latency_ms": {"p50": statistics.median(step_ms), "p99": p99,
                            "min": min(step_ms), "max": max(step_ms)},
-            "e2e": e2e, "cpu_baseline": cpu, "clocks": clocks,
+            "e2e": e2e, "cpu_baseline": cpu, "clocks": clocks, "mixed": mixed,
             "gpu_launches": args.steps, "parity_max_rel_sampled": parity,
         }
         print(json.dumps(line), flush=True)
@@ -363,6 +414,9 @@ def main():
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="order7")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-mixed", action="store_true",
+                    help="skip the mixed-vs-FP64 comparison on the order-9 workload")
+    ap.add_argument("--mixed-steps", type=int, default=5)
     ap.add_argument("--cpu-budget", type=float, default=10.0,
                     help="seconds of oracle time for cpu_baseline")
     ap.add_argument("--reference-sample", type=int, default=1024,

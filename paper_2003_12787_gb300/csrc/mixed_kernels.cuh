@@ -160,10 +160,31 @@ __device__ __forceinline__ uint16_t to_bits(float v, float* back) {
 
 // Quantities each pass differentiates and the accumulator each result feeds:
 // accumulators 0..2 velocities, 3 s12, 4 s13, 5 s23, 6 dv1/dx, 7 dv2/dy, 8 dv3/dz.
-static __constant__ int kPassQty[3][6] = {{kS11, kS12, kS13, kV1, kV2, kV3},
-                                   {kS12, kS22, kS23, kV1, kV2, kV3},
-                                   {kS13, kS23, kS33, kV1, kV2, kV3}};
-static __constant__ int kPassAcc[3][6] = {{0, 1, 2, 6, 3, 4}, {0, 1, 2, 3, 7, 5}, {0, 1, 2, 4, 5, 8}};
+// (functions, so that unrolled loops fold them to constants)
+__host__ __device__ constexpr int pass_qty(int pass, int q6) {
+  // q6 0..2: the stress components sigma_{d,j} (j = x, y, z); 3..5: v1, v2, v3
+  return q6 >= 3 ? (q6 - 3)
+       : pass == 0 ? (q6 == 0 ? kS11 : q6 == 1 ? kS12 : kS13)
+       : pass == 1 ? (q6 == 0 ? kS12 : q6 == 1 ? kS22 : kS23)
+                   : (q6 == 0 ? kS13 : q6 == 1 ? kS23 : kS33);
+}
+// value of quantity pass_qty(pass, q6) from a 9-vector, by selects only
+__device__ __forceinline__ float pick_pass(const float* v, int pass, int q6) {
+  if (q6 >= 3) return v[q6 - 3];
+  const float x = v[q6 == 0 ? kS11 : q6 == 1 ? kS12 : kS13];
+  const float y = v[q6 == 0 ? kS12 : q6 == 1 ? kS22 : kS23];
+  const float z = v[q6 == 0 ? kS13 : q6 == 1 ? kS23 : kS33];
+  return pass == 0 ? x : (pass == 1 ? y : z);
+}
+
+__host__ __device__ constexpr int pass_acc(int pass, int q6) {
+  // stresses feed the velocity accumulators 0..2; d v_i / d x_pass feeds
+  // dv1/dx (6), dv2/dy (7), dv3/dz (8) or the shear sums s12 (3), s13 (4), s23 (5)
+  return q6 < 3 ? q6
+       : pass == 0 ? (q6 == 3 ? 6 : q6 == 4 ? 3 : 4)
+       : pass == 1 ? (q6 == 3 ? 3 : q6 == 4 ? 7 : 5)
+                   : (q6 == 3 ? 4 : q6 == 4 ? 5 : 8);
+}
 
 constexpr int kScaleExp = 14;  // largest scaled magnitude just below 2^14
 
@@ -189,7 +210,8 @@ struct MixedShape {
   static constexpr size_t D0_OFF = B_OFF + (size_t)T * 512;
   static constexpr size_t PHI_OFF = D0_OFF + sizeof(double) * N * LDD;
   static constexpr size_t MAX_OFF = PHI_OFF + sizeof(double) * 2 * N;
-  static constexpr size_t BAR_OFF = (MAX_OFF + 2 * 9 * 4 + 15) & ~(size_t)15;
+  static constexpr size_t FAC_OFF = MAX_OFF + 2 * 9 * 4;  // float [3][6]
+  static constexpr size_t BAR_OFF = (FAC_OFF + 18 * 4 + 15) & ~(size_t)15;
   static constexpr size_t TADDR_OFF = BAR_OFF + 8;
   static constexpr size_t SMEM = TADDR_OFF + 16 + 1024;  // + slack to align the base to 1 KB
   static constexpr int MINB = (2 * (SMEM + 1024) <= 233472 && THREADS <= 512) ? 2 : 1;
@@ -215,6 +237,7 @@ mixed_stp_kernel(const double* __restrict__ q, const double* __restrict__ params
   double* D0 = reinterpret_cast<double*>(smem + Sh::D0_OFF);
   double* phi = reinterpret_cast<double*>(smem + Sh::PHI_OFF);
   unsigned int* smax = reinterpret_cast<unsigned int*>(smem + Sh::MAX_OFF);
+  float* sfac = reinterpret_cast<float*>(smem + Sh::FAC_OFF);
   uint64_t* bar = reinterpret_cast<uint64_t*>(smem + Sh::BAR_OFF);
   uint32_t* taddr_s = reinterpret_cast<uint32_t*>(smem + Sh::TADDR_OFF);
 
@@ -271,10 +294,14 @@ mixed_stp_kernel(const double* __restrict__ q, const double* __restrict__ params
   const uint32_t tmem = *taddr_s;
 
   // ---- FP64 first term r_1 (the correction pass) ----
-  float r[NPT][9];
+  float r[NPT][9];   // current term r_k of the owned nodes (0 for slots without a node)
   float cf[NPT][4];
 #pragma unroll
   for (int j = 0; j < NPT; ++j) {
+#pragma unroll
+    for (int s = 0; s < 9; ++s) r[j][s] = 0.f;
+#pragma unroll
+    for (int c = 0; c < 4; ++c) cf[j][c] = 0.f;
     const int n = tid + j * THREADS;
     if (n >= N3) continue;
     const int x = n % N, y = (n / N) % N, z = n / (N * N);
@@ -326,18 +353,29 @@ mixed_stp_kernel(const double* __restrict__ q, const double* __restrict__ params
     __syncthreads();
     if (tid < 9) smax[9 * ((k + 1) & 1) + tid] = 0u;  // buffer of step k+1 (last read in step k-1)
     float sc[9];  // 2^(14 - e_s): scale of quantity s
-    int ex[9];    // e_s, clamped so that 2^(14 - e_s) stays finite in FP32
+    const float step = (float)(h_inv_dt / (double)(k + 2));  // dt / ((k+2) dx)
 #pragma unroll
     for (int s = 0; s < 9; ++s) {
       int es;
       frexpf(__uint_as_float(mx[s]), &es);
-      ex[s] = es < -100 ? -100 : es;
-      sc[s] = ldexpf(1.f, kScaleExp - ex[s]);
+      es = es < -100 ? -100 : es;  // keeps 2^(14 - e_s) finite in FP32
+      sc[s] = ldexpf(1.f, kScaleExp - es);
+      // factor turning a tensor-core result of quantity s back into the step's
+      // scaled derivative (read by the TMEM readers after the pass barrier)
+      if (tid == 0) {
+#pragma unroll
+        for (int ps = 0; ps < 3; ++ps)
+#pragma unroll
+          for (int q6 = 0; q6 < 6; ++q6)
+            if (pass_qty(ps, q6) == s) sfac[ps * 6 + q6] = ldexpf(step, es + eD - 2 * kScaleExp);
+      }
     }
-    // factor turning a tensor-core result back into the step's scaled derivative
-    const float step = (float)(h_inv_dt / (double)(k + 2));  // dt / ((k+2) dx)
 
+#pragma unroll 1
     for (int pass = 0; pass < 3; ++pass) {
+      float scp[6];  // scales of the pass's six quantities (selects, no indexed arrays)
+#pragma unroll
+      for (int q6 = 0; q6 < 6; ++q6) scp[q6] = pick_pass(sc, pass, q6);
       // 1. slices of this pass's six quantities into the operand tiles
 #pragma unroll
       for (int j = 0; j < NPT; ++j) {
@@ -350,10 +388,9 @@ mixed_stp_kernel(const double* __restrict__ q, const double* __restrict__ params
         else { a = y; b = x; kk = z; }
 #pragma unroll
         for (int q6 = 0; q6 < 6; ++q6) {
-          const int s = kPassQty[pass][q6];
           const int row = (q6 * N + a) * N + b;
           const int off = (row >> 7) * 4096 + tile_offset(row & 127, kk);
-          float rem = r[j][s] * sc[s];
+          float rem = pick_pass(r[j], pass, q6) * scp[q6];
 #pragma unroll
           for (int t = 0; t < T; ++t) {
             float back;
@@ -398,9 +435,8 @@ mixed_stp_kernel(const double* __restrict__ q, const double* __restrict__ params
           if (row < ROWS) {
             const int q6 = row / (N * N);
             const int a = (row / N) % N, b = row % N;
-            const int s = kPassQty[pass][q6];
-            const int acc = kPassAcc[pass][q6];
-            const float f = ldexpf(step, ex[s] + eD - 2 * kScaleExp);
+            const int acc = pass_acc(pass, q6);
+            const float f = sfac[pass * 6 + q6];
 #pragma unroll
             for (int c = 0; c < N; ++c) {
               int node;
