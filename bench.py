@@ -42,6 +42,8 @@ WORKLOADS = {
                "order-3 (N=4) elastic STP, 8^3=512 elements of side 1/8, one launch"),
     "order7_small": (8, (16, 16, 16), 1.0 / 32,
                      "order-7 (N=8) elastic STP, 16^3=4096 elements of side 1/32, one launch"),
+    "order9_small": (10, (16, 16, 8), 1.0 / 32,
+                     "order-9 (N=10) elastic STP, 16x16x8=2048 elements of side 1/32, one launch"),
     "order9": (10, (32, 32, 16), 1.0 / 32,
                "order-9 (N=10) elastic STP, 32x32x16=16384 elements of side 1/32, one launch"),
 }
@@ -235,6 +237,53 @@ def mixed_comparison(stp, torch, args):
     return out
 
 
+def batched_measurement(stp, torch, args):
+    """The batched workload (64 sets, orders 3-11, 64-16384 elements each,
+    seed 1003) as one persistent launch replayed from a CUDA graph: time per
+    replay (CUDA events, mean of args.batch_steps after one warm-up), element
+    throughput, algorithmic FP64 rate, and the autotuner's choice per order."""
+    from paper_2003_12787_gb300.inputs import batched_sets_recipe, elastic_problem
+    recipe = batched_sets_recipe()
+    items, flops, elems = [], 0, 0
+    for r in recipe:
+        prob = elastic_problem(r["N"], grid=r["grid"], E=r["E"], h=r["h"],
+                               seed_material=r["seed_material"], seed_waves=r["seed_waves"],
+                               device="cuda")
+        items.append((stp.Predictor(r["N"] - 1, prob.h, prob.dt), prob.q, prob.params))
+        flops += r["E"] * flops_per_element(r["N"])
+        elems += r["E"]
+    t0 = time.perf_counter()
+    b = stp.Batch(items)
+    plan_s = time.perf_counter() - t0
+    stream = torch.cuda.current_stream()
+    b.launch(stream)
+    s0 = torch.cuda.Event(enable_timing=True)
+    s1 = torch.cuda.Event(enable_timing=True)
+    s0.record(stream)
+    for _ in range(args.batch_steps):
+        b.launch(stream)
+    s1.record(stream)
+    torch.cuda.synchronize()
+    ms = s0.elapsed_time(s1) / args.batch_steps
+    tuned = {}
+    for P, _, _ in items:
+        if P.N not in tuned:
+            tuned[P.N] = stp.stp_autotune(P.handle)
+    out = {"workload": "64 element sets, orders 3-11 (N=4..12), 64-16384 elements each "
+                       "(log-uniform, seed 1003), one persistent launch from a CUDA graph",
+           "sets": len(recipe), "elements": elems, "ms_per_launch": ms,
+           "elements_per_s": elems / (ms / 1e3), "tflops_algorithmic": flops / (ms / 1e3) / 1e12,
+           "frac_fp64_peak": flops / (ms / 1e3) / 1e12 / FP64_PEAK_TFLOPS,
+           "plan_seconds_incl_autotune": plan_s, **b.info(),
+           "autotune": {str(n): {"variant": t["variant"],
+                                 "us_per_element": [round(u, 4) for u in t["us_variants"]]}
+                        for n, t in sorted(tuned.items())}}
+    b.close()
+    for P, _, _ in items:
+        P.close()
+    return out
+
+
 def run_gpu(args):
     import torch
     world, rank, local = dist_env()
@@ -253,7 +302,7 @@ def run_gpu(args):
     E = prob.E
     dev = torch.device("cuda", torch.cuda.current_device())
     stream = torch.cuda.current_stream(dev)
-    P = stp.Predictor(N - 1, prob.h, prob.dt)
+    P = stp.Predictor(N - 1, prob.h, prob.dt, precision=args.precision)
     avg, faces = P.empty_outputs(E, device=dev)
 
     fp64_probe = stp.stp_measure_fp64_peak(stream)
@@ -321,6 +370,9 @@ def run_gpu(args):
     mixed = None
     if rank == 0 and world == 1 and not args.no_mixed:
         mixed = mixed_comparison(stp, torch, args)
+    batched = None
+    if rank == 0 and world == 1 and not args.no_batched:
+        batched = batched_measurement(stp, torch, args)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -341,7 +393,8 @@ def run_gpu(args):
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms_max / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f64", "data": "synthetic",
+            "dtype": "f64" if args.precision == "fp64" else f"{args.precision}+f32+f64",
+            "data": "synthetic",
             "config": {"workload": desc, "N": N, "order": N - 1, "elements": E,
                        "elements_per_gpu": E, "dt": prob.dt, "dx": prob.h,
                        "l2": "inputs larger than L2: %.2f GB read + %.2f GB written per step"
@@ -358,6 +411,7 @@ def run_gpu(args):
             "latency_ms": {"p50": statistics.median(step_ms), "p99": p99,
                            "min": min(step_ms), "max": max(step_ms)},
             "e2e": e2e, "cpu_baseline": cpu, "clocks": clocks, "mixed": mixed,
+            "batched": batched,
             "gpu_launches": args.steps, "parity_max_rel_sampled": parity,
         }
         print(json.dumps(line), flush=True)
@@ -417,6 +471,12 @@ def main():
     ap.add_argument("--no-mixed", action="store_true",
                     help="skip the mixed-vs-FP64 comparison on the order-9 workload")
     ap.add_argument("--mixed-steps", type=int, default=5)
+    ap.add_argument("--no-batched", action="store_true",
+                    help="skip the batched 64-set workload")
+    ap.add_argument("--batch-steps", type=int, default=3)
+    ap.add_argument("--precision", default="fp64",
+                    choices=["fp64", "bf16x2", "bf16x3", "fp16x2", "fp16x3"],
+                    help="arithmetic of the timed workload (default fp64)")
     ap.add_argument("--cpu-budget", type=float, default=10.0,
                     help="seconds of oracle time for cpu_baseline")
     ap.add_argument("--reference-sample", type=int, default=1024,

@@ -137,6 +137,57 @@ stp_precision stp_get_precision(stp_handle h);
  */
 stp_status stp_device_status(stp_handle h, void* stream, unsigned int* flags);
 
+/*
+ * Batched persistent launch: the STPs of several element sets, of different
+ * orders and sizes, in ONE persistent kernel launch replayed from a CUDA
+ * graph. Each set is described by an FP64 handle (order, dx, dt) and its own
+ * device buffers in the layouts above. The paper generates one kernel per
+ * order (Sec. II-C, Sec. III); here every order's element-group body lives in
+ * one kernel and a cost-sorted work list of (set, element range) units is
+ * consumed by one CTA per SM.
+ */
+typedef struct {
+  stp_handle handle;   /* FP64 predictor of this set (its precision must be FP64) */
+  int64_t elements;    /* E >= 0 */
+  const double* q;     /* device [E][N][N][N][9] */
+  const double* params;/* device [E][N][N][N][3] */
+  double* out_avg;     /* device [E][N][N][N][9] */
+  double* out_faces;   /* device [E][6][N][N][9] */
+} stp_batch_set;
+
+typedef struct stp_batch_s* stp_batch; /* opaque plan, owned by the library */
+
+/*
+ * Plan a batch: autotunes (on first use of each order on the device, then
+ * cached) the per-order shape of the persistent kernel, builds and uploads
+ * the work list, and captures counter reset + kernel into a CUDA graph. The
+ * buffers are baked into the plan: they must stay valid, unmoved, until
+ * stp_batch_destroy. Outputs must not overlap any input or any other output.
+ * Synchronous (allocates, copies, times). Errors: STP_ERR_INVALID_ARG for bad
+ * pointers or sizes, STP_ERR_UNSUPPORTED for a handle that is not FP64 or
+ * sets on different devices, STP_ERR_CUDA / STP_ERR_OOM from CUDA.
+ */
+stp_status stp_batch_create(int nsets, const stp_batch_set* sets, stp_batch* out);
+
+/* Enqueue one replay of the plan's graph on `stream` (async). */
+stp_status stp_batch_launch(stp_batch b, void* stream);
+
+/* Work units, CTAs of the persistent grid and dynamic shared memory per CTA. */
+stp_status stp_batch_info(stp_batch b, int* units, int* ctas, int64_t* smem_bytes);
+
+/* Free the plan (after the work it enqueued has finished). NULL is a no-op. */
+stp_status stp_batch_destroy(stp_batch b);
+
+/*
+ * The autotuner's choice for the handle's order on the current device:
+ * *variant = index of the fastest candidate shape (nodes per thread, elements
+ * per CTA), *us_per_element its measured time per element, us_variants[0..1]
+ * the time of every candidate (0 where a candidate does not exist). Any
+ * output may be NULL. The first call per (device, order) measures.
+ */
+stp_status stp_autotune(stp_handle h, int* variant, double* us_per_element,
+                        double* us_variants);
+
 /* Release the handle's device tables and buffers. NULL is a no-op (STP_OK). */
 stp_status stp_destroy(stp_handle h);
 

@@ -63,9 +63,17 @@ def load():
         lib.stp_get_precision.argtypes = [vp]
         lib.stp_get_precision.restype = ctypes.c_int
         lib.stp_device_status.argtypes = [vp, vp, ctypes.POINTER(ctypes.c_uint)]
+        lib.stp_batch_create.argtypes = [ctypes.c_int, vp, ctypes.POINTER(vp)]
+        lib.stp_batch_launch.argtypes = [vp, vp]
+        lib.stp_batch_info.argtypes = [vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
+                                       ctypes.POINTER(i64)]
+        lib.stp_batch_destroy.argtypes = [vp]
+        lib.stp_autotune.argtypes = [vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(dbl),
+                                     ctypes.POINTER(dbl)]
         for name in ("stp_create", "stp_predict", "stp_predict_host", "stp_destroy",
                      "stp_reference_tables", "stp_measure_fp64_peak", "stp_set_precision",
-                     "stp_device_status"):
+                     "stp_device_status", "stp_batch_create", "stp_batch_launch",
+                     "stp_batch_info", "stp_batch_destroy", "stp_autotune"):
             getattr(lib, name).restype = ctypes.c_int
         _lib = lib
         return lib
@@ -159,3 +167,43 @@ def stp_measure_fp64_peak(stream=None) -> float:
     g = ctypes.c_double()
     _check(load().stp_measure_fp64_peak(ctypes.byref(g), _stream(stream)), "stp_measure_fp64_peak")
     return g.value
+
+
+class BatchSet(ctypes.Structure):
+    """Mirror of stp_batch_set."""
+    _fields_ = [("handle", ctypes.c_void_p), ("elements", ctypes.c_int64),
+                ("q", ctypes.c_void_p), ("params", ctypes.c_void_p),
+                ("out_avg", ctypes.c_void_p), ("out_faces", ctypes.c_void_p)]
+
+
+def stp_batch_create(sets) -> int:
+    """sets: sequence of (handle, elements, q, params, out_avg, out_faces)."""
+    arr = (BatchSet * max(1, len(sets)))()
+    for i, (h, E, q, p, a, f) in enumerate(sets):
+        arr[i] = BatchSet(h, E, _ptr(q), _ptr(p), _ptr(a), _ptr(f))
+    b = ctypes.c_void_p()
+    _check(load().stp_batch_create(len(sets), ctypes.cast(arr, ctypes.c_void_p), ctypes.byref(b)),
+           "stp_batch_create")
+    return b.value
+
+
+def stp_batch_launch(b: int, stream=None) -> None:
+    _check(load().stp_batch_launch(b, _stream(stream)), "stp_batch_launch")
+
+
+def stp_batch_info(b: int):
+    u, c, sm = ctypes.c_int(), ctypes.c_int(), ctypes.c_int64()
+    _check(load().stp_batch_info(b, ctypes.byref(u), ctypes.byref(c), ctypes.byref(sm)),
+           "stp_batch_info")
+    return {"units": u.value, "ctas": c.value, "smem_bytes": sm.value}
+
+
+def stp_batch_destroy(b: int | None) -> None:
+    _check(load().stp_batch_destroy(b), "stp_batch_destroy")
+
+
+def stp_autotune(h: int):
+    v, us = ctypes.c_int(), ctypes.c_double()
+    allv = (ctypes.c_double * 2)()
+    _check(load().stp_autotune(h, ctypes.byref(v), ctypes.byref(us), allv), "stp_autotune")
+    return {"variant": v.value, "us_per_element": us.value, "us_variants": [allv[0], allv[1]]}

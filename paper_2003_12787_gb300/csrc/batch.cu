@@ -1,0 +1,377 @@
+// Batched persistent FP64 STP: element sets of different orders and sizes in
+// one launch, replayed from a captured CUDA graph, with shapes picked by an
+// on-device autotuner.
+//
+// The paper's Kernel Generator tailors each kernel to its order at build time
+// (Sec. II-C: generated, order-specific kernels; Sec. III: padding and
+// alignment chosen per order). Here every order's kernel body is compiled
+// into one persistent kernel; a work list of (set, element range) units,
+// sorted by estimated cost (longest first), is consumed by one CTA per SM
+// through an atomic counter, and each unit runs the FP64 element-group body of
+// its order with the (nodes per thread, elements per CTA) shape that the
+// autotuner measured fastest for that order on this device.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <mutex>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "fp64_group.cuh"
+
+namespace stp {
+namespace {
+
+constexpr int kBatchThreads = 512;
+
+// Candidate shapes per N: (N, index, nodes per thread, elements per CTA,
+// average in smem, new term parked in global scratch instead of registers).
+#define STP_BATCH_SHAPES(X)                                                                        \
+  X(1, 0, 1, 256, true, false) X(2, 0, 1, 64, true, false) X(2, 1, 2, 128, true, false)           \
+  X(3, 0, 1, 18, true, false) X(3, 1, 2, 36, true, false) X(4, 0, 1, 8, true, false)              \
+  X(4, 1, 2, 16, true, false) X(5, 0, 1, 4, true, false) X(5, 1, 2, 8, true, false)               \
+  X(6, 0, 1, 2, true, false) X(6, 1, 2, 4, true, false) X(7, 0, 1, 1, true, false)                \
+  X(7, 1, 2, 2, true, false) X(8, 0, 1, 1, true, false) X(8, 1, 2, 2, true, false)                \
+  X(9, 0, 2, 1, true, false) X(9, 1, 4, 1, true, true) X(10, 0, 2, 1, true, false)                \
+  X(10, 1, 4, 1, true, true) X(11, 0, 3, 1, false, true) X(11, 1, 4, 1, false, true)              \
+  X(12, 0, 4, 1, false, true) X(12, 1, 6, 1, false, true)
+
+constexpr int kMaxVariants = 2;
+
+struct ShapeInfo {
+  int valid = 0, epc = 1;
+  size_t smem = 0;
+  size_t scratch = 0;  // bytes of global scratch per CTA (parked new terms)
+};
+
+// host-side table of the candidate shapes
+struct ShapeTable {
+  ShapeInfo s[kMaxNodes + 1][kMaxVariants];
+  ShapeTable() {
+#define X(n, v, npt, epc, avg, rg)                                                   \
+  s[n][v] = ShapeInfo{1, epc, Fp64Shape<n, npt, epc, avg>::SMEM,                     \
+                      rg ? sizeof(double) * 9 * (size_t)Fp64Shape<n, npt, epc, avg>::S * epc : 0};
+    STP_BATCH_SHAPES(X)
+#undef X
+  }
+};
+const ShapeTable& shapes() {
+  static ShapeTable t;
+  return t;
+}
+
+struct SetDev {
+  const double* q;
+  const double* params;
+  double* avg;
+  double* faces;
+  const double* tables;
+  int64_t E;
+  int N;
+  int variant;
+};
+
+struct UnitDev {
+  int64_t e0;
+  int set;
+  int pad;
+};
+
+// One shape of one order over one work unit, as its own (non-inlined) device
+// function, so that every shape gets its own register allocation inside the
+// single persistent kernel.
+template <int N, int V, int NPT, int EPC, bool AVG, bool RG>
+__device__ __noinline__ void run_unit(double* smem, const SetDev& sd, int64_t e0, double* rbuf) {
+  fp64_group<N, NPT, EPC, AVG, kBatchThreads, RG>(smem, sd.q, sd.params, sd.avg, sd.faces,
+                                                  sd.tables, e0, sd.E, rbuf);
+}
+
+__global__ void __launch_bounds__(kBatchThreads, 1)
+batch_kernel(const SetDev* __restrict__ sets, const UnitDev* __restrict__ units, int nunits,
+             unsigned int* __restrict__ counter, double* __restrict__ scratch,
+             int64_t scratch_doubles_per_cta) {
+  double* rbuf = scratch ? scratch + blockIdx.x * scratch_doubles_per_cta : nullptr;
+  extern __shared__ double smem[];
+  __shared__ int cur;
+  for (;;) {
+    if (threadIdx.x == 0) cur = (int)atomicAdd(counter, 1u);
+    __syncthreads();
+    const int u = cur;
+    __syncthreads();  // everyone has read cur before thread 0 may overwrite it
+    if (u >= nunits) break;
+    const UnitDev wu = units[u];
+    const SetDev sd = sets[wu.set];
+    switch (sd.N * kMaxVariants + sd.variant) {
+#define X(n_, v_, npt_, epc_, avgsm_, rg_) \
+  case n_ * kMaxVariants + v_:              \
+    run_unit<n_, v_, npt_, epc_, avgsm_, rg_>(smem, sd, wu.e0, rbuf); \
+    break;
+      STP_BATCH_SHAPES(X)
+#undef X
+      default: break;
+    }
+  }
+}
+
+__global__ void fill_kernel(double* p, int64_t n, double v) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    p[i] = v;
+}
+
+// ---- autotuner ----------------------------------------------------------------
+
+struct Tuned {
+  int variant = -1;
+  double us_per_element = 0.0;
+  double us[kMaxVariants] = {0.0, 0.0};
+};
+std::mutex g_tune_mutex;
+Tuned g_tuned[8][kMaxNodes + 1];  // [device][N]
+
+int sm_count() {
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  return sms;
+}
+
+// Counter reset + one launch of the batch kernel over prepared device arrays
+// (stream operations only, so it can be captured into a graph). The caller
+// has raised the kernel's dynamic shared-memory limit to at least smem.
+cudaError_t launch_batch(const SetDev* d_sets, const UnitDev* d_units, int nunits,
+                         unsigned int* d_counter, double* scratch, size_t scratch_per_cta,
+                         size_t smem, int ctas, cudaStream_t st) {
+  cudaError_t e = cudaMemsetAsync(d_counter, 0, sizeof(unsigned int), st);
+  if (e != cudaSuccess) return e;
+  batch_kernel<<<ctas, kBatchThreads, smem, st>>>(d_sets, d_units, nunits, d_counter, scratch,
+                                                  (int64_t)(scratch_per_cta / sizeof(double)));
+  return cudaGetLastError();
+}
+
+cudaError_t raise_smem_limit(size_t smem) {
+  return cudaFuncSetAttribute(batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)std::max<size_t>(smem, 1));
+}
+
+}  // namespace
+
+int batch_variants(int N, int* epc_out) {
+  int n = 0;
+  for (int v = 0; v < kMaxVariants; ++v)
+    if (N >= 1 && N <= kMaxNodes && shapes().s[N][v].valid) {
+      if (epc_out) epc_out[n] = shapes().s[N][v].epc;
+      ++n;
+    }
+  return n;
+}
+
+// Time every candidate shape of order N on a synthetic set (zero state,
+// unit material) with the persistent kernel; keep the fastest per device.
+cudaError_t autotune(int N, const double* tables, int* variant, double* us_per_element,
+                     double* us_all) {
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev < 0 || dev >= 8 || N < 1 || N > kMaxNodes) return cudaErrorInvalidValue;
+  std::lock_guard<std::mutex> lock(g_tune_mutex);
+  Tuned& t = g_tuned[dev][N];
+  if (t.variant < 0) {
+    const int sms = sm_count();
+    // about 1.5e10 algorithmic flops (~12 ms) per timed launch, at least 4 units per SM
+    const double F = 36.0 * std::pow(N, 5) + 66.0 * std::pow(N, 4) + 108.0 * std::pow(N, 3);
+    int64_t E = (int64_t)std::max(1.5e10 / F, 0.0);
+    int maxepc = 1;
+    for (int v = 0; v < kMaxVariants; ++v)
+      if (shapes().s[N][v].valid) maxepc = std::max(maxepc, shapes().s[N][v].epc);
+    E = std::max<int64_t>(E, (int64_t)4 * sms * maxepc);
+    E = std::min<int64_t>(E, 100000);
+    const size_t n3 = (size_t)N * N * N;
+    double *q = nullptr, *p = nullptr, *a = nullptr, *f = nullptr;
+    SetDev* d_set = nullptr;
+    UnitDev* d_units = nullptr;
+    unsigned int* d_counter = nullptr;
+    cudaStream_t st = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaError_t err = cudaSuccess;
+    auto chk = [&](cudaError_t e) { if (err == cudaSuccess && e != cudaSuccess) err = e; return err == cudaSuccess; };
+    chk(cudaMalloc(&q, E * n3 * 9 * 8));
+    chk(cudaMalloc(&p, E * n3 * 3 * 8));
+    chk(cudaMalloc(&a, E * n3 * 9 * 8));
+    chk(cudaMalloc(&f, E * (size_t)N * N * 54 * 8));
+    chk(cudaMalloc(&d_set, sizeof(SetDev)));
+    chk(cudaMalloc(&d_counter, sizeof(unsigned int)));
+    chk(cudaMalloc(&d_units, sizeof(UnitDev) * (size_t)E));
+    size_t scr = 0;
+    for (int v = 0; v < kMaxVariants; ++v)
+      if (shapes().s[N][v].valid) scr = std::max(scr, shapes().s[N][v].scratch);
+    double* scratch = nullptr;
+    if (scr) chk(cudaMalloc(&scratch, scr * (size_t)sms));
+    chk(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+    chk(cudaEventCreate(&e0));
+    chk(cudaEventCreate(&e1));
+    if (err == cudaSuccess) {
+      chk(cudaMemsetAsync(q, 0, E * n3 * 9 * 8, st));
+      fill_kernel<<<1024, 256, 0, st>>>(p, (int64_t)(E * n3 * 3), 1.0);
+      chk(cudaGetLastError());
+    }
+    double best = 1e300;
+    for (int v = 0; v < kMaxVariants && err == cudaSuccess; ++v) {
+      const ShapeInfo& si = shapes().s[N][v];
+      if (!si.valid) continue;
+      SetDev sd{q, p, a, f, tables, E, N, v};
+      std::vector<UnitDev> units;
+      for (int64_t e = 0; e < E; e += si.epc) units.push_back(UnitDev{e, 0, 0});
+      chk(cudaMemcpyAsync(d_set, &sd, sizeof(sd), cudaMemcpyHostToDevice, st));
+      chk(cudaMemcpyAsync(d_units, units.data(), sizeof(UnitDev) * units.size(),
+                          cudaMemcpyHostToDevice, st));
+      float ms_best = 1e30f;
+      chk(raise_smem_limit(si.smem));
+      for (int rep = 0; rep < 4 && err == cudaSuccess; ++rep) {
+        chk(cudaEventRecord(e0, st));
+        chk(launch_batch(d_set, d_units, (int)units.size(), d_counter, scratch, scr, si.smem, sms,
+                         st));
+        chk(cudaEventRecord(e1, st));
+        chk(cudaEventSynchronize(e1));
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (rep > 0) ms_best = std::min(ms_best, ms);  // first launch warms up
+      }
+      const double us = 1e3 * ms_best / (double)E;
+      t.us[v] = us;
+      if (us < best) { best = us; t.variant = v; t.us_per_element = us; }
+    }
+    if (st) cudaStreamSynchronize(st);
+    cudaFree(q); cudaFree(p); cudaFree(a); cudaFree(f);
+    cudaFree(d_set); cudaFree(d_units); cudaFree(d_counter); cudaFree(scratch);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    if (st) cudaStreamDestroy(st);
+    if (err != cudaSuccess) { t.variant = -1; return err; }
+  }
+  if (variant) *variant = t.variant;
+  if (us_per_element) *us_per_element = t.us_per_element;
+  if (us_all)
+    for (int v = 0; v < kMaxVariants; ++v) us_all[v] = t.us[v];
+  return cudaSuccess;
+}
+
+// ---- plans ------------------------------------------------------------------
+
+struct BatchPlan {
+  int device = -1;
+  int nsets = 0, nunits = 0, ctas = 0;
+  size_t smem = 0;
+  SetDev* d_sets = nullptr;
+  UnitDev* d_units = nullptr;
+  unsigned int* d_counter = nullptr;
+  double* d_scratch = nullptr;  // parked new terms of the large-N shapes, per CTA
+  size_t scratch_per_cta = 0;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+};
+
+void destroy_plan(BatchPlan* p) {
+  if (!p) return;
+  if (p->exec) cudaGraphExecDestroy(p->exec);
+  if (p->graph) cudaGraphDestroy(p->graph);
+  cudaFree(p->d_sets);
+  cudaFree(p->d_units);
+  cudaFree(p->d_counter);
+  delete p;
+}
+
+// Builds the work list (cost-sorted), uploads it and captures counter reset +
+// persistent kernel into a CUDA graph. sets[i].variant < 0 = autotuned.
+cudaError_t create_plan(int nsets, const int* N, const int64_t* E, const double* const* q,
+                        const double* const* params, double* const* avg, double* const* faces,
+                        const double* const* tables, const int* forced_variant, BatchPlan** out) {
+  *out = nullptr;
+  BatchPlan* p = new (std::nothrow) BatchPlan;
+  if (!p) return cudaErrorMemoryAllocation;
+  cudaGetDevice(&p->device);
+  std::vector<SetDev> sets((size_t)nsets);
+  std::vector<double> cost((size_t)nsets);
+  cudaError_t err = cudaSuccess;
+  for (int i = 0; i < nsets && err == cudaSuccess; ++i) {
+    int v = forced_variant ? forced_variant[i] : -1;
+    double us = 0.0;
+    if (v < 0) {
+      err = autotune(N[i], tables[i], &v, &us, nullptr);
+    } else {
+      const double F = 36.0 * std::pow(N[i], 5) + 66.0 * std::pow(N[i], 4) + 108.0 * std::pow(N[i], 3);
+      us = F / 1.2e6;  // FP64-bound estimate
+    }
+    if (err != cudaSuccess) break;
+    if (v < 0 || v >= kMaxVariants || !shapes().s[N[i]][v].valid) { err = cudaErrorInvalidValue; break; }
+    sets[i] = SetDev{q[i], params[i], avg[i], faces[i], tables[i], E[i], N[i], v};
+    cost[i] = us * shapes().s[N[i]][v].epc;
+    p->smem = std::max(p->smem, shapes().s[N[i]][v].smem);
+    p->scratch_per_cta = std::max(p->scratch_per_cta, shapes().s[N[i]][v].scratch);
+  }
+  std::vector<UnitDev> units;
+  if (err == cudaSuccess) {
+    std::vector<int> order((size_t)nsets);
+    for (int i = 0; i < nsets; ++i) order[i] = i;
+    // longest units first; within a set, element order
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return cost[a] > cost[b]; });
+    for (int i : order) {
+      const int epc = shapes().s[sets[i].N][sets[i].variant].epc;
+      for (int64_t e = 0; e < sets[i].E; e += epc) units.push_back(UnitDev{e, i, 0});
+    }
+    if (units.size() > 0x7fffffffu) err = cudaErrorInvalidValue;
+  }
+  p->nsets = nsets;
+  p->nunits = (int)units.size();
+  cudaStream_t st = nullptr;
+  if (err == cudaSuccess) err = cudaMalloc(&p->d_sets, sizeof(SetDev) * std::max(1, nsets));
+  if (err == cudaSuccess) err = cudaMalloc(&p->d_units, sizeof(UnitDev) * std::max<size_t>(1, units.size()));
+  if (err == cudaSuccess) err = cudaMalloc(&p->d_counter, sizeof(unsigned int));
+  if (err == cudaSuccess && nsets > 0)
+    err = cudaMemcpy(p->d_sets, sets.data(), sizeof(SetDev) * nsets, cudaMemcpyHostToDevice);
+  if (err == cudaSuccess && !units.empty())
+    err = cudaMemcpy(p->d_units, units.data(), sizeof(UnitDev) * units.size(), cudaMemcpyHostToDevice);
+  if (err == cudaSuccess) {
+    int per_sm = 0;
+    err = raise_smem_limit(p->smem);
+    if (err == cudaSuccess)
+      err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_kernel, kBatchThreads,
+                                                          std::max<size_t>(p->smem, 1));
+    p->ctas = std::max(1, per_sm) * sm_count();
+    if (p->nunits > 0 && p->ctas > p->nunits) p->ctas = p->nunits;
+  }
+  if (err == cudaSuccess && p->scratch_per_cta)
+    err = cudaMalloc(&p->d_scratch, p->scratch_per_cta * (size_t)p->ctas);
+  if (err == cudaSuccess) err = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+  if (err == cudaSuccess) err = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal);
+  if (err == cudaSuccess) {
+    cudaError_t le = cudaSuccess;
+    if (p->nunits > 0)
+      le = launch_batch(p->d_sets, p->d_units, p->nunits, p->d_counter, p->d_scratch,
+                        p->scratch_per_cta, std::max<size_t>(p->smem, 1), p->ctas, st);
+    err = cudaStreamEndCapture(st, &p->graph);
+    if (le != cudaSuccess) err = le;
+  }
+  if (err == cudaSuccess) err = cudaGraphInstantiate(&p->exec, p->graph, 0);
+  if (st) cudaStreamDestroy(st);
+  if (err != cudaSuccess) {
+    cudaGetLastError();
+    destroy_plan(p);
+    return err;
+  }
+  *out = p;
+  return cudaSuccess;
+}
+
+cudaError_t launch_plan(BatchPlan* p, cudaStream_t stream) {
+  if (p->nunits == 0) return cudaSuccess;
+  return cudaGraphLaunch(p->exec, stream);
+}
+
+void plan_info(const BatchPlan* p, int* units, int* ctas, size_t* smem) {
+  if (units) *units = p->nunits;
+  if (ctas) *ctas = p->ctas;
+  if (smem) *smem = p->smem;
+}
+
+}  // namespace stp

@@ -20,28 +20,10 @@
 // Taylor bookkeeping: r_k = dt^k/(k+1)! q^(k) satisfies r_0 = q,
 // r_{k+1} = dt/(k+2) * L r_k with L q = -sum_d B_d (D_d q)/dx, and the time
 // average of Eq. (exahypeTimeAverage) divided by dt is sum_{k=0..N} r_k.
-#include "ck_fp64.cuh"
-#include "stp_internal.h"
+#include "fp64_group.cuh"
 
 namespace stp {
 namespace {
-
-constexpr int ceil_div(int a, int b) { return (a + b - 1) / b; }
-
-template <int N, int NPT, int EPC, bool AVG_SMEM>
-struct Fp64Shape {
-  static constexpr int N3 = N * N * N;
-  static constexpr int T = ceil_div(N3, NPT);       // threads per element
-  static constexpr int BLOCK = T * EPC;
-  static constexpr int S = N3 | 1;                  // odd row stride: no bank aliasing across quantities
-  static constexpr int LDD = N | 1;                 // odd row stride of D: distinct banks per row
-  static constexpr int SLOT = (kQuantities + 4 + (AVG_SMEM ? kQuantities : 0)) * S;
-  static constexpr int TABLE = N * N * LDD + 2 * N;
-  static constexpr size_t SMEM = sizeof(double) * (size_t)(TABLE + EPC * SLOT);
-  static constexpr int MINB_SMEM = (int)((232448 - 1024) / SMEM);
-  static constexpr int MINB_THR = 2048 / BLOCK;
-  static constexpr int MINB = MINB_SMEM < 1 ? 1 : (MINB_SMEM < MINB_THR ? MINB_SMEM : MINB_THR);
-};
 
 template <int N, int NPT, int EPC, bool AVG_SMEM>
 __global__ void __launch_bounds__(Fp64Shape<N, NPT, EPC, AVG_SMEM>::BLOCK,
@@ -49,105 +31,9 @@ __global__ void __launch_bounds__(Fp64Shape<N, NPT, EPC, AVG_SMEM>::BLOCK,
 fp64_stp_kernel(const double* __restrict__ q, const double* __restrict__ params,
                 double* __restrict__ out_avg, double* __restrict__ out_faces,
                 const double* __restrict__ tables, int64_t E) {
-  using Sh = Fp64Shape<N, NPT, EPC, AVG_SMEM>;
-  constexpr int N3 = Sh::N3, T = Sh::T, S = Sh::S, LDD = Sh::LDD;
-  constexpr int M = kQuantities;
   extern __shared__ double smem[];
-  double* sD = smem;                     // [N steps][N rows][LDD]
-  double* sPhi = sD + N * N * LDD;       // phi0[N], phi1[N]
-  const int tid = threadIdx.x;
-  const int el = tid / T;
-  const int lt = tid - el * T;
-  const int64_t e = (int64_t)blockIdx.x * EPC + el;
-  const bool active = (el < EPC) && (e < E);
-  double* sp = sPhi + 2 * N + el * Sh::SLOT;  // p[M][S]: current Taylor term r_k
-  double* sc = sp + M * S;                     // coef[4][S]: 1/rho, lambda, mu, 2 mu
-  double* sa = sc + 4 * S;                     // avg[M][S] when AVG_SMEM
-  double* gavg = out_avg + e * (int64_t)(M * N3);
-
-  for (int i = tid; i < N * N * N; i += blockDim.x) {
-    const int row = i / N, col = i - row * N;  // row = k*N + r
-    sD[row * LDD + col] = tables[i];
-  }
-  for (int i = tid; i < 2 * N; i += blockDim.x) sPhi[i] = tables[N3 + i];
-
-  if (active) {
-    const double* qe = q + e * (int64_t)(M * N3);
-    for (int f = lt; f < M * N3; f += T) {  // coalesced AoS read, SoA scatter
-      const int n = f / M, s = f - n * M;
-      const double v = __ldg(qe + f);
-      sp[s * S + n] = v;
-      if (AVG_SMEM) sa[s * S + n] = v; else gavg[f] = v;
-    }
-    const double* pe = params + e * (int64_t)(kParams * N3);
-    for (int n = lt; n < N3; n += T) {
-      const double rho = __ldg(pe + 3 * n), cp = __ldg(pe + 3 * n + 1), cs = __ldg(pe + 3 * n + 2);
-      elastic_coefficients(rho, cp, cs, &sc[n], &sc[S + n], &sc[2 * S + n], &sc[3 * S + n]);
-    }
-  }
-  __syncthreads();
-
-  for (int k = 0; k < N; ++k) {
-    const double* Dk = sD + k * N * LDD;
-    double r[NPT][M];
-#pragma unroll
-    for (int j = 0; j < NPT; ++j) {
-      const int n = lt + j * T;
-      if (!active || n >= N3) continue;
-      const int x = n % N, y = (n / N) % N, z = n / (N * N);
-      ck_node_fp64<N, S, LDD>(sp, Dk, x, y, z, sc[n], sc[S + n], sc[2 * S + n], sc[3 * S + n], r[j]);
-      if (AVG_SMEM) {
-#pragma unroll
-        for (int s = 0; s < M; ++s) sa[s * S + n] += r[j][s];
-      } else {
-#pragma unroll
-        for (int s = 0; s < M; ++s) gavg[n * M + s] += r[j][s];
-      }
-    }
-    __syncthreads();  // every thread has read r_k
-    if (k + 1 < N) {
-#pragma unroll
-      for (int j = 0; j < NPT; ++j) {
-        const int n = lt + j * T;
-        if (!active || n >= N3) continue;
-#pragma unroll
-        for (int s = 0; s < M; ++s) sp[s * S + n] = r[j][s];
-      }
-      __syncthreads();  // r_{k+1} visible
-    }
-  }
-
-  if (!active) return;
-  if (AVG_SMEM) {
-    for (int f = lt; f < M * N3; f += T) {
-      const int n = f / M, s = f - n * M;
-      gavg[f] = sa[s * S + n];
-    }
-  }
-  // Face projections of the time average (Sec. II-B): one phi contraction per face.
-  double* fe = out_faces + e * (int64_t)(6 * N * N * M);
-  for (int o = lt; o < 6 * N * N * M; o += T) {
-    const int s = o % M;
-    int rest = o / M;
-    const int bb = rest % N;
-    rest /= N;
-    const int aa = rest % N;
-    const int f = rest / N;
-    const int d = f >> 1;
-    const double* phi = sPhi + (f & 1) * N;
-    int base, stride;
-    if (d == 0) { base = (aa * N + bb) * N; stride = 1; }
-    else if (d == 1) { base = aa * N * N + bb; stride = N; }
-    else { base = aa * N + bb; stride = N * N; }
-    double acc = 0.0;
-#pragma unroll
-    for (int i = 0; i < N; ++i) {
-      const int node = base + i * stride;
-      const double v = AVG_SMEM ? sa[s * S + node] : gavg[node * M + s];
-      acc = fma(phi[i], v, acc);
-    }
-    fe[o] = acc;
-  }
+  fp64_group<N, NPT, EPC, AVG_SMEM, Fp64Shape<N, NPT, EPC, AVG_SMEM>::BLOCK>(
+      smem, q, params, out_avg, out_faces, tables, (int64_t)blockIdx.x * EPC, E);
 }
 
 template <int N, int NPT, int EPC, bool AVG_SMEM>

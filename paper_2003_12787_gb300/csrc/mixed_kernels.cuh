@@ -222,7 +222,7 @@ __global__ void __launch_bounds__(MixedShape<N, T, FP16>::THREADS, MixedShape<N,
 mixed_stp_kernel(const double* __restrict__ q, const double* __restrict__ params,
                  double* __restrict__ out_avg, double* __restrict__ out_faces,
                  const double* __restrict__ tables, const double* __restrict__ Dref,
-                 double h_inv_dt, int64_t E, unsigned int* __restrict__ status) {
+                 float dt_over_dx, int eD, int64_t E, unsigned int* __restrict__ status) {
   using Sh = MixedShape<N, T, FP16>;
   constexpr int N3 = Sh::N3, S = Sh::S, LDD = Sh::LDD, NPT = Sh::NPT, THREADS = Sh::THREADS;
   constexpr int TILES = Sh::TILES, ROWS = Sh::ROWS;
@@ -259,13 +259,7 @@ mixed_stp_kernel(const double* __restrict__ q, const double* __restrict__ params
   for (int i = tid; i < 2 * N; i += THREADS) phi[i] = tables[N3 + i];
   if (tid < 18) smax[tid] = 0u;
   // split derivative matrix: B_t[n=i][k=l] = slice t of D[i][l] * 2^sD (zero padded)
-  int eD;
-  {
-    double dmax = 0.0;
-    for (int i = 0; i < N * N; ++i) dmax = fmax(dmax, fabs(Dref[i]));
-    frexp(dmax, &eD);
-  }
-  const double sD = ldexp(1.0, kScaleExp - eD);
+  const double sD = ldexp(1.0, kScaleExp - eD);  // eD: exponent of max |D| (host)
   for (int i = tid; i < 16 * 16; i += THREADS) {
     const int n = i >> 4, k = i & 15;
     double rem = (n < N && k < N) ? Dref[n * N + k] * sD : 0.0;
@@ -353,7 +347,7 @@ mixed_stp_kernel(const double* __restrict__ q, const double* __restrict__ params
     __syncthreads();
     if (tid < 9) smax[9 * ((k + 1) & 1) + tid] = 0u;  // buffer of step k+1 (last read in step k-1)
     float sc[9];  // 2^(14 - e_s): scale of quantity s
-    const float step = (float)(h_inv_dt / (double)(k + 2));  // dt / ((k+2) dx)
+    const float step = dt_over_dx / (float)(k + 2);  // dt / ((k+2) dx)
 #pragma unroll
     for (int s = 0; s < 9; ++s) {
       int es;
@@ -525,7 +519,7 @@ mixed_stp_kernel(const double* __restrict__ q, const double* __restrict__ params
 template <int N, int T, bool FP16>
 cudaError_t launch_mixed_shape(int64_t E, const double* q, const double* params, double* out_avg,
                                double* out_faces, const double* tables, const double* Dref,
-                               double h_inv_dt, unsigned int* status, cudaStream_t stream) {
+                               double dt_over_dx, int eD, unsigned int* status, cudaStream_t stream) {
   using Sh = MixedShape<N, T, FP16>;
   static_assert(Sh::SMEM <= 232448, "shared memory budget of one CTA exceeded");
   auto kern = mixed_stp_kernel<N, T, FP16>;
@@ -533,20 +527,20 @@ cudaError_t launch_mixed_shape(int64_t E, const double* q, const double* params,
   if (err != cudaSuccess) return err;
   if (E > 0x7fffffffLL) return cudaErrorInvalidValue;
   kern<<<(unsigned)E, Sh::THREADS, Sh::SMEM, stream>>>(q, params, out_avg, out_faces, tables, Dref,
-                                                       h_inv_dt, E, status);
+                                                       (float)dt_over_dx, eD, E, status);
   return cudaGetLastError();
 }
 
 template <int N>
 cudaError_t launch_mixed_n(int variant, int64_t E, const double* q, const double* params,
                            double* out_avg, double* out_faces, const double* tables,
-                           const double* Dref, double h_inv_dt, unsigned int* status,
+                           const double* Dref, double dt_over_dx, int eD, unsigned int* status,
                            cudaStream_t stream) {
   switch (variant) {
-    case 1: return launch_mixed_shape<N, 2, false>(E, q, params, out_avg, out_faces, tables, Dref, h_inv_dt, status, stream);
-    case 2: return launch_mixed_shape<N, 3, false>(E, q, params, out_avg, out_faces, tables, Dref, h_inv_dt, status, stream);
-    case 3: return launch_mixed_shape<N, 2, true>(E, q, params, out_avg, out_faces, tables, Dref, h_inv_dt, status, stream);
-    case 4: return launch_mixed_shape<N, 3, true>(E, q, params, out_avg, out_faces, tables, Dref, h_inv_dt, status, stream);
+    case 1: return launch_mixed_shape<N, 2, false>(E, q, params, out_avg, out_faces, tables, Dref, dt_over_dx, eD, status, stream);
+    case 2: return launch_mixed_shape<N, 3, false>(E, q, params, out_avg, out_faces, tables, Dref, dt_over_dx, eD, status, stream);
+    case 3: return launch_mixed_shape<N, 2, true>(E, q, params, out_avg, out_faces, tables, Dref, dt_over_dx, eD, status, stream);
+    case 4: return launch_mixed_shape<N, 3, true>(E, q, params, out_avg, out_faces, tables, Dref, dt_over_dx, eD, status, stream);
     default: return cudaErrorInvalidValue;
   }
 }
@@ -557,10 +551,10 @@ cudaError_t launch_mixed_n(int variant, int64_t E, const double* q, const double
 template <int N>
 cudaError_t launch_mixed_for(int variant, int64_t E, const double* q, const double* params,
                              double* out_avg, double* out_faces, const double* tables,
-                             const double* Dref, double h_inv_dt, unsigned int* status,
+                             const double* Dref, double dt_over_dx, int eD, unsigned int* status,
                              cudaStream_t stream) {
   return mixed::launch_mixed_n<N>(variant, E, q, params, out_avg, out_faces, tables, Dref,
-                                  h_inv_dt, status, stream);
+                                  dt_over_dx, eD, status, stream);
 }
 
 }  // namespace stp

@@ -3,6 +3,6 @@
 
 namespace stp {
 template cudaError_t launch_mixed_for<10>(int, int64_t, const double*, const double*, double*,
-                                          double*, const double*, const double*, double, unsigned int*,
+                                          double*, const double*, const double*, double, int, unsigned int*,
                                           cudaStream_t);
 }  // namespace stp

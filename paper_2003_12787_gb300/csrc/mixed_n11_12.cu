@@ -3,9 +3,9 @@
 
 namespace stp {
 template cudaError_t launch_mixed_for<11>(int, int64_t, const double*, const double*, double*,
-                                          double*, const double*, const double*, double, unsigned int*,
+                                          double*, const double*, const double*, double, int, unsigned int*,
                                           cudaStream_t);
 template cudaError_t launch_mixed_for<12>(int, int64_t, const double*, const double*, double*,
-                                          double*, const double*, const double*, double, unsigned int*,
+                                          double*, const double*, const double*, double, int, unsigned int*,
                                           cudaStream_t);
 }  // namespace stp

@@ -3,12 +3,12 @@
 
 namespace stp {
 template cudaError_t launch_mixed_for<7>(int, int64_t, const double*, const double*, double*,
-                                          double*, const double*, const double*, double, unsigned int*,
+                                          double*, const double*, const double*, double, int, unsigned int*,
                                           cudaStream_t);
 template cudaError_t launch_mixed_for<8>(int, int64_t, const double*, const double*, double*,
-                                          double*, const double*, const double*, double, unsigned int*,
+                                          double*, const double*, const double*, double, int, unsigned int*,
                                           cudaStream_t);
 template cudaError_t launch_mixed_for<9>(int, int64_t, const double*, const double*, double*,
-                                          double*, const double*, const double*, double, unsigned int*,
+                                          double*, const double*, const double*, double, int, unsigned int*,
                                           cudaStream_t);
 }  // namespace stp

@@ -4,6 +4,7 @@
 #include <cstring>
 #include <new>
 #include <string>
+#include <vector>
 
 #include "stp_internal.h"
 
@@ -14,6 +15,7 @@ struct stp_handle_s {
   stp::HostTables host;
   double* d_tables = nullptr;  // step matrices, phi0, phi1, D (device)
   unsigned int* d_status = nullptr;  // device-side status word (bounded-wait timeouts)
+  int eD = 0;                        // binary exponent of max |D| (mixed-precision scaling)
   stp_precision precision = STP_PRECISION_FP64;
   // host-buffer path: chunked pipeline state, created on first use
   static constexpr int kStages = 3;
@@ -97,8 +99,8 @@ cudaError_t launch_configured(stp_handle h, int64_t E, const double* q, const do
   if (h->precision == STP_PRECISION_FP64 || h->N < 2)
     return stp::launch_fp64(h->N, E, q, params, avg, faces, h->d_tables, stream);
   return stp::launch_mixed(h->N, (int)h->precision, E, q, params, avg, faces, h->d_tables,
-                           h->d_tables + stp::table_offset_D(h->N), h->dt / h->dx, h->d_status,
-                           stream);
+                           h->d_tables + stp::table_offset_D(h->N), h->dt / h->dx, h->eD,
+                           h->d_status, stream);
 }
 
 }  // namespace
@@ -135,6 +137,11 @@ stp_status stp_create(int order, int m, double dx, double dt, stp_handle* out) {
   if (!stp::make_tables(N, &h->host)) {
     delete h;
     return fail(STP_ERR_UNSUPPORTED, "node computation did not converge");
+  }
+  {
+    double dmax = 0.0;
+    for (int i = 0; i < N * N; ++i) dmax = std::fmax(dmax, std::fabs(h->host.D[i]));
+    std::frexp(dmax, &h->eD);
   }
   cudaError_t e = cudaGetDevice(&h->device);
   if (e != cudaSuccess) { delete h; return cuda_fail(e, "cudaGetDevice"); }
@@ -304,6 +311,109 @@ stp_status stp_device_status(stp_handle h, void* stream, unsigned int* flags) {
   if ((e = cudaMemset(h->d_status, 0, sizeof(v))) != cudaSuccess) return cuda_fail(e, "status reset");
   *flags = v;
   return v ? fail(STP_ERR_TIMEOUT, "a bounded device-side wait gave up") : STP_OK;
+}
+
+}  // extern "C"
+
+struct stp_batch_s {
+  stp::BatchPlan* plan = nullptr;
+  int device = -1;
+};
+
+extern "C" {
+
+stp_status stp_batch_create(int nsets, const stp_batch_set* sets, stp_batch* out) {
+  if (!out) return fail(STP_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  if (nsets < 0 || (nsets > 0 && !sets)) return fail(STP_ERR_INVALID_ARG, "bad set list");
+  int dev = -1;
+  cudaGetDevice(&dev);
+  std::vector<int> N(nsets);
+  std::vector<int64_t> E(nsets);
+  std::vector<const double*> q(nsets), p(nsets), tb(nsets);
+  std::vector<double*> a(nsets), f(nsets);
+  for (int i = 0; i < nsets; ++i) {
+    const stp_batch_set& st = sets[i];
+    stp_status s = validate_common(st.handle, st.elements, st.q, st.params, st.out_avg, st.out_faces);
+    if (s != STP_OK) return fail(s, "set " + std::to_string(i) + ": " + g_last_error);
+    if (st.handle->precision != STP_PRECISION_FP64)
+      return fail(STP_ERR_UNSUPPORTED, "set " + std::to_string(i) + ": batched launches are FP64");
+    if (st.handle->device != dev)
+      return fail(STP_ERR_UNSUPPORTED, "set " + std::to_string(i) + ": handle on another device");
+    if (st.elements > 0) {
+      const char* names[4] = {"q", "params", "out_avg", "out_faces"};
+      const void* ptrs[4] = {st.q, st.params, st.out_avg, st.out_faces};
+      for (int k = 0; k < 4; ++k)
+        if ((s = check_device_ptr(ptrs[k], dev, names[k])) != STP_OK)
+          return fail(s, "set " + std::to_string(i) + ": " + g_last_error);
+    }
+    N[i] = st.handle->N;
+    E[i] = st.elements;
+    q[i] = st.q;
+    p[i] = st.params;
+    a[i] = st.out_avg;
+    f[i] = st.out_faces;
+    tb[i] = st.handle->d_tables;
+  }
+  // outputs of different sets must not overlap each other or any set's inputs
+  for (int i = 0; i < nsets; ++i) {
+    const Sizes si = sizes_per_element(N[i]);
+    const void* oi[2] = {a[i], f[i]};
+    const size_t ni[2] = {si.avg * (size_t)E[i], si.faces * (size_t)E[i]};
+    for (int j = 0; j < nsets; ++j) {
+      if (j == i) continue;
+      const Sizes sj = sizes_per_element(N[j]);
+      const void* bj[4] = {q[j], p[j], a[j], f[j]};
+      const size_t nj[4] = {sj.q * (size_t)E[j], sj.params * (size_t)E[j], sj.avg * (size_t)E[j],
+                            sj.faces * (size_t)E[j]};
+      for (int x = 0; x < 2; ++x)
+        for (int y = 0; y < 4; ++y)
+          if (ni[x] && nj[y] && overlap(oi[x], ni[x], bj[y], nj[y]))
+            return fail(STP_ERR_INVALID_ARG, "outputs of set " + std::to_string(i) +
+                                                 " overlap buffers of set " + std::to_string(j));
+    }
+  }
+  stp_batch b = new (std::nothrow) stp_batch_s;
+  if (!b) return fail(STP_ERR_OOM, "host allocation failed");
+  b->device = dev;
+  cudaError_t e = stp::create_plan(nsets, N.data(), E.data(), q.data(), p.data(), a.data(), f.data(),
+                                   tb.data(), nullptr, &b->plan);
+  if (e != cudaSuccess) {
+    delete b;
+    if (e == cudaErrorMemoryAllocation) return fail(STP_ERR_OOM, "batch plan allocation failed");
+    return cuda_fail(e, "batch plan");
+  }
+  *out = b;
+  return STP_OK;
+}
+
+stp_status stp_batch_launch(stp_batch b, void* stream) {
+  if (!b || !b->plan) return fail(STP_ERR_INVALID_ARG, "invalid batch");
+  cudaError_t e = stp::launch_plan(b->plan, static_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) return cuda_fail(e, "batch graph launch");
+  return STP_OK;
+}
+
+stp_status stp_batch_info(stp_batch b, int* units, int* ctas, int64_t* smem_bytes) {
+  if (!b || !b->plan) return fail(STP_ERR_INVALID_ARG, "invalid batch");
+  size_t sm = 0;
+  stp::plan_info(b->plan, units, ctas, &sm);
+  if (smem_bytes) *smem_bytes = (int64_t)sm;
+  return STP_OK;
+}
+
+stp_status stp_batch_destroy(stp_batch b) {
+  if (!b) return STP_OK;
+  stp::destroy_plan(b->plan);
+  delete b;
+  return STP_OK;
+}
+
+stp_status stp_autotune(stp_handle h, int* variant, double* us_per_element, double* us_variants) {
+  if (!h) return fail(STP_ERR_INVALID_ARG, "invalid handle");
+  cudaError_t e = stp::autotune(h->N, h->d_tables, variant, us_per_element, us_variants);
+  if (e != cudaSuccess) return cuda_fail(e, "autotune");
+  return STP_OK;
 }
 
 stp_status stp_measure_fp64_peak(double* gflops, void* stream) {

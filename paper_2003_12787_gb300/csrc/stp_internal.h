@@ -42,11 +42,29 @@ cudaError_t launch_fp64(int N, int64_t E, const double* q, const double* params,
 int fp64_elements_per_cta(int N);
 
 // Mixed-precision kernel (mixed_kernels.cu); variant 1..4 = BF16x2, BF16x3,
-// FP16x2, FP16x3; 2 <= N <= 12. status receives bit 0 on a bounded-wait timeout.
+// FP16x2, FP16x3; 2 <= N <= 12. eD = binary exponent of max |D| (frexp).
+// status receives bit 0 on a bounded-wait timeout.
 cudaError_t launch_mixed(int N, int variant, int64_t E, const double* q, const double* params,
                          double* out_avg, double* out_faces, const double* tables,
-                         const double* Dref, double dt_over_dx, unsigned int* status,
+                         const double* Dref, double dt_over_dx, int eD, unsigned int* status,
                          cudaStream_t stream);
+
+// Batched persistent FP64 launch (batch.cu).
+struct BatchPlan;
+// Candidate shapes of order N for the batched kernel; fills epc_out[v] with
+// the elements per CTA of each; returns their number.
+int batch_variants(int N, int* epc_out);
+// Measures (once per device and N, then cached) every candidate shape on a
+// synthetic set and returns the fastest; us_all[v] gets each candidate's
+// microseconds per element (may be NULL).
+cudaError_t autotune(int N, const double* tables, int* variant, double* us_per_element,
+                     double* us_all);
+cudaError_t create_plan(int nsets, const int* N, const int64_t* E, const double* const* q,
+                        const double* const* params, double* const* avg, double* const* faces,
+                        const double* const* tables, const int* forced_variant, BatchPlan** out);
+cudaError_t launch_plan(BatchPlan* p, cudaStream_t stream);
+void plan_info(const BatchPlan* p, int* units, int* ctas, size_t* smem);
+void destroy_plan(BatchPlan* p);
 
 cudaError_t launch_fp64_peak(double* sink, int blocks, int threads, int iters,
                              cudaStream_t stream);

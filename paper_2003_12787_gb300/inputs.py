@@ -140,3 +140,32 @@ def order7_case(device="cpu") -> Problem:
 def order9_case(device="cpu") -> Problem:
     """Order 9 (N=10), 16384 elements on a 32x32x16 grid, side 1/32."""
     return elastic_problem(10, grid=(32, 32, 16), h=1.0 / 32, device=device)
+
+
+def batched_sets_recipe(seed: int = 1003, n_sets: int = 64, n_min: int = 4, n_max: int = 12,
+                        e_min: int = 64, e_max: int = 16384):
+    """Sizes and seeds of the batched workload: n_sets element sets with
+    N_i ~ U{n_min..n_max} and E_i = round(exp(U[ln e_min, ln e_max])) drawn from
+    PCG64(seed) in that order; set i uses material/wave seeds 1001+16i,
+    1002+16i on a cube grid of side ceil(E_i^(1/3)), h = 1/side, first E_i
+    elements."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    Ns = rng.integers(n_min, n_max + 1, n_sets)
+    Es = np.rint(np.exp(rng.uniform(math.log(e_min), math.log(e_max), n_sets))).astype(int)
+    out = []
+    for i in range(n_sets):
+        E = int(Es[i])
+        G = max(1, math.ceil(round(E ** (1.0 / 3.0), 9)))
+        while G ** 3 < E:
+            G += 1
+        out.append(dict(N=int(Ns[i]), E=E, grid=(G, G, G), h=1.0 / G,
+                        seed_material=1001 + 16 * i, seed_waves=1002 + 16 * i))
+    return out
+
+
+def batched_problems(device="cpu", **kw):
+    """The batched workload's problems (see batched_sets_recipe)."""
+    return [elastic_problem(r["N"], grid=r["grid"], E=r["E"], h=r["h"],
+                            seed_material=r["seed_material"], seed_waves=r["seed_waves"],
+                            device=device)
+            for r in batched_sets_recipe(**kw)]

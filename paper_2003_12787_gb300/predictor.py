@@ -78,3 +78,44 @@ class Predictor:
         avg, faces = out if out is not None else self.empty_outputs(E, device="cpu")
         B.stp_predict_host(self.handle, E, q, params, avg, faces, stream)
         return avg, faces
+
+
+class Batch:
+    """A captured batched launch over several (Predictor, q, params) sets.
+
+    Outputs are allocated here (device tensors) and baked into the plan; each
+    launch() replays the plan's CUDA graph on the given stream.
+    """
+
+    def __init__(self, items):
+        self.items = []
+        sets = []
+        for P, q, params in items:
+            P._check_inputs(q, params)
+            E = q.shape[0]
+            avg, faces = P.empty_outputs(E, device=q.device)
+            self.items.append((P, q, params, avg, faces))
+            sets.append((P.handle, E, q, params, avg, faces))
+        self.handle = B.stp_batch_create(sets)
+
+    def launch(self, stream=None):
+        if stream is None:
+            stream = torch.cuda.current_stream()
+        B.stp_batch_launch(self.handle, stream)
+
+    def outputs(self, i):
+        return self.items[i][3], self.items[i][4]
+
+    def info(self):
+        return B.stp_batch_info(self.handle)
+
+    def close(self):
+        if self.handle is not None:
+            B.stp_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
