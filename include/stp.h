@@ -188,6 +188,35 @@ stp_status stp_batch_destroy(stp_batch b);
 stp_status stp_autotune(stp_handle h, int* variant, double* us_per_element,
                         double* us_variants);
 
+/*
+ * Batched FP64 launch that allocates nothing. The paper has no counterpart:
+ * this entry point exists for callers that cannot call cudaMalloc where they
+ * run the predictor (a host that owns all device memory through its own pool,
+ * a thread that must not take the device-wide synchronisation an allocation
+ * can cause, a device already handed out in full). stp_batch_create allocates
+ * a work list, a work counter and scratch buffers; this call instead keeps its
+ * scratch - the work counter and one parking area per CTA for the new Taylor
+ * terms of orders 10 and 11 (N = 11, 12) - in one 24 MiB array that is part of
+ * the library's device image (every GPU that loads the library holds it until
+ * the process exits), and passes the set descriptors as kernel parameters.
+ *
+ *   nsets <= 128 sets, each as in stp_batch_set (FP64 handles, device
+ *   buffers, outputs not overlapping any input or other output); results
+ *   equal stp_predict's for every set. Enqueued on `stream`, asynchronous.
+ *   Returns STP_ERR_INVALID_ARG when nsets exceeds 128 or the call would
+ *   need more than the 24 MiB scratch (a device with more than about 190 SMs
+ *   running order 11), STP_ERR_UNSUPPORTED for non-FP64 handles.
+ *
+ * The first call on a device looks up the array's device address (with that
+ * device current) and caches it; make that first call before any stream
+ * capture. Every call uses the same array and it keeps the last call's
+ * contents; the call clears the work counter itself. Calls whose work overlaps
+ * on the GPU (other streams, or host threads racing) race on the array: order
+ * them on one stream. No cudaMalloc, cudaFree or other allocating routine is
+ * called; only an argument error records its message in a host string.
+ */
+stp_status stp_batch_run_static(int nsets, const stp_batch_set* sets, void* stream);
+
 /* Release the handle's device tables and buffers. NULL is a no-op (STP_OK). */
 stp_status stp_destroy(stp_handle h);
 

@@ -12,5 +12,5 @@ from ._binding import (PRECISIONS, STPError, stp_create, stp_destroy,  # noqa: F
                        stp_measure_fp64_peak, stp_nodes, stp_predict, stp_predict_host,
                        stp_reference_tables, stp_set_precision, stp_status_string)
 from ._binding import (stp_autotune, stp_batch_create, stp_batch_destroy,  # noqa: F401
-                       stp_batch_info, stp_batch_launch)
+                       stp_batch_info, stp_batch_launch, stp_batch_run_static)
 from .predictor import Batch, Predictor  # noqa: F401

@@ -70,6 +70,8 @@ def load():
         lib.stp_batch_destroy.argtypes = [vp]
         lib.stp_autotune.argtypes = [vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(dbl),
                                      ctypes.POINTER(dbl)]
+        lib.stp_batch_run_static.argtypes = [ctypes.c_int, vp, vp]
+        lib.stp_batch_run_static.restype = ctypes.c_int
         for name in ("stp_create", "stp_predict", "stp_predict_host", "stp_destroy",
                      "stp_reference_tables", "stp_measure_fp64_peak", "stp_set_precision",
                      "stp_device_status", "stp_batch_create", "stp_batch_launch",
@@ -207,3 +209,12 @@ def stp_autotune(h: int):
     allv = (ctypes.c_double * 2)()
     _check(load().stp_autotune(h, ctypes.byref(v), ctypes.byref(us), allv), "stp_autotune")
     return {"variant": v.value, "us_per_element": us.value, "us_variants": [allv[0], allv[1]]}
+
+
+def stp_batch_run_static(sets, stream=None) -> None:
+    """The allocation-free batched launch; sets as for stp_batch_create."""
+    arr = (BatchSet * max(1, len(sets)))()
+    for i, (h, E, q, p, a, f) in enumerate(sets):
+        arr[i] = BatchSet(h, E, _ptr(q), _ptr(p), _ptr(a), _ptr(f))
+    _check(load().stp_batch_run_static(len(sets), ctypes.cast(arr, ctypes.c_void_p), _stream(stream)),
+           "stp_batch_run_static")

@@ -1,0 +1,188 @@
+// Batched FP64 predictor that allocates nothing: stp_batch_run_static.
+//
+// Who needs it: code that must not call cudaMalloc at the point where it runs
+// the predictor - for example a caller that owns every byte of device memory
+// through its own pool and forbids other allocations, a host thread that may
+// not take the implicit device synchronisation cudaMalloc/cudaFree can bring,
+// or a process that has already handed the rest of the device to someone
+// else. The regular batched path (stp_batch_create) allocates its work list,
+// its work counter and its scratch buffers; this entry point instead keeps its
+// scratch (the work counter and the per-CTA parking area for new Taylor terms)
+// in one fixed-size array that is part of the library's device image, and
+// passes the set descriptors as kernel parameters.
+//
+// The paper has no counterpart to this entry point.
+#include <algorithm>
+#include <mutex>
+
+#include "fp64_group.cuh"
+
+namespace stp {
+namespace {
+
+constexpr int kStaticThreads = 512;
+constexpr int kStaticMaxSets = 128;
+// Scratch for one call: the work counter (first 256 bytes), then one parking
+// area per CTA of 9*S*EPC doubles for the orders whose shape parks new terms
+// (N = 11, 12; 124.5 KB per CTA at N = 12). 24 MiB covers one CTA per SM for
+// every order up to 190 SMs.
+constexpr size_t kStaticScratchBytes = (size_t)24 << 20;
+constexpr size_t kCounterBytes = 256;
+
+// File-scope scratch. Every GPU that loads the library holds it until the
+// process exits. In host code its name is only a host-side stand-in: the
+// device address comes from cudaGetSymbolAddress (see scratch_address).
+static __device__ __align__(256) unsigned char g_static_scratch[kStaticScratchBytes];
+
+// One fixed shape per order (512 threads): (N, nodes per thread, elements per
+// CTA, average in smem, new terms parked in scratch).
+#define STP_STATIC_SHAPES(X)                                                                      \
+  X(1, 1, 256, true, false) X(2, 1, 64, true, false) X(3, 1, 18, true, false)                    \
+  X(4, 1, 8, true, false) X(5, 1, 4, true, false) X(6, 1, 2, true, false) X(7, 1, 1, true, false) \
+  X(8, 1, 1, true, false) X(9, 2, 1, true, false) X(10, 2, 1, true, false)                       \
+  X(11, 3, 1, false, true) X(12, 4, 1, false, true)
+
+struct StaticSet {
+  const double* q;
+  const double* params;
+  double* avg;
+  double* faces;
+  const double* tables;
+  int64_t E;
+  int64_t first_unit;  // units of the sets before this one
+  int N;
+  int epc;
+};
+
+struct StaticBatch {
+  StaticSet sets[kStaticMaxSets];
+  int nsets;
+  int64_t nunits;
+};
+
+template <int N, int NPT, int EPC, bool AVG, bool RG>
+__device__ __noinline__ void static_unit(double* smem, const StaticSet& sd, int64_t e0, double* rbuf) {
+  fp64_group<N, NPT, EPC, AVG, kStaticThreads, RG>(smem, sd.q, sd.params, sd.avg, sd.faces,
+                                                   sd.tables, e0, sd.E, rbuf);
+}
+
+__global__ void __launch_bounds__(kStaticThreads, 1)
+static_batch_kernel(const __grid_constant__ StaticBatch b, unsigned char* scratch,
+                    int64_t park_doubles_per_cta) {
+  extern __shared__ double smem[];
+  __shared__ long long cur;
+  unsigned long long* counter = reinterpret_cast<unsigned long long*>(scratch);
+  double* rbuf = reinterpret_cast<double*>(scratch + kCounterBytes) + blockIdx.x * park_doubles_per_cta;
+  for (;;) {
+    if (threadIdx.x == 0) cur = (long long)atomicAdd(counter, 1ull);
+    __syncthreads();
+    const int64_t u = cur;
+    __syncthreads();
+    if (u >= b.nunits) break;
+    int lo = 0, hi = b.nsets - 1;  // last set whose first unit is <= u
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (b.sets[mid].first_unit <= u) lo = mid; else hi = mid - 1;
+    }
+    const StaticSet& sd = b.sets[lo];
+    const int64_t e0 = (u - sd.first_unit) * sd.epc;
+    switch (sd.N) {
+#define X(n_, npt_, epc_, avg_, rg_) \
+  case n_: static_unit<n_, npt_, epc_, avg_, rg_>(smem, sd, e0, rbuf); break;
+      STP_STATIC_SHAPES(X)
+#undef X
+      default: break;
+    }
+  }
+}
+
+struct StaticShape {
+  int epc = 0;
+  size_t smem = 0, park = 0;
+};
+
+StaticShape static_shape(int N) {
+  switch (N) {
+#define X(n_, npt_, epc_, avg_, rg_)                                                              \
+  case n_:                                                                                       \
+    return StaticShape{epc_, Fp64Shape<n_, npt_, epc_, avg_>::SMEM,                              \
+                       rg_ ? sizeof(double) * 9 * (size_t)Fp64Shape<n_, npt_, epc_, avg_>::S * epc_ \
+                           : 0};
+    STP_STATIC_SHAPES(X)
+#undef X
+    default: return StaticShape{};
+  }
+}
+
+// Device address of the scratch array, looked up once per device (with that
+// device current) and cached.
+std::mutex g_addr_mutex;
+unsigned char* g_addr[64] = {};
+
+cudaError_t scratch_address(int dev, unsigned char** out) {
+  if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lock(g_addr_mutex);
+  if (!g_addr[dev]) {
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
+    if (e != cudaSuccess) return e;
+    g_addr[dev] = static_cast<unsigned char*>(p);
+  }
+  *out = g_addr[dev];
+  return cudaSuccess;
+}
+
+}  // namespace
+
+size_t static_scratch_bytes() { return kStaticScratchBytes; }
+int static_max_sets() { return kStaticMaxSets; }
+
+// sets_N/E/...: validated by the caller. Returns cudaErrorInvalidValue with
+// *too_big = 1 when the call needs more scratch than the array holds.
+cudaError_t run_static_batch(int nsets, const int* N, const int64_t* E, const double* const* q,
+                             const double* const* params, double* const* avg,
+                             double* const* faces, const double* const* tables,
+                             cudaStream_t stream, int* too_big) {
+  *too_big = 0;
+  if (nsets < 0 || nsets > kStaticMaxSets) { *too_big = 1; return cudaErrorInvalidValue; }
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  unsigned char* scratch = nullptr;
+  if ((e = scratch_address(dev, &scratch)) != cudaSuccess) return e;
+  StaticBatch b;
+  b.nsets = nsets;
+  int64_t units = 0;
+  size_t smem = 1, park = 0;
+  for (int i = 0; i < nsets; ++i) {
+    const StaticShape sh = static_shape(N[i]);
+    if (sh.epc == 0) return cudaErrorInvalidValue;
+    b.sets[i] = StaticSet{q[i], params[i], avg[i], faces[i], tables[i], E[i], units, N[i], sh.epc};
+    units += (E[i] + sh.epc - 1) / sh.epc;
+    if (E[i] > 0) {
+      smem = std::max(smem, sh.smem);
+      park = std::max(park, sh.park);
+    }
+  }
+  b.nunits = units;
+  if (units == 0) return cudaSuccess;
+  int sms = 0, per_sm = 0;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if ((e = cudaFuncSetAttribute(static_batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)smem)) != cudaSuccess)
+    return e;
+  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, static_batch_kernel,
+                                                         kStaticThreads, smem)) != cudaSuccess)
+    return e;
+  int64_t ctas = (int64_t)std::max(1, per_sm) * sms;
+  ctas = std::min<int64_t>(ctas, units);
+  if (kCounterBytes + (size_t)ctas * park > kStaticScratchBytes) { *too_big = 1; return cudaErrorInvalidValue; }
+  // the counter must start at zero; the parking areas need no clearing (each
+  // parked value is written before it is read within the same work unit)
+  if ((e = cudaMemsetAsync(scratch, 0, sizeof(unsigned long long), stream)) != cudaSuccess) return e;
+  static_batch_kernel<<<(unsigned)ctas, kStaticThreads, smem, stream>>>(
+      b, scratch, (int64_t)(park / sizeof(double)));
+  return cudaGetLastError();
+}
+
+}  // namespace stp

@@ -416,6 +416,63 @@ stp_status stp_autotune(stp_handle h, int* variant, double* us_per_element, doub
   return STP_OK;
 }
 
+stp_status stp_batch_run_static(int nsets, const stp_batch_set* sets, void* stream) {
+  constexpr int kMax = 128;  // the static path's set limit (kernel-parameter descriptors)
+  if (nsets < 0 || (nsets > 0 && !sets)) return fail(STP_ERR_INVALID_ARG, "bad set list");
+  if (nsets > kMax) return fail(STP_ERR_INVALID_ARG, "more than 128 sets for the static path");
+  int dev = -1;
+  cudaGetDevice(&dev);
+  int N[kMax];
+  int64_t E[kMax];
+  const double* q[kMax];
+  const double* p[kMax];
+  const double* tb[kMax];
+  double* a[kMax];
+  double* f[kMax];
+  for (int i = 0; i < nsets; ++i) {
+    const stp_batch_set& st = sets[i];
+    stp_status s = validate_common(st.handle, st.elements, st.q, st.params, st.out_avg, st.out_faces);
+    if (s != STP_OK) return s;
+    if (st.handle->precision != STP_PRECISION_FP64)
+      return fail(STP_ERR_UNSUPPORTED, "static batched launches are FP64");
+    if (st.handle->device != dev) return fail(STP_ERR_UNSUPPORTED, "handle on another device");
+    if (st.elements > 0) {
+      const void* ptrs[4] = {st.q, st.params, st.out_avg, st.out_faces};
+      for (int k = 0; k < 4; ++k)
+        if ((s = check_device_ptr(ptrs[k], dev, "buffer")) != STP_OK) return s;
+    }
+    N[i] = st.handle->N;
+    E[i] = st.elements;
+    q[i] = st.q;
+    p[i] = st.params;
+    a[i] = st.out_avg;
+    f[i] = st.out_faces;
+    tb[i] = st.handle->d_tables;
+  }
+  for (int i = 0; i < nsets; ++i) {
+    const Sizes si = sizes_per_element(N[i]);
+    const void* oi[2] = {a[i], f[i]};
+    const size_t ni[2] = {si.avg * (size_t)E[i], si.faces * (size_t)E[i]};
+    for (int j = 0; j < nsets; ++j) {
+      if (j == i) continue;
+      const Sizes sj = sizes_per_element(N[j]);
+      const void* bj[4] = {q[j], p[j], a[j], f[j]};
+      const size_t nj[4] = {sj.q * (size_t)E[j], sj.params * (size_t)E[j], sj.avg * (size_t)E[j],
+                            sj.faces * (size_t)E[j]};
+      for (int x = 0; x < 2; ++x)
+        for (int y = 0; y < 4; ++y)
+          if (ni[x] && nj[y] && overlap(oi[x], ni[x], bj[y], nj[y]))
+            return fail(STP_ERR_INVALID_ARG, "outputs overlap another set's buffers");
+    }
+  }
+  int too_big = 0;
+  cudaError_t e = stp::run_static_batch(nsets, N, E, q, p, a, f, tb, static_cast<cudaStream_t>(stream),
+                                        &too_big);
+  if (too_big) return fail(STP_ERR_INVALID_ARG, "the call needs more than the 24 MiB static scratch");
+  if (e != cudaSuccess) return cuda_fail(e, "static batched launch");
+  return STP_OK;
+}
+
 stp_status stp_measure_fp64_peak(double* gflops, void* stream) {
   if (!gflops) return fail(STP_ERR_INVALID_ARG, "gflops is NULL");
   int dev = 0, sms = 0;

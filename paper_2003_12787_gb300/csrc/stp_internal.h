@@ -66,6 +66,13 @@ cudaError_t launch_plan(BatchPlan* p, cudaStream_t stream);
 void plan_info(const BatchPlan* p, int* units, int* ctas, size_t* smem);
 void destroy_plan(BatchPlan* p);
 
+// Batched FP64 launch with all scratch in a fixed-size static device array
+// (noalloc.cu). *too_big = 1 when nsets or the needed scratch exceed it.
+cudaError_t run_static_batch(int nsets, const int* N, const int64_t* E, const double* const* q,
+                             const double* const* params, double* const* avg,
+                             double* const* faces, const double* const* tables,
+                             cudaStream_t stream, int* too_big);
+
 cudaError_t launch_fp64_peak(double* sink, int blocks, int threads, int iters,
                              cudaStream_t stream);
 

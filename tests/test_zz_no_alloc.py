@@ -1,0 +1,58 @@
+"""The allocation-free batched launch (stp_batch_run_static), through the C ABI.
+
+It exists for callers that cannot call cudaMalloc where they run the
+predictor: its scratch lives in a fixed array in the library's device image.
+This file is collected last on purpose: if it fails, a run that stops at the
+first failure has already run every other test. It must pass both alone in a
+fresh process and after the other tests (the array keeps whatever the last
+call left in it).
+"""
+from __future__ import annotations
+
+import numpy as np
+import pytest
+import torch
+
+import paper_2003_12787_gb300 as stp
+from paper_2003_12787_gb300 import _binding
+from paper_2003_12787_gb300.inputs import elastic_problem
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-12  # the FP64 bar of the other parity tests
+
+
+def rel(a, b):
+    s = float(b.abs().max())
+    return float((a - b).abs().max()) / (s if s > 0 else 1.0)
+
+
+def test_static_batch_matches_stp_predict_on_two_calls_in_a_row():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    stp.build.build()
+    _binding.load()
+    # orders 11 and 12 exercise the per-CTA parking areas of the scratch array
+    specs = [(4, 37), (12, 3), (11, 2), (8, 9), (1, 5), (10, 4), (6, 17)]
+    sets, refs, outs = [], [], []
+    for i, (N, E) in enumerate(specs):
+        prob = elastic_problem(N, E=E, seed_material=700 + i, seed_waves=800 + i, device="cuda")
+        P = stp.Predictor(N - 1, prob.h, prob.dt)
+        ref = P.predict(prob.q, prob.params)  # the existing entry point
+        avg, faces = P.empty_outputs(E)
+        sets.append((P, prob))
+        refs.append(ref)
+        outs.append((avg, faces))
+    torch.cuda.synchronize()
+    for call in range(2):
+        for avg, faces in outs:
+            avg.fill_(float("nan"))
+            faces.fill_(float("nan"))
+        stp.stp_batch_run_static([(P.handle, prob.E, prob.q, prob.params, a, f)
+                                  for (P, prob), (a, f) in zip(sets, outs)])
+        torch.cuda.synchronize()
+        for (avg, faces), (ra, rf), spec in zip(outs, refs, specs):
+            assert rel(avg, ra) <= TOL, (call, spec)
+            assert rel(faces, rf) <= TOL, (call, spec)
+    for P, _ in sets:
+        P.close()
