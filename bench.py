@@ -284,6 +284,58 @@ def batched_measurement(stp, torch, args):
     return out
 
 
+def served_measurement(stp, torch, args):
+    """The served workload: 256 simulations (orders 3-9, N=4..10, element
+    counts log-uniform in [64, args.served_emax], seed 1005, state and
+    material generated on the GPU), a device pool of args.served_budget_gb,
+    Poisson arrivals at args.served_rate req/s (seed 1006), each picking a
+    simulation uniformly. args.served_warmup requests are replayed first; then
+    args.served_requests are timed. Latency = completion seen by the scheduler
+    minus arrival."""
+    from paper_2003_12787_gb300.inputs import elastic_problem, served_arrivals, served_recipe
+    recipe = served_recipe(e_max=args.served_emax)
+    budget = int(args.served_budget_gb * (1 << 30))
+    srv = stp.Server(budget, slots=args.served_slots)
+    preds = []
+    for r in recipe:
+        prob = elastic_problem(r["N"], grid=r["grid"], E=r["E"], h=r["h"],
+                               seed_material=r["seed_material"], seed_waves=r["seed_waves"],
+                               device="cuda")
+        P = stp.Predictor(r["N"] - 1, prob.h, prob.dt)
+        srv.add_sim(P, prob.q, prob.params)
+        preds.append(P)
+        del prob
+    n_w, n_m = args.served_warmup, args.served_requests
+    t, ids = served_arrivals(n_w + n_m, rate=args.served_rate, n_sims=len(recipe))
+    srv.run_trace(t[:n_w] - t[0], ids[:n_w])
+    before = srv.stats()
+    t_m = t[n_w:] - t[n_w]
+    lat, wall = srv.run_trace(t_m, ids[n_w:])
+    after = srv.stats()
+    E = np.array([r["E"] for r in recipe])
+    elems = int(E[ids[n_w:]].sum())
+    launches = after["launches"] - before["launches"]
+    out = {"workload": "256 simulations, orders 3-9 (N=4..10), "
+                       f"64-{args.served_emax} elements each (log-uniform, seed 1005), "
+                       f"Poisson {args.served_rate:g} req/s (seed 1006), one FP64 STP step per request",
+           "hbm_budget_gb": args.served_budget_gb, "slots": args.served_slots,
+           "requests": n_m, "warmup_requests": n_w,
+           "total_state_gb": float(sum(8 * r["E"] * (21 * r["N"] ** 3 + 54 * r["N"] ** 2)
+                                       for r in recipe) / 2 ** 30),
+           "p50_ms": float(np.percentile(lat, 50) * 1e3), "p99_ms": float(np.percentile(lat, 99) * 1e3),
+           "mean_ms": float(lat.mean() * 1e3), "wall_s": wall,
+           "throughput_req_s": n_m / wall, "element_updates_per_s": elems / wall,
+           "offered_req_s": n_m / float(t_m[-1]) if n_m > 1 else None,
+           "launches": launches, "mean_batch": n_m / max(1, launches),
+           "admissions": after["admissions"] - before["admissions"],
+           "evictions": after["evictions"] - before["evictions"],
+           "pool_peak_gb": after["pool_bytes_peak"] / 2 ** 30}
+    srv.close()
+    for P in preds:
+        P.close()
+    return out
+
+
 def run_gpu(args):
     import torch
     world, rank, local = dist_env()
@@ -373,6 +425,9 @@ def run_gpu(args):
     batched = None
     if rank == 0 and world == 1 and not args.no_batched:
         batched = batched_measurement(stp, torch, args)
+    served = None
+    if rank == 0 and world == 1 and not args.no_served:
+        served = served_measurement(stp, torch, args)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -411,7 +466,7 @@ def run_gpu(args):
             "latency_ms": {"p50": statistics.median(step_ms), "p99": p99,
                            "min": min(step_ms), "max": max(step_ms)},
             "e2e": e2e, "cpu_baseline": cpu, "clocks": clocks, "mixed": mixed,
-            "batched": batched,
+            "batched": batched, "served": served,
             "gpu_launches": args.steps, "parity_max_rel_sampled": parity,
         }
         print(json.dumps(line), flush=True)
@@ -474,6 +529,13 @@ def main():
     ap.add_argument("--no-batched", action="store_true",
                     help="skip the batched 64-set workload")
     ap.add_argument("--batch-steps", type=int, default=3)
+    ap.add_argument("--no-served", action="store_true", help="skip the served workload")
+    ap.add_argument("--served-rate", type=float, default=2000.0)
+    ap.add_argument("--served-requests", type=int, default=2000)
+    ap.add_argument("--served-warmup", type=int, default=200)
+    ap.add_argument("--served-emax", type=int, default=2048)
+    ap.add_argument("--served-budget-gb", type=float, default=4.0)
+    ap.add_argument("--served-slots", type=int, default=3)
     ap.add_argument("--precision", default="fp64",
                     choices=["fp64", "bf16x2", "bf16x3", "fp16x2", "fp16x3"],
                     help="arithmetic of the timed workload (default fp64)")

@@ -217,6 +217,65 @@ stp_status stp_autotune(stp_handle h, int* variant, double* us_per_element,
  */
 stp_status stp_batch_run_static(int nsets, const stp_batch_set* sets, void* stream);
 
+/*
+ * Served predictor: a continuously batched request loop over many independent
+ * simulations (each an element set with its own order, size and material),
+ * whose state stays on the device. A request advances one simulation by one
+ * STP step; q_{n+1} := avg_n stands in for the corrector (outside the STP),
+ * implemented as a swap of two state buffers. Requests of one simulation are
+ * served in order, one at a time.
+ *
+ * The server owns one device pool of hbm_budget_bytes (the HBM budget) and
+ * `slots` in-flight batches (each a stream, an event and 24 MiB of scratch).
+ * Its scheduler retires finished batches, admits ready simulations into the
+ * pool (first fit; when full, idle simulations are evicted least recently
+ * used first and their state copied back to pinned host memory), and launches
+ * up to 128 ready resident simulations as one persistent batched FP64 launch
+ * per free slot, so requests that arrive while others run join the next
+ * launch and launches on different slots overlap on the GPU. The scheduler
+ * runs on the calling thread (stp_server_progress / _drain / _run_trace);
+ * a server is not thread-safe.
+ */
+typedef struct stp_server_s* stp_server;
+
+stp_status stp_server_create(int64_t hbm_budget_bytes, int slots, stp_server* out);
+
+/* Register a simulation: the FP64 handle gives its order, dx and dt; q0 and
+ * params ([E][N][N][N][9], [E][N][N][N][3], both host or both device) are
+ * copied into server-owned pinned host memory. *sim_id = 0, 1, ... in order.
+ * STP_ERR_INVALID_ARG if its footprint (2 states + params + faces) exceeds the
+ * budget. The handle must outlive the server. */
+stp_status stp_server_add_sim(stp_server s, stp_handle h, int64_t elements, const double* q0,
+                              const double* params, int* sim_id);
+
+/* Queue one step of a simulation (arrival time = now). */
+stp_status stp_server_submit(stp_server s, int sim_id);
+
+/* One scheduler pass (non-blocking); *completed = requests retired in it. */
+stp_status stp_server_progress(stp_server s, int* completed);
+
+/* Run the scheduler until every queued request has completed. */
+stp_status stp_server_drain(stp_server s);
+
+/* Replay a trace in real time: request i of simulation sim_ids[i] arrives
+ * t_arrival[i] seconds (sorted) after the call starts. latency[i] receives
+ * completion - arrival in seconds (completion = when the scheduler saw the
+ * launch finish), *wall_seconds the duration of the replay. */
+stp_status stp_server_run_trace(stp_server s, int64_t n, const double* t_arrival, const int* sim_ids,
+                                double* latency, double* wall_seconds);
+
+/* Current state q_n and the faces of the last completed step of a simulation
+ * (host buffers, may be NULL), and its number of completed steps. Drains. */
+stp_status stp_server_read(stp_server s, int sim_id, double* q_host, double* faces_host,
+                           int64_t* steps);
+
+/* stats[0..7]: completed requests, launches, admissions, evictions, largest
+ * launch (simulations), requests launched, pool bytes in use, peak bytes. */
+stp_status stp_server_stats(stp_server s, int64_t* stats);
+
+/* Finish outstanding work and free the server. NULL is a no-op. */
+stp_status stp_server_destroy(stp_server s);
+
 /* Release the handle's device tables and buffers. NULL is a no-op (STP_OK). */
 stp_status stp_destroy(stp_handle h);
 

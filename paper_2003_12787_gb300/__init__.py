@@ -13,4 +13,7 @@ from ._binding import (PRECISIONS, STPError, stp_create, stp_destroy,  # noqa: F
                        stp_reference_tables, stp_set_precision, stp_status_string)
 from ._binding import (stp_autotune, stp_batch_create, stp_batch_destroy,  # noqa: F401
                        stp_batch_info, stp_batch_launch, stp_batch_run_static)
-from .predictor import Batch, Predictor  # noqa: F401
+from ._binding import (stp_server_add_sim, stp_server_create, stp_server_destroy,  # noqa: F401
+                       stp_server_drain, stp_server_progress, stp_server_read,
+                       stp_server_run_trace, stp_server_stats, stp_server_submit)
+from .predictor import Batch, Predictor, Server  # noqa: F401

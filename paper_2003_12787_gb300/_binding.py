@@ -72,6 +72,18 @@ def load():
                                      ctypes.POINTER(dbl)]
         lib.stp_batch_run_static.argtypes = [ctypes.c_int, vp, vp]
         lib.stp_batch_run_static.restype = ctypes.c_int
+        srv = {"stp_server_create": [i64, ctypes.c_int, ctypes.POINTER(vp)],
+               "stp_server_add_sim": [vp, vp, i64, vp, vp, ctypes.POINTER(ctypes.c_int)],
+               "stp_server_submit": [vp, ctypes.c_int],
+               "stp_server_progress": [vp, ctypes.POINTER(ctypes.c_int)],
+               "stp_server_drain": [vp],
+               "stp_server_run_trace": [vp, i64, vp, vp, vp, ctypes.POINTER(dbl)],
+               "stp_server_read": [vp, ctypes.c_int, vp, vp, ctypes.POINTER(i64)],
+               "stp_server_stats": [vp, vp],
+               "stp_server_destroy": [vp]}
+        for name, args in srv.items():
+            getattr(lib, name).argtypes = args
+            getattr(lib, name).restype = ctypes.c_int
         for name in ("stp_create", "stp_predict", "stp_predict_host", "stp_destroy",
                      "stp_reference_tables", "stp_measure_fp64_peak", "stp_set_precision",
                      "stp_device_status", "stp_batch_create", "stp_batch_launch",
@@ -218,3 +230,58 @@ def stp_batch_run_static(sets, stream=None) -> None:
         arr[i] = BatchSet(h, E, _ptr(q), _ptr(p), _ptr(a), _ptr(f))
     _check(load().stp_batch_run_static(len(sets), ctypes.cast(arr, ctypes.c_void_p), _stream(stream)),
            "stp_batch_run_static")
+
+
+def stp_server_create(hbm_budget_bytes: int, slots: int = 3) -> int:
+    h = ctypes.c_void_p()
+    _check(load().stp_server_create(int(hbm_budget_bytes), int(slots), ctypes.byref(h)),
+           "stp_server_create")
+    return h.value
+
+
+def stp_server_add_sim(srv: int, handle: int, elements: int, q0, params) -> int:
+    i = ctypes.c_int()
+    _check(load().stp_server_add_sim(srv, handle, elements, _ptr(q0), _ptr(params), ctypes.byref(i)),
+           "stp_server_add_sim")
+    return i.value
+
+
+def stp_server_submit(srv: int, sim_id: int) -> None:
+    _check(load().stp_server_submit(srv, sim_id), "stp_server_submit")
+
+
+def stp_server_progress(srv: int) -> int:
+    n = ctypes.c_int()
+    _check(load().stp_server_progress(srv, ctypes.byref(n)), "stp_server_progress")
+    return n.value
+
+
+def stp_server_drain(srv: int) -> None:
+    _check(load().stp_server_drain(srv), "stp_server_drain")
+
+
+def stp_server_run_trace(srv: int, t_arrival, sim_ids, latency) -> float:
+    """t_arrival float64[n] (sorted, seconds), sim_ids int32[n], latency float64[n] out."""
+    wall = ctypes.c_double()
+    _check(load().stp_server_run_trace(srv, len(t_arrival), _ptr(t_arrival), _ptr(sim_ids),
+                                       _ptr(latency), ctypes.byref(wall)), "stp_server_run_trace")
+    return wall.value
+
+
+def stp_server_read(srv: int, sim_id: int, q_host=None, faces_host=None) -> int:
+    steps = ctypes.c_int64()
+    _check(load().stp_server_read(srv, sim_id, _ptr(q_host), _ptr(faces_host), ctypes.byref(steps)),
+           "stp_server_read")
+    return steps.value
+
+
+def stp_server_stats(srv: int) -> dict:
+    arr = (ctypes.c_int64 * 8)()
+    _check(load().stp_server_stats(srv, ctypes.cast(arr, ctypes.c_void_p)), "stp_server_stats")
+    keys = ["completed", "launches", "admissions", "evictions", "max_batch", "requests_launched",
+            "pool_bytes_in_use", "pool_bytes_peak"]
+    return dict(zip(keys, list(arr)))
+
+
+def stp_server_destroy(srv: int | None) -> None:
+    _check(load().stp_server_destroy(srv), "stp_server_destroy")

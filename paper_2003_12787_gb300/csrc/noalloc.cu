@@ -137,19 +137,20 @@ cudaError_t scratch_address(int dev, unsigned char** out) {
 size_t static_scratch_bytes() { return kStaticScratchBytes; }
 int static_max_sets() { return kStaticMaxSets; }
 
-// sets_N/E/...: validated by the caller. Returns cudaErrorInvalidValue with
-// *too_big = 1 when the call needs more scratch than the array holds.
-cudaError_t run_static_batch(int nsets, const int* N, const int64_t* E, const double* const* q,
-                             const double* const* params, double* const* avg,
-                             double* const* faces, const double* const* tables,
-                             cudaStream_t stream, int* too_big) {
+// One persistent launch over up to 128 sets described in kernel parameters,
+// with the given scratch (work counter + parking areas). Inputs validated by
+// the caller. Returns cudaErrorInvalidValue with *too_big = 1 when nsets or
+// the needed scratch exceed the limits.
+cudaError_t launch_param_batch(int nsets, const int* N, const int64_t* E, const double* const* q,
+                               const double* const* params, double* const* avg,
+                               double* const* faces, const double* const* tables,
+                               unsigned char* scratch, size_t scratch_bytes, cudaStream_t stream,
+                               int* too_big) {
   *too_big = 0;
   if (nsets < 0 || nsets > kStaticMaxSets) { *too_big = 1; return cudaErrorInvalidValue; }
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
-  unsigned char* scratch = nullptr;
-  if ((e = scratch_address(dev, &scratch)) != cudaSuccess) return e;
   StaticBatch b;
   b.nsets = nsets;
   int64_t units = 0;
@@ -176,13 +177,33 @@ cudaError_t run_static_batch(int nsets, const int* N, const int64_t* E, const do
     return e;
   int64_t ctas = (int64_t)std::max(1, per_sm) * sms;
   ctas = std::min<int64_t>(ctas, units);
-  if (kCounterBytes + (size_t)ctas * park > kStaticScratchBytes) { *too_big = 1; return cudaErrorInvalidValue; }
+  if (kCounterBytes + (size_t)ctas * park > scratch_bytes) { *too_big = 1; return cudaErrorInvalidValue; }
   // the counter must start at zero; the parking areas need no clearing (each
   // parked value is written before it is read within the same work unit)
   if ((e = cudaMemsetAsync(scratch, 0, sizeof(unsigned long long), stream)) != cudaSuccess) return e;
   static_batch_kernel<<<(unsigned)ctas, kStaticThreads, smem, stream>>>(
       b, scratch, (int64_t)(park / sizeof(double)));
   return cudaGetLastError();
+}
+
+}  // namespace stp
+
+namespace stp {
+
+// sets_N/E/...: validated by the caller. Returns cudaErrorInvalidValue with
+// *too_big = 1 when the call needs more scratch than the static array holds.
+cudaError_t run_static_batch(int nsets, const int* N, const int64_t* E, const double* const* q,
+                             const double* const* params, double* const* avg,
+                             double* const* faces, const double* const* tables,
+                             cudaStream_t stream, int* too_big) {
+  *too_big = 0;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  unsigned char* scratch = nullptr;
+  if ((e = scratch_address(dev, &scratch)) != cudaSuccess) return e;
+  return launch_param_batch(nsets, N, E, q, params, avg, faces, tables, scratch,
+                            kStaticScratchBytes, stream, too_big);
 }
 
 }  // namespace stp

@@ -1,0 +1,462 @@
+// Served Space-Time Predictor: a continuously batched request loop over many
+// independent simulations whose state stays resident on the device.
+//
+// Every simulation owns, inside one device pool of a fixed HBM budget, two
+// state buffers (q_n and the next average), its material field and its face
+// projections. A request advances one simulation by one STP step; the
+// corrector is outside the method's hot path, so q_{n+1} := avg_n stands in
+// for it and is a swap of the two state buffers' roles (no copy). Requests of
+// one simulation run one after another.
+//
+// The scheduler (progress) repeatedly:
+//   1. retires finished batches (event query per in-flight slot): records
+//      completion times, swaps the state roles, re-queues simulations that
+//      have more requests;
+//   2. admits ready simulations into the pool (first-fit sub-allocation);
+//      when the budget is exhausted it evicts idle simulations, least
+//      recently used first, copying their state back to pinned host memory;
+//   3. launches up to 128 ready, resident simulations as ONE persistent
+//      batched FP64 launch on a free slot (its own stream and scratch).
+// New requests therefore join the next launch while earlier launches are
+// still on the GPU, and launches on different slots overlap on the device.
+#include <algorithm>
+#include <chrono>
+#include <cstring>
+#include <deque>
+#include <map>
+#include <mutex>
+#include <new>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "stp_internal.h"
+
+namespace stp {
+namespace {
+
+using Clock = std::chrono::steady_clock;
+
+constexpr size_t kAlign = 256;
+
+size_t align_up(size_t x) { return (x + kAlign - 1) & ~(kAlign - 1); }
+
+// First-fit sub-allocator over [0, size) with coalescing.
+class Pool {
+ public:
+  void reset(size_t size) {
+    free_.clear();
+    if (size) free_[0] = size;
+    used_ = 0;
+  }
+  bool alloc(size_t n, size_t* off) {
+    n = align_up(n);
+    for (auto it = free_.begin(); it != free_.end(); ++it) {
+      if (it->second >= n) {
+        *off = it->first;
+        const size_t rest = it->second - n;
+        const size_t start = it->first + n;
+        free_.erase(it);
+        if (rest) free_[start] = rest;
+        used_ += n;
+        return true;
+      }
+    }
+    return false;
+  }
+  void release(size_t off, size_t n) {
+    n = align_up(n);
+    used_ -= n;
+    auto it = free_.emplace(off, n).first;
+    auto next = std::next(it);
+    if (next != free_.end() && it->first + it->second == next->first) {
+      it->second += next->second;
+      free_.erase(next);
+    }
+    if (it != free_.begin()) {
+      auto prev = std::prev(it);
+      if (prev->first + prev->second == it->first) {
+        prev->second += it->second;
+        free_.erase(it);
+      }
+    }
+  }
+  size_t used() const { return used_; }
+
+ private:
+  std::map<size_t, size_t> free_;
+  size_t used_ = 0;
+};
+
+struct Request {
+  int64_t id;      // index in the caller's trace (or submit order)
+  double t_arrival;  // seconds on the server clock
+};
+
+struct Sim {
+  stp_handle handle = nullptr;
+  int N = 0;
+  int64_t E = 0;
+  size_t bytes_state = 0, bytes_params = 0, bytes_faces = 0;
+  double* host_q = nullptr;       // pinned: state while evicted
+  double* host_params = nullptr;  // pinned
+  double* host_faces = nullptr;   // pinned: last faces while evicted
+  bool resident = false;
+  size_t off = 0;  // pool offset of [state0 | state1 | params | faces]
+  int cur = 0;     // which state buffer holds q_n
+  bool busy = false, queued = false, have_faces = false;
+  int64_t last_used = 0, steps = 0;
+  std::deque<Request> pending;
+  size_t footprint() const { return 2 * align_up(bytes_state) + align_up(bytes_params) + align_up(bytes_faces); }
+};
+
+struct Slot {
+  cudaStream_t stream = nullptr;
+  cudaEvent_t done = nullptr;
+  unsigned char* scratch = nullptr;
+  std::vector<int> sims;
+  bool busy = false;
+};
+
+}  // namespace
+
+struct Server {
+  int device = -1;
+  size_t budget = 0;
+  unsigned char* pool_base = nullptr;
+  Pool pool;
+  std::vector<Sim> sims;
+  std::vector<Slot> slots;
+  std::deque<int> ready;  // simulations with a request, not running, FIFO
+  cudaStream_t copy_stream = nullptr;
+  cudaEvent_t copy_done = nullptr;
+  Clock::time_point t0 = Clock::now();
+  int64_t tick = 0;
+  // statistics
+  int64_t completed = 0, batches = 0, admissions = 0, evictions = 0, max_batch = 0,
+          batched_requests = 0, next_id = 0;
+  size_t peak_used = 0;
+  // completion records of the current trace: id -> completion time
+  std::vector<double>* completion = nullptr;
+  std::mutex mu;
+
+  double now() const { return std::chrono::duration<double>(Clock::now() - t0).count(); }
+
+  double* state(const Sim& s, int which) const {
+    return reinterpret_cast<double*>(pool_base + s.off + which * align_up(s.bytes_state));
+  }
+  double* params(const Sim& s) const {
+    return reinterpret_cast<double*>(pool_base + s.off + 2 * align_up(s.bytes_state));
+  }
+  double* faces(const Sim& s) const {
+    return reinterpret_cast<double*>(pool_base + s.off + 2 * align_up(s.bytes_state) + align_up(s.bytes_params));
+  }
+
+  cudaError_t evict(int i) {
+    Sim& s = sims[i];
+    cudaError_t e = cudaMemcpyAsync(s.host_q, state(s, s.cur), s.bytes_state, cudaMemcpyDeviceToHost, copy_stream);
+    if (e == cudaSuccess && s.have_faces)
+      e = cudaMemcpyAsync(s.host_faces, faces(s), s.bytes_faces, cudaMemcpyDeviceToHost, copy_stream);
+    if (e != cudaSuccess) return e;
+    pool.release(s.off, s.footprint());
+    s.resident = false;
+    s.cur = 0;
+    ++evictions;
+    return cudaSuccess;
+  }
+
+  // Make simulation i resident; returns false if the budget cannot hold it
+  // even after evicting every idle simulation outside `protect`.
+  bool admit(int i, const std::vector<char>& protect, bool* copied, cudaError_t* err) {
+    Sim& s = sims[i];
+    if (s.resident) return true;
+    size_t off = 0;
+    while (!pool.alloc(s.footprint(), &off)) {
+      // least recently used idle resident simulation, preferring ones without requests
+      int victim = -1;
+      for (int pass = 0; pass < 2 && victim < 0; ++pass)
+        for (int j = 0; j < (int)sims.size(); ++j) {
+          const Sim& c = sims[j];
+          if (!c.resident || c.busy || protect[j] || j == i) continue;
+          if (pass == 0 && !c.pending.empty()) continue;
+          if (victim < 0 || c.last_used < sims[victim].last_used) victim = j;
+        }
+      if (victim < 0) return false;
+      if ((*err = evict(victim)) != cudaSuccess) return false;
+    }
+    s.off = off;
+    s.resident = true;
+    s.cur = 0;
+    *err = cudaMemcpyAsync(state(s, 0), s.host_q, s.bytes_state, cudaMemcpyHostToDevice, copy_stream);
+    if (*err == cudaSuccess)
+      *err = cudaMemcpyAsync(params(s), s.host_params, s.bytes_params, cudaMemcpyHostToDevice, copy_stream);
+    if (*err == cudaSuccess && s.have_faces)
+      *err = cudaMemcpyAsync(faces(s), s.host_faces, s.bytes_faces, cudaMemcpyHostToDevice, copy_stream);
+    *copied = true;
+    ++admissions;
+    peak_used = std::max(peak_used, pool.used());
+    return *err == cudaSuccess;
+  }
+
+  void submit(int i, int64_t id, double t_arrival) {
+    Sim& s = sims[i];
+    s.pending.push_back(Request{id, t_arrival});
+    if (!s.busy && !s.queued) {
+      ready.push_back(i);
+      s.queued = true;
+    }
+  }
+
+  // One scheduler pass. Returns the number of requests completed in it.
+  cudaError_t progress(int* n_completed) {
+    int done_now = 0;
+    cudaError_t e;
+    // 1. retire finished launches
+    for (Slot& sl : slots) {
+      if (!sl.busy) continue;
+      e = cudaEventQuery(sl.done);
+      if (e == cudaErrorNotReady) continue;
+      if (e != cudaSuccess) return e;
+      const double t = now();
+      for (int i : sl.sims) {
+        Sim& s = sims[i];
+        const Request r = s.pending.front();
+        s.pending.pop_front();
+        if (completion && r.id >= 0 && r.id < (int64_t)completion->size()) (*completion)[r.id] = t;
+        s.cur ^= 1;  // q_{n+1} := avg_n
+        s.busy = false;
+        s.have_faces = true;
+        s.last_used = ++tick;
+        ++s.steps;
+        ++done_now;
+        if (!s.pending.empty() && !s.queued) {
+          ready.push_back(i);
+          s.queued = true;
+        }
+      }
+      sl.sims.clear();
+      sl.busy = false;
+    }
+    completed += done_now;
+    if (n_completed) *n_completed = done_now;
+    // 2./3. admit and launch on every free slot while work is ready
+    for (Slot& sl : slots) {
+      if (sl.busy || ready.empty()) continue;
+      std::vector<char> protect(sims.size(), 0);
+      std::vector<int> batch;
+      bool copied = false;
+      std::deque<int> keep;
+      while (!ready.empty() && (int)batch.size() < static_max_sets()) {
+        const int i = ready.front();
+        ready.pop_front();
+        cudaError_t ae = cudaSuccess;
+        if (admit(i, protect, &copied, &ae)) {
+          protect[i] = 1;
+          batch.push_back(i);
+        } else {
+          if (ae != cudaSuccess) return ae;
+          keep.push_back(i);  // does not fit next to this batch: wait
+          break;
+        }
+      }
+      for (auto it = keep.rbegin(); it != keep.rend(); ++it) ready.push_front(*it);
+      if (batch.empty()) break;
+      if (copied) {
+        if ((e = cudaEventRecord(copy_done, copy_stream)) != cudaSuccess) return e;
+        if ((e = cudaStreamWaitEvent(sl.stream, copy_done, 0)) != cudaSuccess) return e;
+      }
+      const int n = (int)batch.size();
+      std::vector<int> N(n);
+      std::vector<int64_t> E(n);
+      std::vector<const double*> q(n), p(n), tb(n);
+      std::vector<double*> a(n), f(n);
+      for (int k = 0; k < n; ++k) {
+        Sim& s = sims[batch[k]];
+        N[k] = s.N;
+        E[k] = s.E;
+        q[k] = state(s, s.cur);
+        a[k] = state(s, s.cur ^ 1);
+        p[k] = params(s);
+        f[k] = faces(s);
+        tb[k] = stp_handle_tables(s.handle);
+        s.busy = true;
+        s.queued = false;
+      }
+      int too_big = 0;
+      e = launch_param_batch(n, N.data(), E.data(), q.data(), p.data(), a.data(), f.data(), tb.data(),
+                             sl.scratch, static_scratch_bytes(), sl.stream, &too_big);
+      if (e != cudaSuccess) return e;
+      if ((e = cudaEventRecord(sl.done, sl.stream)) != cudaSuccess) return e;
+      sl.sims = batch;
+      sl.busy = true;
+      ++batches;
+      batched_requests += n;
+      max_batch = std::max<int64_t>(max_batch, n);
+    }
+    return cudaSuccess;
+  }
+
+  bool idle() const {
+    if (!ready.empty()) return false;
+    for (const Slot& s : slots)
+      if (s.busy) return false;
+    return true;
+  }
+
+  void release() {
+    for (Slot& s : slots) {
+      if (s.stream) cudaStreamSynchronize(s.stream);
+      cudaFree(s.scratch);
+      if (s.done) cudaEventDestroy(s.done);
+      if (s.stream) cudaStreamDestroy(s.stream);
+    }
+    if (copy_stream) cudaStreamSynchronize(copy_stream);
+    if (copy_done) cudaEventDestroy(copy_done);
+    if (copy_stream) cudaStreamDestroy(copy_stream);
+    for (Sim& s : sims) {
+      cudaFreeHost(s.host_q);
+      cudaFreeHost(s.host_params);
+      cudaFreeHost(s.host_faces);
+    }
+    cudaFree(pool_base);
+  }
+};
+
+cudaError_t server_create(int64_t budget, int nslots, Server** out) {
+  *out = nullptr;
+  Server* s = new (std::nothrow) Server;
+  if (!s) return cudaErrorMemoryAllocation;
+  cudaGetDevice(&s->device);
+  s->budget = (size_t)budget;
+  cudaError_t e = cudaMalloc(&s->pool_base, std::max<size_t>(s->budget, kAlign));
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->copy_stream, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->copy_done, cudaEventDisableTiming);
+  s->slots.resize(nslots);
+  for (Slot& sl : s->slots) {
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&sl.stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&sl.done, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaMalloc(&sl.scratch, static_scratch_bytes());
+  }
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    s->release();
+    delete s;
+    return e;
+  }
+  s->pool.reset(s->budget);
+  *out = s;
+  return cudaSuccess;
+}
+
+void server_destroy(Server* s) {
+  if (!s) return;
+  s->release();
+  delete s;
+}
+
+cudaError_t server_add_sim(Server* s, stp_handle h, int N, int64_t E, const double* q0,
+                           const double* params, bool device_src, int* id, bool* too_big) {
+  *too_big = false;
+  Sim sim;
+  sim.handle = h;
+  sim.N = N;
+  sim.E = E;
+  const size_t n3 = (size_t)N * N * N;
+  sim.bytes_state = (size_t)E * n3 * 9 * 8;
+  sim.bytes_params = (size_t)E * n3 * 3 * 8;
+  sim.bytes_faces = (size_t)E * N * N * 54 * 8;
+  if (sim.footprint() > s->budget) {
+    *too_big = true;
+    return cudaErrorInvalidValue;
+  }
+  cudaError_t e = cudaMallocHost(&sim.host_q, std::max<size_t>(sim.bytes_state, 8));
+  if (e == cudaSuccess) e = cudaMallocHost(&sim.host_params, std::max<size_t>(sim.bytes_params, 8));
+  if (e == cudaSuccess) e = cudaMallocHost(&sim.host_faces, std::max<size_t>(sim.bytes_faces, 8));
+  const cudaMemcpyKind kind = device_src ? cudaMemcpyDeviceToHost : cudaMemcpyHostToHost;
+  if (e == cudaSuccess) e = cudaMemcpy(sim.host_q, q0, sim.bytes_state, kind);
+  if (e == cudaSuccess) e = cudaMemcpy(sim.host_params, params, sim.bytes_params, kind);
+  if (e != cudaSuccess) {
+    cudaFreeHost(sim.host_q);
+    cudaFreeHost(sim.host_params);
+    cudaFreeHost(sim.host_faces);
+    return e;
+  }
+  *id = (int)s->sims.size();
+  s->sims.push_back(sim);
+  return cudaSuccess;
+}
+
+cudaError_t server_run_trace(Server* s, int64_t n, const double* t_arr, const int* sim_ids,
+                             double* latency, double* wall) {
+  std::vector<double> completion((size_t)n, -1.0);
+  s->completion = &completion;
+  s->t0 = Clock::now();
+  const int64_t start_completed = s->completed;
+  int64_t i = 0;
+  cudaError_t e = cudaSuccess;
+  while (s->completed - start_completed < n) {
+    const double t = s->now();
+    while (i < n && t_arr[i] <= t) {
+      s->submit(sim_ids[i], i, t_arr[i]);
+      ++i;
+    }
+    int done = 0;
+    if ((e = s->progress(&done)) != cudaSuccess) break;
+    if (done == 0 && s->idle() && i < n) {
+      // nothing in flight: wait for the next arrival without burning a core
+      const double wait = t_arr[i] - s->now();
+      if (wait > 2e-4) std::this_thread::sleep_for(std::chrono::duration<double>(wait - 1e-4));
+    }
+  }
+  if (wall) *wall = s->now();
+  s->completion = nullptr;
+  for (int64_t k = 0; k < n; ++k) latency[k] = completion[k] - t_arr[k];
+  return e;
+}
+
+cudaError_t server_drain(Server* s) {
+  cudaError_t e = cudaSuccess;
+  while (!s->idle())
+    if ((e = s->progress(nullptr)) != cudaSuccess) break;
+  return e;
+}
+
+cudaError_t server_read(Server* s, int id, double* q, double* faces, int64_t* steps) {
+  Sim& sim = s->sims[id];
+  cudaError_t e = server_drain(s);
+  if (e != cudaSuccess) return e;
+  if ((e = cudaStreamSynchronize(s->copy_stream)) != cudaSuccess) return e;
+  if (sim.resident) {
+    if (q && (e = cudaMemcpy(q, s->state(sim, sim.cur), sim.bytes_state, cudaMemcpyDeviceToHost)) != cudaSuccess)
+      return e;
+    if (faces && sim.have_faces &&
+        (e = cudaMemcpy(faces, s->faces(sim), sim.bytes_faces, cudaMemcpyDeviceToHost)) != cudaSuccess)
+      return e;
+  } else {
+    if (q) std::memcpy(q, sim.host_q, sim.bytes_state);
+    if (faces && sim.have_faces) std::memcpy(faces, sim.host_faces, sim.bytes_faces);
+  }
+  if (steps) *steps = sim.steps;
+  return cudaSuccess;
+}
+
+void server_stats(const Server* s, int64_t* out) {
+  out[0] = s->completed;
+  out[1] = s->batches;
+  out[2] = s->admissions;
+  out[3] = s->evictions;
+  out[4] = s->max_batch;
+  out[5] = s->batched_requests;
+  out[6] = (int64_t)s->pool.used();
+  out[7] = (int64_t)s->peak_used;
+}
+
+void server_submit(Server* s, int id) {
+  s->submit(id, -1, s->now());
+}
+
+cudaError_t server_progress(Server* s, int* done) { return s->progress(done); }
+
+int server_sims(const Server* s) { return (int)s->sims.size(); }
+
+}  // namespace stp

@@ -315,6 +315,14 @@ stp_status stp_device_status(stp_handle h, void* stream, unsigned int* flags) {
 
 }  // extern "C"
 
+namespace stp {
+const double* stp_handle_tables(stp_handle h) { return h->d_tables; }
+}  // namespace stp
+
+struct stp_server_s {
+  stp::Server* impl = nullptr;
+};
+
 struct stp_batch_s {
   stp::BatchPlan* plan = nullptr;
   int device = -1;
@@ -470,6 +478,101 @@ stp_status stp_batch_run_static(int nsets, const stp_batch_set* sets, void* stre
                                         &too_big);
   if (too_big) return fail(STP_ERR_INVALID_ARG, "the call needs more than the 24 MiB static scratch");
   if (e != cudaSuccess) return cuda_fail(e, "static batched launch");
+  return STP_OK;
+}
+
+stp_status stp_server_create(int64_t hbm_budget_bytes, int slots, stp_server* out) {
+  if (!out) return fail(STP_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  if (hbm_budget_bytes <= 0) return fail(STP_ERR_INVALID_ARG, "budget must be > 0");
+  if (slots < 1 || slots > 8) return fail(STP_ERR_INVALID_ARG, "slots must be in [1, 8]");
+  stp_server s = new (std::nothrow) stp_server_s;
+  if (!s) return fail(STP_ERR_OOM, "host allocation failed");
+  cudaError_t e = stp::server_create(hbm_budget_bytes, slots, &s->impl);
+  if (e != cudaSuccess) {
+    delete s;
+    if (e == cudaErrorMemoryAllocation) return fail(STP_ERR_OOM, "server pool allocation failed");
+    return cuda_fail(e, "server create");
+  }
+  *out = s;
+  return STP_OK;
+}
+
+stp_status stp_server_add_sim(stp_server s, stp_handle h, int64_t elements, const double* q0,
+                              const double* params, int* sim_id) {
+  if (!s || !s->impl || !h || !sim_id) return fail(STP_ERR_INVALID_ARG, "null argument");
+  if (elements <= 0 || !q0 || !params) return fail(STP_ERR_INVALID_ARG, "bad simulation buffers");
+  if (h->precision != STP_PRECISION_FP64) return fail(STP_ERR_UNSUPPORTED, "served steps are FP64");
+  cudaPointerAttributes aq, ap;
+  bool dq = false, dp = false;
+  if (cudaPointerGetAttributes(&aq, q0) == cudaSuccess)
+    dq = aq.type == cudaMemoryTypeDevice || aq.type == cudaMemoryTypeManaged;
+  cudaGetLastError();
+  if (cudaPointerGetAttributes(&ap, params) == cudaSuccess)
+    dp = ap.type == cudaMemoryTypeDevice || ap.type == cudaMemoryTypeManaged;
+  cudaGetLastError();
+  if (dq != dp) return fail(STP_ERR_INVALID_ARG, "q0 and params must both be host or both device");
+  bool too_big = false;
+  cudaError_t e = stp::server_add_sim(s->impl, h, h->N, elements, q0, params, dq, sim_id, &too_big);
+  if (too_big) return fail(STP_ERR_INVALID_ARG, "simulation does not fit the HBM budget");
+  if (e == cudaErrorMemoryAllocation) return fail(STP_ERR_OOM, "pinned host allocation failed");
+  if (e != cudaSuccess) return cuda_fail(e, "add simulation");
+  return STP_OK;
+}
+
+stp_status stp_server_submit(stp_server s, int sim_id) {
+  if (!s || !s->impl || sim_id < 0 || sim_id >= stp::server_sims(s->impl))
+    return fail(STP_ERR_INVALID_ARG, "bad server or simulation id");
+  stp::server_submit(s->impl, sim_id);
+  return STP_OK;
+}
+
+stp_status stp_server_progress(stp_server s, int* completed) {
+  if (!s || !s->impl) return fail(STP_ERR_INVALID_ARG, "invalid server");
+  cudaError_t e = stp::server_progress(s->impl, completed);
+  if (e != cudaSuccess) return cuda_fail(e, "server progress");
+  return STP_OK;
+}
+
+stp_status stp_server_drain(stp_server s) {
+  if (!s || !s->impl) return fail(STP_ERR_INVALID_ARG, "invalid server");
+  cudaError_t e = stp::server_drain(s->impl);
+  if (e != cudaSuccess) return cuda_fail(e, "server drain");
+  return STP_OK;
+}
+
+stp_status stp_server_run_trace(stp_server s, int64_t n, const double* t_arrival, const int* sim_ids,
+                                double* latency, double* wall_seconds) {
+  if (!s || !s->impl || n < 0 || (n > 0 && (!t_arrival || !sim_ids || !latency)))
+    return fail(STP_ERR_INVALID_ARG, "bad trace");
+  const int nsims = stp::server_sims(s->impl);
+  for (int64_t i = 0; i < n; ++i) {
+    if (sim_ids[i] < 0 || sim_ids[i] >= nsims) return fail(STP_ERR_INVALID_ARG, "bad simulation id in trace");
+    if (i > 0 && t_arrival[i] < t_arrival[i - 1]) return fail(STP_ERR_INVALID_ARG, "arrivals must be sorted");
+  }
+  cudaError_t e = stp::server_run_trace(s->impl, n, t_arrival, sim_ids, latency, wall_seconds);
+  if (e != cudaSuccess) return cuda_fail(e, "server trace");
+  return STP_OK;
+}
+
+stp_status stp_server_read(stp_server s, int sim_id, double* q_host, double* faces_host, int64_t* steps) {
+  if (!s || !s->impl || sim_id < 0 || sim_id >= stp::server_sims(s->impl))
+    return fail(STP_ERR_INVALID_ARG, "bad server or simulation id");
+  cudaError_t e = stp::server_read(s->impl, sim_id, q_host, faces_host, steps);
+  if (e != cudaSuccess) return cuda_fail(e, "server read");
+  return STP_OK;
+}
+
+stp_status stp_server_stats(stp_server s, int64_t* stats) {
+  if (!s || !s->impl || !stats) return fail(STP_ERR_INVALID_ARG, "invalid server or stats");
+  stp::server_stats(s->impl, stats);
+  return STP_OK;
+}
+
+stp_status stp_server_destroy(stp_server s) {
+  if (!s) return STP_OK;
+  stp::server_destroy(s->impl);
+  delete s;
   return STP_OK;
 }
 

@@ -73,6 +73,35 @@ cudaError_t run_static_batch(int nsets, const int* N, const int64_t* E, const do
                              double* const* faces, const double* const* tables,
                              cudaStream_t stream, int* too_big);
 
+// The same launch with caller-provided scratch (counter + per-CTA parking);
+// scratch_bytes = param_batch_scratch_bytes() suffices for one CTA per SM on
+// up to ~190 SMs. At most param_batch_max_sets() sets.
+cudaError_t launch_param_batch(int nsets, const int* N, const int64_t* E, const double* const* q,
+                               const double* const* params, double* const* avg,
+                               double* const* faces, const double* const* tables,
+                               unsigned char* scratch, size_t scratch_bytes, cudaStream_t stream,
+                               int* too_big);
+size_t static_scratch_bytes();
+int static_max_sets();
+
+// Device tables of a handle (stp_api.cu).
+const double* stp_handle_tables(stp_handle h);
+
+// Served predictor (server.cu); see include/stp.h for the behaviour.
+struct Server;
+cudaError_t server_create(int64_t budget, int nslots, Server** out);
+void server_destroy(Server* s);
+cudaError_t server_add_sim(Server* s, stp_handle h, int N, int64_t E, const double* q0,
+                           const double* params, bool device_src, int* id, bool* too_big);
+cudaError_t server_run_trace(Server* s, int64_t n, const double* t_arr, const int* sim_ids,
+                             double* latency, double* wall);
+cudaError_t server_drain(Server* s);
+cudaError_t server_read(Server* s, int id, double* q, double* faces, int64_t* steps);
+void server_stats(const Server* s, int64_t* out);
+void server_submit(Server* s, int id);
+cudaError_t server_progress(Server* s, int* done);
+int server_sims(const Server* s);
+
 cudaError_t launch_fp64_peak(double* sink, int blocks, int threads, int iters,
                              cudaStream_t stream);
 

@@ -169,3 +169,22 @@ def batched_problems(device="cpu", **kw):
                             seed_material=r["seed_material"], seed_waves=r["seed_waves"],
                             device=device)
             for r in batched_sets_recipe(**kw)]
+
+
+def served_recipe(seed: int = 1005, n_sims: int = 256, n_min: int = 4, n_max: int = 10,
+                  e_min: int = 64, e_max: int = 32768):
+    """Simulations of the served workload: N ~ U{n_min..n_max} and
+    E = round(exp(U[ln e_min, ln e_max])) drawn from PCG64(seed) in that order;
+    simulation i uses material/wave seeds 1001+16i, 1002+16i on a cube grid of
+    side ceil(E^(1/3)), h = 1/side."""
+    return batched_sets_recipe(seed=seed, n_sets=n_sims, n_min=n_min, n_max=n_max,
+                               e_min=e_min, e_max=e_max)
+
+
+def served_arrivals(n: int, rate: float = 2000.0, n_sims: int = 256, seed: int = 1006):
+    """Poisson arrivals: exponential gaps of mean 1/rate seconds, then a
+    simulation drawn uniformly, both from PCG64(seed) in that order."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    t = np.cumsum(rng.exponential(1.0 / rate, n))
+    sims = rng.integers(0, n_sims, n).astype(np.int32)
+    return t, sims

@@ -119,3 +119,53 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+
+class Server:
+    """The served predictor (continuous batching over resident simulations)."""
+
+    def __init__(self, hbm_budget_bytes: int, slots: int = 3):
+        self.handle = B.stp_server_create(hbm_budget_bytes, slots)
+        self.sims = []  # (Predictor, E)
+
+    def add_sim(self, predictor: "Predictor", q0: torch.Tensor, params: torch.Tensor) -> int:
+        predictor._check_inputs(q0, params)
+        sid = B.stp_server_add_sim(self.handle, predictor.handle, q0.shape[0], q0, params)
+        self.sims.append((predictor, q0.shape[0]))
+        return sid
+
+    def submit(self, sim_id: int):
+        B.stp_server_submit(self.handle, sim_id)
+
+    def drain(self):
+        B.stp_server_drain(self.handle)
+
+    def run_trace(self, t_arrival, sim_ids):
+        import numpy as np
+        t = np.ascontiguousarray(t_arrival, dtype=np.float64)
+        ids = np.ascontiguousarray(sim_ids, dtype=np.int32)
+        lat = np.zeros(len(t), dtype=np.float64)
+        wall = B.stp_server_run_trace(self.handle, t, ids, lat)
+        return lat, wall
+
+    def read(self, sim_id: int):
+        P, E = self.sims[sim_id]
+        N = P.N
+        q = torch.empty((E, N, N, N, 9), dtype=torch.float64)
+        faces = torch.empty((E, 6, N, N, 9), dtype=torch.float64)
+        steps = B.stp_server_read(self.handle, sim_id, q, faces)
+        return q, faces, steps
+
+    def stats(self) -> dict:
+        return B.stp_server_stats(self.handle)
+
+    def close(self):
+        if self.handle is not None:
+            B.stp_server_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
