@@ -169,6 +169,13 @@ typedef struct stp_batch_s* stp_batch; /* opaque plan, owned by the library */
  */
 stp_status stp_batch_create(int nsets, const stp_batch_set* sets, stp_batch* out);
 
+/* As stp_batch_create, with the shape of every set chosen by the caller:
+ * shapes[i] = index of one of its order's candidate shapes (0, 1: see
+ * stp_autotune), or -1 for the autotuner's choice. STP_ERR_INVALID_ARG for a
+ * shape the order does not have. */
+stp_status stp_batch_create_ex(int nsets, const stp_batch_set* sets, const int* shapes,
+                               stp_batch* out);
+
 /* Enqueue one replay of the plan's graph on `stream` (async). */
 stp_status stp_batch_launch(stp_batch b, void* stream);
 

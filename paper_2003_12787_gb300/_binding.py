@@ -65,6 +65,7 @@ def load():
         lib.stp_device_status.argtypes = [vp, vp, ctypes.POINTER(ctypes.c_uint)]
         lib.stp_batch_create.argtypes = [ctypes.c_int, vp, ctypes.POINTER(vp)]
         lib.stp_batch_launch.argtypes = [vp, vp]
+        lib.stp_batch_create_ex.argtypes = [ctypes.c_int, vp, vp, ctypes.POINTER(vp)]
         lib.stp_batch_info.argtypes = [vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
                                        ctypes.POINTER(i64)]
         lib.stp_batch_destroy.argtypes = [vp]
@@ -86,7 +87,8 @@ def load():
             getattr(lib, name).restype = ctypes.c_int
         for name in ("stp_create", "stp_predict", "stp_predict_host", "stp_destroy",
                      "stp_reference_tables", "stp_measure_fp64_peak", "stp_set_precision",
-                     "stp_device_status", "stp_batch_create", "stp_batch_launch",
+                     "stp_device_status", "stp_batch_create", "stp_batch_create_ex",
+                     "stp_batch_launch",
                      "stp_batch_info", "stp_batch_destroy", "stp_autotune"):
             getattr(lib, name).restype = ctypes.c_int
         _lib = lib
@@ -190,14 +192,21 @@ class BatchSet(ctypes.Structure):
                 ("out_avg", ctypes.c_void_p), ("out_faces", ctypes.c_void_p)]
 
 
-def stp_batch_create(sets) -> int:
-    """sets: sequence of (handle, elements, q, params, out_avg, out_faces)."""
+def stp_batch_create(sets, shapes=None) -> int:
+    """sets: sequence of (handle, elements, q, params, out_avg, out_faces);
+    shapes: optional per-set candidate shape index (-1 = autotuned)."""
     arr = (BatchSet * max(1, len(sets)))()
     for i, (h, E, q, p, a, f) in enumerate(sets):
         arr[i] = BatchSet(h, E, _ptr(q), _ptr(p), _ptr(a), _ptr(f))
     b = ctypes.c_void_p()
-    _check(load().stp_batch_create(len(sets), ctypes.cast(arr, ctypes.c_void_p), ctypes.byref(b)),
-           "stp_batch_create")
+    if shapes is None:
+        _check(load().stp_batch_create(len(sets), ctypes.cast(arr, ctypes.c_void_p), ctypes.byref(b)),
+               "stp_batch_create")
+    else:
+        sh = (ctypes.c_int * max(1, len(sets)))(*[int(x) for x in shapes])
+        _check(load().stp_batch_create_ex(len(sets), ctypes.cast(arr, ctypes.c_void_p),
+                                          ctypes.cast(sh, ctypes.c_void_p), ctypes.byref(b)),
+               "stp_batch_create_ex")
     return b.value
 
 
@@ -220,7 +229,7 @@ def stp_autotune(h: int):
     v, us = ctypes.c_int(), ctypes.c_double()
     allv = (ctypes.c_double * 2)()
     _check(load().stp_autotune(h, ctypes.byref(v), ctypes.byref(us), allv), "stp_autotune")
-    return {"variant": v.value, "us_per_element": us.value, "us_variants": [allv[0], allv[1]]}
+    return {"variant": v.value, "us_per_element": us.value, "us_variants": list(allv)}
 
 
 def stp_batch_run_static(sets, stream=None) -> None:

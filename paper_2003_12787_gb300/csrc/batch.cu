@@ -18,6 +18,7 @@
 #include <string>
 #include <vector>
 
+#include "fp64_eo.cuh"
 #include "fp64_group.cuh"
 
 namespace stp {
@@ -27,17 +28,20 @@ constexpr int kBatchThreads = 512;
 
 // Candidate shapes per N: (N, index, nodes per thread, elements per CTA,
 // average in smem, new term parked in global scratch instead of registers).
+// Orders 8..11 use the even-odd body instead (STP_BATCH_EO below): every FP64
+// path uses the same arithmetic per order, so results agree bit for bit.
 #define STP_BATCH_SHAPES(X)                                                                        \
   X(1, 0, 1, 256, true, false) X(2, 0, 1, 64, true, false) X(2, 1, 2, 128, true, false)           \
   X(3, 0, 1, 18, true, false) X(3, 1, 2, 36, true, false) X(4, 0, 1, 8, true, false)              \
   X(4, 1, 2, 16, true, false) X(5, 0, 1, 4, true, false) X(5, 1, 2, 8, true, false)               \
   X(6, 0, 1, 2, true, false) X(6, 1, 2, 4, true, false) X(7, 0, 1, 1, true, false)                \
-  X(7, 1, 2, 2, true, false) X(8, 0, 1, 1, true, false) X(8, 1, 2, 2, true, false)                \
-  X(9, 0, 2, 1, true, false) X(9, 1, 4, 1, true, true) X(10, 0, 2, 1, true, false)                \
-  X(10, 1, 4, 1, true, true) X(11, 0, 3, 1, false, true) X(11, 1, 4, 1, false, true)              \
-  X(12, 0, 4, 1, false, true) X(12, 1, 6, 1, false, true)
+  X(7, 1, 2, 2, true, false) X(12, 0, 4, 1, false, true) X(12, 1, 6, 1, false, true)
 
 constexpr int kMaxVariants = 2;
+
+// Even-odd candidates: (N, index, threads doing the work).
+#define STP_BATCH_EO(X) X(8, 0, 384) X(8, 1, 512) X(9, 0, 486) X(9, 1, 512) \
+  X(10, 0, 500) X(10, 1, 512) X(11, 0, 444) X(11, 1, 512)
 
 struct ShapeInfo {
   int valid = 0, epc = 1;
@@ -53,6 +57,9 @@ struct ShapeTable {
   s[n][v] = ShapeInfo{1, epc, Fp64Shape<n, npt, epc, avg>::SMEM,                     \
                       rg ? sizeof(double) * 9 * (size_t)Fp64Shape<n, npt, epc, avg>::S * epc : 0};
     STP_BATCH_SHAPES(X)
+#undef X
+#define X(n, v, use) s[n][v] = ShapeInfo{1, 1, EoShape<n>::SMEM, 0};
+    STP_BATCH_EO(X)
 #undef X
   }
 };
@@ -87,6 +94,12 @@ __device__ __noinline__ void run_unit(double* smem, const SetDev& sd, int64_t e0
                                                   sd.tables, e0, sd.E, rbuf);
 }
 
+template <int N, int USE>
+__device__ __noinline__ void run_unit_eo(double* smem, const SetDev& sd, int64_t e0) {
+  if (e0 < sd.E)
+    fp64_element_eo<N, kBatchThreads, USE>(smem, sd.q, sd.params, sd.avg, sd.faces, sd.tables, e0);
+}
+
 __global__ void __launch_bounds__(kBatchThreads, 1)
 batch_kernel(const SetDev* __restrict__ sets, const UnitDev* __restrict__ units, int nunits,
              unsigned int* __restrict__ counter, double* __restrict__ scratch,
@@ -108,6 +121,10 @@ batch_kernel(const SetDev* __restrict__ sets, const UnitDev* __restrict__ units,
     run_unit<n_, v_, npt_, epc_, avgsm_, rg_>(smem, sd, wu.e0, rbuf); \
     break;
       STP_BATCH_SHAPES(X)
+#undef X
+#define X(n_, v_, use_) \
+  case n_ * kMaxVariants + v_: run_unit_eo<n_, use_>(smem, sd, wu.e0); break;
+      STP_BATCH_EO(X)
 #undef X
       default: break;
     }
@@ -156,6 +173,16 @@ cudaError_t raise_smem_limit(size_t smem) {
 }
 
 }  // namespace
+
+int batch_variants_mask(int N, int* epc_out) {
+  int mask = 0;
+  for (int v = 0; v < kMaxVariants; ++v)
+    if (N >= 1 && N <= kMaxNodes && shapes().s[N][v].valid) {
+      mask |= 1 << v;
+      if (epc_out) epc_out[v] = shapes().s[N][v].epc;
+    }
+  return mask;
+}
 
 int batch_variants(int N, int* epc_out) {
   int n = 0;

@@ -20,6 +20,7 @@
 // Taylor bookkeeping: r_k = dt^k/(k+1)! q^(k) satisfies r_0 = q,
 // r_{k+1} = dt/(k+2) * L r_k with L q = -sum_d B_d (D_d q)/dx, and the time
 // average of Eq. (exahypeTimeAverage) divided by dt is sum_{k=0..N} r_k.
+#include "fp64_eo.cuh"
 #include "fp64_group.cuh"
 
 namespace stp {
@@ -34,6 +35,29 @@ fp64_stp_kernel(const double* __restrict__ q, const double* __restrict__ params,
   extern __shared__ double smem[];
   fp64_group<N, NPT, EPC, AVG_SMEM, Fp64Shape<N, NPT, EPC, AVG_SMEM>::BLOCK>(
       smem, q, params, out_avg, out_faces, tables, (int64_t)blockIdx.x * EPC, E);
+}
+
+// Even-odd kernel: one element per CTA of NT threads (USE doing the work).
+template <int N, int NT, int USE, int MINB>
+__global__ void __launch_bounds__(NT, MINB)
+fp64_eo_kernel(const double* __restrict__ q, const double* __restrict__ params,
+               double* __restrict__ out_avg, double* __restrict__ out_faces,
+               const double* __restrict__ tables, int64_t E) {
+  extern __shared__ double smem[];
+  fp64_element_eo<N, NT, USE>(smem, q, params, out_avg, out_faces, tables, (int64_t)blockIdx.x);
+}
+
+template <int N, int NT, int USE, int MINB>
+cudaError_t launch_eo(int64_t E, const double* q, const double* params, double* out_avg,
+                      double* out_faces, const double* tables, cudaStream_t stream) {
+  constexpr size_t smem = EoShape<N>::SMEM;
+  static_assert(smem <= 232448, "shared memory budget of one CTA exceeded");
+  auto kern = fp64_eo_kernel<N, NT, USE, MINB>;
+  cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (err != cudaSuccess) return err;
+  if (E > 0x7fffffffLL) return cudaErrorInvalidValue;
+  kern<<<(unsigned)E, NT, smem, stream>>>(q, params, out_avg, out_faces, tables, E);
+  return cudaGetLastError();
 }
 
 template <int N, int NPT, int EPC, bool AVG_SMEM>
@@ -68,6 +92,12 @@ cudaError_t launch_shape(int64_t E, const double* q, const double* params, doubl
 
 }  // namespace
 
+// Orders that use the even-odd kernel: (N, threads, working threads, CTAs/SM).
+// The batched, allocation-free and served paths use the even-odd body for the
+// same orders, so every FP64 path rounds alike.
+#define STP_FP64_EO_SHAPES(X) X(8, 192, 192, 2) X(9, 256, 243, 1) X(10, 320, 300, 1) \
+  X(11, 384, 363, 1)
+
 int fp64_elements_per_cta(int N) {
   switch (N) {
 #define X(n, npt, epc, avg) case n: return epc;
@@ -80,6 +110,13 @@ int fp64_elements_per_cta(int N) {
 cudaError_t launch_fp64(int N, int64_t E, const double* q, const double* params,
                         double* out_avg, double* out_faces, const double* tables,
                         cudaStream_t stream) {
+  switch (N) {
+#define X(n, nt, use, minb) \
+  case n: return launch_eo<n, nt, use, minb>(E, q, params, out_avg, out_faces, tables, stream);
+    STP_FP64_EO_SHAPES(X)
+#undef X
+    default: break;
+  }
   switch (N) {
 #define X(n, npt, epc, avg) \
   case n: return launch_shape<n, npt, epc, avg>(E, q, params, out_avg, out_faces, tables, stream);

@@ -15,6 +15,7 @@
 #include <algorithm>
 #include <mutex>
 
+#include "fp64_eo.cuh"
 #include "fp64_group.cuh"
 
 namespace stp {
@@ -39,8 +40,9 @@ static __device__ __align__(256) unsigned char g_static_scratch[kStaticScratchBy
 #define STP_STATIC_SHAPES(X)                                                                      \
   X(1, 1, 256, true, false) X(2, 1, 64, true, false) X(3, 1, 18, true, false)                    \
   X(4, 1, 8, true, false) X(5, 1, 4, true, false) X(6, 1, 2, true, false) X(7, 1, 1, true, false) \
-  X(8, 1, 1, true, false) X(9, 2, 1, true, false) X(10, 2, 1, true, false)                       \
-  X(11, 3, 1, false, true) X(12, 4, 1, false, true)
+  X(12, 4, 1, false, true)
+// Orders 8..11: the even-odd body (N, threads doing the work), as on every FP64 path.
+#define STP_STATIC_EO(X) X(8, 384) X(9, 486) X(10, 500) X(11, 444)
 
 struct StaticSet {
   const double* q;
@@ -59,6 +61,12 @@ struct StaticBatch {
   int nsets;
   int64_t nunits;
 };
+
+template <int N, int USE>
+__device__ __noinline__ void static_unit_eo(double* smem, const StaticSet& sd, int64_t e0) {
+  if (e0 < sd.E)
+    fp64_element_eo<N, kStaticThreads, USE>(smem, sd.q, sd.params, sd.avg, sd.faces, sd.tables, e0);
+}
 
 template <int N, int NPT, int EPC, bool AVG, bool RG>
 __device__ __noinline__ void static_unit(double* smem, const StaticSet& sd, int64_t e0, double* rbuf) {
@@ -91,6 +99,10 @@ static_batch_kernel(const __grid_constant__ StaticBatch b, unsigned char* scratc
   case n_: static_unit<n_, npt_, epc_, avg_, rg_>(smem, sd, e0, rbuf); break;
       STP_STATIC_SHAPES(X)
 #undef X
+#define X(n_, use_) \
+  case n_: static_unit_eo<n_, use_>(smem, sd, e0); break;
+      STP_STATIC_EO(X)
+#undef X
       default: break;
     }
   }
@@ -109,6 +121,10 @@ StaticShape static_shape(int N) {
                        rg_ ? sizeof(double) * 9 * (size_t)Fp64Shape<n_, npt_, epc_, avg_>::S * epc_ \
                            : 0};
     STP_STATIC_SHAPES(X)
+#undef X
+#define X(n_, use_) \
+  case n_: return StaticShape{1, EoShape<n_>::SMEM, 0};
+    STP_STATIC_EO(X)
 #undef X
     default: return StaticShape{};
   }

@@ -331,6 +331,11 @@ struct stp_batch_s {
 extern "C" {
 
 stp_status stp_batch_create(int nsets, const stp_batch_set* sets, stp_batch* out) {
+  return stp_batch_create_ex(nsets, sets, nullptr, out);
+}
+
+stp_status stp_batch_create_ex(int nsets, const stp_batch_set* sets, const int* shapes,
+                               stp_batch* out) {
   if (!out) return fail(STP_ERR_INVALID_ARG, "out is NULL");
   *out = nullptr;
   if (nsets < 0 || (nsets > 0 && !sets)) return fail(STP_ERR_INVALID_ARG, "bad set list");
@@ -384,8 +389,20 @@ stp_status stp_batch_create(int nsets, const stp_batch_set* sets, stp_batch* out
   stp_batch b = new (std::nothrow) stp_batch_s;
   if (!b) return fail(STP_ERR_OOM, "host allocation failed");
   b->device = dev;
+  std::vector<int> forced;
+  if (shapes) {
+    forced.assign(shapes, shapes + nsets);
+    for (int i = 0; i < nsets; ++i) {
+      int epc[4];
+      const int nv = stp::batch_variants_mask(N[i], epc);
+      if (forced[i] >= 0 && (forced[i] >= 8 || !((nv >> forced[i]) & 1))) {
+        delete b;
+        return fail(STP_ERR_INVALID_ARG, "set " + std::to_string(i) + ": no such shape for its order");
+      }
+    }
+  }
   cudaError_t e = stp::create_plan(nsets, N.data(), E.data(), q.data(), p.data(), a.data(), f.data(),
-                                   tb.data(), nullptr, &b->plan);
+                                   tb.data(), shapes ? forced.data() : nullptr, &b->plan);
   if (e != cudaSuccess) {
     delete b;
     if (e == cudaErrorMemoryAllocation) return fail(STP_ERR_OOM, "batch plan allocation failed");

@@ -54,6 +54,8 @@ struct BatchPlan;
 // Candidate shapes of order N for the batched kernel; fills epc_out[v] with
 // the elements per CTA of each; returns their number.
 int batch_variants(int N, int* epc_out);
+// Bit v set when candidate shape v exists for order N; epc_out[v] filled.
+int batch_variants_mask(int N, int* epc_out);
 // Measures (once per device and N, then cached) every candidate shape on a
 // synthetic set and returns the fastest; us_all[v] gets each candidate's
 // microseconds per element (may be NULL).

@@ -87,7 +87,7 @@ class Batch:
     launch() replays the plan's CUDA graph on the given stream.
     """
 
-    def __init__(self, items):
+    def __init__(self, items, shapes=None):
         self.items = []
         sets = []
         for P, q, params in items:
@@ -96,7 +96,7 @@ class Batch:
             avg, faces = P.empty_outputs(E, device=q.device)
             self.items.append((P, q, params, avg, faces))
             sets.append((P.handle, E, q, params, avg, faces))
-        self.handle = B.stp_batch_create(sets)
+        self.handle = B.stp_batch_create(sets, shapes)
 
     def launch(self, stream=None):
         if stream is None:
