@@ -68,8 +68,9 @@ FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
 
 
 def kernel_source_hash() -> str:
+    """Hash of the sources of the FP64 kernel the bench times."""
     h = hashlib.sha256()
-    for name in ("fp64_kernels.cu",):
+    for name in ("fp64_kernels.cu", "fp64_eo.cuh", "fp64_group.cuh", "ck_fp64.cuh"):
         with open(os.path.join(ROOT, "paper_2003_12787_gb300", "csrc", name), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:16]
@@ -243,7 +244,7 @@ def batched_measurement(stp, torch, args):
     replay (CUDA events, mean of args.batch_steps after one warm-up), element
     throughput, algorithmic FP64 rate, and the autotuner's choice per order."""
     from paper_2003_12787_gb300.inputs import batched_sets_recipe, elastic_problem
-    recipe = batched_sets_recipe()
+    recipe = batched_sets_recipe(e_max=args.batched_emax)
     items, flops, elems = [], 0, 0
     for r in recipe:
         prob = elastic_problem(r["N"], grid=r["grid"], E=r["E"], h=r["h"],
@@ -259,17 +260,20 @@ def batched_measurement(stp, torch, args):
     b.launch(stream)
     s0 = torch.cuda.Event(enable_timing=True)
     s1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.nvtx.range_push("batched_timed")
     s0.record(stream)
     for _ in range(args.batch_steps):
         b.launch(stream)
     s1.record(stream)
     torch.cuda.synchronize()
+    torch.cuda.nvtx.range_pop()
     ms = s0.elapsed_time(s1) / args.batch_steps
     tuned = {}
     for P, _, _ in items:
         if P.N not in tuned:
             tuned[P.N] = stp.stp_autotune(P.handle)
-    out = {"workload": "64 element sets, orders 3-11 (N=4..12), 64-16384 elements each "
+    out = {"workload": "64 element sets, orders 3-11 (N=4..12), "
+                       f"64-{args.batched_emax} elements each "
                        "(log-uniform, seed 1003), one persistent launch from a CUDA graph",
            "sets": len(recipe), "elements": elems, "ms_per_launch": ms,
            "elements_per_s": elems / (ms / 1e3), "tflops_algorithmic": flops / (ms / 1e3) / 1e12,
@@ -529,6 +533,8 @@ def main():
     ap.add_argument("--no-batched", action="store_true",
                     help="skip the batched 64-set workload")
     ap.add_argument("--batch-steps", type=int, default=3)
+    ap.add_argument("--batched-emax", type=int, default=16384,
+                    help="largest set of the batched workload (smaller for profiler captures)")
     ap.add_argument("--no-served", action="store_true", help="skip the served workload")
     ap.add_argument("--served-rate", type=float, default=2000.0)
     ap.add_argument("--served-requests", type=int, default=2000)
