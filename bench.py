@@ -333,7 +333,8 @@ def served_measurement(stp, torch, args):
            "launches": launches, "mean_batch": n_m / max(1, launches),
            "admissions": after["admissions"] - before["admissions"],
            "evictions": after["evictions"] - before["evictions"],
-           "pool_peak_gb": after["pool_bytes_peak"] / 2 ** 30}
+           "pool_peak_gb": after["pool_bytes_peak"] / 2 ** 30,
+           "launch_device_s": (after["kernel_us"] - before["kernel_us"]) / 1e6}
     srv.close()
     for P in preds:
         P.close()

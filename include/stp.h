@@ -276,8 +276,11 @@ stp_status stp_server_run_trace(stp_server s, int64_t n, const double* t_arrival
 stp_status stp_server_read(stp_server s, int sim_id, double* q_host, double* faces_host,
                            int64_t* steps);
 
-/* stats[0..7]: completed requests, launches, admissions, evictions, largest
- * launch (simulations), requests launched, pool bytes in use, peak bytes. */
+/* stats[0..8]: completed requests, launches, admissions, evictions, largest
+ * launch (simulations), requests launched, pool bytes in use, peak bytes,
+ * summed device time of the launches in microseconds (each from an event
+ * before the launch to its completion event; launches on different slots
+ * overlap, so the sum can exceed the wall time). */
 stp_status stp_server_stats(stp_server s, int64_t* stats);
 
 /* Finish outstanding work and free the server. NULL is a no-op. */

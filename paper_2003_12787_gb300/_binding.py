@@ -285,10 +285,10 @@ def stp_server_read(srv: int, sim_id: int, q_host=None, faces_host=None) -> int:
 
 
 def stp_server_stats(srv: int) -> dict:
-    arr = (ctypes.c_int64 * 8)()
+    arr = (ctypes.c_int64 * 9)()
     _check(load().stp_server_stats(srv, ctypes.cast(arr, ctypes.c_void_p)), "stp_server_stats")
     keys = ["completed", "launches", "admissions", "evictions", "max_batch", "requests_launched",
-            "pool_bytes_in_use", "pool_bytes_peak"]
+            "pool_bytes_in_use", "pool_bytes_peak", "kernel_us"]
     return dict(zip(keys, list(arr)))
 
 

@@ -145,6 +145,28 @@ __device__ __forceinline__ int tile_offset(int row, int k) {
   return (row >> 3) * 256 + (k >> 3) * 128 + (row & 7) * 16 + (k & 7) * 2;
 }
 
+// Two values rounded to nearest in one conversion instruction; each gets its
+// 16-bit pattern and its value back in FP32 (same rounding as to_bits).
+template <bool FP16>
+__device__ __forceinline__ void to_bits2(float a, float b, uint16_t* ba, uint16_t* bb, float* fa,
+                                         float* fb) {
+  if (FP16) {
+    const __half2 h = __floats2half2_rn(a, b);
+    *ba = __half_as_ushort(__low2half(h));
+    *bb = __half_as_ushort(__high2half(h));
+    const float2 f = __half22float2(h);
+    *fa = f.x;
+    *fb = f.y;
+  } else {
+    const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+    *ba = __bfloat16_as_ushort(__low2bfloat16(h));
+    *bb = __bfloat16_as_ushort(__high2bfloat16(h));
+    const float2 f = __bfloat1622float2(h);
+    *fa = f.x;
+    *fb = f.y;
+  }
+}
+
 template <bool FP16>
 __device__ __forceinline__ uint16_t to_bits(float v, float* back) {
   if (FP16) {
@@ -381,16 +403,21 @@ mixed_stp_kernel(const double* __restrict__ q, const double* __restrict__ params
         else if (pass == 1) { a = z; b = x; kk = y; }
         else { a = y; b = x; kk = z; }
 #pragma unroll
-        for (int q6 = 0; q6 < 6; ++q6) {
-          const int row = (q6 * N + a) * N + b;
-          const int off = (row >> 7) * 4096 + tile_offset(row & 127, kk);
-          float rem = pick_pass(r[j], pass, q6) * scp[q6];
+        for (int q6 = 0; q6 < 6; q6 += 2) {  // two quantities per conversion instruction
+          const int row0 = (q6 * N + a) * N + b, row1 = row0 + N * N;
+          const int off0 = (row0 >> 7) * 4096 + tile_offset(row0 & 127, kk);
+          const int off1 = (row1 >> 7) * 4096 + tile_offset(row1 & 127, kk);
+          float rem0 = pick_pass(r[j], pass, q6) * scp[q6];
+          float rem1 = pick_pass(r[j], pass, q6 + 1) * scp[q6 + 1];
 #pragma unroll
           for (int t = 0; t < T; ++t) {
-            float back;
-            const uint16_t bits = to_bits<FP16>(rem, &back);
-            *reinterpret_cast<uint16_t*>(A + t * TILES * 4096 + off) = bits;
-            rem -= back;
+            uint16_t b0, b1;
+            float f0, f1;
+            to_bits2<FP16>(rem0, rem1, &b0, &b1, &f0, &f1);
+            *reinterpret_cast<uint16_t*>(A + t * TILES * 4096 + off0) = b0;
+            *reinterpret_cast<uint16_t*>(A + t * TILES * 4096 + off1) = b1;
+            rem0 -= f0;
+            rem1 -= f1;
           }
         }
       }

@@ -112,6 +112,7 @@ struct Sim {
 
 struct Slot {
   cudaStream_t stream = nullptr;
+  cudaEvent_t start = nullptr;  // timing events around the launch
   cudaEvent_t done = nullptr;
   unsigned char* scratch = nullptr;
   std::vector<int> sims;
@@ -135,6 +136,7 @@ struct Server {
   // statistics
   int64_t completed = 0, batches = 0, admissions = 0, evictions = 0, max_batch = 0,
           batched_requests = 0, next_id = 0;
+  double kernel_ms = 0.0;  // sum of the launches' device times (start..done events)
   size_t peak_used = 0;
   // completion records of the current trace: id -> completion time
   std::vector<double>* completion = nullptr;
@@ -218,6 +220,8 @@ struct Server {
       if (e == cudaErrorNotReady) continue;
       if (e != cudaSuccess) return e;
       const double t = now();
+      float ms = 0.f;
+      if (cudaEventElapsedTime(&ms, sl.start, sl.done) == cudaSuccess) kernel_ms += ms;
       for (int i : sl.sims) {
         Sim& s = sims[i];
         const Request r = s.pending.front();
@@ -283,6 +287,7 @@ struct Server {
         s.queued = false;
       }
       int too_big = 0;
+      if ((e = cudaEventRecord(sl.start, sl.stream)) != cudaSuccess) return e;
       e = launch_param_batch(n, N.data(), E.data(), q.data(), p.data(), a.data(), f.data(), tb.data(),
                              sl.scratch, static_scratch_bytes(), sl.stream, &too_big);
       if (e != cudaSuccess) return e;
@@ -308,6 +313,7 @@ struct Server {
       if (s.stream) cudaStreamSynchronize(s.stream);
       cudaFree(s.scratch);
       if (s.done) cudaEventDestroy(s.done);
+      if (s.start) cudaEventDestroy(s.start);
       if (s.stream) cudaStreamDestroy(s.stream);
     }
     if (copy_stream) cudaStreamSynchronize(copy_stream);
@@ -334,7 +340,8 @@ cudaError_t server_create(int64_t budget, int nslots, Server** out) {
   s->slots.resize(nslots);
   for (Slot& sl : s->slots) {
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&sl.stream, cudaStreamNonBlocking);
-    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&sl.done, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreate(&sl.done);
+    if (e == cudaSuccess) e = cudaEventCreate(&sl.start);
     if (e == cudaSuccess) e = cudaMalloc(&sl.scratch, static_scratch_bytes());
   }
   if (e != cudaSuccess) {
@@ -449,6 +456,7 @@ void server_stats(const Server* s, int64_t* out) {
   out[5] = s->batched_requests;
   out[6] = (int64_t)s->pool.used();
   out[7] = (int64_t)s->peak_used;
+  out[8] = (int64_t)(s->kernel_ms * 1000.0);  // microseconds
 }
 
 void server_submit(Server* s, int id) {
