@@ -209,7 +209,9 @@ stp_status stp_autotune(stp_handle h, int* variant, double* us_per_element,
  *
  *   nsets <= 128 sets, each as in stp_batch_set (FP64 handles, device
  *   buffers, outputs not overlapping any input or other output); results
- *   equal stp_predict's for every set. Enqueued on `stream`, asynchronous.
+ *   equal stp_predict's for every set (bit for bit up to order 10, N <= 11; to
+ *   rounding at N = 12, where this path keeps a per-node body that parks its
+ *   new Taylor terms in the scratch array). Enqueued on `stream`, asynchronous.
  *   Returns STP_ERR_INVALID_ARG when nsets exceeds 128 or the call would
  *   need more than the 24 MiB scratch (a device with more than about 190 SMs
  *   running order 11), STP_ERR_UNSUPPORTED for non-FP64 handles.

@@ -35,13 +35,15 @@ constexpr int kBatchThreads = 512;
   X(3, 0, 1, 18, true, false) X(3, 1, 2, 36, true, false) X(4, 0, 1, 8, true, false)              \
   X(4, 1, 2, 16, true, false) X(5, 0, 1, 4, true, false) X(5, 1, 2, 8, true, false)               \
   X(6, 0, 1, 2, true, false) X(6, 1, 2, 4, true, false) X(7, 0, 1, 1, true, false)                \
-  X(7, 1, 2, 2, true, false) X(12, 0, 4, 1, false, true) X(12, 1, 6, 1, false, true)
+  X(7, 1, 2, 2, true, false)
 
 constexpr int kMaxVariants = 2;
 
-// Even-odd candidates: (N, index, threads doing the work).
+// Even-odd candidates: (N, index, threads doing the work); N = 12 uses the
+// slot-reusing variant (p and accumulators share 16 arrays).
 #define STP_BATCH_EO(X) X(8, 0, 384) X(8, 1, 512) X(9, 0, 486) X(9, 1, 512) \
   X(10, 0, 500) X(10, 1, 512) X(11, 0, 444) X(11, 1, 512)
+#define STP_BATCH_EO_SLOTS(X) X(12, 0, 432) X(12, 1, 512)
 
 struct ShapeInfo {
   int valid = 0, epc = 1;
@@ -60,6 +62,9 @@ struct ShapeTable {
 #undef X
 #define X(n, v, use) s[n][v] = ShapeInfo{1, 1, EoShape<n>::SMEM, 0};
     STP_BATCH_EO(X)
+#undef X
+#define X(n, v, use) s[n][v] = ShapeInfo{1, 1, EoSlotShape<n>::SMEM, 0};
+    STP_BATCH_EO_SLOTS(X)
 #undef X
   }
 };
@@ -95,6 +100,13 @@ __device__ __noinline__ void run_unit(double* smem, const SetDev& sd, int64_t e0
 }
 
 template <int N, int USE>
+__device__ __noinline__ void run_unit_eo_slots(double* smem, const SetDev& sd, int64_t e0) {
+  if (e0 < sd.E)
+    fp64_element_eo_slots<N, kBatchThreads, USE>(smem, sd.q, sd.params, sd.avg, sd.faces, sd.tables,
+                                                 e0);
+}
+
+template <int N, int USE>
 __device__ __noinline__ void run_unit_eo(double* smem, const SetDev& sd, int64_t e0) {
   if (e0 < sd.E)
     fp64_element_eo<N, kBatchThreads, USE>(smem, sd.q, sd.params, sd.avg, sd.faces, sd.tables, e0);
@@ -125,6 +137,10 @@ batch_kernel(const SetDev* __restrict__ sets, const UnitDev* __restrict__ units,
 #define X(n_, v_, use_) \
   case n_ * kMaxVariants + v_: run_unit_eo<n_, use_>(smem, sd, wu.e0); break;
       STP_BATCH_EO(X)
+#undef X
+#define X(n_, v_, use_) \
+  case n_ * kMaxVariants + v_: run_unit_eo_slots<n_, use_>(smem, sd, wu.e0); break;
+      STP_BATCH_EO_SLOTS(X)
 #undef X
       default: break;
     }

@@ -47,6 +47,28 @@ fp64_eo_kernel(const double* __restrict__ q, const double* __restrict__ params,
   fp64_element_eo<N, NT, USE>(smem, q, params, out_avg, out_faces, tables, (int64_t)blockIdx.x);
 }
 
+template <int N, int NT, int USE>
+__global__ void __launch_bounds__(NT, 1)
+fp64_eo_slots_kernel(const double* __restrict__ q, const double* __restrict__ params,
+                     double* __restrict__ out_avg, double* __restrict__ out_faces,
+                     const double* __restrict__ tables, int64_t E) {
+  extern __shared__ double smem[];
+  fp64_element_eo_slots<N, NT, USE>(smem, q, params, out_avg, out_faces, tables, (int64_t)blockIdx.x);
+}
+
+template <int N, int NT, int USE>
+cudaError_t launch_eo_slots(int64_t E, const double* q, const double* params, double* out_avg,
+                            double* out_faces, const double* tables, cudaStream_t stream) {
+  constexpr size_t smem = EoSlotShape<N>::SMEM;
+  static_assert(smem <= 232448, "shared memory budget of one CTA exceeded");
+  auto kern = fp64_eo_slots_kernel<N, NT, USE>;
+  cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (err != cudaSuccess) return err;
+  if (E > 0x7fffffffLL) return cudaErrorInvalidValue;
+  kern<<<(unsigned)E, NT, smem, stream>>>(q, params, out_avg, out_faces, tables, E);
+  return cudaGetLastError();
+}
+
 template <int N, int NT, int USE, int MINB>
 cudaError_t launch_eo(int64_t E, const double* q, const double* params, double* out_avg,
                       double* out_faces, const double* tables, cudaStream_t stream) {
@@ -115,6 +137,7 @@ cudaError_t launch_fp64(int N, int64_t E, const double* q, const double* params,
   case n: return launch_eo<n, nt, use, minb>(E, q, params, out_avg, out_faces, tables, stream);
     STP_FP64_EO_SHAPES(X)
 #undef X
+    case 12: return launch_eo_slots<12, 512, 432>(E, q, params, out_avg, out_faces, tables, stream);
     default: break;
   }
   switch (N) {
