@@ -81,6 +81,8 @@ stp_status stp_create(int order, int m, double dx, double dt, stp_handle* out);
  * The caller owns the buffers and keeps them alive until the stream has
  * passed the kernel. elements == 0 returns STP_OK without a launch. The
  * handle is not modified, so several streams may use one handle at once.
+ * The call may be captured into a CUDA graph (while `stream` is capturing,
+ * the check that the pointers are device memory is skipped).
  */
 stp_status stp_predict(stp_handle h, int64_t elements, const double* q,
                        const double* params, double* out_avg, double* out_faces,

@@ -202,10 +202,19 @@ stp_status stp_predict(stp_handle h, int64_t elements, const double* q, const do
                        double* out_avg, double* out_faces, void* stream) {
   stp_status s = validate_common(h, elements, q, params, out_avg, out_faces);
   if (s != STP_OK || elements == 0) return s;
-  const char* names[4] = {"q", "params", "out_avg", "out_faces"};
-  const void* ptrs[4] = {q, params, out_avg, out_faces};
-  for (int i = 0; i < 4; ++i)
-    if ((s = check_device_ptr(ptrs[i], h->device, names[i])) != STP_OK) return s;
+  // The memory-kind check queries the driver, which stream capture may forbid;
+  // while the stream is being captured it is skipped (the other checks hold).
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(static_cast<cudaStream_t>(stream), &cap) != cudaSuccess) {
+    cudaGetLastError();
+    cap = cudaStreamCaptureStatusNone;
+  }
+  if (cap == cudaStreamCaptureStatusNone) {
+    const char* names[4] = {"q", "params", "out_avg", "out_faces"};
+    const void* ptrs[4] = {q, params, out_avg, out_faces};
+    for (int i = 0; i < 4; ++i)
+      if ((s = check_device_ptr(ptrs[i], h->device, names[i])) != STP_OK) return s;
+  }
   cudaError_t e = launch_configured(h, elements, q, params, out_avg, out_faces,
                                     static_cast<cudaStream_t>(stream));
   if (e != cudaSuccess) return cuda_fail(e, "STP kernel launch");
