@@ -144,7 +144,7 @@ stp_status stp_device_status(stp_handle h, void* stream, unsigned int* flags);
  * orders and sizes, in ONE persistent kernel launch replayed from a CUDA
  * graph. Each set is described by an FP64 handle (order, dx, dt) and its own
  * device buffers in the layouts above. The paper generates one kernel per
- * order (Sec. II-C, Sec. III); here every order's element-group body lives in
+ * order (Sec. II-D, Sec. III); here every order's element-group body lives in
  * one kernel and a cost-sorted work list of (set, element range) units is
  * consumed by one CTA per SM.
  */

@@ -3,7 +3,7 @@
 // on-device autotuner.
 //
 // The paper's Kernel Generator tailors each kernel to its order at build time
-// (Sec. II-C: generated, order-specific kernels; Sec. III: padding and
+// (Sec. II-D: generated, order-specific kernels; Sec. III: padding and
 // alignment chosen per order). Here every order's kernel body is compiled
 // into one persistent kernel; a work list of (set, element range) units,
 // sorted by estimated cost (longest first), is consumed by one CTA per SM
