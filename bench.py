@@ -210,7 +210,7 @@ def mixed_comparison(stp, torch, args):
            "error": "max over avg and 6 face arrays of max|gpu-oracle|/max|oracle|, "
                     f"{len(idx)} sampled elements", "variants": {}}
     stream = torch.cuda.current_stream()
-    for prec in ("fp64", "bf16x2", "bf16x3", "fp16x2", "fp16x3"):
+    for prec in ("fp64", "bf16x2", "bf16x3", "fp16x2", "fp16x3", "fp32"):
         P = stp.Predictor(N - 1, prob.h, prob.dt, precision=prec)
         avg, faces = P.empty_outputs(E)
         for _ in range(3):
@@ -453,7 +453,7 @@ def run_gpu(args):
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms_max / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f64" if args.precision == "fp64" else f"{args.precision}+f32+f64",
+            "dtype": {"fp64": "f64", "fp32": "f32+f64"}.get(args.precision, f"{args.precision}+f32+f64"),
             "data": "synthetic",
             "config": {"workload": desc, "N": N, "order": N - 1, "elements": E,
                        "elements_per_gpu": E, "dt": prob.dt, "dx": prob.h,
@@ -544,7 +544,7 @@ def main():
     ap.add_argument("--served-budget-gb", type=float, default=4.0)
     ap.add_argument("--served-slots", type=int, default=3)
     ap.add_argument("--precision", default="fp64",
-                    choices=["fp64", "bf16x2", "bf16x3", "fp16x2", "fp16x3"],
+                    choices=["fp64", "bf16x2", "bf16x3", "fp16x2", "fp16x3", "fp32"],
                     help="arithmetic of the timed workload (default fp64)")
     ap.add_argument("--cpu-budget", type=float, default=10.0,
                     help="seconds of oracle time for cpu_baseline")

@@ -113,14 +113,20 @@ stp_status stp_predict_host(stp_handle h, int64_t elements, const double* q,
  *       split D on the tensor cores with FP32 accumulation, and updated
  *       pointwise in FP32. The Taylor average (FP32 tail added to the FP64 sum
  *       of r_0 + r_1) and the face projections are FP64.
- * Mixed variants need 2 <= N; for N = 1 the FP64 kernel runs.
+ *   STP_PRECISION_FP32
+ *       the same split on the CUDA cores: r_1 in FP64, every later term from
+ *       FP32 FMA chains (state, step matrices and coefficients rounded to
+ *       FP32), Taylor average and faces in FP64.
+ * The paper's kernels are FP64 throughout; these variants are additions.
+ * Reduced-precision variants need 2 <= N; for N = 1 the FP64 kernel runs.
  */
 typedef enum {
   STP_PRECISION_FP64 = 0,
   STP_PRECISION_BF16X2 = 1,
   STP_PRECISION_BF16X3 = 2,
   STP_PRECISION_FP16X2 = 3,
-  STP_PRECISION_FP16X3 = 4
+  STP_PRECISION_FP16X3 = 4,
+  STP_PRECISION_FP32 = 5
 } stp_precision;
 
 /* Select the precision used by later stp_predict / stp_predict_host calls on

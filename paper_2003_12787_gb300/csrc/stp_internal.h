@@ -49,6 +49,11 @@ cudaError_t launch_mixed(int N, int variant, int64_t E, const double* q, const d
                          const double* Dref, double dt_over_dx, int eD, unsigned int* status,
                          cudaStream_t stream);
 
+// FP32 variant (fp32_kernels.cu): first CK term in FP64, later terms in FP32
+// on the CUDA cores; 2 <= N <= 12.
+cudaError_t launch_fp32(int N, int64_t E, const double* q, const double* params, double* out_avg,
+                        double* out_faces, const double* tables, cudaStream_t stream);
+
 // Batched persistent FP64 launch (batch.cu).
 struct BatchPlan;
 // Candidate shapes of order N for the batched kernel; fills epc_out[v] with
