@@ -72,63 +72,6 @@ __device__ __forceinline__ void ck_node_fp64(const double* __restrict__ p,
   r[kS23] = mu * s23;
 }
 
-// The same step in FP32 (state, derivative matrix and coefficients in float).
-template <int N, int S, int LDD>
-__device__ __forceinline__ void ck_node_fp32(const float* __restrict__ p,
-                                             const float* __restrict__ Dk, int x, int y, int z,
-                                             float invrho, float lam, float mu, float mu2,
-                                             float r[9]) {
-  const float* Dx = Dk + x * LDD;
-  const float* Dy = Dk + y * LDD;
-  const float* Dz = Dk + z * LDD;
-  const float* px = p + (z * N + y) * N;
-  const float* py = p + z * N * N + x;
-  const float* pz = p + y * N + x;
-  float v1 = 0.f, v2 = 0.f, v3 = 0.f, s12 = 0.f, s13 = 0.f, s23 = 0.f, a = 0.f, b = 0.f, c = 0.f;
-#pragma unroll
-  for (int l = 0; l < N; ++l) {
-    const float d = Dx[l];
-    v1 = fmaf(d, px[kS11 * S + l], v1);
-    v2 = fmaf(d, px[kS12 * S + l], v2);
-    v3 = fmaf(d, px[kS13 * S + l], v3);
-    a = fmaf(d, px[kV1 * S + l], a);
-    s12 = fmaf(d, px[kV2 * S + l], s12);
-    s13 = fmaf(d, px[kV3 * S + l], s13);
-  }
-#pragma unroll
-  for (int l = 0; l < N; ++l) {
-    const float d = Dy[l];
-    const int o = l * N;
-    v1 = fmaf(d, py[kS12 * S + o], v1);
-    v2 = fmaf(d, py[kS22 * S + o], v2);
-    v3 = fmaf(d, py[kS23 * S + o], v3);
-    s12 = fmaf(d, py[kV1 * S + o], s12);
-    b = fmaf(d, py[kV2 * S + o], b);
-    s23 = fmaf(d, py[kV3 * S + o], s23);
-  }
-#pragma unroll
-  for (int l = 0; l < N; ++l) {
-    const float d = Dz[l];
-    const int o = l * N * N;
-    v1 = fmaf(d, pz[kS13 * S + o], v1);
-    v2 = fmaf(d, pz[kS23 * S + o], v2);
-    v3 = fmaf(d, pz[kS33 * S + o], v3);
-    s13 = fmaf(d, pz[kV1 * S + o], s13);
-    s23 = fmaf(d, pz[kV2 * S + o], s23);
-    c = fmaf(d, pz[kV3 * S + o], c);
-  }
-  const float ltr = lam * ((a + b) + c);
-  r[kV1] = invrho * v1;
-  r[kV2] = invrho * v2;
-  r[kV3] = invrho * v3;
-  r[kS11] = fmaf(mu2, a, ltr);
-  r[kS22] = fmaf(mu2, b, ltr);
-  r[kS33] = fmaf(mu2, c, ltr);
-  r[kS12] = mu * s12;
-  r[kS13] = mu * s13;
-  r[kS23] = mu * s23;
-}
-
 // Lame coefficients of one node from (rho, cp, cs): 1/rho, lambda, mu, 2 mu.
 __device__ __forceinline__ void elastic_coefficients(double rho, double cp, double cs,
                                                      double* invrho, double* lam, double* mu,

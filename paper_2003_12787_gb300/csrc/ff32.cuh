@@ -1,0 +1,118 @@
+// Float-float ("double-float") arithmetic on the FP32 pipes.
+//
+// A value is an unevaluated sum hi + lo of two floats with |lo| <= ulp(hi)
+// (about 48 significant bits). The building blocks are the error-free
+// transformations:
+//   TwoSum (Knuth, TAOCP vol. 2, Sec. 4.2.2): s = fl(a + b) and the exact
+//     rounding error of that sum, for any a, b;
+//   FastTwoSum (Dekker 1971): the same for |a| >= |b|, in three operations;
+//   TwoProduct with FMA: p = fl(a b) and the exact error fma(a, b, -p);
+// and the compensated dot product Dot2 of Ogita, Rump and Oishi ("Accurate
+// sum and dot product", SIAM J. Sci. Comput. 26, 2005), which accumulates the
+// high-part products with TwoSum and every error term in a plain FP32 sum.
+// The *_rn intrinsics keep the compiler from fusing a product into a later
+// addition, which would break the error-free transformations.
+//
+// Conversions between double and float-float use integer operations on the
+// IEEE-754 encodings, not the FP64 pipe: on this GPU a float<->double
+// conversion costs as much as a DFMA. Values below the FP32 normal range
+// (|x| < 2^-126) are treated as zero; values above it become infinite.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace stp {
+namespace ff {
+
+__device__ __forceinline__ float2 two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  const float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+  return make_float2(s, e);
+}
+
+__device__ __forceinline__ float2 fast_two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b);
+  return make_float2(s, __fsub_rn(b, __fsub_rn(s, a)));
+}
+
+__device__ __forceinline__ float2 add(float2 x, float2 y) {
+  const float2 s = two_sum(x.x, y.x);
+  return fast_two_sum(s.x, __fadd_rn(s.y, __fadd_rn(x.y, y.y)));
+}
+
+__device__ __forceinline__ float2 neg(float2 x) { return make_float2(-x.x, -x.y); }
+__device__ __forceinline__ float2 sub(float2 x, float2 y) { return add(x, neg(y)); }
+
+__device__ __forceinline__ float2 mul(float2 x, float2 y) {
+  const float p = __fmul_rn(x.x, y.x);
+  float e = __fmaf_rn(x.x, y.x, -p);
+  e = __fmaf_rn(x.x, y.y, e);
+  e = __fmaf_rn(x.y, y.x, e);
+  return fast_two_sum(p, e);
+}
+
+// Dot2 accumulator: running FP32 sum s of the high products and c of all
+// error terms; value() renormalises.
+struct Dot {
+  float s = 0.f, c = 0.f;
+  __device__ __forceinline__ void fma(float2 x, float2 y) {
+    const float p = __fmul_rn(x.x, y.x);
+    const float pe = __fmaf_rn(x.x, y.x, -p);
+    const float2 t = two_sum(s, p);
+    s = t.x;
+    float cc = __fmaf_rn(x.x, y.y, c);
+    cc = __fmaf_rn(x.y, y.x, cc);
+    c = __fadd_rn(cc, __fadd_rn(t.y, pe));
+  }
+  __device__ __forceinline__ float2 value() const { return fast_two_sum(s, c); }
+};
+
+// Float whose bits are sign | exponent | mantissa (no checks).
+__device__ __forceinline__ float make_f(uint32_t sign, int bexp, uint32_t mant) {
+  return __uint_as_float(sign | ((uint32_t)bexp << 23) | (mant & 0x7fffffu));
+}
+
+// double -> float-float, hi + lo = x to within 2^-46 |x| (normalised).
+__device__ __forceinline__ float2 split(double x) {
+  const uint64_t b = (uint64_t)__double_as_longlong(x);
+  const uint32_t sign = (uint32_t)(b >> 32) & 0x80000000u;
+  const int ex = (int)((b >> 52) & 0x7ff);
+  const uint64_t m = b & 0xfffffffffffffull;
+  if (ex == 0x7ff) {  // infinity or NaN
+    return make_float2(__uint_as_float(sign | 0x7f800000u | (m ? 0x400000u : 0u)), 0.f);
+  }
+  const int fe = ex - 1023 + 127;  // biased float exponent of hi
+  if (ex == 0 || fe <= 0) return make_float2(__uint_as_float(sign), 0.f);
+  if (fe >= 255) return make_float2(__uint_as_float(sign | 0x7f800000u), 0.f);
+  const float hi = make_f(sign, fe, (uint32_t)(m >> 29));  // top 23 mantissa bits (truncated)
+  const uint32_t r = (uint32_t)(m & 0x1fffffffu);          // the other 29 bits
+  float lo = 0.f;
+  if (r) {
+    const int pb = 31 - __clz((int)r);                      // leading bit of r
+    const int le = fe - 52 + pb;                            // biased exponent of lo
+    if (le > 0) {
+      const uint32_t mant = pb >= 23 ? (r >> (pb - 23)) : (r << (23 - pb));
+      lo = make_f(sign, le, mant);
+    }
+  }
+  return fast_two_sum(hi, lo);
+}
+
+// float -> double, exact for normal floats (subnormals give zero).
+__device__ __forceinline__ double widen(float f) {
+  const uint32_t u = __float_as_uint(f);
+  const uint32_t e = (u >> 23) & 0xffu;
+  const uint64_t sign = (uint64_t)(u & 0x80000000u) << 32;
+  if (e == 0) return __longlong_as_double((long long)sign);
+  if (e == 0xff) return __longlong_as_double((long long)(sign | 0x7ff0000000000000ull |
+                                                         ((uint64_t)(u & 0x7fffffu) << 29)));
+  return __longlong_as_double((long long)(sign | ((uint64_t)(e - 127 + 1023) << 52) |
+                                          ((uint64_t)(u & 0x7fffffu) << 29)));
+}
+
+// float-float -> double: one FP64 addition of the exactly widened parts.
+__device__ __forceinline__ double to_double(float2 x) { return widen(x.x) + widen(x.y); }
+
+}  // namespace ff
+}  // namespace stp

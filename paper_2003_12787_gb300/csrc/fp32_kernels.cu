@@ -6,214 +6,578 @@
 // average of Eq. (exahypeTimeAverage) divided by dt is sum_{k=0..N} r_k.
 // The paper's kernels are FP64 throughout; this variant splits the arithmetic
 // like the library's tensor-core variants, with FP32 in place of the
-// BF16/FP16 slices:
-//   * r_1 = dt/2 L q in FP64 (the correction pass); r_0 + r_1 in FP64;
-//   * r_2 .. r_N from per-node FP32 FMA chains (state, step matrices and
-//     coefficients rounded to FP32), their sum accumulated in FP32;
-//   * time average = (r_0 + r_1) + FP32 tail, in FP64, and the face
-//     projections of Sec. II-B in FP64.
+// BF16/FP16 slices, and without FP64 instructions on the hot path:
+//   * r_1 = dt/2 L q, r_0 + r_1, the time average and the face projections
+//     of Sec. II-B in float-float arithmetic (about 48 significant bits,
+//     ff32.cuh) on the FP32 pipes;
+//   * r_2 .. r_N in FP32 (state, step matrices and coefficients rounded to
+//     FP32), their sum accumulated in FP32 and added to r_0 + r_1 at the end.
+// On GB300 one FP64 instruction, and likewise one float<->double conversion,
+// takes the issue capacity of about 64 FP32 instructions; the only FP64
+// operations left are one addition per output value (float-float -> double).
 // The contractions are K = N long, too short to feed the tensor cores
-// efficiently once the slice conversions and the scatter of the results back
-// to the nodes are paid; the FP32 pipe (64 FP32 FMA per DFMA on GB300) makes
-// the tail cheap, so the FP64 first term dominates the run time.
+// efficiently once slice conversions and the scatter of results back to the
+// nodes are paid.
 //
-// The per-node step is the dimension-split scheme of Sec. IV (SplitCK).
-// One CTA owns EPC elements; every thread owns NPT nodes of one element. The
-// element's current term lives in shared memory as p[quantity][node] (FP64
-// for the first step, then FP32 in the same bytes). r_0 + r_1 of the owned
-// nodes is parked in the output average (global memory, read back by the
-// same thread at the end), the FP32 tail in registers.
+// The derivative contractions are the dimension-split scheme of Sec. IV
+// (SplitCK) with the even-odd decomposition of the FP64 kernels (D is
+// centro-antisymmetric on the symmetric Gauss-Legendre nodes, so a line of N
+// outputs costs about N^2/2 + 2N operations). One CTA owns one element; the
+// element's current term lives in shared memory as p[quantity][node].
 #include "ck_fp64.cuh"
+#include "ff32.cuh"
 #include "stp_internal.h"
 
 namespace stp {
 namespace {
 
-constexpr int cdiv(int a, int b) { return (a + b - 1) / b; }
-
-template <int N, int NPT, int EPC>
-struct Fp32Shape {
+// Step 0: three direction passes add each line's derivatives into nine
+// per-node float-float accumulators in shared memory, then a pointwise pass
+// forms r_1 from the accumulators and the node's elastic coefficients (or,
+// with PERNODE0, each thread forms r_1 of its nodes directly from p, for N
+// where the accumulators do not fit). Steps 1..N-1: the three passes run at
+// once, each writing its own FP32 partial arrays, so one barrier separates
+// the passes from the pointwise update.
+template <int N, bool PERNODE0 = false>
+struct Fp32EoShape {
   static constexpr int N3 = N * N * N;
-  static constexpr int T = cdiv(N3, NPT);  // threads per element
-  static constexpr int BLOCK = T * EPC;
-  static constexpr int S = N3 | 1;         // odd row stride (doubles or floats)
+  static constexpr int RX = N | 1;  // x rows padded to an odd length (banks)
+  static constexpr int PLANE = N * RX;
+  static constexpr int S = (N * PLANE) | 1;
+  static constexpr int H = N / 2;
+  static constexpr bool ODD = (N & 1) != 0;
+  // per step: E[H][H], O[H][H], middle column (rows < H) and middle-row odd part (odd N)
+  static constexpr int STEP_TABLE = 2 * H * H + (ODD ? 2 * H : 0);
+  // FP32 tables: the same with rows padded to a multiple of 4 (16-byte loads)
+  static constexpr int HP = (H + 3) & ~3;
+  static constexpr int STEP32 = 2 * H * HP + (ODD ? 2 * HP : 0);
+  // floats first: FP32 tables of steps 0..N-1 (row 0 unused); then 8-byte
+  // float-float entries: step-0 table, phi0, phi1, and an area of 18 S
+  // entries holding p[9][S] and acc[9][S] in float-float for step 0, then
+  // p[9][S] and 18 partial-derivative arrays [18][S] in FP32, then the
+  // average in float-float
+  // With PERNODE0, step 0 runs node by node from p alone (no accumulators):
+  // the step-0 table is the full N x LDD matrix and the area only needs
+  // max(9 S pairs, 27 S floats).
   static constexpr int LDD = N | 1;
-  // doubles: step-0 matrix [N][LDD], phi0, phi1, EPC x p[9][S];
-  // then floats: step matrices [N][N][LDD]
-  static constexpr int DOUBLES = N * LDD + 2 * N + EPC * kQuantities * S;
-  static constexpr size_t SMEM = sizeof(double) * (size_t)DOUBLES + sizeof(float) * (size_t)(N * N * LDD);
+  static constexpr int TABLE0 = PERNODE0 ? N * LDD : STEP_TABLE;
+  static constexpr int AREA = PERNODE0 ? (27 * S + 1) / 2 : 18 * S;
+  static constexpr int PAIRS = TABLE0 + 2 * N + AREA;
+  static constexpr size_t SMEM = sizeof(float) * (size_t)(N * STEP32) + sizeof(float2) * (size_t)PAIRS;
+  static_assert((N * STEP32) % 4 == 0, "FP32 tables keep the doubles 16-byte aligned");
 };
 
-template <int N, int NPT, int EPC>
-__global__ void __launch_bounds__(Fp32Shape<N, NPT, EPC>::BLOCK, 1)
-fp32_stp_kernel(const double* __restrict__ q, const double* __restrict__ params,
-                double* __restrict__ out_avg, double* __restrict__ out_faces,
-                const double* __restrict__ tables, int64_t E) {
-  using Sh = Fp32Shape<N, NPT, EPC>;
-  constexpr int N3 = Sh::N3, T = Sh::T, S = Sh::S, LDD = Sh::LDD;
-  constexpr int M = kQuantities;
-  extern __shared__ double smem[];
-  double* sD0 = smem;                  // [N][LDD], FP64 step-0 matrix
-  double* sPhi = sD0 + N * LDD;        // phi0[N], phi1[N]
-  double* sP = sPhi + 2 * N;           // EPC x p[M][S]
-  float* sDf = reinterpret_cast<float*>(sP + EPC * M * S);  // [N][N][LDD] FP32 step matrices
+__device__ __forceinline__ double fmx(double a, double b, double c) { return fma(a, b, c); }
+__device__ __forceinline__ float fmx(float a, float b, float c) { return fmaf(a, b, c); }
 
-  const int tid = threadIdx.x;
-  const int el = tid / T;
-  const int lt = tid - el * T;
-  const int64_t e = (int64_t)blockIdx.x * EPC + el;
-  const bool active = e < E;
-  double* sp = sP + el * M * S;
-  float* spf = reinterpret_cast<float*>(sp);  // FP32 term, in the bytes of the FP64 one
-  double* gavg = out_avg + e * (int64_t)(M * N3);
-
-  for (int i = tid; i < N * N; i += Sh::BLOCK) {
-    const int row = i / N, col = i - row * N;
-    sD0[row * LDD + col] = tables[i];
+// Entry r of the even-odd table of one step matrix Dk (N x N, row-major), in FP64.
+template <int N>
+__device__ __forceinline__ double eo_table_entry(const double* __restrict__ Dk, int r) {
+  constexpr int H = N / 2, mid = H;
+  if (r < 2 * H * H) {
+    const int which = r / (H * H), i = (r / H) % H, l = r % H;
+    const double a = Dk[i * N + l], b = Dk[i * N + (N - 1 - l)];
+    return which == 0 ? 0.5 * (a + b) : 0.5 * (a - b);
   }
-  for (int i = tid; i < N * N * N; i += Sh::BLOCK) {
-    const int row = i / N, col = i - row * N;  // row = k*N + r
-    sDf[row * LDD + col] = __double2float_rn(tables[i]);
-  }
-  for (int i = tid; i < 2 * N; i += Sh::BLOCK) sPhi[i] = tables[N3 + i];
+  const int rr = r - 2 * H * H;  // odd N only
+  if (rr < H) return Dk[rr * N + mid];
+  const int l = rr - H;
+  return 0.5 * (Dk[mid * N + l] - Dk[mid * N + (N - 1 - l)]);
+}
 
-  if (active) {
-    const double* qe = q + e * (int64_t)(M * N3);
-    for (int f = lt; f < M * N3; f += T) {  // coalesced AoS read, SoA scatter
-      const int n = f / M, s = f - n * M;
-      sp[s * S + n] = __ldg(qe + f);
+// Accumulator slots: 0..2 velocity sums, 3 s12, 4 s13, 5 s23, 6 dv1/dx,
+// 7 dv2/dy, 8 dv3/dz. Quantity q6 of pass d (x, y, z) and its accumulator.
+__device__ __forceinline__ int eo32_qty(int pass, int q6) {
+  if (q6 >= 3) return q6 - 3;
+  return pass == 0 ? (q6 == 0 ? kS11 : q6 == 1 ? kS12 : kS13)
+       : pass == 1 ? (q6 == 0 ? kS12 : q6 == 1 ? kS22 : kS23)
+                   : (q6 == 0 ? kS13 : q6 == 1 ? kS23 : kS33);
+}
+__device__ __forceinline__ int eo32_acc(int pass, int q6) {
+  if (q6 < 3) return q6;
+  return pass == 0 ? (q6 == 3 ? 6 : q6 == 4 ? 3 : 4)
+       : pass == 1 ? (q6 == 3 ? 3 : q6 == 4 ? 7 : 5)
+                   : (q6 == 3 ? 4 : q6 == 4 ? 5 : 8);
+}
+__device__ __forceinline__ bool eo32_first(int pass, int acc) {
+  if (acc <= 2) return pass == 0;
+  if (acc == 3 || acc == 4) return pass == 0;
+  if (acc == 5) return pass == 1;
+  return true;
+}
+
+// One direction pass of step 0 in float-float over the 6 N^2 lines of the
+// quantities it couples (threads tid < use); the first contribution to an
+// accumulator is written, later ones added.
+template <int N>
+__device__ __forceinline__ void eo_pass_ff(const float2* __restrict__ sp, float2* __restrict__ sacc,
+                                           const float2* __restrict__ T, int pass, int tid, int use) {
+  using Sh = Fp32EoShape<N>;
+  constexpr int S = Sh::S, H = Sh::H, RX = Sh::RX, PLANE = Sh::PLANE, mid = H;
+  constexpr bool ODD = Sh::ODD;
+  const float2* E = T;
+  const float2* O = E + H * H;
+  const float2* Dm = O + H * H;
+  const float2* Om = Dm + H;
+  for (int task = tid; task < (tid < use ? 6 * N * N : 0); task += use) {
+    const int q6 = task / (N * N);
+    const int a = (task / N) % N, b = task % N;
+    const int s = eo32_qty(pass, q6), acc = eo32_acc(pass, q6);
+    int base, stride;
+    if (pass == 0) { base = a * PLANE + b * RX; stride = 1; }
+    else if (pass == 1) { base = a * PLANE + b; stride = RX; }
+    else { base = a * RX + b; stride = PLANE; }
+    const float2* u = sp + s * S + base;
+    float2 ev[H > 0 ? H : 1], od[H > 0 ? H : 1];
+#pragma unroll
+    for (int l = 0; l < H; ++l) {
+      const float2 lo = u[l * stride], hi = u[(N - 1 - l) * stride];
+      ev[l] = ff::add(lo, hi);
+      od[l] = ff::sub(lo, hi);
     }
-  }
-  double cd[NPT][4];
-  float cf[NPT][4];
-  const double* pe = params + e * (int64_t)(kParams * N3);
+    float2 out[N];
 #pragma unroll
-  for (int j = 0; j < NPT; ++j) {
-    const int n = lt + j * T;
-    cd[j][0] = cd[j][1] = cd[j][2] = cd[j][3] = 0.0;
-    if (active && n < N3)
-      elastic_coefficients(__ldg(pe + 3 * n), __ldg(pe + 3 * n + 1), __ldg(pe + 3 * n + 2),
-                           &cd[j][0], &cd[j][1], &cd[j][2], &cd[j][3]);
+    for (int i = 0; i < H; ++i) {
+      ff::Dot P, Q;
 #pragma unroll
-    for (int c = 0; c < 4; ++c) cf[j][c] = __double2float_rn(cd[j][c]);
-  }
-  __syncthreads();
-
-  // Step 0 in FP64: r_1 from q; r_0 + r_1 parked in the output average.
-  float r[NPT][M];
-#pragma unroll
-  for (int j = 0; j < NPT; ++j) {
-    const int n = lt + j * T;
-    if (!active || n >= N3) continue;
-    const int x = n % N, y = (n / N) % N, z = n / (N * N);
-    double r1[M];
-    ck_node_fp64<N, S, LDD>(sp, sD0, x, y, z, cd[j][0], cd[j][1], cd[j][2], cd[j][3], r1);
-#pragma unroll
-    for (int s = 0; s < M; ++s) {
-      gavg[n * M + s] = sp[s * S + n] + r1[s];
-      r[j][s] = __double2float_rn(r1[s]);
-    }
-  }
-  __syncthreads();  // every thread has read q
-  float acc[NPT][M];
-#pragma unroll
-  for (int j = 0; j < NPT; ++j) {
-    const int n = lt + j * T;
-#pragma unroll
-    for (int s = 0; s < M; ++s) acc[j][s] = 0.f;
-    if (!active || n >= N3) continue;
-#pragma unroll
-    for (int s = 0; s < M; ++s) spf[s * S + n] = r[j][s];
-  }
-  __syncthreads();  // r_1 (FP32) visible
-
-  for (int k = 1; k < N; ++k) {
-    const float* Dk = sDf + k * N * LDD;
-#pragma unroll
-    for (int j = 0; j < NPT; ++j) {
-      const int n = lt + j * T;
-      if (!active || n >= N3) continue;
-      const int x = n % N, y = (n / N) % N, z = n / (N * N);
-      ck_node_fp32<N, S, LDD>(spf, Dk, x, y, z, cf[j][0], cf[j][1], cf[j][2], cf[j][3], r[j]);
-#pragma unroll
-      for (int s = 0; s < M; ++s) acc[j][s] += r[j][s];
-    }
-    __syncthreads();  // every thread has read r_k
-    if (k + 1 < N) {
-#pragma unroll
-      for (int j = 0; j < NPT; ++j) {
-        const int n = lt + j * T;
-        if (!active || n >= N3) continue;
-#pragma unroll
-        for (int s = 0; s < M; ++s) spf[s * S + n] = r[j][s];
+      for (int l = 0; l < H; ++l) {
+        P.fma(E[i * H + l], ev[l]);
+        Q.fma(O[i * H + l], od[l]);
       }
-      __syncthreads();  // r_{k+1} visible
+      if (ODD) P.fma(Dm[i], u[mid * stride]);
+      const float2 pv = P.value(), qv = Q.value();
+      out[i] = ff::add(pv, qv);
+      out[N - 1 - i] = ff::sub(qv, pv);
     }
-  }
-
-  // Time average in FP64 (the FP32 term is no longer read), then the faces.
+    if (ODD) {
+      ff::Dot Q;
 #pragma unroll
-  for (int j = 0; j < NPT; ++j) {
-    const int n = lt + j * T;
-    if (!active || n >= N3) continue;
-#pragma unroll
-    for (int s = 0; s < M; ++s) {
-      const double v = gavg[n * M + s] + (double)acc[j][s];
-      gavg[n * M + s] = v;
-      sp[s * S + n] = v;
+      for (int l = 0; l < H; ++l) Q.fma(Om[l], od[l]);
+      out[mid] = Q.value();
     }
-  }
-  __syncthreads();
-  if (active) {
-    double* fe = out_faces + e * (int64_t)(6 * N * N * M);
-    for (int o = lt; o < 6 * N * N * M; o += T) {
-      const int s = o % M;
-      int rest = o / M;
-      const int bb = rest % N;
-      rest /= N;
-      const int aa = rest % N;
-      const int f = rest / N;
-      const int d = f >> 1;
-      const double* phi = sPhi + (f & 1) * N;
-      int base, stride;
-      if (d == 0) { base = (aa * N + bb) * N; stride = 1; }
-      else if (d == 1) { base = aa * N * N + bb; stride = N; }
-      else { base = aa * N + bb; stride = N * N; }
-      double a = 0.0;
+    float2* dst = sacc + acc * S + base;
+    if (eo32_first(pass, acc)) {
 #pragma unroll
-      for (int i = 0; i < N; ++i) a = fma(phi[i], sp[s * S + base + i * stride], a);
-      fe[o] = a;
+      for (int i = 0; i < N; ++i) dst[i * stride] = out[i];
+    } else {
+#pragma unroll
+      for (int i = 0; i < N; ++i) dst[i * stride] = ff::add(dst[i * stride], out[i]);
     }
   }
 }
 
-template <int N, int NPT, int EPC>
-cudaError_t launch_fp32_shape(int64_t E, const double* q, const double* params, double* out_avg,
-                              double* out_faces, const double* tables, cudaStream_t stream) {
-  using Sh = Fp32Shape<N, NPT, EPC>;
-  static_assert(Sh::SMEM <= 232448, "shared memory budget of one CTA exceeded");
-  static_assert(Sh::BLOCK <= 1024, "too many threads per CTA");
-  auto kern = fp32_stp_kernel<N, NPT, EPC>;
-  cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Sh::SMEM);
+// Entry r of the padded FP32 table of one step (zeros in the padding).
+template <int N>
+__device__ __forceinline__ float eo_table_entry32(const double* __restrict__ Dk, int r) {
+  using Sh = Fp32EoShape<N>;
+  constexpr int H = Sh::H, HP = Sh::HP;
+  int row, col, src;
+  if (r < 2 * H * HP) {
+    const int which = r / (H * HP);
+    row = (r / HP) % H;
+    col = r % HP;
+    src = which * H * H + row * H + col;
+  } else {
+    const int rr = r - 2 * H * HP;  // odd N only
+    col = rr % HP;
+    src = 2 * H * H + (rr / HP) * H + col;
+  }
+  return col < H ? __double2float_rn(eo_table_entry<N>(Dk, src)) : 0.f;
+}
+
+// All three direction passes of one FP32 step at once: every (pass, group of
+// QPT quantities, line position) task contracts QPT lines and writes their
+// derivatives to partial array pass * 6 + q6 (no read-modify-write, so the
+// passes need no barrier between them). Threads tid < use.
+template <int N, int QPT>
+__device__ __forceinline__ void eo32_passes(const float* __restrict__ sp, float* __restrict__ spart,
+                                            const float* __restrict__ T, int tid, int use) {
+  using Sh = Fp32EoShape<N>;
+  constexpr int S = Sh::S, H = Sh::H, HP = Sh::HP, RX = Sh::RX, PLANE = Sh::PLANE, mid = H;
+  constexpr bool ODD = Sh::ODD;
+  constexpr int G = 6 / QPT;
+  static_assert(G * QPT == 6, "QPT divides 6");
+  constexpr int TASKS = 3 * G * N * N;
+  const float4* E4 = reinterpret_cast<const float4*>(T);
+  const float4* O4 = reinterpret_cast<const float4*>(T + H * HP);
+  const float* Dm = T + 2 * H * HP;
+  const float4* Om4 = reinterpret_cast<const float4*>(Dm + HP);
+  for (int task = tid; task < (tid < use ? TASKS : 0); task += use) {
+    const int pass = task / (G * N * N);
+    const int rem = task - pass * (G * N * N);
+    const int grp = rem / (N * N);
+    const int a = (rem / N) % N, b = rem % N;
+    int base, stride;
+    if (pass == 0) { base = a * PLANE + b * RX; stride = 1; }
+    else if (pass == 1) { base = a * PLANE + b; stride = RX; }
+    else { base = a * RX + b; stride = PLANE; }
+    float ev[QPT][HP], od[QPT][HP], um[QPT];
+#pragma unroll
+    for (int qi = 0; qi < QPT; ++qi) {
+      const float* u = sp + eo32_qty(pass, grp * QPT + qi) * S + base;
+#pragma unroll
+      for (int l = 0; l < HP; ++l) {
+        if (l < H) {
+          const float lo = u[l * stride], hi = u[(N - 1 - l) * stride];
+          ev[qi][l] = lo + hi;
+          od[qi][l] = lo - hi;
+        } else {
+          ev[qi][l] = 0.f;
+          od[qi][l] = 0.f;
+        }
+      }
+      um[qi] = ODD ? u[mid * stride] : 0.f;
+    }
+    float out[QPT][N];
+#pragma unroll
+    for (int i = 0; i < H; ++i) {
+      float er[HP], orow[HP];
+#pragma unroll
+      for (int v = 0; v < HP / 4; ++v) {
+        const float4 x = E4[i * (HP / 4) + v], y = O4[i * (HP / 4) + v];
+        er[4 * v] = x.x; er[4 * v + 1] = x.y; er[4 * v + 2] = x.z; er[4 * v + 3] = x.w;
+        orow[4 * v] = y.x; orow[4 * v + 1] = y.y; orow[4 * v + 2] = y.z; orow[4 * v + 3] = y.w;
+      }
+#pragma unroll
+      for (int qi = 0; qi < QPT; ++qi) {
+        float P = 0.f, Q = 0.f;
+#pragma unroll
+        for (int l = 0; l < H; ++l) {
+          P = fmaf(er[l], ev[qi][l], P);
+          Q = fmaf(orow[l], od[qi][l], Q);
+        }
+        if (ODD) P = fmaf(Dm[i], um[qi], P);
+        out[qi][i] = P + Q;
+        out[qi][N - 1 - i] = Q - P;
+      }
+    }
+    if (ODD) {
+      float om[HP];
+#pragma unroll
+      for (int v = 0; v < HP / 4; ++v) {
+        const float4 x = Om4[v];
+        om[4 * v] = x.x; om[4 * v + 1] = x.y; om[4 * v + 2] = x.z; om[4 * v + 3] = x.w;
+      }
+#pragma unroll
+      for (int qi = 0; qi < QPT; ++qi) {
+        float Q = 0.f;
+#pragma unroll
+        for (int l = 0; l < H; ++l) Q = fmaf(om[l], od[qi][l], Q);
+        out[qi][mid] = Q;
+      }
+    }
+#pragma unroll
+    for (int qi = 0; qi < QPT; ++qi) {
+      float* dst = spart + (pass * 6 + grp * QPT + qi) * S + base;
+#pragma unroll
+      for (int i = 0; i < N; ++i) dst[i * stride] = out[qi][i];
+    }
+  }
+}
+
+// The nine accumulator values of node pn from the 18 partial arrays (slot
+// order of eo32_acc; passes added in x, y, z order).
+__device__ __forceinline__ void eo32_gather(const float* __restrict__ spart, int S, int pn, float g[9]) {
+  auto P = [&](int pass, int q6) { return spart[(pass * 6 + q6) * S + pn]; };
+#pragma unroll
+  for (int j = 0; j < 3; ++j) g[j] = (P(0, j) + P(1, j)) + P(2, j);
+  g[3] = P(0, 4) + P(1, 3);
+  g[4] = P(0, 5) + P(2, 3);
+  g[5] = P(1, 5) + P(2, 4);
+  g[6] = P(0, 3);
+  g[7] = P(1, 4);
+  g[8] = P(2, 5);
+}
+
+// New term of one node from its nine accumulators (slot order above).
+template <typename R>
+__device__ __forceinline__ void eo_pointwise(const R g[9], R invrho, R lam, R mu, R mu2, R r[9]) {
+  const R ltr = lam * ((g[6] + g[7]) + g[8]);
+  r[kV1] = invrho * g[0];
+  r[kV2] = invrho * g[1];
+  r[kV3] = invrho * g[2];
+  r[kS11] = fmx(mu2, g[6], ltr);
+  r[kS22] = fmx(mu2, g[7], ltr);
+  r[kS33] = fmx(mu2, g[8], ltr);
+  r[kS12] = mu * g[3];
+  r[kS13] = mu * g[4];
+  r[kS23] = mu * g[5];
+}
+
+// New term of one node in float-float.
+__device__ __forceinline__ void eo_pointwise_ff(const float2 g[9], float2 invrho, float2 lam,
+                                                float2 mu, float2 mu2, float2 r[9]) {
+  const float2 ltr = ff::mul(lam, ff::add(ff::add(g[6], g[7]), g[8]));
+  r[kV1] = ff::mul(invrho, g[0]);
+  r[kV2] = ff::mul(invrho, g[1]);
+  r[kV3] = ff::mul(invrho, g[2]);
+  r[kS11] = ff::add(ff::mul(mu2, g[6]), ltr);
+  r[kS22] = ff::add(ff::mul(mu2, g[7]), ltr);
+  r[kS33] = ff::add(ff::mul(mu2, g[8]), ltr);
+  r[kS12] = ff::mul(mu, g[3]);
+  r[kS13] = ff::mul(mu, g[4]);
+  r[kS23] = ff::mul(mu, g[5]);
+}
+
+// Lame coefficients (1/rho, lambda, mu, 2 mu) in float-float from FP64
+// (rho, cp, cs); 1/rho is the FP32 reciprocal refined by one Newton step.
+__device__ __forceinline__ void elastic_coefficients_ff(double rho, double cp, double cs, float2 c[4]) {
+  const float2 r = ff::split(rho), p = ff::split(cp), v = ff::split(cs);
+  const float2 cs2 = ff::mul(v, v);
+  const float2 m = ff::mul(r, cs2);
+  const float2 y0 = make_float2(1.0f / r.x, 0.f);
+  const float2 res = ff::sub(make_float2(1.f, 0.f), ff::mul(r, y0));
+  c[0] = ff::add(y0, ff::mul(y0, res));
+  c[1] = ff::mul(r, ff::sub(ff::mul(p, p), make_float2(2.f * cs2.x, 2.f * cs2.y)));
+  c[2] = m;
+  c[3] = make_float2(2.f * m.x, 2.f * m.y);
+}
+
+// The first CK step of one node in float-float (same contraction pattern as
+// the FP64 per-node step): dimension-split derivatives of the owned node from
+// the x-, y- and z-lines through it, combined with the node's coefficients.
+template <int N>
+__device__ __forceinline__ void ck_node_ff(const float2* __restrict__ p, const float2* __restrict__ D0,
+                                           int x, int y, int z, const float2 c[4], float2 r[9]) {
+  using Sh = Fp32EoShape<N, true>;
+  constexpr int S = Sh::S, RX = Sh::RX, PLANE = Sh::PLANE, LDD = Sh::LDD;
+  const float2* Dx = D0 + x * LDD;
+  const float2* Dy = D0 + y * LDD;
+  const float2* Dz = D0 + z * LDD;
+  const float2* px = p + z * PLANE + y * RX;
+  const float2* py = p + z * PLANE + x;
+  const float2* pz = p + y * RX + x;
+  ff::Dot v1, v2, v3, s12a, s12b, s13a, s13b, s23a, s23b, a, b, cc;
+#pragma unroll
+  for (int l = 0; l < N; ++l) {
+    const float2 d = Dx[l];
+    v1.fma(d, px[kS11 * S + l]);
+    v2.fma(d, px[kS12 * S + l]);
+    v3.fma(d, px[kS13 * S + l]);
+    a.fma(d, px[kV1 * S + l]);
+    s12a.fma(d, px[kV2 * S + l]);
+    s13a.fma(d, px[kV3 * S + l]);
+  }
+  ff::Dot v1y, v2y, v3y;
+#pragma unroll
+  for (int l = 0; l < N; ++l) {
+    const float2 d = Dy[l];
+    const int o = l * RX;
+    v1y.fma(d, py[kS12 * S + o]);
+    v2y.fma(d, py[kS22 * S + o]);
+    v3y.fma(d, py[kS23 * S + o]);
+    s12b.fma(d, py[kV1 * S + o]);
+    b.fma(d, py[kV2 * S + o]);
+    s23a.fma(d, py[kV3 * S + o]);
+  }
+  ff::Dot v1z, v2z, v3z;
+#pragma unroll
+  for (int l = 0; l < N; ++l) {
+    const float2 d = Dz[l];
+    const int o = l * PLANE;
+    v1z.fma(d, pz[kS13 * S + o]);
+    v2z.fma(d, pz[kS23 * S + o]);
+    v3z.fma(d, pz[kS33 * S + o]);
+    s13b.fma(d, pz[kV1 * S + o]);
+    s23b.fma(d, pz[kV2 * S + o]);
+    cc.fma(d, pz[kV3 * S + o]);
+  }
+  float2 g[9];
+  g[0] = ff::add(ff::add(v1.value(), v1y.value()), v1z.value());
+  g[1] = ff::add(ff::add(v2.value(), v2y.value()), v2z.value());
+  g[2] = ff::add(ff::add(v3.value(), v3y.value()), v3z.value());
+  g[3] = ff::add(s12a.value(), s12b.value());
+  g[4] = ff::add(s13a.value(), s13b.value());
+  g[5] = ff::add(s23a.value(), s23b.value());
+  g[6] = a.value();
+  g[7] = b.value();
+  g[8] = cc.value();
+  eo_pointwise_ff(g, c[0], c[1], c[2], c[3], r);
+}
+
+// One element (e < E) by a CTA of NT threads, the first USE doing the work;
+// thread t < USE owns nodes t, t + USE, ...
+template <int N, int NT, int USE, int QPT, int MINB, bool PERNODE0>
+__global__ void __launch_bounds__(NT, MINB)
+fp32_eo_kernel(const double* __restrict__ q, const double* __restrict__ params,
+               double* __restrict__ out_avg, double* __restrict__ out_faces,
+               const double* __restrict__ tables, int64_t E) {
+  using Sh = Fp32EoShape<N, PERNODE0>;
+  constexpr int N3 = Sh::N3, S = Sh::S, RX = Sh::RX, PLANE = Sh::PLANE, ST = Sh::STEP_TABLE;
+  constexpr int ST32 = Sh::STEP32;
+  constexpr int M = kQuantities;
+  constexpr int NODES = (N3 + USE - 1) / USE;
+  auto pad = [](int n) { return (n / (N * N)) * PLANE + ((n / N) % N) * RX + n % N; };
+  extern __shared__ double smem[];
+  float* sTf = reinterpret_cast<float*>(smem);  // [N][ST32] FP32 tables (16-byte rows)
+  float2* sT0 = reinterpret_cast<float2*>(sTf + N * ST32);  // step-0 even-odd table (float-float)
+  float2* sPhi = sT0 + Sh::TABLE0;          // phi0[N], phi1[N] (float-float)
+  float2* sp = sPhi + 2 * N;                // p[9][S] (float-float, step 0); the average at the end
+  float2* sacc = sp + M * S;                // acc[9][S] (float-float, step 0)
+  float* spf = reinterpret_cast<float*>(sp);  // p[9][S] (FP32, later steps)
+  float* spart = spf + M * S;                 // partial derivatives [18][S] (FP32)
+  const int tid = threadIdx.x;
+  const int64_t e = blockIdx.x;
+  // r_0 + r_1 of the owned nodes is parked in the output average as float-float
+  double* gavg = out_avg + e * (int64_t)(M * N3);
+  float2* gpark = reinterpret_cast<float2*>(gavg);
+
+  if (PERNODE0) {
+    for (int i = tid; i < N * N; i += NT) {
+      const int row = i / N, col = i - row * N;
+      sT0[row * Sh::LDD + col] = ff::split(tables[i]);
+    }
+  } else {
+    for (int i = tid; i < ST; i += NT) sT0[i] = ff::split(eo_table_entry<N>(tables, i));
+  }
+  for (int i = ST32 + tid; i < N * ST32; i += NT) {
+    const int k = i / ST32;
+    sTf[i] = eo_table_entry32<N>(tables + k * N * N, i - k * ST32);
+  }
+  for (int i = tid; i < 2 * N; i += NT) sPhi[i] = ff::split(tables[N3 + i]);
+  const double* qe = q + e * (int64_t)(M * N3);
+  for (int f = tid; f < M * N3; f += NT) {  // coalesced AoS read, SoA scatter
+    const int n = f / M, s = f - n * M;
+    sp[s * S + pad(n)] = ff::split(__ldg(qe + f));
+  }
+  __syncthreads();
+
+  // step 0 in float-float
+  if (!PERNODE0) {
+#pragma unroll 1
+    for (int pass = 0; pass < 3; ++pass) {
+      eo_pass_ff<N>(sp, sacc, sT0, pass, tid, USE);
+      __syncthreads();
+    }
+  }
+  float r[NODES][M], cf[NODES][4];
+  const double* pe = params + e * (int64_t)(kParams * N3);
+#pragma unroll
+  for (int j = 0; j < NODES; ++j) {
+    const int n = tid + j * USE;
+#pragma unroll
+    for (int c = 0; c < 4; ++c) cf[j][c] = 0.f;
+    if (tid >= USE || n >= N3) continue;
+    float2 c2[4];
+    elastic_coefficients_ff(__ldg(pe + 3 * n), __ldg(pe + 3 * n + 1), __ldg(pe + 3 * n + 2), c2);
+#pragma unroll
+    for (int c = 0; c < 4; ++c) cf[j][c] = c2[c].x;
+    const int pn = pad(n);
+    float2 r1[9];
+    if (PERNODE0) {
+      ck_node_ff<N>(sp, sT0, n % N, (n / N) % N, n / (N * N), c2, r1);
+    } else {
+      float2 g[9];
+#pragma unroll
+      for (int c = 0; c < 9; ++c) g[c] = sacc[c * S + pn];
+      eo_pointwise_ff(g, c2[0], c2[1], c2[2], c2[3], r1);
+    }
+#pragma unroll
+    for (int s = 0; s < M; ++s) {
+      gpark[n * M + s] = ff::add(sp[s * S + pn], r1[s]);  // r_0 + r_1
+      r[j][s] = r1[s].x;
+    }
+  }
+  __syncthreads();  // every float-float read is done
+  float acc[NODES][M];
+#pragma unroll
+  for (int j = 0; j < NODES; ++j) {
+    const int n = tid + j * USE;
+#pragma unroll
+    for (int s = 0; s < M; ++s) acc[j][s] = 0.f;
+    if (tid >= USE || n >= N3) continue;
+    const int pn = pad(n);
+#pragma unroll
+    for (int s = 0; s < M; ++s) spf[s * S + pn] = r[j][s];
+  }
+  __syncthreads();
+
+  // steps 1 .. N-1 in FP32
+  for (int k = 1; k < N; ++k) {
+    eo32_passes<N, QPT>(spf, spart, sTf + k * ST32, tid, USE);
+    __syncthreads();
+#pragma unroll
+    for (int j = 0; j < NODES; ++j) {
+      const int n = tid + j * USE;
+      if (tid >= USE || n >= N3) continue;
+      const int pn = pad(n);
+      float g[9], rn[9];
+      eo32_gather(spart, S, pn, g);
+      eo_pointwise<float>(g, cf[j][0], cf[j][1], cf[j][2], cf[j][3], rn);
+#pragma unroll
+      for (int s = 0; s < M; ++s) {
+        acc[j][s] += rn[s];
+        if (k + 1 < N) spf[s * S + pn] = rn[s];
+      }
+    }
+    __syncthreads();
+  }
+
+  // time average (r_0 + r_1 plus the FP32 tail) in float-float, then the faces
+#pragma unroll
+  for (int j = 0; j < NODES; ++j) {
+    const int n = tid + j * USE;
+    if (tid >= USE || n >= N3) continue;
+    const int pn = pad(n);
+#pragma unroll
+    for (int s = 0; s < M; ++s) {
+      const float2 v = ff::add(gpark[n * M + s], make_float2(acc[j][s], 0.f));
+      sp[s * S + pn] = v;
+      gavg[n * M + s] = ff::to_double(v);
+    }
+  }
+  __syncthreads();
+  double* fe = out_faces + e * (int64_t)(6 * N * N * M);
+  for (int o = tid; o < 6 * N * N * M; o += NT) {
+    const int s = o % M;
+    int rest = o / M;
+    const int bb = rest % N;
+    rest /= N;
+    const int aa = rest % N;
+    const int f = rest / N;
+    const int d = f >> 1;
+    const float2* phi = sPhi + (f & 1) * N;
+    int base, stride;
+    if (d == 0) { base = aa * PLANE + bb * RX; stride = 1; }
+    else if (d == 1) { base = aa * PLANE + bb; stride = RX; }
+    else { base = aa * RX + bb; stride = PLANE; }
+    ff::Dot a;
+#pragma unroll
+    for (int i = 0; i < N; ++i) a.fma(phi[i], sp[s * S + base + i * stride]);
+    fe[o] = ff::to_double(a.value());
+  }
+}
+
+template <int N, int NT, int USE, int QPT, int MINB, bool PERNODE0>
+cudaError_t launch_fp32_eo(int64_t E, const double* q, const double* params, double* out_avg,
+                           double* out_faces, const double* tables, cudaStream_t stream) {
+  constexpr size_t smem = Fp32EoShape<N, PERNODE0>::SMEM;
+  static_assert(smem <= 232448, "shared memory budget of one CTA exceeded");
+  static_assert(USE <= NT && NT <= 1024, "bad thread counts");
+  auto kern = fp32_eo_kernel<N, NT, USE, QPT, MINB, PERNODE0>;
+  cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (err != cudaSuccess) return err;
-  const int64_t blocks = (E + EPC - 1) / EPC;
-  if (blocks > 0x7fffffffLL) return cudaErrorInvalidValue;
-  kern<<<(unsigned)blocks, Sh::BLOCK, Sh::SMEM, stream>>>(q, params, out_avg, out_faces, tables, E);
+  if (E > 0x7fffffffLL) return cudaErrorInvalidValue;
+  if (E == 0) return cudaSuccess;
+  kern<<<(unsigned)E, NT, smem, stream>>>(q, params, out_avg, out_faces, tables, E);
   return cudaGetLastError();
 }
 
 }  // namespace
 
-// Launch shape per N: (N, nodes per thread, elements per CTA).
-#define STP_FP32_SHAPES(X)                                                                  \
-  X(2, 1, 64) X(3, 1, 16) X(4, 1, 8) X(5, 1, 4) X(6, 1, 4) X(7, 1, 2) X(8, 1, 1) X(9, 1, 1) \
-  X(10, 1, 1) X(11, 2, 1) X(12, 3, 1)
+// Launch shape per N: (N, threads, working threads, quantities per FP32 line
+// task, CTAs per SM the registers are sized for, step 0 node by node).
+#define STP_FP32_SHAPES(X)                                                                        \
+  X(2, 32, 24, 1, 16, false) X(3, 32, 27, 2, 16, false) X(4, 96, 96, 1, 8, false)                \
+  X(5, 160, 150, 1, 6, false) X(6, 256, 216, 1, 1, false) X(7, 160, 147, 2, 4, false)            \
+  X(8, 576, 576, 1, 1, false) X(9, 512, 486, 2, 1, false) X(10, 640, 600, 2, 1, false)           \
+  X(11, 384, 363, 2, 1, false) X(12, 448, 432, 2, 1, true)
 
 cudaError_t launch_fp32(int N, int64_t E, const double* q, const double* params, double* out_avg,
                         double* out_faces, const double* tables, cudaStream_t stream) {
   switch (N) {
-#define X(n, npt, epc) \
-  case n: return launch_fp32_shape<n, npt, epc>(E, q, params, out_avg, out_faces, tables, stream);
+#define X(n, nt, use, qpt, minb, pn0) \
+  case n: return launch_fp32_eo<n, nt, use, qpt, minb, pn0>(E, q, params, out_avg, out_faces, tables, stream);
     STP_FP32_SHAPES(X)
 #undef X
     default: return cudaErrorInvalidValue;
