@@ -114,9 +114,18 @@ stp_status stp_predict_host(stp_handle h, int64_t elements, const double* q,
  *       pointwise in FP32. The Taylor average (FP32 tail added to the FP64 sum
  *       of r_0 + r_1) and the face projections are FP64.
  *   STP_PRECISION_FP32
- *       the same split on the CUDA cores: r_1 in FP64, every later term from
- *       FP32 FMA chains (state, step matrices and coefficients rounded to
- *       FP32), Taylor average and faces in FP64.
+ *       the same split on the CUDA cores without FP64 instructions: r_1,
+ *       r_0 + r_1, the Taylor average and the faces in float-float (pairs of
+ *       floats, about 48 significant bits, on the FP32 pipes), every later
+ *       term in FP32 (state, step matrices and coefficients rounded to FP32).
+ *   STP_PRECISION_FF
+ *       every step in float-float on the FP32 pipes (about 48 significant
+ *       bits): results agree with the FP64 kernel to about 1e-13 relative,
+ *       several times faster on a GPU whose FP64 rate is low. 2 <= N <= 11
+ *       (stp_set_precision returns STP_ERR_UNSUPPORTED for N = 12).
+ * FP32 and FF scale each element's state by a power of two (exact) so that
+ * its largest magnitude is about 1; within an element, values more than
+ * 2^126 below that largest magnitude contribute as zero.
  * The paper's kernels are FP64 throughout; these variants are additions.
  * Reduced-precision variants need 2 <= N; for N = 1 the FP64 kernel runs.
  */
@@ -126,7 +135,8 @@ typedef enum {
   STP_PRECISION_BF16X3 = 2,
   STP_PRECISION_FP16X2 = 3,
   STP_PRECISION_FP16X3 = 4,
-  STP_PRECISION_FP32 = 5
+  STP_PRECISION_FP32 = 5,
+  STP_PRECISION_FF = 6
 } stp_precision;
 
 /* Select the precision used by later stp_predict / stp_predict_host calls on

@@ -160,7 +160,7 @@ def stp_last_error() -> str:
     return load().stp_last_error().decode()
 
 
-PRECISIONS = {"fp64": 0, "bf16x2": 1, "bf16x3": 2, "fp16x2": 3, "fp16x3": 4, "fp32": 5}
+PRECISIONS = {"fp64": 0, "bf16x2": 1, "bf16x3": 2, "fp16x2": 3, "fp16x3": 4, "fp32": 5, "ff": 6}
 
 
 def stp_set_precision(h: int, precision) -> None:

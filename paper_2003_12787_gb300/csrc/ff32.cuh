@@ -15,8 +15,10 @@
 //
 // Conversions between double and float-float use integer operations on the
 // IEEE-754 encodings, not the FP64 pipe: on this GPU a float<->double
-// conversion costs as much as a DFMA. Values below the FP32 normal range
-// (|x| < 2^-126) are treated as zero; values above it become infinite.
+// conversion costs as much as a DFMA. They take a power-of-two scale 2^sc
+// (exact): split(x, sc) represents x * 2^-sc, widen(f, sc) returns f * 2^sc.
+// Scaled values below the FP32 normal range (2^-126) are treated as zero;
+// values above it become infinite.
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -73,8 +75,14 @@ __device__ __forceinline__ float make_f(uint32_t sign, int bexp, uint32_t mant) 
   return __uint_as_float(sign | ((uint32_t)bexp << 23) | (mant & 0x7fffffu));
 }
 
-// double -> float-float, hi + lo = x to within 2^-46 |x| (normalised).
-__device__ __forceinline__ float2 split(double x) {
+// Biased exponent field of a double (0 for zero and subnormals, 2047 for
+// infinities and NaN).
+__device__ __forceinline__ int exponent_field(double x) {
+  return (int)(((uint64_t)__double_as_longlong(x) >> 52) & 0x7ff);
+}
+
+// double -> float-float of x * 2^-sc, to within 2^-46 of it (normalised).
+__device__ __forceinline__ float2 split(double x, int sc = 0) {
   const uint64_t b = (uint64_t)__double_as_longlong(x);
   const uint32_t sign = (uint32_t)(b >> 32) & 0x80000000u;
   const int ex = (int)((b >> 52) & 0x7ff);
@@ -82,7 +90,7 @@ __device__ __forceinline__ float2 split(double x) {
   if (ex == 0x7ff) {  // infinity or NaN
     return make_float2(__uint_as_float(sign | 0x7f800000u | (m ? 0x400000u : 0u)), 0.f);
   }
-  const int fe = ex - 1023 + 127;  // biased float exponent of hi
+  const int fe = ex - 1023 - sc + 127;  // biased float exponent of hi
   if (ex == 0 || fe <= 0) return make_float2(__uint_as_float(sign), 0.f);
   if (fe >= 255) return make_float2(__uint_as_float(sign | 0x7f800000u), 0.f);
   const float hi = make_f(sign, fe, (uint32_t)(m >> 29));  // top 23 mantissa bits (truncated)
@@ -99,20 +107,28 @@ __device__ __forceinline__ float2 split(double x) {
   return fast_two_sum(hi, lo);
 }
 
-// float -> double, exact for normal floats (subnormals give zero).
-__device__ __forceinline__ double widen(float f) {
+// float * 2^sc -> double, exact for normal floats (subnormals give zero).
+__device__ __forceinline__ double widen(float f, int sc = 0) {
   const uint32_t u = __float_as_uint(f);
-  const uint32_t e = (u >> 23) & 0xffu;
+  const int e = (int)((u >> 23) & 0xffu);
   const uint64_t sign = (uint64_t)(u & 0x80000000u) << 32;
-  if (e == 0) return __longlong_as_double((long long)sign);
-  if (e == 0xff) return __longlong_as_double((long long)(sign | 0x7ff0000000000000ull |
-                                                         ((uint64_t)(u & 0x7fffffu) << 29)));
-  return __longlong_as_double((long long)(sign | ((uint64_t)(e - 127 + 1023) << 52) |
-                                          ((uint64_t)(u & 0x7fffffu) << 29)));
+  const uint64_t mant = (uint64_t)(u & 0x7fffffu) << 29;
+  if (e == 0xff) return __longlong_as_double((long long)(sign | 0x7ff0000000000000ull | mant));
+  const int de = e - 127 + 1023 + sc;
+  if (e == 0 || de <= 0) return __longlong_as_double((long long)sign);
+  if (de >= 0x7ff) return __longlong_as_double((long long)(sign | 0x7ff0000000000000ull));
+  return __longlong_as_double((long long)(sign | ((uint64_t)de << 52) | mant));
 }
 
-// float-float -> double: one FP64 addition of the exactly widened parts.
-__device__ __forceinline__ double to_double(float2 x) { return widen(x.x) + widen(x.y); }
+// float-float * 2^sc -> double: one FP64 addition of the exactly widened parts.
+__device__ __forceinline__ double to_double(float2 x, int sc = 0) { return widen(x.x, sc) + widen(x.y, sc); }
+
+// Scale exponent for a block of values: the largest finite exponent field
+// (folded in by every thread, then reduced), minus the bias, so that the
+// largest magnitude scales into [1, 2); 0 for an all-zero block.
+__device__ __forceinline__ int scale_from_field(int max_field) {
+  return max_field == 0 ? 0 : max_field - 1023;
+}
 
 }  // namespace ff
 }  // namespace stp

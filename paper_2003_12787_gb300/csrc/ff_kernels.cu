@@ -1,0 +1,177 @@
+// Float-float variant of the Space-Time Predictor (precision STP_PRECISION_FF).
+//
+// Same Taylor bookkeeping as the FP64 kernels: r_0 = q,
+// r_{k+1} = dt/(k+2) * L r_k with L q = -sum_d B_d (D_d q)/dx, and the time
+// average of Eq. (exahypeTimeAverage) divided by dt is sum_{k=0..N} r_k, with
+// the face projections of Sec. II-B. Every step runs in float-float
+// arithmetic (ff32.cuh: about 48 significant bits, error-free TwoSum /
+// TwoProduct transformations and Dot2 dot products) on the FP32 pipes; FP64
+// instructions remain only in the one addition per output value that turns a
+// float-float result into a double. On GB300 one FP64 instruction takes the
+// issue capacity of about 64 FP32 ones, so emulating the extra precision
+// costs less than running the contractions in FP64. The paper's kernels are
+// FP64 throughout; this variant is an addition.
+//
+// Structure (eo_ff.cuh): one CTA per element, the element's current term in
+// shared memory as float-float p[quantity][node]; per step three even-odd
+// direction passes (Sec. IV, SplitCK) add each line's derivatives into nine
+// per-node accumulators, then a pointwise pass forms the new term, adds it to
+// the node's running average (registers, or the output buffer as scratch)
+// and overwrites p.
+#include "eo_ff.cuh"
+#include "stp_internal.h"
+
+namespace stp {
+namespace {
+
+template <int N, int NT, int USE, int MINB, bool AVG_REG>
+__global__ void __launch_bounds__(NT, MINB)
+ff_eo_kernel(const double* __restrict__ q, const double* __restrict__ params,
+             double* __restrict__ out_avg, double* __restrict__ out_faces,
+             const double* __restrict__ tables, int64_t E) {
+  using Sh = EoFfShape<N>;
+  constexpr int N3 = Sh::N3, S = Sh::S, RX = Sh::RX, PLANE = Sh::PLANE, ST = Sh::STEP_TABLE;
+  constexpr int M = kQuantities;
+  constexpr int NODES = (N3 + USE - 1) / USE;
+  auto pad = [](int n) { return (n / (N * N)) * PLANE + ((n / N) % N) * RX + n % N; };
+  extern __shared__ float2 smem_ff[];
+  float2* sT = smem_ff;            // [N][ST] even-odd tables of every step
+  float2* sPhi = sT + N * ST;      // phi0[N], phi1[N]
+  float2* sp = sPhi + 2 * N;       // p[9][S]; the average at the end
+  float2* sacc = sp + M * S;       // acc[9][S]
+  const int tid = threadIdx.x;
+  const int64_t e = blockIdx.x;
+  double* gavg = out_avg + e * (int64_t)(M * N3);
+  float2* gpark = reinterpret_cast<float2*>(gavg);  // running average when not in registers
+
+  for (int i = tid; i < N * ST; i += NT) {
+    const int k = i / ST;
+    sT[i] = ff::split(eo_table_entry<N>(tables + k * N * N, i - k * ST));
+  }
+  for (int i = tid; i < 2 * N; i += NT) sPhi[i] = ff::split(tables[N3 + i]);
+  const int sc = load_state_ff<N, NT>(q + e * (int64_t)(M * N3), sp);
+
+  float2 cf[NODES][4], avg[AVG_REG ? NODES : 1][M];
+  const double* pe = params + e * (int64_t)(kParams * N3);
+#pragma unroll
+  for (int j = 0; j < NODES; ++j) {
+    const int n = tid + j * USE;
+    if (tid >= USE || n >= N3) continue;
+    elastic_coefficients_ff(__ldg(pe + 3 * n), __ldg(pe + 3 * n + 1), __ldg(pe + 3 * n + 2), cf[j]);
+    const int pn = pad(n);
+#pragma unroll
+    for (int s = 0; s < M; ++s) {
+      if (AVG_REG) avg[j][s] = sp[s * S + pn];
+      else gpark[n * M + s] = sp[s * S + pn];
+    }
+  }
+
+  for (int k = 0; k < N; ++k) {
+    const float2* T = sT + k * ST;
+#pragma unroll 1
+    for (int pass = 0; pass < 3; ++pass) {
+      eo_pass_ff<N>(sp, sacc, T, pass, tid, USE);
+      __syncthreads();
+    }
+    // pointwise: new term of the owned nodes, running average, overwrite p
+    // (every read of p in this step is done)
+#pragma unroll
+    for (int j = 0; j < NODES; ++j) {
+      const int n = tid + j * USE;
+      if (tid >= USE || n >= N3) continue;
+      const int pn = pad(n);
+      float2 g[9], r[9];
+#pragma unroll
+      for (int c = 0; c < 9; ++c) g[c] = sacc[c * S + pn];
+      eo_pointwise_ff(g, cf[j][0], cf[j][1], cf[j][2], cf[j][3], r);
+#pragma unroll
+      for (int s = 0; s < M; ++s) {
+        if (AVG_REG) avg[j][s] = ff::add(avg[j][s], r[s]);
+        else gpark[n * M + s] = ff::add(gpark[n * M + s], r[s]);
+        if (k + 1 < N) sp[s * S + pn] = r[s];
+      }
+    }
+    __syncthreads();
+  }
+
+  // time average to the output (FP64) and into shared memory for the faces
+#pragma unroll
+  for (int j = 0; j < NODES; ++j) {
+    const int n = tid + j * USE;
+    if (tid >= USE || n >= N3) continue;
+    const int pn = pad(n);
+#pragma unroll
+    for (int s = 0; s < M; ++s) {
+      const float2 v = AVG_REG ? avg[j][s] : gpark[n * M + s];
+      sp[s * S + pn] = v;
+      gavg[n * M + s] = ff::to_double(v, sc);
+    }
+  }
+  __syncthreads();
+  double* fe = out_faces + e * (int64_t)(6 * N * N * M);
+  for (int o = tid; o < 6 * N * N * M; o += NT) {
+    const int s = o % M;
+    int rest = o / M;
+    const int bb = rest % N;
+    rest /= N;
+    const int aa = rest % N;
+    const int f = rest / N;
+    const int d = f >> 1;
+    const float2* phi = sPhi + (f & 1) * N;
+    int base, stride;
+    if (d == 0) { base = aa * PLANE + bb * RX; stride = 1; }
+    else if (d == 1) { base = aa * PLANE + bb; stride = RX; }
+    else { base = aa * RX + bb; stride = PLANE; }
+    ff::Dot a;
+#pragma unroll
+    for (int i = 0; i < N; ++i) a.fma(phi[i], sp[s * S + base + i * stride]);
+    fe[o] = ff::to_double(a.value(), sc);
+  }
+}
+
+template <int N, int NT, int USE, int MINB, bool AVG_REG>
+cudaError_t launch_ff_eo(int64_t E, const double* q, const double* params, double* out_avg,
+                         double* out_faces, const double* tables, cudaStream_t stream) {
+  using Sh = EoFfShape<N>;
+  constexpr size_t smem = sizeof(float2) * (size_t)(N * Sh::STEP_TABLE + 2 * N + 18 * Sh::S);
+  static_assert(smem <= 232448, "shared memory budget of one CTA exceeded");
+  static_assert(USE <= NT && NT <= 1024, "bad thread counts");
+  auto kern = ff_eo_kernel<N, NT, USE, MINB, AVG_REG>;
+  cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (err != cudaSuccess) return err;
+  if (E > 0x7fffffffLL) return cudaErrorInvalidValue;
+  if (E == 0) return cudaSuccess;
+  kern<<<(unsigned)E, NT, smem, stream>>>(q, params, out_avg, out_faces, tables, E);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+// Launch shape per N: (N, threads, working threads, CTAs per SM the registers
+// are sized for, running average in registers).
+#define STP_FF_SHAPES(X)                                                                       \
+  X(2, 32, 24, 16, true) X(3, 32, 27, 16, true) X(4, 96, 96, 8, true) X(5, 160, 150, 4, true) \
+  X(6, 256, 216, 1, true) X(7, 160, 147, 3, false) X(8, 576, 576, 1, true)                    \
+  X(9, 512, 486, 1, false) X(10, 640, 600, 1, false) X(11, 384, 363, 1, false)
+
+bool ff_supported(int N) {
+  switch (N) {
+#define X(n, nt, use, minb, ar) case n: return true;
+    STP_FF_SHAPES(X)
+#undef X
+    default: return false;
+  }
+}
+
+cudaError_t launch_ff(int N, int64_t E, const double* q, const double* params, double* out_avg,
+                      double* out_faces, const double* tables, cudaStream_t stream) {
+  switch (N) {
+#define X(n, nt, use, minb, ar) \
+  case n: return launch_ff_eo<n, nt, use, minb, ar>(E, q, params, out_avg, out_faces, tables, stream);
+    STP_FF_SHAPES(X)
+#undef X
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+}  // namespace stp

@@ -24,152 +24,15 @@
 // centro-antisymmetric on the symmetric Gauss-Legendre nodes, so a line of N
 // outputs costs about N^2/2 + 2N operations). One CTA owns one element; the
 // element's current term lives in shared memory as p[quantity][node].
-#include "ck_fp64.cuh"
-#include "ff32.cuh"
-#include "stp_internal.h"
+#include "eo_ff.cuh"
 
 namespace stp {
 namespace {
 
-// Step 0: three direction passes add each line's derivatives into nine
-// per-node float-float accumulators in shared memory, then a pointwise pass
-// forms r_1 from the accumulators and the node's elastic coefficients (or,
-// with PERNODE0, each thread forms r_1 of its nodes directly from p, for N
-// where the accumulators do not fit). Steps 1..N-1: the three passes run at
-// once, each writing its own FP32 partial arrays, so one barrier separates
-// the passes from the pointwise update.
-template <int N, bool PERNODE0 = false>
-struct Fp32EoShape {
-  static constexpr int N3 = N * N * N;
-  static constexpr int RX = N | 1;  // x rows padded to an odd length (banks)
-  static constexpr int PLANE = N * RX;
-  static constexpr int S = (N * PLANE) | 1;
-  static constexpr int H = N / 2;
-  static constexpr bool ODD = (N & 1) != 0;
-  // per step: E[H][H], O[H][H], middle column (rows < H) and middle-row odd part (odd N)
-  static constexpr int STEP_TABLE = 2 * H * H + (ODD ? 2 * H : 0);
-  // FP32 tables: the same with rows padded to a multiple of 4 (16-byte loads)
-  static constexpr int HP = (H + 3) & ~3;
-  static constexpr int STEP32 = 2 * H * HP + (ODD ? 2 * HP : 0);
-  // floats first: FP32 tables of steps 0..N-1 (row 0 unused); then 8-byte
-  // float-float entries: step-0 table, phi0, phi1, and an area of 18 S
-  // entries holding p[9][S] and acc[9][S] in float-float for step 0, then
-  // p[9][S] and 18 partial-derivative arrays [18][S] in FP32, then the
-  // average in float-float
-  // With PERNODE0, step 0 runs node by node from p alone (no accumulators):
-  // the step-0 table is the full N x LDD matrix and the area only needs
-  // max(9 S pairs, 27 S floats).
-  static constexpr int LDD = N | 1;
-  static constexpr int TABLE0 = PERNODE0 ? N * LDD : STEP_TABLE;
-  static constexpr int AREA = PERNODE0 ? (27 * S + 1) / 2 : 18 * S;
-  static constexpr int PAIRS = TABLE0 + 2 * N + AREA;
-  static constexpr size_t SMEM = sizeof(float) * (size_t)(N * STEP32) + sizeof(float2) * (size_t)PAIRS;
-  static_assert((N * STEP32) % 4 == 0, "FP32 tables keep the doubles 16-byte aligned");
-};
-
-__device__ __forceinline__ double fmx(double a, double b, double c) { return fma(a, b, c); }
-__device__ __forceinline__ float fmx(float a, float b, float c) { return fmaf(a, b, c); }
-
-// Entry r of the even-odd table of one step matrix Dk (N x N, row-major), in FP64.
-template <int N>
-__device__ __forceinline__ double eo_table_entry(const double* __restrict__ Dk, int r) {
-  constexpr int H = N / 2, mid = H;
-  if (r < 2 * H * H) {
-    const int which = r / (H * H), i = (r / H) % H, l = r % H;
-    const double a = Dk[i * N + l], b = Dk[i * N + (N - 1 - l)];
-    return which == 0 ? 0.5 * (a + b) : 0.5 * (a - b);
-  }
-  const int rr = r - 2 * H * H;  // odd N only
-  if (rr < H) return Dk[rr * N + mid];
-  const int l = rr - H;
-  return 0.5 * (Dk[mid * N + l] - Dk[mid * N + (N - 1 - l)]);
-}
-
-// Accumulator slots: 0..2 velocity sums, 3 s12, 4 s13, 5 s23, 6 dv1/dx,
-// 7 dv2/dy, 8 dv3/dz. Quantity q6 of pass d (x, y, z) and its accumulator.
-__device__ __forceinline__ int eo32_qty(int pass, int q6) {
-  if (q6 >= 3) return q6 - 3;
-  return pass == 0 ? (q6 == 0 ? kS11 : q6 == 1 ? kS12 : kS13)
-       : pass == 1 ? (q6 == 0 ? kS12 : q6 == 1 ? kS22 : kS23)
-                   : (q6 == 0 ? kS13 : q6 == 1 ? kS23 : kS33);
-}
-__device__ __forceinline__ int eo32_acc(int pass, int q6) {
-  if (q6 < 3) return q6;
-  return pass == 0 ? (q6 == 3 ? 6 : q6 == 4 ? 3 : 4)
-       : pass == 1 ? (q6 == 3 ? 3 : q6 == 4 ? 7 : 5)
-                   : (q6 == 3 ? 4 : q6 == 4 ? 5 : 8);
-}
-__device__ __forceinline__ bool eo32_first(int pass, int acc) {
-  if (acc <= 2) return pass == 0;
-  if (acc == 3 || acc == 4) return pass == 0;
-  if (acc == 5) return pass == 1;
-  return true;
-}
-
-// One direction pass of step 0 in float-float over the 6 N^2 lines of the
-// quantities it couples (threads tid < use); the first contribution to an
-// accumulator is written, later ones added.
-template <int N>
-__device__ __forceinline__ void eo_pass_ff(const float2* __restrict__ sp, float2* __restrict__ sacc,
-                                           const float2* __restrict__ T, int pass, int tid, int use) {
-  using Sh = Fp32EoShape<N>;
-  constexpr int S = Sh::S, H = Sh::H, RX = Sh::RX, PLANE = Sh::PLANE, mid = H;
-  constexpr bool ODD = Sh::ODD;
-  const float2* E = T;
-  const float2* O = E + H * H;
-  const float2* Dm = O + H * H;
-  const float2* Om = Dm + H;
-  for (int task = tid; task < (tid < use ? 6 * N * N : 0); task += use) {
-    const int q6 = task / (N * N);
-    const int a = (task / N) % N, b = task % N;
-    const int s = eo32_qty(pass, q6), acc = eo32_acc(pass, q6);
-    int base, stride;
-    if (pass == 0) { base = a * PLANE + b * RX; stride = 1; }
-    else if (pass == 1) { base = a * PLANE + b; stride = RX; }
-    else { base = a * RX + b; stride = PLANE; }
-    const float2* u = sp + s * S + base;
-    float2 ev[H > 0 ? H : 1], od[H > 0 ? H : 1];
-#pragma unroll
-    for (int l = 0; l < H; ++l) {
-      const float2 lo = u[l * stride], hi = u[(N - 1 - l) * stride];
-      ev[l] = ff::add(lo, hi);
-      od[l] = ff::sub(lo, hi);
-    }
-    float2 out[N];
-#pragma unroll
-    for (int i = 0; i < H; ++i) {
-      ff::Dot P, Q;
-#pragma unroll
-      for (int l = 0; l < H; ++l) {
-        P.fma(E[i * H + l], ev[l]);
-        Q.fma(O[i * H + l], od[l]);
-      }
-      if (ODD) P.fma(Dm[i], u[mid * stride]);
-      const float2 pv = P.value(), qv = Q.value();
-      out[i] = ff::add(pv, qv);
-      out[N - 1 - i] = ff::sub(qv, pv);
-    }
-    if (ODD) {
-      ff::Dot Q;
-#pragma unroll
-      for (int l = 0; l < H; ++l) Q.fma(Om[l], od[l]);
-      out[mid] = Q.value();
-    }
-    float2* dst = sacc + acc * S + base;
-    if (eo32_first(pass, acc)) {
-#pragma unroll
-      for (int i = 0; i < N; ++i) dst[i * stride] = out[i];
-    } else {
-#pragma unroll
-      for (int i = 0; i < N; ++i) dst[i * stride] = ff::add(dst[i * stride], out[i]);
-    }
-  }
-}
-
 // Entry r of the padded FP32 table of one step (zeros in the padding).
 template <int N>
 __device__ __forceinline__ float eo_table_entry32(const double* __restrict__ Dk, int r) {
-  using Sh = Fp32EoShape<N>;
+  using Sh = EoFfShape<N>;
   constexpr int H = Sh::H, HP = Sh::HP;
   int row, col, src;
   if (r < 2 * H * HP) {
@@ -192,7 +55,7 @@ __device__ __forceinline__ float eo_table_entry32(const double* __restrict__ Dk,
 template <int N, int QPT>
 __device__ __forceinline__ void eo32_passes(const float* __restrict__ sp, float* __restrict__ spart,
                                             const float* __restrict__ T, int tid, int use) {
-  using Sh = Fp32EoShape<N>;
+  using Sh = EoFfShape<N>;
   constexpr int S = Sh::S, H = Sh::H, HP = Sh::HP, RX = Sh::RX, PLANE = Sh::PLANE, mid = H;
   constexpr bool ODD = Sh::ODD;
   constexpr int G = 6 / QPT;
@@ -214,7 +77,7 @@ __device__ __forceinline__ void eo32_passes(const float* __restrict__ sp, float*
     float ev[QPT][HP], od[QPT][HP], um[QPT];
 #pragma unroll
     for (int qi = 0; qi < QPT; ++qi) {
-      const float* u = sp + eo32_qty(pass, grp * QPT + qi) * S + base;
+      const float* u = sp + eo_qty(pass, grp * QPT + qi) * S + base;
 #pragma unroll
       for (int l = 0; l < HP; ++l) {
         if (l < H) {
@@ -276,7 +139,7 @@ __device__ __forceinline__ void eo32_passes(const float* __restrict__ sp, float*
 }
 
 // The nine accumulator values of node pn from the 18 partial arrays (slot
-// order of eo32_acc; passes added in x, y, z order).
+// order of eo_acc; passes added in x, y, z order).
 __device__ __forceinline__ void eo32_gather(const float* __restrict__ spart, int S, int pn, float g[9]) {
   auto P = [&](int pass, int q6) { return spart[(pass * 6 + q6) * S + pn]; };
 #pragma unroll
@@ -289,110 +152,20 @@ __device__ __forceinline__ void eo32_gather(const float* __restrict__ spart, int
   g[8] = P(2, 5);
 }
 
-// New term of one node from its nine accumulators (slot order above).
-template <typename R>
-__device__ __forceinline__ void eo_pointwise(const R g[9], R invrho, R lam, R mu, R mu2, R r[9]) {
-  const R ltr = lam * ((g[6] + g[7]) + g[8]);
+// New term of one node in FP32 from its nine accumulators (slot order of
+// eo_acc).
+__device__ __forceinline__ void eo_pointwise32(const float g[9], float invrho, float lam, float mu,
+                                               float mu2, float r[9]) {
+  const float ltr = lam * ((g[6] + g[7]) + g[8]);
   r[kV1] = invrho * g[0];
   r[kV2] = invrho * g[1];
   r[kV3] = invrho * g[2];
-  r[kS11] = fmx(mu2, g[6], ltr);
-  r[kS22] = fmx(mu2, g[7], ltr);
-  r[kS33] = fmx(mu2, g[8], ltr);
+  r[kS11] = fmaf(mu2, g[6], ltr);
+  r[kS22] = fmaf(mu2, g[7], ltr);
+  r[kS33] = fmaf(mu2, g[8], ltr);
   r[kS12] = mu * g[3];
   r[kS13] = mu * g[4];
   r[kS23] = mu * g[5];
-}
-
-// New term of one node in float-float.
-__device__ __forceinline__ void eo_pointwise_ff(const float2 g[9], float2 invrho, float2 lam,
-                                                float2 mu, float2 mu2, float2 r[9]) {
-  const float2 ltr = ff::mul(lam, ff::add(ff::add(g[6], g[7]), g[8]));
-  r[kV1] = ff::mul(invrho, g[0]);
-  r[kV2] = ff::mul(invrho, g[1]);
-  r[kV3] = ff::mul(invrho, g[2]);
-  r[kS11] = ff::add(ff::mul(mu2, g[6]), ltr);
-  r[kS22] = ff::add(ff::mul(mu2, g[7]), ltr);
-  r[kS33] = ff::add(ff::mul(mu2, g[8]), ltr);
-  r[kS12] = ff::mul(mu, g[3]);
-  r[kS13] = ff::mul(mu, g[4]);
-  r[kS23] = ff::mul(mu, g[5]);
-}
-
-// Lame coefficients (1/rho, lambda, mu, 2 mu) in float-float from FP64
-// (rho, cp, cs); 1/rho is the FP32 reciprocal refined by one Newton step.
-__device__ __forceinline__ void elastic_coefficients_ff(double rho, double cp, double cs, float2 c[4]) {
-  const float2 r = ff::split(rho), p = ff::split(cp), v = ff::split(cs);
-  const float2 cs2 = ff::mul(v, v);
-  const float2 m = ff::mul(r, cs2);
-  const float2 y0 = make_float2(1.0f / r.x, 0.f);
-  const float2 res = ff::sub(make_float2(1.f, 0.f), ff::mul(r, y0));
-  c[0] = ff::add(y0, ff::mul(y0, res));
-  c[1] = ff::mul(r, ff::sub(ff::mul(p, p), make_float2(2.f * cs2.x, 2.f * cs2.y)));
-  c[2] = m;
-  c[3] = make_float2(2.f * m.x, 2.f * m.y);
-}
-
-// The first CK step of one node in float-float (same contraction pattern as
-// the FP64 per-node step): dimension-split derivatives of the owned node from
-// the x-, y- and z-lines through it, combined with the node's coefficients.
-template <int N>
-__device__ __forceinline__ void ck_node_ff(const float2* __restrict__ p, const float2* __restrict__ D0,
-                                           int x, int y, int z, const float2 c[4], float2 r[9]) {
-  using Sh = Fp32EoShape<N, true>;
-  constexpr int S = Sh::S, RX = Sh::RX, PLANE = Sh::PLANE, LDD = Sh::LDD;
-  const float2* Dx = D0 + x * LDD;
-  const float2* Dy = D0 + y * LDD;
-  const float2* Dz = D0 + z * LDD;
-  const float2* px = p + z * PLANE + y * RX;
-  const float2* py = p + z * PLANE + x;
-  const float2* pz = p + y * RX + x;
-  ff::Dot v1, v2, v3, s12a, s12b, s13a, s13b, s23a, s23b, a, b, cc;
-#pragma unroll
-  for (int l = 0; l < N; ++l) {
-    const float2 d = Dx[l];
-    v1.fma(d, px[kS11 * S + l]);
-    v2.fma(d, px[kS12 * S + l]);
-    v3.fma(d, px[kS13 * S + l]);
-    a.fma(d, px[kV1 * S + l]);
-    s12a.fma(d, px[kV2 * S + l]);
-    s13a.fma(d, px[kV3 * S + l]);
-  }
-  ff::Dot v1y, v2y, v3y;
-#pragma unroll
-  for (int l = 0; l < N; ++l) {
-    const float2 d = Dy[l];
-    const int o = l * RX;
-    v1y.fma(d, py[kS12 * S + o]);
-    v2y.fma(d, py[kS22 * S + o]);
-    v3y.fma(d, py[kS23 * S + o]);
-    s12b.fma(d, py[kV1 * S + o]);
-    b.fma(d, py[kV2 * S + o]);
-    s23a.fma(d, py[kV3 * S + o]);
-  }
-  ff::Dot v1z, v2z, v3z;
-#pragma unroll
-  for (int l = 0; l < N; ++l) {
-    const float2 d = Dz[l];
-    const int o = l * PLANE;
-    v1z.fma(d, pz[kS13 * S + o]);
-    v2z.fma(d, pz[kS23 * S + o]);
-    v3z.fma(d, pz[kS33 * S + o]);
-    s13b.fma(d, pz[kV1 * S + o]);
-    s23b.fma(d, pz[kV2 * S + o]);
-    cc.fma(d, pz[kV3 * S + o]);
-  }
-  float2 g[9];
-  g[0] = ff::add(ff::add(v1.value(), v1y.value()), v1z.value());
-  g[1] = ff::add(ff::add(v2.value(), v2y.value()), v2z.value());
-  g[2] = ff::add(ff::add(v3.value(), v3y.value()), v3z.value());
-  g[3] = ff::add(s12a.value(), s12b.value());
-  g[4] = ff::add(s13a.value(), s13b.value());
-  g[5] = ff::add(s23a.value(), s23b.value());
-  g[6] = a.value();
-  g[7] = b.value();
-  g[8] = cc.value();
-  eo_pointwise_ff(g, c[0], c[1], c[2], c[3], r);
 }
 
 // One element (e < E) by a CTA of NT threads, the first USE doing the work;
@@ -402,7 +175,7 @@ __global__ void __launch_bounds__(NT, MINB)
 fp32_eo_kernel(const double* __restrict__ q, const double* __restrict__ params,
                double* __restrict__ out_avg, double* __restrict__ out_faces,
                const double* __restrict__ tables, int64_t E) {
-  using Sh = Fp32EoShape<N, PERNODE0>;
+  using Sh = EoFfShape<N, PERNODE0>;
   constexpr int N3 = Sh::N3, S = Sh::S, RX = Sh::RX, PLANE = Sh::PLANE, ST = Sh::STEP_TABLE;
   constexpr int ST32 = Sh::STEP32;
   constexpr int M = kQuantities;
@@ -435,12 +208,7 @@ fp32_eo_kernel(const double* __restrict__ q, const double* __restrict__ params,
     sTf[i] = eo_table_entry32<N>(tables + k * N * N, i - k * ST32);
   }
   for (int i = tid; i < 2 * N; i += NT) sPhi[i] = ff::split(tables[N3 + i]);
-  const double* qe = q + e * (int64_t)(M * N3);
-  for (int f = tid; f < M * N3; f += NT) {  // coalesced AoS read, SoA scatter
-    const int n = f / M, s = f - n * M;
-    sp[s * S + pad(n)] = ff::split(__ldg(qe + f));
-  }
-  __syncthreads();
+  const int sc = load_state_ff<N, NT, PERNODE0>(q + e * (int64_t)(M * N3), sp);
 
   // step 0 in float-float
   if (!PERNODE0) {
@@ -503,7 +271,7 @@ fp32_eo_kernel(const double* __restrict__ q, const double* __restrict__ params,
       const int pn = pad(n);
       float g[9], rn[9];
       eo32_gather(spart, S, pn, g);
-      eo_pointwise<float>(g, cf[j][0], cf[j][1], cf[j][2], cf[j][3], rn);
+      eo_pointwise32(g, cf[j][0], cf[j][1], cf[j][2], cf[j][3], rn);
 #pragma unroll
       for (int s = 0; s < M; ++s) {
         acc[j][s] += rn[s];
@@ -523,7 +291,7 @@ fp32_eo_kernel(const double* __restrict__ q, const double* __restrict__ params,
     for (int s = 0; s < M; ++s) {
       const float2 v = ff::add(gpark[n * M + s], make_float2(acc[j][s], 0.f));
       sp[s * S + pn] = v;
-      gavg[n * M + s] = ff::to_double(v);
+      gavg[n * M + s] = ff::to_double(v, sc);
     }
   }
   __syncthreads();
@@ -544,14 +312,14 @@ fp32_eo_kernel(const double* __restrict__ q, const double* __restrict__ params,
     ff::Dot a;
 #pragma unroll
     for (int i = 0; i < N; ++i) a.fma(phi[i], sp[s * S + base + i * stride]);
-    fe[o] = ff::to_double(a.value());
+    fe[o] = ff::to_double(a.value(), sc);
   }
 }
 
 template <int N, int NT, int USE, int QPT, int MINB, bool PERNODE0>
 cudaError_t launch_fp32_eo(int64_t E, const double* q, const double* params, double* out_avg,
                            double* out_faces, const double* tables, cudaStream_t stream) {
-  constexpr size_t smem = Fp32EoShape<N, PERNODE0>::SMEM;
+  constexpr size_t smem = EoFfShape<N, PERNODE0>::SMEM;
   static_assert(smem <= 232448, "shared memory budget of one CTA exceeded");
   static_assert(USE <= NT && NT <= 1024, "bad thread counts");
   auto kern = fp32_eo_kernel<N, NT, USE, QPT, MINB, PERNODE0>;

@@ -100,6 +100,8 @@ cudaError_t launch_configured(stp_handle h, int64_t E, const double* q, const do
     return stp::launch_fp64(h->N, E, q, params, avg, faces, h->d_tables, stream);
   if (h->precision == STP_PRECISION_FP32)
     return stp::launch_fp32(h->N, E, q, params, avg, faces, h->d_tables, stream);
+  if (h->precision == STP_PRECISION_FF)
+    return stp::launch_ff(h->N, E, q, params, avg, faces, h->d_tables, stream);
   return stp::launch_mixed(h->N, (int)h->precision, E, q, params, avg, faces, h->d_tables,
                            h->d_tables + stp::table_offset_D(h->N), h->dt / h->dx, h->eD,
                            h->d_status, stream);
@@ -303,8 +305,10 @@ stp_status stp_predict_host(stp_handle h, int64_t elements, const double* q, con
 
 stp_status stp_set_precision(stp_handle h, stp_precision p) {
   if (!h) return fail(STP_ERR_INVALID_ARG, "invalid handle");
-  if (p < STP_PRECISION_FP64 || p > STP_PRECISION_FP32)
+  if (p < STP_PRECISION_FP64 || p > STP_PRECISION_FF)
     return fail(STP_ERR_INVALID_ARG, "unknown precision");
+  if (p == STP_PRECISION_FF && h->N >= 2 && !stp::ff_supported(h->N))
+    return fail(STP_ERR_UNSUPPORTED, "the float-float variant covers 2 <= N <= 11");
   h->precision = p;
   return STP_OK;
 }

@@ -54,6 +54,12 @@ cudaError_t launch_mixed(int N, int variant, int64_t E, const double* q, const d
 cudaError_t launch_fp32(int N, int64_t E, const double* q, const double* params, double* out_avg,
                         double* out_faces, const double* tables, cudaStream_t stream);
 
+// Float-float variant (ff_kernels.cu): every step in float-float on the FP32
+// pipes; the orders it covers are those for which ff_supported(N) is true.
+bool ff_supported(int N);
+cudaError_t launch_ff(int N, int64_t E, const double* q, const double* params, double* out_avg,
+                      double* out_faces, const double* tables, cudaStream_t stream);
+
 // Batched persistent FP64 launch (batch.cu).
 struct BatchPlan;
 // Candidate shapes of order N for the batched kernel; fills epc_out[v] with
