@@ -191,14 +191,18 @@ def oracle_baseline(prob_q, prob_params, h, dt, budget_s: float, max_elems: int)
     return done, spent, oracle.num_threads()
 
 
-def mixed_comparison(stp, torch, args):
-    """Mixed vs FP64 at fixed error on the order-9 workload (N=10, 16384
-    elements): per precision, the CUDA-event time of one launch (mean of
-    args.mixed_steps after 3 warm-ups) and the max normwise error of avg and
-    the six face arrays against the oracle on a sample of elements."""
+PRECISIONS_ALL = ("fp64", "ff", "fp32", "bf16x2", "bf16x3", "fp16x2", "fp16x3")
+
+
+def mixed_comparison(stp, torch, args, workload="order9", precisions=PRECISIONS_ALL):
+    """Reduced-precision variants vs FP64 at their measured error on one
+    workload (default: order 9, N=10, 16384 elements): per precision, the
+    CUDA-event time of one launch (mean of args.mixed_steps after 3 warm-ups)
+    and the max normwise error of avg and the six face arrays against the
+    oracle on a sample of elements."""
     import oracle
     from paper_2003_12787_gb300.inputs import elastic_problem
-    N, grid, h, desc = WORKLOADS["order9"]
+    N, grid, h, desc = WORKLOADS[workload]
     prob = elastic_problem(N, grid=grid, h=h, device="cuda")
     E = prob.E
     rng = np.random.default_rng(4)
@@ -210,7 +214,7 @@ def mixed_comparison(stp, torch, args):
            "error": "max over avg and 6 face arrays of max|gpu-oracle|/max|oracle|, "
                     f"{len(idx)} sampled elements", "variants": {}}
     stream = torch.cuda.current_stream()
-    for prec in ("fp64", "bf16x2", "bf16x3", "fp16x2", "fp16x3", "fp32"):
+    for prec in precisions:
         P = stp.Predictor(N - 1, prob.h, prob.dt, precision=prec)
         avg, faces = P.empty_outputs(E)
         for _ in range(3):
@@ -295,7 +299,9 @@ def served_measurement(stp, torch, args):
     Poisson arrivals at args.served_rate req/s (seed 1006), each picking a
     simulation uniformly. args.served_warmup requests are replayed first; then
     args.served_requests are timed. Latency = completion seen by the scheduler
-    minus arrival."""
+    minus arrival. A second trace (args.served_sub_requests, seed 1007) then
+    runs on the same server at 0.7x the throughput the first one measured, so
+    that its latency is service time rather than queueing."""
     from paper_2003_12787_gb300.inputs import elastic_problem, served_arrivals, served_recipe
     recipe = served_recipe(e_max=args.served_emax)
     budget = int(args.served_budget_gb * (1 << 30))
@@ -309,32 +315,42 @@ def served_measurement(stp, torch, args):
         srv.add_sim(P, prob.q, prob.params)
         preds.append(P)
         del prob
-    n_w, n_m = args.served_warmup, args.served_requests
-    t, ids = served_arrivals(n_w + n_m, rate=args.served_rate, n_sims=len(recipe))
-    srv.run_trace(t[:n_w] - t[0], ids[:n_w])
-    before = srv.stats()
-    t_m = t[n_w:] - t[n_w]
-    lat, wall = srv.run_trace(t_m, ids[n_w:])
-    after = srv.stats()
     E = np.array([r["E"] for r in recipe])
-    elems = int(E[ids[n_w:]].sum())
-    launches = after["launches"] - before["launches"]
+
+    def timed_trace(rate, n_w, n_m, seed):
+        t, ids = served_arrivals(n_w + n_m, rate=rate, n_sims=len(recipe), seed=seed)
+        if n_w:
+            srv.run_trace(t[:n_w] - t[0], ids[:n_w])
+        before = srv.stats()
+        t_m = t[n_w:] - t[n_w]
+        lat, wall = srv.run_trace(t_m, ids[n_w:])
+        after = srv.stats()
+        launches = after["launches"] - before["launches"]
+        return {"rate_req_s": rate, "requests": n_m, "warmup_requests": n_w,
+                "p50_ms": float(np.percentile(lat, 50) * 1e3),
+                "p99_ms": float(np.percentile(lat, 99) * 1e3),
+                "mean_ms": float(lat.mean() * 1e3), "wall_s": wall,
+                "throughput_req_s": n_m / wall,
+                "element_updates_per_s": int(E[ids[n_w:]].sum()) / wall,
+                "offered_req_s": n_m / float(t_m[-1]) if n_m > 1 else None,
+                "launches": launches, "mean_batch": n_m / max(1, launches),
+                "admissions": after["admissions"] - before["admissions"],
+                "evictions": after["evictions"] - before["evictions"],
+                "pool_peak_gb": after["pool_bytes_peak"] / 2 ** 30,
+                "launch_device_s": (after["kernel_us"] - before["kernel_us"]) / 1e6}
+
+    main = timed_trace(args.served_rate, args.served_warmup, args.served_requests, 1006)
     out = {"workload": "256 simulations, orders 3-9 (N=4..10), "
                        f"64-{args.served_emax} elements each (log-uniform, seed 1005), "
                        f"Poisson {args.served_rate:g} req/s (seed 1006), one FP64 STP step per request",
            "hbm_budget_gb": args.served_budget_gb, "slots": args.served_slots,
-           "requests": n_m, "warmup_requests": n_w,
            "total_state_gb": float(sum(8 * r["E"] * (21 * r["N"] ** 3 + 54 * r["N"] ** 2)
-                                       for r in recipe) / 2 ** 30),
-           "p50_ms": float(np.percentile(lat, 50) * 1e3), "p99_ms": float(np.percentile(lat, 99) * 1e3),
-           "mean_ms": float(lat.mean() * 1e3), "wall_s": wall,
-           "throughput_req_s": n_m / wall, "element_updates_per_s": elems / wall,
-           "offered_req_s": n_m / float(t_m[-1]) if n_m > 1 else None,
-           "launches": launches, "mean_batch": n_m / max(1, launches),
-           "admissions": after["admissions"] - before["admissions"],
-           "evictions": after["evictions"] - before["evictions"],
-           "pool_peak_gb": after["pool_bytes_peak"] / 2 ** 30,
-           "launch_device_s": (after["kernel_us"] - before["kernel_us"]) / 1e6}
+                                       for r in recipe) / 2 ** 30), **main}
+    if args.served_sub_requests > 0:
+        # the same server below its measured capacity, so that latency is
+        # service time rather than queueing (arrivals seed 1007)
+        out["below_capacity"] = timed_trace(0.7 * main["throughput_req_s"], 0,
+                                            args.served_sub_requests, 1007)
     srv.close()
     for P in preds:
         P.close()
@@ -424,9 +440,11 @@ def run_gpu(args):
         if not np.array_equal(ah[:4].numpy(), avg[:4].cpu().numpy()):
             e2e["mismatch_vs_device_path"] = True
 
-    mixed = None
+    mixed = variants7 = None
     if rank == 0 and world == 1 and not args.no_mixed:
         mixed = mixed_comparison(stp, torch, args)
+        variants7 = mixed_comparison(stp, torch, args, workload=args.workload,
+                                     precisions=("fp64", "ff", "fp32"))
     batched = None
     if rank == 0 and world == 1 and not args.no_batched:
         batched = batched_measurement(stp, torch, args)
@@ -453,7 +471,7 @@ def run_gpu(args):
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms_max / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": {"fp64": "f64", "fp32": "f32+f64"}.get(args.precision, f"{args.precision}+f32+f64"),
+            "dtype": {"fp64": "f64", "fp32": "f32+ff32", "ff": "ff32"}.get(args.precision, f"{args.precision}+f32+f64"),
             "data": "synthetic",
             "config": {"workload": desc, "N": N, "order": N - 1, "elements": E,
                        "elements_per_gpu": E, "dt": prob.dt, "dx": prob.h,
@@ -470,7 +488,7 @@ def run_gpu(args):
                          "hbm_gbs": E * bytes_per_element(N) / mean_step_s / 1e9},
             "latency_ms": {"p50": statistics.median(step_ms), "p99": p99,
                            "min": min(step_ms), "max": max(step_ms)},
-            "e2e": e2e, "cpu_baseline": cpu, "clocks": clocks, "mixed": mixed,
+            "e2e": e2e, "cpu_baseline": cpu, "clocks": clocks, "mixed": mixed, "variants_same_workload": variants7,
             "batched": batched, "served": served,
             "gpu_launches": args.steps, "parity_max_rel_sampled": parity,
         }
@@ -529,7 +547,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-mixed", action="store_true",
-                    help="skip the mixed-vs-FP64 comparison on the order-9 workload")
+                    help="skip the precision-variant comparisons (order-9 workload and the timed workload)")
     ap.add_argument("--mixed-steps", type=int, default=5)
     ap.add_argument("--no-batched", action="store_true",
                     help="skip the batched 64-set workload")
@@ -538,13 +556,15 @@ def main():
                     help="largest set of the batched workload (smaller for profiler captures)")
     ap.add_argument("--no-served", action="store_true", help="skip the served workload")
     ap.add_argument("--served-rate", type=float, default=2000.0)
-    ap.add_argument("--served-requests", type=int, default=2000)
-    ap.add_argument("--served-warmup", type=int, default=200)
+    ap.add_argument("--served-requests", type=int, default=20000)
+    ap.add_argument("--served-warmup", type=int, default=1000)
+    ap.add_argument("--served-sub-requests", type=int, default=5000,
+                    help="requests of the second trace at 0.7x the measured capacity (0: skip)")
     ap.add_argument("--served-emax", type=int, default=2048)
-    ap.add_argument("--served-budget-gb", type=float, default=4.0)
+    ap.add_argument("--served-budget-gb", type=float, default=2.0)
     ap.add_argument("--served-slots", type=int, default=3)
     ap.add_argument("--precision", default="fp64",
-                    choices=["fp64", "bf16x2", "bf16x3", "fp16x2", "fp16x3", "fp32"],
+                    choices=list(PRECISIONS_ALL),
                     help="arithmetic of the timed workload (default fp64)")
     ap.add_argument("--cpu-budget", type=float, default=10.0,
                     help="seconds of oracle time for cpu_baseline")

@@ -14,7 +14,13 @@
 //      have more requests;
 //   2. admits ready simulations into the pool (first-fit sub-allocation);
 //      when the budget is exhausted it evicts idle simulations, least
-//      recently used first, copying their state back to pinned host memory;
+//      recently used first, copying their state and last faces back to
+//      pinned host memory. Evictions (device to host) and admissions (host
+//      to device: state and material; the faces are not copied in, since the
+//      launch that follows every admission overwrites them and reads drain
+//      first) run on two copy streams, so the two directions overlap; an
+//      admission waits for the evictions issued before it (its memory may be
+//      theirs, and a re-admitted simulation's host copy must be complete);
 //   3. launches up to 128 ready, resident simulations as ONE persistent
 //      batched FP64 launch on a free slot (its own stream and scratch).
 // New requests therefore join the next launch while earlier launches are
@@ -129,8 +135,10 @@ struct Server {
   std::vector<Sim> sims;
   std::vector<Slot> slots;
   std::deque<int> ready;  // simulations with a request, not running, FIFO
-  cudaStream_t copy_stream = nullptr;
+  cudaStream_t copy_stream = nullptr;   // admissions (host to device)
+  cudaStream_t evict_stream = nullptr;  // evictions (device to host)
   cudaEvent_t copy_done = nullptr;
+  cudaEvent_t evict_done = nullptr;
   Clock::time_point t0 = Clock::now();
   int64_t tick = 0;
   // statistics
@@ -156,9 +164,13 @@ struct Server {
 
   cudaError_t evict(int i) {
     Sim& s = sims[i];
-    cudaError_t e = cudaMemcpyAsync(s.host_q, state(s, s.cur), s.bytes_state, cudaMemcpyDeviceToHost, copy_stream);
+    cudaError_t e = cudaMemcpyAsync(s.host_q, state(s, s.cur), s.bytes_state, cudaMemcpyDeviceToHost, evict_stream);
     if (e == cudaSuccess && s.have_faces)
-      e = cudaMemcpyAsync(s.host_faces, faces(s), s.bytes_faces, cudaMemcpyDeviceToHost, copy_stream);
+      e = cudaMemcpyAsync(s.host_faces, faces(s), s.bytes_faces, cudaMemcpyDeviceToHost, evict_stream);
+    // later admissions (which may reuse this memory or re-admit this
+    // simulation) start after these copies
+    if (e == cudaSuccess) e = cudaEventRecord(evict_done, evict_stream);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(copy_stream, evict_done, 0);
     if (e != cudaSuccess) return e;
     pool.release(s.off, s.footprint());
     s.resident = false;
@@ -192,8 +204,6 @@ struct Server {
     *err = cudaMemcpyAsync(state(s, 0), s.host_q, s.bytes_state, cudaMemcpyHostToDevice, copy_stream);
     if (*err == cudaSuccess)
       *err = cudaMemcpyAsync(params(s), s.host_params, s.bytes_params, cudaMemcpyHostToDevice, copy_stream);
-    if (*err == cudaSuccess && s.have_faces)
-      *err = cudaMemcpyAsync(faces(s), s.host_faces, s.bytes_faces, cudaMemcpyHostToDevice, copy_stream);
     *copied = true;
     ++admissions;
     peak_used = std::max(peak_used, pool.used());
@@ -317,8 +327,11 @@ struct Server {
       if (s.stream) cudaStreamDestroy(s.stream);
     }
     if (copy_stream) cudaStreamSynchronize(copy_stream);
+    if (evict_stream) cudaStreamSynchronize(evict_stream);
     if (copy_done) cudaEventDestroy(copy_done);
+    if (evict_done) cudaEventDestroy(evict_done);
     if (copy_stream) cudaStreamDestroy(copy_stream);
+    if (evict_stream) cudaStreamDestroy(evict_stream);
     for (Sim& s : sims) {
       cudaFreeHost(s.host_q);
       cudaFreeHost(s.host_params);
@@ -337,6 +350,8 @@ cudaError_t server_create(int64_t budget, int nslots, Server** out) {
   cudaError_t e = cudaMalloc(&s->pool_base, std::max<size_t>(s->budget, kAlign));
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->copy_stream, cudaStreamNonBlocking);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->copy_done, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->evict_stream, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->evict_done, cudaEventDisableTiming);
   s->slots.resize(nslots);
   for (Slot& sl : s->slots) {
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&sl.stream, cudaStreamNonBlocking);
@@ -433,6 +448,7 @@ cudaError_t server_read(Server* s, int id, double* q, double* faces, int64_t* st
   cudaError_t e = server_drain(s);
   if (e != cudaSuccess) return e;
   if ((e = cudaStreamSynchronize(s->copy_stream)) != cudaSuccess) return e;
+  if ((e = cudaStreamSynchronize(s->evict_stream)) != cudaSuccess) return e;
   if (sim.resident) {
     if (q && (e = cudaMemcpy(q, s->state(sim, sim.cur), sim.bytes_state, cudaMemcpyDeviceToHost)) != cudaSuccess)
       return e;
