@@ -151,8 +151,8 @@ cudaError_t launch_ff_eo(int64_t E, const double* q, const double* params, doubl
 // are sized for, running average in registers).
 #define STP_FF_SHAPES(X)                                                                       \
   X(2, 32, 24, 16, true) X(3, 32, 27, 16, true) X(4, 96, 96, 8, true) X(5, 160, 150, 4, true) \
-  X(6, 256, 216, 1, true) X(7, 160, 147, 3, false) X(8, 576, 576, 1, true)                    \
-  X(9, 512, 486, 1, false) X(10, 640, 600, 1, false) X(11, 384, 363, 1, false)
+  X(6, 256, 216, 1, true) X(7, 352, 343, 2, true) X(8, 384, 384, 2, true)                     \
+  X(9, 768, 729, 1, true) X(10, 1024, 1000, 1, true) X(11, 736, 726, 1, false)
 
 bool ff_supported(int N) {
   switch (N) {
