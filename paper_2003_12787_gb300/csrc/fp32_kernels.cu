@@ -338,7 +338,7 @@ cudaError_t launch_fp32_eo(int64_t E, const double* q, const double* params, dou
 #define STP_FP32_SHAPES(X)                                                                        \
   X(2, 32, 24, 1, 16, false) X(3, 32, 27, 2, 16, false) X(4, 96, 96, 1, 8, false)                \
   X(5, 160, 150, 1, 6, false) X(6, 256, 216, 1, 1, false) X(7, 160, 147, 2, 4, false)            \
-  X(8, 576, 576, 1, 1, false) X(9, 512, 486, 2, 1, false) X(10, 640, 600, 2, 1, false)           \
+  X(8, 384, 384, 1, 2, false) X(9, 768, 729, 1, 1, false) X(10, 1024, 1000, 2, 1, false)         \
   X(11, 384, 363, 2, 1, false) X(12, 448, 432, 2, 1, true)
 
 cudaError_t launch_fp32(int N, int64_t E, const double* q, const double* params, double* out_avg,
