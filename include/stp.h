@@ -121,8 +121,7 @@ stp_status stp_predict_host(stp_handle h, int64_t elements, const double* q,
  *   STP_PRECISION_FF
  *       every step in float-float on the FP32 pipes (about 48 significant
  *       bits): results agree with the FP64 kernel to about 1e-13 relative,
- *       several times faster on a GPU whose FP64 rate is low. 2 <= N <= 11
- *       (stp_set_precision returns STP_ERR_UNSUPPORTED for N = 12).
+ *       several times faster on a GPU whose FP64 rate is low.
  * FP32 and FF scale each element's state by a power of two (exact) so that
  * its largest magnitude is about 1; within an element, values more than
  * 2^126 below that largest magnitude contribute as zero.

@@ -220,10 +220,11 @@ __device__ __forceinline__ void ck_node_ff(const float2* __restrict__ p, const f
 // magnitude lie in [1, 2) (L is linear, so the scale carries through every
 // step and is undone when the results are converted back). Called by all NT
 // threads (NT a multiple of 32); returns sc; ends with a barrier.
-template <int N, int NT, bool PERNODE0 = false>
-__device__ __forceinline__ int load_state_ff(const double* __restrict__ qe, float2* sp) {
-  using Sh = EoFfShape<N, PERNODE0>;
-  constexpr int N3 = Sh::N3, S = Sh::S, RX = Sh::RX, PLANE = Sh::PLANE, M = kQuantities;
+// (load_state_ff_layout: the same for any quantity stride S and row/plane
+// strides RX, PLANE.)
+template <int N, int NT, int S, int RX, int PLANE>
+__device__ __forceinline__ int load_state_ff_layout(const double* __restrict__ qe, float2* sp) {
+  constexpr int N3 = N * N * N, M = kQuantities;
   static_assert(NT % 32 == 0 && NT <= 1024, "whole warps");
   __shared__ int s_field[32];
   double* spd = reinterpret_cast<double*>(sp);  // the same bytes, first as doubles
@@ -250,6 +251,12 @@ __device__ __forceinline__ int load_state_ff(const double* __restrict__ qe, floa
   }
   __syncthreads();
   return sc;
+}
+
+template <int N, int NT, bool PERNODE0 = false>
+__device__ __forceinline__ int load_state_ff(const double* __restrict__ qe, float2* sp) {
+  using Sh = EoFfShape<N, PERNODE0>;
+  return load_state_ff_layout<N, NT, Sh::S, Sh::RX, Sh::PLANE>(qe, sp);
 }
 
 }  // namespace stp

@@ -308,7 +308,7 @@ stp_status stp_set_precision(stp_handle h, stp_precision p) {
   if (p < STP_PRECISION_FP64 || p > STP_PRECISION_FF)
     return fail(STP_ERR_INVALID_ARG, "unknown precision");
   if (p == STP_PRECISION_FF && h->N >= 2 && !stp::ff_supported(h->N))
-    return fail(STP_ERR_UNSUPPORTED, "the float-float variant covers 2 <= N <= 11");
+    return fail(STP_ERR_UNSUPPORTED, "no float-float kernel for this order");
   h->precision = p;
   return STP_OK;
 }

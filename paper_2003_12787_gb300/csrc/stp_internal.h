@@ -55,7 +55,7 @@ cudaError_t launch_fp32(int N, int64_t E, const double* q, const double* params,
                         double* out_faces, const double* tables, cudaStream_t stream);
 
 // Float-float variant (ff_kernels.cu): every step in float-float on the FP32
-// pipes; the orders it covers are those for which ff_supported(N) is true.
+// pipes; ff_supported(N) is true for 2 <= N <= 12.
 bool ff_supported(int N);
 cudaError_t launch_ff(int N, int64_t E, const double* q, const double* params, double* out_avg,
                       double* out_faces, const double* tables, cudaStream_t stream);

@@ -2,7 +2,7 @@
 FP32 pipes) against the FP64 oracle.
 
 Stated bar: normwise relative error (max|gpu - oracle| / max|oracle| per
-output array) <= 1e-12 for 2 <= N <= 11, the same bar as the FP64 kernel.
+output array) <= 1e-12 for 2 <= N <= 12, the same bar as the FP64 kernel.
 The float-float significand has about 48 bits (2^-48 = 3.6e-15); the
 contractions add a few units of that per step.
 
@@ -56,7 +56,7 @@ def errors(avg, faces, a_ref, f_ref):
     return [rel(avg, a_ref)] + [rel(faces[:, f], f_ref[:, f]) for f in range(6)]
 
 
-@pytest.mark.parametrize("N", list(range(2, 12)))
+@pytest.mark.parametrize("N", list(range(2, 13)))
 def test_ff_parity_every_order(N):
     prob = elastic_problem(N, grid=(32, 32, 16), h=1.0 / 32, E=5,
                            seed_material=500 + N, seed_waves=600 + N)
@@ -106,8 +106,19 @@ def test_ff_host_path_matches_device_path():
     assert np.array_equal(avg_h.numpy(), avg_d) and np.array_equal(faces_h.numpy(), faces_d)
 
 
-def test_ff_order_11_is_unsupported():
-    with stp.Predictor(11, 0.1, 0.001) as P:
+def test_ff_order_11_slot_body_matches_its_own_host_path_and_scaling():
+    """N = 12 runs the slot-reusing body: ragged count, host path, exact scaling."""
+    prob = elastic_problem(12, E=3, seed_material=71, seed_waves=72)
+    a0, f0 = run(prob, "ff")
+    a1, f1 = run(prob, "ff", q=prob.q * 2.0 ** -300)
+    assert np.array_equal(a1, a0 * 2.0 ** -300) and np.array_equal(f1, f0 * 2.0 ** -300)
+    with stp.Predictor(11, prob.h, prob.dt, precision="ff") as P:
+        avg_h, faces_h = P.predict_host(prob.q.pin_memory(), prob.params.pin_memory())
+    assert np.array_equal(avg_h.numpy(), a0) and np.array_equal(faces_h.numpy(), f0)
+
+
+def test_ff_unknown_precision_value_is_rejected():
+    with stp.Predictor(5, 0.1, 0.001) as P:
         with pytest.raises(stp.STPError):
-            stp.stp_set_precision(P.handle, "ff")
+            stp.stp_set_precision(P.handle, 7)
         assert stp.stp_get_precision(P.handle) == 0
