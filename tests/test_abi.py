@@ -125,3 +125,16 @@ def test_binding_fails_loudly_without_library(monkeypatch, tmp_path):
     monkeypatch.setattr(_binding, "_lib", None)
     with pytest.raises(RuntimeError, match="no CPU fallback"):
         _binding.load()
+
+
+def test_binding_precision_names_match_the_header_enum():
+    text = open(os.path.join(ROOT, "include", "stp.h")).read()
+    body = text[text.index("typedef enum {\n  STP_PRECISION_FP64"):text.index("} stp_precision;")]
+    enum = {m.group(1).lower(): int(m.group(2))
+            for m in re.finditer(r"STP_PRECISION_(\w+)\s*=\s*(\d+)", body)}
+    assert enum == _binding.PRECISIONS
+
+
+def test_set_precision_rejects_null_handle(lib):
+    assert lib.stp_set_precision(None, 0) == _binding.STP_ERR_INVALID_ARG
+    assert lib.stp_get_precision(None) == 0
