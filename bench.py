@@ -242,6 +242,40 @@ def mixed_comparison(stp, torch, args, workload="order9", precisions=PRECISIONS_
     return out
 
 
+def small_case_latency(stp, torch, args):
+    """The small order-3 workload (N=4, 8^3 = 512 elements, 31 MFLOP): a
+    latency-bound launch. Per launch, the device time (CUDA events around
+    it) and the host launch-to-done time (stp_predict call to stream
+    synchronisation), 5 warm-ups then args.small_launches timed; p50/p99."""
+    from paper_2003_12787_gb300.inputs import elastic_problem
+    N, grid, h, desc = WORKLOADS["order3"]
+    prob = elastic_problem(N, grid=grid, h=h, device="cuda")
+    stream = torch.cuda.current_stream()
+    dev, host = [], []
+    with stp.Predictor(N - 1, prob.h, prob.dt) as P:
+        avg, faces = P.empty_outputs(prob.E)
+        for i in range(5 + args.small_launches):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            e0.record(stream)
+            P.predict(prob.q, prob.params, out=(avg, faces), stream=stream)
+            e1.record(stream)
+            stream.synchronize()
+            t1 = time.perf_counter()
+            if i >= 5:
+                dev.append(e0.elapsed_time(e1) * 1e3)
+                host.append((t1 - t0) * 1e6)
+
+    def pct(v, p):
+        return float(np.percentile(np.array(v), p))
+    return {"workload": desc, "launches": args.small_launches,
+            "device_us": {"p50": pct(dev, 50), "p99": pct(dev, 99)},
+            "launch_to_done_us": {"p50": pct(host, 50), "p99": pct(host, 99)},
+            "elements_per_s_p50": prob.E / (pct(dev, 50) * 1e-6)}
+
+
 def batched_measurement(stp, torch, args):
     """The batched workload (64 sets, orders 3-11, 64-16384 elements each,
     seed 1003) as one persistent launch replayed from a CUDA graph: time per
@@ -445,6 +479,9 @@ def run_gpu(args):
         mixed = mixed_comparison(stp, torch, args)
         variants7 = mixed_comparison(stp, torch, args, workload=args.workload,
                                      precisions=("fp64", "ff", "fp32"))
+    small = None
+    if rank == 0 and world == 1 and args.small_launches > 0:
+        small = small_case_latency(stp, torch, args)
     batched = None
     if rank == 0 and world == 1 and not args.no_batched:
         batched = batched_measurement(stp, torch, args)
@@ -489,7 +526,7 @@ def run_gpu(args):
             "latency_ms": {"p50": statistics.median(step_ms), "p99": p99,
                            "min": min(step_ms), "max": max(step_ms)},
             "e2e": e2e, "cpu_baseline": cpu, "clocks": clocks, "mixed": mixed, "variants_same_workload": variants7,
-            "batched": batched, "served": served,
+            "small_case": small, "batched": batched, "served": served,
             "gpu_launches": args.steps, "parity_max_rel_sampled": parity,
         }
         print(json.dumps(line), flush=True)
@@ -555,6 +592,8 @@ def main():
     ap.add_argument("--batched-emax", type=int, default=16384,
                     help="largest set of the batched workload (smaller for profiler captures)")
     ap.add_argument("--no-served", action="store_true", help="skip the served workload")
+    ap.add_argument("--small-launches", type=int, default=50,
+                    help="timed launches of the order-3 latency measurement (0: skip)")
     ap.add_argument("--served-rate", type=float, default=2000.0)
     ap.add_argument("--served-requests", type=int, default=20000)
     ap.add_argument("--served-warmup", type=int, default=1000)
