@@ -270,6 +270,40 @@ def test_brute_force_dense_operator(N):
                 assert ref.rel_err(faces[e, 2 * d + side], fx) <= 1e-13
 
 
+@pytest.mark.parametrize("N", [2, 3])
+def test_truncation_error_order(N):
+    """The STP average is the degree-N Taylor truncation of the exact time
+    average of the semi-discrete system, (1/dt) int_0^dt exp(t L) q dt =
+    phi_1(dt L) q (matrix exponential of an augmented matrix, scipy). Its
+    error is led by the first omitted term, dt^(N+1)/(N+2)! L^(N+1) q, so
+    halving dt divides it by about 2^(N+1). A dropped or extra Taylor term,
+    or a wrong weight, changes that exponent. Sanity check of the scheme,
+    independent of the oracle's own series."""
+    from scipy.linalg import expm
+    rng = np.random.default_rng(31 + N)
+    params = random_params(1, N, rng)
+    q = rng.uniform(-1, 1, (1, N, N, N, 9))
+    h = 0.5
+    L = ref.dense_operator(N, h, params[0])
+    v = q[0].reshape(-1)
+    n = v.size
+    rho = max(abs(np.linalg.eigvals(L)))
+
+    def exact_average(dt):
+        aug = np.zeros((n + 1, n + 1))
+        aug[:n, :n] = dt * L
+        aug[:n, n] = v
+        return expm(aug)[:n, n]  # = phi_1(dt L) v
+
+    errs = []
+    for dt in (0.4 / rho, 0.2 / rho):
+        avg, _ = oracle.stp(q, params, h=h, dt=dt)
+        errs.append(np.abs(avg[0].reshape(-1) - exact_average(dt)).max() / np.abs(v).max())
+    assert errs[1] > 1e-13  # above rounding, so the ratio measures truncation
+    ratio = errs[0] / errs[1]
+    assert 0.6 * 2 ** (N + 1) < ratio < 1.4 * 2 ** (N + 1), (errs, ratio)
+
+
 @pytest.mark.parametrize("K", [1, 2, 4])
 def test_term_count_parameter(K):
     N = 3
