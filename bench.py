@@ -310,6 +310,37 @@ def batched_measurement(stp, torch, args):
     for P, _, _ in items:
         if P.N not in tuned:
             tuned[P.N] = stp.stp_autotune(P.handle)
+    # the same sets in the float-float and FP32 variants: a graph of per-set
+    # launches; error of element 0 of every set against the oracle
+    import oracle
+    refs = [oracle.stp(q[:1].cpu().numpy(), pr[:1].cpu().numpy(), P.dx, P.dt) for P, q, pr in items]
+    variants = {}
+    for prec in ("ff", "fp32"):
+        for P, _, _ in items:
+            stp.stp_set_precision(P.handle, prec)
+        bv = stp.Batch(items)
+        bv.launch(stream)
+        v0 = torch.cuda.Event(enable_timing=True)
+        v1 = torch.cuda.Event(enable_timing=True)
+        v0.record(stream)
+        for _ in range(args.batch_steps):
+            bv.launch(stream)
+        v1.record(stream)
+        torch.cuda.synchronize()
+        vms = v0.elapsed_time(v1) / args.batch_steps
+        err = 0.0
+        for i, (a_ref, f_ref) in enumerate(refs):
+            a, f = bv.outputs(i)
+            a = a[:1].cpu().numpy()
+            f = f[:1].cpu().numpy()
+            err = max(err, float(np.abs(a - a_ref).max() / np.abs(a_ref).max()),
+                      max(float(np.abs(f[:, j] - f_ref[:, j]).max() / np.abs(f_ref[:, j]).max())
+                          for j in range(6)))
+        variants[prec] = {"ms_per_launch": vms, "speedup_vs_fp64_plan": ms / vms,
+                          "max_rel_err_element0_of_every_set": err}
+        bv.close()
+    for P, _, _ in items:
+        stp.stp_set_precision(P.handle, "fp64")
     out = {"workload": "64 element sets, orders 3-11 (N=4..12), "
                        f"64-{args.batched_emax} elements each "
                        "(log-uniform, seed 1003), one persistent launch from a CUDA graph",
@@ -317,6 +348,7 @@ def batched_measurement(stp, torch, args):
            "elements_per_s": elems / (ms / 1e3), "tflops_algorithmic": flops / (ms / 1e3) / 1e12,
            "frac_fp64_peak": flops / (ms / 1e3) / 1e12 / FP64_PEAK_TFLOPS,
            "plan_seconds_incl_autotune": plan_s, **b.info(),
+           "variants_graph_of_launches": variants,
            "autotune": {str(n): {"variant": t["variant"],
                                  "us_per_element": [round(u, 4) for u in t["us_variants"]]}
                         for n, t in sorted(tuned.items())}}

@@ -122,6 +122,9 @@ stp_status stp_predict_host(stp_handle h, int64_t elements, const double* q,
  *       every step in float-float on the FP32 pipes (about 48 significant
  *       bits): results agree with the FP64 kernel to about 1e-13 relative,
  *       several times faster on a GPU whose FP64 rate is low.
+ * The split and FP32 variants reach about 1e-9 relative on well-resolved
+ * fields; their error grows with the size of the higher Taylor terms
+ * (coarse elements: several 1e-9). FF holds about 1e-13 on any data.
  * FP32 and FF scale each element's state by a power of two (exact) so that
  * its largest magnitude is about 1; within an element, values more than
  * 2^126 below that largest magnitude contribute as zero.
@@ -157,14 +160,15 @@ stp_status stp_device_status(stp_handle h, void* stream, unsigned int* flags);
 /*
  * Batched persistent launch: the STPs of several element sets, of different
  * orders and sizes, in ONE persistent kernel launch replayed from a CUDA
- * graph. Each set is described by an FP64 handle (order, dx, dt) and its own
+ * graph. Each set is described by a handle (order, dx, dt, precision) and its own
  * device buffers in the layouts above. The paper generates one kernel per
- * order (Sec. II-D, Sec. III); here every order's element-group body lives in
- * one kernel and a cost-sorted work list of (set, element range) units is
- * consumed by one CTA per SM.
+ * order (Sec. II-D, Sec. III); here, for FP64 sets, every order's
+ * element-group body lives in one kernel and a cost-sorted work list of
+ * (set, element range) units is consumed by one CTA per SM. Batches with
+ * other precisions replay a graph of per-set launches instead.
  */
 typedef struct {
-  stp_handle handle;   /* FP64 predictor of this set (its precision must be FP64) */
+  stp_handle handle;   /* predictor of this set (FP64 for the static and served paths) */
   int64_t elements;    /* E >= 0 */
   const double* q;     /* device [E][N][N][N][9] */
   const double* params;/* device [E][N][N][N][3] */
@@ -175,28 +179,34 @@ typedef struct {
 typedef struct stp_batch_s* stp_batch; /* opaque plan, owned by the library */
 
 /*
- * Plan a batch: autotunes (on first use of each order on the device, then
- * cached) the per-order shape of the persistent kernel, builds and uploads
- * the work list, and captures counter reset + kernel into a CUDA graph. The
- * buffers are baked into the plan: they must stay valid, unmoved, until
- * stp_batch_destroy. Outputs must not overlap any input or any other output.
- * Synchronous (allocates, copies, times). Errors: STP_ERR_INVALID_ARG for bad
- * pointers or sizes, STP_ERR_UNSUPPORTED for a handle that is not FP64 or
- * sets on different devices, STP_ERR_CUDA / STP_ERR_OOM from CUDA.
+ * Plan a batch. When every handle is FP64: autotunes (on first use of each
+ * order on the device, then cached) the per-order shape of the persistent
+ * kernel, builds and uploads the work list, and captures counter reset +
+ * kernel into a CUDA graph. When some handle has another precision: captures
+ * one launch per set (each set's own kernel, in its handle's precision at
+ * planning time) into a CUDA graph, largest sets first, over up to 8 parallel
+ * branches; results equal stp_predict's for every set. The buffers are baked
+ * into the plan: they must stay valid, unmoved, until stp_batch_destroy.
+ * Outputs must not overlap any input or any other output. Synchronous
+ * (allocates, copies, times). Errors: STP_ERR_INVALID_ARG for bad pointers or
+ * sizes, STP_ERR_UNSUPPORTED for sets on different devices, STP_ERR_CUDA /
+ * STP_ERR_OOM from CUDA.
  */
 stp_status stp_batch_create(int nsets, const stp_batch_set* sets, stp_batch* out);
 
 /* As stp_batch_create, with the shape of every set chosen by the caller:
  * shapes[i] = index of one of its order's candidate shapes (0, 1: see
  * stp_autotune), or -1 for the autotuner's choice. STP_ERR_INVALID_ARG for a
- * shape the order does not have. */
+ * shape the order does not have, or for any shape >= 0 in a batch that is not
+ * all FP64. */
 stp_status stp_batch_create_ex(int nsets, const stp_batch_set* sets, const int* shapes,
                                stp_batch* out);
 
 /* Enqueue one replay of the plan's graph on `stream` (async). */
 stp_status stp_batch_launch(stp_batch b, void* stream);
 
-/* Work units, CTAs of the persistent grid and dynamic shared memory per CTA. */
+/* Work units, CTAs of the persistent grid and dynamic shared memory per CTA
+ * (for a batch of per-set launches: the number of sets, 0, 0). */
 stp_status stp_batch_info(stp_batch b, int* units, int* ctas, int64_t* smem_bytes);
 
 /* Free the plan (after the work it enqueued has finished). NULL is a no-op. */

@@ -1,4 +1,5 @@
 // C ABI of the Space-Time Predictor library (declared in include/stp.h).
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -339,9 +340,68 @@ struct stp_server_s {
 };
 
 struct stp_batch_s {
-  stp::BatchPlan* plan = nullptr;
+  stp::BatchPlan* plan = nullptr;   // all sets FP64: one persistent launch
+  cudaGraph_t graph = nullptr;      // otherwise: one launch per set, parallel branches
+  cudaGraphExec_t exec = nullptr;
+  int nsets = 0;
   int device = -1;
 };
+
+namespace {
+
+// A graph holding one launch per set (the set's own kernel and precision),
+// largest estimated work first, spread round-robin over up to 8 parallel
+// branches so that small sets run beside large ones.
+cudaError_t capture_set_launches(int nsets, const stp_batch_set* sets, cudaGraph_t* graph) {
+  constexpr int kBranches = 8;
+  const int nb = std::max(1, std::min(kBranches, nsets));
+  std::vector<int> order(nsets);
+  std::vector<double> work(nsets);
+  for (int i = 0; i < nsets; ++i) {
+    const double n = sets[i].handle->N;
+    order[i] = i;
+    work[i] = (double)sets[i].elements * (36.0 * std::pow(n, 5) + 66.0 * std::pow(n, 4) + 108.0 * std::pow(n, 3));
+  }
+  std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return work[x] > work[y]; });
+  cudaStream_t origin = nullptr;
+  std::vector<cudaStream_t> br(nb, nullptr);
+  std::vector<cudaEvent_t> ev(nb + 1, nullptr);
+  cudaError_t e = cudaStreamCreateWithFlags(&origin, cudaStreamNonBlocking);
+  for (int b = 0; b < nb && e == cudaSuccess; ++b) e = cudaStreamCreateWithFlags(&br[b], cudaStreamNonBlocking);
+  for (int b = 0; b <= nb && e == cudaSuccess; ++b) e = cudaEventCreateWithFlags(&ev[b], cudaEventDisableTiming);
+  bool capturing = false;
+  if (e == cudaSuccess) e = cudaStreamBeginCapture(origin, cudaStreamCaptureModeThreadLocal);
+  if (e == cudaSuccess) {
+    capturing = true;
+    e = cudaEventRecord(ev[nb], origin);  // fork
+    for (int b = 0; b < nb && e == cudaSuccess; ++b) e = cudaStreamWaitEvent(br[b], ev[nb], 0);
+    for (int k = 0; k < nsets && e == cudaSuccess; ++k) {
+      const stp_batch_set& st = sets[order[k]];
+      if (st.elements > 0)
+        e = launch_configured(st.handle, st.elements, st.q, st.params, st.out_avg, st.out_faces,
+                              br[k % nb]);
+    }
+    for (int b = 0; b < nb && e == cudaSuccess; ++b) {  // join
+      e = cudaEventRecord(ev[b], br[b]);
+      if (e == cudaSuccess) e = cudaStreamWaitEvent(origin, ev[b], 0);
+    }
+  }
+  if (capturing) {
+    cudaGraph_t g = nullptr;
+    const cudaError_t ce = cudaStreamEndCapture(origin, &g);
+    if (e == cudaSuccess) e = ce;
+    if (e == cudaSuccess) *graph = g;
+    else if (g) cudaGraphDestroy(g);
+  }
+  for (cudaEvent_t x : ev)
+    if (x) cudaEventDestroy(x);
+  for (cudaStream_t x : br)
+    if (x) cudaStreamDestroy(x);
+  if (origin) cudaStreamDestroy(origin);
+  return e;
+}
+
+}  // namespace
 
 extern "C" {
 
@@ -364,8 +424,6 @@ stp_status stp_batch_create_ex(int nsets, const stp_batch_set* sets, const int* 
     const stp_batch_set& st = sets[i];
     stp_status s = validate_common(st.handle, st.elements, st.q, st.params, st.out_avg, st.out_faces);
     if (s != STP_OK) return fail(s, "set " + std::to_string(i) + ": " + g_last_error);
-    if (st.handle->precision != STP_PRECISION_FP64)
-      return fail(STP_ERR_UNSUPPORTED, "set " + std::to_string(i) + ": batched launches are FP64");
     if (st.handle->device != dev)
       return fail(STP_ERR_UNSUPPORTED, "set " + std::to_string(i) + ": handle on another device");
     if (st.elements > 0) {
@@ -401,9 +459,30 @@ stp_status stp_batch_create_ex(int nsets, const stp_batch_set* sets, const int* 
                                                  " overlap buffers of set " + std::to_string(j));
     }
   }
+  bool all_fp64 = true;
+  for (int i = 0; i < nsets; ++i)
+    if (sets[i].handle->precision != STP_PRECISION_FP64) all_fp64 = false;
   stp_batch b = new (std::nothrow) stp_batch_s;
   if (!b) return fail(STP_ERR_OOM, "host allocation failed");
   b->device = dev;
+  b->nsets = nsets;
+  if (!all_fp64) {
+    for (int i = 0; shapes && i < nsets; ++i)
+      if (shapes[i] >= 0) {
+        delete b;
+        return fail(STP_ERR_INVALID_ARG, "shapes apply to all-FP64 batches only");
+      }
+    cudaError_t e = capture_set_launches(nsets, sets, &b->graph);
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&b->exec, b->graph, 0);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      if (b->graph) cudaGraphDestroy(b->graph);
+      delete b;
+      return cuda_fail(e, "batch graph");
+    }
+    *out = b;
+    return STP_OK;
+  }
   std::vector<int> forced;
   if (shapes) {
     forced.assign(shapes, shapes + nsets);
@@ -428,14 +507,21 @@ stp_status stp_batch_create_ex(int nsets, const stp_batch_set* sets, const int* 
 }
 
 stp_status stp_batch_launch(stp_batch b, void* stream) {
-  if (!b || !b->plan) return fail(STP_ERR_INVALID_ARG, "invalid batch");
-  cudaError_t e = stp::launch_plan(b->plan, static_cast<cudaStream_t>(stream));
+  if (!b || (!b->plan && !b->exec)) return fail(STP_ERR_INVALID_ARG, "invalid batch");
+  cudaError_t e = b->plan ? stp::launch_plan(b->plan, static_cast<cudaStream_t>(stream))
+                          : cudaGraphLaunch(b->exec, static_cast<cudaStream_t>(stream));
   if (e != cudaSuccess) return cuda_fail(e, "batch graph launch");
   return STP_OK;
 }
 
 stp_status stp_batch_info(stp_batch b, int* units, int* ctas, int64_t* smem_bytes) {
-  if (!b || !b->plan) return fail(STP_ERR_INVALID_ARG, "invalid batch");
+  if (!b || (!b->plan && !b->exec)) return fail(STP_ERR_INVALID_ARG, "invalid batch");
+  if (!b->plan) {  // one launch per set
+    if (units) *units = b->nsets;
+    if (ctas) *ctas = 0;
+    if (smem_bytes) *smem_bytes = 0;
+    return STP_OK;
+  }
   size_t sm = 0;
   stp::plan_info(b->plan, units, ctas, &sm);
   if (smem_bytes) *smem_bytes = (int64_t)sm;
@@ -445,6 +531,8 @@ stp_status stp_batch_info(stp_batch b, int* units, int* ctas, int64_t* smem_byte
 stp_status stp_batch_destroy(stp_batch b) {
   if (!b) return STP_OK;
   stp::destroy_plan(b->plan);
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  if (b->graph) cudaGraphDestroy(b->graph);
   delete b;
   return STP_OK;
 }

@@ -81,6 +81,33 @@ def test_same_alone_and_in_the_mix_and_graph_replay():
     mix.close()
 
 
+def test_batch_of_other_precisions_is_a_graph_of_per_set_launches():
+    """Sets in the float-float, FP32, tensor-core and FP64 precisions in one
+    plan: every set's outputs equal its own stp_predict bit for bit, on every
+    replay; the float-float sets also meet the FP64 bar against the oracle."""
+    specs = [(4, 37), (12, 3), (7, 11), (10, 4), (9, 5), (2, 30), (11, 2), (8, 9)]
+    precisions = ["ff", "ff", "fp32", "bf16x3", "fp64", "ff", "fp32", "ff"]
+    sets = make_sets(specs)
+    for (P, _), prec in zip(sets, precisions):
+        stp.stp_set_precision(P.handle, prec)
+    b = stp.Batch([(P, prob.q, prob.params) for P, prob in sets])
+    info = b.info()
+    assert info["units"] == len(sets) and info["ctas"] == 0
+    for _ in range(2):
+        b.launch()
+        torch.cuda.synchronize()
+        for i, (P, prob) in enumerate(sets):
+            avg_b, faces_b = b.outputs(i)
+            avg_s, faces_s = P.predict(prob.q, prob.params)
+            torch.cuda.synchronize()
+            assert torch.equal(avg_b, avg_s) and torch.equal(faces_b, faces_s), (specs[i], precisions[i])
+            if precisions[i] == "ff":
+                a_ref, f_ref = oracle.stp(prob.q.cpu().numpy(), prob.params.cpu().numpy(),
+                                          prob.h, prob.dt)
+                assert rel(avg_b.cpu().numpy(), a_ref) <= 1e-12
+    b.close()
+
+
 def test_autotune_reports_candidates():
     for N in (4, 8, 12):
         with stp.Predictor(N - 1, 0.1, 1e-4) as P:
@@ -100,8 +127,10 @@ def test_batch_rejects_bad_sets():
         stp.stp_batch_create([(P.handle, 8, prob.q, prob.params, avg, faces),
                               (P.handle, 8, prob.q, prob.params, avg, faces)])
     M = stp.Predictor(3, prob.h, prob.dt, precision="bf16x3")
-    with pytest.raises(stp.STPError):  # batched launches are FP64
-        stp.stp_batch_create([(M.handle, 8, prob.q, prob.params, avg, faces)])
+    with pytest.raises(stp.STPError):  # shapes apply to all-FP64 batches only
+        stp.stp_batch_create([(M.handle, 8, prob.q, prob.params, avg, faces)], shapes=[0])
+    mixed = stp.stp_batch_create([(M.handle, 8, prob.q, prob.params, avg, faces)], shapes=[-1])
+    stp.stp_batch_destroy(mixed)
     empty = stp.stp_batch_create([(P.handle, 0, prob.q, prob.params, avg, faces)])
     stp.stp_batch_launch(empty)  # nothing to do
     stp.stp_batch_destroy(empty)
