@@ -90,8 +90,8 @@ __device__ __forceinline__ void eo_pass_ff(const float2* __restrict__ sp, float2
 #pragma unroll
     for (int l = 0; l < H; ++l) {
       const float2 lo = u[l * stride], hi = u[(N - 1 - l) * stride];
-      ev[l] = ff::add(lo, hi);
-      od[l] = ff::sub(lo, hi);
+      ev[l] = ff::add_lazy(lo, hi);
+      od[l] = ff::sub_lazy(lo, hi);
     }
     float2 out[N];
 #pragma unroll
@@ -103,15 +103,15 @@ __device__ __forceinline__ void eo_pass_ff(const float2* __restrict__ sp, float2
         Q.fma(O[i * H + l], od[l]);
       }
       if (ODD) P.fma(Dm[i], u[mid * stride]);
-      const float2 pv = P.value(), qv = Q.value();
-      out[i] = ff::add(pv, qv);
-      out[N - 1 - i] = ff::sub(qv, pv);
+      const float2 pv = P.value_lazy(), qv = Q.value_lazy();
+      out[i] = ff::add_lazy(pv, qv);
+      out[N - 1 - i] = ff::sub_lazy(qv, pv);
     }
     if (ODD) {
       ff::Dot Q;
 #pragma unroll
       for (int l = 0; l < H; ++l) Q.fma(Om[l], od[l]);
-      out[mid] = Q.value();
+      out[mid] = Q.value_lazy();
     }
     float2* dst = sacc + acc * S + base;
     if (eo_first(pass, acc)) {
@@ -119,7 +119,7 @@ __device__ __forceinline__ void eo_pass_ff(const float2* __restrict__ sp, float2
       for (int i = 0; i < N; ++i) dst[i * stride] = out[i];
     } else {
 #pragma unroll
-      for (int i = 0; i < N; ++i) dst[i * stride] = ff::add(dst[i * stride], out[i]);
+      for (int i = 0; i < N; ++i) dst[i * stride] = ff::add_lazy(dst[i * stride], out[i]);
     }
   }
 }

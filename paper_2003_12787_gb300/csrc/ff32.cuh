@@ -46,6 +46,16 @@ __device__ __forceinline__ float2 add(float2 x, float2 y) {
 __device__ __forceinline__ float2 neg(float2 x) { return make_float2(-x.x, -x.y); }
 __device__ __forceinline__ float2 sub(float2 x, float2 y) { return add(x, neg(y)); }
 
+// The same sum without the closing renormalisation: (fl(x.hi + y.hi), rest),
+// the rest a few ulp of the first part at most. Such pairs are exact-valued
+// inputs to every operation here (TwoSum and TwoProduct take any operands);
+// only a part read alone as a float needs a renormalised pair.
+__device__ __forceinline__ float2 add_lazy(float2 x, float2 y) {
+  const float2 s = two_sum(x.x, y.x);
+  return make_float2(s.x, __fadd_rn(s.y, __fadd_rn(x.y, y.y)));
+}
+__device__ __forceinline__ float2 sub_lazy(float2 x, float2 y) { return add_lazy(x, neg(y)); }
+
 __device__ __forceinline__ float2 mul(float2 x, float2 y) {
   const float p = __fmul_rn(x.x, y.x);
   float e = __fmaf_rn(x.x, y.x, -p);
@@ -68,6 +78,7 @@ struct Dot {
     c = __fadd_rn(cc, __fadd_rn(t.y, pe));
   }
   __device__ __forceinline__ float2 value() const { return fast_two_sum(s, c); }
+  __device__ __forceinline__ float2 value_lazy() const { return make_float2(s, c); }
 };
 
 // Float whose bits are sign | exponent | mantissa (no checks).

@@ -243,8 +243,8 @@ ff_slots_kernel(const double* __restrict__ q, const double* __restrict__ params,
 #pragma unroll
         for (int l = 0; l < H; ++l) {
           const float2 lo = u[l * stride], hi = u[(N - 1 - l) * stride];
-          ev[l] = ff::add(lo, hi);
-          od[l] = ff::sub(lo, hi);
+          ev[l] = ff::add_lazy(lo, hi);
+          od[l] = ff::sub_lazy(lo, hi);
         }
         float2 out[N];
 #pragma unroll
@@ -256,15 +256,15 @@ ff_slots_kernel(const double* __restrict__ q, const double* __restrict__ params,
             Q.fma(Ot[i * H + l], od[l]);
           }
           if (ODD) P.fma(Dm[i], u[mid * stride]);
-          const float2 pv = P.value(), qv = Q.value();
-          out[i] = ff::add(pv, qv);
-          out[N - 1 - i] = ff::sub(qv, pv);
+          const float2 pv = P.value_lazy(), qv = Q.value_lazy();
+          out[i] = ff::add_lazy(pv, qv);
+          out[N - 1 - i] = ff::sub_lazy(qv, pv);
         }
         if (ODD) {
           ff::Dot Q;
 #pragma unroll
           for (int l = 0; l < H; ++l) Q.fma(Om[l], od[l]);
-          out[mid] = Q.value();
+          out[mid] = Q.value_lazy();
         }
         float2* dst = slot + pick9(ac, acc) * S + base;
         if (eo_first(pass, acc)) {
@@ -272,7 +272,7 @@ ff_slots_kernel(const double* __restrict__ q, const double* __restrict__ params,
           for (int i = 0; i < N; ++i) dst[i * stride] = out[i];
         } else {
 #pragma unroll
-          for (int i = 0; i < N; ++i) dst[i * stride] = ff::add(dst[i * stride], out[i]);
+          for (int i = 0; i < N; ++i) dst[i * stride] = ff::add_lazy(dst[i * stride], out[i]);
         }
       }
       __syncthreads();
