@@ -234,7 +234,8 @@ def mixed_comparison(stp, torch, args, workload="order9", precisions=PRECISIONS_
                   [float(np.abs(f[:, i] - f_ref[:, i]).max() / np.abs(f_ref[:, i]).max())
                    for i in range(6)])
         out["variants"][prec] = {"ms_per_launch": ms, "elements_per_s": E / (ms / 1e3),
-                                 "max_rel_err": err}
+                                 "max_rel_err": err,
+                                 "tflops_algorithmic": E * flops_per_element(N) / (ms / 1e3) / 1e12}
         P.close()
     base = out["variants"]["fp64"]["ms_per_launch"]
     for v in out["variants"].values():

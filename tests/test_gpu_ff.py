@@ -90,6 +90,26 @@ def test_power_of_two_scaling_is_exact(precision, k):
     assert np.array_equal(f1, f0 * 2.0 ** k)
 
 
+@pytest.mark.parametrize("N", [4, 8, 11])
+def test_ff_rough_random_data(N):
+    """Uniform random state and material per node (no smoothness, Taylor
+    terms that do not decay): the float-float variant still meets the FP64
+    bar."""
+    rng = np.random.default_rng(2024 + N)
+    E = 6
+    q = torch.from_numpy(rng.uniform(-1, 1, (E, N, N, N, 9)))
+    params = np.stack([rng.uniform(2, 3, (E, N, N, N)), rng.uniform(4, 6, (E, N, N, N)),
+                       rng.uniform(1, 2.5, (E, N, N, N))], axis=-1)
+    h = 0.1
+    dt = 0.4 * h / ((2 * N - 1) * params[..., 1].max())
+    with stp.Predictor(N - 1, h, dt, precision="ff") as P:
+        avg, faces = P.predict(q.cuda(), torch.from_numpy(params).cuda())
+        torch.cuda.synchronize()
+    a_ref, f_ref = oracle.stp(q.numpy(), params, h, dt)
+    errs = errors(avg.cpu().numpy(), faces.cpu().numpy(), a_ref, f_ref)
+    assert max(errs) <= TOL, errs
+
+
 def test_ff_constant_state_exact():
     N, E = 9, 3
     prob = elastic_problem(N, E=E)
