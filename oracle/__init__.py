@@ -65,6 +65,12 @@ def _load():
                                        ctypes.c_void_p, ctypes.c_void_p,
                                        ctypes.c_void_p]
             lib.oracle_stp.restype = ctypes.c_int
+            lib.oracle_gll_nodes.argtypes = [ctypes.c_int, dp, dp]
+            lib.oracle_gll_nodes.restype = ctypes.c_int
+            lib.oracle_tables_nodes.argtypes = [ctypes.c_int, ctypes.c_int, dp, dp, dp, dp]
+            lib.oracle_tables_nodes.restype = ctypes.c_int
+            lib.oracle_stp_nodes.argtypes = [ctypes.c_int] + lib.oracle_stp.argtypes
+            lib.oracle_stp_nodes.restype = ctypes.c_int
             lib.oracle_num_threads.argtypes = []
             lib.oracle_num_threads.restype = ctypes.c_int
             _lib = lib
@@ -84,14 +90,28 @@ def gl_nodes(N: int):
     return xi, w
 
 
-def tables(N: int):
-    """(xi, D, phi0, phi1): nodes, D[i,j] = phi_j'(xi_i), phi_j(0), phi_j(1)."""
+def gll_nodes(N: int):
+    """Gauss-Lobatto nodes and weights on [0,1] (ascending, N >= 2)."""
+    xi = np.zeros(N)
+    w = np.zeros(N)
+    if _load().oracle_gll_nodes(N, _dptr(xi), _dptr(w)) != 0:
+        raise ValueError(f"oracle_gll_nodes failed for N={N}")
+    return xi, w
+
+
+NODE_FAMILIES = {"gl": 0, "gll": 1}
+
+
+def tables(N: int, nodes: str = "gl"):
+    """(xi, D, phi0, phi1): nodes, D[i,j] = phi_j'(xi_i), phi_j(0), phi_j(1).
+    nodes: "gl" (Gauss-Legendre) or "gll" (Gauss-Lobatto)."""
     xi = np.zeros(N)
     D = np.zeros((N, N))
     p0 = np.zeros(N)
     p1 = np.zeros(N)
-    if _load().oracle_tables(N, _dptr(xi), _dptr(D), _dptr(p0), _dptr(p1)) != 0:
-        raise ValueError(f"oracle_tables failed for N={N}")
+    if _load().oracle_tables_nodes(NODE_FAMILIES[nodes], N, _dptr(xi), _dptr(D), _dptr(p0),
+                                   _dptr(p1)) != 0:
+        raise ValueError(f"oracle_tables failed for N={N}, nodes={nodes}")
     return xi, D, p0, p1
 
 
@@ -101,11 +121,12 @@ def num_threads() -> int:
 
 
 def stp(q: np.ndarray, params: np.ndarray, h: float, dt: float, K: int | None = None,
-        return_terms: bool = False):
+        return_terms: bool = False, nodes: str = "gl"):
     """Run the oracle STP.
 
     q: [E][N][N][N][9] float64 (z,y,x,quantity); params: [E][N][N][N][3]
     (rho, cp, cs). K = number of Taylor terms q^(0..K-1), default N+1.
+    nodes: "gl" (Gauss-Legendre) or "gll" (Gauss-Lobatto).
     Returns (avg [E][N][N][N][9], faces [E][6][N][N][9]) and, with
     return_terms, every q^(k) as [E][K][N][N][N][9].
     """
@@ -120,9 +141,10 @@ def stp(q: np.ndarray, params: np.ndarray, h: float, dt: float, K: int | None = 
     avg = np.empty_like(q)
     faces = np.empty((E, 6, N, N, M))
     terms = np.empty((E, K, N, N, N, M)) if return_terms else None
-    rc = _load().oracle_stp(N, K, E, float(h), float(dt), q.ctypes.data,
-                            params.ctypes.data, avg.ctypes.data, faces.ctypes.data,
-                            terms.ctypes.data if terms is not None else None)
+    rc = _load().oracle_stp_nodes(NODE_FAMILIES[nodes], N, K, E, float(h), float(dt),
+                                  q.ctypes.data, params.ctypes.data, avg.ctypes.data,
+                                  faces.ctypes.data,
+                                  terms.ctypes.data if terms is not None else None)
     if rc != 0:
         raise RuntimeError(f"oracle_stp returned {rc}")
     if return_terms:

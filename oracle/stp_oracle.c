@@ -9,9 +9,10 @@
  * What it computes (Gallard et al., "Vectorization and Minimization of Memory
  * Footprint for Linear High-Order Discontinuous Galerkin Schemes", arXiv
  * 2003.12787):
- *   - Sec. II-A: nodal tensor-product Lagrange basis on N Gauss-Legendre nodes
- *     per dimension of the reference cube [0,1]^3; the discrete derivative
- *     operator D; N nodes per dimension ("order N" in the paper's wording).
+ *   - Sec. II-A: nodal tensor-product Lagrange basis on N Gauss-Legendre (or,
+ *     as the paper allows, Gauss-Lobatto) nodes per dimension of the
+ *     reference cube [0,1]^3; the discrete derivative operator D; N nodes per
+ *     dimension ("order N" in the paper's wording).
  *   - Eq. (exahypeTimeAverage) and the recurrence below it: the Taylor series
  *     of the cell-local solution in time, built from powers of the volume
  *     operator V applied to q(t_n): p_o = V p_{o-1}.
@@ -113,6 +114,53 @@ int oracle_gl_nodes(int N, double* xi, double* w) {
   return 0;
 }
 
+/*
+ * Gauss-Lobatto nodes xi[0..N-1] (ascending, N >= 2) and weights w on [0,1]:
+ * the end points and the N-2 roots of P_{N-1}'(2 xi - 1), each interior root
+ * bracketed by a sign change on a fine uniform grid of the open interval and
+ * bisected down to adjacent doubles. Weights: 1 / (N (N-1) P_{N-1}(t)^2) for
+ * t = 2 xi - 1 (the [-1,1] weight 2/(N(N-1) P_{N-1}(t)^2) halved).
+ * Returns 0, or -1 if fewer than N-2 interior roots were found.
+ */
+int oracle_gll_nodes(int N, double* xi, double* w) {
+  if (N < 2 || N > 64) return -1;
+  const int n = N - 1;
+  double t[64];
+  t[0] = -1.0;
+  int found = 1;
+  const int samples = 4000 * N;
+  double a = -1.0 + 1.0 / samples, fa = legendre_deriv(n, a);
+  for (int s = 1; s < samples && found < N - 1; ++s) {
+    double b = -1.0 + (2.0 * s + 1.0) / samples;  /* stays inside (-1,1) */
+    double fb = legendre_deriv(n, b);
+    if (fb == 0.0) {
+      t[found++] = b;
+      a = b; fa = fb;
+      continue;
+    }
+    if (fa != 0.0 && ((fa < 0.0) != (fb < 0.0))) {
+      double lo = a, hi = b, flo = fa;
+      for (int it = 0; it < 200; ++it) {
+        double mid = 0.5 * (lo + hi);
+        if (mid <= lo || mid >= hi) break;
+        double fm = legendre_deriv(n, mid);
+        if (fm == 0.0) { lo = hi = mid; break; }
+        if ((fm < 0.0) == (flo < 0.0)) { lo = mid; flo = fm; } else { hi = mid; }
+      }
+      t[found++] = 0.5 * (lo + hi);
+    }
+    a = b; fa = fb;
+  }
+  if (found != N - 1) return -1;
+  t[N - 1] = 1.0;
+  for (int i = 0; i < N; ++i) {
+    double p = legendre(n, t[i]);
+    if (w) w[i] = 1.0 / (N * (N - 1.0) * p * p);
+    xi[i] = 0.5 * (t[i] + 1.0);
+  }
+  return 0;
+}
+
 /* Lagrange basis phi_j(x) = prod_{l != j} (x - xi_l) / (xi_j - xi_l). */
 static double lagrange(int N, const double* xi, int j, double x) {
   double v = 1.0;
@@ -136,11 +184,18 @@ static double lagrange_deriv(int N, const double* xi, int j, double x) {
 
 /*
  * Tables of the reference element: D[i*N+j] = phi_j'(xi_i), phi0[j] = phi_j(0),
- * phi1[j] = phi_j(1). Any output pointer may be NULL.
+ * phi1[j] = phi_j(1). nodes: 0 Gauss-Legendre, 1 Gauss-Lobatto. Any output
+ * pointer may be NULL.
  */
-int oracle_tables(int N, double* xi_out, double* D, double* phi0, double* phi1) {
+int oracle_tables_nodes(int nodes, int N, double* xi_out, double* D, double* phi0, double* phi1) {
   double xi[64];
-  if (oracle_gl_nodes(N, xi, NULL) != 0) return -1;
+  if (nodes == 0) {
+    if (oracle_gl_nodes(N, xi, NULL) != 0) return -1;
+  } else if (nodes == 1) {
+    if (oracle_gll_nodes(N, xi, NULL) != 0) return -1;
+  } else {
+    return -1;
+  }
   if (xi_out) memcpy(xi_out, xi, sizeof(double) * N);
   for (int i = 0; i < N; ++i)
     for (int j = 0; j < N; ++j)
@@ -150,6 +205,11 @@ int oracle_tables(int N, double* xi_out, double* D, double* phi0, double* phi1) 
     if (phi1) phi1[j] = lagrange(N, xi, j, 1.0);
   }
   return 0;
+}
+
+/* Gauss-Legendre tables (the default node family). */
+int oracle_tables(int N, double* xi_out, double* D, double* phi0, double* phi1) {
+  return oracle_tables_nodes(0, N, xi_out, D, phi0, phi1);
 }
 
 /*
@@ -253,11 +313,11 @@ static void stp_element(int N, int K, double h, double dt, const double* D,
  * Elements are distributed over OpenMP threads when compiled with OpenMP;
  * each element's arithmetic is the same either way.
  */
-int oracle_stp(int N, int K, int64_t E, double h, double dt, const double* q,
-               const double* params, double* avg, double* faces, double* terms) {
+int oracle_stp_nodes(int nodes, int N, int K, int64_t E, double h, double dt, const double* q,
+                     const double* params, double* avg, double* faces, double* terms) {
   if (N < 1 || N > 16 || K < 1 || E < 0 || !(h > 0.0)) return -1;
   double D[16 * 16], phi0[16], phi1[16];
-  if (oracle_tables(N, NULL, D, phi0, phi1) != 0) return -1;
+  if (oracle_tables_nodes(nodes, N, NULL, D, phi0, phi1) != 0) return -1;
   const size_t n3m = (size_t)N * N * N * M;
   int err = 0;
 #pragma omp parallel
@@ -279,6 +339,12 @@ int oracle_stp(int N, int K, int64_t E, double h, double dt, const double* q,
     free(work);
   }
   return err ? -2 : 0;
+}
+
+/* The STP on Gauss-Legendre nodes (the default node family). */
+int oracle_stp(int N, int K, int64_t E, double h, double dt, const double* q,
+               const double* params, double* avg, double* faces, double* terms) {
+  return oracle_stp_nodes(0, N, K, E, h, dt, q, params, avg, faces, terms);
 }
 
 /* number of OpenMP threads the oracle runs on (1 without OpenMP) */

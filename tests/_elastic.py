@@ -7,7 +7,8 @@ Everything here is written from textbook definitions, not from the oracle:
   mapped to the quantity order (v1,v2,v3,s11,s22,s33,s12,s13,s23). It works on
   numbers or on sympy expressions.
 * ``lagrange_D_numpy``: derivative matrix from a Vandermonde solve in the
-  Legendre basis on numpy's Gauss-Legendre points (library routines only).
+  Legendre basis on numpy's Gauss-Legendre points, or on Gauss-Lobatto points
+  from numpy's Legendre-derivative roots (library routines only).
 * ``dense_operator``: the whole per-element spatial operator as a dense matrix
   assembled with Kronecker products.
 """
@@ -63,9 +64,22 @@ def gl_points(N):
     return (t + 1) / 2, w / 2
 
 
-def lagrange_D_numpy(N):
+def gll_points(N):
+    """Gauss-Lobatto points and weights on [0,1]: the end points and the roots
+    of P_{N-1}' (numpy polynomial routines), weights 1/(N(N-1) P_{N-1}(t)^2)."""
+    P = np.polynomial.legendre.Legendre.basis(N - 1)
+    t = np.concatenate([[-1.0], np.sort(P.deriv().roots().real), [1.0]]) if N > 2 else np.array([-1.0, 1.0])
+    w = 1.0 / (N * (N - 1) * P(t) ** 2)
+    return (t + 1) / 2, w
+
+
+def points(N, nodes="gl"):
+    return gl_points(N) if nodes == "gl" else gll_points(N)
+
+
+def lagrange_D_numpy(N, nodes="gl"):
     """D[i,j] = phi_j'(xi_i) via the Legendre Vandermonde matrix V[i,k]=P_k(t_i)."""
-    xi, _ = gl_points(N)
+    xi, _ = points(N, nodes)
     t = 2 * xi - 1
     V = np.polynomial.legendre.legvander(t, N - 1)
     # phi_j = sum_k C[k,j] P_k with V C = I
@@ -78,8 +92,8 @@ def lagrange_D_numpy(N):
     return dV @ C
 
 
-def lagrange_phi_numpy(N, a):
-    xi, _ = gl_points(N)
+def lagrange_phi_numpy(N, a, nodes="gl"):
+    xi, _ = points(N, nodes)
     t = 2 * xi - 1
     V = np.polynomial.legendre.legvander(t, N - 1)
     C = np.linalg.solve(V, np.eye(N))
@@ -87,12 +101,12 @@ def lagrange_phi_numpy(N, a):
     return va @ C
 
 
-def dense_operator(N, h, params):
+def dense_operator(N, h, params, nodes="gl"):
     """Dense L (9N^3 x 9N^3) of one element, state flattened as [z][y][x][s].
 
     params: [N][N][N][3] per-node (rho, cp, cs).
     """
-    D = lagrange_D_numpy(N) / h
+    D = lagrange_D_numpy(N, nodes) / h
     I = np.eye(N)
     Dd = [np.kron(np.kron(I, I), D),  # x: fastest node index
           np.kron(np.kron(I, D), I),  # y

@@ -129,7 +129,7 @@ def test_constant_state_is_steady(N):
 
 # --- terminating series: polynomial data, uniform material ------------------
 
-def _poly_case(N, rho, cp, cs, h, dt, origins, seed):
+def _poly_case(N, rho, cp, cs, h, dt, origins, seed, nodes="gl"):
     sp = pytest.importorskip("sympy")
     x, y, z = sp.symbols("x y z")
     rng = np.random.default_rng(seed)
@@ -155,7 +155,7 @@ def _poly_case(N, rho, cp, cs, h, dt, origins, seed):
                 for s in range(9)]
     q0f = [sp.lambdify((x, y, z), e, "numpy") for e in q0]
     avgf = [sp.lambdify((x, y, z), e, "numpy") for e in avg_expr]
-    xi, _ = ref.gl_points(N)
+    xi, _ = ref.points(N, nodes)
     E = len(origins)
     q = np.zeros((E, N, N, N, 9))
     avg_x = np.zeros_like(q)
@@ -314,6 +314,70 @@ def test_term_count_parameter(K):
     L = ref.dense_operator(N, 0.3, params[0])
     avg_x = ref.dense_time_average(L, q[0].reshape(-1), 0.01, K)
     assert ref.rel_err(avg[0].reshape(-1), avg_x) <= 1e-13
+
+
+# --- Gauss-Lobatto nodes (the paper's other node family, Sec. II-A) ---------
+
+def closed_form_gll(N):
+    """Gauss-Lobatto points on [-1,1] with closed forms (N <= 5)."""
+    t = {2: [-1.0, 1.0], 3: [-1.0, 0.0, 1.0],
+         4: [-1.0, -1 / math.sqrt(5), 1 / math.sqrt(5), 1.0],
+         5: [-1.0, -math.sqrt(3 / 7), 0.0, math.sqrt(3 / 7), 1.0]}[N]
+    return (np.array(t) + 1) / 2
+
+
+@pytest.mark.parametrize("N", [2, 3, 4, 5])
+def test_gll_nodes_closed_form(N):
+    xi, _ = oracle.gll_nodes(N)
+    assert np.abs(xi - closed_form_gll(N)).max() <= 2e-16
+
+
+@pytest.mark.parametrize("N", list(range(2, 13)))
+def test_gll_nodes_weights_and_quadrature(N):
+    xi, w = oracle.gll_nodes(N)
+    xr, wr = ref.gll_points(N)
+    assert np.abs(xi - xr).max() <= 1e-14 and np.abs(w - wr).max() <= 1e-14
+    assert xi[0] == 0.0 and xi[-1] == 1.0
+    for p in range(2 * N - 2):  # exact to degree 2N-3 on [0,1]
+        assert abs(np.dot(w, xi ** p) - 1.0 / (p + 1)) <= 1e-14
+
+
+@pytest.mark.parametrize("N", list(range(2, 13)))
+def test_gll_tables_exact_on_polynomials(N):
+    xi, D, p0, p1 = oracle.tables(N, "gll")
+    assert np.abs(D - ref.lagrange_D_numpy(N, "gll")).max() <= 1e-11 * max(1.0, np.abs(D).max())
+    e0 = np.zeros(N); e0[0] = 1.0
+    eN = np.zeros(N); eN[-1] = 1.0
+    assert np.array_equal(p0, e0) and np.array_equal(p1, eN)
+    for p in range(N):
+        assert np.abs(D @ xi ** p - (p * xi ** (p - 1) if p else 0 * xi)).max() <= 1e-11 * N ** 2
+
+
+@pytest.mark.parametrize("N", [2, 3, 4, 6])
+def test_gll_polynomial_data_matches_symbolic_series(N):
+    h, dt = 0.5, 0.03
+    origins = [(0.0, 0.0, 0.0), (0.5, -1.0, 1.5)]
+    q, params, avg_x, faces_x = _poly_case(N, 2.0, 3.0, 1.0, h, dt, origins, seed=40 + N,
+                                           nodes="gll")
+    avg, faces = oracle.stp(q, params, h=h, dt=dt, nodes="gll")
+    assert ref.rel_err(avg, avg_x) <= 1e-12
+    assert ref.rel_err(faces, faces_x) <= 1e-12
+    assert ref.rel_err(avg - q, avg_x - q) <= 1e-10
+
+
+@pytest.mark.parametrize("N", [2, 3])
+def test_gll_brute_force_dense_operator(N):
+    rng = np.random.default_rng(70 + N)
+    params = random_params(1, N, rng)
+    q = rng.uniform(-1, 1, (1, N, N, N, 9))
+    h, dt = 0.2, 0.004
+    avg, _ = oracle.stp(q, params, h=h, dt=dt, nodes="gll")
+    L = ref.dense_operator(N, h, params[0], "gll")
+    avg_x = ref.dense_time_average(L, q[0].reshape(-1), dt, N + 1).reshape(N, N, N, 9)
+    assert ref.rel_err(avg[0], avg_x) <= 1e-13
+    # the two families differ (so the family switch is not a no-op)
+    avg_gl, _ = oracle.stp(q, params, h=h, dt=dt)
+    assert ref.rel_err(avg_gl[0], avg_x) > 1e-8
 
 
 # --- invariants ----------------------------------------------------------------
