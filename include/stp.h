@@ -315,6 +315,24 @@ stp_status stp_server_stats(stp_server s, int64_t* stats);
 /* Finish outstanding work and free the server. NULL is a no-op. */
 stp_status stp_server_destroy(stp_server s);
 
+/* Interpolation points of the nodal basis (Sec. II-A: Gauss-Legendre or
+ * Gauss-Lobatto points). Gauss-Lobatto points include the element's end
+ * points, so the face projections phi(0), phi(1) are unit vectors. */
+typedef enum {
+  STP_NODES_GAUSS_LEGENDRE = 0,
+  STP_NODES_GAUSS_LOBATTO = 1
+} stp_node_family;
+
+/* As stp_create, on the given node family (stp_create = Gauss-Legendre).
+ * Gauss-Lobatto needs N >= 2 (order >= 1): STP_ERR_UNSUPPORTED otherwise, and
+ * for an unknown family. Every precision, the batched, allocation-free and
+ * served paths take handles of either family. */
+stp_status stp_create_nodes(int order, int m, double dx, double dt, stp_node_family nodes,
+                            stp_handle* out);
+
+/* Node family of the handle (STP_NODES_GAUSS_LEGENDRE for NULL). */
+stp_node_family stp_get_nodes(stp_handle h);
+
 /* Release the handle's device tables and buffers. NULL is a no-op (STP_OK). */
 stp_status stp_destroy(stp_handle h);
 
@@ -328,6 +346,11 @@ stp_status stp_destroy(stp_handle h);
  */
 stp_status stp_reference_tables(int order, double* nodes, double* D, double* phi0,
                                 double* phi1);
+
+/* The same tables on the given node family (STP_ERR_UNSUPPORTED for
+ * Gauss-Lobatto with order 0 or an unknown family). */
+stp_status stp_reference_tables_nodes(int order, stp_node_family family, double* nodes,
+                                      double* D, double* phi0, double* phi1);
 
 /* Nodes per dimension N of the handle, or -1 for an invalid handle. */
 int stp_nodes(stp_handle h);

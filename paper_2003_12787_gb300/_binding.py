@@ -52,6 +52,11 @@ def load():
         lib.stp_predict_host.argtypes = [vp, i64, vp, vp, vp, vp, vp]
         lib.stp_destroy.argtypes = [vp]
         lib.stp_reference_tables.argtypes = [ctypes.c_int, vp, vp, vp, vp]
+        lib.stp_create_nodes.argtypes = [ctypes.c_int, ctypes.c_int, dbl, dbl, ctypes.c_int,
+                                         ctypes.POINTER(vp)]
+        lib.stp_reference_tables_nodes.argtypes = [ctypes.c_int, ctypes.c_int, vp, vp, vp, vp]
+        lib.stp_get_nodes.argtypes = [vp]
+        lib.stp_get_nodes.restype = ctypes.c_int
         lib.stp_nodes.argtypes = [vp]
         lib.stp_nodes.restype = ctypes.c_int
         lib.stp_status_string.argtypes = [ctypes.c_int]
@@ -123,10 +128,21 @@ def _stream(stream) -> int | None:
     return stream.cuda_stream  # torch.cuda.Stream
 
 
-def stp_create(order: int, m: int, dx: float, dt: float) -> int:
+NODE_FAMILIES = {"gl": 0, "gll": 1}
+
+
+def stp_create(order: int, m: int, dx: float, dt: float, nodes="gl") -> int:
     h = ctypes.c_void_p()
-    _check(load().stp_create(order, m, dx, dt, ctypes.byref(h)), "stp_create")
+    if nodes == "gl":
+        _check(load().stp_create(order, m, dx, dt, ctypes.byref(h)), "stp_create")
+    else:
+        fam = NODE_FAMILIES[nodes] if isinstance(nodes, str) else int(nodes)
+        _check(load().stp_create_nodes(order, m, dx, dt, fam, ctypes.byref(h)), "stp_create_nodes")
     return h.value
+
+
+def stp_get_nodes(h: int) -> int:
+    return int(load().stp_get_nodes(h))
 
 
 def stp_predict(h: int, elements: int, q, params, out_avg, out_faces, stream=None) -> None:
@@ -143,9 +159,11 @@ def stp_destroy(h: int | None) -> None:
     _check(load().stp_destroy(h), "stp_destroy")
 
 
-def stp_reference_tables(order: int, nodes=None, D=None, phi0=None, phi1=None) -> None:
-    _check(load().stp_reference_tables(order, _ptr(nodes), _ptr(D), _ptr(phi0), _ptr(phi1)),
-           "stp_reference_tables")
+def stp_reference_tables(order: int, nodes=None, D=None, phi0=None, phi1=None,
+                         family="gl") -> None:
+    fam = NODE_FAMILIES[family] if isinstance(family, str) else int(family)
+    _check(load().stp_reference_tables_nodes(order, fam, _ptr(nodes), _ptr(D), _ptr(phi0),
+                                             _ptr(phi1)), "stp_reference_tables_nodes")
 
 
 def stp_nodes(h: int) -> int:

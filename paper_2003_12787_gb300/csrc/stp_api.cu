@@ -127,6 +127,11 @@ const char* stp_status_string(stp_status s) {
 const char* stp_last_error(void) { return g_last_error.c_str(); }
 
 stp_status stp_create(int order, int m, double dx, double dt, stp_handle* out) {
+  return stp_create_nodes(order, m, dx, dt, STP_NODES_GAUSS_LEGENDRE, out);
+}
+
+stp_status stp_create_nodes(int order, int m, double dx, double dt, stp_node_family nodes,
+                            stp_handle* out) {
   if (!out) return fail(STP_ERR_INVALID_ARG, "out is NULL");
   *out = nullptr;
   const int N = order + 1;
@@ -139,7 +144,15 @@ stp_status stp_create(int order, int m, double dx, double dt, stp_handle* out) {
   h->N = N;
   h->dx = dx;
   h->dt = dt;
-  if (!stp::make_tables(N, &h->host)) {
+  if (nodes != STP_NODES_GAUSS_LEGENDRE && nodes != STP_NODES_GAUSS_LOBATTO) {
+    delete h;
+    return fail(STP_ERR_UNSUPPORTED, "unknown node family");
+  }
+  if (nodes == STP_NODES_GAUSS_LOBATTO && N < 2) {
+    delete h;
+    return fail(STP_ERR_UNSUPPORTED, "Gauss-Lobatto nodes need order >= 1");
+  }
+  if (!stp::make_tables(N, &h->host, nodes)) {
     delete h;
     return fail(STP_ERR_UNSUPPORTED, "node computation did not converge");
   }
@@ -191,11 +204,20 @@ stp_status stp_destroy(stp_handle h) {
 
 int stp_nodes(stp_handle h) { return h ? h->N : -1; }
 
+stp_node_family stp_get_nodes(stp_handle h) {
+  return h ? (stp_node_family)h->host.family : STP_NODES_GAUSS_LEGENDRE;
+}
+
 stp_status stp_reference_tables(int order, double* nodes, double* D, double* phi0, double* phi1) {
+  return stp_reference_tables_nodes(order, STP_NODES_GAUSS_LEGENDRE, nodes, D, phi0, phi1);
+}
+
+stp_status stp_reference_tables_nodes(int order, stp_node_family family, double* nodes, double* D,
+                                      double* phi0, double* phi1) {
   const int N = order + 1;
   stp::HostTables t;
-  if (N < 1 || N > stp::kMaxNodes || !stp::make_tables(N, &t))
-    return fail(STP_ERR_UNSUPPORTED, "order must be in [0, 11]");
+  if (N < 1 || N > stp::kMaxNodes || !stp::make_tables(N, &t, family))
+    return fail(STP_ERR_UNSUPPORTED, "order out of range or unknown node family");
   if (nodes) std::memcpy(nodes, t.nodes, sizeof(double) * N);
   if (D) std::memcpy(D, t.D, sizeof(double) * N * N);
   if (phi0) std::memcpy(phi0, t.phi0, sizeof(double) * N);

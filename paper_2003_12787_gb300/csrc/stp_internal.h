@@ -15,15 +15,18 @@ constexpr int kMaxNodes = 12;
 // double precision, computed in extended precision (tables.cpp).
 struct HostTables {
   int N = 0;
+  int family = STP_NODES_GAUSS_LEGENDRE;
   double nodes[kMaxNodes];
   double D[kMaxNodes * kMaxNodes];  // D[i*N+j] = phi_j'(xi_i)
   double phi0[kMaxNodes];
   double phi1[kMaxNodes];
 };
 
-// Gauss-Legendre nodes, derivative matrix and face vectors. Returns false if
-// the Newton iteration did not converge (never for 1 <= N <= 12).
-bool make_tables(int N, HostTables* t);
+// Nodes (Gauss-Legendre or Gauss-Lobatto, see stp_node_family), derivative
+// matrix and face vectors. Returns false for an unknown family, Gauss-Lobatto
+// with N < 2, or a Newton iteration that did not converge (never for
+// N <= 12).
+bool make_tables(int N, HostTables* t, int family = STP_NODES_GAUSS_LEGENDRE);
 
 // Per-step scaled derivative matrices: Dk[k][i][j] = D[i][j] * dt / ((k+2) dx)
 // for k = 0..N-1, rounded once from extended precision.

@@ -1,11 +1,14 @@
 // Reference-element tables of the library (host, extended precision).
 //
-// Gauss-Legendre nodes on [0,1] (Sec. II-A: nodal Lagrange basis on
-// Gauss-Legendre points, N points per dimension), the collocation derivative
+// Nodes on [0,1] (Sec. II-A: nodal Lagrange basis on Gauss-Legendre or
+// Gauss-Lobatto points, N points per dimension), the collocation derivative
 // matrix D_ij = phi_j'(xi_i) and the face interpolation vectors phi_j(0),
-// phi_j(1). Nodes: Newton's method on the Legendre polynomial from a cosine
-// initial guess; D and phi: barycentric Lagrange formulas (Berrut & Trefethen,
-// SIAM Review 46(3), 2004), with the diagonal of D from the zero row sum.
+// phi_j(1). Gauss-Legendre nodes: Newton's method on P_N from a cosine
+// initial guess. Gauss-Lobatto nodes: the end points and Newton's method on
+// P_{N-1}' (second derivative from the Legendre equation) from the
+// Chebyshev-Lobatto points. D and phi: barycentric Lagrange formulas (Berrut
+// & Trefethen, SIAM Review 46(3), 2004), with the diagonal of D from the zero
+// row sum; phi is a unit vector where the face coincides with a node.
 // Arithmetic in long double, rounded to double once at the end.
 #include <cmath>
 
@@ -31,12 +34,43 @@ void legendre_pair(int n, ld x, ld* p, ld* dp) {
 
 }  // namespace
 
-bool make_tables(int N, HostTables* t) {
+// Gauss-Lobatto points on [-1,1], descending into x[0..N-1] (N >= 2).
+bool lobatto_points(int N, ld* x) {
+  const ld pi = 3.141592653589793238462643383279502884L;
+  const int n = N - 1;
+  x[0] = 1.0L;
+  x[N - 1] = -1.0L;
+  for (int i = 1; i < N - 1; ++i) {
+    ld r = cosl(pi * (ld)i / (ld)n);
+    bool ok = false;
+    for (int it = 0; it < 100; ++it) {
+      ld p, dp;
+      legendre_pair(n, r, &p, &dp);
+      const ld d2p = (2.0L * r * dp - (ld)n * (n + 1) * p) / (1.0L - r * r);
+      const ld step = dp / d2p;
+      r -= step;
+      if (fabsl(step) <= 4.0L * 1.1e-19L * (1.0L + fabsl(r))) { ok = true; break; }
+    }
+    if (!ok) return false;
+    x[i] = r;
+  }
+  return true;
+}
+
+bool make_tables(int N, HostTables* t, int family) {
   if (N < 1 || N > kMaxNodes) return false;
+  if (family != STP_NODES_GAUSS_LEGENDRE && family != STP_NODES_GAUSS_LOBATTO) return false;
+  if (family == STP_NODES_GAUSS_LOBATTO && N < 2) return false;
   t->N = N;
+  t->family = family;
   const ld pi = 3.141592653589793238462643383279502884L;
   ld x[kMaxNodes];
-  for (int i = 0; i < N; ++i) {
+  if (family == STP_NODES_GAUSS_LOBATTO) {
+    ld r[kMaxNodes];
+    if (!lobatto_points(N, r)) return false;
+    for (int i = 0; i < N; ++i) x[N - 1 - i] = 0.5L * (1.0L + r[i]);  // ascending on [0,1]
+  }
+  for (int i = 0; i < N && family == STP_NODES_GAUSS_LEGENDRE; ++i) {
     // i-th largest root on [-1,1]
     ld r = cosl(pi * ((ld)i + 0.75L) / ((ld)N + 0.5L));
     bool ok = false;
@@ -72,12 +106,17 @@ bool make_tables(int N, HostTables* t) {
   }
   for (int side = 0; side < 2; ++side) {
     const ld a = side ? 1.0L : 0.0L;
+    double* phi = side ? t->phi1 : t->phi0;
+    int hit = -1;
+    for (int k = 0; k < N; ++k)
+      if (x[k] == a) hit = k;
+    if (hit >= 0) {  // the face point is a node
+      for (int j = 0; j < N; ++j) phi[j] = j == hit ? 1.0 : 0.0;
+      continue;
+    }
     ld den = 0.0L;
     for (int k = 0; k < N; ++k) den += w[k] / (a - x[k]);
-    for (int j = 0; j < N; ++j) {
-      ld v = (w[j] / (a - x[j])) / den;
-      (side ? t->phi1 : t->phi0)[j] = (double)v;
-    }
+    for (int j = 0; j < N; ++j) phi[j] = (double)((w[j] / (a - x[j])) / den);
   }
   return true;
 }

@@ -52,8 +52,17 @@ class Problem:
         return self.N - 1
 
 
-def sample_points(N: int) -> np.ndarray:
-    t, _ = np.polynomial.legendre.leggauss(N)
+def sample_points(N: int, nodes: str = "gl") -> np.ndarray:
+    """Positions on [0,1] where the state is sampled: Gauss-Legendre points
+    (numpy's leggauss) or Gauss-Lobatto points (end points and the roots of
+    P_{N-1}' from numpy's Legendre class)."""
+    if nodes == "gl":
+        t, _ = np.polynomial.legendre.leggauss(N)
+    elif nodes == "gll":
+        inner = np.polynomial.legendre.Legendre.basis(N - 1).deriv().roots().real if N > 2 else []
+        t = np.concatenate([[-1.0], np.sort(inner), [1.0]])
+    else:
+        raise ValueError(f"unknown node family {nodes!r}")
     return (t + 1.0) / 2.0
 
 
@@ -78,11 +87,12 @@ def material(N: int, E: int, seed_material: int) -> np.ndarray:
 
 def elastic_problem(N: int, grid=None, E: int | None = None, h: float | None = None,
                     seed_material: int = 1001, seed_waves: int = 1002,
-                    device: str | torch.device = "cpu") -> Problem:
+                    device: str | torch.device = "cpu", nodes: str = "gl") -> Problem:
     """Build one seeded elastic STP input set.
 
     grid: (Gx, Gy, Gz); if omitted, a cube of side ceil(E^(1/3)).
-    h: element side; default 1/max(grid).
+    h: element side; default 1/max(grid). nodes: "gl" or "gll", the node
+    family the state is sampled on (it must match the predictor's).
     The state is evaluated with torch on ``device`` (float64) so large inputs
     can be generated where they are used; the random draws are numpy PCG64.
     """
@@ -106,7 +116,7 @@ def elastic_problem(N: int, grid=None, E: int | None = None, h: float | None = N
     k, amp, phase = wave_parameters(seed_waves)
 
     dev = torch.device(device)
-    xi = torch.tensor(sample_points(N), dtype=torch.float64, device=dev)
+    xi = torch.tensor(sample_points(N, nodes), dtype=torch.float64, device=dev)
     e = torch.arange(E, device=dev, dtype=torch.int64)
     ex = (e % Gx).to(torch.float64)
     ey = ((e // Gx) % Gy).to(torch.float64)

@@ -7,14 +7,17 @@ from . import _binding as B
 
 
 class Predictor:
-    """Owns one stp_handle for (order, dx, dt) on the current CUDA device."""
+    """Owns one stp_handle for (order, dx, dt) on the current CUDA device.
+    nodes: "gl" (Gauss-Legendre, default) or "gll" (Gauss-Lobatto)."""
 
-    def __init__(self, order: int, dx: float, dt: float, m: int = 9, precision="fp64"):
+    def __init__(self, order: int, dx: float, dt: float, m: int = 9, precision="fp64",
+                 nodes="gl"):
         self.order = order
         self.N = order + 1
         self.dx = dx
         self.dt = dt
-        self.handle = B.stp_create(order, m, dx, dt)
+        self.nodes = nodes
+        self.handle = B.stp_create(order, m, dx, dt, nodes)
         self.precision = precision
         if precision != "fp64":
             B.stp_set_precision(self.handle, precision)

@@ -67,6 +67,31 @@ def test_library_tables_match_oracle_tables(lib, N):
     assert np.abs(p0 - p0o).max() <= 2e-14 and np.abs(p1 - p1o).max() <= 2e-14
 
 
+@pytest.mark.parametrize("N", range(2, 13))
+def test_library_gauss_lobatto_tables_match_oracle_tables(lib, N):
+    xi = np.zeros(N)
+    D = np.zeros((N, N))
+    p0 = np.zeros(N)
+    p1 = np.zeros(N)
+    stp.stp_reference_tables(N - 1, xi, D, p0, p1, family="gll")
+    xo, Do, p0o, p1o = oracle.tables(N, "gll")
+    assert np.abs(xi - xo).max() <= 4e-16
+    assert np.abs(D - Do).max() <= 1e-14 * max(1.0, np.abs(Do).max())
+    assert np.array_equal(p0, p0o) and np.array_equal(p1, p1o)  # unit vectors
+
+
+def test_node_family_errors_before_touching_the_gpu(lib):
+    with pytest.raises(stp.STPError) as ei:  # Gauss-Lobatto needs N >= 2
+        stp.stp_create(0, 9, 0.1, 0.01, nodes="gll")
+    assert ei.value.status == _binding.STP_ERR_UNSUPPORTED
+    with pytest.raises(stp.STPError) as ei:
+        stp.stp_create(3, 9, 0.1, 0.01, nodes=7)
+    assert ei.value.status == _binding.STP_ERR_UNSUPPORTED
+    with pytest.raises(stp.STPError):
+        stp.stp_reference_tables(0, np.zeros(1), family="gll")
+    assert lib.stp_get_nodes(None) == 0
+
+
 @pytest.mark.parametrize("N", [3, 8, 12])
 def test_library_tables_against_50_digits(lib, N):
     mpmath = pytest.importorskip("mpmath")
