@@ -46,10 +46,12 @@ __device__ __forceinline__ float2 add(float2 x, float2 y) {
 __device__ __forceinline__ float2 neg(float2 x) { return make_float2(-x.x, -x.y); }
 __device__ __forceinline__ float2 sub(float2 x, float2 y) { return add(x, neg(y)); }
 
-// The same sum without the closing renormalisation: (fl(x.hi + y.hi), rest),
-// the rest a few ulp of the first part at most. Such pairs are exact-valued
-// inputs to every operation here (TwoSum and TwoProduct take any operands);
-// only a part read alone as a float needs a renormalised pair.
+// The same sum without the closing renormalisation: (fl(x.hi + y.hi), rest).
+// Such pairs are exact-valued inputs to every operation here (TwoSum and
+// TwoProduct take any operands), but after a cancellation the rest can exceed
+// ulp(first part), and a Dot2 cross term made from it is then rounded at a
+// larger scale: use it for sums that do not feed a product (the lines' mirrored
+// sums and differences stay renormalised).
 __device__ __forceinline__ float2 add_lazy(float2 x, float2 y) {
   const float2 s = two_sum(x.x, y.x);
   return make_float2(s.x, __fadd_rn(s.y, __fadd_rn(x.y, y.y)));
@@ -92,7 +94,12 @@ __device__ __forceinline__ int exponent_field(double x) {
   return (int)(((uint64_t)__double_as_longlong(x) >> 52) & 0x7ff);
 }
 
-// double -> float-float of x * 2^-sc, to within 2^-46 of it (normalised).
+// double -> float-float of x * 2^-sc: hi = x * 2^-sc rounded to the nearest
+// float (ties to even), lo = the rest rounded to the nearest float, so
+// |hi + lo - x 2^-sc| <= 2^-49 |x 2^-sc| (normalised). Integer operations on
+// the encoding only: the 53-bit significand is cut after 24 bits, the cut is
+// rounded by the 29 bits below it, and those bits (or their complement when
+// hi rounded up) become lo.
 __device__ __forceinline__ float2 split(double x, int sc = 0) {
   const uint64_t b = (uint64_t)__double_as_longlong(x);
   const uint32_t sign = (uint32_t)(b >> 32) & 0x80000000u;
@@ -101,21 +108,44 @@ __device__ __forceinline__ float2 split(double x, int sc = 0) {
   if (ex == 0x7ff) {  // infinity or NaN
     return make_float2(__uint_as_float(sign | 0x7f800000u | (m ? 0x400000u : 0u)), 0.f);
   }
-  const int fe = ex - 1023 - sc + 127;  // biased float exponent of hi
-  if (ex == 0 || fe <= 0) return make_float2(__uint_as_float(sign), 0.f);
-  if (fe >= 255) return make_float2(__uint_as_float(sign | 0x7f800000u), 0.f);
-  const float hi = make_f(sign, fe, (uint32_t)(m >> 29));  // top 23 mantissa bits (truncated)
-  const uint32_t r = (uint32_t)(m & 0x1fffffffu);          // the other 29 bits
-  float lo = 0.f;
-  if (r) {
-    const int pb = 31 - __clz((int)r);                      // leading bit of r
-    const int le = fe - 52 + pb;                            // biased exponent of lo
-    if (le > 0) {
-      const uint32_t mant = pb >= 23 ? (r >> (pb - 23)) : (r << (23 - pb));
-      lo = make_f(sign, le, mant);
+  const int fe0 = ex - 1023 - sc + 127;  // biased float exponent of hi before rounding
+  if (ex == 0 || fe0 <= 0) return make_float2(__uint_as_float(sign), 0.f);
+  if (fe0 >= 255) return make_float2(__uint_as_float(sign | 0x7f800000u), 0.f);
+  const uint64_t sig = (1ull << 52) | m;        // 53-bit significand
+  uint32_t hm = (uint32_t)(sig >> 29);           // its top 24 bits
+  uint32_t r = (uint32_t)(sig & 0x1fffffffu);    // the 29 bits below, value r * 2^(e-52)
+  uint32_t lo_sign = sign;
+  int fe = fe0;
+  if (r > (1u << 28) || (r == (1u << 28) && (hm & 1u))) {  // hi rounds up
+    hm += 1u;
+    r = (1u << 29) - r;  // lo = -r * 2^(e-52)
+    lo_sign ^= 0x80000000u;
+    if (hm == (1u << 24)) {
+      hm = 1u << 23;
+      if (++fe >= 255) return make_float2(__uint_as_float(sign | 0x7f800000u), 0.f);
     }
   }
-  return fast_two_sum(hi, lo);
+  const float hi = make_f(sign, fe, hm);
+  float lo = 0.f;
+  if (r) {
+    const int pb = 31 - __clz((int)r);  // leading bit of r (r < 2^29)
+    int le = fe0 - 52 + pb;             // biased exponent of lo
+    uint32_t mant;
+    if (pb > 23) {                      // round r to 24 significant bits
+      const int sh = pb - 23;
+      mant = r >> sh;
+      const uint32_t rem = r & ((1u << sh) - 1u), half = 1u << (sh - 1);
+      if (rem > half || (rem == half && (mant & 1u))) ++mant;
+      if (mant == (1u << 24)) {
+        mant = 1u << 23;
+        ++le;
+      }
+    } else {
+      mant = r << (23 - pb);
+    }
+    if (le > 0) lo = make_f(lo_sign, le, mant);
+  }
+  return make_float2(hi, lo);
 }
 
 // float * 2^sc -> double, exact for normal floats (subnormals give zero).

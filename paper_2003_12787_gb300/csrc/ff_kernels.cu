@@ -243,8 +243,8 @@ ff_slots_kernel(const double* __restrict__ q, const double* __restrict__ params,
 #pragma unroll
         for (int l = 0; l < H; ++l) {
           const float2 lo = u[l * stride], hi = u[(N - 1 - l) * stride];
-          ev[l] = ff::add_lazy(lo, hi);
-          od[l] = ff::sub_lazy(lo, hi);
+          ev[l] = ff::add(lo, hi);
+          od[l] = ff::sub(lo, hi);
         }
         float2 out[N];
 #pragma unroll
