@@ -180,6 +180,21 @@ def barrier(world: int):
         dist.barrier()
 
 
+def cpu_model() -> str:
+    """The host CPU's name as the OS reports it (model name, else the part)."""
+    import platform
+    try:
+        with open("/proc/cpuinfo") as f:
+            info = f.read()
+        for key in ("model name", "Model name", "CPU part"):
+            for line in info.splitlines():
+                if line.startswith(key):
+                    return f"{line.split(':', 1)[1].strip()} ({platform.machine()})"
+    except OSError:
+        pass
+    return platform.processor() or platform.machine()
+
+
 def oracle_baseline(prob_q, prob_params, h, dt, budget_s: float, max_elems: int):
     """Time the oracle as it stands on a bounded sample (elements from the
     front of the workload, in chunks, until the time budget is spent)."""
@@ -534,7 +549,8 @@ def run_gpu(args):
         qn = prob.q.cpu().numpy()
         pn = prob.params.cpu().numpy()
         done, spent, cores = oracle_baseline(qn, pn, prob.h, prob.dt, args.cpu_budget, E)
-        cpu = {"value": done / spent, "unit": UNIT, "cores": cores, "kind": "oracle",
+        cpu = {"value": done / spent, "unit": UNIT, "cores": cores, "cpu": cpu_model(),
+               "kind": "oracle",
                "sample": f"first {done} of {E} elements of the same workload, "
                          f"{spent:.1f} s wall on {cores} OpenMP threads"}
 
@@ -608,7 +624,8 @@ def run_reference(args):
         "data": "synthetic",
         "config": {"workload": desc, "N": N, "order": N - 1, "elements": prob.E,
                    "sample_elements_per_step": sample},
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "cpu": cpu_model(),
+                         "kind": "oracle",
                          "sample": f"first {sample} of {prob.E} elements per step"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
         "gpu_launches": 0,
