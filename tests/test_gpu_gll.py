@@ -89,3 +89,33 @@ def test_gll_and_gl_sets_in_one_batch():
     b.close()
     for P, _, _ in items:
         P.close()
+
+
+def test_gll_simulations_in_the_served_loop():
+    """Gauss-Lobatto and Gauss-Legendre simulations served together under a
+    budget that forces evictions: each equals repeated stp_predict with
+    q_{n+1} := avg_n, bit for bit."""
+    specs = [(5, 24, "gll"), (8, 9, "gl"), (7, 12, "gll"), (4, 40, "gll")]
+    sims = []
+    for i, (N, E, nodes) in enumerate(specs):
+        prob = elastic_problem(N, E=E, seed_material=860 + i, seed_waves=960 + i, nodes=nodes)
+        sims.append((stp.Predictor(N - 1, prob.h, prob.dt, nodes=nodes), prob))
+    foot = max(8 * E * (21 * N ** 3 + 54 * N ** 2) for N, E, _ in specs)
+    srv = stp.Server(2 * foot + (1 << 20), slots=2)
+    ids = [srv.add_sim(P, prob.q, prob.params) for P, prob in sims]
+    steps = 3
+    order = np.tile(np.arange(len(sims)), steps)
+    srv.run_trace(np.linspace(0.0, 0.01, len(order)), np.asarray(ids, dtype=np.int32)[order])
+    assert srv.stats()["evictions"] > 0
+    for i, (P, prob) in enumerate(sims):
+        q_mix, f_mix, n = srv.read(ids[i])
+        assert n == steps
+        q = prob.q.cuda()
+        for _ in range(steps):
+            avg, faces = P.predict(q, prob.params.cuda())
+            q = avg
+        torch.cuda.synchronize()
+        assert torch.equal(q.cpu(), q_mix) and torch.equal(faces.cpu(), f_mix), specs[i]
+    srv.close()
+    for P, _ in sims:
+        P.close()
