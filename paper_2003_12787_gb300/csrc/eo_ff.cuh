@@ -3,7 +3,7 @@
 //
 // Layout of one element in shared memory: p[quantity][node] with x rows padded
 // to an odd length RX and the quantity stride S odd (bank spread). D is
-// centro-antisymmetric on the symmetric Gauss-Legendre nodes, so with
+// centro-antisymmetric on symmetric nodes (Gauss-Legendre, Gauss-Lobatto), so with
 // h = floor(N/2), e_l = u_l + u_{N-1-l}, o_l = u_l - u_{N-1-l} (l < h),
 // E[i][l] = (D[i][l] + D[i][N-1-l]) / 2 and O[i][l] = (D[i][l] - D[i][N-1-l]) / 2,
 // the derivative of a line is (D u)_i = P_i + Q_i and (D u)_{N-1-i} = Q_i - P_i

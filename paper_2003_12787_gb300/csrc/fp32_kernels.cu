@@ -21,7 +21,7 @@
 //
 // The derivative contractions are the dimension-split scheme of Sec. IV
 // (SplitCK) with the even-odd decomposition of the FP64 kernels (D is
-// centro-antisymmetric on the symmetric Gauss-Legendre nodes, so a line of N
+// centro-antisymmetric on symmetric nodes, Gauss-Legendre or Gauss-Lobatto, so a line of N
 // outputs costs about N^2/2 + 2N operations). One CTA owns one element; the
 // element's current term lives in shared memory as p[quantity][node].
 #include "eo_ff.cuh"
