@@ -71,6 +71,13 @@ def _load():
             lib.oracle_tables_nodes.restype = ctypes.c_int
             lib.oracle_stp_nodes.argtypes = [ctypes.c_int] + lib.oracle_stp.argtypes
             lib.oracle_stp_nodes.restype = ctypes.c_int
+            lib.oracle_stp_sources.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                               ctypes.c_int64, ctypes.c_double, ctypes.c_double,
+                                               ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int,
+                                               ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                               ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                               ctypes.c_void_p]
+            lib.oracle_stp_sources.restype = ctypes.c_int
             lib.oracle_num_threads.argtypes = []
             lib.oracle_num_threads.restype = ctypes.c_int
             _lib = lib
@@ -121,12 +128,15 @@ def num_threads() -> int:
 
 
 def stp(q: np.ndarray, params: np.ndarray, h: float, dt: float, K: int | None = None,
-        return_terms: bool = False, nodes: str = "gl"):
+        return_terms: bool = False, nodes: str = "gl", sources=None):
     """Run the oracle STP.
 
     q: [E][N][N][N][9] float64 (z,y,x,quantity); params: [E][N][N][N][3]
     (rho, cp, cs). K = number of Taylor terms q^(0..K-1), default N+1.
     nodes: "gl" (Gauss-Legendre) or "gll" (Gauss-Lobatto).
+    sources: optional list of point sources, each a dict with "element",
+    "position" (x, y, z in [0,1]), "amplitude" (9 values) and "derivatives"
+    (f^(k)(t_n) for k = 0..K-2); see oracle_stp_sources in stp_oracle.c.
     Returns (avg [E][N][N][N][9], faces [E][6][N][N][9]) and, with
     return_terms, every q^(k) as [E][K][N][N][N][9].
     """
@@ -141,10 +151,26 @@ def stp(q: np.ndarray, params: np.ndarray, h: float, dt: float, K: int | None = 
     avg = np.empty_like(q)
     faces = np.empty((E, 6, N, N, M))
     terms = np.empty((E, K, N, N, N, M)) if return_terms else None
-    rc = _load().oracle_stp_nodes(NODE_FAMILIES[nodes], N, K, E, float(h), float(dt),
-                                  q.ctypes.data, params.ctypes.data, avg.ctypes.data,
-                                  faces.ctypes.data,
-                                  terms.ctypes.data if terms is not None else None)
+    if sources:
+        n = len(sources)
+        elem = np.array([int(x["element"]) for x in sources], dtype=np.int64)
+        pos = np.ascontiguousarray([x["position"] for x in sources], dtype=np.float64).reshape(n, 3)
+        amp = np.ascontiguousarray([x["amplitude"] for x in sources], dtype=np.float64).reshape(n, 9)
+        der = np.ascontiguousarray([list(x["derivatives"])[:K - 1] for x in sources],
+                                   dtype=np.float64).reshape(n, max(K - 1, 0))
+        if der.shape[1] != K - 1:
+            raise ValueError(f"each source needs {K - 1} derivatives")
+        rc = _load().oracle_stp_sources(NODE_FAMILIES[nodes], N, K, E, float(h), float(dt),
+                                        q.ctypes.data, params.ctypes.data, n, elem.ctypes.data,
+                                        pos.ctypes.data, amp.ctypes.data,
+                                        der.ctypes.data if der.size else None, avg.ctypes.data,
+                                        faces.ctypes.data,
+                                        terms.ctypes.data if terms is not None else None)
+    else:
+        rc = _load().oracle_stp_nodes(NODE_FAMILIES[nodes], N, K, E, float(h), float(dt),
+                                      q.ctypes.data, params.ctypes.data, avg.ctypes.data,
+                                      faces.ctypes.data,
+                                      terms.ctypes.data if terms is not None else None)
     if rc != 0:
         raise RuntimeError(f"oracle_stp returned {rc}")
     if return_terms:

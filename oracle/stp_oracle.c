@@ -246,8 +246,8 @@ static void elastic_B(int d, double rho, double cp, double cs, double B[M][M]) {
  */
 static void stp_element(int N, int K, double h, double dt, const double* D,
                         const double* phi0, const double* phi1, const double* q,
-                        const double* params, double* avg, double* faces,
-                        double* terms, double* p, double* pn, double* g) {
+                        const double* params, const double* src, double* avg,
+                        double* faces, double* terms, double* p, double* pn, double* g) {
   const int n3 = N * N * N;
   memcpy(p, q, sizeof(double) * n3 * M);
   memcpy(avg, q, sizeof(double) * n3 * M);
@@ -282,6 +282,9 @@ static void stp_element(int N, int K, double h, double dt, const double* D,
       }
     }
     memcpy(p, pn, sizeof(double) * n3 * M);
+    /* point sources of this element: q^(k+1) = L q^(k) + s^(k) */
+    if (src)
+      for (int t = 0; t < n3 * M; ++t) p[t] += src[(size_t)k * n3 * M + t];
     c = c * dt / (double)(k + 2);
     for (int t = 0; t < n3 * M; ++t) avg[t] += c * p[t];
     if (terms) memcpy(terms + (size_t)(k + 1) * n3 * M, p, sizeof(double) * n3 * M);
@@ -331,7 +334,7 @@ int oracle_stp_nodes(int nodes, int N, int K, int64_t E, double h, double dt, co
     for (int64_t e = 0; e < E; ++e) {
       if (!work) continue;
       stp_element(N, K, h, dt, D, phi0, phi1, q + e * n3m,
-                  params + e * (n3m / M) * 3, avg + e * n3m,
+                  params + e * (n3m / M) * 3, NULL, avg + e * n3m,
                   faces + e * (size_t)6 * N * N * M,
                   terms ? terms + e * (size_t)K * n3m : NULL, work, work + n3m,
                   work + 2 * n3m);
@@ -339,6 +342,73 @@ int oracle_stp_nodes(int nodes, int N, int K, int64_t E, double h, double dt, co
     free(work);
   }
   return err ? -2 : 0;
+}
+
+/*
+ * The STP with point sources (the source term of the linear PDE, Sec. II-A,
+ * whose time derivatives enter every CK order in the generic STP figure). A
+ * source is a Dirac delta at reference position pos (in [0,1]^3) of element
+ * elem, times a vector amp over the 9 quantities, times a time function whose
+ * derivatives f^(k)(t_n), k = 0..K-2, are given in der[K-1]. Projected onto
+ * the nodal basis with the diagonal (quadrature) mass matrix, it adds
+ *   s^(k)_node = phi_node(pos) / (w_node h^3) * amp * f^(k)
+ * to every CK term: q^(k+1) = L q^(k) + s^(k), node weight w_node the product
+ * of the 1-D quadrature weights on [0,1], phi_node the product of the 1-D
+ * Lagrange polynomials. Sources in one element add up. Arrays: elem[nsrc],
+ * pos[nsrc][3] (x, y, z), amp[nsrc][9], der[nsrc][K-1].
+ */
+int oracle_stp_sources(int nodes, int N, int K, int64_t E, double h, double dt, const double* q,
+                       const double* params, int nsrc, const int64_t* elem, const double* pos,
+                       const double* amp, const double* der, double* avg, double* faces,
+                       double* terms) {
+  if (N < 1 || N > 16 || K < 1 || E < 0 || !(h > 0.0) || nsrc < 0) return -1;
+  double xi[16], w[16], D[16 * 16], phi0[16], phi1[16];
+  if (oracle_tables_nodes(nodes, N, xi, D, phi0, phi1) != 0) return -1;
+  if ((nodes == 0 ? oracle_gl_nodes(N, xi, w) : oracle_gll_nodes(N, xi, w)) != 0) return -1;
+  const size_t n3 = (size_t)N * N * N, n3m = n3 * M;
+  /* elements with sources, their projected source terms [K-1][N^3][9] */
+  double** src = (double**)calloc((size_t)(E > 0 ? E : 1), sizeof(double*));
+  if (!src) return -2;
+  int err = 0;
+  for (int i = 0; i < nsrc && !err; ++i) {
+    const int64_t e = elem[i];
+    if (e < 0 || e >= E) { err = -1; break; }
+    if (!src[e] && !(src[e] = (double*)calloc((size_t)(K > 1 ? K - 1 : 1) * n3m, sizeof(double)))) {
+      err = -2;
+      break;
+    }
+    for (int z = 0; z < N; ++z)
+      for (int y = 0; y < N; ++y)
+        for (int x = 0; x < N; ++x) {
+          const double proj = lagrange(N, xi, x, pos[3 * i]) * lagrange(N, xi, y, pos[3 * i + 1]) *
+                               lagrange(N, xi, z, pos[3 * i + 2]) / (w[x] * w[y] * w[z] * h * h * h);
+          for (int k = 0; k + 1 < K; ++k)
+            for (int s = 0; s < M; ++s)
+              src[e][(size_t)k * n3m + (size_t)NODE(z, y, x) * M + s] +=
+                  proj * amp[9 * i + s] * der[(size_t)i * (K - 1) + k];
+        }
+  }
+  if (!err) {
+#pragma omp parallel
+    {
+      double* work = (double*)malloc(sizeof(double) * 3 * n3m);
+      if (!work) {
+#pragma omp atomic write
+        err = -2;
+      }
+#pragma omp for schedule(dynamic, 4)
+      for (int64_t e = 0; e < E; ++e) {
+        if (!work) continue;
+        stp_element(N, K, h, dt, D, phi0, phi1, q + e * n3m, params + e * n3 * 3, src[e],
+                    avg + e * n3m, faces + e * (size_t)6 * N * N * M,
+                    terms ? terms + e * (size_t)K * n3m : NULL, work, work + n3m, work + 2 * n3m);
+      }
+      free(work);
+    }
+  }
+  for (int64_t e = 0; e < E; ++e) free(src[e]);
+  free(src);
+  return err;
 }
 
 /* The STP on Gauss-Legendre nodes (the default node family). */

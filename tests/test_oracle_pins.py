@@ -380,6 +380,87 @@ def test_gll_brute_force_dense_operator(N):
     assert ref.rel_err(avg_gl[0], avg_x) > 1e-8
 
 
+# --- point sources ---------------------------------------------------------------
+
+def _source(e, rng, K):
+    return {"element": e, "position": tuple(rng.uniform(0, 1, 3)),
+            "amplitude": rng.uniform(-1, 1, 9), "derivatives": rng.uniform(-2, 2, K - 1)}
+
+
+@pytest.mark.parametrize("K", [2, 3, 5])
+def test_source_single_node_closed_form(K):
+    """N = 1: D = 0, so q^(k+1) = s^(k) = amp f^(k) / h^3 (one node of weight
+    1, basis function 1) and avg = q + sum_k dt^(k+1)/(k+2)! amp f^(k) / h^3."""
+    rng = np.random.default_rng(K)
+    h, dt = 0.4, 0.03
+    q = rng.uniform(-1, 1, (3, 1, 1, 1, 9))
+    params = random_params(3, 1, rng)
+    src = [_source(2, rng, K), _source(2, rng, K), _source(0, rng, K)]
+    avg, faces = oracle.stp(q, params, h, dt, K=K, sources=src)
+    expect = q.copy()
+    for x in src:
+        for k in range(K - 1):
+            expect[x["element"], 0, 0, 0] += (dt ** (k + 1) / math.factorial(k + 2)
+                                              * np.asarray(x["amplitude"]) * x["derivatives"][k] / h ** 3)
+    assert np.abs(avg - expect).max() <= 1e-15 * np.abs(expect).max()
+    assert np.abs(faces[:, 0, 0, 0] - avg[:, 0, 0, 0]).max() <= 1e-15
+
+
+def _nodal_projection(N, pos, h, nodes):
+    """phi_l(pos) / (w_l h^3) on the element's nodes [z][y][x] (numpy
+    Lagrange basis and quadrature weights)."""
+    _, w = ref.points(N, nodes)
+    px = ref.lagrange_phi_numpy(N, pos[0], nodes)
+    py = ref.lagrange_phi_numpy(N, pos[1], nodes)
+    pz = ref.lagrange_phi_numpy(N, pos[2], nodes)
+    P = pz[:, None, None] * py[None, :, None] * px[None, None, :]
+    return P / (w[:, None, None] * w[None, :, None] * w[None, None, :] * h ** 3)
+
+
+@pytest.mark.parametrize("N,nodes", [(2, "gl"), (3, "gl"), (3, "gll")])
+def test_source_brute_force_dense_operator(N, nodes):
+    rng = np.random.default_rng(55 + N)
+    E, K = 2, N + 1
+    params = random_params(E, N, rng)
+    q = rng.uniform(-1, 1, (E, N, N, N, 9))
+    h, dt = 0.3, 0.004
+    src = [_source(0, rng, K), _source(0, rng, K), _source(1, rng, K)]
+    avg, _, terms = oracle.stp(q, params, h, dt, return_terms=True, nodes=nodes, sources=src)
+    for e in range(E):
+        L = ref.dense_operator(N, h, params[e], nodes)
+        S = np.zeros((K - 1, N, N, N, 9))
+        for x in src:
+            if x["element"] != e:
+                continue
+            P = _nodal_projection(N, x["position"], h, nodes)
+            for k in range(K - 1):
+                S[k] += P[..., None] * np.asarray(x["amplitude"]) * x["derivatives"][k]
+        p = q[e].reshape(-1)
+        expect = p.copy()
+        for k in range(K - 1):
+            p = L @ p + S[k].reshape(-1)
+            expect = expect + dt ** (k + 1) / math.factorial(k + 2) * p
+            assert ref.rel_err(terms[e, k + 1].reshape(-1), p) <= 1e-12
+        assert ref.rel_err(avg[e].reshape(-1), expect) <= 1e-13
+
+
+def test_source_superposition_and_linearity():
+    N, E = 4, 3
+    rng = np.random.default_rng(77)
+    params = random_params(E, N, rng)
+    q = rng.uniform(-1, 1, (E, N, N, N, 9))
+    h, dt = 0.25, 0.01
+    s1 = [_source(1, rng, N + 1)]
+    s2 = [_source(1, rng, N + 1), _source(2, rng, N + 1)]
+    a12, f12 = oracle.stp(q, params, h, dt, sources=s1 + s2)
+    a1, f1 = oracle.stp(q, params, h, dt, sources=s1)
+    a2, f2 = oracle.stp(np.zeros_like(q), params, h, dt, sources=s2)
+    assert ref.rel_err(a12, a1 + a2) <= 1e-14 and ref.rel_err(f12, f1 + f2) <= 1e-14
+    a0, _ = oracle.stp(q, params, h, dt)
+    assert np.array_equal(a1[0], a0[0]) and np.array_equal(a1[2], a0[2])  # other elements untouched
+    assert ref.rel_err(a1[1], a0[1]) > 1e-6
+
+
 # --- invariants ----------------------------------------------------------------
 
 def test_linearity_and_element_independence():
