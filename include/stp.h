@@ -89,6 +89,40 @@ stp_status stp_predict(stp_handle h, int64_t elements, const double* q,
                        void* stream);
 
 /*
+ * Point sources (Sec. II-A: the source term of the linear PDE, projected onto
+ * the nodal basis; in the STP the source's time derivatives enter every
+ * Cauchy-Kowalewsky order). A source is a Dirac delta at `position` (reference
+ * coordinates x, y, z in [0,1]) of element `element`, times `amplitude` over
+ * the 9 quantities, times a time function f given by its derivatives
+ * f^(k)(t_n), k = 0..N-1 (`derivatives`, entries from N on are ignored). With
+ * the diagonal quadrature mass matrix it adds
+ *   s^(k)_node = phi_node(position) / (w_node dx^3) * amplitude * f^(k)
+ * to every term: q^(k+1) = L q^(k) + s^(k). The paper gives neither the time
+ * function nor the placement; the caller supplies both.
+ */
+typedef struct {
+  int64_t element;
+  double position[3];
+  double amplitude[9];
+  double derivatives[12];
+} stp_point_source;
+
+/*
+ * stp_predict with point sources: the STP of every element as stp_predict
+ * (any precision), then, for the elements that hold sources, their response
+ * to the sources added to out_avg and out_faces in FP64 (one more launch; the
+ * STP is linear, so the two add up). `sources` is a HOST array of nsources
+ * entries; several sources may share an element. Asynchronous on `stream`
+ * (a small stream-ordered device allocation holds the sources' data; it is
+ * copied from host memory, so the call cannot be captured in a CUDA graph).
+ * STP_ERR_INVALID_ARG for an element outside [0, elements), a position
+ * outside [0,1]^3, a non-finite value or nsources < 0.
+ */
+stp_status stp_predict_sources(stp_handle h, int64_t elements, const double* q,
+                               const double* params, double* out_avg, double* out_faces,
+                               int nsources, const stp_point_source* sources, void* stream);
+
+/*
  * Same computation on HOST buffers (pinned host memory gives full copy
  * bandwidth; pageable memory works but copies slower). Synchronous: returns
  * once out_avg and out_faces hold the results. Elements are processed in

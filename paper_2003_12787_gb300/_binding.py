@@ -57,6 +57,7 @@ def load():
         lib.stp_reference_tables_nodes.argtypes = [ctypes.c_int, ctypes.c_int, vp, vp, vp, vp]
         lib.stp_get_nodes.argtypes = [vp]
         lib.stp_get_nodes.restype = ctypes.c_int
+        lib.stp_predict_sources.argtypes = [vp, i64, vp, vp, vp, vp, ctypes.c_int, vp, vp]
         lib.stp_nodes.argtypes = [vp]
         lib.stp_nodes.restype = ctypes.c_int
         lib.stp_status_string.argtypes = [ctypes.c_int]
@@ -201,6 +202,28 @@ def stp_measure_fp64_peak(stream=None) -> float:
     g = ctypes.c_double()
     _check(load().stp_measure_fp64_peak(ctypes.byref(g), _stream(stream)), "stp_measure_fp64_peak")
     return g.value
+
+
+class PointSource(ctypes.Structure):
+    """Mirror of stp_point_source."""
+    _fields_ = [("element", ctypes.c_int64), ("position", ctypes.c_double * 3),
+                ("amplitude", ctypes.c_double * 9), ("derivatives", ctypes.c_double * 12)]
+
+
+def stp_predict_sources(h: int, elements: int, q, params, out_avg, out_faces, sources,
+                        stream=None) -> None:
+    """sources: sequence of dicts with "element", "position" (3), "amplitude"
+    (9) and "derivatives" (f^(k)(t_n), k = 0..N-1; at most 12 are used)."""
+    arr = (PointSource * max(1, len(sources)))()
+    for i, src in enumerate(sources):
+        der = list(src["derivatives"])[:12]
+        arr[i] = PointSource(int(src["element"]), (ctypes.c_double * 3)(*src["position"]),
+                             (ctypes.c_double * 9)(*src["amplitude"]),
+                             (ctypes.c_double * 12)(*(der + [0.0] * (12 - len(der)))))
+    _check(load().stp_predict_sources(h, elements, _ptr(q), _ptr(params), _ptr(out_avg),
+                                      _ptr(out_faces), len(sources),
+                                      ctypes.cast(arr, ctypes.c_void_p), _stream(stream)),
+           "stp_predict_sources")
 
 
 class BatchSet(ctypes.Structure):

@@ -248,6 +248,115 @@ stp_status stp_predict(stp_handle h, int64_t elements, const double* q, const do
   return STP_OK;
 }
 
+namespace {
+
+// phi_j(a) for the handle's nodes (barycentric form, long double; a unit
+// vector where a is a node).
+void lagrange_at(const stp::HostTables& t, long double a, long double* phi) {
+  const int N = t.N;
+  long double bw[stp::kMaxNodes];
+  for (int j = 0; j < N; ++j) {
+    long double prod = 1.0L;
+    for (int k = 0; k < N; ++k)
+      if (k != j) prod *= ((long double)t.nodes[j] - (long double)t.nodes[k]);
+    bw[j] = 1.0L / prod;
+  }
+  for (int j = 0; j < N; ++j)
+    if ((long double)t.nodes[j] == a) {
+      for (int i = 0; i < N; ++i) phi[i] = i == j ? 1.0L : 0.0L;
+      return;
+    }
+  long double den = 0.0L;
+  for (int k = 0; k < N; ++k) den += bw[k] / (a - (long double)t.nodes[k]);
+  for (int j = 0; j < N; ++j) phi[j] = (bw[j] / (a - (long double)t.nodes[j])) / den;
+}
+
+}  // namespace
+
+stp_status stp_predict_sources(stp_handle h, int64_t elements, const double* q, const double* params,
+                               double* out_avg, double* out_faces, int nsources,
+                               const stp_point_source* sources, void* stream) {
+  if (nsources < 0 || (nsources > 0 && !sources))
+    return fail(STP_ERR_INVALID_ARG, "bad source list");
+  stp_status s = validate_common(h, elements, q, params, out_avg, out_faces);
+  if (s != STP_OK) return s;
+  for (int i = 0; i < nsources; ++i) {
+    const stp_point_source& src = sources[i];
+    if (src.element < 0 || src.element >= elements)
+      return fail(STP_ERR_INVALID_ARG, "source " + std::to_string(i) + ": element out of range");
+    for (int d = 0; d < 3; ++d)
+      if (!(src.position[d] >= 0.0 && src.position[d] <= 1.0))
+        return fail(STP_ERR_INVALID_ARG, "source " + std::to_string(i) + ": position outside [0,1]");
+    for (int k = 0; k < 9; ++k)
+      if (!std::isfinite(src.amplitude[k]))
+        return fail(STP_ERR_INVALID_ARG, "source " + std::to_string(i) + ": non-finite amplitude");
+    for (int k = 0; k < h->N; ++k)
+      if (!std::isfinite(src.derivatives[k]))
+        return fail(STP_ERR_INVALID_ARG, "source " + std::to_string(i) + ": non-finite derivative");
+  }
+  if ((s = stp_predict(h, elements, q, params, out_avg, out_faces, stream)) != STP_OK) return s;
+  if (nsources == 0 || elements == 0) return STP_OK;
+  const int N = h->N, N3 = N * N * N;
+  // group the sources by element; per source: the nodal projection
+  // phi_node(pos) / (w_node dx^3), the amplitude and dt^(k+1)/(k+2)! f^(k)
+  std::vector<int> order(nsources);
+  for (int i = 0; i < nsources; ++i) order[i] = i;
+  std::stable_sort(order.begin(), order.end(),
+                   [&](int a, int b) { return sources[a].element < sources[b].element; });
+  std::vector<stp::SourceGroup> groups;
+  std::vector<double> proj((size_t)nsources * N3), amp((size_t)nsources * 9), cf((size_t)nsources * N);
+  const long double h3 = (long double)h->dx * h->dx * h->dx;
+  for (int r = 0; r < nsources; ++r) {
+    const stp_point_source& src = sources[order[r]];
+    if (groups.empty() || groups.back().element != src.element)
+      groups.push_back(stp::SourceGroup{src.element, r, 0});
+    ++groups.back().count;
+    long double px[stp::kMaxNodes], py[stp::kMaxNodes], pz[stp::kMaxNodes];
+    lagrange_at(h->host, src.position[0], px);
+    lagrange_at(h->host, src.position[1], py);
+    lagrange_at(h->host, src.position[2], pz);
+    const double* w = h->host.weights;
+    for (int z = 0; z < N; ++z)
+      for (int y = 0; y < N; ++y)
+        for (int x = 0; x < N; ++x)
+          proj[(size_t)r * N3 + (z * N + y) * N + x] =
+              (double)(pz[z] * py[y] * px[x] / ((long double)w[z] * w[y] * w[x] * h3));
+    for (int k = 0; k < 9; ++k) amp[(size_t)r * 9 + k] = src.amplitude[k];
+    long double c = 1.0L;  // dt^(k+1) / (k+2)!
+    for (int k = 0; k < N; ++k) {
+      c = c * (long double)h->dt / (long double)(k + 2);
+      cf[(size_t)r * N + k] = (double)(c * (long double)src.derivatives[k]);
+    }
+  }
+  const int G = (int)groups.size();
+  const size_t b_groups = sizeof(stp::SourceGroup) * G, b_proj = sizeof(double) * proj.size(),
+               b_amp = sizeof(double) * amp.size(), b_cf = sizeof(double) * cf.size(),
+               b_scr = sizeof(double) * (size_t)G * 9 * N3;
+  auto up = [](size_t b) { return (b + 255) & ~(size_t)255; };
+  const size_t total = up(b_groups) + up(b_proj) + up(b_amp) + up(b_cf) + up(b_scr);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  char* d = nullptr;
+  cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(&d), total, st);
+  if (e != cudaSuccess) { cudaGetLastError(); return fail(STP_ERR_OOM, "source buffer allocation failed"); }
+  char* d_groups = d;
+  char* d_proj = d_groups + up(b_groups);
+  char* d_amp = d_proj + up(b_proj);
+  char* d_cf = d_amp + up(b_amp);
+  char* d_scr = d_cf + up(b_cf);
+  if ((e = cudaMemcpyAsync(d_groups, groups.data(), b_groups, cudaMemcpyHostToDevice, st)) == cudaSuccess &&
+      (e = cudaMemcpyAsync(d_proj, proj.data(), b_proj, cudaMemcpyHostToDevice, st)) == cudaSuccess &&
+      (e = cudaMemcpyAsync(d_amp, amp.data(), b_amp, cudaMemcpyHostToDevice, st)) == cudaSuccess &&
+      (e = cudaMemcpyAsync(d_cf, cf.data(), b_cf, cudaMemcpyHostToDevice, st)) == cudaSuccess)
+    e = stp::launch_sources(N, G, reinterpret_cast<const stp::SourceGroup*>(d_groups),
+                            reinterpret_cast<const double*>(d_proj), reinterpret_cast<const double*>(d_amp),
+                            reinterpret_cast<const double*>(d_cf), h->d_tables, params, out_avg,
+                            out_faces, reinterpret_cast<double*>(d_scr), st);
+  const cudaError_t fe = cudaFreeAsync(d, st);
+  if (e == cudaSuccess) e = fe;
+  if (e != cudaSuccess) return cuda_fail(e, "point-source launch");
+  return STP_OK;
+}
+
 stp_status stp_predict_host(stp_handle h, int64_t elements, const double* q, const double* params,
                             double* out_avg, double* out_faces, void* stream) {
   stp_status s = validate_common(h, elements, q, params, out_avg, out_faces);

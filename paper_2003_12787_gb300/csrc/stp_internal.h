@@ -20,6 +20,7 @@ struct HostTables {
   double D[kMaxNodes * kMaxNodes];  // D[i*N+j] = phi_j'(xi_i)
   double phi0[kMaxNodes];
   double phi1[kMaxNodes];
+  double weights[kMaxNodes];  // quadrature weights on [0,1] (sum 1)
 };
 
 // Nodes (Gauss-Legendre or Gauss-Lobatto, see stp_node_family), derivative
@@ -62,6 +63,20 @@ cudaError_t launch_fp32(int N, int64_t E, const double* q, const double* params,
 bool ff_supported(int N);
 cudaError_t launch_ff(int N, int64_t E, const double* q, const double* params, double* out_avg,
                       double* out_faces, const double* tables, cudaStream_t stream);
+
+// Point sources (sources.cu): after the STP of a set, adds the response of
+// the point sources to the outputs of the elements holding them (FP64, one
+// CTA per such element). groups[g] = (element, first source, source count);
+// per source: proj[N^3] (phi_node(pos) / (w_node h^3)), amp[9], cf[N]
+// (dt^(k+1)/(k+2)! f^(k)). scratch: 9 N^3 doubles per group.
+struct SourceGroup {
+  int64_t element;
+  int first, count;
+};
+cudaError_t launch_sources(int N, int ngroups, const SourceGroup* groups, const double* proj,
+                           const double* amp, const double* cf, const double* tables,
+                           const double* params, double* out_avg, double* out_faces,
+                           double* scratch, cudaStream_t stream);
 
 // Batched persistent FP64 launch (batch.cu).
 struct BatchPlan;

@@ -85,6 +85,21 @@ bool make_tables(int N, HostTables* t, int family) {
     if (!ok) return false;
     x[N - 1 - i] = 0.5L * (1.0L + r);  // ascending on [0,1]
   }
+  // quadrature weights on [0,1]: Gauss-Legendre 1/((1-t^2) P_N'(t)^2),
+  // Gauss-Lobatto 1/(N (N-1) P_{N-1}(t)^2), t = 2x - 1
+  for (int i = 0; i < N; ++i) {
+    const ld tt = 2.0L * x[i] - 1.0L;
+    ld p, dp;
+    if (family == STP_NODES_GAUSS_LOBATTO) {
+      legendre_pair(N - 1, tt, &p, &dp);
+      t->weights[i] = (double)(1.0L / ((ld)N * (ld)(N - 1) * p * p));
+    } else if (N == 1) {
+      t->weights[i] = 1.0;
+    } else {
+      legendre_pair(N, tt, &p, &dp);
+      t->weights[i] = (double)(1.0L / ((1.0L - tt * tt) * dp * dp));
+    }
+  }
   // barycentric weights
   ld w[kMaxNodes];
   for (int j = 0; j < N; ++j) {

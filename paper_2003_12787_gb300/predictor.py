@@ -64,14 +64,18 @@ class Predictor:
         if not (q.is_contiguous() and params.is_contiguous()):
             raise ValueError("q and params must be contiguous")
 
-    def predict(self, q: torch.Tensor, params: torch.Tensor, out=None, stream=None):
-        """Enqueue on `stream` (default: torch's current stream) for device tensors."""
+    def predict(self, q: torch.Tensor, params: torch.Tensor, out=None, stream=None, sources=None):
+        """Enqueue on `stream` (default: torch's current stream) for device tensors.
+        sources: optional point sources (see stp_predict_sources)."""
         self._check_inputs(q, params)
         E = q.shape[0]
         avg, faces = out if out is not None else self.empty_outputs(E, device=q.device)
         if stream is None and q.is_cuda:
             stream = torch.cuda.current_stream(q.device)
-        B.stp_predict(self.handle, E, q, params, avg, faces, stream)
+        if sources:
+            B.stp_predict_sources(self.handle, E, q, params, avg, faces, sources, stream)
+        else:
+            B.stp_predict(self.handle, E, q, params, avg, faces, stream)
         return avg, faces
 
     def predict_host(self, q: torch.Tensor, params: torch.Tensor, out=None, stream=None):
