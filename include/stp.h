@@ -264,7 +264,7 @@ stp_status stp_autotune(stp_handle h, int* variant, double* us_per_element,
  * can cause, a device already handed out in full). stp_batch_create allocates
  * a work list, a work counter and scratch buffers; this call instead keeps its
  * scratch - the work counter and one parking area per CTA for the new Taylor
- * terms of orders 10 and 11 (N = 11, 12) - in one 24 MiB array that is part of
+ * terms of order 11 (N = 12) - in one 24 MiB array that is part of
  * the library's device image (every GPU that loads the library holds it until
  * the process exits), and passes the set descriptors as kernel parameters.
  *

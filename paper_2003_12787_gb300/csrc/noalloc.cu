@@ -24,8 +24,8 @@ namespace {
 constexpr int kStaticThreads = 512;
 constexpr int kStaticMaxSets = 128;
 // Scratch for one call: the work counter (first 256 bytes), then one parking
-// area per CTA of 9*S*EPC doubles for the orders whose shape parks new terms
-// (N = 11, 12; 124.5 KB per CTA at N = 12). 24 MiB covers one CTA per SM for
+// area per CTA of 9*S*EPC doubles for the order whose shape parks new terms
+// (N = 12: 124.5 KB per CTA). 24 MiB covers one CTA per SM for
 // every order up to 190 SMs.
 constexpr size_t kStaticScratchBytes = (size_t)24 << 20;
 constexpr size_t kCounterBytes = 256;
