@@ -78,6 +78,12 @@ def _load():
                                                ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                                ctypes.c_void_p]
             lib.oracle_stp_sources.restype = ctypes.c_int
+            lib.oracle_stp_curvilinear.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                                   ctypes.c_int64, ctypes.c_double,
+                                                   ctypes.c_void_p, ctypes.c_void_p,
+                                                   ctypes.c_void_p, ctypes.c_void_p,
+                                                   ctypes.c_void_p, ctypes.c_void_p]
+            lib.oracle_stp_curvilinear.restype = ctypes.c_int
             lib.oracle_num_threads.argtypes = []
             lib.oracle_num_threads.restype = ctypes.c_int
             _lib = lib
@@ -173,6 +179,39 @@ def stp(q: np.ndarray, params: np.ndarray, h: float, dt: float, K: int | None = 
                                       terms.ctypes.data if terms is not None else None)
     if rc != 0:
         raise RuntimeError(f"oracle_stp returned {rc}")
+    if return_terms:
+        return avg, faces, terms
+    return avg, faces
+
+
+def stp_curvilinear(q: np.ndarray, params: np.ndarray, metric: np.ndarray, dt: float,
+                    K: int | None = None, return_terms: bool = False, nodes: str = "gl"):
+    """Run the oracle STP on curvilinear elements.
+
+    metric: [E][N][N][N][3][3] (or [..][9]) float64, the inverse Jacobian
+    G[d][j] = dxi_d/dx_j of the map from the reference cube [0,1]^3 to
+    physical space at every node (xi_1, xi_2, xi_3 along the x, y, z node
+    indices); see oracle_stp_curvilinear in stp_oracle.c. Other arguments and
+    the outputs as in ``stp`` (no element side: the metric carries the scale).
+    """
+    q = np.ascontiguousarray(q, dtype=np.float64)
+    params = np.ascontiguousarray(params, dtype=np.float64)
+    if q.ndim != 5 or q.shape[4] != M or not (q.shape[1] == q.shape[2] == q.shape[3]):
+        raise ValueError(f"q must be [E][N][N][N][9], got {q.shape}")
+    E, N = q.shape[0], q.shape[1]
+    if params.shape != (E, N, N, N, 3):
+        raise ValueError(f"params must be {(E, N, N, N, 3)}, got {params.shape}")
+    metric = np.ascontiguousarray(metric, dtype=np.float64).reshape(E, N, N, N, 9)
+    K = N + 1 if K is None else int(K)
+    avg = np.empty_like(q)
+    faces = np.empty((E, 6, N, N, M))
+    terms = np.empty((E, K, N, N, N, M)) if return_terms else None
+    rc = _load().oracle_stp_curvilinear(NODE_FAMILIES[nodes], N, K, E, float(dt), q.ctypes.data,
+                                        params.ctypes.data, metric.ctypes.data, avg.ctypes.data,
+                                        faces.ctypes.data,
+                                        terms.ctypes.data if terms is not None else None)
+    if rc != 0:
+        raise RuntimeError(f"oracle_stp_curvilinear returned {rc}")
     if return_terms:
         return avg, faces, terms
     return avg, faces

@@ -19,7 +19,8 @@
  *   - Sec. II-B: the STP outputs the time-averaged degrees of freedom and
  *     their projection onto the element faces.
  *   - Sec. VI (benchmark setup): 3-D elastic wave equation, 3 velocities and
- *     6 stresses, 3 material parameters per node.
+ *     6 stresses, 3 material parameters per node; on curvilinear meshes 9
+ *     geometry parameters per node more (oracle_stp_curvilinear).
  *
  * Readings (the paper is silent or its pseudocode is garbled on these):
  *   - The operator is taken in the form q_t + sum_d B_d dq/dx_d = 0, so one CK
@@ -41,6 +42,7 @@
  *   params:   [E][N][N][N][3]   (rho, cp, cs)
  *   faces:    [E][6][N][N][9]
  *   terms:    [E][K][N][N][N][9]  (optional: every q^(k), unscaled)
+ *   metric:   [E][N][N][N][9]   (curvilinear elements: dxi_d/dx_j at 3d + j)
  */
 #include <math.h>
 #include <stdint.h>
@@ -242,12 +244,15 @@ static void elastic_B(int d, double rho, double cp, double cs, double B[M][M]) {
 
 /*
  * One element. q, params, avg, faces point at that element's blocks; terms
- * (may be NULL) at its [K][N][N][N][9] block.
+ * (may be NULL) at its [K][N][N][N][9] block. metric (may be NULL) points at
+ * the element's [N][N][N][9] block of inverse Jacobians; without it the
+ * element is a cube of side h.
  */
 static void stp_element(int N, int K, double h, double dt, const double* D,
                         const double* phi0, const double* phi1, const double* q,
-                        const double* params, const double* src, double* avg,
-                        double* faces, double* terms, double* p, double* pn, double* g) {
+                        const double* params, const double* metric, const double* src,
+                        double* avg, double* faces, double* terms, double* p, double* pn,
+                        double* g) {
   const int n3 = N * N * N;
   memcpy(p, q, sizeof(double) * n3 * M);
   memcpy(avg, q, sizeof(double) * n3 * M);
@@ -257,7 +262,8 @@ static void stp_element(int N, int K, double h, double dt, const double* D,
     /* pn = - sum_d B_d (D_d p) / h  : one application of the volume operator */
     memset(pn, 0, sizeof(double) * n3 * M);
     for (int d = 0; d < 3; ++d) {
-      /* g = (1/h) D applied along dimension d, all 9 quantities */
+      /* g = (1/h) D applied along dimension d, all 9 quantities (h = 1 on
+         curvilinear elements, whose metric carries the scale) */
       for (int z = 0; z < N; ++z)
         for (int y = 0; y < N; ++y)
           for (int x = 0; x < N; ++x) {
@@ -273,7 +279,20 @@ static void stp_element(int N, int K, double h, double dt, const double* D,
           }
       for (int n = 0; n < n3; ++n) {
         double B[M][M];
-        elastic_B(d, params[n * 3 + 0], params[n * 3 + 1], params[n * 3 + 2], B);
+        if (metric) {
+          /* reference direction d carries every physical direction j:
+             Bt_d = sum_j G[d][j] B_j, G[d][j] = dxi_d/dx_j at this node */
+          memset(B, 0, sizeof(double) * M * M);
+          for (int j = 0; j < 3; ++j) {
+            double Bj[M][M];
+            elastic_B(j, params[n * 3 + 0], params[n * 3 + 1], params[n * 3 + 2], Bj);
+            const double gdj = metric[n * 9 + 3 * d + j];
+            for (int r = 0; r < M; ++r)
+              for (int s = 0; s < M; ++s) B[r][s] += gdj * Bj[r][s];
+          }
+        } else {
+          elastic_B(d, params[n * 3 + 0], params[n * 3 + 1], params[n * 3 + 2], B);
+        }
         for (int r = 0; r < M; ++r) {
           double acc = 0.0;
           for (int s = 0; s < M; ++s) acc += B[r][s] * g[n * M + s];
@@ -334,7 +353,7 @@ int oracle_stp_nodes(int nodes, int N, int K, int64_t E, double h, double dt, co
     for (int64_t e = 0; e < E; ++e) {
       if (!work) continue;
       stp_element(N, K, h, dt, D, phi0, phi1, q + e * n3m,
-                  params + e * (n3m / M) * 3, NULL, avg + e * n3m,
+                  params + e * (n3m / M) * 3, NULL, NULL, avg + e * n3m,
                   faces + e * (size_t)6 * N * N * M,
                   terms ? terms + e * (size_t)K * n3m : NULL, work, work + n3m,
                   work + 2 * n3m);
@@ -399,7 +418,7 @@ int oracle_stp_sources(int nodes, int N, int K, int64_t E, double h, double dt, 
 #pragma omp for schedule(dynamic, 4)
       for (int64_t e = 0; e < E; ++e) {
         if (!work) continue;
-        stp_element(N, K, h, dt, D, phi0, phi1, q + e * n3m, params + e * n3 * 3, src[e],
+        stp_element(N, K, h, dt, D, phi0, phi1, q + e * n3m, params + e * n3 * 3, NULL, src[e],
                     avg + e * n3m, faces + e * (size_t)6 * N * N * M,
                     terms ? terms + e * (size_t)K * n3m : NULL, work, work + n3m, work + 2 * n3m);
       }
@@ -409,6 +428,46 @@ int oracle_stp_sources(int nodes, int N, int K, int64_t E, double h, double dt, 
   for (int64_t e = 0; e < E; ++e) free(src[e]);
   free(src);
   return err;
+}
+
+/*
+ * The STP on curvilinear elements. The paper's benchmark runs on curvilinear
+ * boundary-fitted meshes and stores 9 geometry parameters at every node beside
+ * the 3 material parameters (Sec. VI). Read here as the inverse Jacobian of
+ * the element map from the reference cube [0,1]^3 to physical space:
+ * metric[E][N][N][N][9] holds G[d][j] = dxi_d/dx_j at index 3d + j, where
+ * xi_1, xi_2, xi_3 run along the element's x, y, z node indices. The chain
+ * rule d/dx_j = sum_d G[d][j] d/dxi_d turns one CK step into
+ *   q^(k+1) = - sum_d (sum_j G[d][j] B_j) (D_d q^(k)),
+ * D applied along reference direction d with no 1/h (G carries the scale). A
+ * cube of side h has G = I/h and gives the Cartesian result. Faces are the
+ * reference faces xi_d = 0, 1.
+ */
+int oracle_stp_curvilinear(int nodes, int N, int K, int64_t E, double dt, const double* q,
+                           const double* params, const double* metric, double* avg,
+                           double* faces, double* terms) {
+  if (N < 1 || N > 16 || K < 1 || E < 0 || !metric) return -1;
+  double D[16 * 16], phi0[16], phi1[16];
+  if (oracle_tables_nodes(nodes, N, NULL, D, phi0, phi1) != 0) return -1;
+  const size_t n3 = (size_t)N * N * N, n3m = n3 * M;
+  int err = 0;
+#pragma omp parallel
+  {
+    double* work = (double*)malloc(sizeof(double) * 3 * n3m);
+    if (!work) {
+#pragma omp atomic write
+      err = 1;
+    }
+#pragma omp for schedule(dynamic, 4)
+    for (int64_t e = 0; e < E; ++e) {
+      if (!work) continue;
+      stp_element(N, K, 1.0, dt, D, phi0, phi1, q + e * n3m, params + e * n3 * 3,
+                  metric + e * n3 * 9, NULL, avg + e * n3m, faces + e * (size_t)6 * N * N * M,
+                  terms ? terms + e * (size_t)K * n3m : NULL, work, work + n3m, work + 2 * n3m);
+    }
+    free(work);
+  }
+  return err ? -2 : 0;
 }
 
 /* The STP on Gauss-Legendre nodes (the default node family). */

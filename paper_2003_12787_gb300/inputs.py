@@ -22,8 +22,18 @@ not available, so seeded synthetic fields of that shape stand in for them):
   q_s(x) = sum_w a[w,s] sin(k_w . x + ph[w,s]).
 * Time step dt = 0.4*h / ((2N-1) * max cp).
 
+Curvilinear elements (the paper's benchmark meshes are curvilinear and store
+9 geometry parameters per node, Sec. VI): the same grid pushed through the
+smooth map x_j = X_j + a/(2 pi) sin(2 pi X_{j+1}) sin(2 pi X_{j+2}) (indices
+mod 3, X the Cartesian position above, a = 0.2 by default), whose Jacobian
+I + a (...) is diagonally dominant for a < 1/2. Each node stores
+G = (h dx/dX)^-1, the inverse Jacobian of its element's map from the
+reference cube; the state is the same plane-wave sum evaluated at the mapped
+positions, and dt uses the smallest singular value s_min of dx/dX over the
+nodes: dt = 0.4*h*s_min / ((2N-1) * max cp).
+
 Layouts: q [E][N][N][N][9] (z,y,x,quantity), params [E][N][N][N][3]
-(rho, cp, cs), float64.
+(rho, cp, cs), metric [E][N][N][N][3][3] (G[d][j] = dxi_d/dx_j), float64.
 """
 from __future__ import annotations
 
@@ -46,6 +56,7 @@ class Problem:
     q: torch.Tensor       # [E][N][N][N][9] float64
     params: torch.Tensor  # [E][N][N][N][3] float64
     grid: tuple
+    metric: torch.Tensor | None = None  # [E][N][N][N][3][3] float64 (curvilinear)
 
     @property
     def order(self) -> int:
@@ -85,17 +96,8 @@ def material(N: int, E: int, seed_material: int) -> np.ndarray:
     return np.stack([rho, cp, cs], axis=-1)
 
 
-def elastic_problem(N: int, grid=None, E: int | None = None, h: float | None = None,
-                    seed_material: int = 1001, seed_waves: int = 1002,
-                    device: str | torch.device = "cpu", nodes: str = "gl") -> Problem:
-    """Build one seeded elastic STP input set.
-
-    grid: (Gx, Gy, Gz); if omitted, a cube of side ceil(E^(1/3)).
-    h: element side; default 1/max(grid). nodes: "gl" or "gll", the node
-    family the state is sampled on (it must match the predictor's).
-    The state is evaluated with torch on ``device`` (float64) so large inputs
-    can be generated where they are used; the random draws are numpy PCG64.
-    """
+def _grid(grid, E, h):
+    """(grid, E, h) with the defaults of ``elastic_problem`` filled in."""
     if grid is None:
         if E is None:
             raise ValueError("give grid or E")
@@ -110,6 +112,22 @@ def elastic_problem(N: int, grid=None, E: int | None = None, h: float | None = N
         raise ValueError("E larger than the grid")
     if h is None:
         h = 1.0 / max(grid)
+    return tuple(grid), E, h
+
+
+def elastic_problem(N: int, grid=None, E: int | None = None, h: float | None = None,
+                    seed_material: int = 1001, seed_waves: int = 1002,
+                    device: str | torch.device = "cpu", nodes: str = "gl") -> Problem:
+    """Build one seeded elastic STP input set.
+
+    grid: (Gx, Gy, Gz); if omitted, a cube of side ceil(E^(1/3)).
+    h: element side; default 1/max(grid). nodes: "gl" or "gll", the node
+    family the state is sampled on (it must match the predictor's).
+    The state is evaluated with torch on ``device`` (float64) so large inputs
+    can be generated where they are used; the random draws are numpy PCG64.
+    """
+    grid, E, h = _grid(grid, E, h)
+    Gx, Gy, Gz = grid
     params_np = material(N, E, seed_material)
     cp_max = float(params_np[..., 1].max()) if E > 0 else 5.0
     dt = 0.4 * h / ((2 * N - 1) * cp_max)
@@ -133,6 +151,51 @@ def elastic_problem(N: int, grid=None, E: int | None = None, h: float | None = N
             q[..., s] += float(amp[w, s]) * torch.sin(arg + float(phase[w, s]))
     params = torch.from_numpy(params_np).to(dev)
     return Problem(N=N, E=E, h=h, dt=dt, q=q, params=params, grid=tuple(grid))
+
+
+def curvilinear_problem(N: int, grid=None, E: int | None = None, h: float | None = None,
+                        seed_material: int = 1001, seed_waves: int = 1002, amplitude: float = 0.2,
+                        device: str | torch.device = "cpu", nodes: str = "gl") -> Problem:
+    """Seeded elastic STP input set on curvilinear elements: the grid of
+    ``elastic_problem`` pushed through the smooth map of the module recipe.
+    Returns a Problem whose ``metric`` holds the per-node inverse Jacobians."""
+    if not 0.0 <= amplitude < 0.5:
+        raise ValueError("amplitude must be in [0, 0.5) for an invertible map")
+    grid, E, h = _grid(grid, E, h)
+    Gx, Gy, Gz = grid
+    dev = torch.device(device)
+    xi = torch.tensor(sample_points(N, nodes), dtype=torch.float64, device=dev)
+    e = torch.arange(E, device=dev, dtype=torch.int64)
+    ex = (e % Gx).to(torch.float64)
+    ey = ((e // Gx) % Gy).to(torch.float64)
+    ez = (e // (Gx * Gy)).to(torch.float64)
+    shape = (E, N, N, N)
+    X = [((ex[:, None] + xi[None, :]) * h)[:, None, None, :].expand(shape),
+         ((ey[:, None] + xi[None, :]) * h)[:, None, :, None].expand(shape),
+         ((ez[:, None] + xi[None, :]) * h)[:, :, None, None].expand(shape)]
+    tw = 2.0 * math.pi
+    sn = [torch.sin(tw * c) for c in X]
+    cs_ = [torch.cos(tw * c) for c in X]
+    x = [X[j] + amplitude / tw * sn[(j + 1) % 3] * sn[(j + 2) % 3] for j in range(3)]
+    J = torch.zeros(shape + (3, 3), dtype=torch.float64, device=dev)  # dx_j/dX_m
+    for j in range(3):
+        J[..., j, j] = 1.0
+        J[..., j, (j + 1) % 3] = amplitude * cs_[(j + 1) % 3] * sn[(j + 2) % 3]
+        J[..., j, (j + 2) % 3] = amplitude * sn[(j + 1) % 3] * cs_[(j + 2) % 3]
+    metric = torch.linalg.inv(J) / h
+    s_min = float(torch.linalg.svdvals(J.reshape(-1, 3, 3)).min()) if E > 0 else 1.0
+    params = torch.from_numpy(material(N, E, seed_material)).to(dev)
+    cp_max = float(params[..., 1].max()) if E > 0 else 5.0
+    dt = 0.4 * h * s_min / ((2 * N - 1) * cp_max)
+    k, amp, phase = wave_parameters(seed_waves)
+    q = torch.zeros((E, N, N, N, M), dtype=torch.float64, device=dev)
+    for w in range(N_WAVES):
+        kx, ky, kz = (float(v) for v in k[w])
+        arg = kx * x[0] + ky * x[1] + kz * x[2]
+        for s in range(M):
+            q[..., s] += float(amp[w, s]) * torch.sin(arg + float(phase[w, s]))
+    return Problem(N=N, E=E, h=h, dt=dt, q=q, params=params, grid=grid,
+                   metric=metric.contiguous())
 
 
 # --- named workloads --------------------------------------------------------

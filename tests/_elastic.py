@@ -138,3 +138,28 @@ def rel_err(a, b):
     b = np.asarray(b)
     scale = np.abs(b).max()
     return float(np.abs(a - b).max() / (scale if scale > 0 else 1.0))
+
+
+def dense_operator_curvilinear(N, params, metric, nodes="gl"):
+    """Dense L of one curvilinear element, physical derivative first:
+    L = sum_j blockdiag_n(A_j(n)) (Dphys_j kron I_9) with
+    Dphys_j = sum_d diag_n(G_n[d][j]) D_d, D_d the reference derivative along
+    d (no 1/h: the metric G_n = dxi/dx at node n carries the scale).
+
+    params: [N][N][N][3]; metric: [N][N][N][3][3] (G[d][j] = dxi_d/dx_j).
+    """
+    D = lagrange_D_numpy(N, nodes)
+    I = np.eye(N)
+    Dd = [np.kron(np.kron(I, I), D), np.kron(np.kron(I, D), I), np.kron(np.kron(D, I), I)]
+    n3 = N ** 3
+    G = metric.reshape(n3, 3, 3)
+    flat = params.reshape(n3, 3)
+    A = [coefficient_matrices(*flat[n]) for n in range(n3)]
+    L = np.zeros((9 * n3, 9 * n3))
+    for j in range(3):
+        Dphys = sum(np.diag(G[:, d, j]) @ Dd[d] for d in range(3))
+        blk = np.zeros((9 * n3, 9 * n3))
+        for n in range(n3):
+            blk[9 * n:9 * n + 9, 9 * n:9 * n + 9] = A[n][j]
+        L += blk @ np.kron(Dphys, np.eye(9))
+    return L
