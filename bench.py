@@ -63,6 +63,16 @@ def flops_per_element_dense(N: int) -> int:
     return 54 * N ** 5 + 66 * N ** 4 + 108 * N ** 3
 
 
+def flops_per_element_curvilinear(N: int) -> int:
+    """Algorithmic FP64 flops of one curvilinear element: per CK step and node,
+    27 reference derivatives (54N flops), the chain rule through the metric
+    (27 x 3 products added into 9 physical sums: 108 flops, counting only the
+    18 nonzero couplings per direction as the elastic system needs them), the
+    pointwise update (48) and the average (18); faces as in the Cartesian
+    count: 54N^5 + 174N^4 + 108N^3."""
+    return 54 * N ** 5 + 174 * N ** 4 + 108 * N ** 3
+
+
 def bytes_per_element(N: int) -> int:
     """Algorithmic HBM bytes of one element: q (9N^3) + params (3N^3) in,
     avg (9N^3) + faces (54N^2) out, 8 bytes each."""
@@ -263,6 +273,51 @@ def mixed_comparison(stp, torch, args, workload="order9", precisions=PRECISIONS_
     for v in out["variants"].values():
         v["speedup_vs_fp64"] = base / v["ms_per_launch"]
     return out
+
+
+def curvilinear_measurement(stp, torch, args, cartesian_ms: float):
+    """The order-7 workload on curvilinear elements (the same 32^3 grid pushed
+    through a smooth map; 9 more per-node parameters, the inverse Jacobian):
+    CUDA-event time of one stp_predict_curvilinear launch (mean of
+    args.mixed_steps after 3 warm-ups), the algorithmic FP64 rate and the
+    error of 12 sampled elements against the oracle."""
+    import oracle
+    from paper_2003_12787_gb300.inputs import curvilinear_problem
+    N, grid, h, _ = WORKLOADS["order7"]
+    prob = curvilinear_problem(N, grid=grid, h=h, device="cuda")
+    E = prob.E
+    stream = torch.cuda.current_stream()
+    with stp.Predictor(N - 1, prob.h, prob.dt) as P:
+        avg, faces = P.empty_outputs(E)
+        for _ in range(3):
+            P.predict(prob.q, prob.params, out=(avg, faces), stream=stream, metric=prob.metric)
+        s0 = torch.cuda.Event(enable_timing=True)
+        s1 = torch.cuda.Event(enable_timing=True)
+        s0.record(stream)
+        for _ in range(args.mixed_steps):
+            P.predict(prob.q, prob.params, out=(avg, faces), stream=stream, metric=prob.metric)
+        s1.record(stream)
+        torch.cuda.synchronize()
+        ms = s0.elapsed_time(s1) / args.mixed_steps
+    rng = np.random.default_rng(8)
+    idx = np.unique(np.concatenate([[0, E - 1], rng.choice(E, 10, replace=False)]))
+    it = torch.as_tensor(idx, device="cuda")
+    a_ref, f_ref = oracle.stp_curvilinear(prob.q[it].cpu().numpy(), prob.params[it].cpu().numpy(),
+                                          prob.metric[it].cpu().numpy(), prob.dt)
+    a = avg[it].cpu().numpy()
+    f = faces[it].cpu().numpy()
+    err = max([float(np.abs(a - a_ref).max() / np.abs(a_ref).max())] +
+              [float(np.abs(f[:, i] - f_ref[:, i]).max() / np.abs(f_ref[:, i]).max())
+               for i in range(6)])
+    tf = E * flops_per_element_curvilinear(N) / (ms / 1e3) / 1e12
+    return {"workload": "order-7 (N=8) elastic STP on curvilinear elements, 32^3=32768 "
+                        "elements, smooth map of amplitude 0.2, one launch",
+            "elements": E, "ms_per_launch": ms, "elements_per_s": E / (ms / 1e3),
+            "flops_per_element": flops_per_element_curvilinear(N),
+            "tflops_algorithmic": tf, "frac_of_fp64_peak": tf / FP64_PEAK_TFLOPS,
+            "hbm_gbs": E * 8 * (30 * N ** 3 + 54 * N ** 2) / (ms / 1e3) / 1e9,
+            "time_vs_cartesian_fp64": ms / cartesian_ms,
+            "max_rel_err": err, "error_sample": f"{len(idx)} elements vs the oracle"}
 
 
 def small_case_latency(stp, torch, args):
@@ -534,6 +589,10 @@ def run_gpu(args):
         mixed = mixed_comparison(stp, torch, args)
         variants7 = mixed_comparison(stp, torch, args, workload=args.workload,
                                      precisions=("fp64", "ff", "fp32"))
+    curvilinear = None
+    if rank == 0 and world == 1 and not args.no_curvilinear and args.workload == "order7" \
+            and args.precision == "fp64":
+        curvilinear = curvilinear_measurement(stp, torch, args, statistics.mean(step_ms))
     small = None
     if rank == 0 and world == 1 and args.small_launches > 0:
         small = small_case_latency(stp, torch, args)
@@ -585,6 +644,7 @@ def run_gpu(args):
                            "min": min(step_ms), "max": max(step_ms)},
             "e2e": e2e, "cpu_baseline": cpu, "clocks": clocks, "mixed": mixed, "variants_same_workload": variants7,
             "small_case": small, "batched": batched, "served": served,
+            "curvilinear": curvilinear,
             "gpu_launches": args.steps, "parity_max_rel_sampled": parity,
         }
         print(json.dumps(line), flush=True)
@@ -651,6 +711,8 @@ def main():
     ap.add_argument("--batched-emax", type=int, default=16384,
                     help="largest set of the batched workload (smaller for profiler captures)")
     ap.add_argument("--no-served", action="store_true", help="skip the served workload")
+    ap.add_argument("--no-curvilinear", action="store_true",
+                    help="skip the curvilinear order-7 measurement")
     ap.add_argument("--small-launches", type=int, default=50,
                     help="timed launches of the order-3 latency measurement (0: skip)")
     ap.add_argument("--served-rate", type=float, default=2000.0)

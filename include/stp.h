@@ -123,6 +123,30 @@ stp_status stp_predict_sources(stp_handle h, int64_t elements, const double* q,
                                int nsources, const stp_point_source* sources, void* stream);
 
 /*
+ * The STP on curvilinear elements. The paper's benchmark meshes are
+ * curvilinear and boundary-fitted and store 9 geometry parameters per node
+ * beside the 3 material parameters (Sec. VI). Here those 9 are the inverse
+ * Jacobian of each element's map from the reference cube [0,1]^3 to physical
+ * space:
+ *   metric: device, [E][N][N][N][9] float64, (z,y,x) nodes as q, entry 3d + j
+ *           = G[d][j] = dxi_d/dx_j, where xi_1, xi_2, xi_3 run along the x, y,
+ *           z node indices.
+ * By the chain rule d/dx_j = sum_d G[d][j] d/dxi_d, so one Cauchy-Kowalewsky
+ * step is q^(k+1) = sum_d (sum_j G[d][j] A_j) (D_d q^(k)) with D along the
+ * reference direction d; a cube of side dx has G = I/dx and gives stp_predict's
+ * result up to rounding. The handle's dx only scales internal tables (the
+ * metric carries the geometry). Faces are the reference faces xi_d = 0, 1 in
+ * stp_predict's order; other buffers and their layouts as stp_predict.
+ * Asynchronous on `stream`, capturable like stp_predict.
+ * STP_ERR_UNSUPPORTED unless the handle's precision is STP_PRECISION_FP64;
+ * STP_ERR_INVALID_ARG for a NULL or unaligned metric, or one that overlaps an
+ * output. The library does not check that the metric is invertible.
+ */
+stp_status stp_predict_curvilinear(stp_handle h, int64_t elements, const double* q,
+                                   const double* params, const double* metric,
+                                   double* out_avg, double* out_faces, void* stream);
+
+/*
  * Same computation on HOST buffers (pinned host memory gives full copy
  * bandwidth; pageable memory works but copies slower). Synchronous: returns
  * once out_avg and out_faces hold the results. Elements are processed in

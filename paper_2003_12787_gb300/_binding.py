@@ -58,6 +58,7 @@ def load():
         lib.stp_get_nodes.argtypes = [vp]
         lib.stp_get_nodes.restype = ctypes.c_int
         lib.stp_predict_sources.argtypes = [vp, i64, vp, vp, vp, vp, ctypes.c_int, vp, vp]
+        lib.stp_predict_curvilinear.argtypes = [vp, i64, vp, vp, vp, vp, vp, vp]
         lib.stp_nodes.argtypes = [vp]
         lib.stp_nodes.restype = ctypes.c_int
         lib.stp_status_string.argtypes = [ctypes.c_int]
@@ -224,6 +225,14 @@ def stp_predict_sources(h: int, elements: int, q, params, out_avg, out_faces, so
                                       _ptr(out_faces), len(sources),
                                       ctypes.cast(arr, ctypes.c_void_p), _stream(stream)),
            "stp_predict_sources")
+
+
+def stp_predict_curvilinear(h: int, elements: int, q, params, metric, out_avg, out_faces,
+                            stream=None) -> None:
+    """metric: device [E][N][N][N][9] (or [..][3][3]) float64, dxi_d/dx_j at 3d + j."""
+    _check(load().stp_predict_curvilinear(h, elements, _ptr(q), _ptr(params), _ptr(metric),
+                                          _ptr(out_avg), _ptr(out_faces), _stream(stream)),
+           "stp_predict_curvilinear")
 
 
 class BatchSet(ctypes.Structure):

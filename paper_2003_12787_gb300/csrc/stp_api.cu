@@ -248,6 +248,36 @@ stp_status stp_predict(stp_handle h, int64_t elements, const double* q, const do
   return STP_OK;
 }
 
+stp_status stp_predict_curvilinear(stp_handle h, int64_t elements, const double* q,
+                                   const double* params, const double* metric, double* out_avg,
+                                   double* out_faces, void* stream) {
+  stp_status s = validate_common(h, elements, q, params, out_avg, out_faces);
+  if (s != STP_OK || elements == 0) return s;
+  if (!metric) return fail(STP_ERR_INVALID_ARG, "null metric");
+  if (!aligned16(metric)) return fail(STP_ERR_INVALID_ARG, "metric must be 16-byte aligned");
+  const Sizes sz = sizes_per_element(h->N);
+  const size_t E_ = (size_t)elements, nmetric = sz.q * E_;  // 9 doubles per node, like q
+  if (overlap(metric, nmetric, out_avg, sz.avg * E_) || overlap(metric, nmetric, out_faces, sz.faces * E_))
+    return fail(STP_ERR_INVALID_ARG, "an output overlaps the metric");
+  if (h->precision != STP_PRECISION_FP64)
+    return fail(STP_ERR_UNSUPPORTED, "curvilinear elements run in FP64 only");
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(static_cast<cudaStream_t>(stream), &cap) != cudaSuccess) {
+    cudaGetLastError();
+    cap = cudaStreamCaptureStatusNone;
+  }
+  if (cap == cudaStreamCaptureStatusNone) {
+    const char* names[5] = {"q", "params", "metric", "out_avg", "out_faces"};
+    const void* ptrs[5] = {q, params, metric, out_avg, out_faces};
+    for (int i = 0; i < 5; ++i)
+      if ((s = check_device_ptr(ptrs[i], h->device, names[i])) != STP_OK) return s;
+  }
+  cudaError_t e = stp::launch_curvilinear(h->N, elements, q, params, metric, out_avg, out_faces,
+                                          h->d_tables, h->dx, static_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) return cuda_fail(e, "curvilinear STP kernel launch");
+  return STP_OK;
+}
+
 namespace {
 
 // phi_j(a) for the handle's nodes (barycentric form, long double; a unit

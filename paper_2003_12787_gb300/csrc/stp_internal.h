@@ -64,6 +64,13 @@ bool ff_supported(int N);
 cudaError_t launch_ff(int N, int64_t E, const double* q, const double* params, double* out_avg,
                       double* out_faces, const double* tables, cudaStream_t stream);
 
+// FP64 STP on curvilinear elements (curvilinear.cu): metric [E][N][N][N][9]
+// holds the per-node inverse Jacobian dxi_d/dx_j at 3d + j; tables are the
+// handle's (step matrices scaled by 1/dx, undone with dx).
+cudaError_t launch_curvilinear(int N, int64_t E, const double* q, const double* params,
+                               const double* metric, double* out_avg, double* out_faces,
+                               const double* tables, double dx, cudaStream_t stream);
+
 // Point sources (sources.cu): after the STP of a set, adds the response of
 // the point sources to the outputs of the elements holding them (FP64, one
 // CTA per such element). groups[g] = (element, first source, source count);

@@ -28,9 +28,10 @@ smooth map x_j = X_j + a/(2 pi) sin(2 pi X_{j+1}) sin(2 pi X_{j+2}) (indices
 mod 3, X the Cartesian position above, a = 0.2 by default), whose Jacobian
 I + a (...) is diagonally dominant for a < 1/2. Each node stores
 G = (h dx/dX)^-1, the inverse Jacobian of its element's map from the
-reference cube; the state is the same plane-wave sum evaluated at the mapped
-positions, and dt uses the smallest singular value s_min of dx/dX over the
-nodes: dt = 0.4*h*s_min / ((2N-1) * max cp).
+reference cube (3x3 inverse by cofactors); the state is the same plane-wave
+sum evaluated at the mapped positions, and dt uses the bound 1 - 2a on the
+smallest singular value of dx/dX (each row of the perturbation has two
+entries of size <= a): dt = 0.4*h*(1 - 2a) / ((2N-1) * max cp).
 
 Layouts: q [E][N][N][N][9] (z,y,x,quantity), params [E][N][N][N][3]
 (rho, cp, cs), metric [E][N][N][N][3][3] (G[d][j] = dxi_d/dx_j), float64.
@@ -182,8 +183,15 @@ def curvilinear_problem(N: int, grid=None, E: int | None = None, h: float | None
         J[..., j, j] = 1.0
         J[..., j, (j + 1) % 3] = amplitude * cs_[(j + 1) % 3] * sn[(j + 2) % 3]
         J[..., j, (j + 2) % 3] = amplitude * sn[(j + 1) % 3] * cs_[(j + 2) % 3]
-    metric = torch.linalg.inv(J) / h
-    s_min = float(torch.linalg.svdvals(J.reshape(-1, 3, 3)).min()) if E > 0 else 1.0
+    # inverse by cofactors: inv[m][j] = cof[j][m] / det
+    cof = torch.empty_like(J)
+    for r in range(3):
+        for c in range(3):
+            r1, r2, c1, c2 = (r + 1) % 3, (r + 2) % 3, (c + 1) % 3, (c + 2) % 3
+            cof[..., r, c] = J[..., r1, c1] * J[..., r2, c2] - J[..., r1, c2] * J[..., r2, c1]
+    det = (J[..., 0, :] * cof[..., 0, :]).sum(-1)
+    metric = cof.transpose(-1, -2) / (det[..., None, None] * h)
+    s_min = 1.0 - 2.0 * amplitude
     params = torch.from_numpy(material(N, E, seed_material)).to(dev)
     cp_max = float(params[..., 1].max()) if E > 0 else 5.0
     dt = 0.4 * h * s_min / ((2 * N - 1) * cp_max)

@@ -64,15 +64,26 @@ class Predictor:
         if not (q.is_contiguous() and params.is_contiguous()):
             raise ValueError("q and params must be contiguous")
 
-    def predict(self, q: torch.Tensor, params: torch.Tensor, out=None, stream=None, sources=None):
+    def predict(self, q: torch.Tensor, params: torch.Tensor, out=None, stream=None, sources=None,
+                metric=None):
         """Enqueue on `stream` (default: torch's current stream) for device tensors.
-        sources: optional point sources (see stp_predict_sources)."""
+        sources: optional point sources (see stp_predict_sources).
+        metric: optional [E][N][N][N][3][3] (or [..][9]) float64 inverse
+        Jacobians dxi_d/dx_j of curvilinear elements (stp_predict_curvilinear)."""
         self._check_inputs(q, params)
         E = q.shape[0]
         avg, faces = out if out is not None else self.empty_outputs(E, device=q.device)
         if stream is None and q.is_cuda:
             stream = torch.cuda.current_stream(q.device)
-        if sources:
+        if metric is not None:
+            N = self.N
+            if sources:
+                raise ValueError("point sources are not supported on curvilinear elements")
+            if metric.dtype != torch.float64 or not metric.is_contiguous() or \
+                    metric.numel() != E * N ** 3 * 9 or metric.shape[:4] != q.shape[:4]:
+                raise ValueError(f"metric must be a contiguous float64 [E][{N}][{N}][{N}][3][3]")
+            B.stp_predict_curvilinear(self.handle, E, q, params, metric, avg, faces, stream)
+        elif sources:
             B.stp_predict_sources(self.handle, E, q, params, avg, faces, sources, stream)
         else:
             B.stp_predict(self.handle, E, q, params, avg, faces, stream)

@@ -1,0 +1,151 @@
+"""GPU parity of the STP on curvilinear elements against the oracle.
+
+The paper's benchmark meshes are curvilinear (Sec. VI: 9 geometry parameters
+per node beside the 3 material parameters). stp_predict_curvilinear takes the
+per-node inverse Jacobian dxi_d/dx_j; the oracle applies the chain rule with
+dense 9x9 matrices (oracle_stp_curvilinear). FP64 bar: normwise 1e-12 per
+output array.
+"""
+from __future__ import annotations
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import paper_2003_12787_gb300 as stp
+from paper_2003_12787_gb300 import _binding
+from paper_2003_12787_gb300.inputs import curvilinear_problem, elastic_problem
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-12
+
+
+def rel(a, b):
+    s = np.abs(b).max()
+    return float(np.abs(a - b).max() / (s if s > 0 else 1.0))
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    stp.build.build()
+    _binding.load()
+
+
+def run(prob, nodes="gl", metric=None):
+    with stp.Predictor(prob.N - 1, prob.h, prob.dt, nodes=nodes) as P:
+        avg, faces = P.predict(prob.q.cuda(), prob.params.cuda(),
+                               metric=(prob.metric if metric is None else metric).cuda())
+        torch.cuda.synchronize()
+    return avg.cpu().numpy(), faces.cpu().numpy()
+
+
+def check(prob, avg, faces, nodes="gl", idx=None):
+    q = prob.q.numpy() if idx is None else prob.q[idx].numpy()
+    p = prob.params.numpy() if idx is None else prob.params[idx].numpy()
+    m = prob.metric.numpy() if idx is None else prob.metric[idx].numpy()
+    a_ref, f_ref = oracle.stp_curvilinear(q, p, m, prob.dt, nodes=nodes)
+    errs = [rel(avg, a_ref)] + [rel(faces[:, f], f_ref[:, f]) for f in range(6)]
+    assert max(errs) <= TOL, errs
+    return errs
+
+
+@pytest.mark.parametrize("N", list(range(1, 13)))
+def test_curvilinear_parity_every_order(N):
+    """A ragged element count (not a multiple of anything), heterogeneous
+    material, a map whose metric varies from node to node."""
+    prob = curvilinear_problem(N, grid=(8, 8, 4), E=5 if N >= 9 else 37, seed_material=1500 + N,
+                               seed_waves=1600 + N)
+    avg, faces = run(prob)
+    check(prob, avg, faces)
+
+
+@pytest.mark.parametrize("N", [2, 5, 8, 12])
+def test_curvilinear_gauss_lobatto(N):
+    prob = curvilinear_problem(N, grid=(8, 8, 4), E=6, seed_material=1700 + N,
+                               seed_waves=1800 + N, nodes="gll")
+    avg, faces = run(prob, nodes="gll")
+    check(prob, avg, faces, nodes="gll")
+
+
+@pytest.mark.parametrize("N", [4, 8, 11])
+def test_cube_metric_matches_cartesian_path(N):
+    """G = I/h: the curvilinear kernel reproduces stp_predict (different
+    kernels and rounding order, so to 1e-13, not bitwise)."""
+    prob = elastic_problem(N, grid=(32, 32, 16), h=1.0 / 32, E=9, seed_material=1900 + N,
+                           seed_waves=1950 + N)
+    G = torch.zeros((prob.E, N, N, N, 3, 3), dtype=torch.float64)
+    G[...] = torch.eye(3, dtype=torch.float64) / prob.h
+    prob.metric = G
+    a_c, f_c = run(prob)
+    with stp.Predictor(N - 1, prob.h, prob.dt) as P:
+        a, f = P.predict(prob.q.cuda(), prob.params.cuda())
+        torch.cuda.synchronize()
+    assert rel(a_c, a.cpu().numpy()) <= 1e-13 and rel(f_c, f.cpu().numpy()) <= 1e-13
+
+
+def test_full_order7_workload_sampled():
+    """The benchmark's curvilinear order-7 workload (32^3 elements), in the
+    launch the benchmark times; 48 sampled elements against the oracle."""
+    prob = curvilinear_problem(8, grid=(32, 32, 32), device="cuda")
+    with stp.Predictor(7, prob.h, prob.dt) as P:
+        avg, faces = P.predict(prob.q, prob.params, metric=prob.metric)
+        torch.cuda.synchronize()
+    rng = np.random.default_rng(11)
+    idx = np.sort(np.concatenate([[0, prob.E - 1], rng.choice(prob.E, 46, replace=False)]))
+    t = torch.as_tensor(idx, device="cuda")
+    sub = type(prob)(N=8, E=len(idx), h=prob.h, dt=prob.dt, q=prob.q[t].cpu(),
+                     params=prob.params[t].cpu(), grid=prob.grid, metric=prob.metric[t].cpu())
+    check(sub, avg[t].cpu().numpy(), faces[t].cpu().numpy())
+
+
+def test_element_independence_and_graph_capture():
+    N = 7
+    prob = curvilinear_problem(N, grid=(8, 8, 8), E=300, seed_material=2001, seed_waves=2002,
+                               device="cuda")
+    perm = torch.randperm(prob.E, generator=torch.Generator().manual_seed(3)).cuda()
+    with stp.Predictor(N - 1, prob.h, prob.dt) as P:
+        a, f = P.predict(prob.q, prob.params, metric=prob.metric)
+        ap, fp = P.predict(prob.q[perm].contiguous(), prob.params[perm].contiguous(),
+                           metric=prob.metric[perm].contiguous())
+        s = torch.cuda.Stream()
+        out = P.empty_outputs(prob.E)
+        torch.cuda.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=s):
+            P.predict(prob.q, prob.params, out=out, metric=prob.metric)
+        g.replay()
+        torch.cuda.synchronize()
+    assert torch.equal(ap, a[perm]) and torch.equal(fp, f[perm])
+    assert torch.equal(out[0], a) and torch.equal(out[1], f)
+
+
+def test_argument_errors():
+    N = 4
+    prob = curvilinear_problem(N, E=8, device="cuda")
+    E = prob.E
+    with stp.Predictor(N - 1, prob.h, prob.dt) as P:
+        avg, faces = P.empty_outputs(E)
+        h = P.handle
+        m = prob.metric
+        with pytest.raises(stp.STPError) as ei:
+            _binding.stp_predict_curvilinear(h, E, prob.q, prob.params, None, avg, faces)
+        assert ei.value.status == _binding.STP_ERR_INVALID_ARG
+        with pytest.raises(stp.STPError) as ei:  # metric overlapping an output
+            _binding.stp_predict_curvilinear(h, E, prob.q, prob.params, avg, avg, faces)
+        assert ei.value.status == _binding.STP_ERR_INVALID_ARG
+        with pytest.raises(stp.STPError) as ei:  # host metric
+            _binding.stp_predict_curvilinear(h, E, prob.q, prob.params, m.cpu(), avg, faces)
+        assert ei.value.status == _binding.STP_ERR_INVALID_ARG
+        _binding.stp_predict_curvilinear(h, 0, prob.q, prob.params, None, avg, faces)  # E = 0
+        with pytest.raises(ValueError):
+            P.predict(prob.q, prob.params, metric=m[:, :, :, :, :2])
+        P.predict(prob.q, prob.params, metric=m)  # valid after the errors
+        torch.cuda.synchronize()
+    with stp.Predictor(N - 1, prob.h, prob.dt, precision="ff") as P:
+        with pytest.raises(stp.STPError) as ei:
+            P.predict(prob.q, prob.params, metric=m)
+        assert ei.value.status == _binding.STP_ERR_UNSUPPORTED
