@@ -205,9 +205,10 @@ def cpu_model() -> str:
     return platform.processor() or platform.machine()
 
 
-def oracle_baseline(prob_q, prob_params, h, dt, budget_s: float, max_elems: int):
+def oracle_baseline(prob_q, prob_params, h, dt, budget_s: float, max_elems: int, metric=None):
     """Time the oracle as it stands on a bounded sample (elements from the
-    front of the workload, in chunks, until the time budget is spent)."""
+    front of the workload, in chunks, until the time budget is spent);
+    curvilinear elements when a metric is given."""
     import oracle
     E = prob_q.shape[0]
     done, spent, chunk = 0, 0.0, 256
@@ -216,7 +217,10 @@ def oracle_baseline(prob_q, prob_params, h, dt, budget_s: float, max_elems: int)
         q = np.ascontiguousarray(prob_q[done:done + n])
         p = np.ascontiguousarray(prob_params[done:done + n])
         t0 = time.perf_counter()
-        oracle.stp(q, p, h, dt)
+        if metric is None:
+            oracle.stp(q, p, h, dt)
+        else:
+            oracle.stp_curvilinear(q, p, np.ascontiguousarray(metric[done:done + n]), dt)
         spent += time.perf_counter() - t0
         done += n
         chunk = min(chunk * 2, 4096)
@@ -514,8 +518,19 @@ def run_gpu(args):
     from paper_2003_12787_gb300.inputs import elastic_problem
 
     N, grid, h, desc = WORKLOADS[args.workload]
-    prob = elastic_problem(N, grid=grid, h=h, seed_material=1001 + 16 * rank,
-                           seed_waves=1002 + 16 * rank, device="cuda")
+    curv = args.geometry == "curvilinear"
+    if curv:
+        from paper_2003_12787_gb300.inputs import curvilinear_problem
+        if args.precision != "fp64":
+            raise SystemExit("curvilinear elements run in FP64 only")
+        prob = curvilinear_problem(N, grid=grid, h=h, seed_material=1001 + 16 * rank,
+                                   seed_waves=1002 + 16 * rank, device="cuda")
+        desc = desc.replace("elastic STP,", "elastic STP on curvilinear elements (smooth map "
+                                            "of amplitude 0.2),")
+    else:
+        prob = elastic_problem(N, grid=grid, h=h, seed_material=1001 + 16 * rank,
+                               seed_waves=1002 + 16 * rank, device="cuda")
+    metric = prob.metric  # None on Cartesian cubes
     E = prob.E
     dev = torch.device("cuda", torch.cuda.current_device())
     stream = torch.cuda.current_stream(dev)
@@ -525,7 +540,7 @@ def run_gpu(args):
     fp64_probe = stp.stp_measure_fp64_peak(stream)
 
     for _ in range(args.warmup):
-        P.predict(prob.q, prob.params, out=(avg, faces), stream=stream)
+        P.predict(prob.q, prob.params, out=(avg, faces), stream=stream, metric=metric)
     torch.cuda.synchronize()
     barrier(world)
     torch.cuda.synchronize()
@@ -540,7 +555,7 @@ def run_gpu(args):
     t_all0.record(stream)
     for i in range(args.steps):
         starts[i].record(stream)
-        P.predict(prob.q, prob.params, out=(avg, faces), stream=stream)
+        P.predict(prob.q, prob.params, out=(avg, faces), stream=stream, metric=metric)
         ends[i].record(stream)
     t_all1.record(stream)
     torch.cuda.synchronize()
@@ -557,8 +572,13 @@ def run_gpu(args):
     if rank == 0:
         import oracle
         idx = torch.tensor([0, E // 3, E - 1], device=dev)
-        a_ref, f_ref = oracle.stp(prob.q[idx].cpu().numpy(), prob.params[idx].cpu().numpy(),
-                                  prob.h, prob.dt)
+        if curv:
+            a_ref, f_ref = oracle.stp_curvilinear(prob.q[idx].cpu().numpy(),
+                                                  prob.params[idx].cpu().numpy(),
+                                                  metric[idx].cpu().numpy(), prob.dt)
+        else:
+            a_ref, f_ref = oracle.stp(prob.q[idx].cpu().numpy(), prob.params[idx].cpu().numpy(),
+                                      prob.h, prob.dt)
         a = avg[idx].cpu().numpy()
         f = faces[idx].cpu().numpy()
         parity = max(float(np.abs(a - a_ref).max() / np.abs(a_ref).max()),
@@ -566,7 +586,7 @@ def run_gpu(args):
 
     # end to end through the host-buffer entry point (pinned memory)
     e2e = None
-    if not args.no_e2e:
+    if not args.no_e2e and not curv:
         qh = prob.q.cpu().pin_memory()
         ph = prob.params.cpu().pin_memory()
         ah, fh = P.empty_outputs(E, device="cpu", pin_memory=True)
@@ -584,30 +604,32 @@ def run_gpu(args):
         if not np.array_equal(ah[:4].numpy(), avg[:4].cpu().numpy()):
             e2e["mismatch_vs_device_path"] = True
 
+    extras = rank == 0 and world == 1 and not curv
     mixed = variants7 = None
-    if rank == 0 and world == 1 and not args.no_mixed:
+    if extras and not args.no_mixed:
         mixed = mixed_comparison(stp, torch, args)
         variants7 = mixed_comparison(stp, torch, args, workload=args.workload,
                                      precisions=("fp64", "ff", "fp32"))
     curvilinear = None
-    if rank == 0 and world == 1 and not args.no_curvilinear and args.workload == "order7" \
+    if extras and not args.no_curvilinear and args.workload == "order7" \
             and args.precision == "fp64":
         curvilinear = curvilinear_measurement(stp, torch, args, statistics.mean(step_ms))
     small = None
-    if rank == 0 and world == 1 and args.small_launches > 0:
+    if extras and args.small_launches > 0:
         small = small_case_latency(stp, torch, args)
     batched = None
-    if rank == 0 and world == 1 and not args.no_batched:
+    if extras and not args.no_batched:
         batched = batched_measurement(stp, torch, args)
     served = None
-    if rank == 0 and world == 1 and not args.no_served:
+    if extras and not args.no_served:
         served = served_measurement(stp, torch, args)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         qn = prob.q.cpu().numpy()
         pn = prob.params.cpu().numpy()
-        done, spent, cores = oracle_baseline(qn, pn, prob.h, prob.dt, args.cpu_budget, E)
+        mn = metric.cpu().numpy() if curv else None
+        done, spent, cores = oracle_baseline(qn, pn, prob.h, prob.dt, args.cpu_budget, E, mn)
         cpu = {"value": done / spent, "unit": UNIT, "cores": cores, "cpu": cpu_model(),
                "kind": "oracle",
                "sample": f"first {done} of {E} elements of the same workload, "
@@ -615,10 +637,12 @@ def run_gpu(args):
 
     if rank == 0:
         mean_step_s = statistics.mean(step_ms) / 1e3
-        achieved = E * flops_per_element(N) / mean_step_s / 1e12
+        fpe = flops_per_element_curvilinear(N) if curv else flops_per_element(N)
+        bpe = 8 * (30 * N ** 3 + 54 * N ** 2) if curv else bytes_per_element(N)
+        achieved = E * fpe / mean_step_s / 1e12
         srt = sorted(step_ms)
         p99 = srt[min(len(srt) - 1, int(math.ceil(0.99 * len(srt))) - 1)]
-        traffic = traffic_from_profile(args.workload)
+        traffic = None if curv else traffic_from_profile(args.workload)
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms_max / args.steps,
@@ -628,7 +652,8 @@ def run_gpu(args):
             "config": {"workload": desc, "N": N, "order": N - 1, "elements": E,
                        "elements_per_gpu": E, "dt": prob.dt, "dx": prob.h,
                        "l2": "inputs larger than L2: %.2f GB read + %.2f GB written per step"
-                             % (E * 8 * 12 * N ** 3 / 1e9, E * 8 * (9 * N ** 3 + 54 * N ** 2) / 1e9),
+                             % (E * 8 * (21 if curv else 12) * N ** 3 / 1e9,
+                                E * 8 * (9 * N ** 3 + 54 * N ** 2) / 1e9),
                        "parallelism": f"dp{world} (element partitions, no collective)"},
             "roofline": {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
                          "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
@@ -636,10 +661,11 @@ def run_gpu(args):
                          "peak_kind": "derived: 152 SM x 2 DFMA/clk x 2 flop x 2.07 GHz",
                          "fp64_probe_tflops": fp64_probe / 1e3,
                          "frac_of_probe": achieved / (fp64_probe / 1e3),
-                         "flops_per_element": flops_per_element(N),
-                         "flops_per_element_dense_count": flops_per_element_dense(N),
-                         "tflops_dense_count": E * flops_per_element_dense(N) / mean_step_s / 1e12,
-                         "hbm_gbs": E * bytes_per_element(N) / mean_step_s / 1e9},
+                         "flops_per_element": fpe,
+                         "flops_per_element_dense_count": None if curv else flops_per_element_dense(N),
+                         "tflops_dense_count": None if curv else
+                         E * flops_per_element_dense(N) / mean_step_s / 1e12,
+                         "hbm_gbs": E * bpe / mean_step_s / 1e9},
             "latency_ms": {"p50": statistics.median(step_ms), "p99": p99,
                            "min": min(step_ms), "max": max(step_ms)},
             "e2e": e2e, "cpu_baseline": cpu, "clocks": clocks, "mixed": mixed, "variants_same_workload": variants7,
@@ -713,6 +739,9 @@ def main():
     ap.add_argument("--no-served", action="store_true", help="skip the served workload")
     ap.add_argument("--no-curvilinear", action="store_true",
                     help="skip the curvilinear order-7 measurement")
+    ap.add_argument("--geometry", choices=["cartesian", "curvilinear"], default="cartesian",
+                    help="time the main workload on Cartesian cubes (default) or on "
+                         "curvilinear elements (FP64; no host-buffer path, no extras)")
     ap.add_argument("--small-launches", type=int, default=50,
                     help="timed launches of the order-3 latency measurement (0: skip)")
     ap.add_argument("--served-rate", type=float, default=2000.0)

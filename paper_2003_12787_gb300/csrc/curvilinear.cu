@@ -23,13 +23,15 @@
 // from which the last pass of the step forms r_{k+1} with the node's elastic
 // coefficients. Taylor bookkeeping as in the Cartesian kernels: the step
 // tables hold D dt/((k+2) dx), so the coefficients are multiplied by dx once.
+#include <type_traits>
+
 #include "ck_fp64.cuh"
 #include "stp_internal.h"
 
 namespace stp {
 namespace {
 
-template <int N, int A>
+template <int N, int A, bool DB>
 struct CurvShape {
   static constexpr int N3 = N * N * N;
   static constexpr int RX = N | 1;  // x rows padded to an odd length
@@ -41,7 +43,8 @@ struct CurvShape {
   static constexpr int STEP_TABLE = 2 * H * H + (ODD ? 2 * H : 0);
   static constexpr int TABLE = N * STEP_TABLE + 2 * N;
   static constexpr int SUBS = (kQuantities + A - 1) / A;  // line passes per direction
-  static constexpr size_t SMEM = sizeof(double) * (size_t)(TABLE + (kQuantities + A) * S);
+  static constexpr size_t SMEM =
+      sizeof(double) * (size_t)(TABLE + (kQuantities + (DB ? 2 : 1) * A) * S);
 };
 
 // Adds the contributions of quantity s, whose derivative along reference
@@ -87,24 +90,27 @@ __device__ __forceinline__ void curv_add(int s, double a, double g0, double g1, 
 // One element per CTA of NT threads; thread t owns nodes t, t + NT, ...
 // (NODES of them). LEAN keeps only the partial sums in registers: the running
 // average accumulates in the output buffer and the coefficients are derived
-// from params at every step (large N, where registers are short).
-template <int N, int NT, int NODES, int A, bool LEAN>
+// from params at every step (large N, where registers are short). GREG keeps
+// the owned nodes' metric in registers instead of reading it through L1. DB
+// double-buffers the reference derivatives (A = 9 only).
+template <int N, int NT, int NODES, int A, bool LEAN, bool GREG, bool DB>
 __global__ void __launch_bounds__(NT, 1)
 curv_eo_kernel(const double* __restrict__ q, const double* __restrict__ params,
                const double* __restrict__ metric, double* __restrict__ out_avg,
                double* __restrict__ out_faces, const double* __restrict__ tables, double dx) {
-  using Sh = CurvShape<N, A>;
+  using Sh = CurvShape<N, A, DB>;
   constexpr int N3 = Sh::N3, S = Sh::S, H = Sh::H, M = kQuantities;
   constexpr int RX = Sh::RX, PLANE = Sh::PLANE, SUBS = Sh::SUBS;
   constexpr bool ODD = Sh::ODD;
   constexpr int mid = H;
   static_assert(NODES * NT >= N3, "every node needs an owner");
+  static_assert(SUBS <= 2 && (!DB || SUBS == 1), "one or two line passes per direction");
   auto pad = [](int n) { return (n / (N * N)) * PLANE + ((n / N) % N) * RX + n % N; };
   extern __shared__ double smem[];
   double* sT = smem;                       // [N steps][STEP_TABLE]
   double* sPhi = sT + N * Sh::STEP_TABLE;  // phi0[N], phi1[N]
   double* sp = sPhi + 2 * N;               // current term r_k [9][S]; the average at the end
-  double* sacc = sp + M * S;               // reference derivatives of one pass [A][S]
+  double* sacc = sp + M * S;               // reference derivatives of a pass [DB ? 2 : 1][A][S]
   const int tid = threadIdx.x;
   const int64_t e = blockIdx.x;
   double* gavg = out_avg + e * (int64_t)(M * N3);
@@ -143,6 +149,15 @@ curv_eo_kernel(const double* __restrict__ q, const double* __restrict__ params,
   constexpr int KEEP = LEAN ? 1 : NODES;  // nodes whose coefficients and average stay in registers
   double cf[KEEP][4];
   double avg[KEEP][M];
+  double gm[GREG ? NODES : 1][9];
+  if constexpr (GREG) {
+#pragma unroll
+    for (int j = 0; j < NODES; ++j) {
+      const int n = tid + j * NT;
+#pragma unroll
+      for (int c = 0; c < 9; ++c) gm[j][c] = n < N3 ? __ldg(ge + 9 * n + c) : 0.0;
+    }
+  }
   if constexpr (!LEAN) {
 #pragma unroll
     for (int j = 0; j < NODES; ++j) {
@@ -166,113 +181,149 @@ curv_eo_kernel(const double* __restrict__ q, const double* __restrict__ params,
     }
   }
 
-  for (int k = 0; k < N; ++k) {
+  double part[NODES][9];
+
+  // Line pass of direction d: reference derivatives of quantities
+  // sub*A .. sub*A+nq-1 of the current term into dst[A][S].
+  auto line_pass = [&](int k, int d, int sub, double* dst_base) {
     const double* Et = sT + k * Sh::STEP_TABLE;
     const double* Ot = Et + H * H;
     const double* Dm = Ot + H * H;  // odd N: middle column (rows < h)
     const double* Om = Dm + H;      // odd N: middle row odd part
-    double part[NODES][9];
+    const int nq = (M - sub * A) < A ? (M - sub * A) : A;
+    for (int task = tid; task < nq * N * N; task += NT) {
+      const int ql = task / (N * N);
+      const int a = (task / N) % N, b = task % N;  // line position (slower, faster)
+      int base, stride;
+      if (d == 0) { base = a * PLANE + b * RX; stride = 1; }   // (z, y), along x
+      else if (d == 1) { base = a * PLANE + b; stride = RX; }  // (z, x), along y
+      else { base = a * RX + b; stride = PLANE; }              // (y, x), along z
+      const double* u = sp + (sub * A + ql) * S + base;
+      double ev[H > 0 ? H : 1], od[H > 0 ? H : 1];
+#pragma unroll
+      for (int l = 0; l < H; ++l) {
+        const double lo = u[l * stride], hi = u[(N - 1 - l) * stride];
+        ev[l] = lo + hi;
+        od[l] = lo - hi;
+      }
+      double out[N];
+#pragma unroll
+      for (int i = 0; i < H; ++i) {
+        double P = 0.0, Q = 0.0;
+#pragma unroll
+        for (int l = 0; l < H; ++l) {
+          P = fma(Et[i * H + l], ev[l], P);
+          Q = fma(Ot[i * H + l], od[l], Q);
+        }
+        if (ODD) P = fma(Dm[i], u[mid * stride], P);
+        out[i] = P + Q;
+        out[N - 1 - i] = Q - P;
+      }
+      if (ODD) {
+        double Q = 0.0;
+#pragma unroll
+        for (int l = 0; l < H; ++l) Q = fma(Om[l], od[l], Q);
+        out[mid] = Q;
+      }
+      double* dst = dst_base + ql * S + base;
+#pragma unroll
+      for (int i = 0; i < N; ++i) dst[i * stride] = out[i];
+    }
+  };
+
+  // Pointwise pass of direction d: metric row d times the reference
+  // derivatives in src[A][S], into the partial sums; the last pass of a step
+  // forms r_{k+1}, adds it to the average and stores it as the next term.
+  auto pointwise = [&](int k, int d, auto SUB, const double* src, bool last) {
+    constexpr int sub = decltype(SUB)::value;
+#pragma unroll
+    for (int j = 0; j < NODES; ++j) {
+      const int n = tid + j * NT;
+      if (n >= N3) continue;
+      const int pn = pad(n);
+      double g0, g1, g2;
+      if constexpr (GREG) {
+        g0 = d == 0 ? gm[j][0] : d == 1 ? gm[j][3] : gm[j][6];
+        g1 = d == 0 ? gm[j][1] : d == 1 ? gm[j][4] : gm[j][7];
+        g2 = d == 0 ? gm[j][2] : d == 1 ? gm[j][5] : gm[j][8];
+      } else {
+        g0 = __ldg(ge + 9 * n + 3 * d);
+        g1 = __ldg(ge + 9 * n + 3 * d + 1);
+        g2 = __ldg(ge + 9 * n + 3 * d + 2);
+      }
+#pragma unroll
+      for (int ql = 0; ql < A; ++ql) {
+        constexpr int s0 = sub * A;
+        if (s0 + ql < M) curv_add(s0 + ql, src[ql * S + pn], g0, g1, g2, part[j]);
+      }
+      if (!last) continue;
+      double invrho, lam, mu, mu2;
+      if constexpr (LEAN) {
+        elastic_coefficients(__ldg(pe + 3 * n), __ldg(pe + 3 * n + 1), __ldg(pe + 3 * n + 2),
+                             &invrho, &lam, &mu, &mu2);
+        invrho *= dx; lam *= dx; mu *= dx; mu2 *= dx;
+      } else {
+        invrho = cf[j][0]; lam = cf[j][1]; mu = cf[j][2]; mu2 = cf[j][3];
+      }
+      const double* pj = part[j];
+      const double ltr = lam * ((pj[kS11] + pj[kS22]) + pj[kS33]);
+      double r[9];
+      r[kV1] = invrho * pj[kV1];
+      r[kV2] = invrho * pj[kV2];
+      r[kV3] = invrho * pj[kV3];
+      r[kS11] = fma(mu2, pj[kS11], ltr);
+      r[kS22] = fma(mu2, pj[kS22], ltr);
+      r[kS33] = fma(mu2, pj[kS33], ltr);
+      r[kS12] = mu * pj[kS12];
+      r[kS13] = mu * pj[kS13];
+      r[kS23] = mu * pj[kS23];
+#pragma unroll
+      for (int s = 0; s < M; ++s) {
+        if constexpr (LEAN) {
+          const double v = gavg[n * M + s] + r[s];
+          if (k + 1 < N) {
+            gavg[n * M + s] = v;
+            sp[s * S + pn] = r[s];
+          } else {
+            sp[s * S + pn] = v;  // final average, staged for the store
+          }
+        } else {
+          avg[j][s] += r[s];
+          if (k + 1 < N) sp[s * S + pn] = r[s];
+        }
+      }
+    }
+  };
+
+  for (int k = 0; k < N; ++k) {
 #pragma unroll
     for (int j = 0; j < NODES; ++j)
 #pragma unroll
       for (int c = 0; c < 9; ++c) part[j][c] = 0.0;
+    if constexpr (DB) {
+      // double-buffered: the pointwise pass of direction d and the line pass
+      // of direction d+1 share a phase (4 barriers per step instead of 6)
+      line_pass(k, 0, 0, sacc);
+      __syncthreads();
 #pragma unroll 1
-    for (int d = 0; d < 3; ++d) {
-#pragma unroll
-      for (int sub = 0; sub < SUBS; ++sub) {
-        const int nq = (M - sub * A) < A ? (M - sub * A) : A;
-        // line pass: reference derivatives of quantities sub*A .. sub*A+nq-1
-        for (int task = tid; task < nq * N * N; task += NT) {
-          const int ql = task / (N * N);
-          const int a = (task / N) % N, b = task % N;  // line position (slower, faster)
-          int base, stride;
-          if (d == 0) { base = a * PLANE + b * RX; stride = 1; }   // (z, y), along x
-          else if (d == 1) { base = a * PLANE + b; stride = RX; }  // (z, x), along y
-          else { base = a * RX + b; stride = PLANE; }              // (y, x), along z
-          const double* u = sp + (sub * A + ql) * S + base;
-          double ev[H > 0 ? H : 1], od[H > 0 ? H : 1];
-#pragma unroll
-          for (int l = 0; l < H; ++l) {
-            const double lo = u[l * stride], hi = u[(N - 1 - l) * stride];
-            ev[l] = lo + hi;
-            od[l] = lo - hi;
-          }
-          double out[N];
-#pragma unroll
-          for (int i = 0; i < H; ++i) {
-            double P = 0.0, Q = 0.0;
-#pragma unroll
-            for (int l = 0; l < H; ++l) {
-              P = fma(Et[i * H + l], ev[l], P);
-              Q = fma(Ot[i * H + l], od[l], Q);
-            }
-            if (ODD) P = fma(Dm[i], u[mid * stride], P);
-            out[i] = P + Q;
-            out[N - 1 - i] = Q - P;
-          }
-          if (ODD) {
-            double Q = 0.0;
-#pragma unroll
-            for (int l = 0; l < H; ++l) Q = fma(Om[l], od[l], Q);
-            out[mid] = Q;
-          }
-          double* dst = sacc + ql * S + base;
-#pragma unroll
-          for (int i = 0; i < N; ++i) dst[i * stride] = out[i];
-        }
+      for (int d = 0; d < 3; ++d) {
+        if (d < 2) line_pass(k, d + 1, 0, sacc + ((d + 1) & 1) * (A * S));
+        pointwise(k, d, std::integral_constant<int, 0>{}, sacc + (d & 1) * (A * S), d == 2);
         __syncthreads();
-        // pointwise pass: metric row d times the reference derivatives
-        const bool last = (d == 2) && (sub == SUBS - 1);
-#pragma unroll
-        for (int j = 0; j < NODES; ++j) {
-          const int n = tid + j * NT;
-          if (n >= N3) continue;
-          const int pn = pad(n);
-          const double g0 = __ldg(ge + 9 * n + 3 * d), g1 = __ldg(ge + 9 * n + 3 * d + 1),
-                       g2 = __ldg(ge + 9 * n + 3 * d + 2);
-#pragma unroll
-          for (int ql = 0; ql < A; ++ql) {
-            const int s = sub * A + ql;
-            if (s < M) curv_add(s, sacc[ql * S + pn], g0, g1, g2, part[j]);
-          }
-          if (!last) continue;
-          double invrho, lam, mu, mu2;
-          if constexpr (LEAN) {
-            elastic_coefficients(__ldg(pe + 3 * n), __ldg(pe + 3 * n + 1), __ldg(pe + 3 * n + 2),
-                                 &invrho, &lam, &mu, &mu2);
-            invrho *= dx; lam *= dx; mu *= dx; mu2 *= dx;
-          } else {
-            invrho = cf[j][0]; lam = cf[j][1]; mu = cf[j][2]; mu2 = cf[j][3];
-          }
-          const double* pj = part[j];
-          const double ltr = lam * ((pj[kS11] + pj[kS22]) + pj[kS33]);
-          double r[9];
-          r[kV1] = invrho * pj[kV1];
-          r[kV2] = invrho * pj[kV2];
-          r[kV3] = invrho * pj[kV3];
-          r[kS11] = fma(mu2, pj[kS11], ltr);
-          r[kS22] = fma(mu2, pj[kS22], ltr);
-          r[kS33] = fma(mu2, pj[kS33], ltr);
-          r[kS12] = mu * pj[kS12];
-          r[kS13] = mu * pj[kS13];
-          r[kS23] = mu * pj[kS23];
-#pragma unroll
-          for (int s = 0; s < M; ++s) {
-            if constexpr (LEAN) {
-              const double v = gavg[n * M + s] + r[s];
-              if (k + 1 < N) {
-                gavg[n * M + s] = v;
-                sp[s * S + pn] = r[s];
-              } else {
-                sp[s * S + pn] = v;  // final average, staged for the store
-              }
-            } else {
-              avg[j][s] += r[s];
-              if (k + 1 < N) sp[s * S + pn] = r[s];
-            }
-          }
-        }
+      }
+    } else {
+#pragma unroll 1
+      for (int d = 0; d < 3; ++d) {
+        line_pass(k, d, 0, sacc);
         __syncthreads();
+        pointwise(k, d, std::integral_constant<int, 0>{}, sacc, SUBS == 1 && d == 2);
+        __syncthreads();
+        if constexpr (SUBS > 1) {
+          line_pass(k, d, 1, sacc);
+          __syncthreads();
+          pointwise(k, d, std::integral_constant<int, 1>{}, sacc, d == 2);
+          __syncthreads();
+        }
       }
     }
   }
@@ -313,13 +364,13 @@ curv_eo_kernel(const double* __restrict__ q, const double* __restrict__ params,
   }
 }
 
-template <int N, int NT, int NODES, int A, bool LEAN>
+template <int N, int NT, int NODES, int A, bool LEAN, bool GREG, bool DB>
 cudaError_t launch_curv_n(int64_t E, const double* q, const double* params, const double* metric,
                           double* out_avg, double* out_faces, const double* tables, double dx,
                           cudaStream_t stream) {
-  constexpr size_t smem = CurvShape<N, A>::SMEM;
+  constexpr size_t smem = CurvShape<N, A, DB>::SMEM;
   static_assert(smem <= 232448, "shared memory budget of one CTA exceeded");
-  auto kern = curv_eo_kernel<N, NT, NODES, A, LEAN>;
+  auto kern = curv_eo_kernel<N, NT, NODES, A, LEAN, GREG, DB>;
   cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (err != cudaSuccess) return err;
   if (E > 0x7fffffffLL) return cudaErrorInvalidValue;
@@ -330,21 +381,26 @@ cudaError_t launch_curv_n(int64_t E, const double* q, const double* params, cons
 }  // namespace
 
 // Launch shapes per N: threads, nodes per thread, quantities per line pass,
-// lean register state.
-#define STP_CURV_SHAPES(X)                                                                       \
-  X(1, 32, 1, 9, false) X(2, 32, 1, 9, false) X(3, 32, 1, 9, false) X(4, 64, 1, 9, false)       \
-  X(5, 128, 1, 9, false) X(6, 224, 1, 9, false) X(7, 352, 1, 9, false) X(8, 512, 1, 9, false)   \
-  X(9, 384, 2, 9, false) X(10, 512, 2, 9, true) X(11, 448, 3, 9, true) X(12, 448, 4, 5, true)
+// lean register state, metric in registers, double buffer (measured on GB300 among 2-6
+// candidates per N; from N = 7 on, enough threads that the 9 N^2 line tasks of
+// a pass take one or two even rounds).
+#define STP_CURV_SHAPES(X)                                                                     \
+  X(1, 32, 1, 9, false, false, false) X(2, 32, 1, 9, false, false, false)                       \
+  X(3, 32, 1, 9, false, false, false) X(4, 64, 1, 9, false, false, false)                       \
+  X(5, 128, 1, 9, false, false, false) X(6, 224, 1, 9, false, false, false)                     \
+  X(7, 448, 1, 9, false, true, true) X(8, 576, 1, 9, false, false, true)                        \
+  X(9, 384, 2, 9, false, true, true) X(10, 512, 2, 9, true, true, false)                        \
+  X(11, 448, 3, 9, true, false, false) X(12, 448, 4, 5, true, false, false)
 
 cudaError_t launch_curvilinear(int N, int64_t E, const double* q, const double* params,
                                const double* metric, double* out_avg, double* out_faces,
                                const double* tables, double dx, cudaStream_t stream) {
   if (E <= 0) return cudaSuccess;
   switch (N) {
-#define X(n, nt, nodes, a, lean)                                                               \
+#define X(n, nt, nodes, a, lean, greg, db)                                                     \
   case n:                                                                                      \
-    return launch_curv_n<n, nt, nodes, a, lean>(E, q, params, metric, out_avg, out_faces,     \
-                                                tables, dx, stream);
+    return launch_curv_n<n, nt, nodes, a, lean, greg, db>(E, q, params, metric, out_avg,      \
+                                                          out_faces, tables, dx, stream);
     STP_CURV_SHAPES(X)
 #undef X
     default: return cudaErrorInvalidValue;
