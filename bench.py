@@ -281,47 +281,54 @@ def mixed_comparison(stp, torch, args, workload="order9", precisions=PRECISIONS_
 
 def curvilinear_measurement(stp, torch, args, cartesian_ms: float):
     """The order-7 workload on curvilinear elements (the same 32^3 grid pushed
-    through a smooth map; 9 more per-node parameters, the inverse Jacobian):
-    CUDA-event time of one stp_predict_curvilinear launch (mean of
-    args.mixed_steps after 3 warm-ups), the algorithmic FP64 rate and the
-    error of 12 sampled elements against the oracle."""
+    through a smooth map; 9 more per-node parameters, the inverse Jacobian),
+    in FP64 and in float-float: CUDA-event time of one
+    stp_predict_curvilinear launch (mean of args.mixed_steps after 3
+    warm-ups), the algorithmic rate and the error of 12 sampled elements
+    against the oracle."""
     import oracle
     from paper_2003_12787_gb300.inputs import curvilinear_problem
     N, grid, h, _ = WORKLOADS["order7"]
     prob = curvilinear_problem(N, grid=grid, h=h, device="cuda")
     E = prob.E
     stream = torch.cuda.current_stream()
-    with stp.Predictor(N - 1, prob.h, prob.dt) as P:
-        avg, faces = P.empty_outputs(E)
-        for _ in range(3):
-            P.predict(prob.q, prob.params, out=(avg, faces), stream=stream, metric=prob.metric)
-        s0 = torch.cuda.Event(enable_timing=True)
-        s1 = torch.cuda.Event(enable_timing=True)
-        s0.record(stream)
-        for _ in range(args.mixed_steps):
-            P.predict(prob.q, prob.params, out=(avg, faces), stream=stream, metric=prob.metric)
-        s1.record(stream)
-        torch.cuda.synchronize()
-        ms = s0.elapsed_time(s1) / args.mixed_steps
     rng = np.random.default_rng(8)
     idx = np.unique(np.concatenate([[0, E - 1], rng.choice(E, 10, replace=False)]))
     it = torch.as_tensor(idx, device="cuda")
     a_ref, f_ref = oracle.stp_curvilinear(prob.q[it].cpu().numpy(), prob.params[it].cpu().numpy(),
                                           prob.metric[it].cpu().numpy(), prob.dt)
-    a = avg[it].cpu().numpy()
-    f = faces[it].cpu().numpy()
-    err = max([float(np.abs(a - a_ref).max() / np.abs(a_ref).max())] +
-              [float(np.abs(f[:, i] - f_ref[:, i]).max() / np.abs(f_ref[:, i]).max())
-               for i in range(6)])
-    tf = E * flops_per_element_curvilinear(N) / (ms / 1e3) / 1e12
-    return {"workload": "order-7 (N=8) elastic STP on curvilinear elements, 32^3=32768 "
-                        "elements, smooth map of amplitude 0.2, one launch",
-            "elements": E, "ms_per_launch": ms, "elements_per_s": E / (ms / 1e3),
-            "flops_per_element": flops_per_element_curvilinear(N),
-            "tflops_algorithmic": tf, "frac_of_fp64_peak": tf / FP64_PEAK_TFLOPS,
+    out = {"workload": "order-7 (N=8) elastic STP on curvilinear elements, 32^3=32768 "
+                       "elements, smooth map of amplitude 0.2, one launch",
+           "elements": E, "flops_per_element": flops_per_element_curvilinear(N),
+           "error": f"max over avg and 6 face arrays, {len(idx)} sampled elements vs the oracle",
+           "variants": {}}
+    for prec in ("fp64", "ff"):
+        with stp.Predictor(N - 1, prob.h, prob.dt, precision=prec) as P:
+            avg, faces = P.empty_outputs(E)
+            for _ in range(3):
+                P.predict(prob.q, prob.params, out=(avg, faces), stream=stream, metric=prob.metric)
+            s0 = torch.cuda.Event(enable_timing=True)
+            s1 = torch.cuda.Event(enable_timing=True)
+            s0.record(stream)
+            for _ in range(args.mixed_steps):
+                P.predict(prob.q, prob.params, out=(avg, faces), stream=stream, metric=prob.metric)
+            s1.record(stream)
+            torch.cuda.synchronize()
+            ms = s0.elapsed_time(s1) / args.mixed_steps
+        a = avg[it].cpu().numpy()
+        f = faces[it].cpu().numpy()
+        err = max([float(np.abs(a - a_ref).max() / np.abs(a_ref).max())] +
+                  [float(np.abs(f[:, i] - f_ref[:, i]).max() / np.abs(f_ref[:, i]).max())
+                   for i in range(6)])
+        tf = E * flops_per_element_curvilinear(N) / (ms / 1e3) / 1e12
+        out["variants"][prec] = {
+            "ms_per_launch": ms, "elements_per_s": E / (ms / 1e3), "tflops_algorithmic": tf,
+            "frac_of_fp64_peak": tf / FP64_PEAK_TFLOPS,
             "hbm_gbs": E * 8 * (30 * N ** 3 + 54 * N ** 2) / (ms / 1e3) / 1e9,
-            "time_vs_cartesian_fp64": ms / cartesian_ms,
-            "max_rel_err": err, "error_sample": f"{len(idx)} elements vs the oracle"}
+            "time_vs_cartesian_fp64": ms / cartesian_ms, "max_rel_err": err}
+    out["variants"]["ff"]["speedup_vs_fp64"] = (out["variants"]["fp64"]["ms_per_launch"] /
+                                                out["variants"]["ff"]["ms_per_launch"])
+    return out
 
 
 def small_case_latency(stp, torch, args):
@@ -521,8 +528,8 @@ def run_gpu(args):
     curv = args.geometry == "curvilinear"
     if curv:
         from paper_2003_12787_gb300.inputs import curvilinear_problem
-        if args.precision != "fp64":
-            raise SystemExit("curvilinear elements run in FP64 only")
+        if args.precision not in ("fp64", "ff"):
+            raise SystemExit("curvilinear elements run in FP64 or float-float only")
         prob = curvilinear_problem(N, grid=grid, h=h, seed_material=1001 + 16 * rank,
                                    seed_waves=1002 + 16 * rank, device="cuda")
         desc = desc.replace("elastic STP,", "elastic STP on curvilinear elements (smooth map "
@@ -741,7 +748,7 @@ def main():
                     help="skip the curvilinear order-7 measurement")
     ap.add_argument("--geometry", choices=["cartesian", "curvilinear"], default="cartesian",
                     help="time the main workload on Cartesian cubes (default) or on "
-                         "curvilinear elements (FP64; no host-buffer path, no extras)")
+                         "curvilinear elements (fp64 or ff; no host-buffer path, no extras)")
     ap.add_argument("--small-launches", type=int, default=50,
                     help="timed launches of the order-3 latency measurement (0: skip)")
     ap.add_argument("--served-rate", type=float, default=2000.0)

@@ -259,8 +259,9 @@ stp_status stp_predict_curvilinear(stp_handle h, int64_t elements, const double*
   const size_t E_ = (size_t)elements, nmetric = sz.q * E_;  // 9 doubles per node, like q
   if (overlap(metric, nmetric, out_avg, sz.avg * E_) || overlap(metric, nmetric, out_faces, sz.faces * E_))
     return fail(STP_ERR_INVALID_ARG, "an output overlaps the metric");
-  if (h->precision != STP_PRECISION_FP64)
-    return fail(STP_ERR_UNSUPPORTED, "curvilinear elements run in FP64 only");
+  const bool ff = h->precision == STP_PRECISION_FF && h->N >= 2;
+  if (h->precision != STP_PRECISION_FP64 && !ff)
+    return fail(STP_ERR_UNSUPPORTED, "curvilinear elements run in FP64 or float-float only");
   cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
   if (cudaStreamIsCapturing(static_cast<cudaStream_t>(stream), &cap) != cudaSuccess) {
     cudaGetLastError();
@@ -272,8 +273,11 @@ stp_status stp_predict_curvilinear(stp_handle h, int64_t elements, const double*
     for (int i = 0; i < 5; ++i)
       if ((s = check_device_ptr(ptrs[i], h->device, names[i])) != STP_OK) return s;
   }
-  cudaError_t e = stp::launch_curvilinear(h->N, elements, q, params, metric, out_avg, out_faces,
-                                          h->d_tables, h->dx, static_cast<cudaStream_t>(stream));
+  cudaError_t e =
+      ff ? stp::launch_ff_curvilinear(h->N, elements, q, params, metric, out_avg, out_faces,
+                                      h->d_tables, h->dx, static_cast<cudaStream_t>(stream))
+         : stp::launch_curvilinear(h->N, elements, q, params, metric, out_avg, out_faces,
+                                   h->d_tables, h->dx, static_cast<cudaStream_t>(stream));
   if (e != cudaSuccess) return cuda_fail(e, "curvilinear STP kernel launch");
   return STP_OK;
 }

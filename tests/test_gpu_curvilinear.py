@@ -3,8 +3,8 @@
 The paper's benchmark meshes are curvilinear (Sec. VI: 9 geometry parameters
 per node beside the 3 material parameters). stp_predict_curvilinear takes the
 per-node inverse Jacobian dxi_d/dx_j; the oracle applies the chain rule with
-dense 9x9 matrices (oracle_stp_curvilinear). FP64 bar: normwise 1e-12 per
-output array.
+dense 9x9 matrices (oracle_stp_curvilinear). FP64 and float-float bar:
+normwise 1e-12 per output array.
 """
 from __future__ import annotations
 
@@ -35,8 +35,8 @@ def _built():
     _binding.load()
 
 
-def run(prob, nodes="gl", metric=None):
-    with stp.Predictor(prob.N - 1, prob.h, prob.dt, nodes=nodes) as P:
+def run(prob, nodes="gl", metric=None, precision="fp64"):
+    with stp.Predictor(prob.N - 1, prob.h, prob.dt, nodes=nodes, precision=precision) as P:
         avg, faces = P.predict(prob.q.cuda(), prob.params.cuda(),
                                metric=(prob.metric if metric is None else metric).cuda())
         torch.cuda.synchronize()
@@ -61,6 +61,26 @@ def test_curvilinear_parity_every_order(N):
                                seed_waves=1600 + N)
     avg, faces = run(prob)
     check(prob, avg, faces)
+
+
+@pytest.mark.parametrize("N", list(range(2, 13)))
+def test_curvilinear_float_float_every_order(N):
+    """Float-float (STP_PRECISION_FF) on curvilinear elements: the FP64 bar."""
+    prob = curvilinear_problem(N, grid=(8, 8, 4), E=5 if N >= 9 else 37, seed_material=2100 + N,
+                               seed_waves=2200 + N)
+    avg, faces = run(prob, precision="ff")
+    check(prob, avg, faces)
+
+
+@pytest.mark.parametrize("N", [4, 9])
+def test_curvilinear_float_float_gauss_lobatto_and_scaled_state(N):
+    """Gauss-Lobatto nodes, and a state scaled by 2^600 (the per-element
+    power-of-two scaling keeps it inside the float range)."""
+    prob = curvilinear_problem(N, grid=(8, 8, 4), E=6, seed_material=2300 + N,
+                               seed_waves=2400 + N, nodes="gll")
+    prob.q = prob.q * 2.0 ** 600
+    avg, faces = run(prob, nodes="gll", precision="ff")
+    check(prob, avg, faces, nodes="gll")
 
 
 @pytest.mark.parametrize("N", [2, 5, 8, 12])
@@ -145,7 +165,8 @@ def test_argument_errors():
             P.predict(prob.q, prob.params, metric=m[:, :, :, :, :2])
         P.predict(prob.q, prob.params, metric=m)  # valid after the errors
         torch.cuda.synchronize()
-    with stp.Predictor(N - 1, prob.h, prob.dt, precision="ff") as P:
-        with pytest.raises(stp.STPError) as ei:
-            P.predict(prob.q, prob.params, metric=m)
-        assert ei.value.status == _binding.STP_ERR_UNSUPPORTED
+    for prec in ("fp32", "bf16x3"):
+        with stp.Predictor(N - 1, prob.h, prob.dt, precision=prec) as P:
+            with pytest.raises(stp.STPError) as ei:
+                P.predict(prob.q, prob.params, metric=m)
+            assert ei.value.status == _binding.STP_ERR_UNSUPPORTED
