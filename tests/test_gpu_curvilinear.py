@@ -107,11 +107,12 @@ def test_cube_metric_matches_cartesian_path(N):
     assert rel(a_c, a.cpu().numpy()) <= 1e-13 and rel(f_c, f.cpu().numpy()) <= 1e-13
 
 
-def test_full_order7_workload_sampled():
+@pytest.mark.parametrize("precision", ["fp64", "ff"])
+def test_full_order7_workload_sampled(precision):
     """The benchmark's curvilinear order-7 workload (32^3 elements), in the
     launch the benchmark times; 48 sampled elements against the oracle."""
     prob = curvilinear_problem(8, grid=(32, 32, 32), device="cuda")
-    with stp.Predictor(7, prob.h, prob.dt) as P:
+    with stp.Predictor(7, prob.h, prob.dt, precision=precision) as P:
         avg, faces = P.predict(prob.q, prob.params, metric=prob.metric)
         torch.cuda.synchronize()
     rng = np.random.default_rng(11)
