@@ -282,7 +282,7 @@ def mixed_comparison(stp, torch, args, workload="order9", precisions=PRECISIONS_
 def curvilinear_measurement(stp, torch, args, cartesian_ms: float):
     """The order-7 workload on curvilinear elements (the same 32^3 grid pushed
     through a smooth map; 9 more per-node parameters, the inverse Jacobian),
-    in FP64 and in float-float: CUDA-event time of one
+    in FP64, float-float and FP32: CUDA-event time of one
     stp_predict_curvilinear launch (mean of args.mixed_steps after 3
     warm-ups), the algorithmic rate and the error of 12 sampled elements
     against the oracle."""
@@ -302,7 +302,7 @@ def curvilinear_measurement(stp, torch, args, cartesian_ms: float):
            "elements": E, "flops_per_element": flops_per_element_curvilinear(N),
            "error": f"max over avg and 6 face arrays, {len(idx)} sampled elements vs the oracle",
            "variants": {}}
-    for prec in ("fp64", "ff"):
+    for prec in ("fp64", "ff", "fp32"):
         with stp.Predictor(N - 1, prob.h, prob.dt, precision=prec) as P:
             avg, faces = P.empty_outputs(E)
             for _ in range(3):
@@ -326,8 +326,9 @@ def curvilinear_measurement(stp, torch, args, cartesian_ms: float):
             "frac_of_fp64_peak": tf / FP64_PEAK_TFLOPS,
             "hbm_gbs": E * 8 * (30 * N ** 3 + 54 * N ** 2) / (ms / 1e3) / 1e9,
             "time_vs_cartesian_fp64": ms / cartesian_ms, "max_rel_err": err}
-    out["variants"]["ff"]["speedup_vs_fp64"] = (out["variants"]["fp64"]["ms_per_launch"] /
-                                                out["variants"]["ff"]["ms_per_launch"])
+    for prec in ("ff", "fp32"):
+        out["variants"][prec]["speedup_vs_fp64"] = (out["variants"]["fp64"]["ms_per_launch"] /
+                                                    out["variants"][prec]["ms_per_launch"])
     return out
 
 
@@ -528,8 +529,8 @@ def run_gpu(args):
     curv = args.geometry == "curvilinear"
     if curv:
         from paper_2003_12787_gb300.inputs import curvilinear_problem
-        if args.precision not in ("fp64", "ff"):
-            raise SystemExit("curvilinear elements run in FP64 or float-float only")
+        if args.precision not in ("fp64", "ff", "fp32"):
+            raise SystemExit("curvilinear elements run in FP64, float-float or FP32 only")
         prob = curvilinear_problem(N, grid=grid, h=h, seed_material=1001 + 16 * rank,
                                    seed_waves=1002 + 16 * rank, device="cuda")
         desc = desc.replace("elastic STP,", "elastic STP on curvilinear elements (smooth map "
@@ -754,7 +755,7 @@ def main():
                     help="skip the curvilinear order-7 measurement")
     ap.add_argument("--geometry", choices=["cartesian", "curvilinear"], default="cartesian",
                     help="time the main workload on Cartesian cubes (default) or on "
-                         "curvilinear elements (fp64 or ff; no host-buffer path, no extras)")
+                         "curvilinear elements (fp64, ff or fp32; no host-buffer path, no extras)")
     ap.add_argument("--small-launches", type=int, default=50,
                     help="timed launches of the order-3 latency measurement (0: skip)")
     ap.add_argument("--served-rate", type=float, default=2000.0)

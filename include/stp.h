@@ -138,9 +138,10 @@ stp_status stp_predict_sources(stp_handle h, int64_t elements, const double* q,
  * metric carries the geometry). Faces are the reference faces xi_d = 0, 1 in
  * stp_predict's order; other buffers and their layouts as stp_predict.
  * Asynchronous on `stream`, capturable like stp_predict.
- * The handle's precision selects FP64 (STP_PRECISION_FP64) or float-float
- * (STP_PRECISION_FF, the FP64 error bar on the FP32 pipes; order 0 runs in
- * FP64); STP_ERR_UNSUPPORTED for any other precision;
+ * The handle's precision selects FP64 (STP_PRECISION_FP64), float-float
+ * (STP_PRECISION_FF, the FP64 error bar on the FP32 pipes) or FP32 with a
+ * float-float first step (STP_PRECISION_FP32, about 1e-9 on resolved fields);
+ * order 0 runs in FP64; STP_ERR_UNSUPPORTED for the tensor-core precisions;
  * STP_ERR_INVALID_ARG for a NULL or unaligned metric, or one that overlaps an
  * output. The library does not check that the metric is invertible.
  */

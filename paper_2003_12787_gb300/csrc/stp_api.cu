@@ -260,8 +260,9 @@ stp_status stp_predict_curvilinear(stp_handle h, int64_t elements, const double*
   if (overlap(metric, nmetric, out_avg, sz.avg * E_) || overlap(metric, nmetric, out_faces, sz.faces * E_))
     return fail(STP_ERR_INVALID_ARG, "an output overlaps the metric");
   const bool ff = h->precision == STP_PRECISION_FF && h->N >= 2;
-  if (h->precision != STP_PRECISION_FP64 && !ff)
-    return fail(STP_ERR_UNSUPPORTED, "curvilinear elements run in FP64 or float-float only");
+  const bool f32 = h->precision == STP_PRECISION_FP32 && h->N >= 2;
+  if (h->precision != STP_PRECISION_FP64 && !ff && !f32)
+    return fail(STP_ERR_UNSUPPORTED, "curvilinear elements run in FP64, float-float or FP32 only");
   cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
   if (cudaStreamIsCapturing(static_cast<cudaStream_t>(stream), &cap) != cudaSuccess) {
     cudaGetLastError();
@@ -273,11 +274,14 @@ stp_status stp_predict_curvilinear(stp_handle h, int64_t elements, const double*
     for (int i = 0; i < 5; ++i)
       if ((s = check_device_ptr(ptrs[i], h->device, names[i])) != STP_OK) return s;
   }
+  const cudaStream_t st = static_cast<cudaStream_t>(stream);
   cudaError_t e =
       ff ? stp::launch_ff_curvilinear(h->N, elements, q, params, metric, out_avg, out_faces,
-                                      h->d_tables, h->dx, static_cast<cudaStream_t>(stream))
-         : stp::launch_curvilinear(h->N, elements, q, params, metric, out_avg, out_faces,
-                                   h->d_tables, h->dx, static_cast<cudaStream_t>(stream));
+                                      h->d_tables, h->dx, st)
+      : f32 ? stp::launch_fp32_curvilinear(h->N, elements, q, params, metric, out_avg, out_faces,
+                                           h->d_tables, h->dx, st)
+            : stp::launch_curvilinear(h->N, elements, q, params, metric, out_avg, out_faces,
+                                      h->d_tables, h->dx, st);
   if (e != cudaSuccess) return cuda_fail(e, "curvilinear STP kernel launch");
   return STP_OK;
 }

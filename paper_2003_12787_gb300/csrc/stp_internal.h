@@ -70,10 +70,14 @@ cudaError_t launch_ff(int N, int64_t E, const double* q, const double* params, d
 cudaError_t launch_curvilinear(int N, int64_t E, const double* q, const double* params,
                                const double* metric, double* out_avg, double* out_faces,
                                const double* tables, double dx, cudaStream_t stream);
-// The same in float-float (ff_curvilinear.cu), 2 <= N <= 12.
+// The same in float-float, and with steps 1..N-1 in FP32 (ff_curvilinear.cu),
+// 2 <= N <= 12.
 cudaError_t launch_ff_curvilinear(int N, int64_t E, const double* q, const double* params,
                                   const double* metric, double* out_avg, double* out_faces,
                                   const double* tables, double dx, cudaStream_t stream);
+cudaError_t launch_fp32_curvilinear(int N, int64_t E, const double* q, const double* params,
+                                    const double* metric, double* out_avg, double* out_faces,
+                                    const double* tables, double dx, cudaStream_t stream);
 
 // Point sources (sources.cu): after the STP of a set, adds the response of
 // the point sources to the outputs of the elements holding them (FP64, one

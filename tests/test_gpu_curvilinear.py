@@ -72,6 +72,19 @@ def test_curvilinear_float_float_every_order(N):
     check(prob, avg, faces)
 
 
+@pytest.mark.parametrize("N", list(range(2, 13)))
+def test_curvilinear_fp32_every_order(N):
+    """FP32 with a float-float first step on resolved fields (h = 1/32): the
+    1e-9-class bar of the Cartesian FP32 variant (2e-9 in the test)."""
+    prob = curvilinear_problem(N, grid=(32, 32, 16), h=1.0 / 32, E=5 if N >= 9 else 37,
+                               seed_material=2500 + N, seed_waves=2600 + N)
+    avg, faces = run(prob, precision="fp32")
+    a_ref, f_ref = oracle.stp_curvilinear(prob.q.numpy(), prob.params.numpy(),
+                                          prob.metric.numpy(), prob.dt)
+    errs = [rel(avg, a_ref)] + [rel(faces[:, f], f_ref[:, f]) for f in range(6)]
+    assert max(errs) <= 2e-9, errs
+
+
 @pytest.mark.parametrize("N", [4, 9])
 def test_curvilinear_float_float_gauss_lobatto_and_scaled_state(N):
     """Gauss-Lobatto nodes, and a state scaled by 2^600 (the per-element
@@ -166,7 +179,7 @@ def test_argument_errors():
             P.predict(prob.q, prob.params, metric=m[:, :, :, :, :2])
         P.predict(prob.q, prob.params, metric=m)  # valid after the errors
         torch.cuda.synchronize()
-    for prec in ("fp32", "bf16x3"):
+    for prec in ("fp16x2", "bf16x3"):
         with stp.Predictor(N - 1, prob.h, prob.dt, precision=prec) as P:
             with pytest.raises(stp.STPError) as ei:
                 P.predict(prob.q, prob.params, metric=m)
