@@ -11,6 +11,9 @@ oracle_order1_seed11.txt / oracle_order2_seed12.txt: the oracle's outputs for
 two small seeded cases, orders 1 and 2 (N = 2, 3; regression fixtures). Written by calling only the
 oracle; any later change to its arithmetic that moves these values must cite,
 in its commit message, the passage that justifies it.
+
+oracle_curvilinear_order2_seed13.txt: the same for the oracle's curvilinear
+STP (N = 3, per-node inverse Jacobians (I + 0.3 U)/h with U ~ U[-1,1]^(3x3)).
 """
 from __future__ import annotations
 
@@ -61,10 +64,31 @@ def oracle_case(N, seed):
     return "\n".join(lines) + "\n"
 
 
+def oracle_curv_case(N, seed):
+    import oracle
+    rng = np.random.default_rng(seed)
+    E = 2
+    params = np.stack([rng.uniform(2, 3, (E, N, N, N)), rng.uniform(4, 6, (E, N, N, N)),
+                       rng.uniform(1, 2, (E, N, N, N))], axis=-1)
+    q = rng.uniform(-1, 1, (E, N, N, N, 9))
+    h, dt = 0.25, 0.005
+    metric = (np.eye(3) + 0.3 * rng.uniform(-1, 1, (E, N, N, N, 3, 3))) / h
+    avg, faces = oracle.stp_curvilinear(q, params, metric, dt)
+    lines = [f"# oracle.stp_curvilinear on numpy default_rng({seed}): E={E}, N={N}; params = stack "
+             "of U[2,3] (rho), U[4,6] (cp), U[1,2] (cs) per node, then q = U[-1,1], then the "
+             "metric (I + 0.3 U[-1,1]^(3x3)) / h per node; h=0.25, dt=0.005.",
+             "# Regression fixture written by tests/golden/make_golden.py (oracle only).",
+             "# avg, then faces, flattened in C order, one value per line (17 significant digits)."]
+    lines += [f"{v:.17g}" for v in avg.ravel()] + [f"{v:.17g}" for v in faces.ravel()]
+    return "\n".join(lines) + "\n"
+
+
 if __name__ == "__main__":
     with open(os.path.join(HERE, "gl_nodes_closed_form.txt"), "w") as f:
         f.write(closed_form_nodes())
     for N, seed in ((2, 11), (3, 12)):
         with open(os.path.join(HERE, f"oracle_order{N - 1}_seed{seed}.txt"), "w") as f:
             f.write(oracle_case(N, seed))
+    with open(os.path.join(HERE, "oracle_curvilinear_order2_seed13.txt"), "w") as f:
+        f.write(oracle_curv_case(3, 13))
     print("written")

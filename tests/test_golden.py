@@ -3,8 +3,9 @@
 gl_nodes_closed_form.txt holds Gauss-Legendre nodes from their closed forms
 (written by tests/golden/make_golden.py with mpmath, without any node routine
 of a library or of the oracle). The oracle_order*_seed*.txt files are
-regression fixtures of the oracle's own outputs on two small seeded cases:
-they catch any later, unintended change of its arithmetic.
+regression fixtures of the oracle's own outputs on small seeded cases (two
+Cartesian, one curvilinear): they catch any later, unintended change of its
+arithmetic.
 """
 from __future__ import annotations
 
@@ -46,6 +47,15 @@ def test_oracle_matches_its_regression_fixture(N, seed):
     rows = read_values(f"oracle_order{N - 1}_seed{seed}.txt")
     stored = np.array([float(r[0]) for r in rows])
     text = generator().oracle_case(N, seed)
+    now = np.array([float(line) for line in text.splitlines() if line and not line.startswith("#")])
+    assert stored.shape == now.shape
+    assert np.abs(now - stored).max() <= 1e-15 * np.abs(stored).max()
+
+
+def test_curvilinear_oracle_matches_its_regression_fixture():
+    rows = read_values("oracle_curvilinear_order2_seed13.txt")
+    stored = np.array([float(r[0]) for r in rows])
+    text = generator().oracle_curv_case(3, 13)
     now = np.array([float(line) for line in text.splitlines() if line and not line.startswith("#")])
     assert stored.shape == now.shape
     assert np.abs(now - stored).max() <= 1e-15 * np.abs(stored).max()
