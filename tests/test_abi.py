@@ -145,6 +145,22 @@ def test_predict_rejects_null_handle(lib):
     stp.stp_destroy(None)  # NULL is a no-op
 
 
+def test_predict_curvilinear_rejects_null_handle(lib):
+    with pytest.raises(stp.STPError) as ei:
+        stp.stp_predict_curvilinear(None, 1, 16, 16, 16, 16, 16)
+    assert ei.value.status == _binding.STP_ERR_INVALID_ARG
+    # a negative element count is rejected before the handle is used
+    assert lib.stp_predict_curvilinear(None, -1, None, None, None, None, None, None) == \
+        _binding.STP_ERR_INVALID_ARG
+
+
+def test_predict_sources_rejects_bad_source_list(lib):
+    assert lib.stp_predict_sources(None, 1, None, None, None, None, -1, None, None) == \
+        _binding.STP_ERR_INVALID_ARG
+    assert lib.stp_predict_sources(None, 1, None, None, None, None, 1, None, None) == \
+        _binding.STP_ERR_INVALID_ARG
+
+
 def test_binding_fails_loudly_without_library(monkeypatch, tmp_path):
     monkeypatch.setattr(build, "LIB", str(tmp_path / "missing.so"))
     monkeypatch.setattr(_binding, "_lib", None)
