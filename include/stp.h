@@ -150,6 +150,15 @@ stp_status stp_predict_curvilinear(stp_handle h, int64_t elements, const double*
                                    double* out_avg, double* out_faces, void* stream);
 
 /*
+ * stp_predict_curvilinear on HOST buffers (q, params, metric in; out_avg,
+ * out_faces out), with the chunked copy/kernel pipeline and the synchronous
+ * completion of stp_predict_host. Errors as stp_predict_curvilinear.
+ */
+stp_status stp_predict_curvilinear_host(stp_handle h, int64_t elements, const double* q,
+                                        const double* params, const double* metric,
+                                        double* out_avg, double* out_faces, void* stream);
+
+/*
  * Same computation on HOST buffers (pinned host memory gives full copy
  * bandwidth; pageable memory works but copies slower). Synchronous: returns
  * once out_avg and out_faces hold the results. Elements are processed in

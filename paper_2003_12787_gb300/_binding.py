@@ -59,6 +59,7 @@ def load():
         lib.stp_get_nodes.restype = ctypes.c_int
         lib.stp_predict_sources.argtypes = [vp, i64, vp, vp, vp, vp, ctypes.c_int, vp, vp]
         lib.stp_predict_curvilinear.argtypes = [vp, i64, vp, vp, vp, vp, vp, vp]
+        lib.stp_predict_curvilinear_host.argtypes = [vp, i64, vp, vp, vp, vp, vp, vp]
         lib.stp_nodes.argtypes = [vp]
         lib.stp_nodes.restype = ctypes.c_int
         lib.stp_status_string.argtypes = [ctypes.c_int]
@@ -233,6 +234,14 @@ def stp_predict_curvilinear(h: int, elements: int, q, params, metric, out_avg, o
     _check(load().stp_predict_curvilinear(h, elements, _ptr(q), _ptr(params), _ptr(metric),
                                           _ptr(out_avg), _ptr(out_faces), _stream(stream)),
            "stp_predict_curvilinear")
+
+
+def stp_predict_curvilinear_host(h: int, elements: int, q, params, metric, out_avg, out_faces,
+                                 stream=None) -> None:
+    """Host tensors in and out (synchronous), as stp_predict_host."""
+    _check(load().stp_predict_curvilinear_host(h, elements, _ptr(q), _ptr(params), _ptr(metric),
+                                               _ptr(out_avg), _ptr(out_faces), _stream(stream)),
+           "stp_predict_curvilinear_host")
 
 
 class BatchSet(ctypes.Structure):

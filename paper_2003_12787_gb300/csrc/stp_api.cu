@@ -23,7 +23,7 @@ struct stp_handle_s {
   cudaStream_t streams[kStages] = {nullptr, nullptr, nullptr};
   cudaEvent_t done[kStages] = {nullptr, nullptr, nullptr};
   double* stage_buf[kStages] = {nullptr, nullptr, nullptr};
-  int64_t stage_elems = 0;
+  size_t stage_bytes = 0;  // bytes of each stage buffer
 };
 
 namespace {
@@ -106,6 +106,37 @@ cudaError_t launch_configured(stp_handle h, int64_t E, const double* q, const do
   return stp::launch_mixed(h->N, (int)h->precision, E, q, params, avg, faces, h->d_tables,
                            h->d_tables + stp::table_offset_D(h->N), h->dt / h->dx, h->eD,
                            h->d_status, stream);
+}
+
+// Checks of stp_predict_curvilinear's arguments beyond validate_common's;
+// STP_OK for elements == 0.
+stp_status validate_curvilinear(stp_handle h, int64_t E, const double* q, const double* params,
+                                const double* metric, const double* avg, const double* faces) {
+  stp_status s = validate_common(h, E, q, params, avg, faces);
+  if (s != STP_OK || E == 0) return s;
+  if (!metric) return fail(STP_ERR_INVALID_ARG, "null metric");
+  if (!aligned16(metric)) return fail(STP_ERR_INVALID_ARG, "metric must be 16-byte aligned");
+  const Sizes sz = sizes_per_element(h->N);
+  const size_t E_ = (size_t)E, nmetric = sz.q * E_;  // 9 doubles per node, like q
+  if (overlap(metric, nmetric, avg, sz.avg * E_) || overlap(metric, nmetric, faces, sz.faces * E_))
+    return fail(STP_ERR_INVALID_ARG, "an output overlaps the metric");
+  const bool other = h->N >= 2 && (h->precision == STP_PRECISION_FF ||
+                                   h->precision == STP_PRECISION_FP32);
+  if (h->precision != STP_PRECISION_FP64 && !other)
+    return fail(STP_ERR_UNSUPPORTED, "curvilinear elements run in FP64, float-float or FP32 only");
+  return STP_OK;
+}
+
+// One launch of the handle's curvilinear kernel (precision checked above).
+cudaError_t launch_curvilinear_configured(stp_handle h, int64_t E, const double* q,
+                                          const double* params, const double* metric, double* avg,
+                                          double* faces, cudaStream_t st) {
+  if (h->N >= 2 && h->precision == STP_PRECISION_FF)
+    return stp::launch_ff_curvilinear(h->N, E, q, params, metric, avg, faces, h->d_tables, h->dx, st);
+  if (h->N >= 2 && h->precision == STP_PRECISION_FP32)
+    return stp::launch_fp32_curvilinear(h->N, E, q, params, metric, avg, faces, h->d_tables, h->dx,
+                                        st);
+  return stp::launch_curvilinear(h->N, E, q, params, metric, avg, faces, h->d_tables, h->dx, st);
 }
 
 }  // namespace
@@ -251,18 +282,8 @@ stp_status stp_predict(stp_handle h, int64_t elements, const double* q, const do
 stp_status stp_predict_curvilinear(stp_handle h, int64_t elements, const double* q,
                                    const double* params, const double* metric, double* out_avg,
                                    double* out_faces, void* stream) {
-  stp_status s = validate_common(h, elements, q, params, out_avg, out_faces);
+  stp_status s = validate_curvilinear(h, elements, q, params, metric, out_avg, out_faces);
   if (s != STP_OK || elements == 0) return s;
-  if (!metric) return fail(STP_ERR_INVALID_ARG, "null metric");
-  if (!aligned16(metric)) return fail(STP_ERR_INVALID_ARG, "metric must be 16-byte aligned");
-  const Sizes sz = sizes_per_element(h->N);
-  const size_t E_ = (size_t)elements, nmetric = sz.q * E_;  // 9 doubles per node, like q
-  if (overlap(metric, nmetric, out_avg, sz.avg * E_) || overlap(metric, nmetric, out_faces, sz.faces * E_))
-    return fail(STP_ERR_INVALID_ARG, "an output overlaps the metric");
-  const bool ff = h->precision == STP_PRECISION_FF && h->N >= 2;
-  const bool f32 = h->precision == STP_PRECISION_FP32 && h->N >= 2;
-  if (h->precision != STP_PRECISION_FP64 && !ff && !f32)
-    return fail(STP_ERR_UNSUPPORTED, "curvilinear elements run in FP64, float-float or FP32 only");
   cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
   if (cudaStreamIsCapturing(static_cast<cudaStream_t>(stream), &cap) != cudaSuccess) {
     cudaGetLastError();
@@ -274,14 +295,8 @@ stp_status stp_predict_curvilinear(stp_handle h, int64_t elements, const double*
     for (int i = 0; i < 5; ++i)
       if ((s = check_device_ptr(ptrs[i], h->device, names[i])) != STP_OK) return s;
   }
-  const cudaStream_t st = static_cast<cudaStream_t>(stream);
-  cudaError_t e =
-      ff ? stp::launch_ff_curvilinear(h->N, elements, q, params, metric, out_avg, out_faces,
-                                      h->d_tables, h->dx, st)
-      : f32 ? stp::launch_fp32_curvilinear(h->N, elements, q, params, metric, out_avg, out_faces,
-                                           h->d_tables, h->dx, st)
-            : stp::launch_curvilinear(h->N, elements, q, params, metric, out_avg, out_faces,
-                                      h->d_tables, h->dx, st);
+  cudaError_t e = launch_curvilinear_configured(h, elements, q, params, metric, out_avg, out_faces,
+                                                static_cast<cudaStream_t>(stream));
   if (e != cudaSuccess) return cuda_fail(e, "curvilinear STP kernel launch");
   return STP_OK;
 }
@@ -395,12 +410,18 @@ stp_status stp_predict_sources(stp_handle h, int64_t elements, const double* q, 
   return STP_OK;
 }
 
-stp_status stp_predict_host(stp_handle h, int64_t elements, const double* q, const double* params,
-                            double* out_avg, double* out_faces, void* stream) {
-  stp_status s = validate_common(h, elements, q, params, out_avg, out_faces);
-  if (s != STP_OK || elements == 0) return s;
+namespace {
+
+// Host-buffer pipeline: chunks of elements cycle through kStages library-owned
+// streams, each doing H2D of the chunk's inputs, the kernel, D2H of its
+// outputs, so copies of one chunk overlap the kernel of another. metric
+// (host, may be NULL) selects the curvilinear kernels.
+stp_status predict_host_impl(stp_handle h, int64_t elements, const double* q, const double* params,
+                             const double* metric, double* out_avg, double* out_faces,
+                             void* stream) {
   const Sizes sz = sizes_per_element(h->N);
-  const size_t per_elem = sz.q + sz.params + sz.avg + sz.faces;
+  const size_t szm = metric ? sz.q : 0;  // 9 doubles per node, like q
+  const size_t per_elem = sz.q + sz.params + szm + sz.avg + sz.faces;
   int prev = -1;
   cudaGetDevice(&prev);
   if (prev != h->device) cudaSetDevice(h->device);
@@ -414,12 +435,12 @@ stp_status stp_predict_host(stp_handle h, int64_t elements, const double* q, con
   int64_t chunk = (int64_t)((64u << 20) / per_elem);
   chunk = chunk < epc ? epc : (chunk / epc) * epc;
   if (chunk > elements) chunk = elements;
-  if (h->stage_elems < chunk) {
+  if (h->stage_bytes < per_elem * (size_t)chunk) {
     for (int i = 0; i < stp_handle_s::kStages; ++i) {
       if (h->streams[i]) cudaStreamSynchronize(h->streams[i]);
       if (h->stage_buf[i]) { cudaFree(h->stage_buf[i]); h->stage_buf[i] = nullptr; }
     }
-    h->stage_elems = 0;
+    h->stage_bytes = 0;
     for (int i = 0; i < stp_handle_s::kStages; ++i) {
       if (!h->streams[i]) {
         if ((e = cudaStreamCreateWithFlags(&h->streams[i], cudaStreamNonBlocking)) != cudaSuccess)
@@ -432,7 +453,7 @@ stp_status stp_predict_host(stp_handle h, int64_t elements, const double* q, con
         return fail(STP_ERR_OOM, "cudaMalloc of staging buffers failed");
       }
     }
-    h->stage_elems = chunk;
+    h->stage_bytes = per_elem * (size_t)chunk;
   }
   // order after the caller's stream
   cudaEvent_t start;
@@ -444,6 +465,7 @@ stp_status stp_predict_host(stp_handle h, int64_t elements, const double* q, con
 
   const char* hq = reinterpret_cast<const char*>(q);
   const char* hp = reinterpret_cast<const char*>(params);
+  const char* hm = reinterpret_cast<const char*>(metric);
   char* ha = reinterpret_cast<char*>(out_avg);
   char* hf = reinterpret_cast<char*>(out_faces);
   int stage = 0;
@@ -453,13 +475,16 @@ stp_status stp_predict_host(stp_handle h, int64_t elements, const double* q, con
     char* b = reinterpret_cast<char*>(h->stage_buf[stage]);
     double* dq = reinterpret_cast<double*>(b);
     double* dp = reinterpret_cast<double*>(b + sz.q * chunk);
-    double* da = reinterpret_cast<double*>(b + (sz.q + sz.params) * chunk);
-    double* df = reinterpret_cast<double*>(b + (sz.q + sz.params + sz.avg) * chunk);
+    double* dm = reinterpret_cast<double*>(b + (sz.q + sz.params) * chunk);
+    double* da = reinterpret_cast<double*>(b + (sz.q + sz.params + szm) * chunk);
+    double* df = reinterpret_cast<double*>(b + (sz.q + sz.params + szm + sz.avg) * chunk);
     // one stream per stage: its previous chunk's copies and kernel finish first
     if ((e = cudaMemcpyAsync(dq, hq + base * sz.q, n * sz.q, cudaMemcpyHostToDevice, st)) != cudaSuccess ||
-        (e = cudaMemcpyAsync(dp, hp + base * sz.params, n * sz.params, cudaMemcpyHostToDevice, st)) != cudaSuccess)
+        (e = cudaMemcpyAsync(dp, hp + base * sz.params, n * sz.params, cudaMemcpyHostToDevice, st)) != cudaSuccess ||
+        (metric && (e = cudaMemcpyAsync(dm, hm + base * szm, n * szm, cudaMemcpyHostToDevice, st)) != cudaSuccess))
       return cuda_fail(e, "host-to-device copy");
-    e = launch_configured(h, n, dq, dp, da, df, st);
+    e = metric ? launch_curvilinear_configured(h, n, dq, dp, dm, da, df, st)
+               : launch_configured(h, n, dq, dp, da, df, st);
     if (e != cudaSuccess) return cuda_fail(e, "STP kernel launch");
     if ((e = cudaMemcpyAsync(ha + base * sz.avg, da, n * sz.avg, cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
         (e = cudaMemcpyAsync(hf + base * sz.faces, df, n * sz.faces, cudaMemcpyDeviceToHost, st)) != cudaSuccess)
@@ -471,6 +496,23 @@ stp_status stp_predict_host(stp_handle h, int64_t elements, const double* q, con
   }
   if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "host-path copy");
   return STP_OK;
+}
+
+}  // namespace
+
+stp_status stp_predict_host(stp_handle h, int64_t elements, const double* q, const double* params,
+                            double* out_avg, double* out_faces, void* stream) {
+  stp_status s = validate_common(h, elements, q, params, out_avg, out_faces);
+  if (s != STP_OK || elements == 0) return s;
+  return predict_host_impl(h, elements, q, params, nullptr, out_avg, out_faces, stream);
+}
+
+stp_status stp_predict_curvilinear_host(stp_handle h, int64_t elements, const double* q,
+                                        const double* params, const double* metric,
+                                        double* out_avg, double* out_faces, void* stream) {
+  stp_status s = validate_curvilinear(h, elements, q, params, metric, out_avg, out_faces);
+  if (s != STP_OK || elements == 0) return s;
+  return predict_host_impl(h, elements, q, params, metric, out_avg, out_faces, stream);
 }
 
 stp_status stp_set_precision(stp_handle h, stp_precision p) {

@@ -79,9 +79,7 @@ class Predictor:
             N = self.N
             if sources:
                 raise ValueError("point sources are not supported on curvilinear elements")
-            if metric.dtype != torch.float64 or not metric.is_contiguous() or \
-                    metric.numel() != E * N ** 3 * 9 or metric.shape[:4] != q.shape[:4]:
-                raise ValueError(f"metric must be a contiguous float64 [E][{N}][{N}][{N}][3][3]")
+            self._check_metric(q, metric)
             B.stp_predict_curvilinear(self.handle, E, q, params, metric, avg, faces, stream)
         elif sources:
             B.stp_predict_sources(self.handle, E, q, params, avg, faces, sources, stream)
@@ -89,12 +87,26 @@ class Predictor:
             B.stp_predict(self.handle, E, q, params, avg, faces, stream)
         return avg, faces
 
-    def predict_host(self, q: torch.Tensor, params: torch.Tensor, out=None, stream=None):
-        """Host tensors in and out (pinned gives full copy bandwidth); synchronous."""
+    def _check_metric(self, q: torch.Tensor, metric: torch.Tensor):
+        N, E = self.N, q.shape[0]
+        if metric.dtype != torch.float64 or not metric.is_contiguous() or \
+                metric.numel() != E * N ** 3 * 9 or metric.shape[:4] != q.shape[:4] or \
+                metric.device != q.device:
+            raise ValueError(f"metric must be a contiguous float64 [E][{N}][{N}][{N}][3][3] "
+                             "on the device of q")
+
+    def predict_host(self, q: torch.Tensor, params: torch.Tensor, out=None, stream=None,
+                     metric=None):
+        """Host tensors in and out (pinned gives full copy bandwidth); synchronous.
+        metric: optional host inverse Jacobians of curvilinear elements."""
         self._check_inputs(q, params)
         E = q.shape[0]
         avg, faces = out if out is not None else self.empty_outputs(E, device="cpu")
-        B.stp_predict_host(self.handle, E, q, params, avg, faces, stream)
+        if metric is not None:
+            self._check_metric(q, metric)
+            B.stp_predict_curvilinear_host(self.handle, E, q, params, metric, avg, faces, stream)
+        else:
+            B.stp_predict_host(self.handle, E, q, params, avg, faces, stream)
         return avg, faces
 
 

@@ -157,6 +157,27 @@ def test_element_independence_and_graph_capture():
     assert torch.equal(out[0], a) and torch.equal(out[1], f)
 
 
+@pytest.mark.parametrize("precision", ["fp64", "ff", "fp32"])
+def test_host_buffer_path_equals_device_path(precision):
+    """stp_predict_curvilinear_host (chunked copies and kernels over three
+    streams; 1000 elements at N = 8 make three chunks) gives the device
+    path's results bit for bit."""
+    N = 8
+    prob = curvilinear_problem(N, grid=(16, 16, 4), E=1000, seed_material=2701, seed_waves=2702)
+    with stp.Predictor(N - 1, prob.h, prob.dt, precision=precision) as P:
+        a_d, f_d = P.predict(prob.q.cuda(), prob.params.cuda(), metric=prob.metric.cuda())
+        torch.cuda.synchronize()
+        a_h, f_h = P.predict_host(prob.q.pin_memory(), prob.params.pin_memory(),
+                                  metric=prob.metric.pin_memory())
+        # the Cartesian host path on the same handle reuses the (larger)
+        # staging buffers of the curvilinear call
+        a_c, _ = P.predict_host(prob.q, prob.params)
+        a_cd, _ = P.predict(prob.q.cuda(), prob.params.cuda())
+        torch.cuda.synchronize()
+    assert torch.equal(a_h, a_d.cpu()) and torch.equal(f_h, f_d.cpu())
+    assert torch.equal(a_c, a_cd.cpu())
+
+
 def test_argument_errors():
     N = 4
     prob = curvilinear_problem(N, E=8, device="cuda")
