@@ -272,6 +272,17 @@ stp_status stp_batch_create(int nsets, const stp_batch_set* sets, stp_batch* out
 stp_status stp_batch_create_ex(int nsets, const stp_batch_set* sets, const int* shapes,
                                stp_batch* out);
 
+/* As stp_batch_create, with curvilinear sets: metrics is a HOST array of
+ * nsets device pointers, metrics[i] the inverse Jacobians of set i in the
+ * layout of stp_predict_curvilinear, or NULL for a Cartesian set. A batch
+ * with any curvilinear set is planned as the CUDA graph of per-set launches;
+ * every set's results equal those of its own stp_predict_curvilinear (or
+ * stp_predict). Metrics must not overlap any output. STP_ERR_INVALID_ARG for
+ * metrics == NULL with nsets > 0, otherwise the errors of stp_batch_create and
+ * stp_predict_curvilinear. */
+stp_status stp_batch_create_curvilinear(int nsets, const stp_batch_set* sets,
+                                        const double* const* metrics, stp_batch* out);
+
 /* Enqueue one replay of the plan's graph on `stream` (async). */
 stp_status stp_batch_launch(stp_batch b, void* stream);
 

@@ -74,6 +74,7 @@ def load():
         lib.stp_batch_create.argtypes = [ctypes.c_int, vp, ctypes.POINTER(vp)]
         lib.stp_batch_launch.argtypes = [vp, vp]
         lib.stp_batch_create_ex.argtypes = [ctypes.c_int, vp, vp, ctypes.POINTER(vp)]
+        lib.stp_batch_create_curvilinear.argtypes = [ctypes.c_int, vp, vp, ctypes.POINTER(vp)]
         lib.stp_batch_info.argtypes = [vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
                                        ctypes.POINTER(i64)]
         lib.stp_batch_destroy.argtypes = [vp]
@@ -251,14 +252,23 @@ class BatchSet(ctypes.Structure):
                 ("out_avg", ctypes.c_void_p), ("out_faces", ctypes.c_void_p)]
 
 
-def stp_batch_create(sets, shapes=None) -> int:
+def stp_batch_create(sets, shapes=None, metrics=None) -> int:
     """sets: sequence of (handle, elements, q, params, out_avg, out_faces);
-    shapes: optional per-set candidate shape index (-1 = autotuned)."""
+    shapes: optional per-set candidate shape index (-1 = autotuned);
+    metrics: optional per-set device metric (None for a Cartesian set)."""
     arr = (BatchSet * max(1, len(sets)))()
     for i, (h, E, q, p, a, f) in enumerate(sets):
         arr[i] = BatchSet(h, E, _ptr(q), _ptr(p), _ptr(a), _ptr(f))
     b = ctypes.c_void_p()
-    if shapes is None:
+    if metrics is not None:
+        if shapes is not None:
+            raise ValueError("shapes apply to Cartesian FP64 batches only")
+        mt = (ctypes.c_void_p * max(1, len(sets)))(*[_ptr(m) for m in metrics])
+        _check(load().stp_batch_create_curvilinear(len(sets), ctypes.cast(arr, ctypes.c_void_p),
+                                                   ctypes.cast(mt, ctypes.c_void_p),
+                                                   ctypes.byref(b)),
+               "stp_batch_create_curvilinear")
+    elif shapes is None:
         _check(load().stp_batch_create(len(sets), ctypes.cast(arr, ctypes.c_void_p), ctypes.byref(b)),
                "stp_batch_create")
     else:

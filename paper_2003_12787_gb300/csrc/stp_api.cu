@@ -563,7 +563,8 @@ namespace {
 // A graph holding one launch per set (the set's own kernel and precision),
 // largest estimated work first, spread round-robin over up to 8 parallel
 // branches so that small sets run beside large ones.
-cudaError_t capture_set_launches(int nsets, const stp_batch_set* sets, cudaGraph_t* graph) {
+cudaError_t capture_set_launches(int nsets, const stp_batch_set* sets, const double* const* metrics,
+                                 cudaGraph_t* graph) {
   constexpr int kBranches = 8;
   const int nb = std::max(1, std::min(kBranches, nsets));
   std::vector<int> order(nsets);
@@ -572,6 +573,7 @@ cudaError_t capture_set_launches(int nsets, const stp_batch_set* sets, cudaGraph
     const double n = sets[i].handle->N;
     order[i] = i;
     work[i] = (double)sets[i].elements * (36.0 * std::pow(n, 5) + 66.0 * std::pow(n, 4) + 108.0 * std::pow(n, 3));
+    if (metrics && metrics[i]) work[i] *= 1.7;  // curvilinear: every quantity along every direction
   }
   std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return work[x] > work[y]; });
   cudaStream_t origin = nullptr;
@@ -588,9 +590,12 @@ cudaError_t capture_set_launches(int nsets, const stp_batch_set* sets, cudaGraph
     for (int b = 0; b < nb && e == cudaSuccess; ++b) e = cudaStreamWaitEvent(br[b], ev[nb], 0);
     for (int k = 0; k < nsets && e == cudaSuccess; ++k) {
       const stp_batch_set& st = sets[order[k]];
+      const double* m = metrics ? metrics[order[k]] : nullptr;
       if (st.elements > 0)
-        e = launch_configured(st.handle, st.elements, st.q, st.params, st.out_avg, st.out_faces,
-                              br[k % nb]);
+        e = m ? launch_curvilinear_configured(st.handle, st.elements, st.q, st.params, m,
+                                              st.out_avg, st.out_faces, br[k % nb])
+              : launch_configured(st.handle, st.elements, st.q, st.params, st.out_avg,
+                                  st.out_faces, br[k % nb]);
     }
     for (int b = 0; b < nb && e == cudaSuccess; ++b) {  // join
       e = cudaEventRecord(ev[b], br[b]);
@@ -614,14 +619,13 @@ cudaError_t capture_set_launches(int nsets, const stp_batch_set* sets, cudaGraph
 
 }  // namespace
 
-extern "C" {
+namespace {
 
-stp_status stp_batch_create(int nsets, const stp_batch_set* sets, stp_batch* out) {
-  return stp_batch_create_ex(nsets, sets, nullptr, out);
-}
-
-stp_status stp_batch_create_ex(int nsets, const stp_batch_set* sets, const int* shapes,
-                               stp_batch* out) {
+// Plans a batch: the persistent FP64 plan when every set is Cartesian FP64,
+// else a CUDA graph of per-set launches (metrics[i], when given and not
+// NULL, makes set i curvilinear).
+stp_status batch_create_impl(int nsets, const stp_batch_set* sets, const int* shapes,
+                             const double* const* metrics, stp_batch* out) {
   if (!out) return fail(STP_ERR_INVALID_ARG, "out is NULL");
   *out = nullptr;
   if (nsets < 0 || (nsets > 0 && !sets)) return fail(STP_ERR_INVALID_ARG, "bad set list");
@@ -631,19 +635,27 @@ stp_status stp_batch_create_ex(int nsets, const stp_batch_set* sets, const int* 
   std::vector<int64_t> E(nsets);
   std::vector<const double*> q(nsets), p(nsets), tb(nsets);
   std::vector<double*> a(nsets), f(nsets);
+  std::vector<const double*> mt(nsets, nullptr);
+  bool any_metric = false;
   for (int i = 0; i < nsets; ++i) {
     const stp_batch_set& st = sets[i];
-    stp_status s = validate_common(st.handle, st.elements, st.q, st.params, st.out_avg, st.out_faces);
+    const double* m = metrics ? metrics[i] : nullptr;
+    stp_status s = m ? validate_curvilinear(st.handle, st.elements, st.q, st.params, m, st.out_avg,
+                                            st.out_faces)
+                     : validate_common(st.handle, st.elements, st.q, st.params, st.out_avg,
+                                       st.out_faces);
     if (s != STP_OK) return fail(s, "set " + std::to_string(i) + ": " + g_last_error);
     if (st.handle->device != dev)
       return fail(STP_ERR_UNSUPPORTED, "set " + std::to_string(i) + ": handle on another device");
     if (st.elements > 0) {
-      const char* names[4] = {"q", "params", "out_avg", "out_faces"};
-      const void* ptrs[4] = {st.q, st.params, st.out_avg, st.out_faces};
-      for (int k = 0; k < 4; ++k)
+      const char* names[5] = {"q", "params", "out_avg", "out_faces", "metric"};
+      const void* ptrs[5] = {st.q, st.params, st.out_avg, st.out_faces, m};
+      for (int k = 0; k < (m ? 5 : 4); ++k)
         if ((s = check_device_ptr(ptrs[k], dev, names[k])) != STP_OK)
           return fail(s, "set " + std::to_string(i) + ": " + g_last_error);
     }
+    mt[i] = m;
+    any_metric = any_metric || (m && st.elements > 0);
     N[i] = st.handle->N;
     E[i] = st.elements;
     q[i] = st.q;
@@ -660,17 +672,17 @@ stp_status stp_batch_create_ex(int nsets, const stp_batch_set* sets, const int* 
     for (int j = 0; j < nsets; ++j) {
       if (j == i) continue;
       const Sizes sj = sizes_per_element(N[j]);
-      const void* bj[4] = {q[j], p[j], a[j], f[j]};
-      const size_t nj[4] = {sj.q * (size_t)E[j], sj.params * (size_t)E[j], sj.avg * (size_t)E[j],
-                            sj.faces * (size_t)E[j]};
+      const void* bj[5] = {q[j], p[j], a[j], f[j], mt[j]};
+      const size_t nj[5] = {sj.q * (size_t)E[j], sj.params * (size_t)E[j], sj.avg * (size_t)E[j],
+                            sj.faces * (size_t)E[j], mt[j] ? sj.q * (size_t)E[j] : 0};
       for (int x = 0; x < 2; ++x)
-        for (int y = 0; y < 4; ++y)
+        for (int y = 0; y < 5; ++y)
           if (ni[x] && nj[y] && overlap(oi[x], ni[x], bj[y], nj[y]))
             return fail(STP_ERR_INVALID_ARG, "outputs of set " + std::to_string(i) +
                                                  " overlap buffers of set " + std::to_string(j));
     }
   }
-  bool all_fp64 = true;
+  bool all_fp64 = !any_metric;  // the persistent kernel holds the Cartesian FP64 bodies
   for (int i = 0; i < nsets; ++i)
     if (sets[i].handle->precision != STP_PRECISION_FP64) all_fp64 = false;
   stp_batch b = new (std::nothrow) stp_batch_s;
@@ -683,7 +695,7 @@ stp_status stp_batch_create_ex(int nsets, const stp_batch_set* sets, const int* 
         delete b;
         return fail(STP_ERR_INVALID_ARG, "shapes apply to all-FP64 batches only");
       }
-    cudaError_t e = capture_set_launches(nsets, sets, &b->graph);
+    cudaError_t e = capture_set_launches(nsets, sets, any_metric ? mt.data() : nullptr, &b->graph);
     if (e == cudaSuccess) e = cudaGraphInstantiate(&b->exec, b->graph, 0);
     if (e != cudaSuccess) {
       cudaGetLastError();
@@ -715,6 +727,25 @@ stp_status stp_batch_create_ex(int nsets, const stp_batch_set* sets, const int* 
   }
   *out = b;
   return STP_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+stp_status stp_batch_create(int nsets, const stp_batch_set* sets, stp_batch* out) {
+  return batch_create_impl(nsets, sets, nullptr, nullptr, out);
+}
+
+stp_status stp_batch_create_ex(int nsets, const stp_batch_set* sets, const int* shapes,
+                               stp_batch* out) {
+  return batch_create_impl(nsets, sets, shapes, nullptr, out);
+}
+
+stp_status stp_batch_create_curvilinear(int nsets, const stp_batch_set* sets,
+                                        const double* const* metrics, stp_batch* out) {
+  if (nsets > 0 && !metrics) return fail(STP_ERR_INVALID_ARG, "metrics is NULL");
+  return batch_create_impl(nsets, sets, nullptr, metrics, out);
 }
 
 stp_status stp_batch_launch(stp_batch b, void* stream) {

@@ -117,16 +117,21 @@ class Batch:
     launch() replays the plan's CUDA graph on the given stream.
     """
 
-    def __init__(self, items, shapes=None):
+    def __init__(self, items, shapes=None, metrics=None):
+        """items: (Predictor, q, params) per set; metrics: optional list with
+        each set's metric tensor (curvilinear) or None (Cartesian)."""
         self.items = []
         sets = []
-        for P, q, params in items:
+        for i, (P, q, params) in enumerate(items):
             P._check_inputs(q, params)
+            if metrics is not None and metrics[i] is not None:
+                P._check_metric(q, metrics[i])
             E = q.shape[0]
             avg, faces = P.empty_outputs(E, device=q.device)
             self.items.append((P, q, params, avg, faces))
             sets.append((P.handle, E, q, params, avg, faces))
-        self.handle = B.stp_batch_create(sets, shapes)
+        self.metrics = metrics  # keeps the tensors alive with the plan
+        self.handle = B.stp_batch_create(sets, shapes, metrics)
 
     def launch(self, stream=None):
         if stream is None:

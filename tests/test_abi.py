@@ -154,6 +154,14 @@ def test_predict_curvilinear_rejects_null_handle(lib):
         _binding.STP_ERR_INVALID_ARG
 
 
+def test_batch_create_curvilinear_rejects_missing_metrics(lib):
+    out = ctypes.c_void_p()
+    assert lib.stp_batch_create_curvilinear(1, None, None, ctypes.byref(out)) == \
+        _binding.STP_ERR_INVALID_ARG
+    assert lib.stp_batch_create_curvilinear(-1, None, None, ctypes.byref(out)) == \
+        _binding.STP_ERR_INVALID_ARG
+
+
 def test_predict_sources_rejects_bad_source_list(lib):
     assert lib.stp_predict_sources(None, 1, None, None, None, None, -1, None, None) == \
         _binding.STP_ERR_INVALID_ARG

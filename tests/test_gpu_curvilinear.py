@@ -178,6 +178,34 @@ def test_host_buffer_path_equals_device_path(precision):
     assert torch.equal(a_c, a_cd.cpu())
 
 
+def test_batch_of_curvilinear_and_cartesian_sets():
+    """stp_batch_create_curvilinear: curvilinear sets of several orders and
+    precisions beside Cartesian ones in one graph plan; each set's results
+    equal its own single-set call bit for bit."""
+    specs = [(8, 300, "fp64", True), (5, 700, "ff", True), (10, 40, "fp32", True),
+             (4, 900, "fp64", False), (7, 120, "ff", False), (12, 9, "fp64", True)]
+    items, metrics, probs = [], [], []
+    for i, (N, E, prec, curv) in enumerate(specs):
+        make = curvilinear_problem if curv else elastic_problem
+        prob = make(N, E=E, seed_material=2800 + i, seed_waves=2900 + i, device="cuda")
+        P = stp.Predictor(N - 1, prob.h, prob.dt, precision=prec)
+        items.append((P, prob.q, prob.params))
+        metrics.append(prob.metric if curv else None)
+        probs.append(prob)
+    b = stp.Batch(items, metrics=metrics)
+    b.launch()
+    b.launch()  # a replay gives the same results
+    torch.cuda.synchronize()
+    for i, (P, q, params) in enumerate(items):
+        a_b, f_b = b.outputs(i)
+        a_s, f_s = P.predict(q, params, metric=metrics[i])
+        torch.cuda.synchronize()
+        assert torch.equal(a_b, a_s) and torch.equal(f_b, f_s), specs[i]
+    b.close()
+    for P, _, _ in items:
+        P.close()
+
+
 def test_argument_errors():
     N = 4
     prob = curvilinear_problem(N, E=8, device="cuda")
