@@ -329,6 +329,31 @@ def curvilinear_measurement(stp, torch, args, cartesian_ms: float):
     for prec in ("ff", "fp32"):
         out["variants"][prec]["speedup_vs_fp64"] = (out["variants"]["fp64"]["ms_per_launch"] /
                                                     out["variants"][prec]["ms_per_launch"])
+    # the paper's own setting for its headline figure: N = 11 (order 10) on
+    # curvilinear elements; 4096 elements of side 1/32 on the smooth map
+    N11 = 11
+    p11 = curvilinear_problem(N11, grid=(16, 16, 16), h=1.0 / 32, device="cuda")
+    out["order10"] = {"workload": "order-10 (N=11) elastic STP on curvilinear elements, "
+                                  "16^3=4096 elements of side 1/32, one launch",
+                      "flops_per_element": flops_per_element_curvilinear(N11), "variants": {}}
+    for prec in ("fp64", "ff"):
+        with stp.Predictor(N11 - 1, p11.h, p11.dt, precision=prec) as P:
+            avg, faces = P.empty_outputs(p11.E)
+            for _ in range(3):
+                P.predict(p11.q, p11.params, out=(avg, faces), stream=stream, metric=p11.metric)
+            s0 = torch.cuda.Event(enable_timing=True)
+            s1 = torch.cuda.Event(enable_timing=True)
+            s0.record(stream)
+            for _ in range(args.mixed_steps):
+                P.predict(p11.q, p11.params, out=(avg, faces), stream=stream, metric=p11.metric)
+            s1.record(stream)
+            torch.cuda.synchronize()
+            ms = s0.elapsed_time(s1) / args.mixed_steps
+        tf = p11.E * flops_per_element_curvilinear(N11) / (ms / 1e3) / 1e12
+        out["order10"]["variants"][prec] = {"ms_per_launch": ms,
+                                            "elements_per_s": p11.E / (ms / 1e3),
+                                            "tflops_algorithmic": tf,
+                                            "frac_of_fp64_peak": tf / FP64_PEAK_TFLOPS}
     return out
 
 
