@@ -365,6 +365,16 @@ stp_status stp_server_create(int64_t hbm_budget_bytes, int slots, stp_server* ou
 stp_status stp_server_add_sim(stp_server s, stp_handle h, int64_t elements, const double* q0,
                               const double* params, int* sim_id);
 
+/* A curvilinear simulation: as stp_server_add_sim, plus its per-node inverse
+ * Jacobians (layout of stp_predict_curvilinear; host or device like q0),
+ * which stay resident beside the material while the simulation is admitted
+ * (its footprint grows by 9N^3 doubles per element). Its steps run in FP64
+ * as stp_predict_curvilinear, in a launch of their own on the slot's stream.
+ * STP_ERR_INVALID_ARG for a NULL metric, otherwise as stp_server_add_sim. */
+stp_status stp_server_add_sim_curvilinear(stp_server s, stp_handle h, int64_t elements,
+                                          const double* q0, const double* params,
+                                          const double* metric, int* sim_id);
+
 /* Queue one step of a simulation (arrival time = now). */
 stp_status stp_server_submit(stp_server s, int sim_id);
 

@@ -84,6 +84,8 @@ def load():
         lib.stp_batch_run_static.restype = ctypes.c_int
         srv = {"stp_server_create": [i64, ctypes.c_int, ctypes.POINTER(vp)],
                "stp_server_add_sim": [vp, vp, i64, vp, vp, ctypes.POINTER(ctypes.c_int)],
+               "stp_server_add_sim_curvilinear": [vp, vp, i64, vp, vp, vp,
+                                                  ctypes.POINTER(ctypes.c_int)],
                "stp_server_submit": [vp, ctypes.c_int],
                "stp_server_progress": [vp, ctypes.POINTER(ctypes.c_int)],
                "stp_server_drain": [vp],
@@ -317,10 +319,16 @@ def stp_server_create(hbm_budget_bytes: int, slots: int = 3) -> int:
     return h.value
 
 
-def stp_server_add_sim(srv: int, handle: int, elements: int, q0, params) -> int:
+def stp_server_add_sim(srv: int, handle: int, elements: int, q0, params, metric=None) -> int:
+    """metric: optional inverse Jacobians of a curvilinear simulation."""
     i = ctypes.c_int()
-    _check(load().stp_server_add_sim(srv, handle, elements, _ptr(q0), _ptr(params), ctypes.byref(i)),
-           "stp_server_add_sim")
+    if metric is None:
+        _check(load().stp_server_add_sim(srv, handle, elements, _ptr(q0), _ptr(params),
+                                         ctypes.byref(i)), "stp_server_add_sim")
+    else:
+        _check(load().stp_server_add_sim_curvilinear(srv, handle, elements, _ptr(q0), _ptr(params),
+                                                     _ptr(metric), ctypes.byref(i)),
+               "stp_server_add_sim_curvilinear")
     return i.value
 
 

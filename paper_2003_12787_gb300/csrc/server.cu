@@ -22,7 +22,10 @@
 //      admission waits for the evictions issued before it (its memory may be
 //      theirs, and a re-admitted simulation's host copy must be complete);
 //   3. launches up to 128 ready, resident simulations as ONE persistent
-//      batched FP64 launch on a free slot (its own stream and scratch).
+//      batched FP64 launch on a free slot (its own stream and scratch);
+//      curvilinear simulations (their per-node inverse Jacobians resident
+//      beside the material) get their own FP64 curvilinear launch on the
+//      same stream, between the same timing events.
 // New requests therefore join the next launch while earlier launches are
 // still on the GPU, and launches on different slots overlap on the device.
 #include <algorithm>
@@ -103,17 +106,21 @@ struct Sim {
   stp_handle handle = nullptr;
   int N = 0;
   int64_t E = 0;
-  size_t bytes_state = 0, bytes_params = 0, bytes_faces = 0;
+  size_t bytes_state = 0, bytes_params = 0, bytes_faces = 0, bytes_metric = 0;
   double* host_q = nullptr;       // pinned: state while evicted
   double* host_params = nullptr;  // pinned
+  double* host_metric = nullptr;  // pinned (curvilinear simulations only)
   double* host_faces = nullptr;   // pinned: last faces while evicted
   bool resident = false;
-  size_t off = 0;  // pool offset of [state0 | state1 | params | faces]
+  size_t off = 0;  // pool offset of [state0 | state1 | params | faces | metric]
   int cur = 0;     // which state buffer holds q_n
   bool busy = false, queued = false, have_faces = false;
   int64_t last_used = 0, steps = 0;
   std::deque<Request> pending;
-  size_t footprint() const { return 2 * align_up(bytes_state) + align_up(bytes_params) + align_up(bytes_faces); }
+  size_t footprint() const {
+    return 2 * align_up(bytes_state) + align_up(bytes_params) + align_up(bytes_faces) +
+           align_up(bytes_metric);
+  }
 };
 
 struct Slot {
@@ -161,6 +168,10 @@ struct Server {
   double* faces(const Sim& s) const {
     return reinterpret_cast<double*>(pool_base + s.off + 2 * align_up(s.bytes_state) + align_up(s.bytes_params));
   }
+  double* metric(const Sim& s) const {
+    return reinterpret_cast<double*>(pool_base + s.off + 2 * align_up(s.bytes_state) +
+                                     align_up(s.bytes_params) + align_up(s.bytes_faces));
+  }
 
   cudaError_t evict(int i) {
     Sim& s = sims[i];
@@ -204,6 +215,8 @@ struct Server {
     *err = cudaMemcpyAsync(state(s, 0), s.host_q, s.bytes_state, cudaMemcpyHostToDevice, copy_stream);
     if (*err == cudaSuccess)
       *err = cudaMemcpyAsync(params(s), s.host_params, s.bytes_params, cudaMemcpyHostToDevice, copy_stream);
+    if (*err == cudaSuccess && s.bytes_metric)
+      *err = cudaMemcpyAsync(metric(s), s.host_metric, s.bytes_metric, cudaMemcpyHostToDevice, copy_stream);
     *copied = true;
     ++admissions;
     peak_used = std::max(peak_used, pool.used());
@@ -280,27 +293,41 @@ struct Server {
         if ((e = cudaStreamWaitEvent(sl.stream, copy_done, 0)) != cudaSuccess) return e;
       }
       const int n = (int)batch.size();
-      std::vector<int> N(n);
-      std::vector<int64_t> E(n);
-      std::vector<const double*> q(n), p(n), tb(n);
-      std::vector<double*> a(n), f(n);
+      std::vector<int> N, curv;
+      std::vector<int64_t> E;
+      std::vector<const double*> q, p, tb;
+      std::vector<double*> a, f;
       for (int k = 0; k < n; ++k) {
         Sim& s = sims[batch[k]];
-        N[k] = s.N;
-        E[k] = s.E;
-        q[k] = state(s, s.cur);
-        a[k] = state(s, s.cur ^ 1);
-        p[k] = params(s);
-        f[k] = faces(s);
-        tb[k] = stp_handle_tables(s.handle);
         s.busy = true;
         s.queued = false;
+        if (s.bytes_metric) {  // curvilinear: a launch of its own
+          curv.push_back(batch[k]);
+          continue;
+        }
+        N.push_back(s.N);
+        E.push_back(s.E);
+        q.push_back(state(s, s.cur));
+        a.push_back(state(s, s.cur ^ 1));
+        p.push_back(params(s));
+        f.push_back(faces(s));
+        tb.push_back(stp_handle_tables(s.handle));
       }
       int too_big = 0;
       if ((e = cudaEventRecord(sl.start, sl.stream)) != cudaSuccess) return e;
-      e = launch_param_batch(n, N.data(), E.data(), q.data(), p.data(), a.data(), f.data(), tb.data(),
-                             sl.scratch, static_scratch_bytes(), sl.stream, &too_big);
-      if (e != cudaSuccess) return e;
+      if (!N.empty()) {
+        e = launch_param_batch((int)N.size(), N.data(), E.data(), q.data(), p.data(), a.data(),
+                               f.data(), tb.data(), sl.scratch, static_scratch_bytes(), sl.stream,
+                               &too_big);
+        if (e != cudaSuccess) return e;
+      }
+      for (int i : curv) {
+        Sim& s = sims[i];
+        e = launch_curvilinear(s.N, s.E, state(s, s.cur), params(s), metric(s), state(s, s.cur ^ 1),
+                               faces(s), stp_handle_tables(s.handle), stp_handle_dx(s.handle),
+                               sl.stream);
+        if (e != cudaSuccess) return e;
+      }
       if ((e = cudaEventRecord(sl.done, sl.stream)) != cudaSuccess) return e;
       sl.sims = batch;
       sl.busy = true;
@@ -336,6 +363,7 @@ struct Server {
       cudaFreeHost(s.host_q);
       cudaFreeHost(s.host_params);
       cudaFreeHost(s.host_faces);
+      cudaFreeHost(s.host_metric);
     }
     cudaFree(pool_base);
   }
@@ -377,7 +405,8 @@ void server_destroy(Server* s) {
 }
 
 cudaError_t server_add_sim(Server* s, stp_handle h, int N, int64_t E, const double* q0,
-                           const double* params, bool device_src, int* id, bool* too_big) {
+                           const double* params, const double* metric, bool device_src, int* id,
+                           bool* too_big) {
   *too_big = false;
   Sim sim;
   sim.handle = h;
@@ -387,6 +416,7 @@ cudaError_t server_add_sim(Server* s, stp_handle h, int N, int64_t E, const doub
   sim.bytes_state = (size_t)E * n3 * 9 * 8;
   sim.bytes_params = (size_t)E * n3 * 3 * 8;
   sim.bytes_faces = (size_t)E * N * N * 54 * 8;
+  sim.bytes_metric = metric ? (size_t)E * n3 * 9 * 8 : 0;
   if (sim.footprint() > s->budget) {
     *too_big = true;
     return cudaErrorInvalidValue;
@@ -394,13 +424,16 @@ cudaError_t server_add_sim(Server* s, stp_handle h, int N, int64_t E, const doub
   cudaError_t e = cudaMallocHost(&sim.host_q, std::max<size_t>(sim.bytes_state, 8));
   if (e == cudaSuccess) e = cudaMallocHost(&sim.host_params, std::max<size_t>(sim.bytes_params, 8));
   if (e == cudaSuccess) e = cudaMallocHost(&sim.host_faces, std::max<size_t>(sim.bytes_faces, 8));
+  if (e == cudaSuccess && metric) e = cudaMallocHost(&sim.host_metric, sim.bytes_metric);
   const cudaMemcpyKind kind = device_src ? cudaMemcpyDeviceToHost : cudaMemcpyHostToHost;
   if (e == cudaSuccess) e = cudaMemcpy(sim.host_q, q0, sim.bytes_state, kind);
   if (e == cudaSuccess) e = cudaMemcpy(sim.host_params, params, sim.bytes_params, kind);
+  if (e == cudaSuccess && metric) e = cudaMemcpy(sim.host_metric, metric, sim.bytes_metric, kind);
   if (e != cudaSuccess) {
     cudaFreeHost(sim.host_q);
     cudaFreeHost(sim.host_params);
     cudaFreeHost(sim.host_faces);
+    cudaFreeHost(sim.host_metric);
     return e;
   }
   *id = (int)s->sims.size();

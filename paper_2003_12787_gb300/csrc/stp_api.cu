@@ -544,6 +544,7 @@ stp_status stp_device_status(stp_handle h, void* stream, unsigned int* flags) {
 
 namespace stp {
 const double* stp_handle_tables(stp_handle h) { return h->d_tables; }
+double stp_handle_dx(stp_handle h) { return h->dx; }
 }  // namespace stp
 
 struct stp_server_s {
@@ -860,26 +861,46 @@ stp_status stp_server_create(int64_t hbm_budget_bytes, int slots, stp_server* ou
   return STP_OK;
 }
 
-stp_status stp_server_add_sim(stp_server s, stp_handle h, int64_t elements, const double* q0,
-                              const double* params, int* sim_id) {
+namespace {
+
+bool is_device_memory(const void* p) {
+  cudaPointerAttributes a;
+  bool d = false;
+  if (cudaPointerGetAttributes(&a, p) == cudaSuccess)
+    d = a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+  cudaGetLastError();
+  return d;
+}
+
+stp_status server_add_sim_impl(stp_server s, stp_handle h, int64_t elements, const double* q0,
+                               const double* params, const double* metric, int* sim_id) {
   if (!s || !s->impl || !h || !sim_id) return fail(STP_ERR_INVALID_ARG, "null argument");
   if (elements <= 0 || !q0 || !params) return fail(STP_ERR_INVALID_ARG, "bad simulation buffers");
   if (h->precision != STP_PRECISION_FP64) return fail(STP_ERR_UNSUPPORTED, "served steps are FP64");
-  cudaPointerAttributes aq, ap;
-  bool dq = false, dp = false;
-  if (cudaPointerGetAttributes(&aq, q0) == cudaSuccess)
-    dq = aq.type == cudaMemoryTypeDevice || aq.type == cudaMemoryTypeManaged;
-  cudaGetLastError();
-  if (cudaPointerGetAttributes(&ap, params) == cudaSuccess)
-    dp = ap.type == cudaMemoryTypeDevice || ap.type == cudaMemoryTypeManaged;
-  cudaGetLastError();
-  if (dq != dp) return fail(STP_ERR_INVALID_ARG, "q0 and params must both be host or both device");
+  const bool dq = is_device_memory(q0), dp = is_device_memory(params);
+  if (dq != dp || (metric && is_device_memory(metric) != dq))
+    return fail(STP_ERR_INVALID_ARG, "q0, params (and metric) must be all host or all device");
   bool too_big = false;
-  cudaError_t e = stp::server_add_sim(s->impl, h, h->N, elements, q0, params, dq, sim_id, &too_big);
+  cudaError_t e = stp::server_add_sim(s->impl, h, h->N, elements, q0, params, metric, dq, sim_id,
+                                      &too_big);
   if (too_big) return fail(STP_ERR_INVALID_ARG, "simulation does not fit the HBM budget");
   if (e == cudaErrorMemoryAllocation) return fail(STP_ERR_OOM, "pinned host allocation failed");
   if (e != cudaSuccess) return cuda_fail(e, "add simulation");
   return STP_OK;
+}
+
+}  // namespace
+
+stp_status stp_server_add_sim(stp_server s, stp_handle h, int64_t elements, const double* q0,
+                              const double* params, int* sim_id) {
+  return server_add_sim_impl(s, h, elements, q0, params, nullptr, sim_id);
+}
+
+stp_status stp_server_add_sim_curvilinear(stp_server s, stp_handle h, int64_t elements,
+                                          const double* q0, const double* params,
+                                          const double* metric, int* sim_id) {
+  if (!metric) return fail(STP_ERR_INVALID_ARG, "null metric");
+  return server_add_sim_impl(s, h, elements, q0, params, metric, sim_id);
 }
 
 stp_status stp_server_submit(stp_server s, int sim_id) {

@@ -132,13 +132,15 @@ int static_max_sets();
 
 // Device tables of a handle (stp_api.cu).
 const double* stp_handle_tables(stp_handle h);
+double stp_handle_dx(stp_handle h);
 
 // Served predictor (server.cu); see include/stp.h for the behaviour.
 struct Server;
 cudaError_t server_create(int64_t budget, int nslots, Server** out);
 void server_destroy(Server* s);
 cudaError_t server_add_sim(Server* s, stp_handle h, int N, int64_t E, const double* q0,
-                           const double* params, bool device_src, int* id, bool* too_big);
+                           const double* params, const double* metric, bool device_src, int* id,
+                           bool* too_big);
 cudaError_t server_run_trace(Server* s, int64_t n, const double* t_arr, const int* sim_ids,
                              double* latency, double* wall);
 cudaError_t server_drain(Server* s);

@@ -163,9 +163,13 @@ class Server:
         self.handle = B.stp_server_create(hbm_budget_bytes, slots)
         self.sims = []  # (Predictor, E)
 
-    def add_sim(self, predictor: "Predictor", q0: torch.Tensor, params: torch.Tensor) -> int:
+    def add_sim(self, predictor: "Predictor", q0: torch.Tensor, params: torch.Tensor,
+                metric=None) -> int:
+        """metric: optional inverse Jacobians (curvilinear simulation)."""
         predictor._check_inputs(q0, params)
-        sid = B.stp_server_add_sim(self.handle, predictor.handle, q0.shape[0], q0, params)
+        if metric is not None:
+            predictor._check_metric(q0, metric)
+        sid = B.stp_server_add_sim(self.handle, predictor.handle, q0.shape[0], q0, params, metric)
         self.sims.append((predictor, q0.shape[0]))
         return sid
 

@@ -162,6 +162,12 @@ def test_batch_create_curvilinear_rejects_missing_metrics(lib):
         _binding.STP_ERR_INVALID_ARG
 
 
+def test_server_add_sim_curvilinear_rejects_null_arguments(lib):
+    i = ctypes.c_int()
+    assert lib.stp_server_add_sim_curvilinear(None, None, 1, None, None, None, ctypes.byref(i)) == \
+        _binding.STP_ERR_INVALID_ARG
+
+
 def test_predict_sources_rejects_bad_source_list(lib):
     assert lib.stp_predict_sources(None, 1, None, None, None, None, -1, None, None) == \
         _binding.STP_ERR_INVALID_ARG

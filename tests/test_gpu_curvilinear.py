@@ -206,6 +206,38 @@ def test_batch_of_curvilinear_and_cartesian_sets():
         P.close()
 
 
+def test_curvilinear_simulations_in_the_served_loop():
+    """Curvilinear and Cartesian simulations served together under a budget
+    that forces evictions (the metric is re-admitted with the state): each
+    equals repeated single-set calls with q_{n+1} := avg_n, bit for bit."""
+    specs = [(5, 24, True), (8, 9, False), (7, 12, True), (4, 40, True)]
+    sims = []
+    for i, (N, E, curv) in enumerate(specs):
+        make = curvilinear_problem if curv else elastic_problem
+        prob = make(N, E=E, seed_material=3000 + i, seed_waves=3100 + i)
+        sims.append((stp.Predictor(N - 1, prob.h, prob.dt), prob))
+    foot = max(8 * E * ((30 if c else 21) * N ** 3 + 54 * N ** 2) for N, E, c in specs)
+    srv = stp.Server(2 * foot + (1 << 20), slots=2)
+    ids = [srv.add_sim(P, prob.q, prob.params, metric=prob.metric) for P, prob in sims]
+    steps = 3
+    order = np.tile(np.arange(len(sims)), steps)
+    srv.run_trace(np.linspace(0.0, 0.01, len(order)), np.asarray(ids, dtype=np.int32)[order])
+    assert srv.stats()["evictions"] > 0
+    for i, (P, prob) in enumerate(sims):
+        q_mix, f_mix, n = srv.read(ids[i])
+        assert n == steps
+        q = prob.q.cuda()
+        m = prob.metric.cuda() if prob.metric is not None else None
+        for _ in range(steps):
+            avg, faces = P.predict(q, prob.params.cuda(), metric=m)
+            q = avg
+        torch.cuda.synchronize()
+        assert torch.equal(q.cpu(), q_mix) and torch.equal(faces.cpu(), f_mix), specs[i]
+    srv.close()
+    for P, _ in sims:
+        P.close()
+
+
 def test_argument_errors():
     N = 4
     prob = curvilinear_problem(N, E=8, device="cuda")
