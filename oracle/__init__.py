@@ -84,6 +84,12 @@ def _load():
                                                    ctypes.c_void_p, ctypes.c_void_p,
                                                    ctypes.c_void_p, ctypes.c_void_p]
             lib.oracle_stp_curvilinear.restype = ctypes.c_int
+            lib.oracle_stp_sources_curvilinear.argtypes = [
+                ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int64, ctypes.c_double,
+                ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p,
+                ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                ctypes.c_void_p, ctypes.c_void_p]
+            lib.oracle_stp_sources_curvilinear.restype = ctypes.c_int
             lib.oracle_num_threads.argtypes = []
             lib.oracle_num_threads.restype = ctypes.c_int
             _lib = lib
@@ -133,6 +139,19 @@ def num_threads() -> int:
     return int(_load().oracle_num_threads())
 
 
+def _source_arrays(sources, K):
+    """(n, elem, pos, amp, der) arrays of a list of point-source dicts."""
+    n = len(sources)
+    elem = np.array([int(x["element"]) for x in sources], dtype=np.int64)
+    pos = np.ascontiguousarray([x["position"] for x in sources], dtype=np.float64).reshape(n, 3)
+    amp = np.ascontiguousarray([x["amplitude"] for x in sources], dtype=np.float64).reshape(n, 9)
+    der = np.ascontiguousarray([list(x["derivatives"])[:K - 1] for x in sources],
+                               dtype=np.float64).reshape(n, max(K - 1, 0))
+    if der.shape[1] != K - 1:
+        raise ValueError(f"each source needs {K - 1} derivatives")
+    return n, elem, pos, amp, der
+
+
 def stp(q: np.ndarray, params: np.ndarray, h: float, dt: float, K: int | None = None,
         return_terms: bool = False, nodes: str = "gl", sources=None):
     """Run the oracle STP.
@@ -158,14 +177,7 @@ def stp(q: np.ndarray, params: np.ndarray, h: float, dt: float, K: int | None = 
     faces = np.empty((E, 6, N, N, M))
     terms = np.empty((E, K, N, N, N, M)) if return_terms else None
     if sources:
-        n = len(sources)
-        elem = np.array([int(x["element"]) for x in sources], dtype=np.int64)
-        pos = np.ascontiguousarray([x["position"] for x in sources], dtype=np.float64).reshape(n, 3)
-        amp = np.ascontiguousarray([x["amplitude"] for x in sources], dtype=np.float64).reshape(n, 9)
-        der = np.ascontiguousarray([list(x["derivatives"])[:K - 1] for x in sources],
-                                   dtype=np.float64).reshape(n, max(K - 1, 0))
-        if der.shape[1] != K - 1:
-            raise ValueError(f"each source needs {K - 1} derivatives")
+        n, elem, pos, amp, der = _source_arrays(sources, K)
         rc = _load().oracle_stp_sources(NODE_FAMILIES[nodes], N, K, E, float(h), float(dt),
                                         q.ctypes.data, params.ctypes.data, n, elem.ctypes.data,
                                         pos.ctypes.data, amp.ctypes.data,
@@ -185,14 +197,16 @@ def stp(q: np.ndarray, params: np.ndarray, h: float, dt: float, K: int | None = 
 
 
 def stp_curvilinear(q: np.ndarray, params: np.ndarray, metric: np.ndarray, dt: float,
-                    K: int | None = None, return_terms: bool = False, nodes: str = "gl"):
+                    K: int | None = None, return_terms: bool = False, nodes: str = "gl",
+                    sources=None):
     """Run the oracle STP on curvilinear elements.
 
     metric: [E][N][N][N][3][3] (or [..][9]) float64, the inverse Jacobian
     G[d][j] = dxi_d/dx_j of the map from the reference cube [0,1]^3 to
     physical space at every node (xi_1, xi_2, xi_3 along the x, y, z node
     indices); see oracle_stp_curvilinear in stp_oracle.c. Other arguments and
-    the outputs as in ``stp`` (no element side: the metric carries the scale).
+    the outputs as in ``stp`` (no element side: the metric carries the scale);
+    point sources project with the node volumes w_node |det J_node|.
     """
     q = np.ascontiguousarray(q, dtype=np.float64)
     params = np.ascontiguousarray(params, dtype=np.float64)
@@ -206,10 +220,18 @@ def stp_curvilinear(q: np.ndarray, params: np.ndarray, metric: np.ndarray, dt: f
     avg = np.empty_like(q)
     faces = np.empty((E, 6, N, N, M))
     terms = np.empty((E, K, N, N, N, M)) if return_terms else None
-    rc = _load().oracle_stp_curvilinear(NODE_FAMILIES[nodes], N, K, E, float(dt), q.ctypes.data,
-                                        params.ctypes.data, metric.ctypes.data, avg.ctypes.data,
-                                        faces.ctypes.data,
-                                        terms.ctypes.data if terms is not None else None)
+    if sources:
+        n, elem, pos, amp, der = _source_arrays(sources, K)
+        rc = _load().oracle_stp_sources_curvilinear(
+            NODE_FAMILIES[nodes], N, K, E, float(dt), q.ctypes.data, params.ctypes.data,
+            metric.ctypes.data, n, elem.ctypes.data, pos.ctypes.data, amp.ctypes.data,
+            der.ctypes.data if der.size else None, avg.ctypes.data, faces.ctypes.data,
+            terms.ctypes.data if terms is not None else None)
+    else:
+        rc = _load().oracle_stp_curvilinear(NODE_FAMILIES[nodes], N, K, E, float(dt),
+                                            q.ctypes.data, params.ctypes.data, metric.ctypes.data,
+                                            avg.ctypes.data, faces.ctypes.data,
+                                            terms.ctypes.data if terms is not None else None)
     if rc != 0:
         raise RuntimeError(f"oracle_stp_curvilinear returned {rc}")
     if return_terms:

@@ -376,11 +376,21 @@ int oracle_stp_nodes(int nodes, int N, int K, int64_t E, double h, double dt, co
  * Lagrange polynomials. Sources in one element add up. Arrays: elem[nsrc],
  * pos[nsrc][3] (x, y, z), amp[nsrc][9], der[nsrc][K-1].
  */
-int oracle_stp_sources(int nodes, int N, int K, int64_t E, double h, double dt, const double* q,
-                       const double* params, int nsrc, const int64_t* elem, const double* pos,
-                       const double* amp, const double* der, double* avg, double* faces,
-                       double* terms) {
-  if (N < 1 || N > 16 || K < 1 || E < 0 || !(h > 0.0) || nsrc < 0) return -1;
+/* determinant of a 3x3 row-major matrix (rule of Sarrus) */
+static double det3(const double* a) {
+  return a[0] * a[4] * a[8] + a[1] * a[5] * a[6] + a[2] * a[3] * a[7] -
+         a[2] * a[4] * a[6] - a[0] * a[5] * a[7] - a[1] * a[3] * a[8];
+}
+
+/* Point sources on cubes of side h (metric NULL) or on curvilinear elements
+ * (metric as in oracle_stp_curvilinear; h unused). The node's volume in the
+ * diagonal mass matrix is w_node h^3 on a cube and w_node |det J_node| on a
+ * curvilinear element, J = dx/dxi = G^-1, so |det J| = 1 / |det G|. */
+static int stp_sources(int nodes, int N, int K, int64_t E, double h, double dt, const double* q,
+                       const double* params, const double* metric, int nsrc, const int64_t* elem,
+                       const double* pos, const double* amp, const double* der, double* avg,
+                       double* faces, double* terms) {
+  if (N < 1 || N > 16 || K < 1 || E < 0 || (!metric && !(h > 0.0)) || nsrc < 0) return -1;
   double xi[16], w[16], D[16 * 16], phi0[16], phi1[16];
   if (oracle_tables_nodes(nodes, N, xi, D, phi0, phi1) != 0) return -1;
   if ((nodes == 0 ? oracle_gl_nodes(N, xi, w) : oracle_gll_nodes(N, xi, w)) != 0) return -1;
@@ -399,8 +409,10 @@ int oracle_stp_sources(int nodes, int N, int K, int64_t E, double h, double dt, 
     for (int z = 0; z < N; ++z)
       for (int y = 0; y < N; ++y)
         for (int x = 0; x < N; ++x) {
+          const double vol = metric ? 1.0 / fabs(det3(metric + ((size_t)e * n3 + NODE(z, y, x)) * 9))
+                                    : h * h * h;
           const double proj = lagrange(N, xi, x, pos[3 * i]) * lagrange(N, xi, y, pos[3 * i + 1]) *
-                               lagrange(N, xi, z, pos[3 * i + 2]) / (w[x] * w[y] * w[z] * h * h * h);
+                               lagrange(N, xi, z, pos[3 * i + 2]) / (w[x] * w[y] * w[z] * vol);
           for (int k = 0; k + 1 < K; ++k)
             for (int s = 0; s < M; ++s)
               src[e][(size_t)k * n3m + (size_t)NODE(z, y, x) * M + s] +=
@@ -418,8 +430,9 @@ int oracle_stp_sources(int nodes, int N, int K, int64_t E, double h, double dt, 
 #pragma omp for schedule(dynamic, 4)
       for (int64_t e = 0; e < E; ++e) {
         if (!work) continue;
-        stp_element(N, K, h, dt, D, phi0, phi1, q + e * n3m, params + e * n3 * 3, NULL, src[e],
-                    avg + e * n3m, faces + e * (size_t)6 * N * N * M,
+        stp_element(N, K, metric ? 1.0 : h, dt, D, phi0, phi1, q + e * n3m, params + e * n3 * 3,
+                    metric ? metric + e * n3 * 9 : NULL, src[e], avg + e * n3m,
+                    faces + e * (size_t)6 * N * N * M,
                     terms ? terms + e * (size_t)K * n3m : NULL, work, work + n3m, work + 2 * n3m);
       }
       free(work);
@@ -428,6 +441,25 @@ int oracle_stp_sources(int nodes, int N, int K, int64_t E, double h, double dt, 
   for (int64_t e = 0; e < E; ++e) free(src[e]);
   free(src);
   return err;
+}
+
+int oracle_stp_sources(int nodes, int N, int K, int64_t E, double h, double dt, const double* q,
+                       const double* params, int nsrc, const int64_t* elem, const double* pos,
+                       const double* amp, const double* der, double* avg, double* faces,
+                       double* terms) {
+  return stp_sources(nodes, N, K, E, h, dt, q, params, NULL, nsrc, elem, pos, amp, der, avg, faces,
+                     terms);
+}
+
+/* Point sources on curvilinear elements (see stp_sources and
+ * oracle_stp_curvilinear). */
+int oracle_stp_sources_curvilinear(int nodes, int N, int K, int64_t E, double dt, const double* q,
+                                   const double* params, const double* metric, int nsrc,
+                                   const int64_t* elem, const double* pos, const double* amp,
+                                   const double* der, double* avg, double* faces, double* terms) {
+  if (!metric) return -1;
+  return stp_sources(nodes, N, K, E, 1.0, dt, q, params, metric, nsrc, elem, pos, amp, der, avg,
+                     faces, terms);
 }
 
 /*

@@ -198,6 +198,63 @@ def test_brute_force_dense_operator(N, nodes):
                 assert ref.rel_err(faces[e, 2 * d + side], fx) <= 1e-13
 
 
+# --- point sources on curvilinear elements (the node volume is w |det J|) ---
+
+def _source(e, rng, K):
+    return {"element": e, "position": tuple(rng.uniform(0, 1, 3)),
+            "amplitude": rng.uniform(-1, 1, 9), "derivatives": rng.uniform(-2, 2, K - 1)}
+
+
+def test_sources_on_a_cube_metric_match_the_cartesian_oracle():
+    N, E, h, dt = 4, 3, 0.3, 0.004
+    rng = np.random.default_rng(91)
+    params = _params(E, N, rng)
+    q = rng.uniform(-1, 1, (E, N, N, N, 9))
+    src = [_source(1, rng, N + 1), _source(1, rng, N + 1), _source(2, rng, N + 1)]
+    G = np.zeros((E, N, N, N, 3, 3))
+    G[...] = np.eye(3) / h
+    a_c, f_c = oracle.stp(q, params, h, dt, sources=src)
+    a, f = oracle.stp_curvilinear(q, params, G, dt, sources=src)
+    assert ref.rel_err(a, a_c) <= 1e-14 and ref.rel_err(f, f_c) <= 1e-14
+
+
+@pytest.mark.parametrize("N,nodes", [(2, "gl"), (3, "gl"), (3, "gll")])
+def test_sources_brute_force_dense_operator(N, nodes):
+    """Dense operator physical derivative first, and the source projected
+    with numpy's Lagrange basis, quadrature weights and determinant:
+    s_node = phi_node(pos) / (w_node |det G_node|^-1) amp f^(k)."""
+    rng = np.random.default_rng(95 + N)
+    E, K, h, dt = 2, N + 1, 0.3, 0.004
+    params = _params(E, N, rng)
+    q = rng.uniform(-1, 1, (E, N, N, N, 9))
+    G = _random_metric(E, N, h, rng)
+    src = [_source(0, rng, K), _source(0, rng, K), _source(1, rng, K)]
+    avg, _, terms = oracle.stp_curvilinear(q, params, G, dt, return_terms=True, nodes=nodes,
+                                           sources=src)
+    _, w = ref.points(N, nodes)
+    W = w[:, None, None] * w[None, :, None] * w[None, None, :]
+    for e in range(E):
+        L = ref.dense_operator_curvilinear(N, params[e], G[e], nodes)
+        vol = W / np.abs(np.linalg.det(G[e]))  # w_node |det J_node|
+        S = np.zeros((K - 1, N, N, N, 9))
+        for x in src:
+            if x["element"] != e:
+                continue
+            px = ref.lagrange_phi_numpy(N, x["position"][0], nodes)
+            py = ref.lagrange_phi_numpy(N, x["position"][1], nodes)
+            pz = ref.lagrange_phi_numpy(N, x["position"][2], nodes)
+            P = pz[:, None, None] * py[None, :, None] * px[None, None, :] / vol
+            for k in range(K - 1):
+                S[k] += P[..., None] * np.asarray(x["amplitude"]) * x["derivatives"][k]
+        p = q[e].reshape(-1)
+        expect = p.copy()
+        for k in range(K - 1):
+            p = L @ p + S[k].reshape(-1)
+            expect = expect + dt ** (k + 1) / math.factorial(k + 2) * p
+            assert ref.rel_err(terms[e, k + 1].reshape(-1), p) <= 1e-12
+        assert ref.rel_err(avg[e].reshape(-1), expect) <= 1e-13
+
+
 def test_rejects_bad_arguments():
     q = np.zeros((1, 3, 3, 3, 9))
     with pytest.raises(ValueError):
@@ -213,6 +270,10 @@ SRC = os.path.join(os.path.dirname(oracle.__file__), "stp_oracle.c")
 MUTANTS = {
     "metric transposed": ("metric[n * 9 + 3 * d + j]", "metric[n * 9 + 3 * j + d]"),
     "reference direction's B": ("elastic_B(j, params[n * 3 + 0]", "elastic_B(d, params[n * 3 + 0]"),
+}
+SOURCE_MUTANTS = {
+    "det G taken for det J": ("1.0 / fabs(det3(metric + ((size_t)e * n3 + NODE(z, y, x)) * 9))",
+                              "fabs(det3(metric + ((size_t)e * n3 + NODE(z, y, x)) * 9))"),
 }
 
 
@@ -258,9 +319,49 @@ def _pins_pass(lib):
     return ref.rel_err(avg_r, _rotate(avg, R)) <= 1e-13
 
 
+def _source_pin_passes(lib):
+    """The dense-operator source pin (N = 2) through a compiled variant."""
+    rng = np.random.default_rng(7)
+    N, E, K, h, dt = 2, 1, 3, 0.3, 0.004
+    params = _params(E, N, rng)
+    q = rng.uniform(-1, 1, (E, N, N, N, 9))
+    G = np.ascontiguousarray(_random_metric(E, N, h, rng))
+    x = _source(0, rng, K)
+    lib.oracle_stp_sources_curvilinear.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                                   ctypes.c_int64, ctypes.c_double] + \
+        [ctypes.c_void_p] * 3 + [ctypes.c_int] + [ctypes.c_void_p] * 7
+    lib.oracle_stp_sources_curvilinear.restype = ctypes.c_int
+    elem = np.zeros(1, dtype=np.int64)
+    pos = np.asarray(x["position"], dtype=np.float64)
+    amp = np.asarray(x["amplitude"], dtype=np.float64)
+    der = np.asarray(x["derivatives"], dtype=np.float64)
+    avg = np.empty_like(q)
+    faces = np.empty((E, 6, N, N, 9))
+    assert lib.oracle_stp_sources_curvilinear(0, N, K, E, dt, q.ctypes.data, params.ctypes.data,
+                                              G.ctypes.data, 1, elem.ctypes.data, pos.ctypes.data,
+                                              amp.ctypes.data, der.ctypes.data, avg.ctypes.data,
+                                              faces.ctypes.data, None) == 0
+    # the independent expectation: dense operator and numpy projection
+    _, w = ref.points(N)
+    W = w[:, None, None] * w[None, :, None] * w[None, None, :]
+    L = ref.dense_operator_curvilinear(N, params[0], G[0])
+    px, py, pz = (ref.lagrange_phi_numpy(N, c) for c in x["position"])
+    P = pz[:, None, None] * py[None, :, None] * px[None, None, :] / (W / np.abs(np.linalg.det(G[0])))
+    p = q[0].reshape(-1)
+    expect = p.copy()
+    for k in range(K - 1):
+        p = L @ p + (P[..., None] * amp * der[k]).reshape(-1)
+        expect = expect + dt ** (k + 1) / math.factorial(k + 2) * p
+    return ref.rel_err(avg[0].reshape(-1), expect) <= 1e-13
+
+
 def test_pins_catch_planted_mistakes(tmp_path):
     text = open(SRC).read()
     assert _pins_pass(_variant(tmp_path, "unmutated", text))
     for name, (old, new) in MUTANTS.items():
         assert text.count(old) == 1, name
         assert not _pins_pass(_variant(tmp_path, name, text.replace(old, new))), name
+    assert _source_pin_passes(_variant(tmp_path, "unmutated_sources", text))
+    for name, (old, new) in SOURCE_MUTANTS.items():
+        assert text.count(old) == 1, name
+        assert not _source_pin_passes(_variant(tmp_path, name + "_src", text.replace(old, new))), name
