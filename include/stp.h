@@ -123,6 +123,20 @@ stp_status stp_predict_sources(stp_handle h, int64_t elements, const double* q,
                                int nsources, const stp_point_source* sources, void* stream);
 
 /*
+ * stp_predict_sources on curvilinear elements (the LOH1-type setting: a point
+ * source in a boundary-fitted mesh): the STP as stp_predict_curvilinear (its
+ * precisions), then the sources' response in FP64 with the curvilinear
+ * operator, the node volume of the mass matrix being w_node |det J_node| =
+ * w_node / |det G_node| from the metric (position in reference coordinates of
+ * the element, as before). Errors as stp_predict_sources and
+ * stp_predict_curvilinear.
+ */
+stp_status stp_predict_sources_curvilinear(stp_handle h, int64_t elements, const double* q,
+                                           const double* params, const double* metric,
+                                           double* out_avg, double* out_faces, int nsources,
+                                           const stp_point_source* sources, void* stream);
+
+/*
  * The STP on curvilinear elements. The paper's benchmark meshes are
  * curvilinear and boundary-fitted and store 9 geometry parameters per node
  * beside the 3 material parameters (Sec. VI). Here those 9 are the inverse

@@ -59,6 +59,8 @@ def load():
         lib.stp_get_nodes.restype = ctypes.c_int
         lib.stp_predict_sources.argtypes = [vp, i64, vp, vp, vp, vp, ctypes.c_int, vp, vp]
         lib.stp_predict_curvilinear.argtypes = [vp, i64, vp, vp, vp, vp, vp, vp]
+        lib.stp_predict_sources_curvilinear.argtypes = [vp, i64, vp, vp, vp, vp, vp,
+                                                        ctypes.c_int, vp, vp]
         lib.stp_predict_curvilinear_host.argtypes = [vp, i64, vp, vp, vp, vp, vp, vp]
         lib.stp_nodes.argtypes = [vp]
         lib.stp_nodes.restype = ctypes.c_int
@@ -215,20 +217,36 @@ class PointSource(ctypes.Structure):
                 ("amplitude", ctypes.c_double * 9), ("derivatives", ctypes.c_double * 12)]
 
 
-def stp_predict_sources(h: int, elements: int, q, params, out_avg, out_faces, sources,
-                        stream=None) -> None:
-    """sources: sequence of dicts with "element", "position" (3), "amplitude"
-    (9) and "derivatives" (f^(k)(t_n), k = 0..N-1; at most 12 are used)."""
+def _source_array(sources):
     arr = (PointSource * max(1, len(sources)))()
     for i, src in enumerate(sources):
         der = list(src["derivatives"])[:12]
         arr[i] = PointSource(int(src["element"]), (ctypes.c_double * 3)(*src["position"]),
                              (ctypes.c_double * 9)(*src["amplitude"]),
                              (ctypes.c_double * 12)(*(der + [0.0] * (12 - len(der)))))
+    return arr
+
+
+def stp_predict_sources(h: int, elements: int, q, params, out_avg, out_faces, sources,
+                        stream=None) -> None:
+    """sources: sequence of dicts with "element", "position" (3), "amplitude"
+    (9) and "derivatives" (f^(k)(t_n), k = 0..N-1; at most 12 are used)."""
+    arr = _source_array(sources)
     _check(load().stp_predict_sources(h, elements, _ptr(q), _ptr(params), _ptr(out_avg),
                                       _ptr(out_faces), len(sources),
                                       ctypes.cast(arr, ctypes.c_void_p), _stream(stream)),
            "stp_predict_sources")
+
+
+def stp_predict_sources_curvilinear(h: int, elements: int, q, params, metric, out_avg, out_faces,
+                                    sources, stream=None) -> None:
+    """stp_predict_sources on curvilinear elements (metric: device inverse Jacobians)."""
+    arr = _source_array(sources)
+    _check(load().stp_predict_sources_curvilinear(h, elements, _ptr(q), _ptr(params), _ptr(metric),
+                                                  _ptr(out_avg), _ptr(out_faces), len(sources),
+                                                  ctypes.cast(arr, ctypes.c_void_p),
+                                                  _stream(stream)),
+           "stp_predict_sources_curvilinear")
 
 
 def stp_predict_curvilinear(h: int, elements: int, q, params, metric, out_avg, out_faces,

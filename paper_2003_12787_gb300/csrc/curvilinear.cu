@@ -25,7 +25,7 @@
 // tables hold D dt/((k+2) dx), so the coefficients are multiplied by dx once.
 #include <type_traits>
 
-#include "ck_fp64.cuh"
+#include "ck_curv.cuh"
 #include "stp_internal.h"
 
 namespace stp {
@@ -46,46 +46,6 @@ struct CurvShape {
   static constexpr size_t SMEM =
       sizeof(double) * (size_t)(TABLE + (kQuantities + (DB ? 2 : 1) * A) * S);
 };
-
-// Adds the contributions of quantity s, whose derivative along reference
-// direction d is a, to a node's partial sums; (g0, g1, g2) = G[d][0..2]. The
-// sums are indexed by the output they feed: part[v_i] = sum_j dsigma_ij/dx_j,
-// part[s_ii] = dv_i/dx_i, part[s_ij] = dv_i/dx_j + dv_j/dx_i.
-__device__ __forceinline__ void curv_add(int s, double a, double g0, double g1, double g2,
-                                         double part[9]) {
-  switch (s) {
-    case kV1:
-      part[kS11] = fma(g0, a, part[kS11]);
-      part[kS12] = fma(g1, a, part[kS12]);
-      part[kS13] = fma(g2, a, part[kS13]);
-      break;
-    case kV2:
-      part[kS12] = fma(g0, a, part[kS12]);
-      part[kS22] = fma(g1, a, part[kS22]);
-      part[kS23] = fma(g2, a, part[kS23]);
-      break;
-    case kV3:
-      part[kS13] = fma(g0, a, part[kS13]);
-      part[kS23] = fma(g1, a, part[kS23]);
-      part[kS33] = fma(g2, a, part[kS33]);
-      break;
-    case kS11: part[kV1] = fma(g0, a, part[kV1]); break;
-    case kS22: part[kV2] = fma(g1, a, part[kV2]); break;
-    case kS33: part[kV3] = fma(g2, a, part[kV3]); break;
-    case kS12:
-      part[kV1] = fma(g1, a, part[kV1]);
-      part[kV2] = fma(g0, a, part[kV2]);
-      break;
-    case kS13:
-      part[kV1] = fma(g2, a, part[kV1]);
-      part[kV3] = fma(g0, a, part[kV3]);
-      break;
-    default:  // kS23
-      part[kV2] = fma(g2, a, part[kV2]);
-      part[kV3] = fma(g1, a, part[kV3]);
-      break;
-  }
-}
 
 // One element per CTA of NT threads; thread t owns nodes t, t + NT, ...
 // (NODES of them). LEAN keeps only the partial sums in registers: the running

@@ -15,7 +15,11 @@
 // (and its face projections) to the outputs: in the Taylor bookkeeping of the
 // FP64 kernels, r_0 = 0 and
 //   r_{k+1} = dt/(k+2) L r_k + dt^(k+1)/(k+2)! s^(k),   avg += sum_k r_k.
-#include "ck_fp64.cuh"
+// On curvilinear elements (metric given) L is the curvilinear operator and the
+// node volume of the mass matrix is w_node |det J_node| = w_node / |det G_node|:
+// the host passes phi_node(pos) / w_node and the kernel multiplies by
+// |det G_node|.
+#include "ck_curv.cuh"
 #include "stp_internal.h"
 
 namespace stp {
@@ -23,13 +27,13 @@ namespace {
 
 constexpr int kSourceThreads = 512;
 
-template <int N>
+template <int N, bool CURV>
 __global__ void __launch_bounds__(kSourceThreads, 1)
 source_kernel(const SourceGroup* __restrict__ groups, const double* __restrict__ proj,
               const double* __restrict__ amp, const double* __restrict__ cf,
               const double* __restrict__ tables, const double* __restrict__ params,
-              double* __restrict__ out_avg, double* __restrict__ out_faces,
-              double* __restrict__ scratch) {
+              const double* __restrict__ metric, double dx, double* __restrict__ out_avg,
+              double* __restrict__ out_faces, double* __restrict__ scratch) {
   constexpr int N3 = N * N * N, S = N3 | 1, LDD = N | 1, M = kQuantities;
   constexpr int NODES = (N3 + kSourceThreads - 1) / kSourceThreads;
   extern __shared__ double smem[];
@@ -48,13 +52,19 @@ source_kernel(const SourceGroup* __restrict__ groups, const double* __restrict__
   for (int i = tid; i < M * N3; i += kSourceThreads) avg_src[i] = 0.0;
   double c[NODES][4];
   const double* pe = params + g.element * (int64_t)(kParams * N3);
+  const double* ge = CURV ? metric + g.element * (int64_t)(9 * N3) : nullptr;
 #pragma unroll
   for (int j = 0; j < NODES; ++j) {
     const int n = tid + j * kSourceThreads;
     c[j][0] = c[j][1] = c[j][2] = c[j][3] = 0.0;
-    if (n < N3)
+    if (n < N3) {
       elastic_coefficients(pe[3 * n], pe[3 * n + 1], pe[3 * n + 2], &c[j][0], &c[j][1], &c[j][2],
                            &c[j][3]);
+      if (CURV) {  // the step tables hold D dt/((k+2) dx)
+#pragma unroll
+        for (int i = 0; i < 4; ++i) c[j][i] *= dx;
+      }
+    }
   }
   __syncthreads();
 
@@ -64,16 +74,28 @@ source_kernel(const SourceGroup* __restrict__ groups, const double* __restrict__
     for (int j = 0; j < NODES; ++j) {
       const int n = tid + j * kSourceThreads;
       if (n >= N3) continue;
+      double gn[9];  // the node's metric (curvilinear)
+      double vol_inv = 1.0;  // |det G_node| (curvilinear), else folded into proj
+      if (CURV) {
+#pragma unroll
+        for (int i = 0; i < 9; ++i) gn[i] = __ldg(ge + 9 * n + i);
+        vol_inv = fabs(gn[0] * (gn[4] * gn[8] - gn[5] * gn[7]) - gn[1] * (gn[3] * gn[8] - gn[5] * gn[6]) +
+                       gn[2] * (gn[3] * gn[7] - gn[4] * gn[6]));
+      }
       if (k == 0) {
 #pragma unroll
         for (int s = 0; s < M; ++s) r[j][s] = 0.0;  // r_0 = 0
       } else {
         const int x = n % N, y = (n / N) % N, z = n / (N * N);
-        ck_node_fp64<N, S, LDD>(sp, sD + k * N * LDD, x, y, z, c[j][0], c[j][1], c[j][2], c[j][3],
-                                r[j]);
+        if (CURV)
+          ck_node_curv_fp64<N, S, LDD>(sp, sD + k * N * LDD, x, y, z, gn, c[j][0], c[j][1], c[j][2],
+                                       c[j][3], r[j]);
+        else
+          ck_node_fp64<N, S, LDD>(sp, sD + k * N * LDD, x, y, z, c[j][0], c[j][1], c[j][2],
+                                  c[j][3], r[j]);
       }
       for (int i = g.first; i < g.first + g.count; ++i) {
-        const double w = proj[(size_t)i * N3 + n] * cf[(size_t)i * N + k];
+        const double w = proj[(size_t)i * N3 + n] * vol_inv * cf[(size_t)i * N + k];
 #pragma unroll
         for (int s = 0; s < M; ++s) r[j][s] = fma(w, amp[(size_t)i * M + s], r[j][s]);
       }
@@ -117,19 +139,20 @@ source_kernel(const SourceGroup* __restrict__ groups, const double* __restrict__
   }
 }
 
-template <int N>
+template <int N, bool CURV>
 cudaError_t launch_sources_n(int ngroups, const SourceGroup* groups, const double* proj,
                              const double* amp, const double* cf, const double* tables,
-                             const double* params, double* out_avg, double* out_faces,
-                             double* scratch, cudaStream_t stream) {
+                             const double* params, const double* metric, double dx,
+                             double* out_avg, double* out_faces, double* scratch,
+                             cudaStream_t stream) {
   constexpr int N3 = N * N * N;
   constexpr size_t smem = sizeof(double) * (size_t)(N * N * (N | 1) + 2 * N + kQuantities * (N3 | 1));
   static_assert(smem <= 232448, "shared memory budget of one CTA exceeded");
-  auto kern = source_kernel<N>;
+  auto kern = source_kernel<N, CURV>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   kern<<<(unsigned)ngroups, kSourceThreads, smem, stream>>>(groups, proj, amp, cf, tables, params,
-                                                           out_avg, out_faces, scratch);
+                                                           metric, dx, out_avg, out_faces, scratch);
   return cudaGetLastError();
 }
 
@@ -137,14 +160,17 @@ cudaError_t launch_sources_n(int ngroups, const SourceGroup* groups, const doubl
 
 cudaError_t launch_sources(int N, int ngroups, const SourceGroup* groups, const double* proj,
                            const double* amp, const double* cf, const double* tables,
-                           const double* params, double* out_avg, double* out_faces,
-                           double* scratch, cudaStream_t stream) {
+                           const double* params, const double* metric, double dx,
+                           double* out_avg, double* out_faces, double* scratch,
+                           cudaStream_t stream) {
   if (ngroups <= 0) return cudaSuccess;
   switch (N) {
 #define X(n)                                                                                     \
   case n:                                                                                        \
-    return launch_sources_n<n>(ngroups, groups, proj, amp, cf, tables, params, out_avg,          \
-                               out_faces, scratch, stream);
+    return metric ? launch_sources_n<n, true>(ngroups, groups, proj, amp, cf, tables, params,    \
+                                              metric, dx, out_avg, out_faces, scratch, stream)   \
+                  : launch_sources_n<n, false>(ngroups, groups, proj, amp, cf, tables, params,   \
+                                               nullptr, dx, out_avg, out_faces, scratch, stream);
     X(1) X(2) X(3) X(4) X(5) X(6) X(7) X(8) X(9) X(10) X(11) X(12)
 #undef X
     default: return cudaErrorInvalidValue;

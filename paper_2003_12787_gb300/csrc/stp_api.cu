@@ -326,12 +326,17 @@ void lagrange_at(const stp::HostTables& t, long double a, long double* phi) {
 
 }  // namespace
 
-stp_status stp_predict_sources(stp_handle h, int64_t elements, const double* q, const double* params,
-                               double* out_avg, double* out_faces, int nsources,
-                               const stp_point_source* sources, void* stream) {
+namespace {
+
+// Point sources after the STP of the set (Cartesian when metric is NULL).
+stp_status predict_sources_impl(stp_handle h, int64_t elements, const double* q,
+                                const double* params, const double* metric, double* out_avg,
+                                double* out_faces, int nsources, const stp_point_source* sources,
+                                void* stream) {
   if (nsources < 0 || (nsources > 0 && !sources))
     return fail(STP_ERR_INVALID_ARG, "bad source list");
-  stp_status s = validate_common(h, elements, q, params, out_avg, out_faces);
+  stp_status s = metric ? validate_curvilinear(h, elements, q, params, metric, out_avg, out_faces)
+                        : validate_common(h, elements, q, params, out_avg, out_faces);
   if (s != STP_OK) return s;
   for (int i = 0; i < nsources; ++i) {
     const stp_point_source& src = sources[i];
@@ -347,18 +352,21 @@ stp_status stp_predict_sources(stp_handle h, int64_t elements, const double* q, 
       if (!std::isfinite(src.derivatives[k]))
         return fail(STP_ERR_INVALID_ARG, "source " + std::to_string(i) + ": non-finite derivative");
   }
-  if ((s = stp_predict(h, elements, q, params, out_avg, out_faces, stream)) != STP_OK) return s;
+  s = metric ? stp_predict_curvilinear(h, elements, q, params, metric, out_avg, out_faces, stream)
+             : stp_predict(h, elements, q, params, out_avg, out_faces, stream);
+  if (s != STP_OK) return s;
   if (nsources == 0 || elements == 0) return STP_OK;
   const int N = h->N, N3 = N * N * N;
   // group the sources by element; per source: the nodal projection
-  // phi_node(pos) / (w_node dx^3), the amplitude and dt^(k+1)/(k+2)! f^(k)
+  // phi_node(pos) / (w_node dx^3) (curvilinear: phi_node(pos) / w_node, the
+  // kernel supplies the node volume), the amplitude and dt^(k+1)/(k+2)! f^(k)
   std::vector<int> order(nsources);
   for (int i = 0; i < nsources; ++i) order[i] = i;
   std::stable_sort(order.begin(), order.end(),
                    [&](int a, int b) { return sources[a].element < sources[b].element; });
   std::vector<stp::SourceGroup> groups;
   std::vector<double> proj((size_t)nsources * N3), amp((size_t)nsources * 9), cf((size_t)nsources * N);
-  const long double h3 = (long double)h->dx * h->dx * h->dx;
+  const long double h3 = metric ? 1.0L : (long double)h->dx * h->dx * h->dx;
   for (int r = 0; r < nsources; ++r) {
     const stp_point_source& src = sources[order[r]];
     if (groups.empty() || groups.back().element != src.element)
@@ -402,12 +410,30 @@ stp_status stp_predict_sources(stp_handle h, int64_t elements, const double* q, 
       (e = cudaMemcpyAsync(d_cf, cf.data(), b_cf, cudaMemcpyHostToDevice, st)) == cudaSuccess)
     e = stp::launch_sources(N, G, reinterpret_cast<const stp::SourceGroup*>(d_groups),
                             reinterpret_cast<const double*>(d_proj), reinterpret_cast<const double*>(d_amp),
-                            reinterpret_cast<const double*>(d_cf), h->d_tables, params, out_avg,
-                            out_faces, reinterpret_cast<double*>(d_scr), st);
+                            reinterpret_cast<const double*>(d_cf), h->d_tables, params, metric, h->dx,
+                            out_avg, out_faces, reinterpret_cast<double*>(d_scr), st);
   const cudaError_t fe = cudaFreeAsync(d, st);
   if (e == cudaSuccess) e = fe;
   if (e != cudaSuccess) return cuda_fail(e, "point-source launch");
   return STP_OK;
+}
+
+}  // namespace
+
+stp_status stp_predict_sources(stp_handle h, int64_t elements, const double* q, const double* params,
+                               double* out_avg, double* out_faces, int nsources,
+                               const stp_point_source* sources, void* stream) {
+  return predict_sources_impl(h, elements, q, params, nullptr, out_avg, out_faces, nsources, sources,
+                              stream);
+}
+
+stp_status stp_predict_sources_curvilinear(stp_handle h, int64_t elements, const double* q,
+                                           const double* params, const double* metric,
+                                           double* out_avg, double* out_faces, int nsources,
+                                           const stp_point_source* sources, void* stream) {
+  if (!metric && elements > 0) return fail(STP_ERR_INVALID_ARG, "null metric");
+  return predict_sources_impl(h, elements, q, params, metric, out_avg, out_faces, nsources, sources,
+                              stream);
 }
 
 namespace {

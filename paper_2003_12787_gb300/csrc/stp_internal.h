@@ -88,10 +88,13 @@ struct SourceGroup {
   int64_t element;
   int first, count;
 };
+// metric (may be NULL): curvilinear elements; proj then omits the node
+// volume, which the kernel takes from |det G| (dx rescales the coefficients).
 cudaError_t launch_sources(int N, int ngroups, const SourceGroup* groups, const double* proj,
                            const double* amp, const double* cf, const double* tables,
-                           const double* params, double* out_avg, double* out_faces,
-                           double* scratch, cudaStream_t stream);
+                           const double* params, const double* metric, double dx,
+                           double* out_avg, double* out_faces, double* scratch,
+                           cudaStream_t stream);
 
 // Batched persistent FP64 launch (batch.cu).
 struct BatchPlan;

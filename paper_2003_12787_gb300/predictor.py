@@ -76,11 +76,12 @@ class Predictor:
         if stream is None and q.is_cuda:
             stream = torch.cuda.current_stream(q.device)
         if metric is not None:
-            N = self.N
-            if sources:
-                raise ValueError("point sources are not supported on curvilinear elements")
             self._check_metric(q, metric)
-            B.stp_predict_curvilinear(self.handle, E, q, params, metric, avg, faces, stream)
+            if sources:
+                B.stp_predict_sources_curvilinear(self.handle, E, q, params, metric, avg, faces,
+                                                  sources, stream)
+            else:
+                B.stp_predict_curvilinear(self.handle, E, q, params, metric, avg, faces, stream)
         elif sources:
             B.stp_predict_sources(self.handle, E, q, params, avg, faces, sources, stream)
         else:

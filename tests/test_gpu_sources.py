@@ -16,7 +16,7 @@ import torch
 import oracle
 import paper_2003_12787_gb300 as stp
 from paper_2003_12787_gb300 import _binding
-from paper_2003_12787_gb300.inputs import elastic_problem
+from paper_2003_12787_gb300.inputs import curvilinear_problem, elastic_problem
 
 pytestmark = pytest.mark.gpu
 
@@ -99,6 +99,49 @@ def test_source_on_a_gauss_lobatto_corner_node():
     a_ref, f_ref = oracle.stp(prob.q.numpy(), prob.params.numpy(), prob.h, prob.dt, nodes="gll",
                               sources=src)
     assert rel(avg, a_ref) <= 1e-12 and rel(faces, f_ref) <= 1e-12
+
+
+def run_curv(prob, sources, precision="fp64", nodes="gl"):
+    with stp.Predictor(prob.N - 1, prob.h, prob.dt, precision=precision, nodes=nodes) as P:
+        q, params, m = prob.q.cuda(), prob.params.cuda(), prob.metric.cuda()
+        a_s, f_s = P.predict(q, params, sources=sources, metric=m)
+        a_0, f_0 = P.predict(q, params, metric=m)
+        torch.cuda.synchronize()
+    return a_s.cpu().numpy(), f_s.cpu().numpy(), a_0.cpu().numpy(), f_0.cpu().numpy()
+
+
+@pytest.mark.parametrize("N,nodes", [(1, "gl"), (2, "gl"), (5, "gl"), (8, "gl"), (12, "gl"),
+                                     (6, "gll")])
+def test_sources_on_curvilinear_elements(N, nodes):
+    """A point source in a curvilinear mesh (the node volume of the mass
+    matrix is w |det J|, taken from the metric on the device)."""
+    rng = np.random.default_rng(3300 + N)
+    prob = curvilinear_problem(N, grid=(32, 32, 16), h=1.0 / 32, E=5, seed_material=3400 + N,
+                               seed_waves=3500 + N, nodes=nodes)
+    src = make_sources(N, prob.E, rng)
+    avg, faces, avg0, faces0 = run_curv(prob, src, nodes=nodes)
+    a_ref, f_ref = oracle.stp_curvilinear(prob.q.numpy(), prob.params.numpy(), prob.metric.numpy(),
+                                          prob.dt, nodes=nodes, sources=src)
+    assert rel(avg, a_ref) <= 1e-12
+    for f in range(6):
+        assert rel(faces[:, f], f_ref[:, f]) <= 1e-12
+    assert rel(avg[1], avg0[1]) > 1e-8
+    for e in (0, 2, 3):
+        assert np.array_equal(avg[e], avg0[e]) and np.array_equal(faces[e], faces0[e])
+
+
+@pytest.mark.parametrize("precision,tol", [("ff", 1e-12), ("fp32", 2e-9)])
+def test_sources_on_curvilinear_elements_other_precisions(precision, tol):
+    N = 7
+    rng = np.random.default_rng(78)
+    prob = curvilinear_problem(N, grid=(32, 32, 16), h=1.0 / 32, E=6, seed_material=3600,
+                               seed_waves=3601)
+    src = make_sources(N, prob.E, rng)
+    avg, faces, _, _ = run_curv(prob, src, precision=precision)
+    a_ref, f_ref = oracle.stp_curvilinear(prob.q.numpy(), prob.params.numpy(), prob.metric.numpy(),
+                                          prob.dt, sources=src)
+    errs = [rel(avg, a_ref)] + [rel(faces[:, f], f_ref[:, f]) for f in range(6)]
+    assert max(errs) <= tol, errs
 
 
 def test_source_argument_errors():
