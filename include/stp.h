@@ -15,7 +15,11 @@
  * written q_t + sum_d B_d(x) dq/dx_d = 0, so that one CK step is
  *     q^(k+1) = - sum_d B_d(x) (D_d q^(k)) / dx
  * with D the N x N Lagrange derivative matrix on N Gauss-Legendre nodes per
- * dimension (Sec. II-A) applied along dimension d.
+ * dimension (Sec. II-A) applied along dimension d. Gauss-Lobatto nodes are
+ * available through stp_create_nodes; curvilinear elements (Sec. VI: 9 more
+ * geometry parameters per node) through stp_predict_curvilinear and its
+ * companions, with D along the reference directions and the chain rule
+ * through the per-node inverse Jacobian.
  *
  * Outputs per element:
  *     avg  = sum_{k=0..N} dt^k/(k+1)! q^(k)          (time average over [t_n, t_n+dt])
