@@ -532,6 +532,14 @@ def served_measurement(stp, torch, args):
         # service time rather than queueing (arrivals seed 1007)
         out["below_capacity"] = timed_trace(0.7 * main["throughput_req_s"], 0,
                                             args.served_sub_requests, 1007)
+    if not args.no_served_ff:
+        # the same trace with every simulation's handle switched to float-float
+        # (FP64-class results, one launch per simulation instead of the
+        # persistent FP64 batch)
+        for P in preds:
+            stp.stp_set_precision(P.handle, "ff")
+        out["float_float"] = timed_trace(args.served_rate, args.served_warmup,
+                                         args.served_requests, 1006)
     srv.close()
     for P in preds:
         P.close()
@@ -778,6 +786,8 @@ def main():
     ap.add_argument("--batched-emax", type=int, default=16384,
                     help="largest set of the batched workload (smaller for profiler captures)")
     ap.add_argument("--no-served", action="store_true", help="skip the served workload")
+    ap.add_argument("--no-served-ff", action="store_true",
+                    help="skip the float-float run of the served trace")
     ap.add_argument("--no-curvilinear", action="store_true",
                     help="skip the curvilinear order-7 measurement")
     ap.add_argument("--geometry", choices=["cartesian", "curvilinear"], default="cartesian",

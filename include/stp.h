@@ -256,7 +256,7 @@ stp_status stp_device_status(stp_handle h, void* stream, unsigned int* flags);
  * other precisions replay a graph of per-set launches instead.
  */
 typedef struct {
-  stp_handle handle;   /* predictor of this set (FP64 for the static and served paths) */
+  stp_handle handle;   /* predictor of this set (FP64 for the allocation-free path) */
   int64_t elements;    /* E >= 0 */
   const double* q;     /* device [E][N][N][N][9] */
   const double* params;/* device [E][N][N][N][3] */
@@ -365,9 +365,11 @@ stp_status stp_batch_run_static(int nsets, const stp_batch_set* sets, void* stre
  * Its scheduler retires finished batches, admits ready simulations into the
  * pool (first fit; when full, idle simulations are evicted least recently
  * used first and their state copied back to pinned host memory), and launches
- * up to 128 ready resident simulations as one persistent batched FP64 launch
- * per free slot, so requests that arrive while others run join the next
- * launch and launches on different slots overlap on the GPU. The scheduler
+ * up to 128 ready resident simulations per free slot: the FP64 ones as one
+ * persistent batched launch, the others (curvilinear, or another precision)
+ * each with its own kernel on the same stream; requests that arrive while
+ * others run join the next launch and launches on different slots overlap on
+ * the GPU. The scheduler
  * runs on the calling thread (stp_server_progress / _drain / _run_trace);
  * a server is not thread-safe.
  */
@@ -375,20 +377,25 @@ typedef struct stp_server_s* stp_server;
 
 stp_status stp_server_create(int64_t hbm_budget_bytes, int slots, stp_server* out);
 
-/* Register a simulation: the FP64 handle gives its order, dx and dt; q0 and
- * params ([E][N][N][N][9], [E][N][N][N][3], both host or both device) are
- * copied into server-owned pinned host memory. *sim_id = 0, 1, ... in order.
- * STP_ERR_INVALID_ARG if its footprint (2 states + params + faces) exceeds the
- * budget. The handle must outlive the server. */
+/* Register a simulation: the handle gives its order, dx, dt and precision;
+ * q0 and params ([E][N][N][N][9], [E][N][N][N][3], both host or both device)
+ * are copied into server-owned pinned host memory. *sim_id = 0, 1, ... in
+ * order. FP64 simulations share the persistent batched launch; a simulation
+ * whose handle runs another precision (read at each launch) gets a launch of
+ * its own with the handle's kernel, on the same slot stream. STP_ERR_INVALID_ARG
+ * if its footprint (2 states + params + faces) exceeds the budget. The handle
+ * must outlive the server. */
 stp_status stp_server_add_sim(stp_server s, stp_handle h, int64_t elements, const double* q0,
                               const double* params, int* sim_id);
 
 /* A curvilinear simulation: as stp_server_add_sim, plus its per-node inverse
  * Jacobians (layout of stp_predict_curvilinear; host or device like q0),
  * which stay resident beside the material while the simulation is admitted
- * (its footprint grows by 9N^3 doubles per element). Its steps run in FP64
- * as stp_predict_curvilinear, in a launch of their own on the slot's stream.
- * STP_ERR_INVALID_ARG for a NULL metric, otherwise as stp_server_add_sim. */
+ * (its footprint grows by 9N^3 doubles per element). Its steps run as
+ * stp_predict_curvilinear (the handle's precision: FP64, float-float or
+ * FP32), in a launch of their own on the slot's stream. STP_ERR_INVALID_ARG
+ * for a NULL metric, STP_ERR_UNSUPPORTED for a tensor-core precision,
+ * otherwise as stp_server_add_sim. */
 stp_status stp_server_add_sim_curvilinear(stp_server s, stp_handle h, int64_t elements,
                                           const double* q0, const double* params,
                                           const double* metric, int* sim_id);

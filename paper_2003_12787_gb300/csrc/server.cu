@@ -24,8 +24,9 @@
 //   3. launches up to 128 ready, resident simulations as ONE persistent
 //      batched FP64 launch on a free slot (its own stream and scratch);
 //      curvilinear simulations (their per-node inverse Jacobians resident
-//      beside the material) get their own FP64 curvilinear launch on the
-//      same stream, between the same timing events.
+//      beside the material) and simulations whose handle runs another
+//      precision get a launch of their own (the handle's kernel) on the same
+//      stream, between the same timing events.
 // New requests therefore join the next launch while earlier launches are
 // still on the GPU, and launches on different slots overlap on the device.
 #include <algorithm>
@@ -293,7 +294,7 @@ struct Server {
         if ((e = cudaStreamWaitEvent(sl.stream, copy_done, 0)) != cudaSuccess) return e;
       }
       const int n = (int)batch.size();
-      std::vector<int> N, curv;
+      std::vector<int> N, curv;  // curv: simulations launched one by one
       std::vector<int64_t> E;
       std::vector<const double*> q, p, tb;
       std::vector<double*> a, f;
@@ -301,7 +302,7 @@ struct Server {
         Sim& s = sims[batch[k]];
         s.busy = true;
         s.queued = false;
-        if (s.bytes_metric) {  // curvilinear: a launch of its own
+        if (s.bytes_metric || !stp_handle_is_fp64(s.handle)) {  // a launch of its own
           curv.push_back(batch[k]);
           continue;
         }
@@ -323,9 +324,9 @@ struct Server {
       }
       for (int i : curv) {
         Sim& s = sims[i];
-        e = launch_curvilinear(s.N, s.E, state(s, s.cur), params(s), metric(s), state(s, s.cur ^ 1),
-                               faces(s), stp_handle_tables(s.handle), stp_handle_dx(s.handle),
-                               sl.stream);
+        e = stp_launch_handle(s.handle, s.E, state(s, s.cur), params(s),
+                              s.bytes_metric ? metric(s) : nullptr, state(s, s.cur ^ 1), faces(s),
+                              sl.stream);
         if (e != cudaSuccess) return e;
       }
       if ((e = cudaEventRecord(sl.done, sl.stream)) != cudaSuccess) return e;

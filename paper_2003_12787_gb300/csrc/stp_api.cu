@@ -571,6 +571,12 @@ stp_status stp_device_status(stp_handle h, void* stream, unsigned int* flags) {
 namespace stp {
 const double* stp_handle_tables(stp_handle h) { return h->d_tables; }
 double stp_handle_dx(stp_handle h) { return h->dx; }
+bool stp_handle_is_fp64(stp_handle h) { return h->precision == STP_PRECISION_FP64 || h->N < 2; }
+cudaError_t stp_launch_handle(stp_handle h, int64_t E, const double* q, const double* params,
+                              const double* metric, double* avg, double* faces, cudaStream_t st) {
+  return metric ? launch_curvilinear_configured(h, E, q, params, metric, avg, faces, st)
+                : launch_configured(h, E, q, params, avg, faces, st);
+}
 }  // namespace stp
 
 struct stp_server_s {
@@ -902,7 +908,9 @@ stp_status server_add_sim_impl(stp_server s, stp_handle h, int64_t elements, con
                                const double* params, const double* metric, int* sim_id) {
   if (!s || !s->impl || !h || !sim_id) return fail(STP_ERR_INVALID_ARG, "null argument");
   if (elements <= 0 || !q0 || !params) return fail(STP_ERR_INVALID_ARG, "bad simulation buffers");
-  if (h->precision != STP_PRECISION_FP64) return fail(STP_ERR_UNSUPPORTED, "served steps are FP64");
+  if (metric && h->N >= 2 && h->precision != STP_PRECISION_FP64 &&
+      h->precision != STP_PRECISION_FF && h->precision != STP_PRECISION_FP32)
+    return fail(STP_ERR_UNSUPPORTED, "curvilinear elements run in FP64, float-float or FP32 only");
   const bool dq = is_device_memory(q0), dp = is_device_memory(params);
   if (dq != dp || (metric && is_device_memory(metric) != dq))
     return fail(STP_ERR_INVALID_ARG, "q0, params (and metric) must be all host or all device");

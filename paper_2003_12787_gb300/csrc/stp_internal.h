@@ -136,6 +136,12 @@ int static_max_sets();
 // Device tables of a handle (stp_api.cu).
 const double* stp_handle_tables(stp_handle h);
 double stp_handle_dx(stp_handle h);
+// Whether the handle's steps are the FP64 ones (its precision, or N = 1).
+bool stp_handle_is_fp64(stp_handle h);
+// One launch of the handle's configured kernel (its precision; curvilinear
+// when metric is not NULL) on stream st.
+cudaError_t stp_launch_handle(stp_handle h, int64_t E, const double* q, const double* params,
+                              const double* metric, double* avg, double* faces, cudaStream_t st);
 
 // Served predictor (server.cu); see include/stp.h for the behaviour.
 struct Server;

@@ -238,6 +238,39 @@ def test_curvilinear_simulations_in_the_served_loop():
         P.close()
 
 
+def test_other_precisions_in_the_served_loop():
+    """Float-float and FP32 simulations (Cartesian and curvilinear) beside
+    FP64 ones in the served loop, with evictions: each equals repeated
+    single-set calls in its handle's precision, bit for bit."""
+    specs = [(6, 30, "ff", False), (8, 9, "fp64", False), (7, 12, "fp32", True),
+             (5, 40, "ff", True), (4, 50, "fp32", False)]
+    sims = []
+    for i, (N, E, prec, curv) in enumerate(specs):
+        make = curvilinear_problem if curv else elastic_problem
+        prob = make(N, E=E, seed_material=3700 + i, seed_waves=3800 + i)
+        sims.append((stp.Predictor(N - 1, prob.h, prob.dt, precision=prec), prob))
+    foot = max(8 * E * ((30 if c else 21) * N ** 3 + 54 * N ** 2) for N, E, _, c in specs)
+    srv = stp.Server(2 * foot + (1 << 20), slots=2)
+    ids = [srv.add_sim(P, prob.q, prob.params, metric=prob.metric) for P, prob in sims]
+    steps = 3
+    order = np.tile(np.arange(len(sims)), steps)
+    srv.run_trace(np.linspace(0.0, 0.01, len(order)), np.asarray(ids, dtype=np.int32)[order])
+    assert srv.stats()["evictions"] > 0
+    for i, (P, prob) in enumerate(sims):
+        q_mix, f_mix, n = srv.read(ids[i])
+        assert n == steps
+        q = prob.q.cuda()
+        m = prob.metric.cuda() if prob.metric is not None else None
+        for _ in range(steps):
+            avg, faces = P.predict(q, prob.params.cuda(), metric=m)
+            q = avg
+        torch.cuda.synchronize()
+        assert torch.equal(q.cpu(), q_mix) and torch.equal(faces.cpu(), f_mix), specs[i]
+    srv.close()
+    for P, _ in sims:
+        P.close()
+
+
 def test_argument_errors():
     N = 4
     prob = curvilinear_problem(N, E=8, device="cuda")
