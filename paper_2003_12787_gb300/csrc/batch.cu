@@ -28,21 +28,20 @@ constexpr int kBatchThreads = 512;
 
 // Candidate shapes per N: (N, index, nodes per thread, elements per CTA,
 // average in smem, new term parked in global scratch instead of registers).
-// Orders 8..11 use the even-odd body instead (STP_BATCH_EO below): every FP64
+// Orders 7..11 use the even-odd body instead (STP_BATCH_EO below): every FP64
 // path uses the same arithmetic per order, so results agree bit for bit.
 #define STP_BATCH_SHAPES(X)                                                                        \
   X(1, 0, 1, 256, true, false) X(2, 0, 1, 64, true, false) X(2, 1, 2, 128, true, false)           \
   X(3, 0, 1, 18, true, false) X(3, 1, 2, 36, true, false) X(4, 0, 1, 8, true, false)              \
   X(4, 1, 2, 16, true, false) X(5, 0, 1, 4, true, false) X(5, 1, 2, 8, true, false)               \
-  X(6, 0, 1, 2, true, false) X(6, 1, 2, 4, true, false) X(7, 0, 1, 1, true, false)                \
-  X(7, 1, 2, 2, true, false)
+  X(6, 0, 1, 2, true, false) X(6, 1, 2, 4, true, false)
 
 constexpr int kMaxVariants = 2;
 
 // Even-odd candidates: (N, index, threads doing the work); N = 12 uses the
 // slot-reusing variant (p and accumulators share 16 arrays).
-#define STP_BATCH_EO(X) X(8, 0, 384) X(8, 1, 512) X(9, 0, 486) X(9, 1, 512) \
-  X(10, 0, 500) X(10, 1, 512) X(11, 0, 444) X(11, 1, 512)
+#define STP_BATCH_EO(X) X(7, 0, 343) X(7, 1, 512) X(8, 0, 384) X(8, 1, 512) X(9, 0, 486) \
+  X(9, 1, 512) X(10, 0, 500) X(10, 1, 512) X(11, 0, 444) X(11, 1, 512)
 #define STP_BATCH_EO_SLOTS(X) X(12, 0, 432) X(12, 1, 512)
 
 struct ShapeInfo {

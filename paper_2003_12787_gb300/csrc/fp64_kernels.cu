@@ -117,8 +117,8 @@ cudaError_t launch_shape(int64_t E, const double* q, const double* params, doubl
 // Orders that use the even-odd kernel: (N, threads, working threads, CTAs/SM).
 // The batched, allocation-free and served paths use the even-odd body for the
 // same orders, so every FP64 path rounds alike.
-#define STP_FP64_EO_SHAPES(X) X(8, 192, 192, 2) X(9, 256, 243, 1) X(10, 320, 300, 1) \
-  X(11, 384, 363, 1)
+#define STP_FP64_EO_SHAPES(X) X(7, 352, 343, 2) X(8, 192, 192, 2) X(9, 256, 243, 1) \
+  X(10, 320, 300, 1) X(11, 384, 363, 1)
 
 int fp64_elements_per_cta(int N) {
   switch (N) {

@@ -39,13 +39,13 @@ static __device__ __align__(256) unsigned char g_static_scratch[kStaticScratchBy
 // CTA, average in smem, new terms parked in scratch).
 #define STP_STATIC_SHAPES(X)                                                                      \
   X(1, 1, 256, true, false) X(2, 1, 64, true, false) X(3, 1, 18, true, false)                    \
-  X(4, 1, 8, true, false) X(5, 1, 4, true, false) X(6, 1, 2, true, false) X(7, 1, 1, true, false) \
+  X(4, 1, 8, true, false) X(5, 1, 4, true, false) X(6, 1, 2, true, false)                       \
   X(12, 4, 1, false, true)
-// Orders 8..11: the even-odd body (N, threads doing the work), as on every other
+// Orders 7..11: the even-odd body (N, threads doing the work), as on every other
 // FP64 path. N = 12 keeps the per-node body here, which parks its new terms in
 // the scratch array; at N = 12 this path (and the served one, which launches
 // this kernel) therefore agrees with stp_predict to rounding, not bit for bit.
-#define STP_STATIC_EO(X) X(8, 384) X(9, 486) X(10, 500) X(11, 444)
+#define STP_STATIC_EO(X) X(7, 343) X(8, 384) X(9, 486) X(10, 500) X(11, 444)
 
 struct StaticSet {
   const double* q;
