@@ -271,6 +271,23 @@ def test_other_precisions_in_the_served_loop():
         P.close()
 
 
+@pytest.mark.parametrize("precision", ["fp64", "ff", "fp32"])
+def test_constant_state_is_steady_on_curvilinear_elements(precision):
+    """A state constant in each element has zero derivatives along every
+    reference direction, whatever the metric: avg = q and every face = q, up
+    to the rounding of D's row sums (which are zero in exact arithmetic)."""
+    N = 6
+    prob = curvilinear_problem(N, grid=(8, 8, 4), E=20, seed_material=3900, seed_waves=3901)
+    rng = np.random.default_rng(3902)
+    const = torch.from_numpy(rng.uniform(-1, 1, (prob.E, 1, 1, 1, 9)))
+    prob.q = const.expand(prob.E, N, N, N, 9).contiguous()
+    avg, faces = run(prob, precision=precision)
+    q = prob.q.numpy()
+    assert np.abs(avg - q).max() <= 1e-12 * np.abs(q).max()
+    for f in range(6):
+        assert np.abs(faces[:, f] - q[:, 0]).max() <= 1e-12 * np.abs(q).max()
+
+
 def test_argument_errors():
     N = 4
     prob = curvilinear_problem(N, E=8, device="cuda")
