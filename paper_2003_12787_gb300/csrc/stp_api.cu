@@ -301,6 +301,8 @@ stp_status stp_predict_curvilinear(stp_handle h, int64_t elements, const double*
   return STP_OK;
 }
 
+}  // extern "C"
+
 namespace {
 
 // phi_j(a) for the handle's nodes (barycentric form, long double; a unit
@@ -420,6 +422,8 @@ stp_status predict_sources_impl(stp_handle h, int64_t elements, const double* q,
 
 }  // namespace
 
+extern "C" {
+
 stp_status stp_predict_sources(stp_handle h, int64_t elements, const double* q, const double* params,
                                double* out_avg, double* out_faces, int nsources,
                                const stp_point_source* sources, void* stream) {
@@ -435,6 +439,8 @@ stp_status stp_predict_sources_curvilinear(stp_handle h, int64_t elements, const
   return predict_sources_impl(h, elements, q, params, metric, out_avg, out_faces, nsources, sources,
                               stream);
 }
+
+}  // extern "C"
 
 namespace {
 
@@ -525,6 +531,8 @@ stp_status predict_host_impl(stp_handle h, int64_t elements, const double* q, co
 }
 
 }  // namespace
+
+extern "C" {
 
 stp_status stp_predict_host(stp_handle h, int64_t elements, const double* q, const double* params,
                             double* out_avg, double* out_faces, void* stream) {
@@ -893,6 +901,8 @@ stp_status stp_server_create(int64_t hbm_budget_bytes, int slots, stp_server* ou
   return STP_OK;
 }
 
+}  // extern "C"
+
 namespace {
 
 bool is_device_memory(const void* p) {
@@ -924,6 +934,8 @@ stp_status server_add_sim_impl(stp_server s, stp_handle h, int64_t elements, con
 }
 
 }  // namespace
+
+extern "C" {
 
 stp_status stp_server_add_sim(stp_server s, stp_handle h, int64_t elements, const double* q0,
                               const double* params, int* sim_id) {
