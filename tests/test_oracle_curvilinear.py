@@ -106,9 +106,9 @@ def _wave(n, pol, rho, cp, cs):
     return _from_tensor(a, sig), c
 
 
-@pytest.mark.parametrize("N", [3, 5, 7])
+@pytest.mark.parametrize("N,nodes", [(3, "gl"), (5, "gl"), (7, "gl"), (4, "gll"), (6, "gll")])
 @pytest.mark.parametrize("pol", ["P", "S"])
-def test_affine_element_plane_wave_exact(N, pol):
+def test_affine_element_plane_wave_exact(N, nodes, pol):
     rho, cp, cs = 2.3, 4.7, 2.1
     h, dt = 0.25, 0.015
     rng = np.random.default_rng(10 * N + (pol == "S"))
@@ -118,7 +118,7 @@ def test_affine_element_plane_wave_exact(N, pol):
     f = np.polynomial.Polynomial(rng.uniform(-1, 1, N))  # degree N-1
     F = f.integ()
     avg_of = lambda s: (F(s) - F(s - c * dt)) / (c * dt)
-    xi, _ = ref.gl_points(N)
+    xi, _ = ref.points(N, nodes)
     # affine elements x = x0 + Jm xi with general (non-symmetric) Jm
     Jms = [h * np.array([[1.0, 0.3, -0.2], [0.1, 0.9, 0.25], [-0.15, 0.2, 1.1]]),
            h * np.array([[0.8, -0.4, 0.1], [0.35, 1.2, 0.0], [0.05, -0.3, 0.7]])]
@@ -149,7 +149,7 @@ def test_affine_element_plane_wave_exact(N, pol):
                 s_face = (x0s[e] + pts @ Jms[e].T) @ n
                 faces_x[e, 2 * d + side] = avg_of(s_face)[..., None] * r
     params = _params(E, N, rng, uniform=(rho, cp, cs))
-    avg, faces = oracle.stp_curvilinear(q, params, G, dt)
+    avg, faces = oracle.stp_curvilinear(q, params, G, dt, nodes=nodes)
     assert ref.rel_err(avg, avg_x) <= 1e-12
     assert ref.rel_err(avg - q, avg_x - q) <= 1e-10
     # the face vectors extrapolate to the boundary (sum |phi_j(0)| grows with
