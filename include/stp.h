@@ -352,6 +352,17 @@ stp_status stp_autotune(stp_handle h, int* variant, double* us_per_element,
  */
 stp_status stp_batch_run_static(int nsets, const stp_batch_set* sets, void* stream);
 
+/* stp_batch_run_static with curvilinear sets: metrics is a HOST array of
+ * nsets device pointers (the inverse Jacobians of set i in the layout of
+ * stp_predict_curvilinear, or NULL for a Cartesian set). The Cartesian sets
+ * run in the persistent launch as above; each curvilinear set is one FP64
+ * curvilinear launch after it on the same stream, with results equal to its
+ * stp_predict_curvilinear. Still no allocating call. STP_ERR_INVALID_ARG for
+ * metrics == NULL with nsets > 0, otherwise as stp_batch_run_static and
+ * stp_predict_curvilinear. */
+stp_status stp_batch_run_static_curvilinear(int nsets, const stp_batch_set* sets,
+                                            const double* const* metrics, void* stream);
+
 /*
  * Served predictor: a continuously batched request loop over many independent
  * simulations (each an element set with its own order, size and material),

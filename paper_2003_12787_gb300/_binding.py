@@ -84,6 +84,8 @@ def load():
                                      ctypes.POINTER(dbl)]
         lib.stp_batch_run_static.argtypes = [ctypes.c_int, vp, vp]
         lib.stp_batch_run_static.restype = ctypes.c_int
+        lib.stp_batch_run_static_curvilinear.argtypes = [ctypes.c_int, vp, vp, vp]
+        lib.stp_batch_run_static_curvilinear.restype = ctypes.c_int
         srv = {"stp_server_create": [i64, ctypes.c_int, ctypes.POINTER(vp)],
                "stp_server_add_sim": [vp, vp, i64, vp, vp, ctypes.POINTER(ctypes.c_int)],
                "stp_server_add_sim_curvilinear": [vp, vp, i64, vp, vp, vp,
@@ -321,13 +323,21 @@ def stp_autotune(h: int):
     return {"variant": v.value, "us_per_element": us.value, "us_variants": list(allv)}
 
 
-def stp_batch_run_static(sets, stream=None) -> None:
-    """The allocation-free batched launch; sets as for stp_batch_create."""
+def stp_batch_run_static(sets, stream=None, metrics=None) -> None:
+    """The allocation-free batched launch; sets as for stp_batch_create;
+    metrics: optional per-set device metric (None for a Cartesian set)."""
     arr = (BatchSet * max(1, len(sets)))()
     for i, (h, E, q, p, a, f) in enumerate(sets):
         arr[i] = BatchSet(h, E, _ptr(q), _ptr(p), _ptr(a), _ptr(f))
-    _check(load().stp_batch_run_static(len(sets), ctypes.cast(arr, ctypes.c_void_p), _stream(stream)),
-           "stp_batch_run_static")
+    if metrics is None:
+        _check(load().stp_batch_run_static(len(sets), ctypes.cast(arr, ctypes.c_void_p),
+                                           _stream(stream)), "stp_batch_run_static")
+    else:
+        mt = (ctypes.c_void_p * max(1, len(sets)))(*[_ptr(m) for m in metrics])
+        _check(load().stp_batch_run_static_curvilinear(len(sets), ctypes.cast(arr, ctypes.c_void_p),
+                                                       ctypes.cast(mt, ctypes.c_void_p),
+                                                       _stream(stream)),
+               "stp_batch_run_static_curvilinear")
 
 
 def stp_server_create(hbm_budget_bytes: int, slots: int = 3) -> int:

@@ -827,7 +827,15 @@ stp_status stp_autotune(stp_handle h, int* variant, double* us_per_element, doub
   return STP_OK;
 }
 
-stp_status stp_batch_run_static(int nsets, const stp_batch_set* sets, void* stream) {
+}  // extern "C"
+
+namespace {
+
+// The allocation-free batched launch; metrics (host array, may be NULL or hold
+// NULLs) marks curvilinear sets, which run as their own FP64 curvilinear
+// launches after the persistent launch of the Cartesian ones.
+stp_status run_static_impl(int nsets, const stp_batch_set* sets, const double* const* metrics,
+                           void* stream) {
   constexpr int kMax = 128;  // the static path's set limit (kernel-parameter descriptors)
   if (nsets < 0 || (nsets > 0 && !sets)) return fail(STP_ERR_INVALID_ARG, "bad set list");
   if (nsets > kMax) return fail(STP_ERR_INVALID_ARG, "more than 128 sets for the static path");
@@ -838,18 +846,23 @@ stp_status stp_batch_run_static(int nsets, const stp_batch_set* sets, void* stre
   const double* q[kMax];
   const double* p[kMax];
   const double* tb[kMax];
+  const double* mt[kMax];
   double* a[kMax];
   double* f[kMax];
   for (int i = 0; i < nsets; ++i) {
     const stp_batch_set& st = sets[i];
-    stp_status s = validate_common(st.handle, st.elements, st.q, st.params, st.out_avg, st.out_faces);
+    const double* m = metrics ? metrics[i] : nullptr;
+    stp_status s = m ? validate_curvilinear(st.handle, st.elements, st.q, st.params, m, st.out_avg,
+                                            st.out_faces)
+                     : validate_common(st.handle, st.elements, st.q, st.params, st.out_avg,
+                                       st.out_faces);
     if (s != STP_OK) return s;
     if (st.handle->precision != STP_PRECISION_FP64)
       return fail(STP_ERR_UNSUPPORTED, "static batched launches are FP64");
     if (st.handle->device != dev) return fail(STP_ERR_UNSUPPORTED, "handle on another device");
     if (st.elements > 0) {
-      const void* ptrs[4] = {st.q, st.params, st.out_avg, st.out_faces};
-      for (int k = 0; k < 4; ++k)
+      const void* ptrs[5] = {st.q, st.params, st.out_avg, st.out_faces, m};
+      for (int k = 0; k < (m ? 5 : 4); ++k)
         if ((s = check_device_ptr(ptrs[k], dev, "buffer")) != STP_OK) return s;
     }
     N[i] = st.handle->N;
@@ -859,6 +872,7 @@ stp_status stp_batch_run_static(int nsets, const stp_batch_set* sets, void* stre
     a[i] = st.out_avg;
     f[i] = st.out_faces;
     tb[i] = st.handle->d_tables;
+    mt[i] = m;
   }
   for (int i = 0; i < nsets; ++i) {
     const Sizes si = sizes_per_element(N[i]);
@@ -867,21 +881,53 @@ stp_status stp_batch_run_static(int nsets, const stp_batch_set* sets, void* stre
     for (int j = 0; j < nsets; ++j) {
       if (j == i) continue;
       const Sizes sj = sizes_per_element(N[j]);
-      const void* bj[4] = {q[j], p[j], a[j], f[j]};
-      const size_t nj[4] = {sj.q * (size_t)E[j], sj.params * (size_t)E[j], sj.avg * (size_t)E[j],
-                            sj.faces * (size_t)E[j]};
+      const void* bj[5] = {q[j], p[j], a[j], f[j], mt[j]};
+      const size_t nj[5] = {sj.q * (size_t)E[j], sj.params * (size_t)E[j], sj.avg * (size_t)E[j],
+                            sj.faces * (size_t)E[j], mt[j] ? sj.q * (size_t)E[j] : 0};
       for (int x = 0; x < 2; ++x)
-        for (int y = 0; y < 4; ++y)
+        for (int y = 0; y < 5; ++y)
           if (ni[x] && nj[y] && overlap(oi[x], ni[x], bj[y], nj[y]))
             return fail(STP_ERR_INVALID_ARG, "outputs overlap another set's buffers");
     }
   }
-  int too_big = 0;
-  cudaError_t e = stp::run_static_batch(nsets, N, E, q, p, a, f, tb, static_cast<cudaStream_t>(stream),
-                                        &too_big);
-  if (too_big) return fail(STP_ERR_INVALID_ARG, "the call needs more than the 24 MiB static scratch");
-  if (e != cudaSuccess) return cuda_fail(e, "static batched launch");
+  // the Cartesian sets in one persistent launch, compacted in call order
+  int nc = 0;
+  for (int i = 0; i < nsets; ++i) {
+    if (mt[i]) continue;
+    N[nc] = N[i]; E[nc] = E[i]; q[nc] = q[i]; p[nc] = p[i]; a[nc] = a[i]; f[nc] = f[i];
+    tb[nc] = tb[i];
+    ++nc;
+  }
+  const cudaStream_t st = static_cast<cudaStream_t>(stream);
+  cudaError_t e = cudaSuccess;
+  if (nc > 0) {
+    int too_big = 0;
+    e = stp::run_static_batch(nc, N, E, q, p, a, f, tb, st, &too_big);
+    if (too_big) return fail(STP_ERR_INVALID_ARG, "the call needs more than the 24 MiB static scratch");
+    if (e != cudaSuccess) return cuda_fail(e, "static batched launch");
+  }
+  for (int i = 0; i < nsets; ++i) {
+    const stp_batch_set& s = sets[i];
+    if (!mt[i] || s.elements == 0) continue;
+    e = stp::launch_curvilinear(s.handle->N, s.elements, s.q, s.params, mt[i], s.out_avg,
+                                s.out_faces, s.handle->d_tables, s.handle->dx, st);
+    if (e != cudaSuccess) return cuda_fail(e, "static curvilinear launch");
+  }
   return STP_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+stp_status stp_batch_run_static(int nsets, const stp_batch_set* sets, void* stream) {
+  return run_static_impl(nsets, sets, nullptr, stream);
+}
+
+stp_status stp_batch_run_static_curvilinear(int nsets, const stp_batch_set* sets,
+                                            const double* const* metrics, void* stream) {
+  if (nsets > 0 && !metrics) return fail(STP_ERR_INVALID_ARG, "metrics is NULL");
+  return run_static_impl(nsets, sets, metrics, stream);
 }
 
 stp_status stp_server_create(int64_t hbm_budget_bytes, int slots, stp_server* out) {

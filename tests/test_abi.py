@@ -168,6 +168,11 @@ def test_server_add_sim_curvilinear_rejects_null_arguments(lib):
         _binding.STP_ERR_INVALID_ARG
 
 
+def test_static_curvilinear_batch_rejects_missing_metrics(lib):
+    assert lib.stp_batch_run_static_curvilinear(1, None, None, None) == _binding.STP_ERR_INVALID_ARG
+    assert lib.stp_batch_run_static_curvilinear(-1, None, None, None) == _binding.STP_ERR_INVALID_ARG
+
+
 def test_predict_sources_rejects_bad_source_list(lib):
     assert lib.stp_predict_sources(None, 1, None, None, None, None, -1, None, None) == \
         _binding.STP_ERR_INVALID_ARG

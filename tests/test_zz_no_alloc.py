@@ -15,7 +15,7 @@ import torch
 
 import paper_2003_12787_gb300 as stp
 from paper_2003_12787_gb300 import _binding
-from paper_2003_12787_gb300.inputs import elastic_problem
+from paper_2003_12787_gb300.inputs import curvilinear_problem, elastic_problem
 
 pytestmark = pytest.mark.gpu
 
@@ -54,5 +54,34 @@ def test_static_batch_matches_stp_predict_on_two_calls_in_a_row():
         for (avg, faces), (ra, rf), spec in zip(outs, refs, specs):
             assert rel(avg, ra) <= TOL, (call, spec)
             assert rel(faces, rf) <= TOL, (call, spec)
+    for P, _ in sets:
+        P.close()
+
+
+def test_static_batch_with_curvilinear_sets():
+    """stp_batch_run_static_curvilinear: curvilinear sets (own FP64 launches
+    after the persistent one) beside Cartesian ones; every set equals its
+    single-set call bit for bit (the curvilinear kernels are the same)."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    specs = [(5, 40, True), (8, 9, False), (7, 12, True), (4, 30, False), (12, 2, True)]
+    sets, refs, outs, metrics = [], [], [], []
+    for i, (N, E, curv) in enumerate(specs):
+        make = curvilinear_problem if curv else elastic_problem
+        prob = make(N, E=E, seed_material=900 + i, seed_waves=950 + i, device="cuda")
+        P = stp.Predictor(N - 1, prob.h, prob.dt)
+        refs.append(P.predict(prob.q, prob.params, metric=prob.metric))
+        outs.append(P.empty_outputs(E))
+        sets.append((P, prob))
+        metrics.append(prob.metric)
+    torch.cuda.synchronize()
+    stp.stp_batch_run_static([(P.handle, prob.E, prob.q, prob.params, a, f)
+                              for (P, prob), (a, f) in zip(sets, outs)], metrics=metrics)
+    torch.cuda.synchronize()
+    for (avg, faces), (ra, rf), (N, E, curv) in zip(outs, refs, specs):
+        if curv or N != 12:
+            assert torch.equal(avg, ra) and torch.equal(faces, rf), (N, E, curv)
+        else:
+            assert rel(avg, ra) <= TOL and rel(faces, rf) <= TOL
     for P, _ in sets:
         P.close()
