@@ -240,10 +240,22 @@ stp_precision stp_get_precision(stp_handle h);
 /*
  * Synchronise `stream`, then read and clear the handle's device status word.
  * *flags receives its bits (bit 0: a tensor-core completion wait in the mixed
- * kernel exceeded its iteration limit; the outputs of that launch are invalid).
+ * kernel exceeded its iteration limit; the outputs of that launch are invalid;
+ * bit 1: set by stp_selftest_bounded_wait).
  * Returns STP_ERR_TIMEOUT if any bit was set, else STP_OK.
  */
 stp_status stp_device_status(stp_handle h, void* stream, unsigned int* flags);
+
+/*
+ * Self-test of the bounded device-side wait: enqueues on `stream` one CTA that
+ * waits on an mbarrier nothing arrives at, polling at most `polls` times (the
+ * poll loop of the tensor-core kernel's MMA completion wait), then sets bit 1
+ * of the handle's status word and returns. A following stp_device_status
+ * reports STP_ERR_TIMEOUT with that bit, and the context stays usable: the
+ * failure path is exercised without a fault, a trap or a hang.
+ * STP_ERR_INVALID_ARG for polls outside [1, 2^22].
+ */
+stp_status stp_selftest_bounded_wait(stp_handle h, int polls, void* stream);
 
 /*
  * Batched persistent launch: the STPs of several element sets, of different

@@ -13,7 +13,8 @@ from ._binding import (NODE_FAMILIES, PRECISIONS, STPError, stp_create,  # noqa:
                        stp_measure_fp64_peak, stp_nodes, stp_predict, stp_predict_host,
                        stp_predict_curvilinear, stp_predict_curvilinear_host,
                        stp_predict_sources, stp_predict_sources_curvilinear,
-                       stp_reference_tables, stp_set_precision, stp_status_string)
+                       stp_reference_tables, stp_selftest_bounded_wait, stp_set_precision,
+                       stp_status_string)
 from ._binding import (stp_autotune, stp_batch_create, stp_batch_destroy,  # noqa: F401
                        stp_batch_info, stp_batch_launch, stp_batch_run_static)
 from ._binding import (stp_server_add_sim, stp_server_create, stp_server_destroy,  # noqa: F401

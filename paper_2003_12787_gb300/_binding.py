@@ -73,6 +73,8 @@ def load():
         lib.stp_get_precision.argtypes = [vp]
         lib.stp_get_precision.restype = ctypes.c_int
         lib.stp_device_status.argtypes = [vp, vp, ctypes.POINTER(ctypes.c_uint)]
+        lib.stp_selftest_bounded_wait.argtypes = [vp, ctypes.c_int, vp]
+        lib.stp_selftest_bounded_wait.restype = ctypes.c_int
         lib.stp_batch_create.argtypes = [ctypes.c_int, vp, ctypes.POINTER(vp)]
         lib.stp_batch_launch.argtypes = [vp, vp]
         lib.stp_batch_create_ex.argtypes = [ctypes.c_int, vp, vp, ctypes.POINTER(vp)]
@@ -198,6 +200,11 @@ def stp_set_precision(h: int, precision) -> None:
 
 def stp_get_precision(h: int) -> int:
     return int(load().stp_get_precision(h))
+
+
+def stp_selftest_bounded_wait(h: int, polls: int, stream=None) -> None:
+    _check(load().stp_selftest_bounded_wait(h, int(polls), _stream(stream)),
+           "stp_selftest_bounded_wait")
 
 
 def stp_device_status(h: int, stream=None) -> int:

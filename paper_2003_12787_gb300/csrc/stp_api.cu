@@ -561,6 +561,14 @@ stp_status stp_set_precision(stp_handle h, stp_precision p) {
 
 stp_precision stp_get_precision(stp_handle h) { return h ? h->precision : STP_PRECISION_FP64; }
 
+stp_status stp_selftest_bounded_wait(stp_handle h, int polls, void* stream) {
+  if (!h) return fail(STP_ERR_INVALID_ARG, "invalid handle");
+  if (polls < 1 || polls > (1 << 22)) return fail(STP_ERR_INVALID_ARG, "polls outside [1, 2^22]");
+  cudaError_t e = stp::launch_wait_selftest(h->d_status, polls, static_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) return cuda_fail(e, "bounded-wait self-test launch");
+  return STP_OK;
+}
+
 stp_status stp_device_status(stp_handle h, void* stream, unsigned int* flags) {
   if (!h || !flags) return fail(STP_ERR_INVALID_ARG, "invalid handle or flags pointer");
   cudaStream_t st = static_cast<cudaStream_t>(stream);

@@ -79,6 +79,10 @@ cudaError_t launch_fp32_curvilinear(int N, int64_t E, const double* q, const dou
                                     const double* metric, double* out_avg, double* out_faces,
                                     const double* tables, double dx, cudaStream_t stream);
 
+// Bounded-wait self-test (selftest.cu): one CTA waits on an mbarrier nothing
+// arrives at, for `limit` polls, then sets bit 1 of *status.
+cudaError_t launch_wait_selftest(unsigned int* status, int limit, cudaStream_t stream);
+
 // Point sources (sources.cu): after the STP of a set, adds the response of
 // the point sources to the outputs of the elements holding them (FP64, one
 // CTA per such element). groups[g] = (element, first source, source count);
