@@ -162,7 +162,10 @@ class Server:
 
     def __init__(self, hbm_budget_bytes: int, slots: int = 3):
         self.handle = B.stp_server_create(hbm_budget_bytes, slots)
+        self.budget, self.slots = hbm_budget_bytes, slots
         self.sims = []  # (Predictor, E)
+        self._inputs = []  # (params, metric) of each simulation, for snapshots
+        self._steps0 = []  # steps taken before a restore
 
     def add_sim(self, predictor: "Predictor", q0: torch.Tensor, params: torch.Tensor,
                 metric=None) -> int:
@@ -172,7 +175,30 @@ class Server:
             predictor._check_metric(q0, metric)
         sid = B.stp_server_add_sim(self.handle, predictor.handle, q0.shape[0], q0, params, metric)
         self.sims.append((predictor, q0.shape[0]))
+        self._inputs.append((params, metric))
+        self._steps0.append(0)
         return sid
+
+    def snapshot(self) -> list:
+        """Drain, then copy every simulation's state to host memory: a list of
+        dicts (q, faces, steps) that ``restore`` turns into a new server in
+        the same state."""
+        return [dict(zip(("q", "faces", "steps"), self.read(i))) for i in range(len(self.sims))]
+
+    @classmethod
+    def restore(cls, snapshot: list, sims: list, hbm_budget_bytes: int, slots: int = 3) -> "Server":
+        """A server holding the simulations of ``snapshot``; ``sims`` gives,
+        in the same order, (Predictor, params, metric or None) of each (the
+        inputs that do not change between steps)."""
+        if len(snapshot) != len(sims):
+            raise ValueError("one (Predictor, params, metric) per snapshot entry")
+        srv = cls(hbm_budget_bytes, slots)
+        for rec, (P, params, metric) in zip(snapshot, sims):
+            dev = params.device
+            srv.add_sim(P, rec["q"].to(dev).contiguous(), params,
+                        metric=None if metric is None else metric.to(dev))
+            srv._steps0[-1] = int(rec["steps"])
+        return srv
 
     def submit(self, sim_id: int):
         B.stp_server_submit(self.handle, sim_id)
@@ -194,7 +220,7 @@ class Server:
         q = torch.empty((E, N, N, N, 9), dtype=torch.float64)
         faces = torch.empty((E, 6, N, N, 9), dtype=torch.float64)
         steps = B.stp_server_read(self.handle, sim_id, q, faces)
-        return q, faces, steps
+        return q, faces, steps + self._steps0[sim_id]
 
     def stats(self) -> dict:
         return B.stp_server_stats(self.handle)

@@ -96,3 +96,47 @@ def test_budget_rejects_a_simulation_that_cannot_fit():
     with pytest.raises(stp.STPError):
         srv.add_sim(P, prob.q, prob.params)
     srv.close()
+
+
+def test_snapshot_and_restore_resume_bit_for_bit():
+    """Checkpoint/resume of the served loop: a snapshot after two steps per
+    simulation, restored into a new server that runs two more, ends in the
+    state of a server that ran four steps without interruption."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2003_12787_gb300.inputs import curvilinear_problem
+    specs = [(5, 20, False), (7, 9, True), (4, 30, False)]
+    probs, preds = [], []
+    for i, (N, E, curv) in enumerate(specs):
+        make = curvilinear_problem if curv else elastic_problem
+        prob = make(N, E=E, seed_material=4200 + i, seed_waves=4300 + i)
+        probs.append(prob)
+        preds.append(stp.Predictor(N - 1, prob.h, prob.dt))
+    budget = 64 << 20
+
+    def run(srv, steps):
+        order = np.tile(np.arange(len(specs)), steps)
+        srv.run_trace(np.linspace(0.0, 0.005, len(order)), order.astype(np.int32))
+
+    full = stp.Server(budget, slots=2)
+    for P, prob in zip(preds, probs):
+        full.add_sim(P, prob.q, prob.params, metric=prob.metric)
+    run(full, 4)
+    first = stp.Server(budget, slots=2)
+    for P, prob in zip(preds, probs):
+        first.add_sim(P, prob.q, prob.params, metric=prob.metric)
+    run(first, 2)
+    snap = first.snapshot()
+    first.close()
+    resumed = stp.Server.restore(snap, [(P, prob.params, prob.metric) for P, prob in zip(preds, probs)],
+                                 budget, slots=2)
+    run(resumed, 2)
+    for i in range(len(specs)):
+        q_a, f_a, n_a = full.read(i)
+        q_b, f_b, n_b = resumed.read(i)
+        assert n_a == n_b == 4
+        assert torch.equal(q_a, q_b) and torch.equal(f_a, f_b), specs[i]
+    full.close()
+    resumed.close()
+    for P in preds:
+        P.close()
