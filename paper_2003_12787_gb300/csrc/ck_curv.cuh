@@ -87,7 +87,9 @@ __device__ __forceinline__ void ck_node_curv_fp64(const double* __restrict__ p,
     const double* row = Dk + i * LDD;
     const int base = d == 0 ? (z * N + y) * N : d == 1 ? z * N * N + x : y * N + x;
     const int stride = d == 0 ? 1 : d == 1 ? N : N * N;
-#pragma unroll
+    // not unrolled: the point-source correction that uses this step runs on
+    // a few elements, and the fully unrolled form multiplies compile time
+#pragma unroll 1
     for (int s = 0; s < 9; ++s) {
       double a = 0.0;
 #pragma unroll

@@ -1,519 +1,8 @@
-// Float-float variant of the STP on curvilinear elements (precision
-// STP_PRECISION_FF with stp_predict_curvilinear).
-//
-// The arithmetic of curvilinear.cu (every quantity differentiated along every
-// reference direction, the chain rule through the per-node inverse Jacobian
-// G[d][j] = dxi_d/dx_j, nine partial sums per node, r_{k+1} from the elastic
-// coefficients) in float-float on the FP32 pipes (ff32.cuh), with the state
-// scaled per element by a power of two as in ff_kernels.cu. The line passes
-// are the even-odd contractions of eo_ff.cuh writing, not adding, their
-// derivatives; the metric products accumulate in Dot2 accumulators; FP64
-// instructions remain only in the conversions of the outputs.
-//
-// The FP32 variant (precision STP_PRECISION_FP32, template flag F32) runs
-// the first CK step as above and the later ones in FP32: r_1 is rounded to
-// float, the line passes, metric products and updates of steps 1..N-1 use
-// plain FP32 on float views of the same shared-memory arrays, and the time
-// average and the faces stay in float-float. The later terms are smaller by
-// factors dt/(k+2) times the operator norm, so their FP32 rounding enters the
-// average at about 1e-9 of its size on resolved fields.
-#include <type_traits>
-
-#include "eo_ff.cuh"
-#include "stp_internal.h"
+// Float-float STP on curvilinear elements: launch shapes and dispatch (the
+// kernel is in ff_curv.cuh).
+#include "ff_curv.cuh"
 
 namespace stp {
-namespace {
-
-template <int N, int A, bool DB>
-struct FfCurvShape {
-  static constexpr int N3 = N * N * N;
-  static constexpr int RX = N | 1;
-  static constexpr int PLANE = N * RX;
-  static constexpr int S = (N * PLANE) | 1;
-  static constexpr int H = N / 2;
-  static constexpr bool ODD = (N & 1) != 0;
-  static constexpr int STEP_TABLE = 2 * H * H + (ODD ? 2 * H : 0);
-  static constexpr int SUBS = (kQuantities + A - 1) / A;
-  static constexpr size_t SMEM =
-      sizeof(float2) * (size_t)(N * STEP_TABLE + 2 * N + (kQuantities + (DB ? 2 : 1) * A) * S);
-};
-
-// FP32 counterpart of ff_curv_add.
-__device__ __forceinline__ void f32_curv_add(int s, float a, float g0, float g1, float g2,
-                                             float part[9]) {
-  switch (s) {
-    case kV1:
-      part[kS11] = fmaf(g0, a, part[kS11]);
-      part[kS12] = fmaf(g1, a, part[kS12]);
-      part[kS13] = fmaf(g2, a, part[kS13]);
-      break;
-    case kV2:
-      part[kS12] = fmaf(g0, a, part[kS12]);
-      part[kS22] = fmaf(g1, a, part[kS22]);
-      part[kS23] = fmaf(g2, a, part[kS23]);
-      break;
-    case kV3:
-      part[kS13] = fmaf(g0, a, part[kS13]);
-      part[kS23] = fmaf(g1, a, part[kS23]);
-      part[kS33] = fmaf(g2, a, part[kS33]);
-      break;
-    case kS11: part[kV1] = fmaf(g0, a, part[kV1]); break;
-    case kS22: part[kV2] = fmaf(g1, a, part[kV2]); break;
-    case kS33: part[kV3] = fmaf(g2, a, part[kV3]); break;
-    case kS12:
-      part[kV1] = fmaf(g1, a, part[kV1]);
-      part[kV2] = fmaf(g0, a, part[kV2]);
-      break;
-    case kS13:
-      part[kV1] = fmaf(g2, a, part[kV1]);
-      part[kV3] = fmaf(g0, a, part[kV3]);
-      break;
-    default:  // kS23
-      part[kV2] = fmaf(g2, a, part[kV2]);
-      part[kV3] = fmaf(g1, a, part[kV3]);
-      break;
-  }
-}
-
-// The contribution of quantity s's reference derivative a along direction d
-// (metric row g0, g1, g2) to a node's nine partial sums, indexed as in
-// curvilinear.cu: part[v_i] = sum_j dsigma_ij/dx_j, part[s_ii] = dv_i/dx_i,
-// part[s_ij] = dv_i/dx_j + dv_j/dx_i.
-__device__ __forceinline__ void ff_curv_add(int s, float2 a, float2 g0, float2 g1, float2 g2,
-                                            ff::Dot part[9]) {
-  switch (s) {
-    case kV1: part[kS11].fma(g0, a); part[kS12].fma(g1, a); part[kS13].fma(g2, a); break;
-    case kV2: part[kS12].fma(g0, a); part[kS22].fma(g1, a); part[kS23].fma(g2, a); break;
-    case kV3: part[kS13].fma(g0, a); part[kS23].fma(g1, a); part[kS33].fma(g2, a); break;
-    case kS11: part[kV1].fma(g0, a); break;
-    case kS22: part[kV2].fma(g1, a); break;
-    case kS33: part[kV3].fma(g2, a); break;
-    case kS12: part[kV1].fma(g1, a); part[kV2].fma(g0, a); break;
-    case kS13: part[kV1].fma(g2, a); part[kV3].fma(g0, a); break;
-    default: part[kV2].fma(g2, a); part[kV3].fma(g1, a); break;  // kS23
-  }
-}
-
-// One element per CTA of NT threads, thread t owning nodes t, t + NT, ...
-// (NODES of them). LEAN parks the running average in the output buffer (as
-// pairs) and derives the coefficients from params at every step; GREG keeps
-// the owned nodes' metric (float-float) in registers instead of converting
-// it from the FP64 input at every pass. DB double-buffers the reference
-// derivatives (A = 9 only). F32: steps 1..N-1 in FP32 (see the top).
-template <int N, int NT, int NODES, int A, bool LEAN, bool GREG, bool DB, bool F32>
-__global__ void __launch_bounds__(NT, 1)
-ff_curv_kernel(const double* __restrict__ q, const double* __restrict__ params,
-               const double* __restrict__ metric, double* __restrict__ out_avg,
-               double* __restrict__ out_faces, const double* __restrict__ tables, double dx) {
-  using Sh = FfCurvShape<N, A, DB>;
-  constexpr int N3 = Sh::N3, S = Sh::S, H = Sh::H, M = kQuantities;
-  constexpr int RX = Sh::RX, PLANE = Sh::PLANE, SUBS = Sh::SUBS, ST = Sh::STEP_TABLE;
-  constexpr bool ODD = Sh::ODD;
-  constexpr int mid = H;
-  static_assert(N >= 2 && NODES * NT >= N3, "every node needs an owner");
-  static_assert(SUBS <= 2 && (!DB || SUBS == 1), "one or two line passes per direction");
-  auto pad = [](int n) { return (n / (N * N)) * PLANE + ((n / N) % N) * RX + n % N; };
-  extern __shared__ float2 smem_ffc[];
-  float2* sT = smem_ffc;         // [N][ST] even-odd tables of every step
-  float2* sPhi = sT + N * ST;    // phi0[N], phi1[N]
-  float2* sp = sPhi + 2 * N;     // current term [9][S]; the average at the end
-  float2* sacc = sp + M * S;     // reference derivatives [DB ? 2 : 1][A][S]
-  float* sp_f = reinterpret_cast<float*>(sp);      // FP32 steps: the term [9][S] floats
-  float* sacc_f = reinterpret_cast<float*>(sacc);  // FP32 steps: derivatives [..][A][S] floats
-  const int tid = threadIdx.x;
-  const int64_t e = blockIdx.x;
-  double* gavg = out_avg + e * (int64_t)(M * N3);
-  float2* gpark = reinterpret_cast<float2*>(gavg);  // running average when LEAN
-  const double* ge = metric + e * (int64_t)(9 * N3);
-  const double* pe = params + e * (int64_t)(kParams * N3);
-
-  for (int i = tid; i < N * ST; i += NT) {
-    const int k = i / ST;
-    sT[i] = ff::split(eo_table_entry<N>(tables + k * N * N, i - k * ST));
-  }
-  for (int i = tid; i < 2 * N; i += NT) sPhi[i] = ff::split(tables[N3 + i]);
-  const int sc = load_state_ff_layout<N, NT, S, RX, PLANE>(q + e * (int64_t)(M * N3), sp);
-
-  const float2 fdx = ff::split(dx);
-  constexpr int KEEP = LEAN ? 1 : NODES;
-  float2 cf[KEEP][4], avg[KEEP][M], gm[GREG ? NODES : 1][9];
-  // coefficients of node n times dx (the step tables hold D dt/((k+2) dx))
-  auto coefficients = [&](int n, float2 c[4]) {
-    elastic_coefficients_ff(__ldg(pe + 3 * n), __ldg(pe + 3 * n + 1), __ldg(pe + 3 * n + 2), c);
-#pragma unroll
-    for (int i = 0; i < 4; ++i) c[i] = ff::mul(c[i], fdx);
-  };
-#pragma unroll
-  for (int j = 0; j < NODES; ++j) {
-    const int n = tid + j * NT;
-    if (n >= N3) continue;
-    if constexpr (!LEAN) coefficients(n, cf[j]);
-    if constexpr (GREG) {
-#pragma unroll
-      for (int c = 0; c < 9; ++c) gm[j][c] = ff::split(__ldg(ge + 9 * n + c));
-    }
-    const int pn = pad(n);
-#pragma unroll
-    for (int s = 0; s < M; ++s) {
-      if constexpr (LEAN) gpark[n * M + s] = sp[s * S + pn];
-      else avg[j][s] = sp[s * S + pn];
-    }
-  }
-
-  ff::Dot part[NODES][9];
-
-  auto line_pass = [&](int k, int d, int sub, float2* dst_base) {
-    const float2* Et = sT + k * ST;
-    const float2* Ot = Et + H * H;
-    const float2* Dm = Ot + H * H;
-    const float2* Om = Dm + H;
-    const int nq = (M - sub * A) < A ? (M - sub * A) : A;
-    for (int task = tid; task < nq * N * N; task += NT) {
-      const int ql = task / (N * N);
-      const int a = (task / N) % N, b = task % N;
-      int base, stride;
-      if (d == 0) { base = a * PLANE + b * RX; stride = 1; }
-      else if (d == 1) { base = a * PLANE + b; stride = RX; }
-      else { base = a * RX + b; stride = PLANE; }
-      const float2* u = sp + (sub * A + ql) * S + base;
-      float2 ev[H > 0 ? H : 1], od[H > 0 ? H : 1];
-#pragma unroll
-      for (int l = 0; l < H; ++l) {
-        const float2 lo = u[l * stride], hi = u[(N - 1 - l) * stride];
-        ev[l] = ff::add(lo, hi);
-        od[l] = ff::sub(lo, hi);
-      }
-      float2 out[N];
-#pragma unroll
-      for (int i = 0; i < H; ++i) {
-        ff::Dot P, Q;
-#pragma unroll
-        for (int l = 0; l < H; ++l) {
-          P.fma(Et[i * H + l], ev[l]);
-          Q.fma(Ot[i * H + l], od[l]);
-        }
-        if (ODD) P.fma(Dm[i], u[mid * stride]);
-        const float2 pv = P.value_lazy(), qv = Q.value_lazy();
-        out[i] = ff::add(pv, qv);
-        out[N - 1 - i] = ff::sub(qv, pv);
-      }
-      if (ODD) {
-        ff::Dot Q;
-#pragma unroll
-        for (int l = 0; l < H; ++l) Q.fma(Om[l], od[l]);
-        out[mid] = Q.value();
-      }
-      float2* dst = dst_base + ql * S + base;
-#pragma unroll
-      for (int i = 0; i < N; ++i) dst[i * stride] = out[i];
-    }
-  };
-
-  auto pointwise = [&](int k, int d, auto SUB, const float2* src, bool last) {
-    constexpr int sub = decltype(SUB)::value;
-#pragma unroll
-    for (int j = 0; j < NODES; ++j) {
-      const int n = tid + j * NT;
-      if (n >= N3) continue;
-      const int pn = pad(n);
-      float2 g0, g1, g2;
-      if constexpr (GREG) {
-        g0 = d == 0 ? gm[j][0] : d == 1 ? gm[j][3] : gm[j][6];
-        g1 = d == 0 ? gm[j][1] : d == 1 ? gm[j][4] : gm[j][7];
-        g2 = d == 0 ? gm[j][2] : d == 1 ? gm[j][5] : gm[j][8];
-      } else {
-        g0 = ff::split(__ldg(ge + 9 * n + 3 * d));
-        g1 = ff::split(__ldg(ge + 9 * n + 3 * d + 1));
-        g2 = ff::split(__ldg(ge + 9 * n + 3 * d + 2));
-      }
-#pragma unroll
-      for (int ql = 0; ql < A; ++ql) {
-        constexpr int s0 = sub * A;
-        if (s0 + ql < M) ff_curv_add(s0 + ql, src[ql * S + pn], g0, g1, g2, part[j]);
-      }
-      if (!last) continue;
-      // the partial sums in the order eo_pointwise_ff expects: velocity sums,
-      // shear sums, then the three normal velocity derivatives
-      float2 g[9], r[9];
-      g[0] = part[j][kV1].value();
-      g[1] = part[j][kV2].value();
-      g[2] = part[j][kV3].value();
-      g[3] = part[j][kS12].value();
-      g[4] = part[j][kS13].value();
-      g[5] = part[j][kS23].value();
-      g[6] = part[j][kS11].value();
-      g[7] = part[j][kS22].value();
-      g[8] = part[j][kS33].value();
-      if constexpr (LEAN) {
-        float2 c[4];
-        coefficients(n, c);
-        eo_pointwise_ff(g, c[0], c[1], c[2], c[3], r);
-      } else {
-        eo_pointwise_ff(g, cf[j][0], cf[j][1], cf[j][2], cf[j][3], r);
-      }
-#pragma unroll
-      for (int s = 0; s < M; ++s) {
-        // the next term: pairs, or (FP32 variant, after step 0) a float in
-        // the float view of the same array (nothing reads it in this phase)
-        if constexpr (LEAN) {
-          const float2 v = ff::add(gpark[n * M + s], r[s]);
-          if (k + 1 < N) {
-            gpark[n * M + s] = v;
-            if constexpr (F32) sp_f[s * S + pn] = __fadd_rn(r[s].x, r[s].y);
-            else sp[s * S + pn] = r[s];
-          } else {
-            sp[s * S + pn] = v;  // final average, staged for the store
-          }
-        } else {
-          avg[j][s] = ff::add(avg[j][s], r[s]);
-          if (k + 1 < N) {
-            if constexpr (F32) sp_f[s * S + pn] = __fadd_rn(r[s].x, r[s].y);
-            else sp[s * S + pn] = r[s];
-          }
-        }
-      }
-    }
-  };
-
-  float part32[NODES][9];
-
-  auto line_pass32 = [&](int k, int d, int sub, float* dst_base) {
-    const float2* Et = sT + k * ST;
-    const float2* Ot = Et + H * H;
-    const float2* Dm = Ot + H * H;
-    const float2* Om = Dm + H;
-    const int nq = (M - sub * A) < A ? (M - sub * A) : A;
-    #pragma unroll 1
-    for (int task = tid; task < nq * N * N; task += NT) {
-      const int ql = task / (N * N);
-      const int a = (task / N) % N, b = task % N;
-      int base, stride;
-      if (d == 0) { base = a * PLANE + b * RX; stride = 1; }
-      else if (d == 1) { base = a * PLANE + b; stride = RX; }
-      else { base = a * RX + b; stride = PLANE; }
-      const float* u = sp_f + (sub * A + ql) * S + base;
-      float ev[H > 0 ? H : 1], od[H > 0 ? H : 1];
-#pragma unroll
-      for (int l = 0; l < H; ++l) {
-        const float lo = u[l * stride], hi = u[(N - 1 - l) * stride];
-        ev[l] = lo + hi;
-        od[l] = lo - hi;
-      }
-      float out[N];
-#pragma unroll
-      for (int i = 0; i < H; ++i) {
-        float P = 0.f, Q = 0.f;
-#pragma unroll
-        for (int l = 0; l < H; ++l) {
-          P = fmaf(Et[i * H + l].x, ev[l], P);
-          Q = fmaf(Ot[i * H + l].x, od[l], Q);
-        }
-        if (ODD) P = fmaf(Dm[i].x, u[mid * stride], P);
-        out[i] = P + Q;
-        out[N - 1 - i] = Q - P;
-      }
-      if (ODD) {
-        float Q = 0.f;
-#pragma unroll
-        for (int l = 0; l < H; ++l) Q = fmaf(Om[l].x, od[l], Q);
-        out[mid] = Q;
-      }
-      float* dst = dst_base + ql * S + base;
-#pragma unroll
-      for (int i = 0; i < N; ++i) dst[i * stride] = out[i];
-    }
-  };
-
-  auto pointwise32 = [&](int k, int d, auto SUB, const float* src, bool last) {
-    constexpr int sub = decltype(SUB)::value;
-#pragma unroll
-    for (int j = 0; j < NODES; ++j) {
-      const int n = tid + j * NT;
-      if (n >= N3) continue;
-      const int pn = pad(n);
-      float g0, g1, g2;
-      if constexpr (GREG) {
-        g0 = d == 0 ? gm[j][0].x : d == 1 ? gm[j][3].x : gm[j][6].x;
-        g1 = d == 0 ? gm[j][1].x : d == 1 ? gm[j][4].x : gm[j][7].x;
-        g2 = d == 0 ? gm[j][2].x : d == 1 ? gm[j][5].x : gm[j][8].x;
-      } else {
-        g0 = ff::split(__ldg(ge + 9 * n + 3 * d)).x;
-        g1 = ff::split(__ldg(ge + 9 * n + 3 * d + 1)).x;
-        g2 = ff::split(__ldg(ge + 9 * n + 3 * d + 2)).x;
-      }
-#pragma unroll
-      for (int ql = 0; ql < A; ++ql) {
-        constexpr int s0 = sub * A;
-        if (s0 + ql < M) f32_curv_add(s0 + ql, src[ql * S + pn], g0, g1, g2, part32[j]);
-      }
-      if (!last) continue;
-      float invrho, lam, mu, mu2;
-      if constexpr (LEAN) {
-        float2 c[4];
-        coefficients(n, c);
-        invrho = c[0].x; lam = c[1].x; mu = c[2].x; mu2 = c[3].x;
-      } else {
-        invrho = cf[j][0].x; lam = cf[j][1].x; mu = cf[j][2].x; mu2 = cf[j][3].x;
-      }
-      const float* pj = part32[j];
-      const float ltr = lam * ((pj[kS11] + pj[kS22]) + pj[kS33]);
-      float r[9];
-      r[kV1] = invrho * pj[kV1];
-      r[kV2] = invrho * pj[kV2];
-      r[kV3] = invrho * pj[kV3];
-      r[kS11] = fmaf(mu2, pj[kS11], ltr);
-      r[kS22] = fmaf(mu2, pj[kS22], ltr);
-      r[kS33] = fmaf(mu2, pj[kS33], ltr);
-      r[kS12] = mu * pj[kS12];
-      r[kS13] = mu * pj[kS13];
-      r[kS23] = mu * pj[kS23];
-#pragma unroll
-      for (int s = 0; s < M; ++s) {
-        const float2 rr = make_float2(r[s], 0.f);
-        if constexpr (LEAN) {
-          const float2 v = ff::add(gpark[n * M + s], rr);
-          if (k + 1 < N) {
-            gpark[n * M + s] = v;
-            sp_f[s * S + pn] = r[s];
-          } else {
-            sp[s * S + pn] = v;  // final average (pairs), staged for the store
-          }
-        } else {
-          avg[j][s] = ff::add(avg[j][s], rr);
-          if (k + 1 < N) sp_f[s * S + pn] = r[s];
-        }
-      }
-    }
-  };
-
-  // one CK step in float-float
-  auto step_ff = [&](int k) {
-#pragma unroll
-    for (int j = 0; j < NODES; ++j)
-#pragma unroll
-      for (int c = 0; c < 9; ++c) part[j][c] = ff::Dot();
-    if constexpr (DB) {
-      line_pass(k, 0, 0, sacc);
-      __syncthreads();
-#pragma unroll 1
-      for (int d = 0; d < 3; ++d) {
-        if (d < 2) line_pass(k, d + 1, 0, sacc + ((d + 1) & 1) * (A * S));
-        pointwise(k, d, std::integral_constant<int, 0>{}, sacc + (d & 1) * (A * S), d == 2);
-        __syncthreads();
-      }
-    } else {
-#pragma unroll 1
-      for (int d = 0; d < 3; ++d) {
-        line_pass(k, d, 0, sacc);
-        __syncthreads();
-        pointwise(k, d, std::integral_constant<int, 0>{}, sacc, SUBS == 1 && d == 2);
-        __syncthreads();
-        if constexpr (SUBS > 1) {
-          line_pass(k, d, 1, sacc);
-          __syncthreads();
-          pointwise(k, d, std::integral_constant<int, 1>{}, sacc, d == 2);
-          __syncthreads();
-        }
-      }
-    }
-  };
-  // one CK step in FP32 (k >= 1, FP32 variant)
-  auto step_f32 = [&](int k) {
-#pragma unroll
-    for (int j = 0; j < NODES; ++j)
-#pragma unroll
-      for (int c = 0; c < 9; ++c) part32[j][c] = 0.f;
-    if constexpr (DB) {
-      line_pass32(k, 0, 0, sacc_f);
-      __syncthreads();
-#pragma unroll 1
-      for (int d = 0; d < 3; ++d) {
-        if (d < 2) line_pass32(k, d + 1, 0, sacc_f + ((d + 1) & 1) * (A * S));
-        pointwise32(k, d, std::integral_constant<int, 0>{}, sacc_f + (d & 1) * (A * S), d == 2);
-        __syncthreads();
-      }
-    } else {
-#pragma unroll 1
-      for (int d = 0; d < 3; ++d) {
-        line_pass32(k, d, 0, sacc_f);
-        __syncthreads();
-        pointwise32(k, d, std::integral_constant<int, 0>{}, sacc_f, SUBS == 1 && d == 2);
-        __syncthreads();
-        if constexpr (SUBS > 1) {
-          line_pass32(k, d, 1, sacc_f);
-          __syncthreads();
-          pointwise32(k, d, std::integral_constant<int, 1>{}, sacc_f, d == 2);
-          __syncthreads();
-        }
-      }
-    }
-  };
-
-  if constexpr (F32) {
-    // k = 0 hidden from the optimiser: with a constant step the table loads
-    // become loop invariants, are hoisted into registers and spill
-    int k0 = 0;
-    asm volatile("" : "+r"(k0));
-    step_ff(k0);
-#pragma unroll 1
-    for (int k = 1; k < N; ++k) step_f32(k);
-  } else {
-#pragma unroll 1
-    for (int k = 0; k < N; ++k) step_ff(k);
-  }
-
-  if constexpr (!LEAN) {
-#pragma unroll
-    for (int j = 0; j < NODES; ++j) {
-      const int n = tid + j * NT;
-      if (n >= N3) continue;
-      const int pn = pad(n);
-#pragma unroll
-      for (int s = 0; s < M; ++s) sp[s * S + pn] = avg[j][s];
-    }
-  }
-  __syncthreads();
-  for (int f = tid; f < M * N3; f += NT) {
-    const int n = f / M, s = f - n * M;
-    gavg[f] = ff::to_double(sp[s * S + pad(n)], sc);
-  }
-  double* fe = out_faces + e * (int64_t)(6 * N * N * M);
-  for (int o = tid; o < 6 * N * N * M; o += NT) {
-    const int s = o % M;
-    int rest = o / M;
-    const int bb = rest % N;
-    rest /= N;
-    const int aa = rest % N;
-    const int f = rest / N;
-    const int dd = f >> 1;
-    const float2* phi = sPhi + (f & 1) * N;
-    int base, stride;
-    if (dd == 0) { base = aa * PLANE + bb * RX; stride = 1; }
-    else if (dd == 1) { base = aa * PLANE + bb; stride = RX; }
-    else { base = aa * RX + bb; stride = PLANE; }
-    ff::Dot acc;
-#pragma unroll
-    for (int i = 0; i < N; ++i) acc.fma(phi[i], sp[s * S + base + i * stride]);
-    fe[o] = ff::to_double(acc.value(), sc);
-  }
-}
-
-template <int N, int NT, int NODES, int A, bool LEAN, bool GREG, bool DB, bool F32 = false>
-cudaError_t launch_ff_curv_n(int64_t E, const double* q, const double* params, const double* metric,
-                             double* out_avg, double* out_faces, const double* tables, double dx,
-                             cudaStream_t stream) {
-  constexpr size_t smem = FfCurvShape<N, A, DB>::SMEM;
-  static_assert(smem <= 232448, "shared memory budget of one CTA exceeded");
-  auto kern = ff_curv_kernel<N, NT, NODES, A, LEAN, GREG, DB, F32>;
-  cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (err != cudaSuccess) return err;
-  if (E > 0x7fffffffLL) return cudaErrorInvalidValue;
-  kern<<<(unsigned)E, NT, smem, stream>>>(q, params, metric, out_avg, out_faces, tables, dx);
-  return cudaGetLastError();
-}
-
-}  // namespace
 
 // Launch shapes per N: threads, nodes per thread, quantities per line pass,
 // lean register state, metric in registers, double buffer (measured on GB300
@@ -537,32 +26,6 @@ cudaError_t launch_ff_curvilinear(int N, int64_t E, const double* q, const doubl
     return launch_ff_curv_n<n, nt, nodes, a, lean, greg, db>(E, q, params, metric, out_avg,   \
                                                              out_faces, tables, dx, stream);
     STP_FF_CURV_SHAPES(X)
-#undef X
-    default: return cudaErrorInvalidValue;
-  }
-}
-
-// FP32 variant (first step in float-float, later steps in FP32): threads,
-// nodes per thread, quantities per line pass, lean register state, metric in
-// registers, double buffer (N = 6..10 measured on GB300 among 2-4 candidates).
-#define STP_FP32_CURV_SHAPES(X)                                                                \
-  X(2, 32, 1, 9, false, true, false) X(3, 32, 1, 9, false, true, false)                       \
-  X(4, 64, 1, 9, false, true, false) X(5, 128, 1, 9, false, true, false)                      \
-  X(6, 224, 1, 9, false, true, true) X(7, 448, 1, 9, false, true, false)                      \
-  X(8, 576, 1, 9, false, true, true) X(9, 384, 2, 9, false, true, true)                       \
-  X(10, 512, 2, 9, true, true, false) X(11, 448, 3, 9, true, false, false)                    \
-  X(12, 448, 4, 5, true, false, false)
-
-cudaError_t launch_fp32_curvilinear(int N, int64_t E, const double* q, const double* params,
-                                    const double* metric, double* out_avg, double* out_faces,
-                                    const double* tables, double dx, cudaStream_t stream) {
-  if (E <= 0) return cudaSuccess;
-  switch (N) {
-#define X(n, nt, nodes, a, lean, greg, db)                                                     \
-  case n:                                                                                      \
-    return launch_ff_curv_n<n, nt, nodes, a, lean, greg, db, true>(                           \
-        E, q, params, metric, out_avg, out_faces, tables, dx, stream);
-    STP_FP32_CURV_SHAPES(X)
 #undef X
     default: return cudaErrorInvalidValue;
   }
