@@ -361,7 +361,9 @@ def small_case_latency(stp, torch, args):
     """The small order-3 workload (N=4, 8^3 = 512 elements, 31 MFLOP): a
     latency-bound launch. Per launch, the device time (CUDA events around
     it) and the host launch-to-done time (stp_predict call to stream
-    synchronisation), 5 warm-ups then args.small_launches timed; p50/p99."""
+    synchronisation), 5 warm-ups then args.small_launches timed; p50/p99.
+    Then the same launch captured once into a CUDA graph: host replay-to-done
+    time of the replays (argument checks and launch set-up paid once)."""
     from paper_2003_12787_gb300.inputs import elastic_problem
     N, grid, h, desc = WORKLOADS["order3"]
     prob = elastic_problem(N, grid=grid, h=h, device="cuda")
@@ -383,11 +385,28 @@ def small_case_latency(stp, torch, args):
                 dev.append(e0.elapsed_time(e1) * 1e3)
                 host.append((t1 - t0) * 1e6)
 
+        # the same launch captured once into a CUDA graph: replay cost only
+        gstream = torch.cuda.Stream()
+        g = torch.cuda.CUDAGraph()
+        torch.cuda.synchronize()
+        with torch.cuda.graph(g, stream=gstream):
+            P.predict(prob.q, prob.params, out=(avg, faces))
+        graph_host = []
+        for i in range(5 + args.small_launches):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            g.replay()
+            torch.cuda.current_stream().synchronize()
+            t1 = time.perf_counter()
+            if i >= 5:
+                graph_host.append((t1 - t0) * 1e6)
+
     def pct(v, p):
         return float(np.percentile(np.array(v), p))
     return {"workload": desc, "launches": args.small_launches,
             "device_us": {"p50": pct(dev, 50), "p99": pct(dev, 99)},
             "launch_to_done_us": {"p50": pct(host, 50), "p99": pct(host, 99)},
+            "graph_replay_to_done_us": {"p50": pct(graph_host, 50), "p99": pct(graph_host, 99)},
             "elements_per_s_p50": prob.E / (pct(dev, 50) * 1e-6)}
 
 
