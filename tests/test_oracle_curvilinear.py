@@ -270,10 +270,15 @@ SRC = os.path.join(os.path.dirname(oracle.__file__), "stp_oracle.c")
 MUTANTS = {
     "metric transposed": ("metric[n * 9 + 3 * d + j]", "metric[n * 9 + 3 * j + d]"),
     "reference direction's B": ("elastic_B(j, params[n * 3 + 0]", "elastic_B(d, params[n * 3 + 0]"),
+    "diagonal of the metric only": ("const double gdj = metric[n * 9 + 3 * d + j];",
+                                    "const double gdj = j == d ? metric[n * 9 + 3 * d + j] : 0.0;"),
 }
 SOURCE_MUTANTS = {
     "det G taken for det J": ("1.0 / fabs(det3(metric + ((size_t)e * n3 + NODE(z, y, x)) * 9))",
                               "fabs(det3(metric + ((size_t)e * n3 + NODE(z, y, x)) * 9))"),
+    "cube volume on a curvilinear element": (
+        "const double vol = metric ? 1.0 / fabs(det3(metric + ((size_t)e * n3 + NODE(z, y, x)) * 9))",
+        "const double vol = metric ? 1.0"),
 }
 
 
