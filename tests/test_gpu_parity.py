@@ -183,3 +183,48 @@ def test_fp64_peak_probe_is_plausible():
     g = stp.stp_measure_fp64_peak()
     # GB300 FP64 is about 1.2 TFLOP/s; anything far outside means a broken probe
     assert 300.0 < g < 5000.0, g
+
+
+# FP32: the profile changes by O(1) across one element, the unresolved regime
+# in which that variant's error grows to a few 1e-9 (stp.h, STP_PRECISION_FP32)
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-12), ("ff", 1e-12), ("fp32", 5e-9)])
+@pytest.mark.parametrize("curvilinear", [False, True])
+def test_gpu_reproduces_the_exact_plane_wave_shift(precision, tol, curvilinear):
+    """Physics, not only the oracle: with uniform material and a P wave whose
+    profile is a polynomial of degree N-1 along a direction n (inside the
+    element's polynomial space, on a cube or on an affine, non-orthogonal
+    curvilinear element), the STP's time average is the closed form
+    r (F(s) - F(s - c dt)) / (c dt), F' = f, r the wave's eigenvector."""
+    N, E = 6, 3
+    rho, cp, cs = 2.3, 4.7, 2.1
+    lam, mu = rho * (cp * cp - 2 * cs * cs), rho * cs * cs
+    h, dt = 0.125, 0.004
+    rng = np.random.default_rng(44)
+    n = rng.standard_normal(3)
+    n /= np.linalg.norm(n)
+    sig = -(lam * np.eye(3) + 2 * mu * np.outer(n, n)) / cp
+    r = np.concatenate([n, [sig[0, 0], sig[1, 1], sig[2, 2], sig[0, 1], sig[0, 2], sig[1, 2]]])
+    f = np.polynomial.Polynomial(rng.uniform(-1, 1, N) / 4)
+    F = f.integ()
+    xi = np.polynomial.legendre.leggauss(N)[0] / 2 + 0.5
+    Z, Y, X = np.meshgrid(xi, xi, xi, indexing="ij")
+    ref_pts = np.stack([X, Y, Z], axis=-1)
+    J = h * (np.array([[1.0, 0.25, -0.1], [0.05, 0.9, 0.2], [-0.1, 0.15, 1.1]]) if curvilinear
+             else np.eye(3))
+    q = np.zeros((E, N, N, N, 9))
+    avg_x = np.zeros_like(q)
+    for e in range(E):
+        s = (np.array([e * h, 0.3, -0.2]) + ref_pts @ J.T) @ n
+        q[e] = f(s)[..., None] * r
+        avg_x[e] = ((F(s) - F(s - cp * dt)) / (cp * dt))[..., None] * r
+    params = np.zeros((E, N, N, N, 3))
+    params[...] = (rho, cp, cs)
+    metric = np.broadcast_to(np.linalg.inv(J), (E, N, N, N, 3, 3)).copy()
+    with stp.Predictor(N - 1, h, dt, precision=precision) as P:
+        avg, _ = P.predict(torch.from_numpy(q).cuda(), torch.from_numpy(params).cuda(),
+                           metric=torch.from_numpy(metric).cuda() if curvilinear else None)
+        torch.cuda.synchronize()
+    a = avg.cpu().numpy()
+    assert np.abs(a - avg_x).max() <= tol * np.abs(avg_x).max()
+    if precision != "fp32":  # the time-dependent part alone (about 1e-3 of the average)
+        assert np.abs((a - q) - (avg_x - q)).max() <= 1e-9 * np.abs(avg_x - q).max()
