@@ -357,7 +357,7 @@ cudaError_t launch_ff_slots(int64_t E, const double* q, const double* params, do
 #define STP_FF_SHAPES(X)                                                                       \
   X(2, 32, 24, 16, true) X(3, 32, 27, 16, true) X(4, 96, 96, 8, true) X(5, 160, 150, 4, true) \
   X(6, 256, 216, 1, true) X(7, 352, 343, 2, true) X(8, 384, 384, 2, true)                     \
-  X(9, 768, 729, 1, true) X(10, 1024, 1000, 1, true) X(11, 736, 726, 1, false)
+  X(9, 768, 729, 1, true) X(10, 640, 600, 1, true) X(11, 736, 726, 1, false)
 
 // N = 12: the slot-reusing body (threads, working threads).
 #define STP_FF_SLOT_SHAPE(X) X(12, 448, 432)
