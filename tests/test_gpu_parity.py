@@ -142,6 +142,25 @@ def test_host_path_equals_device_path_bitwise():
         assert np.array_equal(avg_h2.numpy(), avg_d) and np.array_equal(faces_h2.numpy(), faces_d)
 
 
+def test_host_path_order7_32768_elements_sampled():
+    """The end-to-end form of the order-7 workload (32^3 elements of side
+    1/32): pinned host buffers in and out through stp_predict_host, which
+    pipelines chunked copies with the kernels. Sampled elements against the
+    oracle; the device-buffer path gives the same bits everywhere."""
+    prob = elastic_problem(8, grid=(32, 32, 32), h=1.0 / 32, device="cuda")
+    q_h = prob.q.cpu().pin_memory()
+    p_h = prob.params.cpu().pin_memory()
+    with stp.Predictor(7, prob.h, prob.dt) as P:
+        avg_h, faces_h = P.predict_host(q_h, p_h)
+        avg_d, faces_d = P.predict(prob.q, prob.params)
+        torch.cuda.synchronize()
+    assert torch.equal(avg_h, avg_d.cpu()) and torch.equal(faces_h, faces_d.cpu())
+    rng = np.random.default_rng(5)
+    idx = np.unique(np.concatenate([[0, prob.E - 1], rng.choice(prob.E, 48, replace=False)]))
+    avg_ref, faces_ref = oracle.stp(q_h[idx].numpy(), p_h[idx].numpy(), prob.h, prob.dt)
+    assert_parity(avg_h[idx].numpy(), faces_h[idx].numpy(), avg_ref, faces_ref)
+
+
 def test_non_default_stream_and_zero_elements():
     prob = elastic_problem(5, E=6)
     s = torch.cuda.Stream()

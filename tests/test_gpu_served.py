@@ -140,3 +140,68 @@ def test_snapshot_and_restore_resume_bit_for_bit():
     resumed.close()
     for P in preds:
         P.close()
+
+
+def test_served_workload_at_bench_size_sampled_against_oracle():
+    """The served workload as the benchmark runs it: 256 simulations (orders
+    3-9, 64-2048 elements each, seed 1005) behind a 2 GiB device pool with 3
+    slots, driven by Poisson arrivals at 2000 req/s (seed 1006), so that
+    admissions and evictions run all the time. Afterwards sampled elements of
+    sampled simulations are stepped by the oracle as often as the server
+    stepped them (q_{n+1} := avg_n): the predictor is element-local, so each
+    element's trajectory depends on that element alone."""
+    import oracle
+    from paper_2003_12787_gb300.inputs import served_arrivals, served_recipe
+    recipe = served_recipe(e_max=2048)
+    budget = 2 << 30
+    srv = stp.Server(budget, slots=3)
+    rng = np.random.default_rng(11)
+    # two sampled simulations per order, three elements each (first, last, one drawn)
+    picked = set()
+    for N in range(4, 11):
+        cand = [i for i, r in enumerate(recipe) if r["N"] == N]
+        picked.update(rng.choice(cand, min(2, len(cand)), replace=False).tolist())
+    samples, preds = {}, []
+    for i, r in enumerate(recipe):
+        prob = elastic_problem(r["N"], grid=r["grid"], E=r["E"], h=r["h"],
+                               seed_material=r["seed_material"], seed_waves=r["seed_waves"],
+                               device="cuda")
+        P = stp.Predictor(r["N"] - 1, prob.h, prob.dt)
+        assert srv.add_sim(P, prob.q, prob.params) == i
+        preds.append(P)
+        if i in picked:
+            idx = np.unique([0, r["E"] - 1, int(rng.integers(r["E"]))])
+            it = torch.as_tensor(idx, device="cuda")
+            samples[i] = (idx, prob.q[it].cpu().numpy(), prob.params[it].cpu().numpy(),
+                          prob.h, prob.dt)
+        del prob
+    n_req = 3000
+    t, ids = served_arrivals(n_req, rate=2000.0, n_sims=len(recipe), seed=1006)
+    lat, wall = srv.run_trace(t, ids)
+    assert np.all(np.isfinite(lat)) and np.all(lat > 0) and wall > 0
+    st = srv.stats()
+    assert st["completed"] == n_req
+    assert st["evictions"] > 0 and st["pool_bytes_peak"] <= budget
+    counts = np.bincount(ids, minlength=len(recipe))
+    checked = 0
+    for i, (idx, q_s, p_s, h, dt) in samples.items():
+        q, faces, n = srv.read(i)
+        assert n == counts[i]
+        if n == 0:
+            continue
+        for _ in range(n):
+            avg_ref, faces_ref = oracle.stp(q_s, p_s, h, dt)
+            q_s = avg_ref
+        tol = 1e-12
+        got_q = q[idx].numpy()
+        got_f = faces[idx].numpy()
+        scale = np.abs(avg_ref).max()
+        assert np.abs(got_q - avg_ref).max() <= tol * scale, (i, n)
+        for f in range(6):
+            s = np.abs(faces_ref[:, f]).max()
+            assert np.abs(got_f[:, f] - faces_ref[:, f]).max() <= tol * s, (i, n, f)
+        checked += 1
+    assert checked >= 12
+    srv.close()
+    for P in preds:
+        P.close()
