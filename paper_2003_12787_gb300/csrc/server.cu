@@ -274,13 +274,21 @@ struct Server {
       std::vector<int> batch;
       bool copied = false;
       std::deque<int> keep;
+      size_t batch_bytes = 0;
       while (!ready.empty() && (int)batch.size() < static_max_sets()) {
         const int i = ready.front();
+        // One batch holds at most half the pool (one simulation at least):
+        // its simulations cannot be evicted while it runs, so the other half
+        // lets the next batch be admitted, and its copies overlap this
+        // launch, instead of every batch waiting for the previous one.
+        if (!batch.empty() && slots.size() > 1 && batch_bytes + sims[i].footprint() > budget / 2)
+          break;
         ready.pop_front();
         cudaError_t ae = cudaSuccess;
         if (admit(i, protect, &copied, &ae)) {
           protect[i] = 1;
           batch.push_back(i);
+          batch_bytes += sims[i].footprint();
         } else {
           if (ae != cudaSuccess) return ae;
           keep.push_back(i);  // does not fit next to this batch: wait
