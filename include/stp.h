@@ -388,7 +388,9 @@ stp_status stp_batch_run_static_curvilinear(int nsets, const stp_batch_set* sets
  * Its scheduler retires finished batches, admits ready simulations into the
  * pool (first fit; when full, idle simulations are evicted least recently
  * used first and their state copied back to pinned host memory), and launches
- * up to 128 ready resident simulations per free slot: the FP64 ones as one
+ * up to 128 ready resident simulations per free slot, whose footprints add up
+ * to at most half the budget when slots > 1 (one simulation at least), so the
+ * next batch is admitted while one runs: the FP64 ones as one
  * persistent batched launch, the others (curvilinear, or another precision)
  * each with its own kernel on the same stream; requests that arrive while
  * others run join the next launch and launches on different slots overlap on
