@@ -655,14 +655,17 @@ def run_gpu(args):
         barrier(world)
         t0 = time.perf_counter()
         ke = max(1, min(args.steps, 5))
+        call_ms = []
         for _ in range(ke):
+            tc = time.perf_counter()
             P.predict_host(qh, ph, out=(ah, fh), metric=mh)
+            call_ms.append(round((time.perf_counter() - tc) * 1e3, 2))
         e2e_s = max_over_ranks(time.perf_counter() - t0, world, dev)
         e2e = {"value": E * ke * world / e2e_s, "unit": UNIT,
                "h2d_bytes_per_step": int(qh.numel() * 8 + ph.numel() * 8 +
                                          (mh.numel() * 8 if curv else 0)),
                "d2h_bytes_per_step": int(ah.numel() * 8 + fh.numel() * 8),
-               "steps": ke}
+               "steps": ke, "ms_per_call": call_ms}
         if not np.array_equal(ah[:4].numpy(), avg[:4].cpu().numpy()):
             e2e["mismatch_vs_device_path"] = True
 
