@@ -492,6 +492,44 @@ def batched_measurement(stp, torch, args):
     return out
 
 
+def copy_bound(torch, dev, host_in, host_out, reps=3):
+    """The host-link side of the e2e roofline: the step's own pinned buffers
+    copied in (host to device) and out (device to host), each direction
+    alone and both at once on two streams (best of `reps`)."""
+    d_in = [torch.empty_like(t, device=dev) for t in host_in]
+    d_out = [torch.empty_like(t, device=dev) for t in host_out]
+    s_in, s_out = torch.cuda.Stream(dev), torch.cuda.Stream(dev)
+
+    def h2d():
+        with torch.cuda.stream(s_in):
+            for d, h in zip(d_in, host_in):
+                d.copy_(h, non_blocking=True)
+
+    def d2h():
+        with torch.cuda.stream(s_out):
+            for h, d in zip(host_out, d_out):
+                h.copy_(d, non_blocking=True)
+
+    def best(fns):
+        t = float("inf")
+        for _ in range(reps + 1):
+            torch.cuda.synchronize(dev)
+            t0 = time.perf_counter()
+            for f in fns:
+                f()
+            torch.cuda.synchronize(dev)
+            t = min(t, time.perf_counter() - t0)
+        return t
+
+    b_in = sum(t.numel() * t.element_size() for t in host_in)
+    b_out = sum(t.numel() * t.element_size() for t in host_out)
+    t_in, t_out, t_both = best([h2d]), best([d2h]), best([h2d, d2h])
+    del d_in, d_out
+    return {"h2d_gbs": b_in / t_in / 1e9, "d2h_gbs": b_out / t_out / 1e9,
+            "both_ms": t_both * 1e3, "note": "pinned copies of one step's inputs and outputs; "
+            "the e2e step cannot beat max(kernel time, both_ms)"}
+
+
 def served_measurement(stp, torch, args):
     """The served workload: 256 simulations (orders 3-9, N=4..10, element
     counts log-uniform in [64, args.served_emax], seed 1005, state and
@@ -668,6 +706,7 @@ def run_gpu(args):
                "steps": ke, "ms_per_call": call_ms}
         if not np.array_equal(ah[:4].numpy(), avg[:4].cpu().numpy()):
             e2e["mismatch_vs_device_path"] = True
+        e2e["copy_bound"] = copy_bound(torch, dev, [qh, ph] + ([mh] if curv else []), [ah, fh])
 
     extras = rank == 0 and world == 1 and not curv
     mixed = variants7 = None
