@@ -40,6 +40,7 @@
 #include <thread>
 #include <vector>
 
+#include "pool.h"
 #include "stp_internal.h"
 
 namespace stp {
@@ -47,56 +48,9 @@ namespace {
 
 using Clock = std::chrono::steady_clock;
 
-constexpr size_t kAlign = 256;
+constexpr size_t kAlign = kPoolAlign;
 
-size_t align_up(size_t x) { return (x + kAlign - 1) & ~(kAlign - 1); }
-
-// First-fit sub-allocator over [0, size) with coalescing.
-class Pool {
- public:
-  void reset(size_t size) {
-    free_.clear();
-    if (size) free_[0] = size;
-    used_ = 0;
-  }
-  bool alloc(size_t n, size_t* off) {
-    n = align_up(n);
-    for (auto it = free_.begin(); it != free_.end(); ++it) {
-      if (it->second >= n) {
-        *off = it->first;
-        const size_t rest = it->second - n;
-        const size_t start = it->first + n;
-        free_.erase(it);
-        if (rest) free_[start] = rest;
-        used_ += n;
-        return true;
-      }
-    }
-    return false;
-  }
-  void release(size_t off, size_t n) {
-    n = align_up(n);
-    used_ -= n;
-    auto it = free_.emplace(off, n).first;
-    auto next = std::next(it);
-    if (next != free_.end() && it->first + it->second == next->first) {
-      it->second += next->second;
-      free_.erase(next);
-    }
-    if (it != free_.begin()) {
-      auto prev = std::prev(it);
-      if (prev->first + prev->second == it->first) {
-        prev->second += it->second;
-        free_.erase(it);
-      }
-    }
-  }
-  size_t used() const { return used_; }
-
- private:
-  std::map<size_t, size_t> free_;
-  size_t used_ = 0;
-};
+size_t align_up(size_t x) { return pool_align_up(x); }
 
 struct Request {
   int64_t id;      // index in the caller's trace (or submit order)

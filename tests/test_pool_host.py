@@ -1,0 +1,60 @@
+"""Host logic of the served loop: the first-fit device-pool sub-allocator
+(csrc/pool.h, plain C++) compiled with g++ and checked by tests/c/pool_check.cpp
+against a byte map of the pool under seeded random allocations and releases
+(first-fit offsets, no overlap, alignment, used bytes, full merge on release).
+No GPU involved."""
+from __future__ import annotations
+
+import os
+import shutil
+import subprocess
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def test_first_fit_pool_against_a_byte_map(tmp_path):
+    if shutil.which("g++") is None:
+        pytest.skip("g++ not available")
+    exe = tmp_path / "pool_check"
+    subprocess.run(["g++", "-std=c++17", "-O1", "-Wall", "-Wextra", "-Werror",
+                    "-I", os.path.join(ROOT, "paper_2003_12787_gb300", "csrc"),
+                    os.path.join(ROOT, "tests", "c", "pool_check.cpp"), "-o", str(exe)],
+                   check=True)
+    r = subprocess.run([str(exe)], capture_output=True, text=True, timeout=120)
+    assert r.returncode == 0, r.stdout + r.stderr
+    assert r.stdout.startswith("ok ")
+
+
+# Plausible mistakes in the allocator; the byte-map check must catch each.
+MUTANTS = {
+    "no merge with the next free block":
+        ("if (next != free_.end() && it->first + it->second == next->first) {", "if (false) {"),
+    "no merge with the previous free block":
+        ("if (prev->first + prev->second == it->first) {", "if (false) {"),
+    "alloc without rounding up": ("n = pool_align_up(n);\n    for", "for"),
+    "release does not return the bytes": ("used_ -= n;", ""),
+    "block carved from the end of the free run":
+        ("*off = it->first;\n        const size_t rest = it->second - n;\n"
+         "        const size_t start = it->first + n;\n        free_.erase(it);\n"
+         "        if (rest) free_[start] = rest;",
+         "*off = it->first + it->second - n;\n        it->second -= n;\n"
+         "        if (!it->second) free_.erase(it);"),
+}
+
+
+@pytest.mark.parametrize("name", sorted(MUTANTS))
+def test_planted_allocator_mistakes_are_caught(tmp_path, name):
+    if shutil.which("g++") is None:
+        pytest.skip("g++ not available")
+    src = open(os.path.join(ROOT, "paper_2003_12787_gb300", "csrc", "pool.h")).read()
+    old, new = MUTANTS[name]
+    assert src.count(old) >= 1, name
+    (tmp_path / "pool.h").write_text(src.replace(old, new, 1))
+    exe = tmp_path / "pool_check"
+    subprocess.run(["g++", "-std=c++17", "-O1", "-I", str(tmp_path),
+                    os.path.join(ROOT, "tests", "c", "pool_check.cpp"), "-o", str(exe)],
+                   check=True)
+    r = subprocess.run([str(exe)], capture_output=True, text=True, timeout=120)
+    assert r.returncode != 0 and "mismatch" in r.stdout, (name, r.stdout)
