@@ -74,3 +74,39 @@ def test_recipes_are_reproducible_and_cartesian_for_zero_amplitude():
     assert torch.equal(c.metric, torch.eye(3, dtype=torch.float64).expand_as(c.metric) / c.h)
     r1, r2 = inputs.batched_sets_recipe(), inputs.batched_sets_recipe()
     assert r1 == r2 and len(r1) == 64
+
+
+def test_workloads_follow_their_stated_distributions():
+    """Material, time step, plane waves, set sizes and arrivals: the ranges
+    and formulas the workload descriptions state."""
+    prob = inputs.small_case()
+    N, E = prob.N, prob.E
+    assert (N, E, prob.h, prob.grid) == (4, 512, 1.0 / 8, (8, 8, 8))
+    rho, cp, cs = (prob.params[..., i].numpy() for i in range(3))
+    assert rho.min() >= 2.0 and rho.max() <= 3.0 and cp.min() >= 4.0 and cp.max() <= 6.0
+    assert np.abs(cs * math.sqrt(3.0) - cp).max() <= 1e-14 * cp.max()
+    # the draws fill their ranges (2048 and more samples each)
+    assert rho.max() - rho.min() > 0.95 and cp.max() - cp.min() > 1.9
+    assert prob.dt == 0.4 * prob.h / ((2 * N - 1) * cp.max())
+    k, amp, phase = inputs.wave_parameters(1002)
+    assert k.shape == (4, 3) and amp.shape == (4, 9) and phase.shape == (4, 9)
+    assert np.linalg.norm(k, axis=1).max() <= 2 * math.pi
+    assert amp.min() >= 0.5 and amp.max() <= 1.0 and phase.min() >= 0 and phase.max() < 2 * math.pi
+    assert np.abs(prob.q.numpy()).max() <= amp.sum(axis=0).max() + 1e-12
+    for recipe, n_sets, n_range, e_range in ((inputs.batched_sets_recipe(), 64, (4, 12), (64, 16384)),
+                                             (inputs.served_recipe(e_max=2048), 256, (4, 10), (64, 2048))):
+        assert len(recipe) == n_sets
+        Ns = np.array([r["N"] for r in recipe])
+        Es = np.array([r["E"] for r in recipe])
+        assert Ns.min() == n_range[0] and Ns.max() == n_range[1]
+        assert Es.min() >= e_range[0] and Es.max() <= e_range[1]
+        # log-uniform sizes: the median sits near the geometric mean of the range
+        gm = math.sqrt(e_range[0] * e_range[1])
+        assert gm / 2.5 < np.median(Es) < gm * 2.5
+        for r in recipe:
+            G = r["grid"][0]
+            assert G ** 3 >= r["E"] > (G - 1) ** 3 and r["h"] == 1.0 / G
+    t, ids = inputs.served_arrivals(20000, rate=2000.0, n_sims=256, seed=1006)
+    gaps = np.diff(np.concatenate([[0.0], t]))
+    assert np.all(gaps > 0) and abs(gaps.mean() * 2000.0 - 1.0) < 0.03
+    assert ids.min() == 0 and ids.max() == 255
