@@ -198,3 +198,40 @@ def test_binding_precision_names_match_the_header_enum():
 def test_set_precision_rejects_null_handle(lib):
     assert lib.stp_set_precision(None, 0) == _binding.STP_ERR_INVALID_ARG
     assert lib.stp_get_precision(None) == 0
+
+
+def test_server_and_batch_entries_reject_bad_arguments_before_the_gpu(lib):
+    """Every served and batched entry point checks its handle and arguments
+    before any CUDA call; NULL handles are no-ops for the destroy calls."""
+    bad = _binding.STP_ERR_INVALID_ARG
+    out = ctypes.c_void_p()
+    assert lib.stp_server_create(1 << 20, 1, None) == bad
+    assert lib.stp_server_create(0, 1, ctypes.byref(out)) == bad and not out.value
+    assert lib.stp_server_create(-5, 1, ctypes.byref(out)) == bad
+    assert lib.stp_server_create(1 << 20, 0, ctypes.byref(out)) == bad
+    assert lib.stp_server_create(1 << 20, 9, ctypes.byref(out)) == bad
+    sid, n = ctypes.c_int(), ctypes.c_int()
+    steps = ctypes.c_int64()
+    stats = (ctypes.c_int64 * 16)()
+    assert lib.stp_server_add_sim(None, None, 1, None, None, ctypes.byref(sid)) == bad
+    assert lib.stp_server_submit(None, 0) == bad
+    assert lib.stp_server_progress(None, ctypes.byref(n)) == bad
+    assert lib.stp_server_drain(None) == bad
+    assert lib.stp_server_run_trace(None, 0, None, None, None, None) == bad
+    assert lib.stp_server_read(None, 0, None, None, ctypes.byref(steps)) == bad
+    assert lib.stp_server_stats(None, stats) == bad
+    assert lib.stp_server_destroy(None) == _binding.STP_OK
+    assert lib.stp_batch_create(1, None, ctypes.byref(out)) == bad
+    assert lib.stp_batch_create(-1, None, ctypes.byref(out)) == bad
+    assert lib.stp_batch_create(0, None, None) == bad
+    assert lib.stp_batch_launch(None, None) == bad
+    assert lib.stp_batch_info(None, None, None, None) == bad
+    assert lib.stp_batch_destroy(None) == _binding.STP_OK
+    sets = (ctypes.c_byte * (129 * 256))()  # contents never read: the count is checked first
+    assert lib.stp_batch_run_static(129, sets, None) == bad
+    assert lib.stp_batch_run_static(-1, None, None) == bad
+    assert lib.stp_batch_run_static(1, None, None) == bad
+    assert lib.stp_measure_fp64_peak(None, None) == bad
+    # the message of the last failure names the problem
+    assert lib.stp_server_create(1 << 20, 0, ctypes.byref(out)) == bad
+    assert b"slots" in lib.stp_last_error()
