@@ -41,6 +41,7 @@
 #include <vector>
 
 #include "pool.h"
+#include "serve_policy.h"
 #include "stp_internal.h"
 
 namespace stp {
@@ -153,14 +154,7 @@ struct Server {
     size_t off = 0;
     while (!pool.alloc(s.footprint(), &off)) {
       // least recently used idle resident simulation, preferring ones without requests
-      int victim = -1;
-      for (int pass = 0; pass < 2 && victim < 0; ++pass)
-        for (int j = 0; j < (int)sims.size(); ++j) {
-          const Sim& c = sims[j];
-          if (!c.resident || c.busy || protect[j] || j == i) continue;
-          if (pass == 0 && !c.pending.empty()) continue;
-          if (victim < 0 || c.last_used < sims[victim].last_used) victim = j;
-        }
+      const int victim = choose_victim(sims, protect, i);
       if (victim < 0) return false;
       if ((*err = evict(victim)) != cudaSuccess) return false;
     }
@@ -231,11 +225,8 @@ struct Server {
       size_t batch_bytes = 0;
       while (!ready.empty() && (int)batch.size() < static_max_sets()) {
         const int i = ready.front();
-        // One batch holds at most half the pool (one simulation at least):
-        // its simulations cannot be evicted while it runs, so the other half
-        // lets the next batch be admitted, and its copies overlap this
-        // launch, instead of every batch waiting for the previous one.
-        if (!batch.empty() && slots.size() > 1 && batch_bytes + sims[i].footprint() > budget / 2)
+        // at most half the pool per batch, so the next one is admitted meanwhile
+        if (!batch_has_room(batch.size(), batch_bytes, sims[i].footprint(), slots.size(), budget))
           break;
         ready.pop_front();
         cudaError_t ae = cudaSuccess;

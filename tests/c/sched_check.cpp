@@ -1,0 +1,86 @@
+// Host check of the served scheduler's policy rules (serve_policy.h): the eviction
+// victim against a brute-force reading of the rule over seeded random
+// simulation tables, and the half-pool batch bound on its cases.
+// Prints "ok <cases>" and exits 0, or the first mismatch and exits 1.
+#include <cstdint>
+#include <cstdio>
+#include <deque>
+#include <vector>
+
+#include "serve_policy.h"
+
+namespace {
+
+struct SimRec {
+  bool resident = false, busy = false;
+  std::deque<int> pending;
+  int64_t last_used = 0;
+};
+
+uint64_t state = 0x2545F4914F6CDD1Dull;
+uint64_t next_u64() {  // xorshift64*
+  state ^= state >> 12;
+  state ^= state << 25;
+  state ^= state >> 27;
+  return state * 0x2545F4914F6CDD1Dull;
+}
+
+// The rule read literally: candidates are resident, idle, unprotected and not
+// the excluded one; prefer those without requests; the smallest tick wins,
+// the lower index on a tie.
+int expected_victim(const std::vector<SimRec>& s, const std::vector<char>& prot, int ex) {
+  for (int want_idle_queue = 1; want_idle_queue >= 0; --want_idle_queue) {
+    int best = -1;
+    for (int j = 0; j < (int)s.size(); ++j) {
+      if (!s[j].resident || s[j].busy || prot[j] || j == ex) continue;
+      if (want_idle_queue && !s[j].pending.empty()) continue;
+      if (best < 0 || s[j].last_used < s[best].last_used) best = j;
+    }
+    if (best >= 0) return best;
+  }
+  return -1;
+}
+
+}  // namespace
+
+int main() {
+  int cases = 0;
+  for (int t = 0; t < 20000; ++t) {
+    const int n = 1 + (int)(next_u64() % 12);
+    std::vector<SimRec> sims((size_t)n);
+    std::vector<char> prot((size_t)n, 0);
+    for (int j = 0; j < n; ++j) {
+      sims[j].resident = next_u64() % 4 != 0;
+      sims[j].busy = next_u64() % 4 == 0;
+      if (next_u64() % 2) sims[j].pending.push_back(1);
+      sims[j].last_used = (int64_t)(next_u64() % 8);  // ties on purpose
+      prot[j] = next_u64() % 5 == 0;
+    }
+    const int ex = (int)(next_u64() % (uint64_t)(n + 1)) - 1;  // -1: nothing excluded
+    const int got = stp::choose_victim(sims, prot, ex);
+    const int want = expected_victim(sims, prot, ex);
+    if (got != want) {
+      std::printf("mismatch: victim %d, expected %d (case %d)\n", got, want, t);
+      return 1;
+    }
+    ++cases;
+  }
+  struct { size_t size, bytes, add, slots, budget; bool room; } b[] = {
+      {0, 0, 900, 3, 1000, true},     // an empty batch takes anything, even > budget/2
+      {1, 400, 100, 3, 1000, true},   // 500 <= 500
+      {1, 400, 101, 3, 1000, false},  // 501 > 500
+      {5, 499, 2, 2, 1000, false},
+      {5, 900, 900, 1, 1000, true},   // one slot: no bound
+      {2, 0, 0, 8, 0, true},
+  };
+  for (const auto& c : b) {
+    if (stp::batch_has_room(c.size, c.bytes, c.add, c.slots, c.budget) != c.room) {
+      std::printf("mismatch: batch bound (%zu, %zu, %zu, %zu, %zu)\n", c.size, c.bytes, c.add,
+                  c.slots, c.budget);
+      return 1;
+    }
+    ++cases;
+  }
+  std::printf("ok %d\n", cases);
+  return 0;
+}

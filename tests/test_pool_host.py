@@ -1,8 +1,10 @@
-"""Host logic of the served loop: the first-fit device-pool sub-allocator
-(csrc/pool.h, plain C++) compiled with g++ and checked by tests/c/pool_check.cpp
-against a byte map of the pool under seeded random allocations and releases
-(first-fit offsets, no overlap, alignment, used bytes, full merge on release).
-No GPU involved."""
+"""Host logic of the served loop, compiled with g++ (no GPU involved): the
+first-fit device-pool sub-allocator (csrc/pool.h), checked by
+tests/c/pool_check.cpp against a byte map of the pool under seeded random
+allocations and releases (first-fit offsets, no overlap, alignment, used
+bytes, full merge on release); and the scheduler's policy rules
+(csrc/serve_policy.h: eviction victim, half-pool batch bound), checked by
+tests/c/sched_check.cpp."""
 from __future__ import annotations
 
 import os
@@ -58,3 +60,41 @@ def test_planted_allocator_mistakes_are_caught(tmp_path, name):
                    check=True)
     r = subprocess.run([str(exe)], capture_output=True, text=True, timeout=120)
     assert r.returncode != 0 and "mismatch" in r.stdout, (name, r.stdout)
+
+
+def _compile_and_run(tmp_path, source, include_dir, werror=True):
+    exe = tmp_path / "check"
+    flags = ["-Wall", "-Wextra"] + (["-Werror"] if werror else [])
+    subprocess.run(["g++", "-std=c++17", "-O1", *flags, "-I", include_dir,
+                    os.path.join(ROOT, "tests", "c", source), "-o", str(exe)], check=True)
+    return subprocess.run([str(exe)], capture_output=True, text=True, timeout=120)
+
+
+def test_scheduler_rules_against_their_literal_reading(tmp_path):
+    if shutil.which("g++") is None:
+        pytest.skip("g++ not available")
+    r = _compile_and_run(tmp_path, "sched_check.cpp",
+                         os.path.join(ROOT, "paper_2003_12787_gb300", "csrc"))
+    assert r.returncode == 0 and r.stdout.startswith("ok "), r.stdout + r.stderr
+
+
+SCHED_MUTANTS = {
+    "busy simulations may be evicted": ("c.busy || ", ""),
+    "no preference for simulations without requests":
+        ("if (pass == 0 && !c.pending.empty()) continue;", ""),
+    "most recently used instead of least": ("c.last_used < sims[victim].last_used",
+                                            "c.last_used > sims[victim].last_used"),
+    "no half-pool bound": ("return batch_bytes + bytes <= budget / 2;", "return true;"),
+}
+
+
+@pytest.mark.parametrize("name", sorted(SCHED_MUTANTS))
+def test_planted_scheduler_mistakes_are_caught(tmp_path, name):
+    if shutil.which("g++") is None:
+        pytest.skip("g++ not available")
+    src = open(os.path.join(ROOT, "paper_2003_12787_gb300", "csrc", "serve_policy.h")).read()
+    old, new = SCHED_MUTANTS[name]
+    assert old in src, name
+    (tmp_path / "serve_policy.h").write_text(src.replace(old, new, 1))
+    r = _compile_and_run(tmp_path, "sched_check.cpp", str(tmp_path), werror=False)
+    assert r.returncode != 0 and "mismatch" in r.stdout, (name, r.stdout + r.stderr)
