@@ -829,7 +829,7 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
-def main():
+def build_parser():
     ap = argparse.ArgumentParser(description=__doc__.splitlines()[0])
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=20)
@@ -871,7 +871,11 @@ def main():
                     help="seconds of oracle time for cpu_baseline")
     ap.add_argument("--reference-sample", type=int, default=1024,
                     help="elements per step of the reference arm")
-    args = ap.parse_args()
+    return ap
+
+
+def main():
+    args = build_parser().parse_args()
     if args.warmup < 3 and args.impl == "gpu":
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)
     if args.impl == "reference":
