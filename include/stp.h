@@ -400,6 +400,12 @@ stp_status stp_batch_run_static_curvilinear(int nsets, const stp_batch_set* sets
  */
 typedef struct stp_server_s* stp_server;
 
+/* Create a server on the current device: hbm_budget_bytes (> 0) is the size
+ * of its device pool, allocated here; slots in [1, 8] is the number of
+ * batches in flight. *out receives the server (NULL on failure), released
+ * with stp_server_destroy. STP_ERR_INVALID_ARG for a NULL out, a budget <= 0
+ * or slots outside [1, 8] (checked before any CUDA call); STP_ERR_OOM or
+ * STP_ERR_CUDA when the pool or a stream cannot be made. */
 stp_status stp_server_create(int64_t hbm_budget_bytes, int slots, stp_server* out);
 
 /* Register a simulation: the handle gives its order, dx, dt and precision;
