@@ -235,3 +235,22 @@ def test_server_and_batch_entries_reject_bad_arguments_before_the_gpu(lib):
     # the message of the last failure names the problem
     assert lib.stp_server_create(1 << 20, 0, ctypes.byref(out)) == bad
     assert b"slots" in lib.stp_last_error()
+
+
+def test_every_entry_point_is_documented_in_the_header():
+    """Each declaration in include/stp.h follows a comment (its own, or the
+    block that documents a group of related calls declared together)."""
+    lines = open(os.path.join(ROOT, "include", "stp.h")).read().splitlines()
+    decl = re.compile(r"^(stp_status|const char\*|int|void|double|int64_t) (stp_\w+)\(")
+    cont = re.compile(r"^\s+\S.*[,;)]\s*$")  # continuation lines of a declaration
+    undocumented = []
+    for i, line in enumerate(lines):
+        m = decl.match(line)
+        if not m:
+            continue
+        j = i - 1
+        while j >= 0 and (not lines[j].strip() or decl.match(lines[j]) or cont.match(lines[j])):
+            j -= 1
+        if j < 0 or not lines[j].rstrip().endswith("*/"):
+            undocumented.append(m.group(2))
+    assert not undocumented, undocumented
