@@ -254,3 +254,27 @@ def test_every_entry_point_is_documented_in_the_header():
         if j < 0 or not lines[j].rstrip().endswith("*/"):
             undocumented.append(m.group(2))
     assert not undocumented, undocumented
+
+
+def test_product_and_oracle_share_no_code():
+    """The product (package, CUDA sources, header) never imports, includes or
+    links the oracle, and the oracle never imports the product."""
+    pkg = os.path.join(ROOT, "paper_2003_12787_gb300")
+    for path in glob_sources(pkg) + [os.path.join(ROOT, "include", "stp.h")]:
+        text = open(path).read()
+        assert not re.search(r"^\s*(import|from)\s+oracle\b", text, re.M), path
+        assert not re.search(r"#\s*include\s*[<\"][^>\"]*oracle", text), path
+        assert "stp_oracle" not in text, path
+    for name in ("__init__.py", "stp_oracle.c"):
+        text = open(os.path.join(ROOT, "oracle", name)).read()
+        assert not re.search(r"^\s*(import|from)\s+paper_2003_12787_gb300", text, re.M), name
+        assert not re.search(r"#\s*include\s*[<\"][^>\"]*(stp\.h|csrc)", text), name
+    assert "TEST INFRASTRUCTURE ONLY" in open(os.path.join(ROOT, "oracle", "__init__.py")).read()
+
+
+def glob_sources(pkg):
+    out = []
+    for d, _, files in os.walk(pkg):
+        out += [os.path.join(d, f) for f in files
+                if f.endswith((".py", ".cu", ".cuh", ".h", ".cpp"))]
+    return out
