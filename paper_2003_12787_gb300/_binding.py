@@ -171,9 +171,30 @@ def stp_destroy(h: int | None) -> None:
     _check(load().stp_destroy(h), "stp_destroy")
 
 
+def _host_f64(x, n: int, name: str):
+    """A host output buffer the library writes n doubles into: float64,
+    C-contiguous, at least n elements (None passes through)."""
+    if x is None:
+        return None
+    dtype = getattr(x, "dtype", None)
+    ok_dtype = str(dtype) in ("float64", "torch.float64")
+    contiguous = x.is_contiguous() if hasattr(x, "is_contiguous") else x.flags["C_CONTIGUOUS"]
+    size = x.numel() if hasattr(x, "numel") else x.size
+    if getattr(x, "is_cuda", False):
+        raise ValueError(f"{name} must be a host buffer")
+    if not ok_dtype or not contiguous or size < n:
+        raise ValueError(f"{name} must be a C-contiguous float64 buffer of at least {n} "
+                         f"elements (got {dtype}, {size} elements, contiguous={contiguous})")
+    return x
+
+
 def stp_reference_tables(order: int, nodes=None, D=None, phi0=None, phi1=None,
                          family="gl") -> None:
     fam = NODE_FAMILIES[family] if isinstance(family, str) else int(family)
+    N = int(order) + 1
+    if N >= 1:
+        nodes, D = _host_f64(nodes, N, "nodes"), _host_f64(D, N * N, "D")
+        phi0, phi1 = _host_f64(phi0, N, "phi0"), _host_f64(phi1, N, "phi1")
     _check(load().stp_reference_tables_nodes(order, fam, _ptr(nodes), _ptr(D), _ptr(phi0),
                                              _ptr(phi1)), "stp_reference_tables_nodes")
 

@@ -278,3 +278,17 @@ def glob_sources(pkg):
         out += [os.path.join(d, f) for f in files
                 if f.endswith((".py", ".cu", ".cuh", ".h", ".cpp"))]
     return out
+
+
+def test_reference_tables_binding_checks_its_buffers(lib):
+    """The binding refuses output buffers the library would overrun or
+    misread (wrong dtype, too short, not contiguous) before calling it."""
+    N = 5
+    for bad in (np.zeros(N, dtype=np.float32), np.zeros(N - 1), np.zeros(2 * N)[::2]):
+        with pytest.raises(ValueError):
+            stp.stp_reference_tables(N - 1, bad)
+    with pytest.raises(ValueError):
+        stp.stp_reference_tables(N - 1, np.zeros(N), np.zeros(N * N - 1))
+    xi, D = np.zeros(N), np.zeros((N, N))
+    stp.stp_reference_tables(N - 1, xi, D)
+    assert np.all(np.diff(xi) > 0) and np.abs(D.sum(axis=1)).max() < 1e-12  # D 1 = 0
