@@ -171,20 +171,19 @@ def stp_destroy(h: int | None) -> None:
     _check(load().stp_destroy(h), "stp_destroy")
 
 
-def _host_f64(x, n: int, name: str):
-    """A host output buffer the library writes n doubles into: float64,
-    C-contiguous, at least n elements (None passes through)."""
+def _host_buf(x, n: int, name: str, dtype: str = "float64"):
+    """A host buffer the library reads or writes n elements of: the given
+    dtype, C-contiguous, at least n elements (None passes through)."""
     if x is None:
         return None
-    dtype = getattr(x, "dtype", None)
-    ok_dtype = str(dtype) in ("float64", "torch.float64")
+    got = str(getattr(x, "dtype", None)).replace("torch.", "")
     contiguous = x.is_contiguous() if hasattr(x, "is_contiguous") else x.flags["C_CONTIGUOUS"]
     size = x.numel() if hasattr(x, "numel") else x.size
     if getattr(x, "is_cuda", False):
         raise ValueError(f"{name} must be a host buffer")
-    if not ok_dtype or not contiguous or size < n:
-        raise ValueError(f"{name} must be a C-contiguous float64 buffer of at least {n} "
-                         f"elements (got {dtype}, {size} elements, contiguous={contiguous})")
+    if got != dtype or not contiguous or size < n:
+        raise ValueError(f"{name} must be a C-contiguous {dtype} buffer of at least {n} "
+                         f"elements (got {got}, {size} elements, contiguous={contiguous})")
     return x
 
 
@@ -193,8 +192,8 @@ def stp_reference_tables(order: int, nodes=None, D=None, phi0=None, phi1=None,
     fam = NODE_FAMILIES[family] if isinstance(family, str) else int(family)
     N = int(order) + 1
     if N >= 1:
-        nodes, D = _host_f64(nodes, N, "nodes"), _host_f64(D, N * N, "D")
-        phi0, phi1 = _host_f64(phi0, N, "phi0"), _host_f64(phi1, N, "phi1")
+        nodes, D = _host_buf(nodes, N, "nodes"), _host_buf(D, N * N, "D")
+        phi0, phi1 = _host_buf(phi0, N, "phi0"), _host_buf(phi1, N, "phi1")
     _check(load().stp_reference_tables_nodes(order, fam, _ptr(nodes), _ptr(D), _ptr(phi0),
                                              _ptr(phi1)), "stp_reference_tables_nodes")
 
@@ -404,6 +403,10 @@ def stp_server_drain(srv: int) -> None:
 
 def stp_server_run_trace(srv: int, t_arrival, sim_ids, latency) -> float:
     """t_arrival float64[n] (sorted, seconds), sim_ids int32[n], latency float64[n] out."""
+    n = len(t_arrival)
+    _host_buf(t_arrival, n, "t_arrival")
+    _host_buf(sim_ids, n, "sim_ids", "int32")
+    _host_buf(latency, n, "latency")
     wall = ctypes.c_double()
     _check(load().stp_server_run_trace(srv, len(t_arrival), _ptr(t_arrival), _ptr(sim_ids),
                                        _ptr(latency), ctypes.byref(wall)), "stp_server_run_trace")

@@ -292,3 +292,17 @@ def test_reference_tables_binding_checks_its_buffers(lib):
     xi, D = np.zeros(N), np.zeros((N, N))
     stp.stp_reference_tables(N - 1, xi, D)
     assert np.all(np.diff(xi) > 0) and np.abs(D.sum(axis=1)).max() < 1e-12  # D 1 = 0
+
+
+def test_run_trace_binding_checks_its_buffers(lib):
+    """A trace whose arrays have the wrong dtype or length is refused before
+    the library reads them (the server handle is never touched)."""
+    t = np.linspace(0.0, 1.0, 4)
+    ids = np.zeros(4, dtype=np.int32)
+    lat = np.zeros(4)
+    for args in ((t.astype(np.float32), ids, lat), (t, ids.astype(np.int64), lat),
+                 (t, ids, np.zeros(3)), (t, ids[:3], lat)):
+        with pytest.raises(ValueError):
+            stp.stp_server_run_trace(None, *args)
+    with pytest.raises(stp.STPError):  # well-formed arrays reach the library: NULL server
+        stp.stp_server_run_trace(None, t, ids, lat)
