@@ -306,3 +306,33 @@ def test_run_trace_binding_checks_its_buffers(lib):
             stp.stp_server_run_trace(None, *args)
     with pytest.raises(stp.STPError):  # well-formed arrays reach the library: NULL server
         stp.stp_server_run_trace(None, t, ids, lat)
+
+
+@pytest.mark.parametrize("std,lang,compiler", [("c99", "c", "gcc"), ("c11", "c", "gcc"),
+                                               ("c++17", "c++", "g++")])
+def test_header_stands_alone_in_c_and_cpp(tmp_path, std, lang, compiler):
+    """include/stp.h needs no CUDA or torch header: it compiles on its own as
+    C99, C11 and C++17 with warnings as errors."""
+    import shutil
+    import subprocess
+    if shutil.which(compiler) is None:
+        pytest.skip(f"{compiler} not available")
+    subprocess.run([compiler, f"-std={std}", "-fsyntax-only", "-Wall", "-Wextra", "-Werror",
+                    "-pedantic", "-x", lang, os.path.join(ROOT, "include", "stp.h")], check=True)
+
+
+def test_plain_c_user_links_against_the_library_alone(lib, tmp_path):
+    """The C example (tests/c/abi_host_predict.c) compiles with gcc and links
+    against the library with no CUDA, torch or Python flags (it runs in the
+    GPU tests)."""
+    import shutil
+    import subprocess
+    if shutil.which("gcc") is None:
+        pytest.skip("gcc not available")
+    so = build.LIB
+    exe = tmp_path / "abi_host_predict"
+    subprocess.run(["gcc", "-O2", "-std=c11", "-Wall", "-Werror", "-I", os.path.join(ROOT, "include"),
+                    os.path.join(ROOT, "tests", "c", "abi_host_predict.c"), "-o", str(exe),
+                    "-L", os.path.dirname(so), "-l:" + os.path.basename(so),
+                    "-Wl,-rpath," + os.path.dirname(so)], check=True)
+    assert exe.exists()
