@@ -336,3 +336,33 @@ def test_plain_c_user_links_against_the_library_alone(lib, tmp_path):
                     "-L", os.path.dirname(so), "-l:" + os.path.basename(so),
                     "-Wl,-rpath," + os.path.dirname(so)], check=True)
     assert exe.exists()
+
+
+@pytest.mark.parametrize("family,Ns", [("gl", range(1, 13)), ("gll", range(2, 13))])
+def test_library_tables_have_the_symmetry_the_even_odd_kernels_use(lib, family, Ns):
+    """Both node families are symmetric about 1/2, so the library's D is
+    centro-antisymmetric (D[N-1-i][N-1-l] = -D[i][l]) and phi(1) mirrors
+    phi(0); on such a D the even-odd split (sums and differences of mirrored
+    values against the even and odd halves of D) reproduces D u."""
+    rng = np.random.default_rng(7)
+    for N in Ns:
+        xi, D, p0, p1 = np.zeros(N), np.zeros((N, N)), np.zeros(N), np.zeros(N)
+        stp.stp_reference_tables(N - 1, xi, D, p0, p1, family=family)
+        scale = max(1.0, np.abs(D).max())
+        assert np.abs(xi + xi[::-1] - 1.0).max() <= 2e-16, N
+        assert np.abs(D[::-1, ::-1] + D).max() <= 4e-15 * scale, N
+        assert np.abs(p1 - p0[::-1]).max() <= 4e-16, N
+        u = rng.standard_normal(N)
+        h = N // 2
+        e = u[:h] + u[::-1][:h]
+        o = u[:h] - u[::-1][:h]
+        Dv = np.empty(N)
+        for i in range(h):
+            E_i = (D[i, :h] + D[i, ::-1][:h]) / 2
+            O_i = (D[i, :h] - D[i, ::-1][:h]) / 2
+            P = E_i @ e + (D[i, h] * u[h] if N % 2 else 0.0)
+            Q = O_i @ o
+            Dv[i], Dv[N - 1 - i] = P + Q, Q - P
+        if N % 2:
+            Dv[h] = ((D[h, :h] - D[h, ::-1][:h]) / 2) @ o
+        assert np.abs(Dv - D @ u).max() <= 1e-13 * scale * np.abs(u).sum(), N
