@@ -355,8 +355,12 @@ stp_status stp_autotune(stp_handle h, int* variant, double* us_per_element,
  *   running order 11), STP_ERR_UNSUPPORTED for non-FP64 handles.
  *
  * The first call on a device looks up the array's device address (with that
- * device current) and caches it; make that first call before any stream
- * capture. Every call uses the same array and it keeps the last call's
+ * device current) and caches it together with the identity of the device's
+ * current CUDA context; make that first call before any stream capture. After
+ * cudaDeviceReset (or any new context on the device) the module can load at
+ * another address: the first call in the new context sees the changed
+ * identity and looks the address up again, so make that call before any
+ * capture as well. Every call uses the same array and it keeps the last call's
  * contents; the call clears the work counter itself. Calls whose work overlaps
  * on the GPU (other streams, or host threads racing) race on the array: order
  * them on one stream. No cudaMalloc, cudaFree or other allocating routine is

@@ -133,21 +133,86 @@ StaticShape static_shape(int N) {
   }
 }
 
-// Device address of the scratch array, looked up once per device (with that
-// device current) and cached.
-std::mutex g_addr_mutex;
-unsigned char* g_addr[64] = {};
+// Largest dynamic shared memory over every shape of the kernel. The kernel's
+// attribute is set to this one value (never to a call's own need), so calls
+// on different host threads - the allocation-free entry and the served loop
+// - cannot lower it between another call's set and its launch.
+size_t max_static_smem() {
+  size_t m = 1;
+#define X(n_, npt_, epc_, avg_, rg_) m = std::max(m, (size_t)Fp64Shape<n_, npt_, epc_, avg_>::SMEM);
+  STP_STATIC_SHAPES(X)
+#undef X
+#define X(n_, use_) m = std::max(m, (size_t)EoShape<n_>::SMEM);
+  STP_STATIC_EO(X)
+#undef X
+  return m;
+}
 
+// Identity of the calling thread's current CUDA context, through the driver
+// entry points the runtime exposes (no link-time dependency on the driver
+// library). A context created after cudaDeviceReset, or after the primary
+// context was released and retained again, gets a new identifier, and the
+// module holding the scratch array may then sit at a new address.
+typedef int (*CtxGetCurrentFn)(void**);
+typedef int (*CtxGetIdFn)(void*, unsigned long long*);
+std::once_flag g_driver_once;
+CtxGetCurrentFn g_ctx_get_current = nullptr;
+CtxGetIdFn g_ctx_get_id = nullptr;
+
+bool current_context_id(unsigned long long* id) {
+  std::call_once(g_driver_once, [] {
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess && q == cudaDriverEntryPointSuccess)
+      g_ctx_get_current = reinterpret_cast<CtxGetCurrentFn>(f);
+    f = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess && q == cudaDriverEntryPointSuccess)
+      g_ctx_get_id = reinterpret_cast<CtxGetIdFn>(f);
+    cudaGetLastError();
+  });
+  if (!g_ctx_get_current || !g_ctx_get_id) return false;
+  void* ctx = nullptr;
+  if (g_ctx_get_current(&ctx) != 0 || !ctx) return false;
+  return g_ctx_get_id(ctx, id) == 0;
+}
+
+// Per device: the context the cached address belongs to, and the address.
+struct ScratchAddr {
+  unsigned long long ctx_id = 0;
+  unsigned char* addr = nullptr;
+};
+std::mutex g_addr_mutex;
+ScratchAddr g_addr[64];
+
+// Device address of the scratch array for the current context of device
+// `dev` (which must be current). The set-up - cudaGetSymbolAddress, and the
+// kernel's shared-memory attribute - runs on the first call in each context
+// and is cached with that context's identifier; a later call in a new context
+// (after a device reset) repeats it. If the context's identity cannot be
+// read, the address is looked up on every call.
 cudaError_t scratch_address(int dev, unsigned char** out) {
   if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+  // a runtime call on the kernel makes the device's context current (creating
+  // it on first use) before its identity is read
+  cudaFuncAttributes fa;
+  cudaError_t e = cudaFuncGetAttributes(&fa, static_batch_kernel);
+  if (e != cudaSuccess) return e;
+  unsigned long long id = 0;
+  const bool have_id = current_context_id(&id);
   std::lock_guard<std::mutex> lock(g_addr_mutex);
-  if (!g_addr[dev]) {
+  ScratchAddr& c = g_addr[dev];
+  if (!have_id || !c.addr || c.ctx_id != id) {
     void* p = nullptr;
-    cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
-    if (e != cudaSuccess) return e;
-    g_addr[dev] = static_cast<unsigned char*>(p);
+    if ((e = cudaGetSymbolAddress(&p, g_static_scratch)) != cudaSuccess) return e;
+    if ((e = cudaFuncSetAttribute(static_batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)max_static_smem())) != cudaSuccess)
+      return e;
+    c.addr = static_cast<unsigned char*>(p);
+    c.ctx_id = have_id ? id : 0;
   }
-  *out = g_addr[dev];
+  *out = c.addr;
   return cudaSuccess;
 }
 
@@ -188,8 +253,10 @@ cudaError_t launch_param_batch(int nsets, const int* N, const int64_t* E, const 
   if (units == 0) return cudaSuccess;
   int sms = 0, per_sm = 0;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  // the attribute is the largest shape's, set to that one value on every call
+  // (an idempotent set, so a call on another thread cannot lower it)
   if ((e = cudaFuncSetAttribute(static_batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)smem)) != cudaSuccess)
+                                (int)max_static_smem())) != cudaSuccess)
     return e;
   if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, static_batch_kernel,
                                                          kStaticThreads, smem)) != cudaSuccess)

@@ -235,7 +235,11 @@ struct Server {
           batch.push_back(i);
           batch_bytes += sims[i].footprint();
         } else {
-          if (ae != cudaSuccess) return ae;
+          if (ae != cudaSuccess) {  // a copy failed: nothing of this batch runs
+            ready.push_front(i);
+            requeue_front(batch);
+            return ae;
+          }
           keep.push_back(i);  // does not fit next to this batch: wait
           break;
         }
@@ -243,8 +247,12 @@ struct Server {
       for (auto it = keep.rbegin(); it != keep.rend(); ++it) ready.push_front(*it);
       if (batch.empty()) break;
       if (copied) {
-        if ((e = cudaEventRecord(copy_done, copy_stream)) != cudaSuccess) return e;
-        if ((e = cudaStreamWaitEvent(sl.stream, copy_done, 0)) != cudaSuccess) return e;
+        e = cudaEventRecord(copy_done, copy_stream);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(sl.stream, copy_done, 0);
+        if (e != cudaSuccess) {
+          requeue_front(batch);
+          return e;
+        }
       }
       const int n = (int)batch.size();
       std::vector<int> N, curv;  // curv: simulations launched one by one
@@ -268,21 +276,25 @@ struct Server {
         tb.push_back(stp_handle_tables(s.handle));
       }
       int too_big = 0;
-      if ((e = cudaEventRecord(sl.start, sl.stream)) != cudaSuccess) return e;
-      if (!N.empty()) {
+      e = cudaEventRecord(sl.start, sl.stream);
+      if (e == cudaSuccess && !N.empty())
         e = launch_param_batch((int)N.size(), N.data(), E.data(), q.data(), p.data(), a.data(),
                                f.data(), tb.data(), sl.scratch, static_scratch_bytes(), sl.stream,
                                &too_big);
-        if (e != cudaSuccess) return e;
-      }
-      for (int i : curv) {
-        Sim& s = sims[i];
+      for (size_t k = 0; e == cudaSuccess && k < curv.size(); ++k) {
+        Sim& s = sims[curv[k]];
         e = stp_launch_handle(s.handle, s.E, state(s, s.cur), params(s),
                               s.bytes_metric ? metric(s) : nullptr, state(s, s.cur ^ 1), faces(s),
                               sl.stream);
-        if (e != cudaSuccess) return e;
       }
-      if ((e = cudaEventRecord(sl.done, sl.stream)) != cudaSuccess) return e;
+      if (e == cudaSuccess) e = cudaEventRecord(sl.done, sl.stream);
+      if (e != cudaSuccess) {
+        // nothing of this batch counts as launched: its simulations go back to
+        // the front of the ready queue, in their order, so drain() and later
+        // passes still see their requests
+        requeue_front(batch);
+        return e;
+      }
       sl.sims = batch;
       sl.busy = true;
       ++batches;
@@ -290,6 +302,17 @@ struct Server {
       max_batch = std::max<int64_t>(max_batch, n);
     }
     return cudaSuccess;
+  }
+
+  // Undo the marks of a batch whose launch failed: not running, queued again
+  // at the front of the ready queue in their original order.
+  void requeue_front(const std::vector<int>& batch) {
+    for (auto it = batch.rbegin(); it != batch.rend(); ++it) {
+      Sim& s = sims[*it];
+      s.busy = false;
+      ready.push_front(*it);  // batch members were taken off the queue
+      s.queued = true;
+    }
   }
 
   bool idle() const {

@@ -13,6 +13,7 @@ import numpy as np
 import pytest
 import torch
 
+import oracle
 import paper_2003_12787_gb300 as stp
 from paper_2003_12787_gb300 import _binding
 from paper_2003_12787_gb300.inputs import curvilinear_problem, elastic_problem
@@ -54,6 +55,39 @@ def test_static_batch_matches_stp_predict_on_two_calls_in_a_row():
         for (avg, faces), (ra, rf), spec in zip(outs, refs, specs):
             assert rel(avg, ra) <= TOL, (call, spec)
             assert rel(faces, rf) <= TOL, (call, spec)
+    # two sets straight against the oracle as well (order 3 whole, and order
+    # 11, the order that parks its new Taylor terms in the static array)
+    for k in (0, 1):
+        (P, prob), (avg, faces) = sets[k], outs[k]
+        a_ref, f_ref = oracle.stp(prob.q.cpu().numpy(), prob.params.cpu().numpy(), prob.h, prob.dt)
+        assert rel(avg.cpu(), torch.from_numpy(a_ref)) <= TOL, specs[k]
+        assert rel(faces.cpu(), torch.from_numpy(f_ref)) <= TOL, specs[k]
+    for P, _ in sets:
+        P.close()
+
+
+def test_static_batch_allocates_no_device_memory():
+    """After the first call (which loads the module holding the array), a
+    call changes the device's free memory by nothing: the entry point takes
+    no memory from the device beyond what the library image already holds."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    specs = [(12, 2), (8, 3), (4, 20)]
+    sets, outs = [], []
+    for i, (N, E) in enumerate(specs):
+        prob = elastic_problem(N, E=E, seed_material=720 + i, seed_waves=820 + i, device="cuda")
+        P = stp.Predictor(N - 1, prob.h, prob.dt)
+        sets.append((P, prob))
+        outs.append(P.empty_outputs(E))
+    args = [(P.handle, prob.E, prob.q, prob.params, a, f) for (P, prob), (a, f) in zip(sets, outs)]
+    stp.stp_batch_run_static(args)  # first call: module load, address look-up
+    torch.cuda.synchronize()
+    free_before, _ = torch.cuda.mem_get_info()
+    for _ in range(3):
+        stp.stp_batch_run_static(args)
+    torch.cuda.synchronize()
+    free_after, _ = torch.cuda.mem_get_info()
+    assert free_after == free_before, (free_before, free_after)
     for P, _ in sets:
         P.close()
 
