@@ -21,6 +21,7 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "stp_oracle.c")
+_SRCS = [_SRC, os.path.join(_HERE, "corrector_oracle.c")]
 _OUT_DIR = os.path.join(_HERE, "_build")
 _LIB_PATH = os.path.join(_OUT_DIR, "liboracle_stp.so")
 _lock = threading.Lock()
@@ -38,11 +39,11 @@ def build(force: bool = False) -> str:
     """
     os.makedirs(_OUT_DIR, exist_ok=True)
     if (not force and os.path.exists(_LIB_PATH)
-            and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC)):
+            and all(os.path.getmtime(_LIB_PATH) >= os.path.getmtime(s) for s in _SRCS)):
         return _LIB_PATH
     tmp = _LIB_PATH + f".tmp{os.getpid()}"
     cmd = ["gcc", "-O3", "-std=c11", "-ffp-contract=off", "-fno-fast-math",
-           "-fPIC", "-shared", "-fopenmp", _SRC, "-o", tmp, "-lm"]
+           "-fPIC", "-shared", "-fopenmp"] + _SRCS + ["-o", tmp, "-lm"]
     subprocess.run(cmd, check=True)
     os.replace(tmp, _LIB_PATH)
     return _LIB_PATH
@@ -90,6 +91,17 @@ def _load():
                 ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                 ctypes.c_void_p, ctypes.c_void_p]
             lib.oracle_stp_sources_curvilinear.restype = ctypes.c_int
+            lib.oracle_face_params.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int64,
+                                               ctypes.c_void_p, ctypes.c_void_p]
+            lib.oracle_face_params.restype = ctypes.c_int
+            lib.oracle_correct.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                           ctypes.c_int, ctypes.c_int, ctypes.c_double,
+                                           ctypes.c_double, ctypes.c_void_p, ctypes.c_void_p,
+                                           ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
+            lib.oracle_correct.restype = ctypes.c_int
+            lib.oracle_elastic_B.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_double,
+                                             ctypes.c_double, ctypes.c_void_p]
+            lib.oracle_elastic_B.restype = None
             lib.oracle_num_threads.argtypes = []
             lib.oracle_num_threads.restype = ctypes.c_int
             _lib = lib
@@ -237,3 +249,55 @@ def stp_curvilinear(q: np.ndarray, params: np.ndarray, metric: np.ndarray, dt: f
     if return_terms:
         return avg, faces, terms
     return avg, faces
+
+
+def elastic_B(d: int, rho: float, cp: float, cs: float) -> np.ndarray:
+    """B_d (9x9) of q_t + sum_d B_d dq/dx_d = 0 for one material point."""
+    B = np.zeros((M, M))
+    _load().oracle_elastic_B(int(d), float(rho), float(cp), float(cs), B.ctypes.data)
+    return B
+
+
+def face_params(params: np.ndarray, nodes: str = "gl") -> np.ndarray:
+    """Face projection of the material: [E][N][N][N][3] -> [E][6][N][N][3]."""
+    params = np.ascontiguousarray(params, dtype=np.float64)
+    E, N = params.shape[0], params.shape[1]
+    out = np.empty((E, 6, N, N, 3))
+    if _load().oracle_face_params(NODE_FAMILIES[nodes], N, E, params.ctypes.data,
+                                  out.ctypes.data) != 0:
+        raise RuntimeError("oracle_face_params failed")
+    return out
+
+
+def correct(q: np.ndarray, params: np.ndarray, avg: np.ndarray, faces: np.ndarray, grid,
+            h: float, dt: float, nodes: str = "gl") -> np.ndarray:
+    """One corrector step on a periodic grid of gx*gy*gz elements (element
+    e = (ez*gy + ey)*gx + ex); see corrector_oracle.c for the flux and the
+    readings. avg, faces: the predictor's outputs for q. Returns q(t_n + dt)."""
+    q = np.ascontiguousarray(q, dtype=np.float64)
+    params = np.ascontiguousarray(params, dtype=np.float64)
+    avg = np.ascontiguousarray(avg, dtype=np.float64)
+    faces = np.ascontiguousarray(faces, dtype=np.float64)
+    gx, gy, gz = (int(g) for g in grid)
+    E, N = q.shape[0], q.shape[1]
+    if E != gx * gy * gz:
+        raise ValueError(f"grid {grid} holds {gx * gy * gz} elements, q has {E}")
+    if avg.shape != q.shape or faces.shape != (E, 6, N, N, M) or params.shape != (E, N, N, N, 3):
+        raise ValueError("avg, faces or params of the wrong shape")
+    out = np.empty_like(q)
+    rc = _load().oracle_correct(NODE_FAMILIES[nodes], N, gx, gy, gz, float(h), float(dt),
+                                q.ctypes.data, params.ctypes.data, avg.ctypes.data,
+                                faces.ctypes.data, out.ctypes.data)
+    if rc != 0:
+        raise RuntimeError(f"oracle_correct returned {rc}")
+    return out
+
+
+def ader_steps(q: np.ndarray, params: np.ndarray, grid, h: float, dt: float, steps: int,
+               nodes: str = "gl") -> np.ndarray:
+    """`steps` full ADER-DG steps (predictor, then corrector) on the periodic
+    grid; returns q after the last one."""
+    for _ in range(int(steps)):
+        avg, faces = stp(q, params, h, dt, nodes=nodes)
+        q = correct(q, params, avg, faces, grid, h, dt, nodes=nodes)
+    return q

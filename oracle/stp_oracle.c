@@ -239,6 +239,14 @@ static void elastic_B(int d, double rho, double cp, double cs, double B[M][M]) {
     }
 }
 
+/* B_d as a row-major 9x9 array, for the corrector (corrector_oracle.c) and
+   the tests */
+void oracle_elastic_B(int d, double rho, double cp, double cs, double* B) {
+  double b[M][M];
+  elastic_B(d, rho, cp, cs, b);
+  memcpy(B, b, sizeof(b));
+}
+
 /* flat index of node (z,y,x) quantity s inside one element */
 #define NODE(z, y, x) (((z) * N + (y)) * N + (x))
 
