@@ -93,6 +93,67 @@ stp_status stp_predict(stp_handle h, int64_t elements, const double* q,
                        void* stream);
 
 /*
+ * Face projection of the material, the input the corrector takes for it:
+ *   face_params[e][f][a][b][c] = sum_i phi_i(side) params[e][line node i][c]
+ * with faces and in-plane indices ordered as out_faces (f = x-,x+,y-,y+,z-,z+;
+ * x-faces [z][y], y-faces [z][x], z-faces [y][x]) and c = (rho, cp, cs). In the
+ * paper's code the material is stored inside the state vector and reaches the
+ * faces through the same projection as the state (Sec. II-A, Sec. VI); it does
+ * not change in time, so it is projected once per mesh here.
+ *   params       device, [E][N][N][N][3] (input)
+ *   face_params  device, [E][6][N][N][3] (output, must not overlap params)
+ * Asynchronous on `stream`, capturable. elements == 0 is a no-op.
+ */
+stp_status stp_face_params(stp_handle h, int64_t elements, const double* params,
+                           double* face_params, void* stream);
+
+/*
+ * Corrector step of the linear ADER-DG scheme (Sec. II-A, the update that
+ * follows Eq. (exahypeTimeAverage)): the predictor's time-averaged state and
+ * face projections give the state at t_{n+1},
+ *   q_out = q + dt * ( sum_d A_d (D_d avg)/dx  -  lift(F) ),
+ * on a structured grid of gx * gy * gz cubes of side dx (the handle's), periodic
+ * in every direction, element e = (ez * gy + ey) * gx + ex. The paper leaves
+ * the numerical flux open (it only requires it to be linear); this library
+ * takes the Rusanov fluctuation of a linear non-conservative system on face f
+ * (direction d, side 0/1) at face point (a,b):
+ *   F = 1/2 ( Bn (q+ - q-) - s (q+ - q-) ),
+ *   Bn = +-1/2 (B_d(m-) + B_d(m+))  (+ on the side-1 face, - on the side-0 face),
+ *   s = max(|cp-|, |cp+|),
+ * with q- = faces[e][f][a][b], q+ = the neighbour's faces[e'][f^1][a][b],
+ * m-/m+ = the two sides' face_params, B_d = -A_d of q_t + sum_d B_d dq/dx_d = 0,
+ * and the strong-form lift onto node i of the line through (a,b) along d:
+ * phi_i(side) / (w_i dx) F (w the quadrature weights on [0,1]: the diagonal
+ * mass matrix of the nodal basis). FP64 whatever the handle's precision.
+ *   q, avg     device, [E][N][N][N][9]: the state at t_n and its predictor
+ *              average (stp_predict of q with this handle)
+ *   faces      device, [E][6][N][N][9]: the predictor's face projections
+ *   params     device, [E][N][N][N][3]; face_params from stp_face_params
+ *   q_out      device, [E][N][N][N][9]: may be q itself (in place); must not
+ *              overlap any other input
+ * E = gx * gy * gz. Asynchronous on `stream`, capturable like stp_predict.
+ * STP_ERR_INVALID_ARG for a grid dimension < 1, a NULL or misaligned buffer,
+ * overlapping buffers, or pointers that are not device memory on the
+ * handle's device.
+ */
+stp_status stp_correct(stp_handle h, int gx, int gy, int gz, const double* q,
+                       const double* params, const double* face_params, const double* avg,
+                       const double* faces, double* q_out, void* stream);
+
+/*
+ * `steps` full ADER-DG steps on the periodic grid of stp_correct: each is
+ * stp_predict(q -> avg, faces) in the handle's precision followed by
+ * stp_correct(q -> q) in place. avg and faces are the caller's work buffers
+ * ([E][N][N][N][9] and [E][6][N][N][9]); after the call they hold the last
+ * step's predictor outputs. Arguments and errors as stp_predict and
+ * stp_correct; steps == 0 validates and returns. Asynchronous on `stream`,
+ * capturable.
+ */
+stp_status stp_ader_step(stp_handle h, int gx, int gy, int gz, int steps, double* q,
+                         const double* params, const double* face_params, double* avg,
+                         double* faces, void* stream);
+
+/*
  * Point sources (Sec. II-A: the source term of the linear PDE, projected onto
  * the nodal basis; in the STP the source's time derivatives enter every
  * Cauchy-Kowalewsky order). A source is a Dirac delta at `position` (reference

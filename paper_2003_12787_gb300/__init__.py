@@ -7,6 +7,7 @@ elastic problems.
 """
 from __future__ import annotations
 
+from ._binding import stp_ader_step, stp_correct, stp_face_params  # noqa: F401
 from ._binding import (NODE_FAMILIES, PRECISIONS, STPError, stp_create,  # noqa: F401
                        stp_destroy, stp_device_status, stp_get_nodes, stp_get_precision,
                        stp_last_error,

@@ -84,6 +84,13 @@ def load():
         lib.stp_batch_destroy.argtypes = [vp]
         lib.stp_autotune.argtypes = [vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(dbl),
                                      ctypes.POINTER(dbl)]
+        ci = ctypes.c_int
+        lib.stp_face_params.argtypes = [vp, i64, vp, vp, vp]
+        lib.stp_face_params.restype = ci
+        lib.stp_correct.argtypes = [vp, ci, ci, ci, vp, vp, vp, vp, vp, vp, vp]
+        lib.stp_correct.restype = ci
+        lib.stp_ader_step.argtypes = [vp, ci, ci, ci, ci, vp, vp, vp, vp, vp, vp]
+        lib.stp_ader_step.restype = ci
         lib.stp_batch_run_static.argtypes = [ctypes.c_int, vp, vp]
         lib.stp_batch_run_static.restype = ctypes.c_int
         lib.stp_batch_run_static_curvilinear.argtypes = [ctypes.c_int, vp, vp, vp]
@@ -165,6 +172,25 @@ def stp_predict(h: int, elements: int, q, params, out_avg, out_faces, stream=Non
 def stp_predict_host(h: int, elements: int, q, params, out_avg, out_faces, stream=None) -> None:
     _check(load().stp_predict_host(h, elements, _ptr(q), _ptr(params), _ptr(out_avg),
                                    _ptr(out_faces), _stream(stream)), "stp_predict_host")
+
+
+def stp_face_params(h: int, elements: int, params, face_params, stream=None) -> None:
+    _check(load().stp_face_params(h, elements, _ptr(params), _ptr(face_params), _stream(stream)),
+           "stp_face_params")
+
+
+def stp_correct(h: int, grid, q, params, face_params, avg, faces, q_out, stream=None) -> None:
+    gx, gy, gz = (int(g) for g in grid)
+    _check(load().stp_correct(h, gx, gy, gz, _ptr(q), _ptr(params), _ptr(face_params), _ptr(avg),
+                              _ptr(faces), _ptr(q_out), _stream(stream)), "stp_correct")
+
+
+def stp_ader_step(h: int, grid, steps: int, q, params, face_params, avg, faces,
+                  stream=None) -> None:
+    gx, gy, gz = (int(g) for g in grid)
+    _check(load().stp_ader_step(h, gx, gy, gz, int(steps), _ptr(q), _ptr(params),
+                                _ptr(face_params), _ptr(avg), _ptr(faces), _stream(stream)),
+           "stp_ader_step")
 
 
 def stp_destroy(h: int | None) -> None:

@@ -1096,3 +1096,117 @@ stp_status stp_measure_fp64_peak(double* gflops, void* stream) {
 }
 
 }  // extern "C"
+
+// ---- corrector (Sec. II-A) ---------------------------------------------------
+
+namespace {
+
+// Checks of stp_correct's arguments; E receives gx * gy * gz.
+stp_status validate_correct(stp_handle h, int gx, int gy, int gz, const double* q,
+                            const double* params, const double* face_params, const double* avg,
+                            const double* faces, const double* q_out, int64_t* E) {
+  if (!h || h->N < 1) return fail(STP_ERR_INVALID_ARG, "invalid handle");
+  if (gx < 1 || gy < 1 || gz < 1) return fail(STP_ERR_INVALID_ARG, "grid dimensions must be >= 1");
+  const int64_t n = (int64_t)gx * gy * gz;
+  if (n > ((int64_t)1 << 31) - 1) return fail(STP_ERR_INVALID_ARG, "grid too large");
+  *E = n;
+  if (!q || !params || !face_params || !avg || !faces || !q_out)
+    return fail(STP_ERR_INVALID_ARG, "null buffer");
+  const void* all[6] = {q, params, face_params, avg, faces, q_out};
+  for (const void* p : all)
+    if (!aligned16(p)) return fail(STP_ERR_INVALID_ARG, "buffers must be 16-byte aligned");
+  const Sizes s = sizes_per_element(h->N);
+  const size_t E_ = (size_t)n, nfp = (size_t)6 * h->N * h->N * 3 * 8 * E_;
+  if (E_ > ((size_t)1 << 40) / s.q) return fail(STP_ERR_INVALID_ARG, "elements too large");
+  const void* ins[4] = {params, face_params, avg, faces};
+  const size_t nin[4] = {s.params * E_, nfp, s.avg * E_, s.faces * E_};
+  for (int i = 0; i < 4; ++i)
+    if (overlap(q_out, s.q * E_, ins[i], nin[i]))
+      return fail(STP_ERR_INVALID_ARG, "q_out overlaps an input other than q");
+  if (q_out != q && overlap(q_out, s.q * E_, q, s.q * E_))
+    return fail(STP_ERR_INVALID_ARG, "q_out overlaps q without being q");
+  return STP_OK;
+}
+
+bool capturing(cudaStream_t st) {
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(st, &cap) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return cap != cudaStreamCaptureStatusNone;
+}
+
+}  // namespace
+
+extern "C" {
+
+stp_status stp_face_params(stp_handle h, int64_t elements, const double* params,
+                           double* face_params, void* stream) {
+  if (!h || h->N < 1) return fail(STP_ERR_INVALID_ARG, "invalid handle");
+  if (elements < 0) return fail(STP_ERR_INVALID_ARG, "elements < 0");
+  if (elements == 0) return STP_OK;
+  if (!params || !face_params) return fail(STP_ERR_INVALID_ARG, "null buffer");
+  if (!aligned16(params) || !aligned16(face_params))
+    return fail(STP_ERR_INVALID_ARG, "buffers must be 16-byte aligned");
+  const Sizes s = sizes_per_element(h->N);
+  const size_t E_ = (size_t)elements;
+  if (E_ > ((size_t)1 << 40) / s.q) return fail(STP_ERR_INVALID_ARG, "elements too large");
+  if (overlap(params, s.params * E_, face_params, (size_t)6 * h->N * h->N * 3 * 8 * E_))
+    return fail(STP_ERR_INVALID_ARG, "face_params overlaps params");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (!capturing(st)) {
+    stp_status r;
+    if ((r = check_device_ptr(params, h->device, "params")) != STP_OK) return r;
+    if ((r = check_device_ptr(face_params, h->device, "face_params")) != STP_OK) return r;
+  }
+  cudaError_t e = stp::launch_face_params(h->N, elements, h->d_tables, params, face_params, st);
+  if (e != cudaSuccess) return cuda_fail(e, "face-parameter kernel launch");
+  return STP_OK;
+}
+
+stp_status stp_correct(stp_handle h, int gx, int gy, int gz, const double* q,
+                       const double* params, const double* face_params, const double* avg,
+                       const double* faces, double* q_out, void* stream) {
+  int64_t E = 0;
+  stp_status s = validate_correct(h, gx, gy, gz, q, params, face_params, avg, faces, q_out, &E);
+  if (s != STP_OK) return s;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (!capturing(st)) {
+    const char* names[6] = {"q", "params", "face_params", "avg", "faces", "q_out"};
+    const void* ptrs[6] = {q, params, face_params, avg, faces, q_out};
+    for (int i = 0; i < 6; ++i)
+      if ((s = check_device_ptr(ptrs[i], h->device, names[i])) != STP_OK) return s;
+  }
+  cudaError_t e = stp::launch_corrector(h->N, gx, gy, gz, h->host, h->dx, h->dt, h->d_tables, q,
+                                        params, face_params, avg, faces, q_out, st);
+  if (e != cudaSuccess) return cuda_fail(e, "corrector kernel launch");
+  return STP_OK;
+}
+
+stp_status stp_ader_step(stp_handle h, int gx, int gy, int gz, int steps, double* q,
+                         const double* params, const double* face_params, double* avg,
+                         double* faces, void* stream) {
+  if (steps < 0) return fail(STP_ERR_INVALID_ARG, "steps < 0");
+  int64_t E = 0;
+  stp_status s = validate_correct(h, gx, gy, gz, q, params, face_params, avg, faces, q, &E);
+  if (s != STP_OK) return s;
+  if ((s = validate_common(h, E, q, params, avg, faces)) != STP_OK) return s;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (!capturing(st)) {
+    const char* names[5] = {"q", "params", "face_params", "avg", "faces"};
+    const void* ptrs[5] = {q, params, face_params, avg, faces};
+    for (int i = 0; i < 5; ++i)
+      if ((s = check_device_ptr(ptrs[i], h->device, names[i])) != STP_OK) return s;
+  }
+  for (int k = 0; k < steps; ++k) {
+    cudaError_t e = launch_configured(h, E, q, params, avg, faces, st);
+    if (e != cudaSuccess) return cuda_fail(e, "STP kernel launch");
+    e = stp::launch_corrector(h->N, gx, gy, gz, h->host, h->dx, h->dt, h->d_tables, q, params,
+                              face_params, avg, faces, q, st);
+    if (e != cudaSuccess) return cuda_fail(e, "corrector kernel launch");
+  }
+  return STP_OK;
+}
+
+}  // extern "C"

@@ -163,6 +163,17 @@ void server_submit(Server* s, int id);
 cudaError_t server_progress(Server* s, int* done);
 int server_sims(const Server* s);
 
+// Corrector on a periodic grid of gx*gy*gz cubes (corrector.cu): q_out = q +
+// dt (A.(D avg)/dx - lift of the Rusanov fluctuations of the face values);
+// q_out may be q. face_params: [E][6][N][N][3] from launch_face_params.
+cudaError_t launch_corrector(int N, int gx, int gy, int gz, const HostTables& t, double dx,
+                             double dt, const double* tables, const double* q,
+                             const double* params, const double* face_params, const double* avg,
+                             const double* faces, double* q_out, cudaStream_t stream);
+// Face projection of the per-node material (rho, cp, cs) with phi(0), phi(1).
+cudaError_t launch_face_params(int N, int64_t E, const double* tables, const double* params,
+                               double* out, cudaStream_t stream);
+
 cudaError_t launch_fp64_peak(double* sink, int blocks, int threads, int iters,
                              cudaStream_t stream);
 

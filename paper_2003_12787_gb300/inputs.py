@@ -206,6 +206,65 @@ def curvilinear_problem(N: int, grid=None, E: int | None = None, h: float | None
                    metric=metric.contiguous())
 
 
+def periodic_problem(N: int, grid, h: float | None = None, seed_material: int = 1001,
+                     seed_waves: int = 1002, device: str | torch.device = "cpu",
+                     nodes: str = "gl", per_node_material: bool = False) -> Problem:
+    """Input set of the full ADER-DG step (predictor + corrector) on a grid that
+    is periodic in every direction, box [0, Gx h] x [0, Gy h] x [0, Gz h].
+
+    * State, seed ``seed_waves``: 4 plane waves periodic on the box. Integer
+      wave numbers n ~ U{-2..2}^3 (drawn again while all three are 0),
+      k = 2 pi (n_x/(Gx h), n_y/(Gy h), n_z/(Gz h)); amplitudes a[w,s] ~
+      U[0.5,1] and phases ph[w,s] ~ U[0,2 pi) of shape (4,9), drawn in that
+      order; q_s(x) = sum_w a[w,s] sin(k_w . x + ph[w,s]).
+    * Material, seed ``seed_material``: constant inside each element (the
+      paper's LOH1 benchmark is a layered medium: piecewise constant
+      material), rho ~ U[2,3] and cp ~ U[4,6] per element, cs = cp/sqrt(3);
+      with per_node_material, the per-node draw of ``material`` instead.
+    * dt = 0.4*h / ((2N-1) * max cp), as for the predictor alone.
+    """
+    Gx, Gy, Gz = (int(g) for g in grid)
+    E = Gx * Gy * Gz
+    if h is None:
+        h = 1.0 / max(Gx, Gy, Gz)
+    if per_node_material:
+        params_np = material(N, E, seed_material)
+    else:
+        rng = np.random.Generator(np.random.PCG64(seed_material))
+        rho = rng.uniform(2.0, 3.0, E)
+        cp = rng.uniform(4.0, 6.0, E)
+        params_np = np.empty((E, N, N, N, 3))
+        params_np[..., 0] = rho[:, None, None, None]
+        params_np[..., 1] = cp[:, None, None, None]
+        params_np[..., 2] = (cp / math.sqrt(3.0))[:, None, None, None]
+    dt = 0.4 * h / ((2 * N - 1) * float(params_np[..., 1].max()))
+    rng = np.random.Generator(np.random.PCG64(seed_waves))
+    ks = []
+    while len(ks) < N_WAVES:
+        n = rng.integers(-2, 3, 3)
+        if np.any(n != 0):
+            ks.append(2.0 * math.pi * n / (np.array([Gx, Gy, Gz]) * h))
+    amp = rng.uniform(0.5, 1.0, (N_WAVES, M))
+    phase = rng.uniform(0.0, 2.0 * math.pi, (N_WAVES, M))
+    dev = torch.device(device)
+    xi = torch.tensor(sample_points(N, nodes), dtype=torch.float64, device=dev)
+    e = torch.arange(E, device=dev, dtype=torch.int64)
+    ex = (e % Gx).to(torch.float64)
+    ey = ((e // Gx) % Gy).to(torch.float64)
+    ez = (e // (Gx * Gy)).to(torch.float64)
+    X = ((ex[:, None] + xi[None, :]) * h)[:, None, None, :]
+    Y = ((ey[:, None] + xi[None, :]) * h)[:, None, :, None]
+    Z = ((ez[:, None] + xi[None, :]) * h)[:, :, None, None]
+    q = torch.zeros((E, N, N, N, M), dtype=torch.float64, device=dev)
+    for w in range(N_WAVES):
+        kx, ky, kz = (float(v) for v in ks[w])
+        arg = kx * X + ky * Y + kz * Z
+        for s in range(M):
+            q[..., s] += float(amp[w, s]) * torch.sin(arg + float(phase[w, s]))
+    params = torch.from_numpy(params_np).to(dev)
+    return Problem(N=N, E=E, h=h, dt=dt, q=q, params=params, grid=(Gx, Gy, Gz))
+
+
 # --- named workloads --------------------------------------------------------
 
 def small_case() -> Problem:
@@ -216,6 +275,11 @@ def small_case() -> Problem:
 def order7_case(device="cpu") -> Problem:
     """Order 7 (N=8), 32^3 = 32768 elements of side 1/32."""
     return elastic_problem(8, grid=(32, 32, 32), device=device)
+
+
+def ader_order7_case(device="cpu") -> Problem:
+    """Full ADER-DG step, order 7 (N=8), periodic 32^3 grid of side 1/32."""
+    return periodic_problem(8, (32, 32, 32), device=device)
 
 
 def order9_case(device="cpu") -> Problem:

@@ -53,6 +53,46 @@ class Predictor:
             faces = torch.empty((E, 6, N, N, 9), dtype=torch.float64, device=device)
         return avg, faces
 
+    def face_params(self, params: torch.Tensor, stream=None) -> torch.Tensor:
+        """Face projection of the material, [E][6][N][N][3] (stp_face_params)."""
+        N = self.N
+        if params.dtype != torch.float64 or params.dim() != 5 or tuple(params.shape[1:]) != (N, N, N, 3):
+            raise ValueError(f"params must be float64 [E][{N}][{N}][{N}][3]")
+        if not params.is_contiguous():
+            raise ValueError("params must be contiguous")
+        out = torch.empty((params.shape[0], 6, N, N, 3), dtype=torch.float64, device=params.device)
+        if stream is None and params.is_cuda:
+            stream = torch.cuda.current_stream(params.device)
+        B.stp_face_params(self.handle, params.shape[0], params, out, stream)
+        return out
+
+    def _check_grid(self, grid, q: torch.Tensor):
+        gx, gy, gz = (int(g) for g in grid)
+        if gx * gy * gz != q.shape[0]:
+            raise ValueError(f"grid {tuple(grid)} holds {gx * gy * gz} elements, q has {q.shape[0]}")
+
+    def correct(self, grid, q, params, face_params, avg, faces, out=None, stream=None):
+        """Corrector step on the periodic grid (stp_correct); returns q(t + dt).
+        out may be q (in place)."""
+        self._check_inputs(q, params)
+        self._check_grid(grid, q)
+        q_out = torch.empty_like(q) if out is None else out
+        if stream is None and q.is_cuda:
+            stream = torch.cuda.current_stream(q.device)
+        B.stp_correct(self.handle, grid, q, params, face_params, avg, faces, q_out, stream)
+        return q_out
+
+    def ader_steps(self, grid, q, params, face_params, steps: int, work=None, stream=None):
+        """`steps` full ADER-DG steps (predictor + corrector) in place on q
+        (stp_ader_step); work = (avg, faces) buffers or None."""
+        self._check_inputs(q, params)
+        self._check_grid(grid, q)
+        avg, faces = work if work is not None else self.empty_outputs(q.shape[0], device=q.device)
+        if stream is None and q.is_cuda:
+            stream = torch.cuda.current_stream(q.device)
+        B.stp_ader_step(self.handle, grid, steps, q, params, face_params, avg, faces, stream)
+        return q
+
     def _check_inputs(self, q: torch.Tensor, params: torch.Tensor):
         N = self.N
         if q.dtype != torch.float64 or params.dtype != torch.float64:
