@@ -603,6 +603,126 @@ def served_measurement(stp, torch, args):
     return out
 
 
+def corrector_fp64_ops_per_node(N: int) -> int:
+    """FP64 instructions the corrector issues per node: 18 derivative chains of
+    N DFMA (elastic sparsity), 12 for the elastic update, 54 for the lift of
+    the six face fluctuations (9 quantities x 6 faces) and 9 for q + update."""
+    return 18 * N + 12 + 54 + 9
+
+
+def ader_measurement(stp, torch, args):
+    """Full ADER-DG steps (predictor + corrector) on the periodic order-7
+    workload: the corrector alone, the predictor alone and whole steps through
+    stp_ader_step; sampled elements checked against the oracle."""
+    import oracle
+    from paper_2003_12787_gb300.inputs import ader_order7_case
+    prob = ader_order7_case(device="cuda")
+    E, N, grid = prob.E, prob.N, prob.grid
+    P = stp.Predictor(N - 1, prob.h, prob.dt)
+    s = torch.cuda.current_stream()
+    qd = prob.q.clone()
+    fp = P.face_params(prob.params)
+    avg, faces = P.empty_outputs(E)
+    out = torch.empty_like(qd)
+
+    def timed(fn, reps):
+        for _ in range(3):
+            fn()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        a.record(s)
+        for _ in range(reps):
+            fn()
+        b.record(s)
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / reps
+
+    P.predict(prob.q, prob.params, out=(avg, faces))
+    pred_ms = timed(lambda: P.predict(prob.q, prob.params, out=(avg, faces)), 5)
+    corr_ms = timed(lambda: P.correct(grid, prob.q, prob.params, fp, avg, faces, out=out), 10)
+    fp_ms = timed(lambda: P.face_params(prob.params), 5)
+    steps = 5
+    qd.copy_(prob.q)
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    a.record(s)
+    P.ader_steps(grid, qd, prob.params, fp, steps, work=(avg, faces))
+    b.record(s)
+    torch.cuda.synchronize()
+    step_ms = a.elapsed_time(b) / steps
+    # parity: one step from the initial state, sampled elements vs the oracle
+    qd.copy_(prob.q)
+    P.ader_steps(grid, qd, prob.params, fp, 1, work=(avg, faces))
+    torch.cuda.synchronize()
+    q, pa = prob.q.cpu().numpy(), prob.params.cpu().numpy()
+    got = qd.cpu().numpy()
+    gx, gy, gz = grid
+    err = 0.0
+    for e in (0, E // 2 + 17, E - 1):
+        ex, ey, ez = e % gx, (e // gx) % gy, e // (gx * gy)
+        idx = [((ez + dz) % gz * gy + (ey + dy) % gy) * gx + (ex + dx) % gx
+               for dz in (-1, 0, 1) for dy in (-1, 0, 1) for dx in (-1, 0, 1)]
+        ref = oracle.ader_steps(q[idx], pa[idx], (3, 3, 3), prob.h, prob.dt, 1)[13]
+        err = max(err, float(np.abs(got[e] - ref).max() / np.abs(ref).max()))
+    ops = corrector_fp64_ops_per_node(N) * N ** 3
+    P.close()
+    return {"workload": "order-7 (N=8) full ADER-DG step (predictor + corrector, Rusanov flux), "
+                        "periodic 32^3 grid of side 1/32, element-wise material",
+            "elements": E, "predictor_ms": pred_ms, "corrector_ms": corr_ms,
+            "face_params_ms_once_per_mesh": fp_ms, "step_ms": step_ms,
+            "steps_timed": steps, "element_steps_per_s": E / (step_ms / 1e3),
+            "corrector_share_of_step": corr_ms / step_ms,
+            "corrector_fp64_ops_per_element": ops,
+            "corrector_fp64_pipe_frac_est": E * ops / (corr_ms / 1e3) /
+            (FP64_PEAK_TFLOPS * 1e12 / 2),
+            # algorithmic bytes: q, avg, params, q_out, faces and face_params once each
+            "corrector_hbm_gbs": E * 8 * (30 * N ** 3 + 54 * N ** 2 + 18 * N ** 2) /
+            (corr_ms / 1e3) / 1e9,
+            "max_rel_err_sampled_one_step": err}
+
+
+def compact_summary(line):
+    """The secondary figures in a few hundred characters, placed last in the
+    line: speed-up and error per arithmetic variant at order 9, the batched
+    plan's FP64 fraction, the served trace's rate and latency, the full
+    ADER-DG step and the small-case latency."""
+    def r(x, n=4):
+        return None if x is None else float(f"{x:.{n}g}")
+    out = {"fp64_frac": r(line["roofline"]["frac"]),
+           "fp64_pipe_frac": r(line["roofline"].get("fp64_pipe_frac"))}
+    mixed = line.get("mixed")
+    if mixed:
+        out["order9_speedup_err"] = {k: [r(v["speedup_vs_fp64"], 3), r(v["max_rel_err"], 2)]
+                                     for k, v in mixed["variants"].items()}
+    b = line.get("batched")
+    if b:
+        out["batched"] = {"ms": r(b["ms_per_launch"]), "fp64_frac": r(b["frac_fp64_peak"])}
+    sv = line.get("served")
+    if sv:
+        out["served"] = {"req_s": r(sv["throughput_req_s"]), "p50_ms": r(sv["p50_ms"]),
+                         "p99_ms": r(sv["p99_ms"])}
+        bc = sv.get("below_capacity")
+        if bc:
+            out["served"]["below_capacity"] = [r(bc["throughput_req_s"]), r(bc["p50_ms"]),
+                                               r(bc["p99_ms"])]
+        ff = sv.get("float_float")
+        if ff:
+            out["served"]["ff"] = [r(ff["throughput_req_s"]), r(ff["p50_ms"]), r(ff["p99_ms"])]
+        c5 = sv.get("cfg5")
+        if c5:
+            out["served"]["cfg5"] = [r(c5["throughput_req_s"]), r(c5["p50_ms"]), r(c5["p99_ms"])]
+    a = line.get("ader_step")
+    if a:
+        out["ader_step"] = {"step_ms": r(a["step_ms"]), "corrector_ms": r(a["corrector_ms"]),
+                            "err": r(a["max_rel_err_sampled_one_step"], 2)}
+    sc = line.get("small_case")
+    if sc:
+        out["small_case_us_p50_p99"] = [r(sc["device_us"]["p50"]), r(sc["device_us"]["p99"])]
+    return out
+
+
 def run_gpu(args):
     import torch
     world, rank, local = dist_env()
@@ -727,6 +847,9 @@ def run_gpu(args):
     served = None
     if extras and not args.no_served:
         served = served_measurement(stp, torch, args)
+    ader = None
+    if extras and not args.no_ader:
+        ader = ader_measurement(stp, torch, args)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -774,7 +897,7 @@ def run_gpu(args):
                            "min": min(step_ms), "max": max(step_ms)},
             "e2e": e2e, "cpu_baseline": cpu, "clocks": clocks, "mixed": mixed, "variants_same_workload": variants7,
             "small_case": small, "batched": batched, "served": served,
-            "curvilinear": curvilinear,
+            "curvilinear": curvilinear, "ader_step": ader,
             "gpu_launches": args.steps, "parity_max_rel_sampled": parity,
             "paper_context": {
                 "figure": "22.5 % of available FP64 performance",
@@ -783,6 +906,7 @@ def run_gpu(args):
                        "60.8 GFLOP/s per core available",
                 "this_run_frac_of_fp64_peak": achieved / FP64_PEAK_TFLOPS},
         }
+        line["summary"] = compact_summary(line)  # last key: survives a cut-off tail
         print(json.dumps(line), flush=True)
     P.close()
     if world > 1:
@@ -847,6 +971,8 @@ def build_parser():
     ap.add_argument("--batched-emax", type=int, default=16384,
                     help="largest set of the batched workload (smaller for profiler captures)")
     ap.add_argument("--no-served", action="store_true", help="skip the served workload")
+    ap.add_argument("--no-ader", action="store_true",
+                    help="skip the full ADER-DG step (predictor + corrector) measurement")
     ap.add_argument("--no-served-ff", action="store_true",
                     help="skip the float-float run of the served trace")
     ap.add_argument("--no-curvilinear", action="store_true",

@@ -302,7 +302,11 @@ stp_precision stp_get_precision(stp_handle h);
  * Synchronise `stream`, then read and clear the handle's device status word.
  * *flags receives its bits (bit 0: a tensor-core completion wait in the mixed
  * kernel exceeded its iteration limit; the outputs of that launch are invalid;
- * bit 1: set by stp_selftest_bounded_wait).
+ * bit 1: set by stp_selftest_bounded_wait; bit 2: after such a timeout the
+ * kernel's last bounded wait for the tensor cores to drain gave up too, so an
+ * MMA may still have been writing tensor memory when the CTA released it -
+ * discard every result computed on this CUDA context from then on and
+ * recreate the context).
  * Returns STP_ERR_TIMEOUT if any bit was set, else STP_OK.
  */
 stp_status stp_device_status(stp_handle h, void* stream, unsigned int* flags);

@@ -259,4 +259,34 @@ __device__ __forceinline__ int load_state_ff(const double* __restrict__ qe, floa
   return load_state_ff_layout<N, NT, Sh::S, Sh::RX, Sh::PLANE>(qe, sp);
 }
 
+// The nine accumulator values of node pn from the 18 partial arrays (slot
+// order of eo_acc; passes added in x, y, z order).
+__device__ __forceinline__ void eo32_gather(const float* __restrict__ spart, int S, int pn, float g[9]) {
+  auto P = [&](int pass, int q6) { return spart[(pass * 6 + q6) * S + pn]; };
+#pragma unroll
+  for (int j = 0; j < 3; ++j) g[j] = (P(0, j) + P(1, j)) + P(2, j);
+  g[3] = P(0, 4) + P(1, 3);
+  g[4] = P(0, 5) + P(2, 3);
+  g[5] = P(1, 5) + P(2, 4);
+  g[6] = P(0, 3);
+  g[7] = P(1, 4);
+  g[8] = P(2, 5);
+}
+
+// New term of one node in FP32 from its nine accumulators (slot order of
+// eo_acc).
+__device__ __forceinline__ void eo_pointwise32(const float g[9], float invrho, float lam, float mu,
+                                               float mu2, float r[9]) {
+  const float ltr = lam * ((g[6] + g[7]) + g[8]);
+  r[kV1] = invrho * g[0];
+  r[kV2] = invrho * g[1];
+  r[kV3] = invrho * g[2];
+  r[kS11] = fmaf(mu2, g[6], ltr);
+  r[kS22] = fmaf(mu2, g[7], ltr);
+  r[kS33] = fmaf(mu2, g[8], ltr);
+  r[kS12] = mu * g[3];
+  r[kS13] = mu * g[4];
+  r[kS23] = mu * g[5];
+}
+
 }  // namespace stp

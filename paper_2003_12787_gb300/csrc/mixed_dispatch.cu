@@ -1,5 +1,5 @@
 // Dispatch of the mixed-precision STP over N (instantiations in mixed_n*.cu).
-#include "mixed_kernels.cuh"
+#include "tc_kernels.cuh"
 
 namespace stp {
 

@@ -1,5 +1,8 @@
 // Mixed-precision Space-Time Predictor for sm_103a: derivative contractions
 // on the 5th-generation tensor cores (tcgen05.mma, accumulators in TMEM).
+// Kernel of the orders N = 11, 12 (where one node pair per thread of the
+// kernel in tc_kernels.cuh would not fit the registers); the helpers below
+// (descriptors, mbarriers, TMEM) serve both kernels.
 //
 // Per element (one CTA):
 //   1. r_0 = q; the first Cauchy-Kowalewsky term r_1 = dt/2 L q is computed in
@@ -574,15 +577,5 @@ cudaError_t launch_mixed_n(int variant, int64_t E, const double* q, const double
 }
 
 }  // namespace mixed
-
-// Per-N entry points, instantiated in mixed_n*.cu.
-template <int N>
-cudaError_t launch_mixed_for(int variant, int64_t E, const double* q, const double* params,
-                             double* out_avg, double* out_faces, const double* tables,
-                             const double* Dref, double dt_over_dx, int eD, unsigned int* status,
-                             cudaStream_t stream) {
-  return mixed::launch_mixed_n<N>(variant, E, q, params, out_avg, out_faces, tables, Dref,
-                                  dt_over_dx, eD, status, stream);
-}
 
 }  // namespace stp

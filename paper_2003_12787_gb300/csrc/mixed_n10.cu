@@ -1,5 +1,5 @@
-// Explicit instantiations of the mixed-precision STP kernel for N = 10.
-#include "mixed_kernels.cuh"
+// Explicit instantiations of the tensor-core STP kernels for N = 10.
+#include "tc_kernels.cuh"
 
 namespace stp {
 template cudaError_t launch_mixed_for<10>(int, int64_t, const double*, const double*, double*,

@@ -579,6 +579,9 @@ stp_status stp_device_status(stp_handle h, void* stream, unsigned int* flags) {
     return cuda_fail(e, "status read");
   if ((e = cudaMemset(h->d_status, 0, sizeof(v))) != cudaSuccess) return cuda_fail(e, "status reset");
   *flags = v;
+  if (v & 4u)
+    return fail(STP_ERR_TIMEOUT, "a bounded device-side wait gave up and the tensor cores were "
+                                 "not drained: discard results of this context and recreate it");
   return v ? fail(STP_ERR_TIMEOUT, "a bounded device-side wait gave up") : STP_OK;
 }
 

@@ -1,14 +1,22 @@
 """GPU parity of the reduced-precision STP variants against the FP64 oracle:
-the split-precision tensor-core variants and the FP32 CUDA-core variant.
+the tensor-core variants (BF16/FP16 slices) and the FP32 CUDA-core variant.
 
-Stated error bars (normwise per output array, max|gpu - oracle| / max|oracle|)
-on the seeded plane-wave inputs. At order 9 (N=10, the mixed-precision
-workload): BF16x3, FP16x2 and FP16x3 <= 1e-9; BF16x2 (16 significant bits
-per operand) <= 1e-7. Over N = 2..12 the same bars hold except FP16x2, which
-is stated at 2e-9 (measured up to 1.1e-9 at N = 8). The first CK term is
-computed in FP64, the later terms on the tensor cores with FP32 accumulation;
-the FP32 accumulation sets the ~1e-10 floor. The FP32 variant (same FP64
-first term, later terms from FP32 FMA chains) is held to 1e-9 at every N.
+Stated error bars, normwise per output array (max|gpu - oracle| / max|oracle|
+over avg and each face array), on seeded plane-wave inputs:
+
+* Tensor-core variants, N <= 10 (per-term precision: float-float while a
+  Taylor term is above 1e-3 of the state, then 3, 2 or 1 slices by its size):
+  BF16x3 and FP16x3 <= 1e-9 on resolved fields (h = 1/32) AND on coarse ones
+  (h = 1/4, 1/5, where the later terms stay large); BF16x2 and FP16x2 <= 5e-8
+  (measured up to 2.2e-8 on the coarse fields).
+* Tensor-core variants, N = 11, 12 (the earlier kernel: first term in FP64,
+  every later term with the variant's slices), resolved fields only:
+  BF16x3, FP16x3 <= 1e-9, FP16x2 <= 2e-9, BF16x2 <= 1e-7.
+* FP32 (first term in float-float, later terms in FP32): <= 1e-9 on resolved
+  fields, <= 1e-8 on coarse ones.
+
+The time-dependent part avg - q (what the predictor adds to the state) is held
+to its own bars, relative to max|avg - q| of the oracle.
 """
 from __future__ import annotations
 
@@ -23,8 +31,15 @@ from paper_2003_12787_gb300.inputs import elastic_problem
 
 pytestmark = pytest.mark.gpu
 
-TOL = {"bf16x2": 1e-7, "bf16x3": 1e-9, "fp16x2": 1e-9, "fp16x3": 1e-9, "fp32": 1e-9}  # order 9
-TOL_ANY_N = dict(TOL, fp16x2=2e-9)
+TC = ["bf16x2", "bf16x3", "fp16x2", "fp16x3"]
+# resolved fields, N <= 10
+TOL = {"bf16x2": 5e-8, "bf16x3": 1e-9, "fp16x2": 5e-8, "fp16x3": 1e-9, "fp32": 1e-9}
+# resolved fields, N = 11, 12 (earlier tensor-core kernel)
+TOL_N11 = {"bf16x2": 1e-7, "bf16x3": 1e-9, "fp16x2": 2e-9, "fp16x3": 1e-9, "fp32": 1e-9}
+# coarse fields, N <= 10
+TOL_COARSE = {"bf16x2": 5e-8, "bf16x3": 1e-9, "fp16x2": 5e-8, "fp16x3": 1e-9, "fp32": 1e-8}
+# the increment avg - q, relative to its own size
+TOL_INCR = {"bf16x2": 1e-5, "bf16x3": 3e-7, "fp16x2": 1e-5, "fp16x3": 3e-7, "fp32": 3e-6}
 
 
 def rel(a, b):
@@ -56,17 +71,34 @@ def errors(avg, faces, a_ref, f_ref):
     return [rel(avg, a_ref)] + [rel(faces[:, f], f_ref[:, f]) for f in range(6)]
 
 
+def check(prob, precision, tol, idx=None):
+    avg, faces = run(prob, precision, idx)
+    q = prob.q.cpu().numpy() if idx is None else prob.q[torch.as_tensor(idx)].cpu().numpy()
+    pa = prob.params.cpu().numpy() if idx is None else prob.params[torch.as_tensor(idx)].cpu().numpy()
+    a_ref, f_ref = oracle.stp(q, pa, prob.h, prob.dt)
+    errs = errors(avg, faces, a_ref, f_ref)
+    assert max(errs) <= tol, errs
+    incr = rel(avg - q, a_ref - q)
+    assert incr <= TOL_INCR[precision], incr
+    return max(errs), incr
+
+
 @pytest.mark.parametrize("precision", list(TOL))
-@pytest.mark.parametrize("N", [2, 4, 6, 8, 10, 12])
-def test_mixed_parity_small(precision, N):
+@pytest.mark.parametrize("N", [2, 3, 4, 5, 6, 7, 8, 9, 10, 11, 12])
+def test_mixed_parity_resolved(precision, N):
     prob = elastic_problem(N, grid=(32, 32, 16), h=1.0 / 32, E=5,
                            seed_material=300 + N, seed_waves=400 + N)
-    avg, faces = run(prob, precision)
-    a_ref, f_ref = oracle.stp(prob.q.numpy(), prob.params.numpy(), prob.h, prob.dt)
-    errs = errors(avg, faces, a_ref, f_ref)
-    assert max(errs) <= TOL_ANY_N[precision], errs
-    # the time-dependent part is really computed (not just q passed through)
-    assert rel(avg - prob.q.numpy(), a_ref - prob.q.numpy()) < 1e-3
+    check(prob, precision, (TOL if N <= 10 else TOL_N11)[precision])
+
+
+@pytest.mark.parametrize("precision", list(TOL_COARSE))
+@pytest.mark.parametrize("N,h", [(3, 0.25), (5, 0.2), (7, 0.25), (9, 0.2), (10, 0.25), (10, 0.2)])
+def test_mixed_parity_coarse(precision, N, h):
+    """Coarse fields (the large sets of the batched workload have h = 1/4 ..
+    1/9): the later Taylor terms stay large, so more of them need float-float."""
+    prob = elastic_problem(N, grid=(4, 4, 4), h=h, E=6, seed_material=500 + N,
+                           seed_waves=600 + N)
+    check(prob, precision, TOL_COARSE[precision])
 
 
 @pytest.mark.parametrize("precision", list(TOL))
@@ -75,21 +107,24 @@ def test_mixed_order9_16384_elements_sampled(precision):
     prob = elastic_problem(10, grid=(32, 32, 16), h=1.0 / 32, device="cuda")
     rng = np.random.default_rng(9)
     idx = np.unique(np.concatenate([[0, prob.E - 1], rng.choice(prob.E, 40, replace=False)]))
-    avg, faces = run(prob, precision, idx)
-    it = torch.as_tensor(idx, device="cuda")
-    a_ref, f_ref = oracle.stp(prob.q[it].cpu().numpy(), prob.params[it].cpu().numpy(),
-                              prob.h, prob.dt)
-    errs = errors(avg, faces, a_ref, f_ref)
-    assert max(errs) <= TOL[precision], errs
+    check(prob, precision, TOL[precision], idx)
 
 
-@pytest.mark.parametrize("precision", ["bf16x3", "fp32"])
+@pytest.mark.parametrize("precision", ["bf16x3", "fp16x2", "fp32"])
 def test_mixed_constant_state_exact(precision):
     N, E = 8, 3
     prob = elastic_problem(N, E=E)
     prob.q = prob.q[:, :1, :1, :1, :].expand(E, N, N, N, 9).contiguous()
     avg, faces = run(prob, precision)
     assert rel(avg, prob.q.numpy()) <= 1e-13
+
+
+@pytest.mark.parametrize("precision", TC)
+def test_zero_state_stays_zero(precision):
+    prob = elastic_problem(6, E=4)
+    prob.q = torch.zeros_like(prob.q)
+    avg, faces = run(prob, precision)
+    assert not np.any(avg) and not np.any(faces)
 
 
 @pytest.mark.parametrize("precision", ["fp16x3", "fp32"])
