@@ -93,9 +93,9 @@ def kernel_source_hash() -> str:
     return h.hexdigest()[:16]
 
 
-def traffic_from_profile(workload: str):
-    """DRAM bytes per launch from the committed ncu summary, if it was taken
-    on the current kernel source; else None."""
+def profile_record(workload: str):
+    """The committed ncu record of the FP64 kernel on this workload, if it was
+    taken on the current kernel source; else None."""
     path = os.path.join(PROFILES, f"traffic_fp64_stp_{workload}.json")
     try:
         with open(path) as f:
@@ -104,7 +104,25 @@ def traffic_from_profile(workload: str):
         return None
     if rec.get("kernel_source_sha") != kernel_source_hash():
         return None
-    return rec.get("dram_bytes_per_launch")
+    return rec
+
+
+def traffic_from_profile(workload: str):
+    """DRAM bytes per launch from the committed ncu record (stored figure, not
+    measured in this run), or None."""
+    rec = profile_record(workload)
+    return None if rec is None else rec.get("dram_bytes_per_launch")
+
+
+def fp64_pipe_fraction(workload: str, ms_per_launch: float, sm_mhz):
+    """Share of the FP64 pipe's issue capacity the kernel used: thread-level
+    FP64 instructions per launch (committed ncu record) over 2 per clock per
+    SM x 152 SMs x the SM clock sampled during the timed region x the launch
+    time. Independent of how many flops an instruction is counted for."""
+    rec = profile_record(workload)
+    if rec is None or not rec.get("fp64_thread_inst_per_launch") or not sm_mhz:
+        return None
+    return rec["fp64_thread_inst_per_launch"] / (2 * 152 * sm_mhz * 1e6 * ms_per_launch / 1e3)
 
 
 class ClockSampler:
@@ -756,6 +774,7 @@ def run_gpu(args):
     avg, faces = P.empty_outputs(E, device=dev)
 
     fp64_probe = stp.stp_measure_fp64_peak(stream)
+    dmma_probe = stp.stp_measure_fp64_peak_kind("dmma", stream)
 
     for _ in range(args.warmup):
         P.predict(prob.q, prob.params, out=(avg, faces), stream=stream, metric=metric)
@@ -887,6 +906,11 @@ def run_gpu(args):
                          "traffic": traffic,
                          "peak_kind": "derived: 152 SM x 2 DFMA/clk x 2 flop x 2.07 GHz",
                          "fp64_probe_tflops": fp64_probe / 1e3,
+                         "dmma_probe_tflops": dmma_probe / 1e3,
+                         "fp64_pipe_frac": None if curv else fp64_pipe_fraction(
+                             args.workload, mean_step_s * 1e3, (clocks or {}).get("sm_mhz")),
+                         "traffic_source": "stored ncu record of this kernel source (4096-element "
+                                           "capture scaled by elements), not measured in this run",
                          "frac_of_probe": achieved / (fp64_probe / 1e3),
                          "flops_per_element": fpe,
                          "flops_per_element_dense_count": None if curv else flops_per_element_dense(N),

@@ -585,6 +585,15 @@ const char* stp_last_error(void);
  */
 stp_status stp_measure_fp64_peak(double* gflops, void* stream);
 
+/*
+ * The FP64 throughput probe with a choice of instruction: kind 0 = DFMA (as
+ * stp_measure_fp64_peak), kind 1 = the warp-level FP64 MMA m8n8k4 (DMMA,
+ * 512 flop per warp instruction), the tensor-core alternative for FP64
+ * contractions. *gflops receives the best of five launches on `stream`.
+ * STP_ERR_INVALID_ARG for another kind or a NULL gflops.
+ */
+stp_status stp_measure_fp64_peak_kind(int kind, double* gflops, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -11,7 +11,7 @@ from ._binding import stp_ader_step, stp_correct, stp_face_params  # noqa: F401
 from ._binding import (NODE_FAMILIES, PRECISIONS, STPError, stp_create,  # noqa: F401
                        stp_destroy, stp_device_status, stp_get_nodes, stp_get_precision,
                        stp_last_error,
-                       stp_measure_fp64_peak, stp_nodes, stp_predict, stp_predict_host,
+                       stp_measure_fp64_peak, stp_measure_fp64_peak_kind, stp_nodes, stp_predict, stp_predict_host,
                        stp_predict_curvilinear, stp_predict_curvilinear_host,
                        stp_predict_sources, stp_predict_sources_curvilinear,
                        stp_reference_tables, stp_selftest_bounded_wait, stp_set_precision,

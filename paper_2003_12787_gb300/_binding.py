@@ -266,6 +266,18 @@ def stp_measure_fp64_peak(stream=None) -> float:
     return g.value
 
 
+def stp_measure_fp64_peak_kind(kind: str, stream=None) -> float:
+    """FP64 probe in GFLOP/s with kind "dfma" or "dmma" (warp-level FP64 MMA)."""
+    g = ctypes.c_double()
+    lib = load()
+    lib.stp_measure_fp64_peak_kind.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_double),
+                                               ctypes.c_void_p]
+    lib.stp_measure_fp64_peak_kind.restype = ctypes.c_int
+    _check(lib.stp_measure_fp64_peak_kind({"dfma": 0, "dmma": 1}[kind], ctypes.byref(g),
+                                          _stream(stream)), "stp_measure_fp64_peak_kind")
+    return g.value
+
+
 class PointSource(ctypes.Structure):
     """Mirror of stp_point_source."""
     _fields_ = [("element", ctypes.c_int64), ("position", ctypes.c_double * 3),

@@ -1063,7 +1063,12 @@ stp_status stp_server_destroy(stp_server s) {
 }
 
 stp_status stp_measure_fp64_peak(double* gflops, void* stream) {
+  return stp_measure_fp64_peak_kind(0, gflops, stream);
+}
+
+stp_status stp_measure_fp64_peak_kind(int kind, double* gflops, void* stream) {
   if (!gflops) return fail(STP_ERR_INVALID_ARG, "gflops is NULL");
+  if (kind != 0 && kind != 1) return fail(STP_ERR_INVALID_ARG, "kind must be 0 (DFMA) or 1 (DMMA)");
   int dev = 0, sms = 0;
   cudaError_t e;
   if ((e = cudaGetDevice(&dev)) != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
@@ -1076,17 +1081,24 @@ stp_status stp_measure_fp64_peak(double* gflops, void* stream) {
   cudaEventCreate(&a);
   cudaEventCreate(&b);
   // warm-up long enough (~100 ms) for the SM clock to leave its idle state
-  for (int rep = 0; rep < 6; ++rep) stp::launch_fp64_peak(sink, blocks, threads, iters, st);
+  auto launch = [&]() {
+    return kind == 0 ? stp::launch_fp64_peak(sink, blocks, threads, iters, st)
+                     : stp::launch_dmma_peak(sink, blocks, threads, iters / 4, st);
+  };
+  for (int rep = 0; rep < 6; ++rep) launch();
   double best = 0.0;
   for (int rep = 0; rep < 5; ++rep) {
     cudaEventRecord(a, st);
-    e = stp::launch_fp64_peak(sink, blocks, threads, iters, st);
+    e = launch();
     cudaEventRecord(b, st);
     if (e != cudaSuccess) break;
     if ((e = cudaEventSynchronize(b)) != cudaSuccess) break;
     float ms = 0.f;
     cudaEventElapsedTime(&ms, a, b);
-    const double flops = 2.0 * 8.0 * iters * (double)blocks * threads;
+    // DFMA: 8 chains x 2 flop per thread and iteration; DMMA: 4 fragments x
+    // 512 flop per warp and iteration
+    const double flops = kind == 0 ? 2.0 * 8.0 * iters * (double)blocks * threads
+                                   : 4.0 * 512.0 * (iters / 4) * (double)blocks * (threads / 32);
     const double g = flops / (ms * 1e-3) / 1e9;
     if (g > best) best = g;
   }

@@ -176,5 +176,8 @@ cudaError_t launch_face_params(int N, int64_t E, const double* tables, const dou
 
 cudaError_t launch_fp64_peak(double* sink, int blocks, int threads, int iters,
                              cudaStream_t stream);
+// The same with the warp-level FP64 MMA (m8n8k4, 512 flop per warp instruction).
+cudaError_t launch_dmma_peak(double* sink, int blocks, int threads, int iters,
+                             cudaStream_t stream);
 
 }  // namespace stp
