@@ -604,9 +604,15 @@ def served_measurement(stp, torch, args):
                                        for r in recipe) / 2 ** 30), **main}
     if args.served_sub_requests > 0:
         # the same server below its measured capacity, so that latency is
-        # service time rather than queueing (arrivals seed 1007)
-        out["below_capacity"] = timed_trace(0.7 * main["throughput_req_s"], 0,
-                                            args.served_sub_requests, 1007)
+        # service time rather than queueing (arrivals seed 1007), with the
+        # default resident-first order and then with FIFO on the same trace
+        sub_rate = 0.7 * main["throughput_req_s"]
+        out["below_capacity"] = timed_trace(sub_rate, 0, args.served_sub_requests, 1007)
+        out["below_capacity"]["policy"] = "resident first, age bound 0.05 s"
+        srv.set_policy(0)
+        out["below_capacity_fifo"] = timed_trace(sub_rate, 0, args.served_sub_requests, 1007)
+        out["below_capacity_fifo"]["policy"] = "FIFO"
+        srv.set_policy(1, 0.05)
     if not args.no_served_ff:
         # the same trace with every simulation's handle switched to float-float
         # (FP64-class results, one launch per simulation instead of the
@@ -618,6 +624,68 @@ def served_measurement(stp, torch, args):
     srv.close()
     for P in preds:
         P.close()
+    return out
+
+
+def served_cfg5_measurement(stp, torch, args):
+    """The served workload at its stated sizes: 256 simulations, orders 3-9,
+    64-32768 elements each (log-uniform, seed 1005), state and material
+    generated on the GPU and added from device buffers (they start resident;
+    pinned host copies would be made only on eviction), a pool of
+    args.cfg5_budget_gb, Poisson arrivals at args.served_rate req/s (seed
+    1006): far above the FP64 capacity (about 8.7 GFLOP per request), so the
+    latency of the over-capacity trace is queueing, reported as measured. A
+    second trace at 0.7x the measured throughput (seed 1007) gives the service
+    latency."""
+    from paper_2003_12787_gb300.inputs import elastic_problem, served_arrivals, served_recipe
+    recipe = served_recipe(e_max=32768)
+    budget = int(args.cfg5_budget_gb * 1e9)
+    srv = stp.Server(budget, slots=args.served_slots)
+    preds = []
+    for r in recipe:
+        prob = elastic_problem(r["N"], grid=r["grid"], E=r["E"], h=r["h"],
+                               seed_material=r["seed_material"], seed_waves=r["seed_waves"],
+                               device="cuda")
+        P = stp.Predictor(r["N"] - 1, prob.h, prob.dt)
+        srv.add_sim(P, prob.q, prob.params)
+        preds.append(P)
+        del prob
+    torch.cuda.empty_cache()
+    E = np.array([r["E"] for r in recipe])
+    flops = np.array([r["E"] * flops_per_element(r["N"]) for r in recipe], dtype=np.float64)
+
+    def trace(rate, n, seed):
+        t, ids = served_arrivals(n, rate=rate, n_sims=len(recipe), seed=seed)
+        before = srv.stats()
+        lat, wall = srv.run_trace(t - t[0], ids)
+        after = srv.stats()
+        launches = after["launches"] - before["launches"]
+        return {"rate_req_s": rate, "requests": n,
+                "p50_ms": float(np.percentile(lat, 50) * 1e3),
+                "p99_ms": float(np.percentile(lat, 99) * 1e3),
+                "mean_ms": float(lat.mean() * 1e3), "wall_s": wall,
+                "throughput_req_s": n / wall,
+                "element_updates_per_s": int(E[ids].sum()) / wall,
+                "tflops_algorithmic": float(flops[ids].sum()) / wall / 1e12,
+                "launches": launches, "mean_batch": n / max(1, launches),
+                "admissions": after["admissions"] - before["admissions"],
+                "evictions": after["evictions"] - before["evictions"],
+                "pool_peak_gb": after["pool_bytes_peak"] / 1e9}
+
+    over = trace(args.served_rate, args.cfg5_requests, 1006)
+    out = {"workload": "256 simulations, orders 3-9 (N=4..10), 64-32768 elements each "
+                       "(log-uniform, seed 1005), one FP64 STP step per request",
+           "hbm_budget_gb": args.cfg5_budget_gb,
+           "total_footprint_gb": float(sum(8 * r["E"] * (21 * r["N"] ** 3 + 54 * r["N"] ** 2
+                                                         + 9 * r["N"] ** 3) for r in recipe) / 1e9),
+           "mean_gflop_per_request": float(flops.mean() / 1e9),
+           "over_capacity": over}
+    if args.cfg5_sub_requests > 0:
+        out["below_capacity"] = trace(0.7 * over["throughput_req_s"], args.cfg5_sub_requests, 1007)
+    srv.close()
+    for P in preds:
+        P.close()
+    torch.cuda.empty_cache()
     return out
 
 
@@ -728,9 +796,19 @@ def compact_summary(line):
         ff = sv.get("float_float")
         if ff:
             out["served"]["ff"] = [r(ff["throughput_req_s"]), r(ff["p50_ms"]), r(ff["p99_ms"])]
-        c5 = sv.get("cfg5")
-        if c5:
-            out["served"]["cfg5"] = [r(c5["throughput_req_s"]), r(c5["p50_ms"]), r(c5["p99_ms"])]
+        bf = sv.get("below_capacity_fifo")
+        if bf:
+            out["served"]["below_capacity_fifo"] = [r(bf["throughput_req_s"]), r(bf["p50_ms"]),
+                                                    r(bf["p99_ms"])]
+    c5 = line.get("served_cfg5")
+    if c5:
+        o = c5["over_capacity"]
+        out["served_cfg5"] = {"req_s": r(o["throughput_req_s"]), "p50_ms": r(o["p50_ms"]),
+                              "p99_ms": r(o["p99_ms"]), "tflops": r(o["tflops_algorithmic"])}
+        b = c5.get("below_capacity")
+        if b:
+            out["served_cfg5"]["below_capacity"] = [r(b["throughput_req_s"]), r(b["p50_ms"]),
+                                                    r(b["p99_ms"])]
     a = line.get("ader_step")
     if a:
         out["ader_step"] = {"step_ms": r(a["step_ms"]), "corrector_ms": r(a["corrector_ms"]),
@@ -866,6 +944,9 @@ def run_gpu(args):
     served = None
     if extras and not args.no_served:
         served = served_measurement(stp, torch, args)
+    served_cfg5 = None
+    if extras and not args.no_served and args.cfg5_requests > 0:
+        served_cfg5 = served_cfg5_measurement(stp, torch, args)
     ader = None
     if extras and not args.no_ader:
         ader = ader_measurement(stp, torch, args)
@@ -920,7 +1001,7 @@ def run_gpu(args):
             "latency_ms": {"p50": statistics.median(step_ms), "p99": p99,
                            "min": min(step_ms), "max": max(step_ms)},
             "e2e": e2e, "cpu_baseline": cpu, "clocks": clocks, "mixed": mixed, "variants_same_workload": variants7,
-            "small_case": small, "batched": batched, "served": served,
+            "small_case": small, "batched": batched, "served": served, "served_cfg5": served_cfg5,
             "curvilinear": curvilinear, "ader_step": ader,
             "gpu_launches": args.steps, "parity_max_rel_sampled": parity,
             "paper_context": {
@@ -1014,6 +1095,12 @@ def build_parser():
     ap.add_argument("--served-emax", type=int, default=2048)
     ap.add_argument("--served-budget-gb", type=float, default=2.0)
     ap.add_argument("--served-slots", type=int, default=3)
+    ap.add_argument("--cfg5-requests", type=int, default=1200,
+                    help="requests of the full-size served trace (0 skips it)")
+    ap.add_argument("--cfg5-sub-requests", type=int, default=300,
+                    help="requests of its below-capacity trace")
+    ap.add_argument("--cfg5-budget-gb", type=float, default=160.0,
+                    help="HBM pool of the full-size served trace (GB)")
     ap.add_argument("--precision", default="fp64",
                     choices=list(PRECISIONS_ALL),
                     help="arithmetic of the timed workload (default fp64)")

@@ -479,7 +479,13 @@ stp_status stp_server_create(int64_t hbm_budget_bytes, int slots, stp_server* ou
 
 /* Register a simulation: the handle gives its order, dx, dt and precision;
  * q0 and params ([E][N][N][N][9], [E][N][N][N][3], both host or both device)
- * are copied into server-owned pinned host memory. *sim_id = 0, 1, ... in
+ * are copied into the server, which keeps no reference to them. Device
+ * buffers whose simulation fits the pool as it is are copied straight into the
+ * pool (the simulation starts resident, and its pinned host copies are made
+ * only when it is first evicted, so the pinned footprint follows what is
+ * evicted); otherwise, and for host buffers, they are copied into
+ * server-owned pinned host memory and admitted on the first request. The call
+ * is synchronous. *sim_id = 0, 1, ... in
  * order. FP64 simulations share the persistent batched launch; a simulation
  * whose handle runs another precision (read at each launch) gets a launch of
  * its own with the handle's kernel, on the same slot stream. STP_ERR_INVALID_ARG
@@ -499,6 +505,20 @@ stp_status stp_server_add_sim(stp_server s, stp_handle h, int64_t elements, cons
 stp_status stp_server_add_sim_curvilinear(stp_server s, stp_handle h, int64_t elements,
                                           const double* q0, const double* params,
                                           const double* metric, int* sim_id);
+
+/*
+ * Order in which the scheduler offers ready simulations to a launch.
+ *   policy 0  FIFO: in the order their requests became ready.
+ *   policy 1  resident first (the default, age bound 0.05 s): first every
+ *             simulation whose oldest request has waited at least age_bound_s
+ *             seconds, then those already resident in the pool, then the
+ *             rest, each group in FIFO order. A resident simulation needs no
+ *             admission copy and evicts nothing; the age bound keeps the
+ *             others from waiting without limit.
+ * Takes effect at the next scheduler pass. STP_ERR_INVALID_ARG for another
+ * policy or a negative or non-finite bound.
+ */
+stp_status stp_server_set_policy(stp_server s, int policy, double age_bound_s);
 
 /* Queue one step of a simulation (arrival time = now). */
 stp_status stp_server_submit(stp_server s, int sim_id);

@@ -20,5 +20,6 @@ from ._binding import (stp_autotune, stp_batch_create, stp_batch_destroy,  # noq
                        stp_batch_info, stp_batch_launch, stp_batch_run_static)
 from ._binding import (stp_server_add_sim, stp_server_create, stp_server_destroy,  # noqa: F401
                        stp_server_drain, stp_server_progress, stp_server_read,
-                       stp_server_run_trace, stp_server_stats, stp_server_submit)
+                       stp_server_run_trace, stp_server_set_policy, stp_server_stats,
+                       stp_server_submit)
 from .predictor import Batch, Predictor, Server  # noqa: F401

@@ -100,6 +100,7 @@ def load():
                "stp_server_add_sim_curvilinear": [vp, vp, i64, vp, vp, vp,
                                                   ctypes.POINTER(ctypes.c_int)],
                "stp_server_submit": [vp, ctypes.c_int],
+               "stp_server_set_policy": [vp, ctypes.c_int, ctypes.c_double],
                "stp_server_progress": [vp, ctypes.POINTER(ctypes.c_int)],
                "stp_server_drain": [vp],
                "stp_server_run_trace": [vp, i64, vp, vp, vp, ctypes.POINTER(dbl)],
@@ -423,6 +424,12 @@ def stp_server_add_sim(srv: int, handle: int, elements: int, q0, params, metric=
                                                      _ptr(metric), ctypes.byref(i)),
                "stp_server_add_sim_curvilinear")
     return i.value
+
+
+def stp_server_set_policy(srv: int, policy: int, age_bound_s: float = 0.05) -> None:
+    """Ready order of the scheduler: 0 FIFO, 1 resident first with an age bound."""
+    _check(load().stp_server_set_policy(srv, int(policy), float(age_bound_s)),
+           "stp_server_set_policy")
 
 
 def stp_server_submit(srv: int, sim_id: int) -> None:

@@ -4,6 +4,7 @@
 // tests compile them on their own.
 #pragma once
 #include <cstddef>
+#include <vector>
 
 namespace stp {
 
@@ -34,6 +35,32 @@ inline bool batch_has_room(size_t batch_size, size_t batch_bytes, size_t bytes, 
                            size_t budget) {
   if (batch_size == 0 || slots <= 1) return true;
   return batch_bytes + bytes <= budget / 2;
+}
+
+// Order in which the ready simulations are offered to the batch being formed.
+// `ready` lists simulation ids in the order they became ready (FIFO). Policy 0
+// (FIFO): that order. Policy 1 (resident first, with an age bound): first
+// every simulation whose oldest request has waited at least `age_bound`
+// seconds, then the ones already resident in the pool, then the rest, each
+// group in FIFO order - a resident simulation needs no admission copy (and
+// evicts nothing), while the age bound keeps a non-resident one from waiting
+// without limit behind them. Uses sims[i].resident and
+// sims[i].pending.front().t_arrival (every ready simulation has a request).
+template <class Sims, class Ready>
+void ready_order(const Sims& sims, const Ready& ready, int policy, double now, double age_bound,
+                 std::vector<int>* out) {
+  out->clear();
+  if (policy == 0) {
+    for (int i : ready) out->push_back(i);
+    return;
+  }
+  auto aged = [&](int i) { return now - sims[i].pending.front().t_arrival >= age_bound; };
+  for (int i : ready)
+    if (aged(i)) out->push_back(i);
+  for (int i : ready)
+    if (!aged(i) && sims[i].resident) out->push_back(i);
+  for (int i : ready)
+    if (!aged(i) && !sims[i].resident) out->push_back(i);
 }
 
 }  // namespace stp

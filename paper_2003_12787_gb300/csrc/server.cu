@@ -67,6 +67,10 @@ struct Sim {
   double* host_params = nullptr;  // pinned
   double* host_metric = nullptr;  // pinned (curvilinear simulations only)
   double* host_faces = nullptr;   // pinned: last faces while evicted
+  // whether the pinned host copies exist: a simulation added from device
+  // buffers that fit the pool starts resident without them, and gets them on
+  // its first eviction (the pinned footprint follows what is evicted)
+  bool host_backed = false;
   bool resident = false;
   size_t off = 0;  // pool offset of [state0 | state1 | params | faces | metric]
   int cur = 0;     // which state buffer holds q_n
@@ -98,12 +102,15 @@ struct Server {
   std::vector<Sim> sims;
   std::vector<Slot> slots;
   std::deque<int> ready;  // simulations with a request, not running, FIFO
+  int policy = 1;           // ready order (serve_policy.h): 0 FIFO, 1 resident first
+  double age_bound = 0.05;  // seconds a request may wait before it goes first
   cudaStream_t copy_stream = nullptr;   // admissions (host to device)
   cudaStream_t evict_stream = nullptr;  // evictions (device to host)
   cudaEvent_t copy_done = nullptr;
   cudaEvent_t evict_done = nullptr;
   Clock::time_point t0 = Clock::now();
   int64_t tick = 0;
+  std::vector<int> order;  // scratch of the ready order
   // statistics
   int64_t completed = 0, batches = 0, admissions = 0, evictions = 0, max_batch = 0,
           batched_requests = 0, next_id = 0;
@@ -129,9 +136,27 @@ struct Server {
                                      align_up(s.bytes_params) + align_up(s.bytes_faces));
   }
 
+  // Pinned host copies of simulation i (state, material, faces, metric).
+  cudaError_t make_host_backing(Sim& s) {
+    cudaError_t e = cudaMallocHost(&s.host_q, std::max<size_t>(s.bytes_state, 8));
+    if (e == cudaSuccess) e = cudaMallocHost(&s.host_params, std::max<size_t>(s.bytes_params, 8));
+    if (e == cudaSuccess) e = cudaMallocHost(&s.host_faces, std::max<size_t>(s.bytes_faces, 8));
+    if (e == cudaSuccess && s.bytes_metric) e = cudaMallocHost(&s.host_metric, s.bytes_metric);
+    if (e == cudaSuccess) s.host_backed = true;
+    return e;
+  }
+
   cudaError_t evict(int i) {
     Sim& s = sims[i];
-    cudaError_t e = cudaMemcpyAsync(s.host_q, state(s, s.cur), s.bytes_state, cudaMemcpyDeviceToHost, evict_stream);
+    cudaError_t e = cudaSuccess;
+    if (!s.host_backed) {  // first eviction: the material (and metric) leave the pool too
+      if ((e = make_host_backing(s)) != cudaSuccess) return e;
+      e = cudaMemcpyAsync(s.host_params, params(s), s.bytes_params, cudaMemcpyDeviceToHost, evict_stream);
+      if (e == cudaSuccess && s.bytes_metric)
+        e = cudaMemcpyAsync(s.host_metric, metric(s), s.bytes_metric, cudaMemcpyDeviceToHost, evict_stream);
+      if (e != cudaSuccess) return e;
+    }
+    e = cudaMemcpyAsync(s.host_q, state(s, s.cur), s.bytes_state, cudaMemcpyDeviceToHost, evict_stream);
     if (e == cudaSuccess && s.have_faces)
       e = cudaMemcpyAsync(s.host_faces, faces(s), s.bytes_faces, cudaMemcpyDeviceToHost, evict_stream);
     // later admissions (which may reuse this memory or re-admit this
@@ -221,14 +246,15 @@ struct Server {
       std::vector<char> protect(sims.size(), 0);
       std::vector<int> batch;
       bool copied = false;
-      std::deque<int> keep;
       size_t batch_bytes = 0;
-      while (!ready.empty() && (int)batch.size() < static_max_sets()) {
-        const int i = ready.front();
+      // candidates in the policy's order; the ones taken leave the ready
+      // queue, the others keep their FIFO places
+      ready_order(sims, ready, policy, now(), age_bound, &order);
+      for (int i : order) {
+        if ((int)batch.size() >= static_max_sets()) break;
         // at most half the pool per batch, so the next one is admitted meanwhile
         if (!batch_has_room(batch.size(), batch_bytes, sims[i].footprint(), slots.size(), budget))
           break;
-        ready.pop_front();
         cudaError_t ae = cudaSuccess;
         if (admit(i, protect, &copied, &ae)) {
           protect[i] = 1;
@@ -236,16 +262,19 @@ struct Server {
           batch_bytes += sims[i].footprint();
         } else {
           if (ae != cudaSuccess) {  // a copy failed: nothing of this batch runs
-            ready.push_front(i);
-            requeue_front(batch);
-            return ae;
+            for (int j : batch) sims[j].busy = false;
+            return ae;  // the ready queue still holds every simulation of the batch
           }
-          keep.push_back(i);  // does not fit next to this batch: wait
-          break;
+          break;  // does not fit next to this batch: wait
         }
       }
-      for (auto it = keep.rbegin(); it != keep.rend(); ++it) ready.push_front(*it);
       if (batch.empty()) break;
+      {
+        std::deque<int> rest;
+        for (int i : ready)
+          if (!protect[i]) rest.push_back(i);
+        ready.swap(rest);
+      }
       if (copied) {
         e = cudaEventRecord(copy_done, copy_stream);
         if (e == cudaSuccess) e = cudaStreamWaitEvent(sl.stream, copy_done, 0);
@@ -398,10 +427,37 @@ cudaError_t server_add_sim(Server* s, stp_handle h, int N, int64_t E, const doub
     *too_big = true;
     return cudaErrorInvalidValue;
   }
-  cudaError_t e = cudaMallocHost(&sim.host_q, std::max<size_t>(sim.bytes_state, 8));
-  if (e == cudaSuccess) e = cudaMallocHost(&sim.host_params, std::max<size_t>(sim.bytes_params, 8));
-  if (e == cudaSuccess) e = cudaMallocHost(&sim.host_faces, std::max<size_t>(sim.bytes_faces, 8));
-  if (e == cudaSuccess && metric) e = cudaMallocHost(&sim.host_metric, sim.bytes_metric);
+  size_t off = 0;
+  if (device_src && s->pool.alloc(sim.footprint(), &off)) {
+    // fits the pool as it is: admitted now by device-to-device copies, with
+    // no host copies until its first eviction
+    sim.off = off;
+    sim.resident = true;
+    sim.cur = 0;
+    // device-to-device copies return before they complete: they run on the
+    // admission stream, which is synchronised before the call returns (the
+    // caller may free its buffers then, and the launches that read the pool
+    // run on other, non-blocking streams)
+    cudaError_t e = cudaMemcpyAsync(s->state(sim, 0), q0, sim.bytes_state, cudaMemcpyDeviceToDevice,
+                                    s->copy_stream);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(s->params(sim), params, sim.bytes_params, cudaMemcpyDeviceToDevice,
+                          s->copy_stream);
+    if (e == cudaSuccess && metric)
+      e = cudaMemcpyAsync(s->metric(sim), metric, sim.bytes_metric, cudaMemcpyDeviceToDevice,
+                          s->copy_stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s->copy_stream);
+    if (e != cudaSuccess) {
+      s->pool.release(off, sim.footprint());
+      return e;
+    }
+    ++s->admissions;
+    s->peak_used = std::max(s->peak_used, s->pool.used());
+    *id = (int)s->sims.size();
+    s->sims.push_back(sim);
+    return cudaSuccess;
+  }
+  cudaError_t e = s->make_host_backing(sim);
   const cudaMemcpyKind kind = device_src ? cudaMemcpyDeviceToHost : cudaMemcpyHostToHost;
   if (e == cudaSuccess) e = cudaMemcpy(sim.host_q, q0, sim.bytes_state, kind);
   if (e == cudaSuccess) e = cudaMemcpy(sim.host_params, params, sim.bytes_params, kind);
@@ -492,5 +548,14 @@ void server_submit(Server* s, int id) {
 cudaError_t server_progress(Server* s, int* done) { return s->progress(done); }
 
 int server_sims(const Server* s) { return (int)s->sims.size(); }
+
+}  // namespace stp
+
+namespace stp {
+
+void server_set_policy(Server* s, int policy, double age_bound) {
+  s->policy = policy;
+  s->age_bound = age_bound;
+}
 
 }  // namespace stp

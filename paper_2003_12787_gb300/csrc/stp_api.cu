@@ -1006,6 +1006,15 @@ stp_status stp_server_add_sim_curvilinear(stp_server s, stp_handle h, int64_t el
   return server_add_sim_impl(s, h, elements, q0, params, metric, sim_id);
 }
 
+stp_status stp_server_set_policy(stp_server s, int policy, double age_bound_s) {
+  if (!s || !s->impl) return fail(STP_ERR_INVALID_ARG, "invalid server");
+  if (policy != 0 && policy != 1) return fail(STP_ERR_INVALID_ARG, "policy must be 0 or 1");
+  if (!(age_bound_s >= 0.0) || !std::isfinite(age_bound_s))
+    return fail(STP_ERR_INVALID_ARG, "age bound must be finite and >= 0");
+  stp::server_set_policy(s->impl, policy, age_bound_s);
+  return STP_OK;
+}
+
 stp_status stp_server_submit(stp_server s, int sim_id) {
   if (!s || !s->impl || sim_id < 0 || sim_id >= stp::server_sims(s->impl))
     return fail(STP_ERR_INVALID_ARG, "bad server or simulation id");

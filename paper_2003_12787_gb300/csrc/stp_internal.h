@@ -162,6 +162,7 @@ void server_stats(const Server* s, int64_t* out);
 void server_submit(Server* s, int id);
 cudaError_t server_progress(Server* s, int* done);
 int server_sims(const Server* s);
+void server_set_policy(Server* s, int policy, double age_bound);
 
 // Corrector on a periodic grid of gx*gy*gz cubes (corrector.cu): q_out = q +
 // dt (A.(D avg)/dx - lift of the Rusanov fluctuations of the face values);

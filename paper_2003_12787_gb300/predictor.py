@@ -204,7 +204,6 @@ class Server:
         self.handle = B.stp_server_create(hbm_budget_bytes, slots)
         self.budget, self.slots = hbm_budget_bytes, slots
         self.sims = []  # (Predictor, E)
-        self._inputs = []  # (params, metric) of each simulation, for snapshots
         self._steps0 = []  # steps taken before a restore
 
     def add_sim(self, predictor: "Predictor", q0: torch.Tensor, params: torch.Tensor,
@@ -215,7 +214,6 @@ class Server:
             predictor._check_metric(q0, metric)
         sid = B.stp_server_add_sim(self.handle, predictor.handle, q0.shape[0], q0, params, metric)
         self.sims.append((predictor, q0.shape[0]))
-        self._inputs.append((params, metric))
         self._steps0.append(0)
         return sid
 
@@ -239,6 +237,10 @@ class Server:
                         metric=None if metric is None else metric.to(dev))
             srv._steps0[-1] = int(rec["steps"])
         return srv
+
+    def set_policy(self, policy: int, age_bound_s: float = 0.05):
+        """Ready order of the scheduler: 0 FIFO, 1 resident first (default)."""
+        B.stp_server_set_policy(self.handle, policy, age_bound_s)
 
     def submit(self, sim_id: int):
         B.stp_server_submit(self.handle, sim_id)

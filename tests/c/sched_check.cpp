@@ -2,6 +2,7 @@
 // victim against a brute-force reading of the rule over seeded random
 // simulation tables, and the half-pool batch bound on its cases.
 // Prints "ok <cases>" and exits 0, or the first mismatch and exits 1.
+#include <algorithm>
 #include <cstdint>
 #include <cstdio>
 #include <deque>
@@ -41,6 +42,28 @@ int expected_victim(const std::vector<SimRec>& s, const std::vector<char>& prot,
   return -1;
 }
 
+struct Req {
+  double t_arrival;
+};
+struct ReadyRec {
+  bool resident = false;
+  std::deque<Req> pending;
+};
+
+// The ready order read literally: a stable sort of the FIFO list by the key
+// (aged: 0, resident: 1, other: 2); FIFO unchanged for policy 0.
+std::vector<int> expected_order(const std::vector<ReadyRec>& s, const std::vector<int>& ready,
+                                int policy, double now, double bound) {
+  std::vector<int> out(ready);
+  if (policy == 0) return out;
+  auto key = [&](int i) {
+    if (now - s[i].pending.front().t_arrival >= bound) return 0;
+    return s[i].resident ? 1 : 2;
+  };
+  std::stable_sort(out.begin(), out.end(), [&](int a, int b) { return key(a) < key(b); });
+  return out;
+}
+
 }  // namespace
 
 int main() {
@@ -77,6 +100,27 @@ int main() {
     if (stp::batch_has_room(c.size, c.bytes, c.add, c.slots, c.budget) != c.room) {
       std::printf("mismatch: batch bound (%zu, %zu, %zu, %zu, %zu)\n", c.size, c.bytes, c.add,
                   c.slots, c.budget);
+      return 1;
+    }
+    ++cases;
+  }
+  for (int t = 0; t < 20000; ++t) {
+    const int n = 1 + (int)(next_u64() % 10);
+    std::vector<ReadyRec> sims((size_t)n);
+    for (int j = 0; j < n; ++j) {
+      sims[j].resident = next_u64() % 2 != 0;
+      sims[j].pending.push_back(Req{(double)(next_u64() % 100) * 1e-3});
+    }
+    std::vector<int> ready;
+    for (int j = 0; j < n; ++j)
+      if (next_u64() % 4 != 0) ready.push_back(j);
+    for (size_t a = ready.size(); a > 1; --a) std::swap(ready[a - 1], ready[next_u64() % a]);
+    const int policy = (int)(next_u64() % 2);
+    const double now = 0.1, bound = (double)(next_u64() % 60) * 1e-3;
+    std::vector<int> got;
+    stp::ready_order(sims, ready, policy, now, bound, &got);
+    if (got != expected_order(sims, ready, policy, now, bound)) {
+      std::printf("mismatch: ready order (case %d)\n", t);
       return 1;
     }
     ++cases;

@@ -205,3 +205,112 @@ def test_served_workload_at_bench_size_sampled_against_oracle():
     srv.close()
     for P in preds:
         P.close()
+
+
+def _repeated_predict(P, prob, steps):
+    """Reference: `steps` single-set predictor calls with q_{n+1} := avg_n."""
+    q = prob.q.cuda() if not prob.q.is_cuda else prob.q.clone()
+    pa = prob.params.cuda()
+    for _ in range(steps):
+        q, faces = P.predict(q, pa)
+    torch.cuda.synchronize()
+    return q.cpu(), faces.cpu()
+
+
+def test_device_added_simulations_start_resident_and_survive_evictions():
+    """Simulations added from device buffers are copied straight into the
+    pool while it has room (no pinned copies); the later ones get pinned copies
+    at once, the early ones on their first eviction. Every result equals the
+    repeated single-set call bit for bit."""
+    sims = []
+    for i, (N, E) in enumerate(SPECS):
+        prob = elastic_problem(N, E=E, seed_material=1900 + i, seed_waves=1950 + i, device="cuda")
+        sims.append((stp.Predictor(N - 1, prob.h, prob.dt), prob))
+    budget = max(footprint(N, E) for N, E in SPECS) * 2 + (1 << 20)
+    srv = stp.Server(budget, slots=3)
+    ids = [srv.add_sim(P, prob.q, prob.params) for P, prob in sims]
+    steps = 3
+    order = np.tile(np.arange(len(sims)), steps)
+    t = np.linspace(0.0, 0.01, len(order))
+    srv.run_trace(t, np.asarray(ids, dtype=np.int32)[order])
+    assert srv.stats()["evictions"] > 0
+    for sid, (P, prob) in zip(ids, sims):
+        q, faces, n = srv.read(sid)
+        q_ref, f_ref = _repeated_predict(P, prob, steps)
+        assert n == steps and torch.equal(q, q_ref) and torch.equal(faces, f_ref), sid
+    srv.close()
+    for P, _ in sims:
+        P.close()
+
+
+def test_ready_order_does_not_change_results():
+    """FIFO and resident-first orders run the same requests in other batches:
+    each simulation's result is the same bit for bit."""
+    sims = problems()
+    budget = max(footprint(N, E) for N, E in SPECS) * 2 + (1 << 20)
+    t, ids = served_arrivals(60, rate=3000.0, n_sims=len(sims), seed=77)
+    out = []
+    for policy in (0, 1):
+        srv = stp.Server(budget, slots=3)
+        srv.set_policy(policy, 0.002)
+        sid = [srv.add_sim(P, prob.q, prob.params) for P, prob in sims]
+        srv.run_trace(t - t[0], np.asarray(sid, dtype=np.int32)[ids])
+        out.append([srv.read(i) for i in sid])
+        srv.close()
+    for (qa, fa, na), (qb, fb, nb) in zip(*out):
+        assert na == nb and torch.equal(qa, qb) and torch.equal(fa, fb)
+    for P, _ in sims:
+        P.close()
+
+
+def test_policy_arguments_are_checked():
+    srv = stp.Server(1 << 24, slots=1)
+    for bad in ((2, 0.1), (1, -1.0), (1, float("inf"))):
+        with pytest.raises(stp.STPError):
+            srv.set_policy(*bad)
+    srv.set_policy(0)
+    srv.close()
+
+
+def test_full_size_simulations_same_alone_and_in_the_mix():
+    """Simulations of the full-size served recipe's extremes (order 9 on
+    32768 elements, 6.8 GB of pool; order 6 on 20000; order 3 on 64; order 8
+    on 5000), added from device buffers: the results of a mixed trace equal
+    each simulation run alone bit for bit, and sampled elements of the largest
+    one match the oracle stepped as often."""
+    import oracle
+    specs = [(10, 32768), (7, 20000), (4, 64), (9, 5000)]
+    probs = [elastic_problem(N, E=E, seed_material=2100 + i, seed_waves=2150 + i, device="cuda")
+             for i, (N, E) in enumerate(specs)]
+    preds = [stp.Predictor(p.N - 1, p.h, p.dt) for p in probs]
+    steps = [2, 3, 4, 2]
+    budget = 40 * 10 ** 9
+    alone = []
+    for P, prob, n in zip(preds, probs, steps):
+        srv = stp.Server(budget, slots=2)
+        sid = srv.add_sim(P, prob.q, prob.params)
+        for _ in range(n):
+            srv.submit(sid)
+        srv.drain()
+        alone.append(srv.read(sid))
+        srv.close()
+    srv = stp.Server(budget, slots=3)
+    ids = [srv.add_sim(P, prob.q, prob.params) for P, prob in zip(preds, probs)]
+    order = np.concatenate([np.full(n, i) for i, n in enumerate(steps)])
+    np.random.default_rng(5).shuffle(order)
+    t = np.linspace(0.0, 0.02, len(order))
+    srv.run_trace(t, np.asarray(ids, dtype=np.int32)[order])
+    for sid, (qa, fa, na) in zip(ids, alone):
+        q, faces, n = srv.read(sid)
+        assert n == na and torch.equal(q, qa) and torch.equal(faces, fa), sid
+    q_big = srv.read(ids[0])[0]
+    srv.close()
+    prob = probs[0]
+    idx = [0, 12345, prob.E - 1]
+    qs = prob.q[idx].cpu().numpy()
+    for _ in range(steps[0]):
+        qs, _f = oracle.stp(qs, prob.params[idx].cpu().numpy(), prob.h, prob.dt)
+    got = q_big[idx].numpy()
+    assert float(np.abs(got - qs).max() / np.abs(qs).max()) <= 1e-12
+    for P in preds:
+        P.close()

@@ -85,6 +85,10 @@ SCHED_MUTANTS = {
     "most recently used instead of least": ("c.last_used < sims[victim].last_used",
                                             "c.last_used > sims[victim].last_used"),
     "no half-pool bound": ("return batch_bytes + bytes <= budget / 2;", "return true;"),
+    "no age bound": ("return now - sims[i].pending.front().t_arrival >= age_bound;", "return false;"),
+    "resident ones last": ("if (!aged(i) && sims[i].resident) out->push_back(i);\n  for (int i : ready)\n    if (!aged(i) && !sims[i].resident)",
+                           "if (!aged(i) && !sims[i].resident) out->push_back(i);\n  for (int i : ready)\n    if (!aged(i) && sims[i].resident)"),
+    "FIFO policy reordered": ("if (policy == 0) {", "if (policy == 2) {"),
 }
 
 
