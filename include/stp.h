@@ -378,6 +378,20 @@ stp_status stp_batch_create_ex(int nsets, const stp_batch_set* sets, const int* 
 stp_status stp_batch_create_curvilinear(int nsets, const stp_batch_set* sets,
                                         const double* const* metrics, stp_batch* out);
 
+/*
+ * A batch plan whose sets may carry point sources (the source term of
+ * Sec. II-A, as in stp_predict_sources): nsources[i] sources at sources[i]
+ * (host arrays) for set i (0 = none); metrics as stp_batch_create_curvilinear
+ * or NULL for a Cartesian batch. The sources' data are prepared and copied to
+ * the device once, here; every stp_batch_launch then runs the plan and, on the
+ * same stream after it, the sources' FP64 response of each set that has any,
+ * added to that set's outputs. Each set's result equals its own
+ * stp_predict_sources. Errors as stp_batch_create and stp_predict_sources.
+ */
+stp_status stp_batch_create_sources(int nsets, const stp_batch_set* sets,
+                                    const double* const* metrics, const int* nsources,
+                                    const stp_point_source* const* sources, stp_batch* out);
+
 /* Enqueue one replay of the plan's graph on `stream` (async). */
 stp_status stp_batch_launch(stp_batch b, void* stream);
 
@@ -443,6 +457,19 @@ stp_status stp_batch_run_static(int nsets, const stp_batch_set* sets, void* stre
  * stp_predict_curvilinear. */
 stp_status stp_batch_run_static_curvilinear(int nsets, const stp_batch_set* sets,
                                             const double* const* metrics, void* stream);
+
+/* stp_batch_run_static with point sources per set (nsources[i] entries at
+ * sources[i], host arrays; metrics as in stp_batch_run_static_curvilinear or
+ * NULL). The sources' prepared data are copied into the top of the same
+ * static array (no allocation), below which the persistent launch keeps its
+ * own scratch; their FP64 response follows the launches on `stream`. The copy
+ * is from pageable host memory: the call returns once the data are staged.
+ * STP_ERR_INVALID_ARG when the data and the launch's scratch together exceed
+ * the 24 MiB array, otherwise as stp_batch_run_static and stp_predict_sources.
+ * The paper has no counterpart to the allocation-free form. */
+stp_status stp_batch_run_static_sources(int nsets, const stp_batch_set* sets,
+                                        const double* const* metrics, const int* nsources,
+                                        const stp_point_source* const* sources, void* stream);
 
 /*
  * Served predictor: a continuously batched request loop over many independent

@@ -17,7 +17,8 @@ from ._binding import (NODE_FAMILIES, PRECISIONS, STPError, stp_create,  # noqa:
                        stp_reference_tables, stp_selftest_bounded_wait, stp_set_precision,
                        stp_status_string)
 from ._binding import (stp_autotune, stp_batch_create, stp_batch_destroy,  # noqa: F401
-                       stp_batch_info, stp_batch_launch, stp_batch_run_static)
+                       stp_batch_info, stp_batch_launch, stp_batch_run_static,
+                       stp_batch_run_static_sources)
 from ._binding import (stp_server_add_sim, stp_server_create, stp_server_destroy,  # noqa: F401
                        stp_server_drain, stp_server_progress, stp_server_read,
                        stp_server_run_trace, stp_server_set_policy, stp_server_stats,

@@ -389,6 +389,66 @@ def stp_autotune(h: int):
     return {"variant": v.value, "us_per_element": us.value, "us_variants": list(allv)}
 
 
+def _source_lists(sources_per_set, N_of_set=None):
+    """Per-set ctypes arrays of PointSource (None or [] for a set without)."""
+    n = len(sources_per_set)
+    counts = (ctypes.c_int * max(1, n))()
+    arrays = []
+    ptrs = (ctypes.c_void_p * max(1, n))()
+    for i, lst in enumerate(sources_per_set):
+        lst = lst or []
+        counts[i] = len(lst)
+        arr = _source_array(lst) if lst else None
+        arrays.append(arr)
+        ptrs[i] = ctypes.cast(arr, ctypes.c_void_p).value if arr is not None else None
+    return counts, ptrs, arrays
+
+
+def stp_batch_create_sources(sets, sources_per_set, N_of_set, metrics=None) -> int:
+    """A batch plan with per-set point sources (lists of source dicts)."""
+    arr = (BatchSet * max(1, len(sets)))()
+    for i, (h, E, q, p, a, f) in enumerate(sets):
+        arr[i] = BatchSet(h, E, _ptr(q), _ptr(p), _ptr(a), _ptr(f))
+    counts, ptrs, keep = _source_lists(sources_per_set, N_of_set)
+    mt = None
+    if metrics is not None:
+        mt = (ctypes.c_void_p * max(1, len(sets)))(*[_ptr(m) for m in metrics])
+    out = ctypes.c_void_p()
+    lib = load()
+    lib.stp_batch_create_sources.argtypes = [ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
+                                             ctypes.c_void_p, ctypes.c_void_p,
+                                             ctypes.POINTER(ctypes.c_void_p)]
+    lib.stp_batch_create_sources.restype = ctypes.c_int
+    _check(lib.stp_batch_create_sources(len(sets), ctypes.cast(arr, ctypes.c_void_p),
+                                        ctypes.cast(mt, ctypes.c_void_p) if mt is not None else None,
+                                        ctypes.cast(counts, ctypes.c_void_p),
+                                        ctypes.cast(ptrs, ctypes.c_void_p), ctypes.byref(out)),
+           "stp_batch_create_sources")
+    del keep
+    return out.value
+
+
+def stp_batch_run_static_sources(sets, sources_per_set, N_of_set, stream=None, metrics=None) -> None:
+    """The allocation-free batched launch with per-set point sources."""
+    arr = (BatchSet * max(1, len(sets)))()
+    for i, (h, E, q, p, a, f) in enumerate(sets):
+        arr[i] = BatchSet(h, E, _ptr(q), _ptr(p), _ptr(a), _ptr(f))
+    counts, ptrs, keep = _source_lists(sources_per_set, N_of_set)
+    mt = None
+    if metrics is not None:
+        mt = (ctypes.c_void_p * max(1, len(sets)))(*[_ptr(m) for m in metrics])
+    lib = load()
+    lib.stp_batch_run_static_sources.argtypes = [ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
+                                                 ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
+    lib.stp_batch_run_static_sources.restype = ctypes.c_int
+    _check(lib.stp_batch_run_static_sources(len(sets), ctypes.cast(arr, ctypes.c_void_p),
+                                            ctypes.cast(mt, ctypes.c_void_p) if mt is not None else None,
+                                            ctypes.cast(counts, ctypes.c_void_p),
+                                            ctypes.cast(ptrs, ctypes.c_void_p), _stream(stream)),
+           "stp_batch_run_static_sources")
+    del keep
+
+
 def stp_batch_run_static(sets, stream=None, metrics=None) -> None:
     """The allocation-free batched launch; sets as for stp_batch_create;
     metrics: optional per-set device metric (None for a Cartesian set)."""

@@ -276,20 +276,39 @@ cudaError_t launch_param_batch(int nsets, const int* N, const int64_t* E, const 
 
 namespace stp {
 
-// sets_N/E/...: validated by the caller. Returns cudaErrorInvalidValue with
-// *too_big = 1 when the call needs more scratch than the static array holds.
+// sets_N/E/...: validated by the caller. The persistent launch uses the
+// array below its top `reserve_top` bytes (which hold the caller's
+// point-source data, see static_scratch_top). Returns cudaErrorInvalidValue
+// with *too_big = 1 when the call needs more scratch than that.
 cudaError_t run_static_batch(int nsets, const int* N, const int64_t* E, const double* const* q,
                              const double* const* params, double* const* avg,
                              double* const* faces, const double* const* tables,
-                             cudaStream_t stream, int* too_big) {
+                             cudaStream_t stream, int* too_big, size_t reserve_top) {
   *too_big = 0;
+  if (reserve_top > kStaticScratchBytes - kCounterBytes) {
+    *too_big = 1;
+    return cudaErrorInvalidValue;
+  }
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
   unsigned char* scratch = nullptr;
   if ((e = scratch_address(dev, &scratch)) != cudaSuccess) return e;
   return launch_param_batch(nsets, N, E, q, params, avg, faces, tables, scratch,
-                            kStaticScratchBytes, stream, too_big);
+                            kStaticScratchBytes - reserve_top, stream, too_big);
+}
+
+// Device address of the top `bytes` of the static array (bytes a multiple of
+// 256): where the allocation-free path keeps point-source data.
+cudaError_t static_scratch_top(size_t bytes, unsigned char** out) {
+  if (bytes > kStaticScratchBytes - kCounterBytes || (bytes & 255u)) return cudaErrorInvalidValue;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  unsigned char* scratch = nullptr;
+  if ((e = scratch_address(dev, &scratch)) != cudaSuccess) return e;
+  *out = scratch + (kStaticScratchBytes - bytes);
+  return cudaSuccess;
 }
 
 }  // namespace stp

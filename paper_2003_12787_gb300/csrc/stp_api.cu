@@ -331,15 +331,28 @@ void lagrange_at(const stp::HostTables& t, long double a, long double* phi) {
 namespace {
 
 // Point sources after the STP of the set (Cartesian when metric is NULL).
-stp_status predict_sources_impl(stp_handle h, int64_t elements, const double* q,
-                                const double* params, const double* metric, double* out_avg,
-                                double* out_faces, int nsources, const stp_point_source* sources,
-                                void* stream) {
+// Point-source data of one set, prepared on the host: sources grouped by
+// element; per source the nodal projection phi_node(pos) / (w_node dx^3)
+// (curvilinear: phi_node(pos) / w_node, the kernel supplies the node volume),
+// the amplitude and dt^(k+1)/(k+2)! f^(k).
+struct SourceData {
+  int N = 0;
+  std::vector<stp::SourceGroup> groups;
+  std::vector<double> proj, amp, cf;
+  // device block layout: groups | proj | amp | cf | scratch (9 N^3 per group)
+  static size_t up(size_t b) { return (b + 255) & ~(size_t)255; }
+  size_t b_groups() const { return sizeof(stp::SourceGroup) * groups.size(); }
+  size_t b_proj() const { return sizeof(double) * proj.size(); }
+  size_t b_amp() const { return sizeof(double) * amp.size(); }
+  size_t b_cf() const { return sizeof(double) * cf.size(); }
+  size_t b_scr() const { return sizeof(double) * groups.size() * 9 * (size_t)N * N * N; }
+  size_t bytes() const { return up(b_groups()) + up(b_proj()) + up(b_amp()) + up(b_cf()) + up(b_scr()); }
+};
+
+stp_status validate_sources(stp_handle h, int64_t elements, int nsources,
+                            const stp_point_source* sources) {
   if (nsources < 0 || (nsources > 0 && !sources))
     return fail(STP_ERR_INVALID_ARG, "bad source list");
-  stp_status s = metric ? validate_curvilinear(h, elements, q, params, metric, out_avg, out_faces)
-                        : validate_common(h, elements, q, params, out_avg, out_faces);
-  if (s != STP_OK) return s;
   for (int i = 0; i < nsources; ++i) {
     const stp_point_source& src = sources[i];
     if (src.element < 0 || src.element >= elements)
@@ -354,26 +367,27 @@ stp_status predict_sources_impl(stp_handle h, int64_t elements, const double* q,
       if (!std::isfinite(src.derivatives[k]))
         return fail(STP_ERR_INVALID_ARG, "source " + std::to_string(i) + ": non-finite derivative");
   }
-  s = metric ? stp_predict_curvilinear(h, elements, q, params, metric, out_avg, out_faces, stream)
-             : stp_predict(h, elements, q, params, out_avg, out_faces, stream);
-  if (s != STP_OK) return s;
-  if (nsources == 0 || elements == 0) return STP_OK;
+  return STP_OK;
+}
+
+void prepare_sources(stp_handle h, bool curvilinear, int nsources, const stp_point_source* sources,
+                     SourceData* out) {
   const int N = h->N, N3 = N * N * N;
-  // group the sources by element; per source: the nodal projection
-  // phi_node(pos) / (w_node dx^3) (curvilinear: phi_node(pos) / w_node, the
-  // kernel supplies the node volume), the amplitude and dt^(k+1)/(k+2)! f^(k)
+  out->N = N;
+  out->groups.clear();
   std::vector<int> order(nsources);
   for (int i = 0; i < nsources; ++i) order[i] = i;
   std::stable_sort(order.begin(), order.end(),
                    [&](int a, int b) { return sources[a].element < sources[b].element; });
-  std::vector<stp::SourceGroup> groups;
-  std::vector<double> proj((size_t)nsources * N3), amp((size_t)nsources * 9), cf((size_t)nsources * N);
-  const long double h3 = metric ? 1.0L : (long double)h->dx * h->dx * h->dx;
+  out->proj.assign((size_t)nsources * N3, 0.0);
+  out->amp.assign((size_t)nsources * 9, 0.0);
+  out->cf.assign((size_t)nsources * N, 0.0);
+  const long double h3 = curvilinear ? 1.0L : (long double)h->dx * h->dx * h->dx;
   for (int r = 0; r < nsources; ++r) {
     const stp_point_source& src = sources[order[r]];
-    if (groups.empty() || groups.back().element != src.element)
-      groups.push_back(stp::SourceGroup{src.element, r, 0});
-    ++groups.back().count;
+    if (out->groups.empty() || out->groups.back().element != src.element)
+      out->groups.push_back(stp::SourceGroup{src.element, r, 0});
+    ++out->groups.back().count;
     long double px[stp::kMaxNodes], py[stp::kMaxNodes], pz[stp::kMaxNodes];
     lagrange_at(h->host, src.position[0], px);
     lagrange_at(h->host, src.position[1], py);
@@ -382,38 +396,63 @@ stp_status predict_sources_impl(stp_handle h, int64_t elements, const double* q,
     for (int z = 0; z < N; ++z)
       for (int y = 0; y < N; ++y)
         for (int x = 0; x < N; ++x)
-          proj[(size_t)r * N3 + (z * N + y) * N + x] =
+          out->proj[(size_t)r * N3 + (z * N + y) * N + x] =
               (double)(pz[z] * py[y] * px[x] / ((long double)w[z] * w[y] * w[x] * h3));
-    for (int k = 0; k < 9; ++k) amp[(size_t)r * 9 + k] = src.amplitude[k];
+    for (int k = 0; k < 9; ++k) out->amp[(size_t)r * 9 + k] = src.amplitude[k];
     long double c = 1.0L;  // dt^(k+1) / (k+2)!
     for (int k = 0; k < N; ++k) {
       c = c * (long double)h->dt / (long double)(k + 2);
-      cf[(size_t)r * N + k] = (double)(c * (long double)src.derivatives[k]);
+      out->cf[(size_t)r * N + k] = (double)(c * (long double)src.derivatives[k]);
     }
   }
-  const int G = (int)groups.size();
-  const size_t b_groups = sizeof(stp::SourceGroup) * G, b_proj = sizeof(double) * proj.size(),
-               b_amp = sizeof(double) * amp.size(), b_cf = sizeof(double) * cf.size(),
-               b_scr = sizeof(double) * (size_t)G * 9 * N3;
-  auto up = [](size_t b) { return (b + 255) & ~(size_t)255; };
-  const size_t total = up(b_groups) + up(b_proj) + up(b_amp) + up(b_cf) + up(b_scr);
+}
+
+// Copies the prepared data into a device block of sd.bytes() bytes on `st`.
+cudaError_t upload_sources(const SourceData& sd, char* d, cudaStream_t st) {
+  char* d_proj = d + SourceData::up(sd.b_groups());
+  char* d_amp = d_proj + SourceData::up(sd.b_proj());
+  char* d_cf = d_amp + SourceData::up(sd.b_amp());
+  cudaError_t e = cudaMemcpyAsync(d, sd.groups.data(), sd.b_groups(), cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(d_proj, sd.proj.data(), sd.b_proj(), cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(d_amp, sd.amp.data(), sd.b_amp(), cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(d_cf, sd.cf.data(), sd.b_cf(), cudaMemcpyHostToDevice, st);
+  return e;
+}
+
+// The sources' response of one set from an uploaded block, added to its outputs.
+cudaError_t launch_source_block(stp_handle h, const SourceData& sd, const char* d,
+                                const double* params, const double* metric, double* avg,
+                                double* faces, cudaStream_t st) {
+  const char* d_proj = d + SourceData::up(sd.b_groups());
+  const char* d_amp = d_proj + SourceData::up(sd.b_proj());
+  const char* d_cf = d_amp + SourceData::up(sd.b_amp());
+  char* d_scr = const_cast<char*>(d_cf + SourceData::up(sd.b_cf()));
+  return stp::launch_sources(sd.N, (int)sd.groups.size(), reinterpret_cast<const stp::SourceGroup*>(d),
+                             reinterpret_cast<const double*>(d_proj), reinterpret_cast<const double*>(d_amp),
+                             reinterpret_cast<const double*>(d_cf), h->d_tables, params, metric, h->dx,
+                             avg, faces, reinterpret_cast<double*>(d_scr), st);
+}
+
+stp_status predict_sources_impl(stp_handle h, int64_t elements, const double* q,
+                                const double* params, const double* metric, double* out_avg,
+                                double* out_faces, int nsources, const stp_point_source* sources,
+                                void* stream) {
+  stp_status s = metric ? validate_curvilinear(h, elements, q, params, metric, out_avg, out_faces)
+                        : validate_common(h, elements, q, params, out_avg, out_faces);
+  if (s != STP_OK) return s;
+  if ((s = validate_sources(h, elements, nsources, sources)) != STP_OK) return s;
+  s = metric ? stp_predict_curvilinear(h, elements, q, params, metric, out_avg, out_faces, stream)
+             : stp_predict(h, elements, q, params, out_avg, out_faces, stream);
+  if (s != STP_OK) return s;
+  if (nsources == 0 || elements == 0) return STP_OK;
+  SourceData sd;
+  prepare_sources(h, metric != nullptr, nsources, sources, &sd);
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   char* d = nullptr;
-  cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(&d), total, st);
+  cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(&d), sd.bytes(), st);
   if (e != cudaSuccess) { cudaGetLastError(); return fail(STP_ERR_OOM, "source buffer allocation failed"); }
-  char* d_groups = d;
-  char* d_proj = d_groups + up(b_groups);
-  char* d_amp = d_proj + up(b_proj);
-  char* d_cf = d_amp + up(b_amp);
-  char* d_scr = d_cf + up(b_cf);
-  if ((e = cudaMemcpyAsync(d_groups, groups.data(), b_groups, cudaMemcpyHostToDevice, st)) == cudaSuccess &&
-      (e = cudaMemcpyAsync(d_proj, proj.data(), b_proj, cudaMemcpyHostToDevice, st)) == cudaSuccess &&
-      (e = cudaMemcpyAsync(d_amp, amp.data(), b_amp, cudaMemcpyHostToDevice, st)) == cudaSuccess &&
-      (e = cudaMemcpyAsync(d_cf, cf.data(), b_cf, cudaMemcpyHostToDevice, st)) == cudaSuccess)
-    e = stp::launch_sources(N, G, reinterpret_cast<const stp::SourceGroup*>(d_groups),
-                            reinterpret_cast<const double*>(d_proj), reinterpret_cast<const double*>(d_amp),
-                            reinterpret_cast<const double*>(d_cf), h->d_tables, params, metric, h->dx,
-                            out_avg, out_faces, reinterpret_cast<double*>(d_scr), st);
+  e = upload_sources(sd, d, st);
+  if (e == cudaSuccess) e = launch_source_block(h, sd, d, params, metric, out_avg, out_faces, st);
   const cudaError_t fe = cudaFreeAsync(d, st);
   if (e == cudaSuccess) e = fe;
   if (e != cudaSuccess) return cuda_fail(e, "point-source launch");
@@ -602,12 +641,26 @@ struct stp_server_s {
   stp::Server* impl = nullptr;
 };
 
+// Point sources of one set of a batch: prepared data, its offset in the
+// batch's device block, and the set's buffers the response is added to.
+struct BatchSetSources {
+  stp_handle h = nullptr;
+  SourceData sd;
+  size_t off = 0;
+  const double* params = nullptr;
+  const double* metric = nullptr;
+  double* avg = nullptr;
+  double* faces = nullptr;
+};
+
 struct stp_batch_s {
   stp::BatchPlan* plan = nullptr;   // all sets FP64: one persistent launch
   cudaGraph_t graph = nullptr;      // otherwise: one launch per set, parallel branches
   cudaGraphExec_t exec = nullptr;
   int nsets = 0;
   int device = -1;
+  std::vector<BatchSetSources> sources;  // sets with point sources
+  char* d_sources = nullptr;             // their data, one device block
 };
 
 namespace {
@@ -800,11 +853,63 @@ stp_status stp_batch_create_curvilinear(int nsets, const stp_batch_set* sets,
   return batch_create_impl(nsets, sets, nullptr, metrics, out);
 }
 
+stp_status stp_batch_create_sources(int nsets, const stp_batch_set* sets,
+                                    const double* const* metrics, const int* nsources,
+                                    const stp_point_source* const* sources, stp_batch* out) {
+  if (!out) return fail(STP_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  if (nsets > 0 && (!sets || !nsources || !sources))
+    return fail(STP_ERR_INVALID_ARG, "sets, nsources and sources must not be NULL");
+  for (int i = 0; i < nsets; ++i) {
+    if (!sets[i].handle || sets[i].handle->N < 1)
+      return fail(STP_ERR_INVALID_ARG, "set " + std::to_string(i) + ": invalid handle");
+    stp_status s = validate_sources(sets[i].handle, sets[i].elements, nsources[i], sources[i]);
+    if (s != STP_OK) return fail(s, "set " + std::to_string(i) + ": " + g_last_error);
+  }
+  stp_status s = batch_create_impl(nsets, sets, nullptr, metrics, out);
+  if (s != STP_OK) return s;
+  stp_batch b = *out;
+  size_t total = 0;
+  for (int i = 0; i < nsets; ++i) {
+    if (nsources[i] == 0 || sets[i].elements == 0) continue;
+    BatchSetSources bs;
+    bs.h = sets[i].handle;
+    const double* m = metrics ? metrics[i] : nullptr;
+    prepare_sources(bs.h, m != nullptr, nsources[i], sources[i], &bs.sd);
+    bs.off = total;
+    bs.params = sets[i].params;
+    bs.metric = m;
+    bs.avg = sets[i].out_avg;
+    bs.faces = sets[i].out_faces;
+    total += bs.sd.bytes();
+    b->sources.push_back(std::move(bs));
+  }
+  if (total == 0) return STP_OK;
+  cudaError_t e = cudaMalloc(reinterpret_cast<void**>(&b->d_sources), total);
+  for (size_t k = 0; e == cudaSuccess && k < b->sources.size(); ++k)
+    e = upload_sources(b->sources[k].sd, b->d_sources + b->sources[k].off, nullptr);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(nullptr);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    stp_batch_destroy(b);
+    *out = nullptr;
+    return e == cudaErrorMemoryAllocation ? fail(STP_ERR_OOM, "source buffer allocation failed")
+                                          : cuda_fail(e, "source upload");
+  }
+  return STP_OK;
+}
+
 stp_status stp_batch_launch(stp_batch b, void* stream) {
   if (!b || (!b->plan && !b->exec)) return fail(STP_ERR_INVALID_ARG, "invalid batch");
-  cudaError_t e = b->plan ? stp::launch_plan(b->plan, static_cast<cudaStream_t>(stream))
-                          : cudaGraphLaunch(b->exec, static_cast<cudaStream_t>(stream));
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  cudaError_t e = b->plan ? stp::launch_plan(b->plan, st) : cudaGraphLaunch(b->exec, st);
   if (e != cudaSuccess) return cuda_fail(e, "batch graph launch");
+  // the sets' point-source responses, after the STP of every set on the same stream
+  for (const BatchSetSources& bs : b->sources) {
+    e = launch_source_block(bs.h, bs.sd, b->d_sources + bs.off, bs.params, bs.metric, bs.avg,
+                            bs.faces, st);
+    if (e != cudaSuccess) return cuda_fail(e, "batch point-source launch");
+  }
   return STP_OK;
 }
 
@@ -825,6 +930,7 @@ stp_status stp_batch_info(stp_batch b, int* units, int* ctas, int64_t* smem_byte
 stp_status stp_batch_destroy(stp_batch b) {
   if (!b) return STP_OK;
   stp::destroy_plan(b->plan);
+  cudaFree(b->d_sources);
   if (b->exec) cudaGraphExecDestroy(b->exec);
   if (b->graph) cudaGraphDestroy(b->graph);
   delete b;
@@ -846,7 +952,8 @@ namespace {
 // NULLs) marks curvilinear sets, which run as their own FP64 curvilinear
 // launches after the persistent launch of the Cartesian ones.
 stp_status run_static_impl(int nsets, const stp_batch_set* sets, const double* const* metrics,
-                           void* stream) {
+                           void* stream, const int* nsources = nullptr,
+                           const stp_point_source* const* sources = nullptr) {
   constexpr int kMax = 128;  // the static path's set limit (kernel-parameter descriptors)
   if (nsets < 0 || (nsets > 0 && !sets)) return fail(STP_ERR_INVALID_ARG, "bad set list");
   if (nsets > kMax) return fail(STP_ERR_INVALID_ARG, "more than 128 sets for the static path");
@@ -901,6 +1008,37 @@ stp_status run_static_impl(int nsets, const stp_batch_set* sets, const double* c
             return fail(STP_ERR_INVALID_ARG, "outputs overlap another set's buffers");
     }
   }
+  // point sources: prepared on the host, copied into the top of the static
+  // array before the launches (the persistent launch keeps below them)
+  std::vector<SourceData> sds;
+  std::vector<int> src_set;
+  size_t reserve = 0;
+  if (nsources) {
+    for (int i = 0; i < nsets; ++i) {
+      stp_status s = validate_sources(sets[i].handle, sets[i].elements, nsources[i],
+                                      sources ? sources[i] : nullptr);
+      if (s != STP_OK) return fail(s, "set " + std::to_string(i) + ": " + g_last_error);
+      if (nsources[i] == 0 || sets[i].elements == 0) continue;
+      sds.emplace_back();
+      prepare_sources(sets[i].handle, mt[i] != nullptr, nsources[i], sources[i], &sds.back());
+      src_set.push_back(i);
+      reserve += sds.back().bytes();
+    }
+  }
+  const cudaStream_t st = static_cast<cudaStream_t>(stream);
+  unsigned char* top = nullptr;
+  if (reserve > 0) {
+    cudaError_t e = stp::static_scratch_top(reserve, &top);
+    if (e == cudaErrorInvalidValue)
+      return fail(STP_ERR_INVALID_ARG, "point-source data exceed the 24 MiB static scratch");
+    if (e != cudaSuccess) return cuda_fail(e, "static scratch address");
+    size_t off = 0;
+    for (const SourceData& sd : sds) {
+      if ((e = upload_sources(sd, reinterpret_cast<char*>(top) + off, st)) != cudaSuccess)
+        return cuda_fail(e, "point-source copy");
+      off += sd.bytes();
+    }
+  }
   // the Cartesian sets in one persistent launch, compacted in call order
   int nc = 0;
   for (int i = 0; i < nsets; ++i) {
@@ -909,11 +1047,10 @@ stp_status run_static_impl(int nsets, const stp_batch_set* sets, const double* c
     tb[nc] = tb[i];
     ++nc;
   }
-  const cudaStream_t st = static_cast<cudaStream_t>(stream);
   cudaError_t e = cudaSuccess;
   if (nc > 0) {
     int too_big = 0;
-    e = stp::run_static_batch(nc, N, E, q, p, a, f, tb, st, &too_big);
+    e = stp::run_static_batch(nc, N, E, q, p, a, f, tb, st, &too_big, reserve);
     if (too_big) return fail(STP_ERR_INVALID_ARG, "the call needs more than the 24 MiB static scratch");
     if (e != cudaSuccess) return cuda_fail(e, "static batched launch");
   }
@@ -924,12 +1061,28 @@ stp_status run_static_impl(int nsets, const stp_batch_set* sets, const double* c
                                 s.out_faces, s.handle->d_tables, s.handle->dx, st);
     if (e != cudaSuccess) return cuda_fail(e, "static curvilinear launch");
   }
+  size_t off = 0;
+  for (size_t k = 0; k < sds.size(); ++k) {
+    const stp_batch_set& s = sets[src_set[k]];
+    e = launch_source_block(s.handle, sds[k], reinterpret_cast<const char*>(top) + off, s.params,
+                            mt[src_set[k]], s.out_avg, s.out_faces, st);
+    if (e != cudaSuccess) return cuda_fail(e, "static point-source launch");
+    off += sds[k].bytes();
+  }
   return STP_OK;
 }
 
 }  // namespace
 
 extern "C" {
+
+stp_status stp_batch_run_static_sources(int nsets, const stp_batch_set* sets,
+                                        const double* const* metrics, const int* nsources,
+                                        const stp_point_source* const* sources, void* stream) {
+  if (nsets > 0 && (!nsources || !sources))
+    return fail(STP_ERR_INVALID_ARG, "nsources and sources must not be NULL");
+  return run_static_impl(nsets, sets, metrics, stream, nsources, sources);
+}
 
 stp_status stp_batch_run_static(int nsets, const stp_batch_set* sets, void* stream) {
   return run_static_impl(nsets, sets, nullptr, stream);

@@ -124,7 +124,9 @@ void destroy_plan(BatchPlan* p);
 cudaError_t run_static_batch(int nsets, const int* N, const int64_t* E, const double* const* q,
                              const double* const* params, double* const* avg,
                              double* const* faces, const double* const* tables,
-                             cudaStream_t stream, int* too_big);
+                             cudaStream_t stream, int* too_big, size_t reserve_top = 0);
+// Device address of the top `bytes` (a multiple of 256) of that static array.
+cudaError_t static_scratch_top(size_t bytes, unsigned char** out);
 
 // The same launch with caller-provided scratch (counter + per-CTA parking);
 // scratch_bytes = param_batch_scratch_bytes() suffices for one CTA per SM on

@@ -158,9 +158,11 @@ class Batch:
     launch() replays the plan's CUDA graph on the given stream.
     """
 
-    def __init__(self, items, shapes=None, metrics=None):
+    def __init__(self, items, shapes=None, metrics=None, sources=None):
         """items: (Predictor, q, params) per set; metrics: optional list with
-        each set's metric tensor (curvilinear) or None (Cartesian)."""
+        each set's metric tensor (curvilinear) or None (Cartesian); sources:
+        optional list with each set's point sources (list of source dicts as
+        for predict, or None)."""
         self.items = []
         sets = []
         for i, (P, q, params) in enumerate(items):
@@ -172,7 +174,13 @@ class Batch:
             self.items.append((P, q, params, avg, faces))
             sets.append((P.handle, E, q, params, avg, faces))
         self.metrics = metrics  # keeps the tensors alive with the plan
-        self.handle = B.stp_batch_create(sets, shapes, metrics)
+        if sources is not None:
+            if shapes is not None:
+                raise ValueError("shapes and sources cannot be combined")
+            self.handle = B.stp_batch_create_sources(sets, sources, [it[0].N for it in self.items],
+                                                     metrics)
+        else:
+            self.handle = B.stp_batch_create(sets, shapes, metrics)
 
     def launch(self, stream=None):
         if stream is None:

@@ -158,3 +158,81 @@ def test_source_argument_errors():
             assert ei.value.status == _binding.STP_ERR_INVALID_ARG
         P.predict(prob.q, prob.params, sources=[good])  # valid after the errors
         torch.cuda.synchronize()
+
+
+BATCH_SPECS = [(4, 30, True), (8, 7, False), (10, 5, True), (6, 12, False), (12, 2, True), (1, 9, True)]
+
+
+def _batch_problems(seed0):
+    rng = np.random.default_rng(seed0)
+    out = []
+    for i, (N, E, with_src) in enumerate(BATCH_SPECS):
+        prob = elastic_problem(N, E=E, seed_material=seed0 + i, seed_waves=seed0 + 50 + i,
+                               device="cuda")
+        src = make_sources(N, E, rng, per_element=((0, 2), (E - 1, 1))) if with_src else None
+        out.append((prob, src))
+    return out
+
+
+def _oracle_set(prob, src):
+    q, pa = prob.q.cpu().numpy(), prob.params.cpu().numpy()
+    return oracle.stp(q, pa, prob.h, prob.dt, sources=src) if src else oracle.stp(q, pa, prob.h, prob.dt)
+
+
+@pytest.mark.parametrize("precisions", [("fp64",) * 6, ("fp64", "ff", "fp64", "fp32", "fp64", "fp64")])
+def test_batch_plan_with_and_without_sources(precisions):
+    """A batch plan mixing sets with and without point sources: every set
+    equals the oracle with its sources (FP64 and float-float sets within
+    1e-12; the FP32 set within its coarse-field 1e-8), and the sets without sources are
+    unchanged by the others'. All-FP64 sets run in the persistent launch,
+    the mixed-precision plan as a graph of per-set launches."""
+    sets = _batch_problems(4100)
+    preds = [stp.Predictor(p.N - 1, p.h, p.dt, precision=prec)
+             for (p, _), prec in zip(sets, precisions)]
+    b = stp.Batch([(P, p.q, p.params) for P, (p, _) in zip(preds, sets)],
+                  sources=[src for _, src in sets])
+    for _ in range(2):  # a second replay gives the same result (no accumulation)
+        b.launch()
+    torch.cuda.synchronize()
+    for i, ((prob, src), prec) in enumerate(zip(sets, precisions)):
+        a_ref, f_ref = _oracle_set(prob, src)
+        avg, faces = b.outputs(i)
+        tol = 1e-8 if prec == "fp32" else 1e-12  # FP32 on these coarse cubes: its 1e-8 bar
+        assert rel(avg.cpu().numpy(), a_ref) <= tol, (i, prec)
+        assert rel(faces.cpu().numpy(), f_ref) <= tol, (i, prec)
+    for P in preds:
+        P.close()
+
+
+def test_static_batch_with_and_without_sources():
+    """The allocation-free launch with per-set point sources (their data in
+    the static array's top): every set equals the oracle within 1e-12, on two
+    calls in a row."""
+    sets = _batch_problems(4300)
+    preds = [stp.Predictor(p.N - 1, p.h, p.dt) for p, _ in sets]
+    outs = [P.empty_outputs(p.E) for P, (p, _) in zip(preds, sets)]
+    args = [(P.handle, p.E, p.q, p.params, a, f) for P, (p, _), (a, f) in zip(preds, sets, outs)]
+    refs = [_oracle_set(p, src) for p, src in sets]
+    for call in range(2):
+        for a, f in outs:
+            a.fill_(float("nan"))
+            f.fill_(float("nan"))
+        stp.stp_batch_run_static_sources(args, [src for _, src in sets], [p.N for p, _ in sets])
+        torch.cuda.synchronize()
+        for i, ((a, f), (a_ref, f_ref)) in enumerate(zip(outs, refs)):
+            assert rel(a.cpu().numpy(), a_ref) <= 1e-12, (call, i)
+            assert rel(f.cpu().numpy(), f_ref) <= 1e-12, (call, i)
+    for P in preds:
+        P.close()
+
+
+def test_batch_source_arguments_are_checked():
+    prob = elastic_problem(4, E=3, device="cuda")
+    P = stp.Predictor(3, prob.h, prob.dt)
+    a, f = P.empty_outputs(3)
+    bad = [{"element": 5, "position": (0.5, 0.5, 0.5), "amplitude": [1.0] * 9, "derivatives": [1.0] * 4}]
+    with pytest.raises(stp.STPError):
+        stp._binding.stp_batch_create_sources([(P.handle, 3, prob.q, prob.params, a, f)], [bad], [4])
+    with pytest.raises(stp.STPError):
+        stp.stp_batch_run_static_sources([(P.handle, 3, prob.q, prob.params, a, f)], [bad], [4])
+    P.close()
