@@ -255,13 +255,18 @@ stp_status stp_predict_host(stp_handle h, int64_t elements, const double* q,
  * Arithmetic of the derivative contractions.
  *   STP_PRECISION_FP64    every step in FP64 (default)
  *   STP_PRECISION_BF16X2 / _BF16X3 / _FP16X2 / _FP16X3
- *       split precision on the tensor cores: the first CK term
- *       r_1 = dt/2 L q is computed in FP64 (the FP64 correction pass); every
- *       later term r_k = dt^k/(k+1)! q^(k) is scaled per quantity by a power of
- *       two, split into 2 or 3 BF16/FP16 slices, contracted with the equally
- *       split D on the tensor cores with FP32 accumulation, and updated
- *       pointwise in FP32. The Taylor average (FP32 tail added to the FP64 sum
- *       of r_0 + r_1) and the face projections are FP64.
+ *       derivative contractions on the tensor cores (2 <= N <= 10): the
+ *       first CK term r_1 = dt/2 L q, and every later term while it is above
+ *       1e-3 of the state, runs in float-float on the CUDA cores; each later
+ *       term is written per quantity in fixed point and cut into up to three
+ *       (x3) or two (x2) integer digits of 10 bits (FP16) or 8 bits (BF16),
+ *       contracted exactly against the equally cut D on the tensor cores
+ *       (leading digit products exact in FP32, the rest accumulated in
+ *       FP32), and updated pointwise in FP32. The Taylor average and the face
+ *       projections are float-float. Stated bars (resolved and coarse
+ *       fields): FP16X3 1e-9, FP16X2 5e-8, BF16X3 5e-9, BF16X2 5e-7 relative.
+ *       For N = 11, 12 an earlier kernel runs (first term FP64, later terms
+ *       split into 2 or 3 BF16/FP16 slices with FP32 accumulation).
  *   STP_PRECISION_FP32
  *       the same split on the CUDA cores without FP64 instructions: r_1,
  *       r_0 + r_1, the Taylor average and the faces in float-float (pairs of
@@ -271,9 +276,9 @@ stp_status stp_predict_host(stp_handle h, int64_t elements, const double* q,
  *       every step in float-float on the FP32 pipes (about 48 significant
  *       bits): results agree with the FP64 kernel to about 1e-13 relative,
  *       several times faster on a GPU whose FP64 rate is low.
- * The split and FP32 variants reach about 1e-9 relative on well-resolved
- * fields; their error grows with the size of the higher Taylor terms
- * (coarse elements: several 1e-9). FF holds about 1e-13 on any data.
+ * FP32 reaches about 1e-9 relative on well-resolved fields; its error grows
+ * with the size of the higher Taylor terms (coarse elements: several 1e-9).
+ * FF holds about 1e-13 on any data.
  * FP32 and FF scale each element's state by a power of two (exact) so that
  * its largest magnitude is about 1; within an element, values more than
  * 2^126 below that largest magnitude contribute as zero.

@@ -13,6 +13,7 @@
 // them into nine per-node accumulators; the pointwise update then forms the
 // new term from the accumulators and the node's elastic coefficients.
 #pragma once
+#include "bulk.cuh"
 #include "fp64_eo.cuh"
 #include "ff32.cuh"
 
@@ -229,13 +230,27 @@ __device__ __forceinline__ int load_state_ff_layout(const double* __restrict__ q
   __shared__ int s_field[32];
   double* spd = reinterpret_cast<double*>(sp);  // the same bytes, first as doubles
   int lmax = 0;
-  for (int f = threadIdx.x; f < M * N3; f += NT) {  // coalesced AoS read, SoA scatter
-    const int n = f / M, s = f - n * M;
-    const int pn = (n / (N * N)) * PLANE + ((n / N) % N) * RX + n % N;
-    const double v = __ldg(qe + f);
-    spd[s * S + pn] = v;
-    const int fld = ff::exponent_field(v);
-    if (fld != 0x7ff) lmax = max(lmax, fld);
+  // coalesced AoS read, SoA scatter; loads issued in batches of eight so that
+  // eight of them are in flight per thread instead of one
+  constexpr int TOTAL = M * N3, ITER = (TOTAL + NT - 1) / NT, BATCH = 8;
+#pragma unroll 1
+  for (int i0 = 0; i0 < ITER; i0 += BATCH) {
+    double v[BATCH];
+#pragma unroll
+    for (int u = 0; u < BATCH; ++u) {
+      const int f = threadIdx.x + (i0 + u) * NT;
+      v[u] = (i0 + u < ITER && f < TOTAL) ? __ldg(qe + f) : 0.0;
+    }
+#pragma unroll
+    for (int u = 0; u < BATCH; ++u) {
+      const int f = threadIdx.x + (i0 + u) * NT;
+      if (i0 + u >= ITER || f >= TOTAL) continue;
+      const int n = f / M, s = f - n * M;
+      const int pn = (n / (N * N)) * PLANE + ((n / N) % N) * RX + n % N;
+      spd[s * S + pn] = v[u];
+      const int fld = ff::exponent_field(v[u]);
+      if (fld != 0x7ff) lmax = max(lmax, fld);
+    }
   }
   lmax = __reduce_max_sync(0xffffffffu, lmax);
   if ((threadIdx.x & 31) == 0) s_field[threadIdx.x >> 5] = lmax;
@@ -248,6 +263,44 @@ __device__ __forceinline__ int load_state_ff_layout(const double* __restrict__ q
     const int n = f / M, s = f - n * M;
     const int pn = (n / (N * N)) * PLANE + ((n / N) % N) * RX + n % N;
     sp[s * S + pn] = ff::split(spd[s * S + pn], sc);
+  }
+  __syncthreads();
+  return sc;
+}
+
+// The same, with the element's AoS block first copied in one bulk copy into
+// `stage` (shared, 16-byte aligned, at least 72 N^3 bytes, not overlapping
+// sp) when q_e allows it (16-byte aligned, 72 N^3 a multiple of 16, so even
+// N); otherwise the batched loads above. bar: an initialised mbarrier of the
+// CTA, parity: its next phase parity (advanced when used). A wait that gives
+// up sets bit 0 of *status (the results are then not to be trusted).
+template <int N, int NT, int S, int RX, int PLANE>
+__device__ __forceinline__ int load_state_ff_bulk(const double* __restrict__ qe, float2* sp, double* stage,
+                                                  uint64_t* bar, uint32_t& parity, unsigned* status) {
+  constexpr int N3 = N * N * N, M = kQuantities, TOTAL = M * N3;
+  constexpr uint32_t BYTES = 8u * TOTAL;
+  if (!bulk::can_copy(qe, BYTES)) return load_state_ff_layout<N, NT, S, RX, PLANE>(qe, sp);
+  if (threadIdx.x == 0) bulk::start(stage, qe, BYTES, bar);
+  const bool ok = bulk::wait(bar, parity);
+  parity ^= 1u;
+  if (!ok && threadIdx.x == 0) atomicOr(status, 1u);
+  __shared__ int s_field[32];
+  int lmax = 0;
+  for (int f = threadIdx.x; f < TOTAL; f += NT) {
+    const int fld = ff::exponent_field(stage[f]);
+    if (fld != 0x7ff) lmax = max(lmax, fld);
+  }
+  lmax = __reduce_max_sync(0xffffffffu, lmax);
+  if ((threadIdx.x & 31) == 0) s_field[threadIdx.x >> 5] = lmax;
+  __syncthreads();
+  int field = 0;
+#pragma unroll 1
+  for (int w = 0; w < NT / 32; ++w) field = max(field, s_field[w]);
+  const int sc = ff::scale_from_field(field);
+  for (int f = threadIdx.x; f < TOTAL; f += NT) {  // SoA scatter from the AoS copy
+    const int n = f / M, s = f - n * M;
+    const int pn = (n / (N * N)) * PLANE + ((n / N) % N) * RX + n % N;
+    sp[s * S + pn] = ff::split(stage[f], sc);
   }
   __syncthreads();
   return sc;

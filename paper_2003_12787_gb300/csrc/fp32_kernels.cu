@@ -257,9 +257,12 @@ fp32_eo_kernel(const double* __restrict__ q, const double* __restrict__ params,
     const int n = tid + j * USE;
     if (tid >= USE || n >= N3) continue;
     const int pn = pad(n);
+    float2 pk[M];  // the parked r_0 + r_1 first (all loads in flight), then the sums
+#pragma unroll
+    for (int s = 0; s < M; ++s) pk[s] = gpark[n * M + s];
 #pragma unroll
     for (int s = 0; s < M; ++s) {
-      const float2 v = ff::add(gpark[n * M + s], make_float2(acc[j][s], 0.f));
+      const float2 v = ff::add(pk[s], make_float2(acc[j][s], 0.f));
       sp[s * S + pn] = v;
       gavg[n * M + s] = ff::to_double(v, sc);
     }

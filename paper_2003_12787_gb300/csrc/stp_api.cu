@@ -196,11 +196,15 @@ stp_status stp_create_nodes(int order, int m, double dx, double dt, stp_node_fam
   if (e != cudaSuccess) { delete h; return cuda_fail(e, "cudaGetDevice"); }
   const int nt = stp::table_doubles(N);
   double buf[stp::kMaxNodes * stp::kMaxNodes * stp::kMaxNodes + 2 * stp::kMaxNodes +
-             stp::kMaxNodes * stp::kMaxNodes];
+             stp::kMaxNodes * stp::kMaxNodes + stp::kTcRegionBytes / 8];
   stp::make_step_matrices(h->host, dx, dt, buf);
   std::memcpy(buf + N * N * N, h->host.phi0, sizeof(double) * N);
   std::memcpy(buf + N * N * N + N, h->host.phi1, sizeof(double) * N);
   std::memcpy(buf + stp::table_offset_D(N), h->host.D, sizeof(double) * N * N);
+  if (!stp::make_tc_tiles(h->host, h->eD, reinterpret_cast<unsigned char*>(buf + stp::table_offset_tc(N)))) {
+    delete h;
+    return fail(STP_ERR_UNSUPPORTED, "tensor-core tiles of D are not exactly representable");
+  }
   e = cudaMalloc(&h->d_tables, sizeof(double) * nt);
   if (e != cudaSuccess) { cudaGetLastError(); delete h; return fail(STP_ERR_OOM, "cudaMalloc of tables failed"); }
   e = cudaMalloc(&h->d_status, 16);

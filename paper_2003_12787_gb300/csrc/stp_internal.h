@@ -34,9 +34,26 @@ bool make_tables(int N, HostTables* t, int family = STP_NODES_GAUSS_LEGENDRE);
 void make_step_matrices(const HostTables& t, double dx, double dt, double* Dk);
 
 // Device tables: [N][N][N] step matrices, then phi0[N], phi1[N], then the
-// unscaled D[N][N].
-inline int table_doubles(int N) { return N * N * N + 2 * N + N * N; }
+// unscaled D[N][N], then the tensor-core operand tiles of D (make_tc_tiles).
+// N^3 + N^2 + 2N is even, so the tile region starts 16-byte aligned.
+constexpr int kTcChunkBytes = 1024;   // 32 rows (N) x 16 K of 16-bit values
+constexpr int kTcOperandBytes = 2 * kTcChunkBytes;  // K = 32: two chunks
+constexpr int kTcRegionBytes = 2 * 3 * kTcOperandBytes;  // FP16 then BF16; T = 1, 2, 3
 inline int table_offset_D(int N) { return N * N * N + 2 * N; }
+inline int table_offset_tc(int N) { return table_offset_D(N) + N * N; }
+inline int table_doubles(int N) { return table_offset_tc(N) + kTcRegionBytes / 8; }
+
+// Tensor-core operand tiles of D (tc_kernels.cuh), for N <= 10. D 2^(W-1-eD)
+// is written as balanced base-2^W digits B_0 + B_1 2^-W + ... (W = 10 for
+// FP16, 8 for BF16; |B_t| <= 2^(W-1)), each digit an exact 16-bit value. The
+// state's T digits sit side by side along K (digit s at k = N s + l), so one
+// operand per T (1, 2, 3) holds, for output i and digit s, three column
+// blocks of N columns: [L0: B_0 if s = 0 | X: B_(1-s) 2^c | Y: B_(2-s) 2^(c-W)]
+// (zero where the index is negative or s >= T); c = 6 for FP16 (keeps every
+// value a normal FP16 number), 0 for BF16. Each operand is two K-major
+// no-swizzle chunks of 16 K (k = 0..15, 16..31) x 32 rows. Returns false if
+// a value is not exactly representable (never for 2 <= N <= 10).
+bool make_tc_tiles(const HostTables& t, int eD, unsigned char* out);
 
 // Kernel launchers (fp64_kernels.cu). Return cudaSuccess or the launch error.
 cudaError_t launch_fp64(int N, int64_t E, const double* q, const double* params,

@@ -11,6 +11,8 @@
 // row sum; phi is a unit vector where the face coincides with a node.
 // Arithmetic in long double, rounded to double once at the end.
 #include <cmath>
+#include <cstdint>
+#include <cstring>
 
 #include "stp_internal.h"
 
@@ -142,6 +144,74 @@ void make_step_matrices(const HostTables& t, double dx, double dt, double* Dk) {
     const ld s = (ld)dt / ((ld)(k + 2) * (ld)dx);
     for (int i = 0; i < N * N; ++i) Dk[k * N * N + i] = (double)((ld)t.D[i] * s);
   }
+}
+
+}  // namespace stp
+
+namespace stp {
+namespace {
+
+// IEEE binary16 (bf16 = false) or bfloat16 bits of v, which must be exactly
+// representable (checked; false otherwise).
+bool encode16(double v, bool bf16, uint16_t* bits) {
+  if (v == 0.0) { *bits = 0; return true; }
+  const uint16_t sign = v < 0 ? 0x8000u : 0u;
+  const double a = std::fabs(v);
+  int ex;
+  const double m = std::frexp(a, &ex);  // a = m 2^ex, m in [0.5, 1)
+  const int mbits = bf16 ? 7 : 10, bias = bf16 ? 127 : 15;
+  const int E = ex - 1 + bias;
+  if (E >= (bf16 ? 255 : 31)) return false;
+  double frac;
+  uint32_t e_field;
+  if (E >= 1) {
+    frac = std::ldexp(2.0 * m - 1.0, mbits);
+    e_field = (uint32_t)E;
+  } else {  // subnormal: a = frac 2^(1 - bias - mbits)
+    frac = std::ldexp(a, bias - 1 + mbits);
+    e_field = 0;
+  }
+  if (frac != std::floor(frac) || frac >= std::ldexp(1.0, mbits)) return false;
+  *bits = (uint16_t)(sign | (e_field << mbits) | (uint32_t)frac);
+  return true;
+}
+
+}  // namespace
+
+bool make_tc_tiles(const HostTables& t, int eD, unsigned char* out) {
+  const int N = t.N;
+  std::memset(out, 0, kTcRegionBytes);
+  if (N > 10) return true;  // the tensor-core kernel covers N <= 10
+  for (int type = 0; type < 2; ++type) {
+    const bool bf16 = type == 1;
+    const int W = bf16 ? 8 : 10, c = bf16 ? 0 : 6;
+    for (int i = 0; i < N; ++i)
+      for (int l = 0; l < N; ++l) {
+        double dig[3];
+        double x = std::ldexp(t.D[i * N + l], W - 1 - eD);
+        for (int d = 0; d < 3; ++d) {
+          dig[d] = std::nearbyint(x);
+          x = std::ldexp(x - dig[d], W);
+        }
+        for (int T = 1; T <= 3; ++T) {
+          unsigned char* op = out + (type * 3 + (T - 1)) * kTcOperandBytes;
+          for (int s = 0; s < T; ++s) {
+            const int k = N * s + l, chunk = k >> 4, kk = k & 15;
+            auto put = [&](int row, double v) {
+              uint16_t b;
+              if (!encode16(v, bf16, &b)) return false;
+              const int off = chunk * kTcChunkBytes + (row >> 3) * 256 + (kk >> 3) * 128 + (row & 7) * 16 + (kk & 7) * 2;
+              std::memcpy(op + off, &b, 2);
+              return true;
+            };
+            if (s == 0 && !put(i, dig[0])) return false;
+            if (s <= 1 && !put(N + i, std::ldexp(dig[1 - s], c))) return false;
+            if (!put(2 * N + i, std::ldexp(dig[2 - s], c - W))) return false;
+          }
+        }
+      }
+  }
+  return true;
 }
 
 }  // namespace stp

@@ -1,14 +1,15 @@
 """GPU parity of the reduced-precision STP variants against the FP64 oracle:
-the tensor-core variants (BF16/FP16 slices) and the FP32 CUDA-core variant.
+the tensor-core variants (BF16/FP16 digits) and the FP32 CUDA-core variant.
 
 Stated error bars, normwise per output array (max|gpu - oracle| / max|oracle|
 over avg and each face array), on seeded plane-wave inputs:
 
-* Tensor-core variants, N <= 10 (per-term precision: float-float while a
-  Taylor term is above 1e-3 of the state, then 3, 2 or 1 slices by its size):
-  BF16x3 and FP16x3 <= 1e-9 on resolved fields (h = 1/32) AND on coarse ones
-  (h = 1/4, 1/5, where the later terms stay large); BF16x2 and FP16x2 <= 5e-8
-  (measured up to 2.2e-8 on the coarse fields).
+* Tensor-core variants, N <= 10 (float-float steps while a Taylor term is
+  above 1e-3 of the state, then the term's contraction as exact products of
+  fixed-point digits: up to three 10-bit FP16 digits for FP16x3, two for
+  FP16x2, three or two 8-bit BF16 digits for BF16x3 / BF16x2), on resolved
+  fields (h = 1/32) AND coarse ones (h = 1/4, 1/5, where the later terms stay
+  large): FP16x3 <= 1e-9, FP16x2 <= 5e-8, BF16x3 <= 5e-9, BF16x2 <= 5e-7.
 * Tensor-core variants, N = 11, 12 (the earlier kernel: first term in FP64,
   every later term with the variant's slices), resolved fields only:
   BF16x3, FP16x3 <= 1e-9, FP16x2 <= 2e-9, BF16x2 <= 1e-7.
@@ -33,11 +34,11 @@ pytestmark = pytest.mark.gpu
 
 TC = ["bf16x2", "bf16x3", "fp16x2", "fp16x3"]
 # resolved fields, N <= 10
-TOL = {"bf16x2": 5e-8, "bf16x3": 1e-9, "fp16x2": 5e-8, "fp16x3": 1e-9, "fp32": 1e-9}
+TOL = {"bf16x2": 5e-7, "bf16x3": 5e-9, "fp16x2": 5e-8, "fp16x3": 1e-9, "fp32": 1e-9}
 # resolved fields, N = 11, 12 (earlier tensor-core kernel)
 TOL_N11 = {"bf16x2": 1e-7, "bf16x3": 1e-9, "fp16x2": 2e-9, "fp16x3": 1e-9, "fp32": 1e-9}
 # coarse fields, N <= 10
-TOL_COARSE = {"bf16x2": 5e-8, "bf16x3": 1e-9, "fp16x2": 5e-8, "fp16x3": 1e-9, "fp32": 1e-8}
+TOL_COARSE = {"bf16x2": 5e-7, "bf16x3": 5e-9, "fp16x2": 5e-8, "fp16x3": 1e-9, "fp32": 1e-8}
 # the increment avg - q, relative to its own size
 TOL_INCR = {"bf16x2": 1e-5, "bf16x3": 3e-7, "fp16x2": 1e-5, "fp16x3": 3e-7, "fp32": 3e-6}
 
