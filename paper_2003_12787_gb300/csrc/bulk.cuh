@@ -49,6 +49,10 @@ __device__ __forceinline__ bool wait(uint64_t* bar, uint32_t parity, int limit =
   return false;
 }
 
+// Orders this thread's earlier generic-proxy shared-memory accesses before
+// a later bulk copy into the same bytes (with a barrier in between).
+__device__ __forceinline__ void fence_shared() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
 // Orders this thread's earlier generic-proxy global writes before later
 // bulk-copy reads of them.
 __device__ __forceinline__ void fence_global_writes() { asm volatile("fence.proxy.async.global;" ::: "memory"); }

@@ -144,7 +144,7 @@ template <int N, int NT, int USE, int QPT, int MINB, bool PERNODE0>
 __global__ void __launch_bounds__(NT, MINB)
 fp32_eo_kernel(const double* __restrict__ q, const double* __restrict__ params,
                double* __restrict__ out_avg, double* __restrict__ out_faces,
-               const double* __restrict__ tables, int64_t E) {
+               const double* __restrict__ tables, int64_t E, unsigned int* __restrict__ status) {
   using Sh = EoFfShape<N, PERNODE0>;
   constexpr int N3 = Sh::N3, S = Sh::S, RX = Sh::RX, PLANE = Sh::PLANE, ST = Sh::STEP_TABLE;
   constexpr int ST32 = Sh::STEP32;
@@ -178,7 +178,18 @@ fp32_eo_kernel(const double* __restrict__ q, const double* __restrict__ params,
     sTf[i] = eo_table_entry32<N>(tables + k * N * N, i - k * ST32);
   }
   for (int i = tid; i < 2 * N; i += NT) sPhi[i] = ff::split(tables[N3 + i]);
-  const int sc = load_state_ff<N, NT, PERNODE0>(q + e * (int64_t)(M * N3), sp);
+  // bulk copies (state in, parked average back) land in the accumulator half
+  // of the area, 16-byte aligned (its 72 S bytes hold 72 N^3 + 8 for even N)
+  __shared__ uint64_t s_bar;
+  uint32_t bparity = 0u;
+  double* stage = reinterpret_cast<double*>((reinterpret_cast<uintptr_t>(sacc) + 15) & ~(uintptr_t)15);
+  if (tid == 0) bulk::init(&s_bar);
+  __syncthreads();
+  int sc;
+  if constexpr (PERNODE0)
+    sc = load_state_ff<N, NT, PERNODE0>(q + e * (int64_t)(M * N3), sp);
+  else
+    sc = load_state_ff_bulk<N, NT, S, RX, PLANE>(q + e * (int64_t)(M * N3), sp, stage, &s_bar, bparity, status);
 
   // step 0 in float-float
   if (!PERNODE0) {
@@ -216,6 +227,7 @@ fp32_eo_kernel(const double* __restrict__ q, const double* __restrict__ params,
       r[j][s] = r1[s].x;
     }
   }
+  bulk::fence_global_writes();  // the parked values are read back by a bulk copy
   __syncthreads();  // every float-float read is done
   float acc[NODES][M];
 #pragma unroll
@@ -251,7 +263,18 @@ fp32_eo_kernel(const double* __restrict__ q, const double* __restrict__ params,
     __syncthreads();
   }
 
-  // time average (r_0 + r_1 plus the FP32 tail) in float-float, then the faces
+  // time average (r_0 + r_1 plus the FP32 tail) in float-float, then the
+  // faces; the parked r_0 + r_1 comes back in one bulk copy into the
+  // accumulator half (the partial arrays there are dead; sp is not touched)
+  const float2* park = gpark;
+  if (!PERNODE0 && bulk::can_copy(gpark, 8u * M * N3)) {
+    bulk::fence_shared();
+    __syncthreads();
+    if (tid == 0) bulk::start(stage, gpark, 8u * M * N3, &s_bar);
+    if (!bulk::wait(&s_bar, bparity) && tid == 0) atomicOr(status, 1u);
+    bparity ^= 1u;
+    park = reinterpret_cast<const float2*>(stage);
+  }
 #pragma unroll
   for (int j = 0; j < NODES; ++j) {
     const int n = tid + j * USE;
@@ -259,7 +282,7 @@ fp32_eo_kernel(const double* __restrict__ q, const double* __restrict__ params,
     const int pn = pad(n);
     float2 pk[M];  // the parked r_0 + r_1 first (all loads in flight), then the sums
 #pragma unroll
-    for (int s = 0; s < M; ++s) pk[s] = gpark[n * M + s];
+    for (int s = 0; s < M; ++s) pk[s] = park[n * M + s];
 #pragma unroll
     for (int s = 0; s < M; ++s) {
       const float2 v = ff::add(pk[s], make_float2(acc[j][s], 0.f));
@@ -291,7 +314,8 @@ fp32_eo_kernel(const double* __restrict__ q, const double* __restrict__ params,
 
 template <int N, int NT, int USE, int QPT, int MINB, bool PERNODE0>
 cudaError_t launch_fp32_eo(int64_t E, const double* q, const double* params, double* out_avg,
-                           double* out_faces, const double* tables, cudaStream_t stream) {
+                           double* out_faces, const double* tables, unsigned int* status,
+                           cudaStream_t stream) {
   constexpr size_t smem = EoFfShape<N, PERNODE0>::SMEM;
   static_assert(smem <= 232448, "shared memory budget of one CTA exceeded");
   static_assert(USE <= NT && NT <= 1024, "bad thread counts");
@@ -300,7 +324,7 @@ cudaError_t launch_fp32_eo(int64_t E, const double* q, const double* params, dou
   if (err != cudaSuccess) return err;
   if (E > 0x7fffffffLL) return cudaErrorInvalidValue;
   if (E == 0) return cudaSuccess;
-  kern<<<(unsigned)E, NT, smem, stream>>>(q, params, out_avg, out_faces, tables, E);
+  kern<<<(unsigned)E, NT, smem, stream>>>(q, params, out_avg, out_faces, tables, E, status);
   return cudaGetLastError();
 }
 
@@ -315,10 +339,11 @@ cudaError_t launch_fp32_eo(int64_t E, const double* q, const double* params, dou
   X(11, 384, 363, 2, 1, false) X(12, 448, 432, 2, 1, true)
 
 cudaError_t launch_fp32(int N, int64_t E, const double* q, const double* params, double* out_avg,
-                        double* out_faces, const double* tables, cudaStream_t stream) {
+                        double* out_faces, const double* tables, unsigned int* status,
+                        cudaStream_t stream) {
   switch (N) {
 #define X(n, nt, use, qpt, minb, pn0) \
-  case n: return launch_fp32_eo<n, nt, use, qpt, minb, pn0>(E, q, params, out_avg, out_faces, tables, stream);
+  case n: return launch_fp32_eo<n, nt, use, qpt, minb, pn0>(E, q, params, out_avg, out_faces, tables, status, stream);
     STP_FP32_SHAPES(X)
 #undef X
     default: return cudaErrorInvalidValue;

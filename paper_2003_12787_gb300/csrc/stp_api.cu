@@ -100,7 +100,7 @@ cudaError_t launch_configured(stp_handle h, int64_t E, const double* q, const do
   if (h->precision == STP_PRECISION_FP64 || h->N < 2)
     return stp::launch_fp64(h->N, E, q, params, avg, faces, h->d_tables, stream);
   if (h->precision == STP_PRECISION_FP32)
-    return stp::launch_fp32(h->N, E, q, params, avg, faces, h->d_tables, stream);
+    return stp::launch_fp32(h->N, E, q, params, avg, faces, h->d_tables, h->d_status, stream);
   if (h->precision == STP_PRECISION_FF)
     return stp::launch_ff(h->N, E, q, params, avg, faces, h->d_tables, stream);
   return stp::launch_mixed(h->N, (int)h->precision, E, q, params, avg, faces, h->d_tables,

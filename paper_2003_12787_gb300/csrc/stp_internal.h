@@ -70,10 +70,12 @@ cudaError_t launch_mixed(int N, int variant, int64_t E, const double* q, const d
                          const double* Dref, double dt_over_dx, int eD, unsigned int* status,
                          cudaStream_t stream);
 
-// FP32 variant (fp32_kernels.cu): first CK term in FP64, later terms in FP32
-// on the CUDA cores; 2 <= N <= 12.
+// FP32 variant (fp32_kernels.cu): first CK term in float-float, later terms in
+// FP32 on the CUDA cores; 2 <= N <= 12. status receives bit 0 when a bounded
+// wait on a bulk copy gave up.
 cudaError_t launch_fp32(int N, int64_t E, const double* q, const double* params, double* out_avg,
-                        double* out_faces, const double* tables, cudaStream_t stream);
+                        double* out_faces, const double* tables, unsigned int* status,
+                        cudaStream_t stream);
 
 // Float-float variant (ff_kernels.cu): every step in float-float on the FP32
 // pipes; ff_supported(N) is true for 2 <= N <= 12.
