@@ -91,6 +91,9 @@ struct Digits<true> {
   static constexpr float RHO3 = 1e-8f, RHO2 = 1e-10f;
 };
 
+// 8-row groups of a digit tile are kGroupBytes apart (see a_offset).
+constexpr int kGroupBytes = 528, kTileBytes = 16 * kGroupBytes;
+
 template <int N>
 struct TcShape {
   using Ff = EoFfShape<N>;
@@ -105,7 +108,7 @@ struct TcShape {
   static constexpr int RQ = (N * N + 7) & ~7;      // rows of one quantity (multiple of 8)
   static constexpr int TILES = (6 * RQ + 127) / 128;
   static constexpr int COMBOS = 3 * TILES;         // (pass, tile) pairs
-  static constexpr int DIG_BYTES = COMBOS * 8192;  // 128 rows x 32 K digits per pair
+  static constexpr int DIG_BYTES = COMBOS * kTileBytes;  // 128 rows x 32 K digits per pair
   static constexpr int TMEM_USED = COMBOS * CW;
   static constexpr int TMEM_COLS = TMEM_USED <= 32 ? 32 : TMEM_USED <= 64 ? 64 : TMEM_USED <= 128 ? 128
                                  : TMEM_USED <= 256 ? 256 : 512;
@@ -130,15 +133,22 @@ struct TcShape {
   static_assert(OWN >= PAIRS && NT <= 1024, "bad thread counts");
 };
 
-// Byte offset of (row, k) of pass p in its tile set (tiles of 128 rows x 32
-// K, 8192 bytes each; core matrices of 8 x 16 bytes, K groups of 8 128 bytes
-// apart, 8-row groups 512 bytes apart, so tile m = row / 128 starts at
-// 8192 m). Pass 0 is K-major (16 bytes hold 8 consecutive k of a row), passes
-// 1, 2 MN-major (16 bytes hold 8 consecutive rows of one k). The MMA of K
-// chunk c (k = 16 c .. 16 c + 15) starts 256 c bytes into the tile.
+// Byte offset of (row, k) of pass p in its tile set: tiles of 128 rows x 32
+// K; core matrices of 8 x 16 bytes, K groups of 8 128 bytes apart, 8-row
+// groups kGroupBytes = 528 bytes apart (512 + 16: consecutive row groups then
+// start four banks apart, so the stores of a warp that spans several row
+// groups at one k do not collide), so tile m = row / 128 starts at
+// kTileBytes m. Pass 0 is K-major (16 bytes hold 8 consecutive k of a row),
+// passes 1, 2 MN-major (16 bytes hold 8 consecutive rows of one k). The MMA
+// of K chunk c (k = 16 c .. 16 c + 15) starts 256 c bytes into the tile.
 __device__ __forceinline__ int a_offset(int pass, int row, int k) {
-  const int base = (row >> 3) * 512 + (k >> 3) * 128;
+  const int base = (row >> 3) * kGroupBytes + (k >> 3) * 128;
   return pass == 0 ? base + (row & 7) * 16 + (k & 7) * 2 : base + (k & 7) * 16 + (row & 7) * 2;
+}
+
+// Nearest integer of |x| < 2^22, ties to even (two FP32 additions).
+__device__ __forceinline__ float round_int(float x) {
+  return __fsub_rn(__fadd_rn(x, 12582912.0f), 12582912.0f);  // 1.5 2^23
 }
 
 // Row-quantity index of quantity s in pass `pass` (inverse of eo_qty; -1:
@@ -194,7 +204,7 @@ tc_stp_kernel(const double* __restrict__ q, const double* __restrict__ params,
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
   float2* sp = reinterpret_cast<float2*>(smem);    // first step: p[9][S]; the average at the end
   float2* sacc = sp + M * S;                       // first step: accumulators [9][S]
-  unsigned char* dig = smem;                       // later steps: digit tiles [COMBOS][8192]
+  unsigned char* dig = smem;                       // later steps: digit tiles [COMBOS][kTileBytes]
   float* spart = reinterpret_cast<float*>(smem + Sh::PART_OFF);  // [18][S]
   unsigned char* stile = smem + Sh::TILE_OFF;      // operands of D [T - 1][2 chunks][1024]
   float2* sT0 = reinterpret_cast<float2*>(smem + Sh::T0_OFF);
@@ -357,7 +367,7 @@ tc_stp_kernel(const double* __restrict__ q, const double* __restrict__ params,
       for (int sd = 0; sd < T; ++sd) {
 #pragma unroll
         for (int s = 0; s < M; ++s) {
-          const float d0 = rintf(r[0][s]), d1 = rintf(r[1][s]);
+          const float d0 = round_int(r[0][s]), d1 = round_int(r[1][s]);
           r[0][s] = (r[0][s] - d0) * (float)(1 << W);  // exact: the residual has few bits
           r[1][s] = (r[1][s] - d1) * (float)(1 << W);
           const uint32_t wd = pack_digits<BF16>(d0, d1);
@@ -365,7 +375,7 @@ tc_stp_kernel(const double* __restrict__ q, const double* __restrict__ params,
           for (int pass = 0; pass < 3; ++pass) {
             const int q6 = q6_of(pass, s);
             if (q6 < 0) continue;
-            unsigned char* At = dig + pass * TILES * 8192 + q6 * (RQ / 8) * 512;
+            unsigned char* At = dig + pass * TILES * kTileBytes + q6 * (RQ / 8) * kGroupBytes;
             if (pass == 0) {
               const int kx = N * sd + px;
               if ((kx & 1) == 0) {  // an aligned word within one 8-k group
@@ -394,12 +404,12 @@ tc_stp_kernel(const double* __restrict__ q, const double* __restrict__ params,
       tc_fence_after();
       // descriptors advance by (byte offset >> 4) in their 14-bit address
       // field; shared-memory addresses stay below 2^18, so no carry
-      const uint64_t a0 = umma_desc(smem_u32(dig), 128, 512);
+      const uint64_t a0 = umma_desc(smem_u32(dig), 128, kGroupBytes);
       const uint64_t b0 = umma_desc(smem_u32(stile + (T - 1) * kTcOperandBytes), 128, 256);
       const int nch = (N * T + 15) / 16;  // K chunks holding the T digits
 #pragma unroll 1
       for (int j = iss; j < COMBOS; j += 2) {
-        const uint64_t ad = a0 + (uint64_t)(j * (8192 >> 4));
+        const uint64_t ad = a0 + (uint64_t)(j * (kTileBytes >> 4));
         const uint32_t dcol = tmem + (uint32_t)(j * CW);
         const uint32_t id = j < TILES ? idK : idMN;
         umma_f16(dcol, ad, b0, id, 0u);
