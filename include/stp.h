@@ -305,8 +305,11 @@ stp_precision stp_get_precision(stp_handle h);
 
 /*
  * Synchronise `stream`, then read and clear the handle's device status word.
- * *flags receives its bits (bit 0: a tensor-core completion wait in the mixed
- * kernel exceeded its iteration limit; the outputs of that launch are invalid;
+ * *flags receives its bits (bit 0: a bounded device-side wait exceeded its
+ * iteration limit - a tensor-core completion wait of the tensor-core
+ * precisions, or the wait for a bulk copy of an element into shared memory
+ * in the FP32 and tensor-core precisions; the outputs of that launch are
+ * invalid;
  * bit 1: set by stp_selftest_bounded_wait; bit 2: after such a timeout the
  * kernel's last bounded wait for the tensor cores to drain gave up too, so an
  * MMA may still have been writing tensor memory when the CTA released it -

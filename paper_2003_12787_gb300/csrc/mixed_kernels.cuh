@@ -516,11 +516,12 @@ mixed_stp_kernel(const double* __restrict__ q, const double* __restrict__ params
 #pragma unroll
     for (int s = 0; s < 9; ++s) ae[n * 9 + s] += (double)tail[j][s];
   }
-  if (!ok) {
+  if (!ok && tid == 0) {
     // the tensor-core work of the last pass did not signal completion in time:
-    // report it, give it one more bounded wait, then release TMEM and finish
-    if (tid == 0) atomicOr(status, 1u);
-    mbar_wait(bar, phase ^ 1u);
+    // report it, give it one more bounded wait, flag the context (bit 2) if
+    // the tensor cores are still not drained, then release TMEM and finish
+    const bool drained = mbar_wait(bar, phase ^ 1u);
+    atomicOr(status, drained ? 1u : 5u);
   }
   tc_fence_before();
   __syncthreads();

@@ -194,7 +194,7 @@ tc_stp_kernel(const double* __restrict__ q, const double* __restrict__ params,
               float dt_over_dx, int eD, int64_t E, unsigned int* __restrict__ status) {
   using Sh = TcShape<N>;
   using Dg = Digits<BF16>;
-  static_assert(TMAX >= 1 && TMAX <= 4, "one to four digits");
+  static_assert(TMAX >= 1 && TMAX <= 3, "one to three digits (operands of D exist for T <= 3)");
   constexpr int NT = Sh::NT, N3 = Sh::N3, S = Sh::S, RX = Sh::RX, PLANE = Sh::PLANE;
   constexpr int M = kQuantities, TILES = Sh::TILES, RQ = Sh::RQ, HP2 = Sh::HP2, CW = Sh::CW;
   constexpr int PAIRS = Sh::PAIRS, COMBOS = Sh::COMBOS, W = Dg::W;
@@ -551,9 +551,9 @@ cudaError_t launch_tc(int64_t E, const double* q, const double* params, double* 
   return cudaGetLastError();
 }
 
-// Variants 1..4 = BF16x2, BF16x3, FP16x2, FP16x3: the x3 settings aim at
-// 1e-9 (FP16: up to three 10-bit digits, BF16: up to four 8-bit digits), the
-// x2 settings cap the digits at two.
+// Variants 1..4 = BF16x2, BF16x3, FP16x2, FP16x3: the x3 settings use up to
+// three digits (10-bit FP16: stated 1e-9; 8-bit BF16: 5e-9), the x2
+// settings cap the digits at two.
 template <int N>
 cudaError_t launch_tc_n(int variant, int64_t E, const double* q, const double* params,
                         double* out_avg, double* out_faces, const double* tables,
@@ -563,7 +563,7 @@ cudaError_t launch_tc_n(int variant, int64_t E, const double* q, const double* p
   const unsigned char* tiles = reinterpret_cast<const unsigned char*>(tables + table_offset_tc(N));
   switch (variant) {
     case 1: return launch_tc<N, true, 2>(E, q, params, out_avg, out_faces, tables, tiles, dt_over_dx, eD, status, stream);
-    case 2: return launch_tc<N, true, 4>(E, q, params, out_avg, out_faces, tables, tiles, dt_over_dx, eD, status, stream);
+    case 2: return launch_tc<N, true, 3>(E, q, params, out_avg, out_faces, tables, tiles, dt_over_dx, eD, status, stream);
     case 3: return launch_tc<N, false, 2>(E, q, params, out_avg, out_faces, tables, tiles, dt_over_dx, eD, status, stream);
     case 4: return launch_tc<N, false, 3>(E, q, params, out_avg, out_faces, tables, tiles, dt_over_dx, eD, status, stream);
     default: return cudaErrorInvalidValue;
