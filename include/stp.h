@@ -541,6 +541,23 @@ stp_status stp_server_add_sim_curvilinear(stp_server s, stp_handle h, int64_t el
                                           const double* q0, const double* params,
                                           const double* metric, int* sim_id);
 
+/* A simulation with point sources (Sec. II-A: the source term, whose time
+ * derivatives enter every Cauchy-Kowalewsky order; the stp_point_source
+ * fields as for stp_predict_sources). Cartesian when metric is NULL, else
+ * curvilinear as stp_server_add_sim_curvilinear. The sources are validated,
+ * projected onto the nodes and uploaded once, by this call, into a small
+ * device block the server owns outside its HBM budget (freed by
+ * stp_server_destroy); after every step of the simulation their response is
+ * added in FP64 to the new average and faces, on the slot's stream and before
+ * the step counts as complete. Each step uses the same source derivatives.
+ * Errors as stp_server_add_sim and stp_predict_sources (an element outside
+ * [0, elements), a position outside [0,1]^3, a non-finite value or
+ * nsources < 0: STP_ERR_INVALID_ARG); STP_ERR_OOM when the device block
+ * cannot be allocated. nsources = 0 registers a simulation without sources. */
+stp_status stp_server_add_sim_sources(stp_server s, stp_handle h, int64_t elements,
+                                      const double* q0, const double* params, const double* metric,
+                                      int nsources, const stp_point_source* sources, int* sim_id);
+
 /*
  * Order in which the scheduler offers ready simulations to a launch.
  *   policy 0  FIFO: in the order their requests became ready.

@@ -99,6 +99,8 @@ def load():
                "stp_server_add_sim": [vp, vp, i64, vp, vp, ctypes.POINTER(ctypes.c_int)],
                "stp_server_add_sim_curvilinear": [vp, vp, i64, vp, vp, vp,
                                                   ctypes.POINTER(ctypes.c_int)],
+               "stp_server_add_sim_sources": [vp, vp, i64, vp, vp, vp, ctypes.c_int, vp,
+                                              ctypes.POINTER(ctypes.c_int)],
                "stp_server_submit": [vp, ctypes.c_int],
                "stp_server_set_policy": [vp, ctypes.c_int, ctypes.c_double],
                "stp_server_progress": [vp, ctypes.POINTER(ctypes.c_int)],
@@ -473,10 +475,19 @@ def stp_server_create(hbm_budget_bytes: int, slots: int = 3) -> int:
     return h.value
 
 
-def stp_server_add_sim(srv: int, handle: int, elements: int, q0, params, metric=None) -> int:
-    """metric: optional inverse Jacobians of a curvilinear simulation."""
+def stp_server_add_sim(srv: int, handle: int, elements: int, q0, params, metric=None,
+                       sources=None) -> int:
+    """metric: optional inverse Jacobians of a curvilinear simulation;
+    sources: optional point sources (dicts as for stp_predict_sources), added
+    after every step of the simulation."""
     i = ctypes.c_int()
-    if metric is None:
+    if sources:
+        arr = _source_array(sources)
+        _check(load().stp_server_add_sim_sources(srv, handle, elements, _ptr(q0), _ptr(params),
+                                                 None if metric is None else _ptr(metric),
+                                                 len(sources), ctypes.cast(arr, ctypes.c_void_p),
+                                                 ctypes.byref(i)), "stp_server_add_sim_sources")
+    elif metric is None:
         _check(load().stp_server_add_sim(srv, handle, elements, _ptr(q0), _ptr(params),
                                          ctypes.byref(i)), "stp_server_add_sim")
     else:

@@ -72,6 +72,7 @@ struct Sim {
   // its first eviction (the pinned footprint follows what is evicted)
   bool host_backed = false;
   bool resident = false;
+  ServedSources* sources = nullptr;  // point sources (owned), or none
   size_t off = 0;  // pool offset of [state0 | state1 | params | faces | metric]
   int cur = 0;     // which state buffer holds q_n
   bool busy = false, queued = false, have_faces = false;
@@ -316,6 +317,14 @@ struct Server {
                               s.bytes_metric ? metric(s) : nullptr, state(s, s.cur ^ 1), faces(s),
                               sl.stream);
       }
+      // point sources: their response added to the new average and faces,
+      // on the same stream and before the batch's completion event
+      for (int k = 0; e == cudaSuccess && k < n; ++k) {
+        Sim& s = sims[batch[k]];
+        if (s.sources)
+          e = served_sources_launch(s.sources, params(s), s.bytes_metric ? metric(s) : nullptr,
+                                    state(s, s.cur ^ 1), faces(s), sl.stream);
+      }
       if (e == cudaSuccess) e = cudaEventRecord(sl.done, sl.stream);
       if (e != cudaSuccess) {
         // nothing of this batch counts as launched: its simulations go back to
@@ -370,6 +379,7 @@ struct Server {
       cudaFreeHost(s.host_params);
       cudaFreeHost(s.host_faces);
       cudaFreeHost(s.host_metric);
+      served_sources_free(s.sources);
     }
     cudaFree(pool_base);
   }
@@ -412,10 +422,11 @@ void server_destroy(Server* s) {
 
 cudaError_t server_add_sim(Server* s, stp_handle h, int N, int64_t E, const double* q0,
                            const double* params, const double* metric, bool device_src, int* id,
-                           bool* too_big) {
+                           bool* too_big, ServedSources* sources) {
   *too_big = false;
   Sim sim;
   sim.handle = h;
+  sim.sources = sources;  // owned from here on only if this call succeeds
   sim.N = N;
   sim.E = E;
   const size_t n3 = (size_t)N * N * N;

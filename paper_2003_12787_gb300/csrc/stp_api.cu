@@ -437,6 +437,32 @@ cudaError_t launch_source_block(stp_handle h, const SourceData& sd, const char* 
                              avg, faces, reinterpret_cast<double*>(d_scr), st);
 }
 
+}  // namespace
+
+namespace stp {
+
+// Point sources of a served simulation: the prepared data and its device block.
+struct ServedSources {
+  stp_handle handle = nullptr;
+  SourceData sd;
+  char* d = nullptr;
+};
+
+cudaError_t served_sources_launch(const ServedSources* src, const double* params,
+                                  const double* metric, double* avg, double* faces, cudaStream_t st) {
+  return launch_source_block(src->handle, src->sd, src->d, params, metric, avg, faces, st);
+}
+
+void served_sources_free(ServedSources* src) {
+  if (!src) return;
+  cudaFree(src->d);
+  delete src;
+}
+
+}  // namespace stp
+
+namespace {
+
 stp_status predict_sources_impl(stp_handle h, int64_t elements, const double* q,
                                 const double* params, const double* metric, double* out_avg,
                                 double* out_faces, int nsources, const stp_point_source* sources,
@@ -1129,7 +1155,8 @@ bool is_device_memory(const void* p) {
 }
 
 stp_status server_add_sim_impl(stp_server s, stp_handle h, int64_t elements, const double* q0,
-                               const double* params, const double* metric, int* sim_id) {
+                               const double* params, const double* metric, int* sim_id,
+                               int nsources = 0, const stp_point_source* sources = nullptr) {
   if (!s || !s->impl || !h || !sim_id) return fail(STP_ERR_INVALID_ARG, "null argument");
   if (elements <= 0 || !q0 || !params) return fail(STP_ERR_INVALID_ARG, "bad simulation buffers");
   if (metric && h->N >= 2 && h->precision != STP_PRECISION_FP64 &&
@@ -1138,9 +1165,32 @@ stp_status server_add_sim_impl(stp_server s, stp_handle h, int64_t elements, con
   const bool dq = is_device_memory(q0), dp = is_device_memory(params);
   if (dq != dp || (metric && is_device_memory(metric) != dq))
     return fail(STP_ERR_INVALID_ARG, "q0, params (and metric) must be all host or all device");
+  stp::ServedSources* src = nullptr;
+  if (nsources > 0) {
+    stp_status st = validate_sources(h, elements, nsources, sources);
+    if (st != STP_OK) return st;
+    src = new (std::nothrow) stp::ServedSources;
+    if (!src) return fail(STP_ERR_OOM, "host allocation failed");
+    src->handle = h;
+    prepare_sources(h, metric != nullptr, nsources, sources, &src->sd);
+    cudaError_t e = cudaMalloc(&src->d, src->sd.bytes());
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      src->d = nullptr;
+      stp::served_sources_free(src);
+      return fail(STP_ERR_OOM, "cudaMalloc of the point-source data failed");
+    }
+    e = upload_sources(src->sd, src->d, nullptr);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(nullptr);
+    if (e != cudaSuccess) {
+      stp::served_sources_free(src);
+      return cuda_fail(e, "point-source upload");
+    }
+  }
   bool too_big = false;
   cudaError_t e = stp::server_add_sim(s->impl, h, h->N, elements, q0, params, metric, dq, sim_id,
-                                      &too_big);
+                                      &too_big, src);
+  if (e != cudaSuccess || too_big) stp::served_sources_free(src);
   if (too_big) return fail(STP_ERR_INVALID_ARG, "simulation does not fit the HBM budget");
   if (e == cudaErrorMemoryAllocation) return fail(STP_ERR_OOM, "pinned host allocation failed");
   if (e != cudaSuccess) return cuda_fail(e, "add simulation");
@@ -1161,6 +1211,13 @@ stp_status stp_server_add_sim_curvilinear(stp_server s, stp_handle h, int64_t el
                                           const double* metric, int* sim_id) {
   if (!metric) return fail(STP_ERR_INVALID_ARG, "null metric");
   return server_add_sim_impl(s, h, elements, q0, params, metric, sim_id);
+}
+
+stp_status stp_server_add_sim_sources(stp_server s, stp_handle h, int64_t elements,
+                                      const double* q0, const double* params, const double* metric,
+                                      int nsources, const stp_point_source* sources, int* sim_id) {
+  if (nsources < 0 || (nsources > 0 && !sources)) return fail(STP_ERR_INVALID_ARG, "bad source list");
+  return server_add_sim_impl(s, h, elements, q0, params, metric, sim_id, nsources, sources);
 }
 
 stp_status stp_server_set_policy(stp_server s, int policy, double age_bound_s) {

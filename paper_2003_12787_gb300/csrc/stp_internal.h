@@ -168,13 +168,22 @@ bool stp_handle_is_fp64(stp_handle h);
 cudaError_t stp_launch_handle(stp_handle h, int64_t E, const double* q, const double* params,
                               const double* metric, double* avg, double* faces, cudaStream_t st);
 
+// Point-source data of one served simulation, prepared and uploaded once
+// (stp_api.cu): the sources' response, added after every STP step of the
+// simulation to its new average and faces on stream st.
+struct ServedSources;
+cudaError_t served_sources_launch(const ServedSources* src, const double* params,
+                                  const double* metric, double* avg, double* faces, cudaStream_t st);
+void served_sources_free(ServedSources* src);
+
 // Served predictor (server.cu); see include/stp.h for the behaviour.
+// server_add_sim takes ownership of `sources` (may be NULL) when it succeeds.
 struct Server;
 cudaError_t server_create(int64_t budget, int nslots, Server** out);
 void server_destroy(Server* s);
 cudaError_t server_add_sim(Server* s, stp_handle h, int N, int64_t E, const double* q0,
                            const double* params, const double* metric, bool device_src, int* id,
-                           bool* too_big);
+                           bool* too_big, ServedSources* sources = nullptr);
 cudaError_t server_run_trace(Server* s, int64_t n, const double* t_arr, const int* sim_ids,
                              double* latency, double* wall);
 cudaError_t server_drain(Server* s);

@@ -215,12 +215,15 @@ class Server:
         self._steps0 = []  # steps taken before a restore
 
     def add_sim(self, predictor: "Predictor", q0: torch.Tensor, params: torch.Tensor,
-                metric=None) -> int:
-        """metric: optional inverse Jacobians (curvilinear simulation)."""
+                metric=None, sources=None) -> int:
+        """metric: optional inverse Jacobians (curvilinear simulation);
+        sources: optional point sources (as for ``predict_sources``), whose
+        response is added after every step."""
         predictor._check_inputs(q0, params)
         if metric is not None:
             predictor._check_metric(q0, metric)
-        sid = B.stp_server_add_sim(self.handle, predictor.handle, q0.shape[0], q0, params, metric)
+        sid = B.stp_server_add_sim(self.handle, predictor.handle, q0.shape[0], q0, params, metric,
+                                   sources)
         self.sims.append((predictor, q0.shape[0]))
         self._steps0.append(0)
         return sid
@@ -234,15 +237,17 @@ class Server:
     @classmethod
     def restore(cls, snapshot: list, sims: list, hbm_budget_bytes: int, slots: int = 3) -> "Server":
         """A server holding the simulations of ``snapshot``; ``sims`` gives,
-        in the same order, (Predictor, params, metric or None) of each (the
-        inputs that do not change between steps)."""
+        in the same order, (Predictor, params, metric or None[, sources]) of
+        each (the inputs that do not change between steps)."""
         if len(snapshot) != len(sims):
             raise ValueError("one (Predictor, params, metric) per snapshot entry")
         srv = cls(hbm_budget_bytes, slots)
-        for rec, (P, params, metric) in zip(snapshot, sims):
+        for rec, spec in zip(snapshot, sims):
+            P, params, metric = spec[:3]
+            sources = spec[3] if len(spec) > 3 else None
             dev = params.device
             srv.add_sim(P, rec["q"].to(dev).contiguous(), params,
-                        metric=None if metric is None else metric.to(dev))
+                        metric=None if metric is None else metric.to(dev), sources=sources)
             srv._steps0[-1] = int(rec["steps"])
         return srv
 

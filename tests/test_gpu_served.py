@@ -314,3 +314,69 @@ def test_full_size_simulations_same_alone_and_in_the_mix():
     assert float(np.abs(got - qs).max() / np.abs(qs).max()) <= 1e-12
     for P in preds:
         P.close()
+
+
+def _served_sources(N, E, rng):
+    return [{"element": e, "position": tuple(rng.uniform(0, 1, 3)),
+             "amplitude": rng.uniform(-1, 1, 9) * 50.0, "derivatives": rng.uniform(-2, 2, N)}
+            for e in (0, E - 1)]
+
+
+def test_point_sources_in_served_simulations_match_the_oracle():
+    """A served simulation with point sources: every step adds the sources'
+    response, so after `steps` requests its state equals the oracle's STP with
+    sources applied step by step (q_{n+1} = avg_n), within the FP64 bar; the
+    same holds alone and in a mix with simulations without sources under a
+    budget that evicts, bit for bit."""
+    import oracle
+    rng = np.random.default_rng(4100)
+    steps = 3
+    sims = problems()
+    srcs = [_served_sources(prob.N, prob.E, rng) if i % 2 == 0 else None
+            for i, (P, prob) in enumerate(sims)]
+    # alone
+    alone = []
+    for (P, prob), src in zip(sims, srcs):
+        srv = stp.Server(1 << 30, slots=2)
+        sid = srv.add_sim(P, prob.q, prob.params, sources=src)
+        for _ in range(steps):
+            srv.submit(sid)
+        srv.drain()
+        alone.append(srv.read(sid))
+        srv.close()
+    # the oracle, step by step
+    for (P, prob), src, (q_s, f_s, n) in zip(sims, srcs, alone):
+        assert n == steps
+        q = prob.q.cpu().numpy()
+        for _ in range(steps):
+            q, faces = oracle.stp(q, prob.params.cpu().numpy(), prob.h, prob.dt, sources=src)
+        s_q, s_f = np.abs(q).max(), np.abs(faces).max()
+        assert np.abs(q_s.numpy() - q).max() <= 1e-12 * s_q, prob.N
+        assert np.abs(f_s.numpy() - faces).max() <= 1e-12 * s_f, prob.N
+    # in the mix, with evictions
+    budget = max(footprint(N, E) for N, E in SPECS) * 2 + (1 << 20)
+    srv = stp.Server(budget, slots=3)
+    ids = [srv.add_sim(P, prob.q, prob.params, sources=src) for (P, prob), src in zip(sims, srcs)]
+    order = np.tile(np.arange(len(sims)), steps)
+    t = np.linspace(0.0, 0.02, len(order))
+    srv.run_trace(t, np.asarray(ids, dtype=np.int32)[order])
+    for i, sid in enumerate(ids):
+        q_m, f_m, n = srv.read(sid)
+        assert n == steps
+        assert torch.equal(q_m, alone[i][0]) and torch.equal(f_m, alone[i][1]), i
+    assert srv.stats()["evictions"] > 0
+    srv.close()
+
+
+def test_served_source_arguments_are_checked():
+    P, prob = problems()[0]
+    srv = stp.Server(1 << 28, slots=1)
+    N = prob.N
+    good = {"element": 0, "position": (0.5, 0.5, 0.5), "amplitude": [1.0] * 9, "derivatives": [1.0] * N}
+    for bad in (dict(good, element=prob.E), dict(good, position=(0.5, 1.5, 0.5)),
+                dict(good, amplitude=[np.nan] * 9), dict(good, derivatives=[np.inf] * N)):
+        with pytest.raises(RuntimeError):
+            srv.add_sim(P, prob.q, prob.params, sources=[bad])
+    sid = srv.add_sim(P, prob.q, prob.params, sources=[good])
+    assert sid == 0  # the failed registrations left no simulation behind
+    srv.close()
