@@ -337,8 +337,10 @@ stp_status stp_selftest_bounded_wait(stp_handle h, int polls, void* stream);
  * device buffers in the layouts above. The paper generates one kernel per
  * order (Sec. II-D, Sec. III); here, for FP64 sets, every order's
  * element-group body lives in one kernel and a cost-sorted work list of
- * (set, element range) units is consumed by one CTA per SM. Batches with
- * other precisions replay a graph of per-set launches instead.
+ * (set, element range) units is consumed by one CTA per SM; curvilinear FP64
+ * sets (stp_batch_create_curvilinear) are units of the same launch, one
+ * element each. Batches with other precisions replay a graph of per-set
+ * launches instead.
  */
 typedef struct {
   stp_handle handle;   /* predictor of this set (FP64 for the allocation-free path) */
@@ -377,12 +379,15 @@ stp_status stp_batch_create_ex(int nsets, const stp_batch_set* sets, const int* 
 
 /* As stp_batch_create, with curvilinear sets: metrics is a HOST array of
  * nsets device pointers, metrics[i] the inverse Jacobians of set i in the
- * layout of stp_predict_curvilinear, or NULL for a Cartesian set. A batch
- * with any curvilinear set is planned as the CUDA graph of per-set launches;
- * every set's results equal those of its own stp_predict_curvilinear (or
- * stp_predict). Metrics must not overlap any output. STP_ERR_INVALID_ARG for
- * metrics == NULL with nsets > 0, otherwise the errors of stp_batch_create and
- * stp_predict_curvilinear. */
+ * layout of stp_predict_curvilinear, or NULL for a Cartesian set. When every
+ * handle is FP64 the curvilinear sets join the Cartesian ones in the one
+ * persistent launch (a unit is one curvilinear element, run by the
+ * curvilinear FP64 body with the same arithmetic as stp_predict_curvilinear);
+ * otherwise the batch is the CUDA graph of per-set launches. Either way every
+ * set's results equal those of its own stp_predict_curvilinear (or
+ * stp_predict), bit for bit. Metrics must not overlap any output.
+ * STP_ERR_INVALID_ARG for metrics == NULL with nsets > 0, otherwise the errors
+ * of stp_batch_create and stp_predict_curvilinear. */
 stp_status stp_batch_create_curvilinear(int nsets, const stp_batch_set* sets,
                                         const double* const* metrics, stp_batch* out);
 

@@ -18,6 +18,7 @@
 #include <string>
 #include <vector>
 
+#include "curv_body.cuh"
 #include "fp64_eo.cuh"
 #include "fp64_group.cuh"
 
@@ -81,7 +82,29 @@ struct SetDev {
   int64_t E;
   int N;
   int variant;
+  const double* metric;  // curvilinear set: per-node inverse Jacobians; NULL: Cartesian
+  double dx;             // the handle's dx (curvilinear sets)
 };
+
+// Curvilinear element shapes in the 512-thread CTA: (N, nodes per thread,
+// quantities per line pass, lean register state). The quantities per pass
+// and the step arithmetic are those of the curvilinear kernel's own shapes
+// (curvilinear.cu), so a set gives the same bits in a batch as alone.
+#define STP_BATCH_CURV(X)                                                                      \
+  X(1, 1, 9, false) X(2, 1, 9, false) X(3, 1, 9, false) X(4, 1, 9, false) X(5, 1, 9, false)    \
+  X(6, 1, 9, false) X(7, 1, 9, false) X(8, 1, 9, false) X(9, 2, 9, false) X(10, 2, 9, true)    \
+  X(11, 3, 9, true) X(12, 4, 5, true)
+
+// Shared memory of order N's curvilinear shape (0 for other N).
+size_t curv_batch_smem(int N) {
+  switch (N) {
+#define X(n_, nodes_, a_, lean_) \
+  case n_: return CurvShape<n_, a_, false>::SMEM;
+    STP_BATCH_CURV(X)
+#undef X
+    default: return 0;
+  }
+}
 
 struct UnitDev {
   int64_t e0;
@@ -111,6 +134,14 @@ __device__ __noinline__ void run_unit_eo(double* smem, const SetDev& sd, int64_t
     fp64_element_eo<N, kBatchThreads, USE>(smem, sd.q, sd.params, sd.avg, sd.faces, sd.tables, e0);
 }
 
+template <int N, int NODES, int A, bool LEAN>
+__device__ __noinline__ void run_unit_curv(double* smem, const SetDev& sd, int64_t e0) {
+  if (e0 < sd.E)
+    curv_element<N, kBatchThreads, NODES, A, LEAN, false, false>(smem, sd.q, sd.params, sd.metric,
+                                                                 sd.avg, sd.faces, sd.tables, sd.dx,
+                                                                 e0);
+}
+
 __global__ void __launch_bounds__(kBatchThreads, 1)
 batch_kernel(const SetDev* __restrict__ sets, const UnitDev* __restrict__ units, int nunits,
              unsigned int* __restrict__ counter, double* __restrict__ scratch,
@@ -126,6 +157,16 @@ batch_kernel(const SetDev* __restrict__ sets, const UnitDev* __restrict__ units,
     if (u >= nunits) break;
     const UnitDev wu = units[u];
     const SetDev sd = sets[wu.set];
+    if (sd.metric) {  // a curvilinear set
+      switch (sd.N) {
+#define X(n_, nodes_, a_, lean_) \
+  case n_: run_unit_curv<n_, nodes_, a_, lean_>(smem, sd, wu.e0); break;
+        STP_BATCH_CURV(X)
+#undef X
+        default: break;
+      }
+      continue;
+    }
     switch (sd.N * kMaxVariants + sd.variant) {
 #define X(n_, v_, npt_, epc_, avgsm_, rg_) \
   case n_ * kMaxVariants + v_:              \
@@ -261,7 +302,7 @@ cudaError_t autotune(int N, const double* tables, int* variant, double* us_per_e
     for (int v = 0; v < kMaxVariants && err == cudaSuccess; ++v) {
       const ShapeInfo& si = shapes().s[N][v];
       if (!si.valid) continue;
-      SetDev sd{q, p, a, f, tables, E, N, v};
+      SetDev sd{q, p, a, f, tables, E, N, v, nullptr, 0.0};
       std::vector<UnitDev> units;
       for (int64_t e = 0; e < E; e += si.epc) units.push_back(UnitDev{e, 0, 0});
       chk(cudaMemcpyAsync(d_set, &sd, sizeof(sd), cudaMemcpyHostToDevice, st));
@@ -327,7 +368,8 @@ void destroy_plan(BatchPlan* p) {
 // persistent kernel into a CUDA graph. sets[i].variant < 0 = autotuned.
 cudaError_t create_plan(int nsets, const int* N, const int64_t* E, const double* const* q,
                         const double* const* params, double* const* avg, double* const* faces,
-                        const double* const* tables, const int* forced_variant, BatchPlan** out) {
+                        const double* const* tables, const int* forced_variant, BatchPlan** out,
+                        const double* const* metrics, const double* dx) {
   *out = nullptr;
   BatchPlan* p = new (std::nothrow) BatchPlan;
   if (!p) return cudaErrorMemoryAllocation;
@@ -336,6 +378,15 @@ cudaError_t create_plan(int nsets, const int* N, const int64_t* E, const double*
   std::vector<double> cost((size_t)nsets);
   cudaError_t err = cudaSuccess;
   for (int i = 0; i < nsets && err == cudaSuccess; ++i) {
+    if (metrics && metrics[i]) {  // curvilinear: one element per unit, cost by the FP64 estimate
+      if (N[i] < 1 || N[i] > kMaxNodes) { err = cudaErrorInvalidValue; break; }
+      const double F = 36.0 * std::pow(N[i], 5) + 66.0 * std::pow(N[i], 4) + 108.0 * std::pow(N[i], 3);
+      sets[i] = SetDev{q[i], params[i], avg[i], faces[i], tables[i], E[i], N[i], 0, metrics[i],
+                       dx ? dx[i] : 1.0};
+      cost[i] = 1.7 * F / 1.2e6;  // every quantity along every direction
+      p->smem = std::max(p->smem, curv_batch_smem(N[i]));
+      continue;
+    }
     int v = forced_variant ? forced_variant[i] : -1;
     double us = 0.0;
     if (v < 0) {
@@ -346,7 +397,7 @@ cudaError_t create_plan(int nsets, const int* N, const int64_t* E, const double*
     }
     if (err != cudaSuccess) break;
     if (v < 0 || v >= kMaxVariants || !shapes().s[N[i]][v].valid) { err = cudaErrorInvalidValue; break; }
-    sets[i] = SetDev{q[i], params[i], avg[i], faces[i], tables[i], E[i], N[i], v};
+    sets[i] = SetDev{q[i], params[i], avg[i], faces[i], tables[i], E[i], N[i], v, nullptr, 0.0};
     cost[i] = us * shapes().s[N[i]][v].epc;
     p->smem = std::max(p->smem, shapes().s[N[i]][v].smem);
     p->scratch_per_cta = std::max(p->scratch_per_cta, shapes().s[N[i]][v].scratch);
@@ -358,7 +409,7 @@ cudaError_t create_plan(int nsets, const int* N, const int64_t* E, const double*
     // longest units first; within a set, element order
     std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return cost[a] > cost[b]; });
     for (int i : order) {
-      const int epc = shapes().s[sets[i].N][sets[i].variant].epc;
+      const int epc = sets[i].metric ? 1 : shapes().s[sets[i].N][sets[i].variant].epc;
       for (int64_t e = 0; e < sets[i].E; e += epc) units.push_back(UnitDev{e, i, 0});
     }
     if (units.size() > 0x7fffffffu) err = cudaErrorInvalidValue;

@@ -73,12 +73,15 @@ __device__ __forceinline__ void ck_node_fp64(const double* __restrict__ p,
 }
 
 // Lame coefficients of one node from (rho, cp, cs): 1/rho, lambda, mu, 2 mu.
+// Every product is rounded on its own (no contraction into an FMA), so every
+// kernel that inlines this gets the same bits whatever the compiler fuses.
 __device__ __forceinline__ void elastic_coefficients(double rho, double cp, double cs,
                                                      double* invrho, double* lam, double* mu,
                                                      double* mu2) {
-  const double m = rho * (cs * cs);
+  const double cs2 = __dmul_rn(cs, cs);
+  const double m = __dmul_rn(rho, cs2);
   *invrho = 1.0 / rho;
-  *lam = rho * (cp * cp - 2.0 * (cs * cs));
+  *lam = __dmul_rn(rho, __dsub_rn(__dmul_rn(cp, cp), 2.0 * cs2));
   *mu = m;
   *mu2 = m + m;
 }

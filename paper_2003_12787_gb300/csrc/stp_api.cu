@@ -756,9 +756,9 @@ cudaError_t capture_set_launches(int nsets, const stp_batch_set* sets, const dou
 
 namespace {
 
-// Plans a batch: the persistent FP64 plan when every set is Cartesian FP64,
-// else a CUDA graph of per-set launches (metrics[i], when given and not
-// NULL, makes set i curvilinear).
+// Plans a batch: the persistent FP64 plan when every set is FP64 (metrics[i],
+// when given and not NULL, makes set i curvilinear: one element per unit),
+// else a CUDA graph of per-set launches.
 stp_status batch_create_impl(int nsets, const stp_batch_set* sets, const int* shapes,
                              const double* const* metrics, stp_batch* out) {
   if (!out) return fail(STP_ERR_INVALID_ARG, "out is NULL");
@@ -817,7 +817,8 @@ stp_status batch_create_impl(int nsets, const stp_batch_set* sets, const int* sh
                                                  " overlap buffers of set " + std::to_string(j));
     }
   }
-  bool all_fp64 = !any_metric;  // the persistent kernel holds the Cartesian FP64 bodies
+  // the persistent kernel holds the FP64 bodies, Cartesian and curvilinear
+  bool all_fp64 = true;
   for (int i = 0; i < nsets; ++i)
     if (sets[i].handle->precision != STP_PRECISION_FP64) all_fp64 = false;
   stp_batch b = new (std::nothrow) stp_batch_s;
@@ -845,6 +846,10 @@ stp_status batch_create_impl(int nsets, const stp_batch_set* sets, const int* sh
   if (shapes) {
     forced.assign(shapes, shapes + nsets);
     for (int i = 0; i < nsets; ++i) {
+      if (mt[i] && forced[i] >= 0) {
+        delete b;
+        return fail(STP_ERR_INVALID_ARG, "set " + std::to_string(i) + ": shapes apply to Cartesian sets");
+      }
       int epc[4];
       const int nv = stp::batch_variants_mask(N[i], epc);
       if (forced[i] >= 0 && (forced[i] >= 8 || !((nv >> forced[i]) & 1))) {
@@ -853,8 +858,11 @@ stp_status batch_create_impl(int nsets, const stp_batch_set* sets, const int* sh
       }
     }
   }
+  std::vector<double> dxs(nsets);
+  for (int i = 0; i < nsets; ++i) dxs[i] = sets[i].handle->dx;
   cudaError_t e = stp::create_plan(nsets, N.data(), E.data(), q.data(), p.data(), a.data(), f.data(),
-                                   tb.data(), shapes ? forced.data() : nullptr, &b->plan);
+                                   tb.data(), shapes ? forced.data() : nullptr, &b->plan,
+                                   any_metric ? mt.data() : nullptr, dxs.data());
   if (e != cudaSuccess) {
     delete b;
     if (e == cudaErrorMemoryAllocation) return fail(STP_ERR_OOM, "batch plan allocation failed");

@@ -131,9 +131,12 @@ int batch_variants_mask(int N, int* epc_out);
 // microseconds per element (may be NULL).
 cudaError_t autotune(int N, const double* tables, int* variant, double* us_per_element,
                      double* us_all);
+// metrics[i] (when metrics and it are not NULL) makes set i curvilinear, with
+// the handle's dx[i]; such sets run the curvilinear body in the same launch.
 cudaError_t create_plan(int nsets, const int* N, const int64_t* E, const double* const* q,
                         const double* const* params, double* const* avg, double* const* faces,
-                        const double* const* tables, const int* forced_variant, BatchPlan** out);
+                        const double* const* tables, const int* forced_variant, BatchPlan** out,
+                        const double* const* metrics = nullptr, const double* dx = nullptr);
 cudaError_t launch_plan(BatchPlan* p, cudaStream_t stream);
 void plan_info(const BatchPlan* p, int* units, int* ctas, size_t* smem);
 void destroy_plan(BatchPlan* p);

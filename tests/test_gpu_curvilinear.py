@@ -206,6 +206,39 @@ def test_batch_of_curvilinear_and_cartesian_sets():
         P.close()
 
 
+def test_fp64_curvilinear_sets_share_the_persistent_launch():
+    """An all-FP64 batch with curvilinear sets of every order beside Cartesian
+    ones is one persistent launch (units: one per curvilinear element, plus the
+    Cartesian element groups); every set equals its single-set call bit for
+    bit, replayed twice, and the curvilinear ones also meet the oracle."""
+    specs = [(N, 3 if N >= 10 else 7, True) for N in range(1, 13)]
+    specs += [(6, 250, False), (9, 40, False), (12, 6, False)]
+    items, metrics, probs = [], [], []
+    for i, (N, E, curv) in enumerate(specs):
+        make = curvilinear_problem if curv else elastic_problem
+        prob = make(N, E=E, seed_material=4200 + i, seed_waves=4300 + i)
+        items.append((stp.Predictor(N - 1, prob.h, prob.dt), prob.q.cuda(), prob.params.cuda()))
+        metrics.append(prob.metric.cuda() if curv else None)
+        probs.append(prob)
+    b = stp.Batch(items, metrics=metrics)
+    info = b.info()
+    assert info["ctas"] > 0, "an all-FP64 batch is one persistent launch"
+    assert info["units"] >= sum(E for _, E, c in specs if c)
+    b.launch()
+    b.launch()
+    torch.cuda.synchronize()
+    for i, (P, q, params) in enumerate(items):
+        a_b, f_b = b.outputs(i)
+        a_s, f_s = P.predict(q, params, metric=metrics[i])
+        torch.cuda.synchronize()
+        assert torch.equal(a_b, a_s) and torch.equal(f_b, f_s), specs[i]
+        if specs[i][2] and specs[i][0] in (1, 4, 7, 12):
+            check(probs[i], a_b.cpu().numpy(), f_b.cpu().numpy())
+    b.close()
+    for P, _, _ in items:
+        P.close()
+
+
 def test_curvilinear_simulations_in_the_served_loop():
     """Curvilinear and Cartesian simulations served together under a budget
     that forces evictions (the metric is re-admitted with the state): each
