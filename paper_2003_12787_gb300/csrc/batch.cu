@@ -86,21 +86,12 @@ struct SetDev {
   double dx;             // the handle's dx (curvilinear sets)
 };
 
-// Curvilinear element shapes in the 512-thread CTA: (N, nodes per thread,
-// quantities per line pass, lean register state). The quantities per pass
-// and the step arithmetic are those of the curvilinear kernel's own shapes
-// (curvilinear.cu), so a set gives the same bits in a batch as alone.
-#define STP_BATCH_CURV(X)                                                                      \
-  X(1, 1, 9, false) X(2, 1, 9, false) X(3, 1, 9, false) X(4, 1, 9, false) X(5, 1, 9, false)    \
-  X(6, 1, 9, false) X(7, 1, 9, false) X(8, 1, 9, false) X(9, 2, 9, false) X(10, 2, 9, true)    \
-  X(11, 3, 9, true) X(12, 4, 5, true)
-
 // Shared memory of order N's curvilinear shape (0 for other N).
 size_t curv_batch_smem(int N) {
   switch (N) {
 #define X(n_, nodes_, a_, lean_) \
   case n_: return CurvShape<n_, a_, false>::SMEM;
-    STP_BATCH_CURV(X)
+    STP_CURV512_SHAPES(X)
 #undef X
     default: return 0;
   }
@@ -161,7 +152,7 @@ batch_kernel(const SetDev* __restrict__ sets, const UnitDev* __restrict__ units,
       switch (sd.N) {
 #define X(n_, nodes_, a_, lean_) \
   case n_: run_unit_curv<n_, nodes_, a_, lean_>(smem, sd, wu.e0); break;
-        STP_BATCH_CURV(X)
+        STP_CURV512_SHAPES(X)
 #undef X
         default: break;
       }

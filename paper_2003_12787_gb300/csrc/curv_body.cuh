@@ -48,6 +48,16 @@ struct CurvShape {
       sizeof(double) * (size_t)(TABLE + (kQuantities + (DB ? 2 : 1) * A) * S);
 };
 
+// Curvilinear element shapes in the persistent kernels' 512-thread CTAs:
+// (N, nodes per thread, quantities per line pass, lean register state). The
+// quantities per pass follow the curvilinear kernel's own shapes; as the
+// arithmetic does not depend on the thread layout, a set gives the same bits
+// in a persistent launch as alone.
+#define STP_CURV512_SHAPES(X)                                                                  \
+  X(1, 1, 9, false) X(2, 1, 9, false) X(3, 1, 9, false) X(4, 1, 9, false) X(5, 1, 9, false)    \
+  X(6, 1, 9, false) X(7, 1, 9, false) X(8, 1, 9, false) X(9, 2, 9, false) X(10, 2, 9, true)    \
+  X(11, 3, 9, true) X(12, 4, 5, true)
+
 // One element (index e, by a CTA of NT threads; the caller guarantees
 // e < E); thread t owns nodes t, t + NT, ...
 // (NODES of them). LEAN keeps only the partial sums in registers: the running

@@ -15,6 +15,7 @@
 #include <algorithm>
 #include <mutex>
 
+#include "curv_body.cuh"
 #include "fp64_eo.cuh"
 #include "fp64_group.cuh"
 
@@ -57,6 +58,8 @@ struct StaticSet {
   int64_t first_unit;  // units of the sets before this one
   int N;
   int epc;
+  const double* metric;  // curvilinear set: per-node inverse Jacobians; NULL: Cartesian
+  double dx;             // the handle's dx (curvilinear sets)
 };
 
 struct StaticBatch {
@@ -75,6 +78,13 @@ template <int N, int NPT, int EPC, bool AVG, bool RG>
 __device__ __noinline__ void static_unit(double* smem, const StaticSet& sd, int64_t e0, double* rbuf) {
   fp64_group<N, NPT, EPC, AVG, kStaticThreads, RG>(smem, sd.q, sd.params, sd.avg, sd.faces,
                                                    sd.tables, e0, sd.E, rbuf);
+}
+
+template <int N, int NODES, int A, bool LEAN>
+__device__ __noinline__ void static_unit_curv(double* smem, const StaticSet& sd, int64_t e0) {
+  if (e0 < sd.E)
+    curv_element<N, kStaticThreads, NODES, A, LEAN, false, false>(
+        smem, sd.q, sd.params, sd.metric, sd.avg, sd.faces, sd.tables, sd.dx, e0);
 }
 
 __global__ void __launch_bounds__(kStaticThreads, 1)
@@ -97,6 +107,16 @@ static_batch_kernel(const __grid_constant__ StaticBatch b, unsigned char* scratc
     }
     const StaticSet& sd = b.sets[lo];
     const int64_t e0 = (u - sd.first_unit) * sd.epc;
+    if (sd.metric) {  // a curvilinear set, one element per unit
+      switch (sd.N) {
+#define X(n_, nodes_, a_, lean_) \
+  case n_: static_unit_curv<n_, nodes_, a_, lean_>(smem, sd, e0); break;
+        STP_CURV512_SHAPES(X)
+#undef X
+        default: break;
+      }
+      continue;
+    }
     switch (sd.N) {
 #define X(n_, npt_, epc_, avg_, rg_) \
   case n_: static_unit<n_, npt_, epc_, avg_, rg_>(smem, sd, e0, rbuf); break;
@@ -116,7 +136,16 @@ struct StaticShape {
   size_t smem = 0, park = 0;
 };
 
-StaticShape static_shape(int N) {
+StaticShape static_shape(int N, bool curvilinear) {
+  if (curvilinear) {
+    switch (N) {
+#define X(n_, nodes_, a_, lean_) \
+  case n_: return StaticShape{1, CurvShape<n_, a_, false>::SMEM, 0};
+      STP_CURV512_SHAPES(X)
+#undef X
+      default: return StaticShape{};
+    }
+  }
   switch (N) {
 #define X(n_, npt_, epc_, avg_, rg_)                                                              \
   case n_:                                                                                       \
@@ -144,6 +173,9 @@ size_t max_static_smem() {
 #undef X
 #define X(n_, use_) m = std::max(m, (size_t)EoShape<n_>::SMEM);
   STP_STATIC_EO(X)
+#undef X
+#define X(n_, nodes_, a_, lean_) m = std::max(m, (size_t)CurvShape<n_, a_, false>::SMEM);
+  STP_CURV512_SHAPES(X)
 #undef X
   return m;
 }
@@ -229,7 +261,7 @@ cudaError_t launch_param_batch(int nsets, const int* N, const int64_t* E, const 
                                const double* const* params, double* const* avg,
                                double* const* faces, const double* const* tables,
                                unsigned char* scratch, size_t scratch_bytes, cudaStream_t stream,
-                               int* too_big) {
+                               int* too_big, const double* const* metrics, const double* dx) {
   *too_big = 0;
   if (nsets < 0 || nsets > kStaticMaxSets) { *too_big = 1; return cudaErrorInvalidValue; }
   int dev = 0;
@@ -240,9 +272,11 @@ cudaError_t launch_param_batch(int nsets, const int* N, const int64_t* E, const 
   int64_t units = 0;
   size_t smem = 1, park = 0;
   for (int i = 0; i < nsets; ++i) {
-    const StaticShape sh = static_shape(N[i]);
+    const double* m = metrics ? metrics[i] : nullptr;
+    const StaticShape sh = static_shape(N[i], m != nullptr);
     if (sh.epc == 0) return cudaErrorInvalidValue;
-    b.sets[i] = StaticSet{q[i], params[i], avg[i], faces[i], tables[i], E[i], units, N[i], sh.epc};
+    b.sets[i] = StaticSet{q[i], params[i], avg[i], faces[i], tables[i], E[i], units, N[i], sh.epc,
+                          m, m && dx ? dx[i] : 0.0};
     units += (E[i] + sh.epc - 1) / sh.epc;
     if (E[i] > 0) {
       smem = std::max(smem, sh.smem);
@@ -283,7 +317,8 @@ namespace stp {
 cudaError_t run_static_batch(int nsets, const int* N, const int64_t* E, const double* const* q,
                              const double* const* params, double* const* avg,
                              double* const* faces, const double* const* tables,
-                             cudaStream_t stream, int* too_big, size_t reserve_top) {
+                             cudaStream_t stream, int* too_big, size_t reserve_top,
+                             const double* const* metrics, const double* dx) {
   *too_big = 0;
   if (reserve_top > kStaticScratchBytes - kCounterBytes) {
     *too_big = 1;
@@ -295,7 +330,7 @@ cudaError_t run_static_batch(int nsets, const int* N, const int64_t* E, const do
   unsigned char* scratch = nullptr;
   if ((e = scratch_address(dev, &scratch)) != cudaSuccess) return e;
   return launch_param_batch(nsets, N, E, q, params, avg, faces, tables, scratch,
-                            kStaticScratchBytes - reserve_top, stream, too_big);
+                            kStaticScratchBytes - reserve_top, stream, too_big, metrics, dx);
 }
 
 // Device address of the top `bytes` of the static array (bytes a multiple of

@@ -22,11 +22,11 @@
 //      admission waits for the evictions issued before it (its memory may be
 //      theirs, and a re-admitted simulation's host copy must be complete);
 //   3. launches up to 128 ready, resident simulations as ONE persistent
-//      batched FP64 launch on a free slot (its own stream and scratch);
-//      curvilinear simulations (their per-node inverse Jacobians resident
-//      beside the material) and simulations whose handle runs another
-//      precision get a launch of their own (the handle's kernel) on the same
-//      stream, between the same timing events.
+//      batched FP64 launch on a free slot (its own stream and scratch),
+//      Cartesian and curvilinear ones (their per-node inverse Jacobians
+//      resident beside the material) alike; simulations whose handle runs
+//      another precision get a launch of their own (the handle's kernel) on
+//      the same stream, between the same timing events.
 // New requests therefore join the next launch while earlier launches are
 // still on the GPU, and launches on different slots overlap on the device.
 #include <algorithm>
@@ -285,16 +285,17 @@ struct Server {
         }
       }
       const int n = (int)batch.size();
-      std::vector<int> N, curv;  // curv: simulations launched one by one
+      std::vector<int> N, own;  // own: simulations launched one by one (not FP64)
       std::vector<int64_t> E;
-      std::vector<const double*> q, p, tb;
+      std::vector<const double*> q, p, tb, mt;
       std::vector<double*> a, f;
+      std::vector<double> dx;
       for (int k = 0; k < n; ++k) {
         Sim& s = sims[batch[k]];
         s.busy = true;
         s.queued = false;
-        if (s.bytes_metric || !stp_handle_is_fp64(s.handle)) {  // a launch of its own
-          curv.push_back(batch[k]);
+        if (!stp_handle_is_fp64(s.handle)) {  // a launch of its own
+          own.push_back(batch[k]);
           continue;
         }
         N.push_back(s.N);
@@ -304,15 +305,17 @@ struct Server {
         p.push_back(params(s));
         f.push_back(faces(s));
         tb.push_back(stp_handle_tables(s.handle));
+        mt.push_back(s.bytes_metric ? metric(s) : nullptr);  // curvilinear: same launch
+        dx.push_back(stp_handle_dx(s.handle));
       }
       int too_big = 0;
       e = cudaEventRecord(sl.start, sl.stream);
       if (e == cudaSuccess && !N.empty())
         e = launch_param_batch((int)N.size(), N.data(), E.data(), q.data(), p.data(), a.data(),
                                f.data(), tb.data(), sl.scratch, static_scratch_bytes(), sl.stream,
-                               &too_big);
-      for (size_t k = 0; e == cudaSuccess && k < curv.size(); ++k) {
-        Sim& s = sims[curv[k]];
+                               &too_big, mt.data(), dx.data());
+      for (size_t k = 0; e == cudaSuccess && k < own.size(); ++k) {
+        Sim& s = sims[own[k]];
         e = stp_launch_handle(s.handle, s.E, state(s, s.cur), params(s),
                               s.bytes_metric ? metric(s) : nullptr, state(s, s.cur ^ 1), faces(s),
                               sl.stream);

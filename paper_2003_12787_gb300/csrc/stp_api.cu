@@ -987,8 +987,8 @@ stp_status stp_autotune(stp_handle h, int* variant, double* us_per_element, doub
 namespace {
 
 // The allocation-free batched launch; metrics (host array, may be NULL or hold
-// NULLs) marks curvilinear sets, which run as their own FP64 curvilinear
-// launches after the persistent launch of the Cartesian ones.
+// NULLs) marks curvilinear sets, which run in the same persistent launch as
+// the Cartesian ones (one element per work unit).
 stp_status run_static_impl(int nsets, const stp_batch_set* sets, const double* const* metrics,
                            void* stream, const int* nsources = nullptr,
                            const stp_point_source* const* sources = nullptr) {
@@ -1077,27 +1077,15 @@ stp_status run_static_impl(int nsets, const stp_batch_set* sets, const double* c
       off += sd.bytes();
     }
   }
-  // the Cartesian sets in one persistent launch, compacted in call order
-  int nc = 0;
-  for (int i = 0; i < nsets; ++i) {
-    if (mt[i]) continue;
-    N[nc] = N[i]; E[nc] = E[i]; q[nc] = q[i]; p[nc] = p[i]; a[nc] = a[i]; f[nc] = f[i];
-    tb[nc] = tb[i];
-    ++nc;
-  }
+  // every set, Cartesian and curvilinear, in one persistent launch
+  double dxs[kMax];
+  for (int i = 0; i < nsets; ++i) dxs[i] = sets[i].handle->dx;
   cudaError_t e = cudaSuccess;
-  if (nc > 0) {
+  if (nsets > 0) {
     int too_big = 0;
-    e = stp::run_static_batch(nc, N, E, q, p, a, f, tb, st, &too_big, reserve);
+    e = stp::run_static_batch(nsets, N, E, q, p, a, f, tb, st, &too_big, reserve, mt, dxs);
     if (too_big) return fail(STP_ERR_INVALID_ARG, "the call needs more than the 24 MiB static scratch");
     if (e != cudaSuccess) return cuda_fail(e, "static batched launch");
-  }
-  for (int i = 0; i < nsets; ++i) {
-    const stp_batch_set& s = sets[i];
-    if (!mt[i] || s.elements == 0) continue;
-    e = stp::launch_curvilinear(s.handle->N, s.elements, s.q, s.params, mt[i], s.out_avg,
-                                s.out_faces, s.handle->d_tables, s.handle->dx, st);
-    if (e != cudaSuccess) return cuda_fail(e, "static curvilinear launch");
   }
   size_t off = 0;
   for (size_t k = 0; k < sds.size(); ++k) {

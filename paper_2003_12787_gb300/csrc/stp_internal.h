@@ -143,10 +143,13 @@ void destroy_plan(BatchPlan* p);
 
 // Batched FP64 launch with all scratch in a fixed-size static device array
 // (noalloc.cu). *too_big = 1 when nsets or the needed scratch exceed it.
+// metrics[i] (when metrics and it are not NULL) makes set i curvilinear, with
+// the handle's dx[i]: one element per work unit of the same launch.
 cudaError_t run_static_batch(int nsets, const int* N, const int64_t* E, const double* const* q,
                              const double* const* params, double* const* avg,
                              double* const* faces, const double* const* tables,
-                             cudaStream_t stream, int* too_big, size_t reserve_top = 0);
+                             cudaStream_t stream, int* too_big, size_t reserve_top = 0,
+                             const double* const* metrics = nullptr, const double* dx = nullptr);
 // Device address of the top `bytes` (a multiple of 256) of that static array.
 cudaError_t static_scratch_top(size_t bytes, unsigned char** out);
 
@@ -157,7 +160,8 @@ cudaError_t launch_param_batch(int nsets, const int* N, const int64_t* E, const 
                                const double* const* params, double* const* avg,
                                double* const* faces, const double* const* tables,
                                unsigned char* scratch, size_t scratch_bytes, cudaStream_t stream,
-                               int* too_big);
+                               int* too_big, const double* const* metrics = nullptr,
+                               const double* dx = nullptr);
 size_t static_scratch_bytes();
 int static_max_sets();
 

@@ -10,7 +10,7 @@ import torch
 
 import paper_2003_12787_gb300 as stp
 from paper_2003_12787_gb300 import _binding
-from paper_2003_12787_gb300.inputs import elastic_problem, served_arrivals
+from paper_2003_12787_gb300.inputs import curvilinear_problem, elastic_problem, served_arrivals
 
 pytestmark = pytest.mark.gpu
 
@@ -380,3 +380,56 @@ def test_served_source_arguments_are_checked():
     sid = srv.add_sim(P, prob.q, prob.params, sources=[good])
     assert sid == 0  # the failed registrations left no simulation behind
     srv.close()
+
+
+def test_curvilinear_simulations_with_sources_match_the_oracle():
+    """The paper's LOH1 setting in the served loop: curvilinear FP64
+    simulations, half of them with point sources, share the persistent
+    launch with Cartesian ones. Alone, each equals the oracle's curvilinear
+    STP with its sources applied step by step (q_{n+1} = avg_n) within the
+    FP64 bar; in the mix, under a budget that evicts, each equals its run
+    alone bit for bit."""
+    import oracle
+    rng = np.random.default_rng(4400)
+    steps = 3
+    specs = [(4, 40, True), (7, 10, True), (10, 4, True), (6, 20, False), (12, 2, True)]
+    sims, srcs = [], []
+    for i, (N, E, curv) in enumerate(specs):
+        make = curvilinear_problem if curv else elastic_problem
+        prob = make(N, E=E, seed_material=4500 + i, seed_waves=4600 + i)
+        sims.append((stp.Predictor(N - 1, prob.h, prob.dt), prob))
+        srcs.append(_served_sources(N, E, rng) if i % 2 == 0 else None)
+    alone = []
+    for (P, prob), src in zip(sims, srcs):
+        srv = stp.Server(1 << 30, slots=2)
+        sid = srv.add_sim(P, prob.q, prob.params, metric=prob.metric, sources=src)
+        for _ in range(steps):
+            srv.submit(sid)
+        srv.drain()
+        alone.append(srv.read(sid))
+        srv.close()
+    for (P, prob), src, (q_s, f_s, n) in zip(sims, srcs, alone):
+        assert n == steps
+        q = prob.q.cpu().numpy()
+        for _ in range(steps):
+            if prob.metric is not None:
+                q, faces = oracle.stp_curvilinear(q, prob.params.numpy(), prob.metric.numpy(), prob.dt,
+                                                  sources=src)
+            else:
+                q, faces = oracle.stp(q, prob.params.numpy(), prob.h, prob.dt, sources=src)
+        assert np.abs(q_s.numpy() - q).max() <= 1e-12 * np.abs(q).max(), prob.N
+        assert np.abs(f_s.numpy() - faces).max() <= 1e-12 * np.abs(faces).max(), prob.N
+    foot = max(8 * E * ((30 if c else 21) * N ** 3 + 54 * N ** 2) + 5 * 256 for N, E, c in specs)
+    srv = stp.Server(2 * foot + (1 << 20), slots=3)
+    ids = [srv.add_sim(P, prob.q, prob.params, metric=prob.metric, sources=src)
+           for (P, prob), src in zip(sims, srcs)]
+    order = np.tile(np.arange(len(sims)), steps)
+    srv.run_trace(np.linspace(0.0, 0.02, len(order)), np.asarray(ids, dtype=np.int32)[order])
+    assert srv.stats()["evictions"] > 0
+    for i, sid in enumerate(ids):
+        q_m, f_m, n = srv.read(sid)
+        assert n == steps
+        assert torch.equal(q_m, alone[i][0]) and torch.equal(f_m, alone[i][1]), specs[i]
+    srv.close()
+    for P, _ in sims:
+        P.close()

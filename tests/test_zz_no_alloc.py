@@ -93,12 +93,15 @@ def test_static_batch_allocates_no_device_memory():
 
 
 def test_static_batch_with_curvilinear_sets():
-    """stp_batch_run_static_curvilinear: curvilinear sets (own FP64 launches
-    after the persistent one) beside Cartesian ones; every set equals its
-    single-set call bit for bit (the curvilinear kernels are the same)."""
+    """stp_batch_run_static_curvilinear: curvilinear sets of every order in
+    the same persistent launch as Cartesian ones (one element per work unit);
+    every curvilinear set equals its single-set call bit for bit (the same
+    element body and rounding order), the Cartesian ones as in the tests
+    above."""
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
-    specs = [(5, 40, True), (8, 9, False), (7, 12, True), (4, 30, False), (12, 2, True)]
+    specs = [(N, 3 if N >= 10 else 11, True) for N in range(1, 13)]
+    specs += [(8, 9, False), (4, 30, False), (12, 2, False)]
     sets, refs, outs, metrics = [], [], [], []
     for i, (N, E, curv) in enumerate(specs):
         make = curvilinear_problem if curv else elastic_problem
