@@ -103,38 +103,61 @@ struct UnitDev {
   int pad;
 };
 
-// One shape of one order over one work unit, as its own (non-inlined) device
-// function, so that every shape gets its own register allocation inside the
-// single persistent kernel.
-template <int N, int V, int NPT, int EPC, bool AVG, bool RG>
-__device__ __noinline__ void run_unit(double* smem, const SetDev& sd, int64_t e0, double* rbuf) {
-  fp64_group<N, NPT, EPC, AVG, kBatchThreads, RG>(smem, sd.q, sd.params, sd.avg, sd.faces,
-                                                  sd.tables, e0, sd.E, rbuf);
-}
+// Set descriptors of one launch, passed as a kernel parameter: read from the
+// parameter space, the buffer pointers reach the element bodies as they do in
+// the single-set kernels. Loaded from a device array instead, the same bodies
+// ran 7 % slower (N = 12, measured on GB300), spilled or not, persistent or not.
+constexpr int kParamSets = 128;
+struct SetTable {
+  SetDev sets[kParamSets];
+};
+
+// The body of one shape over one work unit. Every shape gets a persistent
+// kernel of its own (order_kernel<Unit>) with its body inlined, so that its
+// register allocation is that of its single-set kernel (hosting every body
+// in one kernel, as calls or inlined, capped them at that kernel's 128
+// registers and spilled the large-N ones).
+template <int N, int NPT, int EPC, bool AVG, bool RG>
+struct GroupUnit {
+  static __device__ __forceinline__ void run(double* smem, const SetDev& sd, int64_t e0,
+                                             double* rbuf) {
+    fp64_group<N, NPT, EPC, AVG, kBatchThreads, RG>(smem, sd.q, sd.params, sd.avg, sd.faces,
+                                                    sd.tables, e0, sd.E, rbuf);
+  }
+};
 
 template <int N, int USE>
-__device__ __noinline__ void run_unit_eo_slots(double* smem, const SetDev& sd, int64_t e0) {
-  if (e0 < sd.E)
-    fp64_element_eo_slots<N, kBatchThreads, USE>(smem, sd.q, sd.params, sd.avg, sd.faces, sd.tables,
-                                                 e0);
-}
+struct EoUnit {
+  static __device__ __forceinline__ void run(double* smem, const SetDev& sd, int64_t e0, double*) {
+    if (e0 < sd.E)
+      fp64_element_eo<N, kBatchThreads, USE>(smem, sd.q, sd.params, sd.avg, sd.faces, sd.tables, e0);
+  }
+};
 
 template <int N, int USE>
-__device__ __noinline__ void run_unit_eo(double* smem, const SetDev& sd, int64_t e0) {
-  if (e0 < sd.E)
-    fp64_element_eo<N, kBatchThreads, USE>(smem, sd.q, sd.params, sd.avg, sd.faces, sd.tables, e0);
-}
+struct EoSlotsUnit {
+  static __device__ __forceinline__ void run(double* smem, const SetDev& sd, int64_t e0, double*) {
+    if (e0 < sd.E)
+      fp64_element_eo_slots<N, kBatchThreads, USE>(smem, sd.q, sd.params, sd.avg, sd.faces,
+                                                   sd.tables, e0);
+  }
+};
 
 template <int N, int NODES, int A, bool LEAN>
-__device__ __noinline__ void run_unit_curv(double* smem, const SetDev& sd, int64_t e0) {
-  if (e0 < sd.E)
-    curv_element<N, kBatchThreads, NODES, A, LEAN, false, false>(smem, sd.q, sd.params, sd.metric,
-                                                                 sd.avg, sd.faces, sd.tables, sd.dx,
-                                                                 e0);
-}
+struct CurvUnit {
+  static __device__ __forceinline__ void run(double* smem, const SetDev& sd, int64_t e0, double*) {
+    if (e0 < sd.E)
+      curv_element<N, kBatchThreads, NODES, A, LEAN, false, false>(
+          smem, sd.q, sd.params, sd.metric, sd.avg, sd.faces, sd.tables, sd.dx, e0);
+  }
+};
 
+// Persistent kernel of one shape: its CTAs take units of its own work list
+// (units of up to kParamSets sets of that shape; UnitDev::set indexes tb)
+// through an atomic counter until the list is exhausted.
+template <class Unit>
 __global__ void __launch_bounds__(kBatchThreads, 1)
-batch_kernel(const SetDev* __restrict__ sets, const UnitDev* __restrict__ units, int nunits,
+order_kernel(const __grid_constant__ SetTable tb, const UnitDev* __restrict__ units, int nunits,
              unsigned int* __restrict__ counter, double* __restrict__ scratch,
              int64_t scratch_doubles_per_cta) {
   double* rbuf = scratch ? scratch + blockIdx.x * scratch_doubles_per_cta : nullptr;
@@ -147,34 +170,39 @@ batch_kernel(const SetDev* __restrict__ sets, const UnitDev* __restrict__ units,
     __syncthreads();  // everyone has read cur before thread 0 may overwrite it
     if (u >= nunits) break;
     const UnitDev wu = units[u];
-    const SetDev sd = sets[wu.set];
-    if (sd.metric) {  // a curvilinear set
-      switch (sd.N) {
-#define X(n_, nodes_, a_, lean_) \
-  case n_: run_unit_curv<n_, nodes_, a_, lean_>(smem, sd, wu.e0); break;
-        STP_CURV512_SHAPES(X)
-#undef X
-        default: break;
-      }
-      continue;
-    }
-    switch (sd.N * kMaxVariants + sd.variant) {
+    Unit::run(smem, tb.sets[wu.set], wu.e0, rbuf);
+  }
+}
+
+using OrderKernel = void (*)(const SetTable, const UnitDev*, int, unsigned int*, double*, int64_t);
+
+// Kernel of order N's Cartesian shape v.
+OrderKernel cart_kernel(int N, int v) {
+  switch (N * kMaxVariants + v) {
 #define X(n_, v_, npt_, epc_, avgsm_, rg_) \
-  case n_ * kMaxVariants + v_:              \
-    run_unit<n_, v_, npt_, epc_, avgsm_, rg_>(smem, sd, wu.e0, rbuf); \
-    break;
-      STP_BATCH_SHAPES(X)
+  case n_ * kMaxVariants + v_: return order_kernel<GroupUnit<n_, npt_, epc_, avgsm_, rg_>>;
+    STP_BATCH_SHAPES(X)
 #undef X
 #define X(n_, v_, use_) \
-  case n_ * kMaxVariants + v_: run_unit_eo<n_, use_>(smem, sd, wu.e0); break;
-      STP_BATCH_EO(X)
+  case n_ * kMaxVariants + v_: return order_kernel<EoUnit<n_, use_>>;
+    STP_BATCH_EO(X)
 #undef X
 #define X(n_, v_, use_) \
-  case n_ * kMaxVariants + v_: run_unit_eo_slots<n_, use_>(smem, sd, wu.e0); break;
-      STP_BATCH_EO_SLOTS(X)
+  case n_ * kMaxVariants + v_: return order_kernel<EoSlotsUnit<n_, use_>>;
+    STP_BATCH_EO_SLOTS(X)
 #undef X
-      default: break;
-    }
+    default: return nullptr;
+  }
+}
+
+// Kernel of order N's curvilinear shape.
+OrderKernel curv_kernel(int N) {
+  switch (N) {
+#define X(n_, nodes_, a_, lean_) \
+  case n_: return order_kernel<CurvUnit<n_, nodes_, a_, lean_>>;
+    STP_CURV512_SHAPES(X)
+#undef X
+    default: return nullptr;
   }
 }
 
@@ -201,22 +229,27 @@ int sm_count() {
   return sms;
 }
 
-// Counter reset + one launch of the batch kernel over prepared device arrays
-// (stream operations only, so it can be captured into a graph). The caller
-// has raised the kernel's dynamic shared-memory limit to at least smem.
-cudaError_t launch_batch(const SetDev* d_sets, const UnitDev* d_units, int nunits,
+// One launch of a shape's persistent kernel over its part of the work list
+// (stream operations only, so it can be captured into a graph); the caller
+// resets the counter and has raised the kernel's dynamic shared-memory limit
+// to at least smem (prepare_kernel).
+cudaError_t launch_order(OrderKernel k, const SetTable& tb, const UnitDev* d_units, int nunits,
                          unsigned int* d_counter, double* scratch, size_t scratch_per_cta,
                          size_t smem, int ctas, cudaStream_t st) {
-  cudaError_t e = cudaMemsetAsync(d_counter, 0, sizeof(unsigned int), st);
-  if (e != cudaSuccess) return e;
-  batch_kernel<<<ctas, kBatchThreads, smem, st>>>(d_sets, d_units, nunits, d_counter, scratch,
-                                                  (int64_t)(scratch_per_cta / sizeof(double)));
+  k<<<ctas, kBatchThreads, std::max<size_t>(smem, 1), st>>>(
+      tb, d_units, nunits, d_counter, scratch, (int64_t)(scratch_per_cta / sizeof(double)));
   return cudaGetLastError();
 }
 
-cudaError_t raise_smem_limit(size_t smem) {
-  return cudaFuncSetAttribute(batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)std::max<size_t>(smem, 1));
+// Raises kernel k's shared-memory limit to smem; *per_sm = its CTAs per SM.
+cudaError_t prepare_kernel(OrderKernel k, size_t smem, int* per_sm) {
+  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)std::max<size_t>(smem, 1));
+  if (e == cudaSuccess)
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, k, kBatchThreads,
+                                                      std::max<size_t>(smem, 1));
+  if (e == cudaSuccess && *per_sm < 1) e = cudaErrorInvalidConfiguration;
+  return e;
 }
 
 }  // namespace
@@ -242,7 +275,7 @@ int batch_variants(int N, int* epc_out) {
 }
 
 // Time every candidate shape of order N on a synthetic set (zero state,
-// unit material) with the persistent kernel; keep the fastest per device.
+// unit material) with its persistent kernel; keep the fastest per device.
 cudaError_t autotune(int N, const double* tables, int* variant, double* us_per_element,
                      double* us_all) {
   int dev = 0;
@@ -262,7 +295,6 @@ cudaError_t autotune(int N, const double* tables, int* variant, double* us_per_e
     E = std::min<int64_t>(E, 100000);
     const size_t n3 = (size_t)N * N * N;
     double *q = nullptr, *p = nullptr, *a = nullptr, *f = nullptr;
-    SetDev* d_set = nullptr;
     UnitDev* d_units = nullptr;
     unsigned int* d_counter = nullptr;
     cudaStream_t st = nullptr;
@@ -273,14 +305,13 @@ cudaError_t autotune(int N, const double* tables, int* variant, double* us_per_e
     chk(cudaMalloc(&p, E * n3 * 3 * 8));
     chk(cudaMalloc(&a, E * n3 * 9 * 8));
     chk(cudaMalloc(&f, E * (size_t)N * N * 54 * 8));
-    chk(cudaMalloc(&d_set, sizeof(SetDev)));
     chk(cudaMalloc(&d_counter, sizeof(unsigned int)));
     chk(cudaMalloc(&d_units, sizeof(UnitDev) * (size_t)E));
     size_t scr = 0;
     for (int v = 0; v < kMaxVariants; ++v)
       if (shapes().s[N][v].valid) scr = std::max(scr, shapes().s[N][v].scratch);
     double* scratch = nullptr;
-    if (scr) chk(cudaMalloc(&scratch, scr * (size_t)sms));
+    if (scr) chk(cudaMalloc(&scratch, scr * (size_t)sms * 4));  // up to 4 CTAs of 512 threads per SM
     chk(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
     chk(cudaEventCreate(&e0));
     chk(cudaEventCreate(&e1));
@@ -293,17 +324,21 @@ cudaError_t autotune(int N, const double* tables, int* variant, double* us_per_e
     for (int v = 0; v < kMaxVariants && err == cudaSuccess; ++v) {
       const ShapeInfo& si = shapes().s[N][v];
       if (!si.valid) continue;
-      SetDev sd{q, p, a, f, tables, E, N, v, nullptr, 0.0};
+      SetTable tb{};
+      tb.sets[0] = SetDev{q, p, a, f, tables, E, N, v, nullptr, 0.0};
       std::vector<UnitDev> units;
       for (int64_t e = 0; e < E; e += si.epc) units.push_back(UnitDev{e, 0, 0});
-      chk(cudaMemcpyAsync(d_set, &sd, sizeof(sd), cudaMemcpyHostToDevice, st));
       chk(cudaMemcpyAsync(d_units, units.data(), sizeof(UnitDev) * units.size(),
                           cudaMemcpyHostToDevice, st));
       float ms_best = 1e30f;
-      chk(raise_smem_limit(si.smem));
+      const OrderKernel k = cart_kernel(N, v);
+      int per_sm = 1;
+      chk(prepare_kernel(k, si.smem, &per_sm));
+      const int ctas = (int)std::min<int64_t>((int64_t)per_sm * sms, (int64_t)units.size());
       for (int rep = 0; rep < 4 && err == cudaSuccess; ++rep) {
+        chk(cudaMemsetAsync(d_counter, 0, sizeof(unsigned int), st));
         chk(cudaEventRecord(e0, st));
-        chk(launch_batch(d_set, d_units, (int)units.size(), d_counter, scratch, scr, si.smem, sms,
+        chk(launch_order(k, tb, d_units, (int)units.size(), d_counter, scratch, scr, si.smem, ctas,
                          st));
         chk(cudaEventRecord(e1, st));
         chk(cudaEventSynchronize(e1));
@@ -317,7 +352,7 @@ cudaError_t autotune(int N, const double* tables, int* variant, double* us_per_e
     }
     if (st) cudaStreamSynchronize(st);
     cudaFree(q); cudaFree(p); cudaFree(a); cudaFree(f);
-    cudaFree(d_set); cudaFree(d_units); cudaFree(d_counter); cudaFree(scratch);
+    cudaFree(d_units); cudaFree(d_counter); cudaFree(scratch);
     if (e0) cudaEventDestroy(e0);
     if (e1) cudaEventDestroy(e1);
     if (st) cudaStreamDestroy(st);
@@ -332,15 +367,27 @@ cudaError_t autotune(int N, const double* tables, int* variant, double* us_per_e
 
 // ---- plans ------------------------------------------------------------------
 
+// One persistent launch: up to kParamSets sets of one shape (one order,
+// Cartesian shape v or curvilinear) over work-list entries [begin, begin + count).
+struct Launch {
+  OrderKernel kernel = nullptr;
+  SetTable table{};
+  int nsets = 0;
+  size_t smem = 0, scratch_per_cta = 0, scratch_off = 0;  // scratch_off in doubles
+  int64_t begin = 0, count = 0;
+  double cost = 0.0;  // estimated us of the whole launch
+  int ctas = 0, branch = 0;
+};
+
+constexpr int kMaxBranches = 4;
+
 struct BatchPlan {
   int device = -1;
   int nsets = 0, nunits = 0, ctas = 0;
   size_t smem = 0;
-  SetDev* d_sets = nullptr;
   UnitDev* d_units = nullptr;
-  unsigned int* d_counter = nullptr;
-  double* d_scratch = nullptr;  // parked new terms of the large-N shapes, per CTA
-  size_t scratch_per_cta = 0;
+  unsigned int* d_counter = nullptr;  // one per launch
+  double* d_scratch = nullptr;        // parked new terms of the large-N shapes, per CTA
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
 };
@@ -349,14 +396,19 @@ void destroy_plan(BatchPlan* p) {
   if (!p) return;
   if (p->exec) cudaGraphExecDestroy(p->exec);
   if (p->graph) cudaGraphDestroy(p->graph);
-  cudaFree(p->d_sets);
   cudaFree(p->d_units);
   cudaFree(p->d_counter);
+  cudaFree(p->d_scratch);
   delete p;
 }
 
-// Builds the work list (cost-sorted), uploads it and captures counter reset +
-// persistent kernel into a CUDA graph. sets[i].variant < 0 = autotuned.
+// Groups the sets by shape (at most kParamSets per launch), uploads the work
+// list and captures into a CUDA graph the counters' reset and one persistent
+// launch per group, spread over up to kMaxBranches parallel branches (longest
+// first, each to the branch with the least estimated work). Launches on
+// different branches run concurrently: one shape's CTAs take the SMs that
+// another's finished CTAs free, so no SM waits out a shape's tail.
+// forced_variant[i] < 0 = autotuned.
 cudaError_t create_plan(int nsets, const int* N, const int64_t* E, const double* const* q,
                         const double* const* params, double* const* avg, double* const* faces,
                         const double* const* tables, const int* forced_variant, BatchPlan** out,
@@ -366,77 +418,144 @@ cudaError_t create_plan(int nsets, const int* N, const int64_t* E, const double*
   if (!p) return cudaErrorMemoryAllocation;
   cudaGetDevice(&p->device);
   std::vector<SetDev> sets((size_t)nsets);
-  std::vector<double> cost((size_t)nsets);
+  std::vector<double> unit_cost((size_t)nsets);
+  std::vector<int> epc((size_t)nsets, 1);
+  std::vector<OrderKernel> kern((size_t)nsets, nullptr);
+  std::vector<size_t> smem((size_t)nsets, 0), scratch((size_t)nsets, 0);
   cudaError_t err = cudaSuccess;
   for (int i = 0; i < nsets && err == cudaSuccess; ++i) {
-    if (metrics && metrics[i]) {  // curvilinear: one element per unit, cost by the FP64 estimate
-      if (N[i] < 1 || N[i] > kMaxNodes) { err = cudaErrorInvalidValue; break; }
-      const double F = 36.0 * std::pow(N[i], 5) + 66.0 * std::pow(N[i], 4) + 108.0 * std::pow(N[i], 3);
+    if (N[i] < 1 || N[i] > kMaxNodes) { err = cudaErrorInvalidValue; break; }
+    const double F = 36.0 * std::pow(N[i], 5) + 66.0 * std::pow(N[i], 4) + 108.0 * std::pow(N[i], 3);
+    if (metrics && metrics[i]) {  // curvilinear: one element per unit
       sets[i] = SetDev{q[i], params[i], avg[i], faces[i], tables[i], E[i], N[i], 0, metrics[i],
                        dx ? dx[i] : 1.0};
-      cost[i] = 1.7 * F / 1.2e6;  // every quantity along every direction
-      p->smem = std::max(p->smem, curv_batch_smem(N[i]));
+      unit_cost[i] = 1.7 * F / 1.2e6;  // every quantity along every direction
+      kern[i] = curv_kernel(N[i]);
+      smem[i] = curv_batch_smem(N[i]);
       continue;
     }
     int v = forced_variant ? forced_variant[i] : -1;
     double us = 0.0;
-    if (v < 0) {
-      err = autotune(N[i], tables[i], &v, &us, nullptr);
-    } else {
-      const double F = 36.0 * std::pow(N[i], 5) + 66.0 * std::pow(N[i], 4) + 108.0 * std::pow(N[i], 3);
-      us = F / 1.2e6;  // FP64-bound estimate
-    }
+    if (v < 0) err = autotune(N[i], tables[i], &v, &us, nullptr);
+    else us = F / 1.2e6;  // FP64-bound estimate
     if (err != cudaSuccess) break;
     if (v < 0 || v >= kMaxVariants || !shapes().s[N[i]][v].valid) { err = cudaErrorInvalidValue; break; }
+    const ShapeInfo& si = shapes().s[N[i]][v];
     sets[i] = SetDev{q[i], params[i], avg[i], faces[i], tables[i], E[i], N[i], v, nullptr, 0.0};
-    cost[i] = us * shapes().s[N[i]][v].epc;
-    p->smem = std::max(p->smem, shapes().s[N[i]][v].smem);
-    p->scratch_per_cta = std::max(p->scratch_per_cta, shapes().s[N[i]][v].scratch);
+    epc[i] = si.epc;
+    unit_cost[i] = us * si.epc;
+    kern[i] = cart_kernel(N[i], v);
+    smem[i] = si.smem;
+    scratch[i] = si.scratch;
   }
+  for (int i = 0; i < nsets && err == cudaSuccess; ++i)
+    if (!kern[i]) err = cudaErrorInvalidValue;
+  // launches: the sets of each shape, kParamSets at a time, in set order
+  std::vector<Launch> launches;
+  if (err == cudaSuccess) {
+    std::vector<char> done((size_t)nsets, 0);
+    for (int i = 0; i < nsets; ++i) {
+      if (done[i] || E[i] == 0) continue;
+      Launch* l = nullptr;
+      for (int j = i; j < nsets; ++j) {
+        if (done[j] || E[j] == 0 || kern[j] != kern[i]) continue;
+        if (!l || l->nsets == kParamSets) {
+          launches.emplace_back();
+          l = &launches.back();
+          l->kernel = kern[i];
+          l->smem = smem[i];
+          l->scratch_per_cta = scratch[i];
+        }
+        l->table.sets[l->nsets++] = sets[j];
+        l->cost += unit_cost[j] * (double)((E[j] + epc[j] - 1) / epc[j]);
+        done[j] = 1;
+      }
+    }
+  }
+  // work list: launches longest first; within one, units by set, then element
   std::vector<UnitDev> units;
   if (err == cudaSuccess) {
-    std::vector<int> order((size_t)nsets);
-    for (int i = 0; i < nsets; ++i) order[i] = i;
-    // longest units first; within a set, element order
-    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return cost[a] > cost[b]; });
-    for (int i : order) {
-      const int epc = sets[i].metric ? 1 : shapes().s[sets[i].N][sets[i].variant].epc;
-      for (int64_t e = 0; e < sets[i].E; e += epc) units.push_back(UnitDev{e, i, 0});
+    std::stable_sort(launches.begin(), launches.end(),
+                     [](const Launch& a, const Launch& b) { return a.cost > b.cost; });
+    for (Launch& l : launches) {
+      l.begin = (int64_t)units.size();
+      for (int k = 0; k < l.nsets; ++k) {
+        const SetDev& sd = l.table.sets[k];
+        const int step = sd.metric ? 1 : shapes().s[sd.N][sd.variant].epc;
+        for (int64_t e = 0; e < sd.E; e += step) units.push_back(UnitDev{e, k, 0});
+      }
+      l.count = (int64_t)units.size() - l.begin;
     }
     if (units.size() > 0x7fffffffu) err = cudaErrorInvalidValue;
   }
+  // grids, branches, scratch
+  size_t scratch_doubles = 0;
+  if (err == cudaSuccess) {
+    const int sms = sm_count();
+    double load[kMaxBranches] = {0.0};
+    const int nb = std::min<int>(kMaxBranches, (int)std::max<size_t>(1, launches.size()));
+    for (Launch& l : launches) {
+      int per_sm = 1;
+      if ((err = prepare_kernel(l.kernel, l.smem, &per_sm)) != cudaSuccess) break;
+      l.ctas = (int)std::min<int64_t>((int64_t)per_sm * sms, l.count);
+      l.branch = (int)(std::min_element(load, load + nb) - load);
+      load[l.branch] += l.cost;
+      l.scratch_off = scratch_doubles;
+      scratch_doubles += l.scratch_per_cta / sizeof(double) * (size_t)l.ctas;
+      p->ctas += l.ctas;
+      p->smem = std::max(p->smem, l.smem);
+    }
+  }
   p->nsets = nsets;
   p->nunits = (int)units.size();
-  cudaStream_t st = nullptr;
-  if (err == cudaSuccess) err = cudaMalloc(&p->d_sets, sizeof(SetDev) * std::max(1, nsets));
   if (err == cudaSuccess) err = cudaMalloc(&p->d_units, sizeof(UnitDev) * std::max<size_t>(1, units.size()));
-  if (err == cudaSuccess) err = cudaMalloc(&p->d_counter, sizeof(unsigned int));
-  if (err == cudaSuccess && nsets > 0)
-    err = cudaMemcpy(p->d_sets, sets.data(), sizeof(SetDev) * nsets, cudaMemcpyHostToDevice);
+  if (err == cudaSuccess)
+    err = cudaMalloc(&p->d_counter, sizeof(unsigned int) * std::max<size_t>(1, launches.size()));
+  if (err == cudaSuccess && scratch_doubles)
+    err = cudaMalloc(&p->d_scratch, sizeof(double) * scratch_doubles);
   if (err == cudaSuccess && !units.empty())
     err = cudaMemcpy(p->d_units, units.data(), sizeof(UnitDev) * units.size(), cudaMemcpyHostToDevice);
-  if (err == cudaSuccess) {
-    int per_sm = 0;
-    err = raise_smem_limit(p->smem);
-    if (err == cudaSuccess)
-      err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_kernel, kBatchThreads,
-                                                          std::max<size_t>(p->smem, 1));
-    p->ctas = std::max(1, per_sm) * sm_count();
-    if (p->nunits > 0 && p->ctas > p->nunits) p->ctas = p->nunits;
-  }
-  if (err == cudaSuccess && p->scratch_per_cta)
-    err = cudaMalloc(&p->d_scratch, p->scratch_per_cta * (size_t)p->ctas);
+  // capture: reset, fork, one launch per group on its branch, join
+  cudaStream_t st = nullptr;
+  cudaStream_t br[kMaxBranches] = {nullptr};
+  cudaEvent_t fork = nullptr, join[kMaxBranches] = {nullptr};
   if (err == cudaSuccess) err = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+  for (int b = 0; b < kMaxBranches && err == cudaSuccess; ++b) {
+    err = cudaStreamCreateWithFlags(&br[b], cudaStreamNonBlocking);
+    if (err == cudaSuccess) err = cudaEventCreateWithFlags(&join[b], cudaEventDisableTiming);
+  }
+  if (err == cudaSuccess) err = cudaEventCreateWithFlags(&fork, cudaEventDisableTiming);
   if (err == cudaSuccess) err = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal);
   if (err == cudaSuccess) {
     cudaError_t le = cudaSuccess;
-    if (p->nunits > 0)
-      le = launch_batch(p->d_sets, p->d_units, p->nunits, p->d_counter, p->d_scratch,
-                        p->scratch_per_cta, std::max<size_t>(p->smem, 1), p->ctas, st);
+    if (!launches.empty()) {
+      le = cudaMemsetAsync(p->d_counter, 0, sizeof(unsigned int) * launches.size(), st);
+      if (le == cudaSuccess) le = cudaEventRecord(fork, st);
+      bool used[kMaxBranches] = {false};
+      for (const Launch& l : launches) used[l.branch] = true;
+      for (int b = 0; b < kMaxBranches && le == cudaSuccess; ++b)
+        if (used[b]) le = cudaStreamWaitEvent(br[b], fork, 0);
+      for (size_t li = 0; li < launches.size() && le == cudaSuccess; ++li) {
+        const Launch& l = launches[li];
+        le = launch_order(l.kernel, l.table, p->d_units + l.begin, (int)l.count, p->d_counter + li,
+                          p->d_scratch ? p->d_scratch + l.scratch_off : nullptr, l.scratch_per_cta,
+                          l.smem, l.ctas, br[l.branch]);
+      }
+      for (int b = 0; b < kMaxBranches && le == cudaSuccess; ++b)
+        if (used[b]) {
+          le = cudaEventRecord(join[b], br[b]);
+          if (le == cudaSuccess) le = cudaStreamWaitEvent(st, join[b], 0);
+        }
+    }
     err = cudaStreamEndCapture(st, &p->graph);
     if (le != cudaSuccess) err = le;
   }
   if (err == cudaSuccess) err = cudaGraphInstantiate(&p->exec, p->graph, 0);
+  if (fork) cudaEventDestroy(fork);
+  for (int b = 0; b < kMaxBranches; ++b) {
+    if (join[b]) cudaEventDestroy(join[b]);
+    if (br[b]) cudaStreamDestroy(br[b]);
+  }
   if (st) cudaStreamDestroy(st);
   if (err != cudaSuccess) {
     cudaGetLastError();

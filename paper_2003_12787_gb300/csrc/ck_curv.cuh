@@ -57,16 +57,16 @@ __device__ __forceinline__ void curv_add(int s, double a, double g0, double g1, 
 // like the step tables' derivatives).
 __device__ __forceinline__ void curv_pointwise(const double part[9], double invrho, double lam,
                                                double mu, double mu2, double r[9]) {
-  const double ltr = lam * ((part[kS11] + part[kS22]) + part[kS33]);
-  r[kV1] = invrho * part[kV1];
-  r[kV2] = invrho * part[kV2];
-  r[kV3] = invrho * part[kV3];
+  const double ltr = __dmul_rn(lam, (part[kS11] + part[kS22]) + part[kS33]);
+  r[kV1] = __dmul_rn(invrho, part[kV1]);
+  r[kV2] = __dmul_rn(invrho, part[kV2]);
+  r[kV3] = __dmul_rn(invrho, part[kV3]);
   r[kS11] = fma(mu2, part[kS11], ltr);
   r[kS22] = fma(mu2, part[kS22], ltr);
   r[kS33] = fma(mu2, part[kS33], ltr);
-  r[kS12] = mu * part[kS12];
-  r[kS13] = mu * part[kS13];
-  r[kS23] = mu * part[kS23];
+  r[kS12] = __dmul_rn(mu, part[kS12]);
+  r[kS13] = __dmul_rn(mu, part[kS13]);
+  r[kS23] = __dmul_rn(mu, part[kS23]);
 }
 
 // One curvilinear CK step at node (x, y, z) straight from shared memory:

@@ -60,16 +60,18 @@ __device__ __forceinline__ void ck_node_fp64(const double* __restrict__ p,
     s23 = fma(d, pz[kV2 * S + o], s23);
     c = fma(d, pz[kV3 * S + o], c);
   }
-  const double ltr = lam * ((a + b) + c);
-  r[kV1] = invrho * v1;
-  r[kV2] = invrho * v2;
-  r[kV3] = invrho * v3;
+  // products rounded on their own: no kernel that inlines this step may fuse
+  // them into its later additions, so every FP64 path gives the same bits
+  const double ltr = __dmul_rn(lam, (a + b) + c);
+  r[kV1] = __dmul_rn(invrho, v1);
+  r[kV2] = __dmul_rn(invrho, v2);
+  r[kV3] = __dmul_rn(invrho, v3);
   r[kS11] = fma(mu2, a, ltr);
   r[kS22] = fma(mu2, b, ltr);
   r[kS33] = fma(mu2, c, ltr);
-  r[kS12] = mu * s12;
-  r[kS13] = mu * s13;
-  r[kS23] = mu * s23;
+  r[kS12] = __dmul_rn(mu, s12);
+  r[kS13] = __dmul_rn(mu, s13);
+  r[kS23] = __dmul_rn(mu, s23);
 }
 
 // Lame coefficients of one node from (rho, cp, cs): 1/rho, lambda, mu, 2 mu.

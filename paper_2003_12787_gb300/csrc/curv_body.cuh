@@ -239,17 +239,17 @@ __device__ __forceinline__ void curv_element(double* smem, const double* __restr
         invrho = cf[j][0]; lam = cf[j][1]; mu = cf[j][2]; mu2 = cf[j][3];
       }
       const double* pj = part[j];
-      const double ltr = lam * ((pj[kS11] + pj[kS22]) + pj[kS33]);
+      const double ltr = __dmul_rn(lam, (pj[kS11] + pj[kS22]) + pj[kS33]);
       double r[9];
-      r[kV1] = invrho * pj[kV1];
-      r[kV2] = invrho * pj[kV2];
-      r[kV3] = invrho * pj[kV3];
+      r[kV1] = __dmul_rn(invrho, pj[kV1]);
+      r[kV2] = __dmul_rn(invrho, pj[kV2]);
+      r[kV3] = __dmul_rn(invrho, pj[kV3]);
       r[kS11] = fma(mu2, pj[kS11], ltr);
       r[kS22] = fma(mu2, pj[kS22], ltr);
       r[kS33] = fma(mu2, pj[kS33], ltr);
-      r[kS12] = mu * pj[kS12];
-      r[kS13] = mu * pj[kS13];
-      r[kS23] = mu * pj[kS23];
+      r[kS12] = __dmul_rn(mu, pj[kS12]);
+      r[kS13] = __dmul_rn(mu, pj[kS13]);
+      r[kS23] = __dmul_rn(mu, pj[kS23]);
 #pragma unroll
       for (int s = 0; s < M; ++s) {
         if constexpr (LEAN) {

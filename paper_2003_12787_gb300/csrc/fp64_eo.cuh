@@ -196,17 +196,17 @@ __device__ __forceinline__ void fp64_element_eo(double* smem, const double* __re
 #pragma unroll
       for (int c = 0; c < 9; ++c) g[c] = sacc[c * S + pn];
       const double invrho = cf[j][0], lam = cf[j][1], mu = cf[j][2], mu2 = cf[j][3];
-      const double ltr = lam * ((g[6] + g[7]) + g[8]);
+      const double ltr = __dmul_rn(lam, (g[6] + g[7]) + g[8]);
       double r[9];
-      r[kV1] = invrho * g[0];
-      r[kV2] = invrho * g[1];
-      r[kV3] = invrho * g[2];
+      r[kV1] = __dmul_rn(invrho, g[0]);
+      r[kV2] = __dmul_rn(invrho, g[1]);
+      r[kV3] = __dmul_rn(invrho, g[2]);
       r[kS11] = fma(mu2, g[6], ltr);
       r[kS22] = fma(mu2, g[7], ltr);
       r[kS33] = fma(mu2, g[8], ltr);
-      r[kS12] = mu * g[3];
-      r[kS13] = mu * g[4];
-      r[kS23] = mu * g[5];
+      r[kS12] = __dmul_rn(mu, g[3]);
+      r[kS13] = __dmul_rn(mu, g[4]);
+      r[kS23] = __dmul_rn(mu, g[5]);
 #pragma unroll
       for (int s = 0; s < 9; ++s) {
         avg[j][s] += r[s];
@@ -432,17 +432,17 @@ __device__ __forceinline__ void fp64_element_eo_slots(double* smem, const double
 #pragma unroll
       for (int c = 0; c < 9; ++c) g[c] = slot[ac[c] * S + n];
       const double invrho = cf[j][0], lam = cf[j][1], mu = cf[j][2], mu2 = cf[j][3];
-      const double ltr = lam * ((g[6] + g[7]) + g[8]);
+      const double ltr = __dmul_rn(lam, (g[6] + g[7]) + g[8]);
       double r[9];
-      r[kV1] = invrho * g[0];
-      r[kV2] = invrho * g[1];
-      r[kV3] = invrho * g[2];
+      r[kV1] = __dmul_rn(invrho, g[0]);
+      r[kV2] = __dmul_rn(invrho, g[1]);
+      r[kV3] = __dmul_rn(invrho, g[2]);
       r[kS11] = fma(mu2, g[6], ltr);
       r[kS22] = fma(mu2, g[7], ltr);
       r[kS33] = fma(mu2, g[8], ltr);
-      r[kS12] = mu * g[3];
-      r[kS13] = mu * g[4];
-      r[kS23] = mu * g[5];
+      r[kS12] = __dmul_rn(mu, g[3]);
+      r[kS13] = __dmul_rn(mu, g[4]);
+      r[kS23] = __dmul_rn(mu, g[5]);
 #pragma unroll
       for (int s = 0; s < 9; ++s) {
         gavg[n * M + s] += r[s];
