@@ -46,7 +46,7 @@ static __device__ __align__(256) unsigned char g_static_scratch[kStaticScratchBy
 // FP64 path. N = 12 keeps the per-node body here, which parks its new terms in
 // the scratch array; at N = 12 this path (and the served one, which launches
 // this kernel) therefore agrees with stp_predict to rounding, not bit for bit.
-#define STP_STATIC_EO(X) X(7, 343) X(8, 384) X(9, 486) X(10, 500) X(11, 444)
+#define STP_STATIC_EO(X) X(7, 343) X(8, 384) X(9, 512) X(10, 512) X(11, 512)
 
 struct StaticSet {
   const double* q;
