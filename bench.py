@@ -430,7 +430,7 @@ def small_case_latency(stp, torch, args):
 
 def batched_measurement(stp, torch, args):
     """The batched workload (64 sets, orders 3-11, 64-16384 elements each,
-    seed 1003) as one persistent launch replayed from a CUDA graph: time per
+    seed 1003) as one persistent launch per shape, replayed from a CUDA graph: time per
     replay (CUDA events, mean of args.batch_steps after one warm-up), element
     throughput, algorithmic FP64 rate, and the autotuner's choice per order."""
     from paper_2003_12787_gb300.inputs import batched_sets_recipe, elastic_problem
@@ -495,7 +495,7 @@ def batched_measurement(stp, torch, args):
         stp.stp_set_precision(P.handle, "fp64")
     out = {"workload": "64 element sets, orders 3-11 (N=4..12), "
                        f"64-{args.batched_emax} elements each "
-                       "(log-uniform, seed 1003), one persistent launch from a CUDA graph",
+                       "(log-uniform, seed 1003), one persistent launch per shape from a CUDA graph",
            "sets": len(recipe), "elements": elems, "ms_per_launch": ms,
            "elements_per_s": elems / (ms / 1e3), "tflops_algorithmic": flops / (ms / 1e3) / 1e12,
            "frac_fp64_peak": flops / (ms / 1e3) / 1e12 / FP64_PEAK_TFLOPS,

@@ -331,16 +331,18 @@ stp_status stp_device_status(stp_handle h, void* stream, unsigned int* flags);
 stp_status stp_selftest_bounded_wait(stp_handle h, int polls, void* stream);
 
 /*
- * Batched persistent launch: the STPs of several element sets, of different
- * orders and sizes, in ONE persistent kernel launch replayed from a CUDA
- * graph. Each set is described by a handle (order, dx, dt, precision) and its own
- * device buffers in the layouts above. The paper generates one kernel per
- * order (Sec. II-D, Sec. III); here, for FP64 sets, every order's
- * element-group body lives in one kernel and a cost-sorted work list of
- * (set, element range) units is consumed by one CTA per SM; curvilinear FP64
- * sets (stp_batch_create_curvilinear) are units of the same launch, one
- * element each. Batches with other precisions replay a graph of per-set
- * launches instead.
+ * Batched persistent launches: the STPs of several element sets, of
+ * different orders and sizes, replayed from one CUDA graph. Each set is
+ * described by a handle (order, dx, dt, precision) and its own device buffers
+ * in the layouts above. The paper generates one kernel per order (Sec. II-D,
+ * Sec. III); here, for FP64 sets, every shape (order and layout) has one
+ * persistent kernel whose CTAs, one per SM, consume its sets' (set, element
+ * range) units; a plan launches one such kernel per shape present (128 sets
+ * at most per launch), over parallel graph branches so that shapes share the
+ * SMs as their work runs out. Curvilinear FP64 sets
+ * (stp_batch_create_curvilinear) are one-element units of the curvilinear
+ * shape of their order. Batches with other precisions replay a graph of
+ * per-set launches instead.
  */
 typedef struct {
   stp_handle handle;   /* predictor of this set (FP64 for the allocation-free path) */
@@ -355,9 +357,9 @@ typedef struct stp_batch_s* stp_batch; /* opaque plan, owned by the library */
 
 /*
  * Plan a batch. When every handle is FP64: autotunes (on first use of each
- * order on the device, then cached) the per-order shape of the persistent
- * kernel, builds and uploads the work list, and captures counter reset +
- * kernel into a CUDA graph. When some handle has another precision: captures
+ * order on the device, then cached) the per-order shape, builds and uploads
+ * the work list, and captures the counters' reset and the per-shape
+ * persistent launches into a CUDA graph. When some handle has another precision: captures
  * one launch per set (each set's own kernel, in its handle's precision at
  * planning time) into a CUDA graph, largest sets first, over up to 8 parallel
  * branches; results equal stp_predict's for every set. The buffers are baked
@@ -408,8 +410,9 @@ stp_status stp_batch_create_sources(int nsets, const stp_batch_set* sets,
 /* Enqueue one replay of the plan's graph on `stream` (async). */
 stp_status stp_batch_launch(stp_batch b, void* stream);
 
-/* Work units, CTAs of the persistent grid and dynamic shared memory per CTA
- * (for a batch of per-set launches: the number of sets, 0, 0). */
+/* Work units, CTAs over the plan's persistent launches and the largest
+ * dynamic shared memory per CTA among them (for a batch of per-set launches:
+ * the number of sets, 0, 0). */
 stp_status stp_batch_info(stp_batch b, int* units, int* ctas, int64_t* smem_bytes);
 
 /* Free the plan (after the work it enqueued has finished). NULL is a no-op. */
