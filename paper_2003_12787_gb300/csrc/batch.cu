@@ -39,16 +39,20 @@ constexpr int kBatchThreads = 512;
 
 constexpr int kMaxVariants = 2;
 
-// Even-odd candidates: (N, index, threads doing the work); N = 12 uses the
-// slot-reusing variant (p and accumulators share 16 arrays).
-#define STP_BATCH_EO(X) X(7, 0, 343) X(7, 1, 512) X(8, 0, 384) X(8, 1, 512) X(9, 0, 486) \
-  X(9, 1, 512) X(10, 0, 500) X(10, 1, 512) X(11, 0, 444) X(11, 1, 512)
+// Even-odd candidates: (N, index, threads, threads doing the work, CTAs per
+// SM); shape 0 of N = 7, 8 is the single-set kernel's (two CTAs per SM).
+// N = 12 uses the slot-reusing variant (p and accumulators share 16 arrays),
+// in 512-thread CTAs.
+#define STP_BATCH_EO(X) X(7, 0, 352, 343, 2) X(7, 1, 512, 512, 1) X(8, 0, 192, 192, 2) \
+  X(8, 1, 512, 512, 1) X(9, 0, 512, 486, 1) X(9, 1, 512, 512, 1) X(10, 0, 512, 500, 1)  \
+  X(10, 1, 512, 512, 1) X(11, 0, 512, 444, 1) X(11, 1, 512, 512, 1)
 #define STP_BATCH_EO_SLOTS(X) X(12, 0, 432) X(12, 1, 512)
 
 struct ShapeInfo {
   int valid = 0, epc = 1;
   size_t smem = 0;
   size_t scratch = 0;  // bytes of global scratch per CTA (parked new terms)
+  int threads = kBatchThreads;
 };
 
 // host-side table of the candidate shapes
@@ -60,7 +64,7 @@ struct ShapeTable {
                       rg ? sizeof(double) * 9 * (size_t)Fp64Shape<n, npt, epc, avg>::S * epc : 0};
     STP_BATCH_SHAPES(X)
 #undef X
-#define X(n, v, use) s[n][v] = ShapeInfo{1, 1, EoShape<n>::SMEM, 0};
+#define X(n, v, nt, use, minb) s[n][v] = ShapeInfo{1, 1, EoShape<n>::SMEM, 0, nt};
     STP_BATCH_EO(X)
 #undef X
 #define X(n, v, use) s[n][v] = ShapeInfo{1, 1, EoSlotShape<n>::SMEM, 0};
@@ -119,6 +123,7 @@ struct SetTable {
 // registers and spilled the large-N ones).
 template <int N, int NPT, int EPC, bool AVG, bool RG>
 struct GroupUnit {
+  static constexpr int NT = kBatchThreads, MINB = 1;
   static __device__ __forceinline__ void run(double* smem, const SetDev& sd, int64_t e0,
                                              double* rbuf) {
     fp64_group<N, NPT, EPC, AVG, kBatchThreads, RG>(smem, sd.q, sd.params, sd.avg, sd.faces,
@@ -126,16 +131,18 @@ struct GroupUnit {
   }
 };
 
-template <int N, int USE>
+template <int N, int THREADS, int USE, int BLOCKS_PER_SM>
 struct EoUnit {
+  static constexpr int NT = THREADS, MINB = BLOCKS_PER_SM;
   static __device__ __forceinline__ void run(double* smem, const SetDev& sd, int64_t e0, double*) {
     if (e0 < sd.E)
-      fp64_element_eo<N, kBatchThreads, USE>(smem, sd.q, sd.params, sd.avg, sd.faces, sd.tables, e0);
+      fp64_element_eo<N, THREADS, USE>(smem, sd.q, sd.params, sd.avg, sd.faces, sd.tables, e0);
   }
 };
 
 template <int N, int USE>
 struct EoSlotsUnit {
+  static constexpr int NT = kBatchThreads, MINB = 1;
   static __device__ __forceinline__ void run(double* smem, const SetDev& sd, int64_t e0, double*) {
     if (e0 < sd.E)
       fp64_element_eo_slots<N, kBatchThreads, USE>(smem, sd.q, sd.params, sd.avg, sd.faces,
@@ -145,6 +152,7 @@ struct EoSlotsUnit {
 
 template <int N, int NODES, int A, bool LEAN>
 struct CurvUnit {
+  static constexpr int NT = kBatchThreads, MINB = 1;
   static __device__ __forceinline__ void run(double* smem, const SetDev& sd, int64_t e0, double*) {
     if (e0 < sd.E)
       curv_element<N, kBatchThreads, NODES, A, LEAN, false, false>(
@@ -156,7 +164,7 @@ struct CurvUnit {
 // (units of up to kParamSets sets of that shape; UnitDev::set indexes tb)
 // through an atomic counter until the list is exhausted.
 template <class Unit>
-__global__ void __launch_bounds__(kBatchThreads, 1)
+__global__ void __launch_bounds__(Unit::NT, Unit::MINB)
 order_kernel(const __grid_constant__ SetTable tb, const UnitDev* __restrict__ units, int nunits,
              unsigned int* __restrict__ counter, double* __restrict__ scratch,
              int64_t scratch_doubles_per_cta) {
@@ -183,8 +191,8 @@ OrderKernel cart_kernel(int N, int v) {
   case n_ * kMaxVariants + v_: return order_kernel<GroupUnit<n_, npt_, epc_, avgsm_, rg_>>;
     STP_BATCH_SHAPES(X)
 #undef X
-#define X(n_, v_, use_) \
-  case n_ * kMaxVariants + v_: return order_kernel<EoUnit<n_, use_>>;
+#define X(n_, v_, nt_, use_, minb_) \
+  case n_ * kMaxVariants + v_: return order_kernel<EoUnit<n_, nt_, use_, minb_>>;
     STP_BATCH_EO(X)
 #undef X
 #define X(n_, v_, use_) \
@@ -233,20 +241,20 @@ int sm_count() {
 // (stream operations only, so it can be captured into a graph); the caller
 // resets the counter and has raised the kernel's dynamic shared-memory limit
 // to at least smem (prepare_kernel).
-cudaError_t launch_order(OrderKernel k, const SetTable& tb, const UnitDev* d_units, int nunits,
-                         unsigned int* d_counter, double* scratch, size_t scratch_per_cta,
-                         size_t smem, int ctas, cudaStream_t st) {
-  k<<<ctas, kBatchThreads, std::max<size_t>(smem, 1), st>>>(
+cudaError_t launch_order(OrderKernel k, int threads, const SetTable& tb, const UnitDev* d_units,
+                         int nunits, unsigned int* d_counter, double* scratch,
+                         size_t scratch_per_cta, size_t smem, int ctas, cudaStream_t st) {
+  k<<<ctas, threads, std::max<size_t>(smem, 1), st>>>(
       tb, d_units, nunits, d_counter, scratch, (int64_t)(scratch_per_cta / sizeof(double)));
   return cudaGetLastError();
 }
 
 // Raises kernel k's shared-memory limit to smem; *per_sm = its CTAs per SM.
-cudaError_t prepare_kernel(OrderKernel k, size_t smem, int* per_sm) {
+cudaError_t prepare_kernel(OrderKernel k, int threads, size_t smem, int* per_sm) {
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)std::max<size_t>(smem, 1));
   if (e == cudaSuccess)
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, k, kBatchThreads,
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, k, threads,
                                                       std::max<size_t>(smem, 1));
   if (e == cudaSuccess && *per_sm < 1) e = cudaErrorInvalidConfiguration;
   return e;
@@ -333,13 +341,13 @@ cudaError_t autotune(int N, const double* tables, int* variant, double* us_per_e
       float ms_best = 1e30f;
       const OrderKernel k = cart_kernel(N, v);
       int per_sm = 1;
-      chk(prepare_kernel(k, si.smem, &per_sm));
+      chk(prepare_kernel(k, si.threads, si.smem, &per_sm));
       const int ctas = (int)std::min<int64_t>((int64_t)per_sm * sms, (int64_t)units.size());
       for (int rep = 0; rep < 4 && err == cudaSuccess; ++rep) {
         chk(cudaMemsetAsync(d_counter, 0, sizeof(unsigned int), st));
         chk(cudaEventRecord(e0, st));
-        chk(launch_order(k, tb, d_units, (int)units.size(), d_counter, scratch, scr, si.smem, ctas,
-                         st));
+        chk(launch_order(k, si.threads, tb, d_units, (int)units.size(), d_counter, scratch, scr,
+                         si.smem, ctas, st));
         chk(cudaEventRecord(e1, st));
         chk(cudaEventSynchronize(e1));
         float ms = 0.f;
@@ -371,6 +379,7 @@ cudaError_t autotune(int N, const double* tables, int* variant, double* us_per_e
 // Cartesian shape v or curvilinear) over work-list entries [begin, begin + count).
 struct Launch {
   OrderKernel kernel = nullptr;
+  int threads = kBatchThreads;
   SetTable table{};
   int nsets = 0;
   size_t smem = 0, scratch_per_cta = 0, scratch_off = 0;  // scratch_off in doubles
@@ -422,6 +431,7 @@ cudaError_t create_plan(int nsets, const int* N, const int64_t* E, const double*
   std::vector<int> epc((size_t)nsets, 1);
   std::vector<OrderKernel> kern((size_t)nsets, nullptr);
   std::vector<size_t> smem((size_t)nsets, 0), scratch((size_t)nsets, 0);
+  std::vector<int> threads((size_t)nsets, kBatchThreads);
   cudaError_t err = cudaSuccess;
   for (int i = 0; i < nsets && err == cudaSuccess; ++i) {
     if (N[i] < 1 || N[i] > kMaxNodes) { err = cudaErrorInvalidValue; break; }
@@ -447,6 +457,7 @@ cudaError_t create_plan(int nsets, const int* N, const int64_t* E, const double*
     kern[i] = cart_kernel(N[i], v);
     smem[i] = si.smem;
     scratch[i] = si.scratch;
+    threads[i] = si.threads;
   }
   for (int i = 0; i < nsets && err == cudaSuccess; ++i)
     if (!kern[i]) err = cudaErrorInvalidValue;
@@ -463,6 +474,7 @@ cudaError_t create_plan(int nsets, const int* N, const int64_t* E, const double*
           launches.emplace_back();
           l = &launches.back();
           l->kernel = kern[i];
+          l->threads = threads[i];
           l->smem = smem[i];
           l->scratch_per_cta = scratch[i];
         }
@@ -496,7 +508,7 @@ cudaError_t create_plan(int nsets, const int* N, const int64_t* E, const double*
     const int nb = std::min<int>(kMaxBranches, (int)std::max<size_t>(1, launches.size()));
     for (Launch& l : launches) {
       int per_sm = 1;
-      if ((err = prepare_kernel(l.kernel, l.smem, &per_sm)) != cudaSuccess) break;
+      if ((err = prepare_kernel(l.kernel, l.threads, l.smem, &per_sm)) != cudaSuccess) break;
       l.ctas = (int)std::min<int64_t>((int64_t)per_sm * sms, l.count);
       l.branch = (int)(std::min_element(load, load + nb) - load);
       load[l.branch] += l.cost;
@@ -537,7 +549,8 @@ cudaError_t create_plan(int nsets, const int* N, const int64_t* E, const double*
         if (used[b]) le = cudaStreamWaitEvent(br[b], fork, 0);
       for (size_t li = 0; li < launches.size() && le == cudaSuccess; ++li) {
         const Launch& l = launches[li];
-        le = launch_order(l.kernel, l.table, p->d_units + l.begin, (int)l.count, p->d_counter + li,
+        le = launch_order(l.kernel, l.threads, l.table, p->d_units + l.begin, (int)l.count,
+                          p->d_counter + li,
                           p->d_scratch ? p->d_scratch + l.scratch_off : nullptr, l.scratch_per_cta,
                           l.smem, l.ctas, br[l.branch]);
       }
