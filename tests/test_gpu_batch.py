@@ -1,5 +1,5 @@
-"""GPU tests of the batched persistent launch (mixed orders and sizes, one
-kernel launch replayed from a CUDA graph, autotuned shapes).
+"""GPU tests of the batched persistent launches (mixed orders and sizes, one
+persistent kernel per shape replayed from a CUDA graph, autotuned shapes).
 
 Every unit of the batch runs the same per-node FP64 arithmetic as the
 single-set kernel, so batched results must equal single-set results bit for
@@ -163,3 +163,31 @@ def test_batched_workload_64_sets_sampled():
             worst = max(worst, rel(faces[it][:, f].cpu().numpy(), f_ref[:, f]))
     assert worst <= 1e-12, worst
     b.close()
+
+
+def test_more_sets_of_one_shape_than_one_launch_holds():
+    """A launch carries at most 128 set descriptors (a kernel-parameter table):
+    150 sets of one order are split over two launches of the same shape's
+    kernel, beside sets of other orders; every set still equals its
+    single-set call bit for bit, over two replays, and the plan's units
+    cover every element."""
+    specs = [(4, 1 + (i % 5)) for i in range(150)] + [(7, 6), (12, 2), (9, 3)]
+    sets = []
+    for i, (N, E) in enumerate(specs):
+        prob = elastic_problem(N, E=E, seed_material=7000 + i, seed_waves=7500 + i, device="cuda")
+        sets.append((stp.Predictor(N - 1, prob.h, prob.dt), prob))
+    b = stp.Batch([(P, prob.q, prob.params) for P, prob in sets], shapes=[0] * len(specs))
+    info = b.info()
+    # shape 0 of N = 4 holds 8 elements per unit: one unit per set there
+    assert info["units"] == 150 + 6 + 2 + 3
+    b.launch()
+    b.launch()
+    torch.cuda.synchronize()
+    for i, (P, prob) in enumerate(sets):
+        a_b, f_b = b.outputs(i)
+        a_s, f_s = P.predict(prob.q, prob.params)
+        torch.cuda.synchronize()
+        assert torch.equal(a_b, a_s) and torch.equal(f_b, f_s), specs[i]
+    b.close()
+    for P, _ in sets:
+        P.close()
