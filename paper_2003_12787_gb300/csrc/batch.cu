@@ -40,13 +40,13 @@ constexpr int kBatchThreads = 512;
 constexpr int kMaxVariants = 2;
 
 // Even-odd candidates: (N, index, threads, threads doing the work, CTAs per
-// SM); shape 0 of N = 7, 8 is the single-set kernel's (two CTAs per SM).
-// N = 12 uses the slot-reusing variant (p and accumulators share 16 arrays),
-// in 512-thread CTAs.
+// SM); shape 0 of N = 7, 8, 10 is the single-set kernel's (N = 7, 8: two CTAs per SM).
+// N = 12 uses the slot-reusing variant (p and accumulators share 16 arrays):
+// (N, index, threads, threads doing the work).
 #define STP_BATCH_EO(X) X(7, 0, 352, 343, 2) X(7, 1, 512, 512, 1) X(8, 0, 192, 192, 2) \
-  X(8, 1, 512, 512, 1) X(9, 0, 512, 486, 1) X(9, 1, 512, 512, 1) X(10, 0, 512, 500, 1)  \
+  X(8, 1, 512, 512, 1) X(9, 0, 512, 486, 1) X(9, 1, 512, 512, 1) X(10, 0, 640, 640, 1)  \
   X(10, 1, 512, 512, 1) X(11, 0, 512, 444, 1) X(11, 1, 512, 512, 1)
-#define STP_BATCH_EO_SLOTS(X) X(12, 0, 432) X(12, 1, 512)
+#define STP_BATCH_EO_SLOTS(X) X(12, 0, 576, 576) X(12, 1, 512, 512)
 
 struct ShapeInfo {
   int valid = 0, epc = 1;
@@ -67,7 +67,7 @@ struct ShapeTable {
 #define X(n, v, nt, use, minb) s[n][v] = ShapeInfo{1, 1, EoShape<n>::SMEM, 0, nt};
     STP_BATCH_EO(X)
 #undef X
-#define X(n, v, use) s[n][v] = ShapeInfo{1, 1, EoSlotShape<n>::SMEM, 0};
+#define X(n, v, nt, use) s[n][v] = ShapeInfo{1, 1, EoSlotShape<n>::SMEM, 0, nt};
     STP_BATCH_EO_SLOTS(X)
 #undef X
   }
@@ -140,12 +140,12 @@ struct EoUnit {
   }
 };
 
-template <int N, int USE>
+template <int N, int THREADS, int USE>
 struct EoSlotsUnit {
-  static constexpr int NT = kBatchThreads, MINB = 1;
+  static constexpr int NT = THREADS, MINB = 1;
   static __device__ __forceinline__ void run(double* smem, const SetDev& sd, int64_t e0, double*) {
     if (e0 < sd.E)
-      fp64_element_eo_slots<N, kBatchThreads, USE>(smem, sd.q, sd.params, sd.avg, sd.faces,
+      fp64_element_eo_slots<N, THREADS, USE>(smem, sd.q, sd.params, sd.avg, sd.faces,
                                                    sd.tables, e0);
   }
 };
@@ -195,8 +195,8 @@ OrderKernel cart_kernel(int N, int v) {
   case n_ * kMaxVariants + v_: return order_kernel<EoUnit<n_, nt_, use_, minb_>>;
     STP_BATCH_EO(X)
 #undef X
-#define X(n_, v_, use_) \
-  case n_ * kMaxVariants + v_: return order_kernel<EoSlotsUnit<n_, use_>>;
+#define X(n_, v_, nt_, use_) \
+  case n_ * kMaxVariants + v_: return order_kernel<EoSlotsUnit<n_, nt_, use_>>;
     STP_BATCH_EO_SLOTS(X)
 #undef X
     default: return nullptr;

@@ -116,11 +116,13 @@ cudaError_t launch_shape(int64_t E, const double* q, const double* params, doubl
 
 // Orders that use the even-odd kernel: (N, threads, working threads, CTAs/SM).
 // The batched, allocation-free and served paths use the even-odd body for the
-// same orders, so every FP64 path rounds alike. From N = 9 on, 512 threads all
-// working beat the thread counts fitted to the 9 N^2 line tasks (N = 9..12 by
-// 4, 2, 4 and 2 %, measured on GB300 in the batched kernel's shapes).
+// same orders, so every FP64 path rounds alike. From N = 9 on, CTAs with every
+// thread working beat the thread counts fitted to the 9 N^2 line tasks; the
+// counts below are the fastest of a sweep on GB300 (N = 10: 640 threads,
+// 12.29 ms for 4096 elements against 13.02 with 512 and 13.20 with 300 of 320;
+// N = 12: 576, 14.39 against 14.58 with 512 and 14.79 with 432 of 448).
 #define STP_FP64_EO_SHAPES(X) X(7, 352, 343, 2) X(8, 192, 192, 2) X(9, 512, 512, 1) \
-  X(10, 512, 512, 1) X(11, 512, 512, 1)
+  X(10, 640, 640, 1) X(11, 512, 512, 1)
 
 int fp64_elements_per_cta(int N) {
   switch (N) {
@@ -139,7 +141,7 @@ cudaError_t launch_fp64(int N, int64_t E, const double* q, const double* params,
   case n: return launch_eo<n, nt, use, minb>(E, q, params, out_avg, out_faces, tables, stream);
     STP_FP64_EO_SHAPES(X)
 #undef X
-    case 12: return launch_eo_slots<12, 512, 512>(E, q, params, out_avg, out_faces, tables, stream);
+    case 12: return launch_eo_slots<12, 576, 576>(E, q, params, out_avg, out_faces, tables, stream);
     default: break;
   }
   switch (N) {
