@@ -90,12 +90,23 @@ struct SetDev {
   double dx;             // the handle's dx (curvilinear sets)
 };
 
-// Shared memory of order N's curvilinear shape (0 for other N).
+// Shared memory and threads of order N's curvilinear shape (0 for other N):
+// the single-set kernel's.
 size_t curv_batch_smem(int N) {
   switch (N) {
-#define X(n_, nodes_, a_, lean_) \
-  case n_: return CurvShape<n_, a_, false>::SMEM;
-    STP_CURV512_SHAPES(X)
+#define X(n_, nt_, nodes_, a_, lean_, greg_, db_) \
+  case n_: return CurvShape<n_, a_, db_>::SMEM;
+    STP_CURV_SHAPES(X)
+#undef X
+    default: return 0;
+  }
+}
+
+int curv_batch_threads(int N) {
+  switch (N) {
+#define X(n_, nt_, nodes_, a_, lean_, greg_, db_) \
+  case n_: return nt_;
+    STP_CURV_SHAPES(X)
 #undef X
     default: return 0;
   }
@@ -150,12 +161,12 @@ struct EoSlotsUnit {
   }
 };
 
-template <int N, int NODES, int A, bool LEAN>
+template <int N, int THREADS, int NODES, int A, bool LEAN, bool GREG, bool DB>
 struct CurvUnit {
-  static constexpr int NT = kBatchThreads, MINB = 1;
+  static constexpr int NT = THREADS, MINB = 1;
   static __device__ __forceinline__ void run(double* smem, const SetDev& sd, int64_t e0, double*) {
     if (e0 < sd.E)
-      curv_element<N, kBatchThreads, NODES, A, LEAN, false, false>(
+      curv_element<N, THREADS, NODES, A, LEAN, GREG, DB>(
           smem, sd.q, sd.params, sd.metric, sd.avg, sd.faces, sd.tables, sd.dx, e0);
   }
 };
@@ -206,9 +217,9 @@ OrderKernel cart_kernel(int N, int v) {
 // Kernel of order N's curvilinear shape.
 OrderKernel curv_kernel(int N) {
   switch (N) {
-#define X(n_, nodes_, a_, lean_) \
-  case n_: return order_kernel<CurvUnit<n_, nodes_, a_, lean_>>;
-    STP_CURV512_SHAPES(X)
+#define X(n_, nt_, nodes_, a_, lean_, greg_, db_) \
+  case n_: return order_kernel<CurvUnit<n_, nt_, nodes_, a_, lean_, greg_, db_>>;
+    STP_CURV_SHAPES(X)
 #undef X
     default: return nullptr;
   }
@@ -442,6 +453,7 @@ cudaError_t create_plan(int nsets, const int* N, const int64_t* E, const double*
       unit_cost[i] = 1.7 * F / 1.2e6;  // every quantity along every direction
       kern[i] = curv_kernel(N[i]);
       smem[i] = curv_batch_smem(N[i]);
+      threads[i] = curv_batch_threads(N[i]);
       continue;
     }
     int v = forced_variant ? forced_variant[i] : -1;

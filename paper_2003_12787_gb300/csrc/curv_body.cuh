@@ -48,7 +48,20 @@ struct CurvShape {
       sizeof(double) * (size_t)(TABLE + (kQuantities + (DB ? 2 : 1) * A) * S);
 };
 
-// Curvilinear element shapes in the persistent kernels' 512-thread CTAs:
+// Launch shapes of the curvilinear kernels per N (its own kernel and the
+// batched plan's): threads, nodes per thread, quantities per line pass,
+// lean register state, metric in registers, double buffer (measured on GB300 among 2-6
+// candidates per N; from N = 7 on, enough threads that the 9 N^2 line tasks of
+// a pass take one or two even rounds).
+#define STP_CURV_SHAPES(X)                                                                     \
+  X(1, 32, 1, 9, false, false, false) X(2, 32, 1, 9, false, false, false)                       \
+  X(3, 32, 1, 9, false, false, false) X(4, 64, 1, 9, false, false, false)                       \
+  X(5, 128, 1, 9, false, false, false) X(6, 224, 1, 9, false, false, false)                     \
+  X(7, 448, 1, 9, false, true, true) X(8, 576, 1, 9, false, false, true)                        \
+  X(9, 384, 2, 9, false, true, true) X(10, 512, 2, 9, true, true, false)                        \
+  X(11, 448, 3, 9, true, false, false) X(12, 448, 4, 5, true, false, false)
+
+// Curvilinear element shapes in the allocation-free kernel's 512-thread CTAs:
 // (N, nodes per thread, quantities per line pass, lean register state). The
 // quantities per pass follow the curvilinear kernel's own shapes; as the
 // arithmetic does not depend on the thread layout, a set gives the same bits

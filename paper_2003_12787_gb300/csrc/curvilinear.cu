@@ -34,18 +34,7 @@ cudaError_t launch_curv_n(int64_t E, const double* q, const double* params, cons
 
 }  // namespace
 
-// Launch shapes per N: threads, nodes per thread, quantities per line pass,
-// lean register state, metric in registers, double buffer (measured on GB300 among 2-6
-// candidates per N; from N = 7 on, enough threads that the 9 N^2 line tasks of
-// a pass take one or two even rounds).
-#define STP_CURV_SHAPES(X)                                                                     \
-  X(1, 32, 1, 9, false, false, false) X(2, 32, 1, 9, false, false, false)                       \
-  X(3, 32, 1, 9, false, false, false) X(4, 64, 1, 9, false, false, false)                       \
-  X(5, 128, 1, 9, false, false, false) X(6, 224, 1, 9, false, false, false)                     \
-  X(7, 448, 1, 9, false, true, true) X(8, 576, 1, 9, false, false, true)                        \
-  X(9, 384, 2, 9, false, true, true) X(10, 512, 2, 9, true, true, false)                        \
-  X(11, 448, 3, 9, true, false, false) X(12, 448, 4, 5, true, false, false)
-
+// Launch shapes per N: STP_CURV_SHAPES (curv_body.cuh).
 cudaError_t launch_curvilinear(int N, int64_t E, const double* q, const double* params,
                                const double* metric, double* out_avg, double* out_faces,
                                const double* tables, double dx, cudaStream_t stream) {
