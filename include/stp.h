@@ -502,11 +502,12 @@ stp_status stp_batch_run_static_sources(int nsets, const stp_batch_set* sets,
  * used first and their state copied back to pinned host memory), and launches
  * up to 128 ready resident simulations per free slot, whose footprints add up
  * to at most half the budget when slots > 1 (one simulation at least), so the
- * next batch is admitted while one runs: the FP64 ones as one
- * persistent batched launch, the others (curvilinear, or another precision)
- * each with its own kernel on the same stream; requests that arrive while
- * others run join the next launch and launches on different slots overlap on
- * the GPU. The scheduler
+ * next batch is admitted while one runs. The FP64 ones, Cartesian and
+ * curvilinear, run as one persistent launch when the batch is small, or as
+ * one persistent launch per shape when it is large; simulations of another
+ * precision each run with their own kernel on the same stream. Requests that
+ * arrive while others run join the next batch, and batches on different
+ * slots overlap on the GPU. The scheduler
  * runs on the calling thread (stp_server_progress / _drain / _run_trace);
  * a server is not thread-safe.
  */

@@ -88,6 +88,9 @@ struct SetDev {
   int variant;
   const double* metric;  // curvilinear set: per-node inverse Jacobians; NULL: Cartesian
   double dx;             // the handle's dx (curvilinear sets)
+  int64_t first_unit;    // work units of the launch's sets before this one
+  int epc;               // elements per work unit
+  int pad;
 };
 
 // Shared memory and threads of order N's curvilinear shape (0 for other N):
@@ -111,12 +114,6 @@ int curv_batch_threads(int N) {
     default: return 0;
   }
 }
-
-struct UnitDev {
-  int64_t e0;
-  int set;
-  int pad;
-};
 
 // Set descriptors of one launch, passed as a kernel parameter: read from the
 // parameter space, the buffer pointers reach the element bodies as they do in
@@ -172,11 +169,12 @@ struct CurvUnit {
 };
 
 // Persistent kernel of one shape: its CTAs take units of its own work list
-// (units of up to kParamSets sets of that shape; UnitDev::set indexes tb)
-// through an atomic counter until the list is exhausted.
+// (the units of up to kParamSets sets of that shape, set by set; a unit's
+// set is found from the sets' first units) through an atomic counter until
+// the list is exhausted.
 template <class Unit>
 __global__ void __launch_bounds__(Unit::NT, Unit::MINB)
-order_kernel(const __grid_constant__ SetTable tb, const UnitDev* __restrict__ units, int nunits,
+order_kernel(const __grid_constant__ SetTable tb, int nsets, int nunits,
              unsigned int* __restrict__ counter, double* __restrict__ scratch,
              int64_t scratch_doubles_per_cta) {
   double* rbuf = scratch ? scratch + blockIdx.x * scratch_doubles_per_cta : nullptr;
@@ -188,12 +186,17 @@ order_kernel(const __grid_constant__ SetTable tb, const UnitDev* __restrict__ un
     const int u = cur;
     __syncthreads();  // everyone has read cur before thread 0 may overwrite it
     if (u >= nunits) break;
-    const UnitDev wu = units[u];
-    Unit::run(smem, tb.sets[wu.set], wu.e0, rbuf);
+    int lo = 0, hi = nsets - 1;  // the last set whose first unit is <= u
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (tb.sets[mid].first_unit <= u) lo = mid; else hi = mid - 1;
+    }
+    const SetDev& sd = tb.sets[lo];
+    Unit::run(smem, sd, (u - sd.first_unit) * sd.epc, rbuf);
   }
 }
 
-using OrderKernel = void (*)(const SetTable, const UnitDev*, int, unsigned int*, double*, int64_t);
+using OrderKernel = void (*)(const SetTable, int, int, unsigned int*, double*, int64_t);
 
 // Kernel of order N's Cartesian shape v.
 OrderKernel cart_kernel(int N, int v) {
@@ -252,11 +255,11 @@ int sm_count() {
 // (stream operations only, so it can be captured into a graph); the caller
 // resets the counter and has raised the kernel's dynamic shared-memory limit
 // to at least smem (prepare_kernel).
-cudaError_t launch_order(OrderKernel k, int threads, const SetTable& tb, const UnitDev* d_units,
-                         int nunits, unsigned int* d_counter, double* scratch,
-                         size_t scratch_per_cta, size_t smem, int ctas, cudaStream_t st) {
+cudaError_t launch_order(OrderKernel k, int threads, const SetTable& tb, int nsets, int nunits,
+                         unsigned int* d_counter, double* scratch, size_t scratch_per_cta,
+                         size_t smem, int ctas, cudaStream_t st) {
   k<<<ctas, threads, std::max<size_t>(smem, 1), st>>>(
-      tb, d_units, nunits, d_counter, scratch, (int64_t)(scratch_per_cta / sizeof(double)));
+      tb, nsets, nunits, d_counter, scratch, (int64_t)(scratch_per_cta / sizeof(double)));
   return cudaGetLastError();
 }
 
@@ -314,7 +317,6 @@ cudaError_t autotune(int N, const double* tables, int* variant, double* us_per_e
     E = std::min<int64_t>(E, 100000);
     const size_t n3 = (size_t)N * N * N;
     double *q = nullptr, *p = nullptr, *a = nullptr, *f = nullptr;
-    UnitDev* d_units = nullptr;
     unsigned int* d_counter = nullptr;
     cudaStream_t st = nullptr;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
@@ -325,7 +327,6 @@ cudaError_t autotune(int N, const double* tables, int* variant, double* us_per_e
     chk(cudaMalloc(&a, E * n3 * 9 * 8));
     chk(cudaMalloc(&f, E * (size_t)N * N * 54 * 8));
     chk(cudaMalloc(&d_counter, sizeof(unsigned int)));
-    chk(cudaMalloc(&d_units, sizeof(UnitDev) * (size_t)E));
     size_t scr = 0;
     for (int v = 0; v < kMaxVariants; ++v)
       if (shapes().s[N][v].valid) scr = std::max(scr, shapes().s[N][v].scratch);
@@ -344,21 +345,17 @@ cudaError_t autotune(int N, const double* tables, int* variant, double* us_per_e
       const ShapeInfo& si = shapes().s[N][v];
       if (!si.valid) continue;
       SetTable tb{};
-      tb.sets[0] = SetDev{q, p, a, f, tables, E, N, v, nullptr, 0.0};
-      std::vector<UnitDev> units;
-      for (int64_t e = 0; e < E; e += si.epc) units.push_back(UnitDev{e, 0, 0});
-      chk(cudaMemcpyAsync(d_units, units.data(), sizeof(UnitDev) * units.size(),
-                          cudaMemcpyHostToDevice, st));
+      tb.sets[0] = SetDev{q, p, a, f, tables, E, N, v, nullptr, 0.0, 0, si.epc, 0};
+      const int nunits = (int)((E + si.epc - 1) / si.epc);
       float ms_best = 1e30f;
       const OrderKernel k = cart_kernel(N, v);
       int per_sm = 1;
       chk(prepare_kernel(k, si.threads, si.smem, &per_sm));
-      const int ctas = (int)std::min<int64_t>((int64_t)per_sm * sms, (int64_t)units.size());
+      const int ctas = (int)std::min<int64_t>((int64_t)per_sm * sms, nunits);
       for (int rep = 0; rep < 4 && err == cudaSuccess; ++rep) {
         chk(cudaMemsetAsync(d_counter, 0, sizeof(unsigned int), st));
         chk(cudaEventRecord(e0, st));
-        chk(launch_order(k, si.threads, tb, d_units, (int)units.size(), d_counter, scratch, scr,
-                         si.smem, ctas, st));
+        chk(launch_order(k, si.threads, tb, 1, nunits, d_counter, scratch, scr, si.smem, ctas, st));
         chk(cudaEventRecord(e1, st));
         chk(cudaEventSynchronize(e1));
         float ms = 0.f;
@@ -371,7 +368,7 @@ cudaError_t autotune(int N, const double* tables, int* variant, double* us_per_e
     }
     if (st) cudaStreamSynchronize(st);
     cudaFree(q); cudaFree(p); cudaFree(a); cudaFree(f);
-    cudaFree(d_units); cudaFree(d_counter); cudaFree(scratch);
+    cudaFree(d_counter); cudaFree(scratch);
     if (e0) cudaEventDestroy(e0);
     if (e1) cudaEventDestroy(e1);
     if (st) cudaStreamDestroy(st);
@@ -384,20 +381,151 @@ cudaError_t autotune(int N, const double* tables, int* variant, double* us_per_e
   return cudaSuccess;
 }
 
-// ---- plans ------------------------------------------------------------------
+// ---- launches -----------------------------------------------------------------
+
+namespace {
 
 // One persistent launch: up to kParamSets sets of one shape (one order,
-// Cartesian shape v or curvilinear) over work-list entries [begin, begin + count).
+// Cartesian shape v or curvilinear), their units numbered set by set.
 struct Launch {
   OrderKernel kernel = nullptr;
   int threads = kBatchThreads;
   SetTable table{};
   int nsets = 0;
   size_t smem = 0, scratch_per_cta = 0, scratch_off = 0;  // scratch_off in doubles
-  int64_t begin = 0, count = 0;
+  int64_t count = 0;  // work units
   double cost = 0.0;  // estimated us of the whole launch
   int ctas = 0, branch = 0;
 };
+
+// A shape's kernel, block size, shared memory and parking scratch per CTA.
+struct ShapeRef {
+  OrderKernel kernel = nullptr;
+  int threads = kBatchThreads;
+  size_t smem = 0, scratch_per_cta = 0;
+};
+
+// Shape of a set: its kernel, block size, shared memory, parking scratch per
+// CTA, elements per unit and estimated us per unit. variant < 0 for a
+// Cartesian set picks the autotuned shape (tuning the order first when
+// `tune`, else the cached choice or a default that allocates nothing).
+cudaError_t set_shape(int N, const double* tables, bool curvilinear, int variant, bool tune,
+                      ShapeRef* shape, int* v_out, int* epc, double* unit_us) {
+  if (N < 1 || N > kMaxNodes) return cudaErrorInvalidValue;
+  const double F = 36.0 * std::pow(N, 5) + 66.0 * std::pow(N, 4) + 108.0 * std::pow(N, 3);
+  if (curvilinear) {
+    shape->kernel = curv_kernel(N);
+    shape->threads = curv_batch_threads(N);
+    shape->smem = curv_batch_smem(N);
+    shape->scratch_per_cta = 0;
+    *v_out = 0;
+    *epc = 1;
+    *unit_us = 1.7 * F / 1.2e6;  // every quantity along every direction
+    return shape->kernel ? cudaSuccess : cudaErrorInvalidValue;
+  }
+  int v = variant;
+  double us = F / 1.2e6;  // FP64-bound estimate
+  if (v < 0 && tune) {
+    cudaError_t err = autotune(N, tables, &v, &us, nullptr);
+    if (err != cudaSuccess) return err;
+  } else if (v < 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    std::lock_guard<std::mutex> lock(g_tune_mutex);
+    if (dev >= 0 && dev < 8 && g_tuned[dev][N].variant >= 0) {
+      v = g_tuned[dev][N].variant;
+      us = g_tuned[dev][N].us_per_element;
+    } else {
+      // the shapes the autotuner picks on GB300
+      static const int kDefault[kMaxNodes + 1] = {0, 0, 0, 0, 0, 1, 1, 0, 0, 1, 0, 1, 0};
+      v = kDefault[N];
+    }
+  }
+  if (v < 0 || v >= kMaxVariants || !shapes().s[N][v].valid) return cudaErrorInvalidValue;
+  const ShapeInfo& si = shapes().s[N][v];
+  shape->kernel = cart_kernel(N, v);
+  shape->threads = si.threads;
+  shape->smem = si.smem;
+  shape->scratch_per_cta = si.scratch;
+  *v_out = v;
+  *epc = si.epc;
+  *unit_us = us * si.epc;
+  return shape->kernel ? cudaSuccess : cudaErrorInvalidValue;
+}
+
+// Groups the sets by shape into launches (at most kParamSets sets each, in set
+// order), longest first; sets without elements are left out.
+cudaError_t build_launches(int nsets, const int* N, const int64_t* E, const double* const* q,
+                           const double* const* params, double* const* avg,
+                           double* const* faces, const double* const* tables,
+                           const int* forced_variant, const double* const* metrics,
+                           const double* dx, bool tune, std::vector<Launch>* out) {
+  std::vector<ShapeRef> shape((size_t)nsets);
+  std::vector<SetDev> sets((size_t)nsets);
+  std::vector<double> unit_us((size_t)nsets);
+  for (int i = 0; i < nsets; ++i) {
+    const bool curv = metrics && metrics[i];
+    int v = 0, epc = 1;
+    cudaError_t err = set_shape(N[i], tables[i], curv, forced_variant ? forced_variant[i] : -1,
+                                tune, &shape[i], &v, &epc, &unit_us[i]);
+    if (err != cudaSuccess) return err;
+    sets[i] = SetDev{q[i], params[i], avg[i], faces[i], tables[i], E[i], N[i], v,
+                     curv ? metrics[i] : nullptr, curv && dx ? dx[i] : 0.0, 0, epc, 0};
+  }
+  std::vector<char> done((size_t)nsets, 0);
+  std::vector<Launch> built;
+  built.reserve(8);
+  for (int i = 0; i < nsets; ++i) {
+    if (done[i] || E[i] <= 0) continue;
+    Launch* l = nullptr;
+    for (int j = i; j < nsets; ++j) {
+      if (done[j] || E[j] <= 0 || shape[j].kernel != shape[i].kernel) continue;
+      if (!l || l->nsets == kParamSets) {
+        built.emplace_back();
+        l = &built.back();
+        l->kernel = shape[i].kernel;
+        l->threads = shape[i].threads;
+        l->smem = shape[i].smem;
+        l->scratch_per_cta = shape[i].scratch_per_cta;
+      }
+      const int64_t units = (E[j] + sets[j].epc - 1) / sets[j].epc;
+      sets[j].first_unit = l->count;
+      l->table.sets[l->nsets++] = sets[j];
+      l->count += units;
+      l->cost += unit_us[j] * (double)units;
+      done[j] = 1;
+    }
+  }
+  std::vector<size_t> order(built.size());
+  for (size_t k = 0; k < order.size(); ++k) {
+    if (built[k].count > 0x7fffffffLL) return cudaErrorInvalidValue;
+    order[k] = k;
+  }
+  std::stable_sort(order.begin(), order.end(),
+                   [&](size_t a, size_t b) { return built[a].cost > built[b].cost; });
+  out->reserve(out->size() + order.size());
+  for (size_t k : order) out->push_back(built[k]);
+  return cudaSuccess;
+}
+
+// CTAs per SM of each kernel at its shared memory, set up once per device.
+std::mutex g_occ_mutex;
+std::vector<std::pair<std::pair<int, OrderKernel>, int>> g_occ;
+
+cudaError_t kernel_ctas_per_sm(OrderKernel k, int threads, size_t smem, int* per_sm) {
+  int dev = 0;
+  cudaGetDevice(&dev);
+  std::lock_guard<std::mutex> lock(g_occ_mutex);
+  for (const auto& e : g_occ)
+    if (e.first.first == dev && e.first.second == k) { *per_sm = e.second; return cudaSuccess; }
+  cudaError_t err = prepare_kernel(k, threads, smem, per_sm);
+  if (err == cudaSuccess) g_occ.push_back({{dev, k}, *per_sm});
+  return err;
+}
+
+}  // namespace
+
+// ---- plans ------------------------------------------------------------------
 
 constexpr int kMaxBranches = 4;
 
@@ -405,7 +533,6 @@ struct BatchPlan {
   int device = -1;
   int nsets = 0, nunits = 0, ctas = 0;
   size_t smem = 0;
-  UnitDev* d_units = nullptr;
   unsigned int* d_counter = nullptr;  // one per launch
   double* d_scratch = nullptr;        // parked new terms of the large-N shapes, per CTA
   cudaGraph_t graph = nullptr;
@@ -416,19 +543,17 @@ void destroy_plan(BatchPlan* p) {
   if (!p) return;
   if (p->exec) cudaGraphExecDestroy(p->exec);
   if (p->graph) cudaGraphDestroy(p->graph);
-  cudaFree(p->d_units);
   cudaFree(p->d_counter);
   cudaFree(p->d_scratch);
   delete p;
 }
 
-// Groups the sets by shape (at most kParamSets per launch), uploads the work
-// list and captures into a CUDA graph the counters' reset and one persistent
-// launch per group, spread over up to kMaxBranches parallel branches (longest
-// first, each to the branch with the least estimated work). Launches on
-// different branches run concurrently: one shape's CTAs take the SMs that
-// another's finished CTAs free, so no SM waits out a shape's tail.
-// forced_variant[i] < 0 = autotuned.
+// Groups the sets by shape (at most kParamSets per launch) and captures into a
+// CUDA graph the counters' reset and one persistent launch per group, spread
+// over up to kMaxBranches parallel branches (longest first, each to the
+// branch with the least estimated work). Launches on different branches run
+// concurrently: one shape's CTAs take the SMs that another's finished CTAs
+// free, so no SM waits out a shape's tail. forced_variant[i] < 0 = autotuned.
 cudaError_t create_plan(int nsets, const int* N, const int64_t* E, const double* const* q,
                         const double* const* params, double* const* avg, double* const* faces,
                         const double* const* tables, const int* forced_variant, BatchPlan** out,
@@ -437,90 +562,19 @@ cudaError_t create_plan(int nsets, const int* N, const int64_t* E, const double*
   BatchPlan* p = new (std::nothrow) BatchPlan;
   if (!p) return cudaErrorMemoryAllocation;
   cudaGetDevice(&p->device);
-  std::vector<SetDev> sets((size_t)nsets);
-  std::vector<double> unit_cost((size_t)nsets);
-  std::vector<int> epc((size_t)nsets, 1);
-  std::vector<OrderKernel> kern((size_t)nsets, nullptr);
-  std::vector<size_t> smem((size_t)nsets, 0), scratch((size_t)nsets, 0);
-  std::vector<int> threads((size_t)nsets, kBatchThreads);
-  cudaError_t err = cudaSuccess;
-  for (int i = 0; i < nsets && err == cudaSuccess; ++i) {
-    if (N[i] < 1 || N[i] > kMaxNodes) { err = cudaErrorInvalidValue; break; }
-    const double F = 36.0 * std::pow(N[i], 5) + 66.0 * std::pow(N[i], 4) + 108.0 * std::pow(N[i], 3);
-    if (metrics && metrics[i]) {  // curvilinear: one element per unit
-      sets[i] = SetDev{q[i], params[i], avg[i], faces[i], tables[i], E[i], N[i], 0, metrics[i],
-                       dx ? dx[i] : 1.0};
-      unit_cost[i] = 1.7 * F / 1.2e6;  // every quantity along every direction
-      kern[i] = curv_kernel(N[i]);
-      smem[i] = curv_batch_smem(N[i]);
-      threads[i] = curv_batch_threads(N[i]);
-      continue;
-    }
-    int v = forced_variant ? forced_variant[i] : -1;
-    double us = 0.0;
-    if (v < 0) err = autotune(N[i], tables[i], &v, &us, nullptr);
-    else us = F / 1.2e6;  // FP64-bound estimate
-    if (err != cudaSuccess) break;
-    if (v < 0 || v >= kMaxVariants || !shapes().s[N[i]][v].valid) { err = cudaErrorInvalidValue; break; }
-    const ShapeInfo& si = shapes().s[N[i]][v];
-    sets[i] = SetDev{q[i], params[i], avg[i], faces[i], tables[i], E[i], N[i], v, nullptr, 0.0};
-    epc[i] = si.epc;
-    unit_cost[i] = us * si.epc;
-    kern[i] = cart_kernel(N[i], v);
-    smem[i] = si.smem;
-    scratch[i] = si.scratch;
-    threads[i] = si.threads;
-  }
-  for (int i = 0; i < nsets && err == cudaSuccess; ++i)
-    if (!kern[i]) err = cudaErrorInvalidValue;
-  // launches: the sets of each shape, kParamSets at a time, in set order
   std::vector<Launch> launches;
-  if (err == cudaSuccess) {
-    std::vector<char> done((size_t)nsets, 0);
-    for (int i = 0; i < nsets; ++i) {
-      if (done[i] || E[i] == 0) continue;
-      Launch* l = nullptr;
-      for (int j = i; j < nsets; ++j) {
-        if (done[j] || E[j] == 0 || kern[j] != kern[i]) continue;
-        if (!l || l->nsets == kParamSets) {
-          launches.emplace_back();
-          l = &launches.back();
-          l->kernel = kern[i];
-          l->threads = threads[i];
-          l->smem = smem[i];
-          l->scratch_per_cta = scratch[i];
-        }
-        l->table.sets[l->nsets++] = sets[j];
-        l->cost += unit_cost[j] * (double)((E[j] + epc[j] - 1) / epc[j]);
-        done[j] = 1;
-      }
-    }
-  }
-  // work list: launches longest first; within one, units by set, then element
-  std::vector<UnitDev> units;
-  if (err == cudaSuccess) {
-    std::stable_sort(launches.begin(), launches.end(),
-                     [](const Launch& a, const Launch& b) { return a.cost > b.cost; });
-    for (Launch& l : launches) {
-      l.begin = (int64_t)units.size();
-      for (int k = 0; k < l.nsets; ++k) {
-        const SetDev& sd = l.table.sets[k];
-        const int step = sd.metric ? 1 : shapes().s[sd.N][sd.variant].epc;
-        for (int64_t e = 0; e < sd.E; e += step) units.push_back(UnitDev{e, k, 0});
-      }
-      l.count = (int64_t)units.size() - l.begin;
-    }
-    if (units.size() > 0x7fffffffu) err = cudaErrorInvalidValue;
-  }
+  cudaError_t err = build_launches(nsets, N, E, q, params, avg, faces, tables, forced_variant,
+                                   metrics, dx, true, &launches);
   // grids, branches, scratch
   size_t scratch_doubles = 0;
+  int64_t units = 0;
   if (err == cudaSuccess) {
     const int sms = sm_count();
     double load[kMaxBranches] = {0.0};
     const int nb = std::min<int>(kMaxBranches, (int)std::max<size_t>(1, launches.size()));
     for (Launch& l : launches) {
       int per_sm = 1;
-      if ((err = prepare_kernel(l.kernel, l.threads, l.smem, &per_sm)) != cudaSuccess) break;
+      if ((err = kernel_ctas_per_sm(l.kernel, l.threads, l.smem, &per_sm)) != cudaSuccess) break;
       l.ctas = (int)std::min<int64_t>((int64_t)per_sm * sms, l.count);
       l.branch = (int)(std::min_element(load, load + nb) - load);
       load[l.branch] += l.cost;
@@ -528,17 +582,16 @@ cudaError_t create_plan(int nsets, const int* N, const int64_t* E, const double*
       scratch_doubles += l.scratch_per_cta / sizeof(double) * (size_t)l.ctas;
       p->ctas += l.ctas;
       p->smem = std::max(p->smem, l.smem);
+      units += l.count;
     }
   }
+  if (err == cudaSuccess && units > 0x7fffffffLL) err = cudaErrorInvalidValue;
   p->nsets = nsets;
-  p->nunits = (int)units.size();
-  if (err == cudaSuccess) err = cudaMalloc(&p->d_units, sizeof(UnitDev) * std::max<size_t>(1, units.size()));
+  p->nunits = (int)units;
   if (err == cudaSuccess)
     err = cudaMalloc(&p->d_counter, sizeof(unsigned int) * std::max<size_t>(1, launches.size()));
   if (err == cudaSuccess && scratch_doubles)
     err = cudaMalloc(&p->d_scratch, sizeof(double) * scratch_doubles);
-  if (err == cudaSuccess && !units.empty())
-    err = cudaMemcpy(p->d_units, units.data(), sizeof(UnitDev) * units.size(), cudaMemcpyHostToDevice);
   // capture: reset, fork, one launch per group on its branch, join
   cudaStream_t st = nullptr;
   cudaStream_t br[kMaxBranches] = {nullptr};
@@ -561,8 +614,7 @@ cudaError_t create_plan(int nsets, const int* N, const int64_t* E, const double*
         if (used[b]) le = cudaStreamWaitEvent(br[b], fork, 0);
       for (size_t li = 0; li < launches.size() && le == cudaSuccess; ++li) {
         const Launch& l = launches[li];
-        le = launch_order(l.kernel, l.threads, l.table, p->d_units + l.begin, (int)l.count,
-                          p->d_counter + li,
+        le = launch_order(l.kernel, l.threads, l.table, l.nsets, (int)l.count, p->d_counter + li,
                           p->d_scratch ? p->d_scratch + l.scratch_off : nullptr, l.scratch_per_cta,
                           l.smem, l.ctas, br[l.branch]);
       }
@@ -589,6 +641,44 @@ cudaError_t create_plan(int nsets, const int* N, const int64_t* E, const double*
   }
   *out = p;
   return cudaSuccess;
+}
+
+// The same per-shape persistent launches issued directly on `stream`, one
+// after another, with caller-provided scratch (counters, then the parking
+// areas): no allocation, no graph. Used by the served loop for large batches.
+cudaError_t launch_shape_batches(int nsets, const int* N, const int64_t* E,
+                                 const double* const* q, const double* const* params,
+                                 double* const* avg, double* const* faces,
+                                 const double* const* tables, const double* const* metrics,
+                                 const double* dx, unsigned char* scratch, size_t scratch_bytes,
+                                 cudaStream_t stream, int* too_big) {
+  *too_big = 0;
+  std::vector<Launch> launches;
+  cudaError_t err = build_launches(nsets, N, E, q, params, avg, faces, tables, nullptr, metrics,
+                                   dx, false, &launches);
+  if (err != cudaSuccess || launches.empty()) return err;
+  constexpr size_t kCounters = 256;  // bytes of counters at the start of scratch
+  if (launches.size() * sizeof(unsigned int) > kCounters) { *too_big = 1; return cudaErrorInvalidValue; }
+  const int sms = sm_count();
+  size_t off = kCounters;
+  for (Launch& l : launches) {
+    int per_sm = 1;
+    if ((err = kernel_ctas_per_sm(l.kernel, l.threads, l.smem, &per_sm)) != cudaSuccess) return err;
+    l.ctas = (int)std::min<int64_t>((int64_t)per_sm * sms, l.count);
+    l.scratch_off = off;  // bytes here
+    off += l.scratch_per_cta * (size_t)l.ctas;
+  }
+  if (off > scratch_bytes) { *too_big = 1; return cudaErrorInvalidValue; }
+  unsigned int* counters = reinterpret_cast<unsigned int*>(scratch);
+  if ((err = cudaMemsetAsync(counters, 0, sizeof(unsigned int) * launches.size(), stream)) != cudaSuccess)
+    return err;
+  for (size_t li = 0; li < launches.size() && err == cudaSuccess; ++li) {
+    const Launch& l = launches[li];
+    double* park = l.scratch_per_cta ? reinterpret_cast<double*>(scratch + l.scratch_off) : nullptr;
+    err = launch_order(l.kernel, l.threads, l.table, l.nsets, (int)l.count, counters + li, park,
+                       l.scratch_per_cta, l.smem, l.ctas, stream);
+  }
+  return err;
 }
 
 cudaError_t launch_plan(BatchPlan* p, cudaStream_t stream) {

@@ -138,6 +138,18 @@ cudaError_t create_plan(int nsets, const int* N, const int64_t* E, const double*
                         const double* const* tables, const int* forced_variant, BatchPlan** out,
                         const double* const* metrics = nullptr, const double* dx = nullptr);
 cudaError_t launch_plan(BatchPlan* p, cudaStream_t stream);
+// The sets' FP64 STPs as per-shape persistent launches issued one after
+// another on `stream`, with caller-provided scratch (256 bytes of counters,
+// then parking areas); metrics[i] (when metrics and it are not NULL) makes
+// set i curvilinear with the handle's dx[i]. Allocates nothing; *too_big = 1
+// (cudaErrorInvalidValue) when the scratch is too small. Shapes: the
+// autotuner's cached choice per order, else the default GB300 choice.
+cudaError_t launch_shape_batches(int nsets, const int* N, const int64_t* E,
+                                 const double* const* q, const double* const* params,
+                                 double* const* avg, double* const* faces,
+                                 const double* const* tables, const double* const* metrics,
+                                 const double* dx, unsigned char* scratch, size_t scratch_bytes,
+                                 cudaStream_t stream, int* too_big);
 void plan_info(const BatchPlan* p, int* units, int* ctas, size_t* smem);
 void destroy_plan(BatchPlan* p);
 
