@@ -433,3 +433,67 @@ def test_curvilinear_simulations_with_sources_match_the_oracle():
     srv.close()
     for P, _ in sims:
         P.close()
+
+
+def _stepped(P, prob, steps):
+    q = prob.q.cuda()
+    m = prob.metric.cuda() if prob.metric is not None else None
+    for _ in range(steps):
+        q, faces = P.predict(q, prob.params.cuda(), metric=m)
+    torch.cuda.synchronize()
+    return q.cpu(), faces.cpu()
+
+
+def test_large_batches_run_per_shape_and_match_single_set_calls():
+    """A batch with more than about 50 ms of FP64 work (eight order-9 sets of
+    2000 elements, a curvilinear order-7 set, an order-11 set) runs as
+    per-shape persistent launches; served twice, every simulation equals
+    repeated single-set calls bit for bit."""
+    specs = [(10, 2000, False)] * 8 + [(8, 3000, True), (12, 40, False)]
+    sims = []
+    for i, (N, E, curv) in enumerate(specs):
+        make = curvilinear_problem if curv else elastic_problem
+        prob = make(N, E=E, seed_material=8100 + i, seed_waves=8200 + i, device="cuda")
+        sims.append((stp.Predictor(N - 1, prob.h, prob.dt), prob))
+    srv = stp.Server(6 << 30, slots=1)
+    ids = [srv.add_sim(P, prob.q, prob.params, metric=prob.metric) for P, prob in sims]
+    steps = 2
+    for _ in range(steps):
+        for sid in ids:
+            srv.submit(sid)
+        srv.drain()
+    assert srv.stats()["launches"] == steps  # all ten in one batch per step
+    for (P, prob), sid in zip(sims, ids):
+        q_s, f_s, n = srv.read(sid)
+        assert n == steps
+        q_r, f_r = _stepped(P, prob, steps)
+        assert torch.equal(q_s, q_r) and torch.equal(f_s, f_r), prob.N
+    srv.close()
+    for P, _ in sims:
+        P.close()
+
+
+def test_order_11_simulations_round_alike_in_small_batches():
+    """In a small batch the order-11 (N = 12) simulation takes the per-shape
+    launch while the others share one allocation-free launch; each still
+    equals repeated single-set calls bit for bit."""
+    specs = [(12, 6), (5, 40), (9, 12)]
+    sims = []
+    for i, (N, E) in enumerate(specs):
+        prob = elastic_problem(N, E=E, seed_material=8300 + i, seed_waves=8400 + i)
+        sims.append((stp.Predictor(N - 1, prob.h, prob.dt), prob))
+    srv = stp.Server(1 << 30, slots=2)
+    ids = [srv.add_sim(P, prob.q, prob.params) for P, prob in sims]
+    steps = 3
+    for _ in range(steps):
+        for sid in ids:
+            srv.submit(sid)
+        srv.drain()
+    for (P, prob), sid in zip(sims, ids):
+        q_s, f_s, n = srv.read(sid)
+        assert n == steps
+        q_r, f_r = _stepped(P, prob, steps)
+        assert torch.equal(q_s, q_r) and torch.equal(f_s, f_r), prob.N
+    srv.close()
+    for P, _ in sims:
+        P.close()
