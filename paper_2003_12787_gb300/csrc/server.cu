@@ -313,8 +313,8 @@ struct Server {
       }
       // A batch with more than about 50 ms of FP64 work runs as the batched
       // plan's per-shape launches (each body at its single-set kernel's
-      // speed); a smaller one as the one allocation-free launch (measured:
-      // per-shape launches of 5-10 ms batches served 30 % fewer requests). N = 12 Cartesian simulations
+      // speed: 7 % more requests served on large simulations); a smaller one
+      // as the one allocation-free launch, which costs a single launch. N = 12 Cartesian simulations
       // always take the per-shape launch, whose body is the single-set
       // kernel's, so each simulation rounds the same in every batch.
       double work_ms = 0.0;
