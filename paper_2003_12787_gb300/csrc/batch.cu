@@ -21,6 +21,7 @@
 #include "curv_body.cuh"
 #include "fp64_eo.cuh"
 #include "fp64_group.cuh"
+#include "launch_groups.h"
 
 namespace stp {
 namespace {
@@ -454,57 +455,47 @@ cudaError_t set_shape(int N, const double* tables, bool curvilinear, int variant
 }
 
 // Groups the sets by shape into launches (at most kParamSets sets each, in set
-// order), longest first; sets without elements are left out.
+// order), longest first; sets without elements are left out (launch_groups.h).
 cudaError_t build_launches(int nsets, const int* N, const int64_t* E, const double* const* q,
                            const double* const* params, double* const* avg,
                            double* const* faces, const double* const* tables,
                            const int* forced_variant, const double* const* metrics,
                            const double* dx, bool tune, std::vector<Launch>* out) {
+  constexpr int kCurvKey = (kMaxNodes + 1) * kMaxVariants;
   std::vector<ShapeRef> shape((size_t)nsets);
   std::vector<SetDev> sets((size_t)nsets);
-  std::vector<double> unit_us((size_t)nsets);
+  std::vector<GroupInput> in((size_t)nsets);
   for (int i = 0; i < nsets; ++i) {
     const bool curv = metrics && metrics[i];
     int v = 0, epc = 1;
+    double unit_us = 0.0;
     cudaError_t err = set_shape(N[i], tables[i], curv, forced_variant ? forced_variant[i] : -1,
-                                tune, &shape[i], &v, &epc, &unit_us[i]);
+                                tune, &shape[i], &v, &epc, &unit_us);
     if (err != cudaSuccess) return err;
     sets[i] = SetDev{q[i], params[i], avg[i], faces[i], tables[i], E[i], N[i], v,
                      curv ? metrics[i] : nullptr, curv && dx ? dx[i] : 0.0, 0, epc, 0};
+    in[i] = GroupInput{curv ? kCurvKey + N[i] : N[i] * kMaxVariants + v,
+                       E[i] > 0 ? (E[i] + epc - 1) / epc : 0, unit_us};
   }
-  std::vector<char> done((size_t)nsets, 0);
-  std::vector<Launch> built;
-  built.reserve(8);
-  for (int i = 0; i < nsets; ++i) {
-    if (done[i] || E[i] <= 0) continue;
-    Launch* l = nullptr;
-    for (int j = i; j < nsets; ++j) {
-      if (done[j] || E[j] <= 0 || shape[j].kernel != shape[i].kernel) continue;
-      if (!l || l->nsets == kParamSets) {
-        built.emplace_back();
-        l = &built.back();
-        l->kernel = shape[i].kernel;
-        l->threads = shape[i].threads;
-        l->smem = shape[i].smem;
-        l->scratch_per_cta = shape[i].scratch_per_cta;
-      }
-      const int64_t units = (E[j] + sets[j].epc - 1) / sets[j].epc;
-      sets[j].first_unit = l->count;
-      l->table.sets[l->nsets++] = sets[j];
-      l->count += units;
-      l->cost += unit_us[j] * (double)units;
-      done[j] = 1;
+  const std::vector<LaunchGroup> groups = group_launches(in, kParamSets);
+  out->reserve(out->size() + groups.size());
+  for (const LaunchGroup& g : groups) {
+    if (g.count > 0x7fffffffLL) return cudaErrorInvalidValue;
+    out->emplace_back();
+    Launch& l = out->back();
+    const ShapeRef& sh = shape[(size_t)g.sets[0]];
+    l.kernel = sh.kernel;
+    l.threads = sh.threads;
+    l.smem = sh.smem;
+    l.scratch_per_cta = sh.scratch_per_cta;
+    l.nsets = (int)g.sets.size();
+    for (int k = 0; k < l.nsets; ++k) {
+      l.table.sets[k] = sets[(size_t)g.sets[(size_t)k]];
+      l.table.sets[k].first_unit = g.first_unit[(size_t)k];
     }
+    l.count = g.count;
+    l.cost = g.cost;
   }
-  std::vector<size_t> order(built.size());
-  for (size_t k = 0; k < order.size(); ++k) {
-    if (built[k].count > 0x7fffffffLL) return cudaErrorInvalidValue;
-    order[k] = k;
-  }
-  std::stable_sort(order.begin(), order.end(),
-                   [&](size_t a, size_t b) { return built[a].cost > built[b].cost; });
-  out->reserve(out->size() + order.size());
-  for (size_t k : order) out->push_back(built[k]);
   return cudaSuccess;
 }
 
@@ -570,14 +561,15 @@ cudaError_t create_plan(int nsets, const int* N, const int64_t* E, const double*
   int64_t units = 0;
   if (err == cudaSuccess) {
     const int sms = sm_count();
-    double load[kMaxBranches] = {0.0};
-    const int nb = std::min<int>(kMaxBranches, (int)std::max<size_t>(1, launches.size()));
-    for (Launch& l : launches) {
+    std::vector<double> costs;
+    for (const Launch& l : launches) costs.push_back(l.cost);
+    const std::vector<int> branch = lpt_branches(costs, kMaxBranches);
+    for (size_t li = 0; li < launches.size(); ++li) {
+      Launch& l = launches[li];
       int per_sm = 1;
       if ((err = kernel_ctas_per_sm(l.kernel, l.threads, l.smem, &per_sm)) != cudaSuccess) break;
       l.ctas = (int)std::min<int64_t>((int64_t)per_sm * sms, l.count);
-      l.branch = (int)(std::min_element(load, load + nb) - load);
-      load[l.branch] += l.cost;
+      l.branch = branch[li];
       l.scratch_off = scratch_doubles;
       scratch_doubles += l.scratch_per_cta / sizeof(double) * (size_t)l.ctas;
       p->ctas += l.ctas;
