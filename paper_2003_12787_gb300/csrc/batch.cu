@@ -1,15 +1,16 @@
-// Batched persistent FP64 STP: element sets of different orders and sizes in
-// one launch, replayed from a captured CUDA graph, with shapes picked by an
-// on-device autotuner.
+// Batched persistent FP64 STP: element sets of different orders and sizes,
+// replayed from a captured CUDA graph, with shapes picked by an on-device
+// autotuner.
 //
 // The paper's Kernel Generator tailors each kernel to its order at build time
 // (Sec. II-D: generated, order-specific kernels; Sec. III: padding and
-// alignment chosen per order). Here every order's kernel body is compiled
-// into one persistent kernel; a work list of (set, element range) units,
-// sorted by estimated cost (longest first), is consumed by one CTA per SM
-// through an atomic counter, and each unit runs the FP64 element-group body of
-// its order with the (nodes per thread, elements per CTA) shape that the
-// autotuner measured fastest for that order on this device.
+// alignment chosen per order). Here every shape (order and CTA layout) is a
+// persistent kernel of its own with the FP64 element body inlined; a plan
+// groups the sets by shape, and each group's launch consumes its (set,
+// element range) units through an atomic counter, the sets' descriptors
+// travelling in a kernel-parameter table. The groups' launches, longest
+// first, share the GPU over parallel graph branches; each order runs the
+// shape the autotuner measured fastest for it on this device.
 #include <algorithm>
 #include <cmath>
 #include <cstring>

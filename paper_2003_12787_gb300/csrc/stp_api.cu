@@ -684,7 +684,7 @@ struct BatchSetSources {
 };
 
 struct stp_batch_s {
-  stp::BatchPlan* plan = nullptr;   // all sets FP64: one persistent launch
+  stp::BatchPlan* plan = nullptr;   // all sets FP64: per-shape persistent launches
   cudaGraph_t graph = nullptr;      // otherwise: one launch per set, parallel branches
   cudaGraphExec_t exec = nullptr;
   int nsets = 0;
@@ -817,7 +817,7 @@ stp_status batch_create_impl(int nsets, const stp_batch_set* sets, const int* sh
                                                  " overlap buffers of set " + std::to_string(j));
     }
   }
-  // the persistent kernel holds the FP64 bodies, Cartesian and curvilinear
+  // the persistent kernels hold the FP64 bodies, Cartesian and curvilinear
   bool all_fp64 = true;
   for (int i = 0; i < nsets; ++i)
     if (sets[i].handle->precision != STP_PRECISION_FP64) all_fp64 = false;
