@@ -4,6 +4,7 @@
 // tests compile them on their own.
 #pragma once
 #include <cstddef>
+#include <cstdint>
 #include <vector>
 
 namespace stp {
@@ -61,6 +62,32 @@ void ready_order(const Sims& sims, const Ready& ready, int policy, double now, d
     if (!aged(i) && sims[i].resident) out->push_back(i);
   for (int i : ready)
     if (!aged(i) && !sims[i].resident) out->push_back(i);
+}
+
+// Estimated FP64 work of one STP step, in milliseconds at 1.2 TFLOP/s: E
+// elements with N nodes per direction, a curvilinear element counted 1.7
+// times a Cartesian one (every quantity is differentiated along every
+// direction).
+inline double step_work_ms(int N, int64_t E, bool curvilinear) {
+  const double n = N;
+  const double flops = 36.0 * n * n * n * n * n + 66.0 * n * n * n * n + 108.0 * n * n * n;
+  return (curvilinear ? 1.7 : 1.0) * (double)E * flops / 1.2e9;
+}
+
+// Launch form of each FP64 simulation of a batch: 1 = the per-shape
+// persistent launches, 0 = the one allocation-free launch. A batch with more
+// than `threshold_ms` of work runs per shape as a whole; an N = 12 Cartesian
+// simulation always does (there the allocation-free kernel's body differs
+// from the single-set kernel's, and a simulation must round the same in
+// every batch).
+inline std::vector<char> launch_forms(const std::vector<int>& N, const std::vector<int64_t>& E,
+                                      const std::vector<char>& curvilinear, double threshold_ms) {
+  double work = 0.0;
+  for (size_t k = 0; k < N.size(); ++k) work += step_work_ms(N[k], E[k], curvilinear[k] != 0);
+  std::vector<char> out(N.size(), 0);
+  for (size_t k = 0; k < N.size(); ++k)
+    out[k] = (work > threshold_ms || (N[k] == 12 && !curvilinear[k])) ? 1 : 0;
+  return out;
 }
 
 }  // namespace stp

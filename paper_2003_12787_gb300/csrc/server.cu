@@ -317,15 +317,11 @@ struct Server {
       // as the one allocation-free launch, which costs a single launch. N = 12 Cartesian simulations
       // always take the per-shape launch, whose body is the single-set
       // kernel's, so each simulation rounds the same in every batch.
-      double work_ms = 0.0;
-      for (size_t k = 0; k < N.size(); ++k) {
-        const double n = N[k];
-        work_ms += (mt[k] ? 1.7 : 1.0) * (double)E[k] *
-                   (36.0 * n * n * n * n * n + 66.0 * n * n * n * n + 108.0 * n * n * n) / 1.2e9;
-      }
+      std::vector<char> curv(N.size());
+      for (size_t k = 0; k < N.size(); ++k) curv[k] = mt[k] != nullptr;
+      const std::vector<char> form = launch_forms(N, E, curv, 50.0);
       std::vector<size_t> direct, shaped;  // allocation-free launch / per-shape launches
-      for (size_t k = 0; k < N.size(); ++k)
-        (work_ms > 50.0 || (N[k] == 12 && !mt[k]) ? shaped : direct).push_back(k);
+      for (size_t k = 0; k < N.size(); ++k) (form[k] ? shaped : direct).push_back(k);
       int too_big = 0;
       e = cudaEventRecord(sl.start, sl.stream);
       for (int pass = 0; pass < 2 && e == cudaSuccess; ++pass) {

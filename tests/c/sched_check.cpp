@@ -125,6 +125,47 @@ int main() {
     }
     ++cases;
   }
+  // launch forms: the flop count of one element written out per order, the
+  // batch's work against the threshold, and the N = 12 Cartesian rule
+  {
+    const double fl4 = 36.0 * 1024 + 66.0 * 256 + 108.0 * 64;  // N = 4
+    const double got = stp::step_work_ms(4, 1000, false), want = 1000 * fl4 / 1.2e9;
+    if (got < want * (1 - 1e-12) || got > want * (1 + 1e-12)) {
+      std::printf("mismatch: step work N=4 %g vs %g\n", got, want);
+      return 1;
+    }
+    const double gc = stp::step_work_ms(4, 1000, true);
+    if (gc < 1.7 * want * (1 - 1e-12) || gc > 1.7 * want * (1 + 1e-12)) {
+      std::printf("mismatch: curvilinear step work\n");
+      return 1;
+    }
+    ++cases;
+  }
+  for (int t = 0; t < 20000; ++t) {
+    const int n = 1 + (int)(next_u64() % 10);
+    std::vector<int> N((size_t)n);
+    std::vector<int64_t> E((size_t)n);
+    std::vector<char> curv((size_t)n);
+    double work = 0.0;
+    for (int j = 0; j < n; ++j) {
+      N[(size_t)j] = 1 + (int)(next_u64() % 12);
+      E[(size_t)j] = 1 + (int64_t)(next_u64() % 3000);
+      curv[(size_t)j] = next_u64() % 3 == 0;
+      const double m = N[(size_t)j];
+      work += (curv[(size_t)j] ? 1.7 : 1.0) * (double)E[(size_t)j] *
+              (36 * m * m * m * m * m + 66 * m * m * m * m + 108 * m * m * m) / 1.2e9;
+    }
+    const double thr = (double)(next_u64() % 80);
+    const std::vector<char> got = stp::launch_forms(N, E, curv, thr);
+    for (int j = 0; j < n; ++j) {
+      const bool want = work > thr || (N[(size_t)j] == 12 && !curv[(size_t)j]);
+      if ((got[(size_t)j] != 0) != want) {
+        std::printf("mismatch: launch form (case %d, set %d)\n", t, j);
+        return 1;
+      }
+    }
+    ++cases;
+  }
   std::printf("ok %d\n", cases);
   return 0;
 }

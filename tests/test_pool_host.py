@@ -3,8 +3,8 @@ first-fit device-pool sub-allocator (csrc/pool.h), checked by
 tests/c/pool_check.cpp against a byte map of the pool under seeded random
 allocations and releases (first-fit offsets, no overlap, alignment, used
 bytes, full merge on release); and the scheduler's policy rules
-(csrc/serve_policy.h: eviction victim, half-pool batch bound), checked by
-tests/c/sched_check.cpp."""
+(csrc/serve_policy.h: eviction victim, half-pool batch bound, ready order,
+the launch form of a batch), checked by tests/c/sched_check.cpp."""
 from __future__ import annotations
 
 import os
@@ -89,6 +89,11 @@ SCHED_MUTANTS = {
     "resident ones last": ("if (!aged(i) && sims[i].resident) out->push_back(i);\n  for (int i : ready)\n    if (!aged(i) && !sims[i].resident)",
                            "if (!aged(i) && !sims[i].resident) out->push_back(i);\n  for (int i : ready)\n    if (!aged(i) && sims[i].resident)"),
     "FIFO policy reordered": ("if (policy == 0) {", "if (policy == 2) {"),
+    "N = 12 rule dropped": ("(work > threshold_ms || (N[k] == 12 && !curvilinear[k]))", "(work > threshold_ms)"),
+    "threshold compared the wrong way": ("(work > threshold_ms ||", "(work < threshold_ms ||"),
+    "curvilinear weight missing": ("(curvilinear ? 1.7 : 1.0)", "1.0"),
+    "per-set instead of per-batch work": ("out[k] = (work > threshold_ms ||",
+                                          "out[k] = (step_work_ms(N[k], E[k], curvilinear[k] != 0) > threshold_ms ||"),
 }
 
 
